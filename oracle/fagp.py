@@ -1,0 +1,344 @@
+"""Plain FP64 CPU oracle for the decomposed-kernel (FAGP) Gaussian process.
+
+TEST INFRASTRUCTURE ONLY. This module is the slow, obviously correct
+definition that the CUDA path is checked against. Only the test suite, the
+package's ``smoke()`` check and the CPU-baseline leg of the benchmark may
+import it; the library itself never does, and this module imports nothing
+from the library.
+
+Everything is float64 numpy. Library primitives used as single steps: the
+matrix product (numpy ``@``), the Cholesky factorisation
+(``numpy.linalg.cholesky``), triangular solves (``scipy.linalg``) and the
+symmetric tridiagonal eigenvalues (``numpy.linalg.eigvalsh``, for Golub-Welsch).
+
+Notation follows the paper: eps = epsilon (SE shape parameter, Eq. 13),
+rho = the global scale factor of the eigen-decomposition (Eq. 14-16; the
+library's ``alpha`` argument), sigma2 = sigma^2 (noise variance, Eq. 1),
+n eigenfunctions per input dimension, p input dimensions, M = n**p
+tensor-product columns (Eq. 19-20).
+
+Readings of the paper taken here (each is pinned by a test):
+  * delta^2 = rho^2 (beta^2 - 1) / 2.  Eq. 14 prints rho/2 (beta^2 - 1); only
+    the rho^2 form makes the Mercer sum (Eq. 5) converge to the SE kernel and
+    the eigenfunctions orthonormal when rho != 1.
+  * H_k in Eq. 15 are the physicists' Hermite polynomials (H_1(t) = 2t); only
+    those are normalised by the gamma_i of Eq. 14.
+  * The multi-index set of Eq. 18 is the full grid {0..n-1}^p; column
+    m = sum_j m_j n^(p-1-j) (last dimension fastest).
+  * The predictive variance is the diagonal of Sigma_* of Eq. 12 (latent f,
+    no added noise), with prior mean zero (Sec. 2.1).
+  * sigma^2 / lambda_m is clamped at 1e200 (CLAMP_D) so that eigenvalues
+    that underflow stay finite; columns that hit the clamp contribute below
+    1e-180 relative.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional
+
+import numpy as np
+import scipy.linalg as sla
+
+# Degree up to which the eigenfunctions are evaluated with the literal
+# physicists' Hermite recurrence times gamma_i (Eq. 14-15). Beyond it H_k(t)
+# overflows float64, and the algebraically identical normalised recurrence
+# (see eigenfunctions_1d) is used instead.
+LITERAL_MAX_N = 100
+
+# Upper bound on sigma^2 / lambda_m (reading A5).
+CLAMP_D = 1e200
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3: one-dimensional SE eigenpairs
+# --------------------------------------------------------------------------
+
+def se_constants(eps: float, rho: float):
+    """beta and delta^2 of Eq. 14 (delta^2 with the rho^2 reading)."""
+    beta = (1.0 + (2.0 * eps / rho) ** 2) ** 0.25
+    delta2 = rho ** 2 / 2.0 * (beta ** 2 - 1.0)
+    return beta, delta2
+
+
+def gamma_coeffs(n: int, beta: float) -> np.ndarray:
+    """gamma_i = sqrt(beta / (2^(i-1) Gamma(i))), i = 1..n (Eq. 14).
+
+    Evaluated through log-gamma so that large i does not overflow.
+    """
+    i = np.arange(1, n + 1, dtype=np.float64)
+    lg = np.array([math.lgamma(v) for v in i])
+    return np.exp(0.5 * (math.log(beta) - (i - 1.0) * math.log(2.0) - lg))
+
+
+def hermite_phys(n: int, t: np.ndarray) -> np.ndarray:
+    """Physicists' Hermite polynomials H_0..H_{n-1} at t, shape t.shape + (n,).
+
+    Three-term recurrence H_0 = 1, H_1 = 2t, H_{k+1} = 2t H_k - 2k H_{k-1}.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    H = np.empty(t.shape + (n,), dtype=np.float64)
+    H[..., 0] = 1.0
+    if n > 1:
+        H[..., 1] = 2.0 * t
+    for k in range(1, n - 1):
+        H[..., k + 1] = 2.0 * t * H[..., k] - 2.0 * k * H[..., k - 1]
+    return H
+
+
+def eigenvalues_1d(n: int, eps: float, rho: float) -> np.ndarray:
+    """lambda_i, i = 1..n, of Eq. 16 (may underflow to 0 for large i)."""
+    return np.exp(log_eigenvalues_1d(n, eps, rho))
+
+
+def log_eigenvalues_1d(n: int, eps: float, rho: float) -> np.ndarray:
+    """log lambda_i of Eq. 16:
+    lambda_i = sqrt(rho^2 / D) * (eps^2 / D)^(i-1),  D = rho^2 + delta^2 + eps^2.
+    """
+    _, delta2 = se_constants(eps, rho)
+    D = rho ** 2 + delta2 + eps ** 2
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return 0.5 * math.log(rho ** 2 / D) + (i - 1.0) * math.log(eps ** 2 / D)
+
+
+def eigenfunctions_1d(x: np.ndarray, n: int, eps: float, rho: float) -> np.ndarray:
+    """phi_i(x) = gamma_i exp(-delta^2 x^2) H_{i-1}(rho beta x), i = 1..n (Eq. 15).
+
+    Returns shape x.shape + (n,). For n <= LITERAL_MAX_N the literal product
+    gamma_i * H_{i-1} is used. For larger n, gamma_i H_{i-1}(t) is computed by
+    the recurrence it satisfies (divide the Hermite recurrence by
+    sqrt(2^k k!)): with q_k = gamma_{k+1} H_k(t),
+        q_0 = sqrt(beta), q_1 = sqrt(2) t q_0,
+        q_{k+1} = sqrt(2/(k+1)) t q_k - sqrt(k/(k+1)) q_{k-1},
+    which is the same quantity without the overflow of H_k.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    beta, delta2 = se_constants(eps, rho)
+    t = rho * beta * x
+    env = np.exp(-delta2 * x * x)
+    if n <= LITERAL_MAX_N:
+        q = hermite_phys(n, t) * gamma_coeffs(n, beta)
+    else:
+        q = np.empty(x.shape + (n,), dtype=np.float64)
+        q[..., 0] = math.sqrt(beta)
+        if n > 1:
+            q[..., 1] = math.sqrt(2.0) * t * q[..., 0]
+        for k in range(1, n - 1):
+            q[..., k + 1] = (math.sqrt(2.0 / (k + 1)) * t * q[..., k]
+                             - math.sqrt(k / (k + 1.0)) * q[..., k - 1])
+    return q * env[..., None]
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3: tensor-product (multi-index) eigenpairs, Eq. 18-20
+# --------------------------------------------------------------------------
+
+def multi_index(n: int, p: int) -> np.ndarray:
+    """All n^p multi-indices (m_1..m_p), 0-based, as an (M, p) int array.
+
+    Row m holds the digits of m in base n, most significant first, so the
+    last dimension varies fastest.
+    """
+    grids = np.indices((n,) * p).reshape(p, -1).T
+    return np.ascontiguousarray(grids, dtype=np.int64)
+
+
+def log_eigenvalues(n: int, p: int, eps: float, rho: float) -> np.ndarray:
+    """log lambda_m = sum_j log lambda_{m_j} (Eq. 20, isotropic eps and rho)."""
+    l1 = log_eigenvalues_1d(n, eps, rho)
+    return l1[multi_index(n, p)].sum(axis=1)
+
+
+def phi_matrix(X: np.ndarray, n: int, eps: float, rho: float) -> np.ndarray:
+    """Phi[i, m] = prod_j phi_{m_j}(x_ij) (Eq. 19), shape (N, n^p)."""
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    N, p = X.shape
+    idx = multi_index(n, p)
+    Phi = np.ones((N, idx.shape[0]), dtype=np.float64)
+    for j in range(p):
+        E = eigenfunctions_1d(X[:, j], n, eps, rho)      # (N, n)
+        Phi *= E[:, idx[:, j]]
+    return Phi
+
+
+def kernel_approx(X1: np.ndarray, X2: np.ndarray, n: int, eps: float, rho: float) -> np.ndarray:
+    """Truncated Mercer kernel Phi(X1) Lambda Phi(X2)^T (Eq. 6-7)."""
+    P1 = phi_matrix(X1, n, eps, rho)
+    P2 = phi_matrix(X2, n, eps, rho)
+    p = np.atleast_2d(X1).shape[1]
+    lam = np.exp(log_eigenvalues(n, p, eps, rho))
+    return (P1 * lam) @ P2.T
+
+
+def kernel_se(X1: np.ndarray, X2: np.ndarray, eps: float) -> np.ndarray:
+    """The SE kernel exp(-eps^2 |x - x'|^2) (Eq. 13, Eq. 17 with eps_j = eps)."""
+    X1 = np.atleast_2d(X1)
+    X2 = np.atleast_2d(X2)
+    d2 = ((X1[:, None, :] - X2[None, :, :]) ** 2).sum(axis=2)
+    return np.exp(-eps ** 2 * d2)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: fit and predict in the M x M (Woodbury) form
+# --------------------------------------------------------------------------
+
+def noise_diagonal(n: int, p: int, eps: float, rho: float, sigma2: float) -> np.ndarray:
+    """d_m = sigma^2 / lambda_m, clamped at CLAMP_D (the sigma^2 Lambda^{-1} of A)."""
+    logd = math.log(sigma2) - log_eigenvalues(n, p, eps, rho)
+    return np.where(logd >= math.log(CLAMP_D), CLAMP_D,
+                    np.exp(np.minimum(logd, math.log(CLAMP_D))))
+
+
+def gram(X: np.ndarray, y: np.ndarray, n: int, eps: float, rho: float,
+         row_block: int = 16384):
+    """G = Phi^T Phi and b = Phi^T y.
+
+    Both are sums over training points (G = sum_i phi(x_i) phi(x_i)^T), taken
+    here over consecutive blocks of rows so that Phi need not be held whole.
+    """
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    y = np.asarray(y, dtype=np.float64)
+    N, p = X.shape
+    M = n ** p
+    G = np.zeros((M, M), dtype=np.float64)
+    b = np.zeros(M, dtype=np.float64)
+    for r0 in range(0, N, row_block):
+        P = phi_matrix(X[r0:r0 + row_block], n, eps, rho)
+        G += P.T @ P
+        b += P.T @ y[r0:r0 + row_block]
+    return G, b
+
+
+def fit(X: np.ndarray, y: np.ndarray, n: int, eps: float, rho: float, sigma2: float,
+        row_block: int = 16384) -> Dict[str, np.ndarray]:
+    """Fit in the M x M form derived from Eq. 10-12.
+
+    With Sigma_n = sigma^2 I, Lambda-bar = Lambda^{-1} + Phi^T Phi / sigma^2
+    (Sec. 2.2). Multiplying by sigma^2 gives A = sigma^2 Lambda-bar
+    = Phi^T Phi + sigma^2 Lambda^{-1}. Substituting into W of Eq. 11 reduces
+    it to W = Phi_* A^{-1} Phi^T, so mu_* = Phi_* c with c = A^{-1} Phi^T y.
+    A is symmetric positive definite, so it is factored A = L L^T.
+    """
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    N, p = X.shape
+    G, b = gram(X, y, n, eps, rho, row_block)
+    d = noise_diagonal(n, p, eps, rho, sigma2)
+    A = G + np.diag(d)
+    L = np.linalg.cholesky(A)
+    w = sla.solve_triangular(L, b, lower=True)
+    c = sla.solve_triangular(L.T, w, lower=False)
+    return dict(G=G, b=b, d=d, A=A, L=L, c=c, n=n, p=p, eps=eps, rho=rho, sigma2=sigma2)
+
+
+def predict(model: Dict[str, np.ndarray], Xs: np.ndarray, row_block: int = 16384):
+    """Predictive mean and variance at Xs (Eq. 11-12 in the M x M form).
+
+    mu_* = Phi_* c.  The diagonal of Sigma_* of Eq. 12 reduces, with the
+    substitution used in ``fit``, to sigma^2 Phi_* A^{-1} Phi_*^T, so
+    var_i = sigma^2 |L^{-1} phi(x*_i)|^2.
+    """
+    Xs = np.atleast_2d(np.asarray(Xs, dtype=np.float64))
+    Ns = Xs.shape[0]
+    mean = np.empty(Ns)
+    var = np.empty(Ns)
+    for r0 in range(0, Ns, row_block):
+        Ps = phi_matrix(Xs[r0:r0 + row_block], model["n"], model["eps"], model["rho"])
+        mean[r0:r0 + row_block] = Ps @ model["c"]
+        V = sla.solve_triangular(model["L"], Ps.T, lower=True)
+        var[r0:r0 + row_block] = model["sigma2"] * np.sum(V * V, axis=0)
+    return mean, var
+
+
+# --------------------------------------------------------------------------
+# Other routes to the same posterior (used to pin the M x M form)
+# --------------------------------------------------------------------------
+
+def posterior_nxn(X, y, Xs, n, eps, rho, sigma2):
+    """Eq. 8-9 directly: the N x N GP posterior with the truncated kernel.
+
+    K = Phi Lambda Phi^T + sigma^2 I is N x N; only for small N.
+    Returns (mean, diagonal of Sigma_*).
+    """
+    Kxx = kernel_approx(X, X, n, eps, rho)
+    Ksx = kernel_approx(Xs, X, n, eps, rho)
+    Kss = kernel_approx(Xs, Xs, n, eps, rho)
+    Kt = Kxx + sigma2 * np.eye(Kxx.shape[0])
+    mean = Ksx @ np.linalg.solve(Kt, y)
+    cov = Kss - Ksx @ np.linalg.solve(Kt, Ksx.T)
+    return mean, np.diag(cov).copy()
+
+
+def posterior_fagp_w(X, y, Xs, n, eps, rho, sigma2):
+    """Eq. 11-12 with the explicit W and Lambda-bar of Sec. 2.2 (Woodbury, Eq. 10).
+
+    Forms the N_* x N matrix W; only for small sizes.
+    """
+    X = np.atleast_2d(X)
+    p = X.shape[1]
+    Phi = phi_matrix(X, n, eps, rho)
+    Phis = phi_matrix(Xs, n, eps, rho)
+    lam = np.exp(log_eigenvalues(n, p, eps, rho))
+    Lam = np.diag(lam)
+    N = Phi.shape[0]
+    Sinv = np.eye(N) / sigma2                       # Sigma_N^{-1}
+    Lbar = np.diag(1.0 / lam) + Phi.T @ Sinv @ Phi  # Lambda-bar
+    W = Phis @ Lam @ Phi.T @ (Sinv - Sinv @ Phi @ np.linalg.solve(Lbar, Phi.T @ Sinv))
+    mean = W @ y
+    cov = Phis @ Lam @ Phis.T - W @ Phi @ Lam @ Phis.T
+    return mean, np.diag(cov).copy()
+
+
+def posterior_exact_se(X, y, Xs, eps, sigma2):
+    """Eq. 3-4 with the true SE kernel (no truncation), zero prior mean."""
+    K = kernel_se(X, X, eps) + sigma2 * np.eye(np.atleast_2d(X).shape[0])
+    Ks = kernel_se(Xs, X, eps)
+    Kss = kernel_se(Xs, Xs, eps)
+    mean = Ks @ np.linalg.solve(K, y)
+    cov = Kss - Ks @ np.linalg.solve(K, Ks.T)
+    return mean, np.diag(cov).copy()
+
+
+def prior_variance(Xs, n, eps, rho):
+    """diag(Phi_* Lambda Phi_*^T): the truncated prior variance (first term of Eq. 12)."""
+    Xs = np.atleast_2d(Xs)
+    Ps = phi_matrix(Xs, n, eps, rho)
+    lam = np.exp(log_eigenvalues(n, Xs.shape[1], eps, rho))
+    return (Ps * Ps) @ lam
+
+
+# --------------------------------------------------------------------------
+# Gauss-Hermite quadrature by Golub-Welsch (used to check orthonormality)
+# --------------------------------------------------------------------------
+
+def gauss_hermite(K: int):
+    """Nodes and weights of K-point Gauss-Hermite quadrature (weight e^{-t^2}).
+
+    Golub-Welsch: the nodes are the eigenvalues of the symmetric tridiagonal
+    Jacobi matrix of the monic Hermite recurrence (zero diagonal, off-diagonal
+    sqrt(k/2), k = 1..K-1). The weights are the Christoffel numbers
+    w_k = 1 / sum_{j<K} p_j(t_k)^2 with p_j the orthonormal Hermite
+    polynomials (p_j = H_j / sqrt(sqrt(pi) 2^j j!)); this equals sqrt(pi)
+    times the squared first eigenvector component, but keeps full relative
+    accuracy for the tiny outer weights.
+    """
+    J = np.zeros((K, K))
+    for k in range(1, K):
+        J[k - 1, k] = J[k, k - 1] = math.sqrt(k / 2.0)
+    t = np.linalg.eigvalsh(J)
+    # orthonormal recurrence: p_0 = pi^{-1/4}, p_1 = sqrt(2) t p_0,
+    # p_{j+1} = sqrt(2/(j+1)) t p_j - sqrt(j/(j+1)) p_{j-1}
+    s = np.zeros_like(t)
+    pm1 = np.zeros_like(t)
+    pj = np.full_like(t, math.pi ** -0.25)
+    for j in range(K):
+        s += pj * pj
+        pn = math.sqrt(2.0 / (j + 1)) * t * pj - math.sqrt(j / (j + 1.0)) * pm1
+        pm1, pj = pj, pn
+    return t, 1.0 / s
+
+
+def relerr(a: np.ndarray, ref: np.ndarray) -> float:
+    """Relative L2 error |a - ref|_2 / |ref|_2."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = float(np.linalg.norm(ref))
+    return float(np.linalg.norm(a - ref)) / (den if den > 0 else 1.0)
