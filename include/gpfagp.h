@@ -1,0 +1,185 @@
+/*
+ * gpfagp.h -- C ABI of the GB300 decomposed-kernel (FAGP) Gaussian process.
+ *
+ * The library fits and evaluates the Gaussian-process posterior of Sec. 2.2
+ * of "Parallel Gaussian Process with Kernel Approximation in CUDA"
+ * (arXiv 2403.12797) with the squared-exponential kernel expanded in its
+ * Hermite eigenfunctions (Sec. 2.3, Eq. 14-16), taken as a tensor product
+ * over the p input dimensions (Eq. 18-20): M = n^p basis columns.
+ *
+ *   fit:      Phi (N x M, never stored), A = Phi^T Phi + sigma^2 Lambda^{-1},
+ *             b = Phi^T y, A = L L^T, c = A^{-1} b          (Eq. 10-12, Woodbury form)
+ *   predict:  mean_i = phi(x*_i)^T c,
+ *             var_i  = sigma^2 |L^{-1} phi(x*_i)|^2           (diagonal of Eq. 12)
+ *
+ * Conventions shared by every entry point
+ *  - X and X* are row-major (N x p), (Ns x p) float64; y, mean, var float64.
+ *  - alpha is the eigen-decomposition's global scale factor (rho, Sec. 2.3);
+ *    eps the SE shape parameter (epsilon, Eq. 13); sigma2 the noise
+ *    variance (sigma^2, Eq. 1). One eps and one alpha serve all dimensions.
+ *  - The column order of Phi is m = sum_j m_j n^(p-1-j) (last dimension
+ *    fastest); results do not depend on it.
+ *  - Ownership: the caller owns every array it passes; the library copies
+ *    what it needs and keeps no caller pointer after a call returns. A
+ *    gp_model is owned by the library until gp_free.
+ *  - Errors: every int-returning call returns GP_OK (0) or a negative
+ *    status; gp_last_error() returns the calling thread's last status and
+ *    gp_last_error_detail() an integer detail (the failing pivot column for
+ *    GP_ENOTPD, the CUDA error code for GP_ECUDA). No call traps or aborts.
+ *  - Streams: the _ex variants take a cudaStream_t (NULL = the legacy
+ *    default stream). With dev_ptrs = 1 all array arguments are device
+ *    pointers and the call is asynchronous with respect to the host except
+ *    for the final status read back (one 8-byte device-to-host copy);
+ *    with dev_ptrs = 0 they are host pointers and the call returns after
+ *    the results are in host memory.
+ *  - Thread safety: a fitted gp_model is immutable; concurrent predicts on
+ *    the same model (on different streams) are safe.
+ */
+#ifndef GPFAGP_H
+#define GPFAGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GPFAGP_API __attribute__((visibility("default")))
+#else
+#define GPFAGP_API
+#endif
+
+typedef struct gp_model gp_model;
+
+/* ---- status codes ------------------------------------------------------- */
+#define GP_OK        0
+#define GP_EINVAL   (-1)  /* bad argument: N<1, p<1, n<1, p>32, M=n^p > GP_MAX_M,
+                             non-finite or non-positive eps/alpha/sigma2,
+                             NaN/Inf in X, y or X* (detected on the device)   */
+#define GP_ENOMEM   (-2)  /* a device allocation failed                       */
+#define GP_ENOTPD   (-3)  /* A is not numerically positive definite; detail =
+                             first failing pivot column                         */
+#define GP_ECUDA    (-4)  /* a CUDA runtime call failed; detail = cudaError_t  */
+#define GP_ETIMEOUT (-5)  /* a bounded device-side wait ran out (pipeline
+                             barrier of a tensor-core kernel)                   */
+#define GP_ENODEV   (-6)  /* no usable sm_103 device                           */
+
+/* ---- precision modes ---------------------------------------------------- */
+/* GP_PREC_FP64:   every step in float64 on the CUDA cores.
+ * GP_PREC_BF16X3: Phi generated in float32 and split into bf16 hi + lo; the
+ *                 contractions Phi^T Phi and Phi_* L^{-T} run on the tensor
+ *                 cores as hi*hi + hi*lo + lo*hi with float32 accumulation;
+ *                 Phi^T y and the predictive mean use float32 products;
+ *                 split-N partials are summed, A assembled, factored and
+ *                 inverted, and c solved and refined, in float64.           */
+#define GP_PREC_FP64    0
+#define GP_PREC_BF16X3  3
+
+/* Largest supported M = n^p (the M x M float64 factor must fit in memory). */
+#define GP_MAX_M  32768
+
+/* ---- spec entry points -------------------------------------------- */
+
+/* Fit the posterior of Sec. 2.2 on host arrays X (N x p) and y (N), in the
+ * GP_PREC_BF16X3 mode on the current device and the legacy default stream.
+ * Returns a model handle, or NULL on failure (gp_last_error() tells why). */
+GPFAGP_API gp_model* gp_fit(const double* X, const double* y, int64_t N, int p, int n,
+                            double eps, double alpha, double sigma2);
+
+/* Predictive mean and variance (Eq. 11-12, diagonal) at Ns host points Xs
+ * (Ns x p) into host arrays mean (Ns) and var (Ns). var may be NULL (the
+ * variance is then not computed). Ns = 0 is a no-op. */
+GPFAGP_API int gp_predict(const gp_model* h, const double* Xs, int64_t Ns,
+                          double* mean, double* var);
+
+/* Release a model (NULL is a no-op). Synchronises the model's device. */
+GPFAGP_API void gp_free(gp_model* h);
+
+GPFAGP_API int gp_last_error(void);
+GPFAGP_API int64_t gp_last_error_detail(void);
+GPFAGP_API const char* gp_strerror(int status);
+
+/* ---- extended entry points ---------------------------------------------- */
+
+/* gp_fit with an explicit precision mode, stream and pointer kind.
+ * On GP_OK *out receives the model. */
+GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int n,
+                         double eps, double alpha, double sigma2, int prec,
+                         void* cuda_stream, int dev_ptrs, gp_model** out);
+
+/* gp_predict with an explicit stream and pointer kind. The prediction uses
+ * the model's precision mode. */
+GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
+                             double* mean, double* var, void* cuda_stream, int dev_ptrs);
+
+/* Model shape and mode: any output pointer may be NULL. */
+GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
+
+/* Copy a fitted quantity of the model to host memory, in float64.
+ *   GP_FIELD_L: the Cholesky factor L (M x M row-major, lower; upper = 0)
+ *   GP_FIELD_C: c = A^{-1} b (M)
+ *   GP_FIELD_B: b = Phi^T y (M)
+ *   GP_FIELD_D: the diagonal sigma^2 / lambda_m (clamped at 1e200) (M)
+ * dst must hold M*M (L) or M (others) doubles. */
+#define GP_FIELD_L 1
+#define GP_FIELD_C 2
+#define GP_FIELD_B 3
+#define GP_FIELD_D 4
+GPFAGP_API int gp_model_read(const gp_model* h, int field, double* dst);
+
+/* The fused Phi generation + contraction step on its own (Sec. 2.2: the
+ * Phi^T Sigma_n^{-1} Phi and Phi^T y products of Lambda-bar and W):
+ * G = Phi^T Phi (M x M, full symmetric, row-major) and b = Phi^T y (M),
+ * in float64, computed in mode prec. Pointer kind as in gp_fit_ex. */
+GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, int n,
+                          double eps, double alpha, int prec, double* G, double* b,
+                          void* cuda_stream, int dev_ptrs);
+
+/* ---- batched fit -------------------------------------------------------- */
+
+/* One independent problem of a batched fit. Pointer kind as in the call. */
+typedef struct gp_fit_args {
+    const double* X;   /* N x p */
+    const double* y;   /* N     */
+    int64_t N;
+    int p, n;
+    double eps, alpha, sigma2;
+} gp_fit_args;
+
+/* Fit `count` independent problems of uneven N, p and n. The contraction of
+ * all problems runs as ONE persistent launch over a shared work list; the
+ * float64 factorisations run batched. out[i] receives problem i's model
+ * (or NULL); the return value is GP_OK when every problem succeeded, else
+ * the first failing problem's status (gp_last_error_detail() = its index).
+ * Each model is the same as the one gp_fit_ex would produce on its own. */
+GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec,
+                            void* cuda_stream, int dev_ptrs, gp_model** out);
+
+/* One predict request of a batched predict. */
+typedef struct gp_predict_args {
+    const gp_model* model;
+    const double* Xs;  /* Ns x p */
+    int64_t Ns;
+    double* mean;      /* Ns */
+    double* var;       /* Ns, or NULL */
+} gp_predict_args;
+
+/* Run `count` predict requests against (possibly different) models as one
+ * persistent launch per precision mode. Device pointers only. Each result
+ * is bitwise the same as gp_predict_ex on that request alone. */
+GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream);
+
+/* ---- test hooks ----------------------------------------------------------- */
+
+/* Make the k-th device allocation from now fail with GP_ENOMEM (k >= 1);
+ * k = 0 disarms. For error-path tests. */
+GPFAGP_API void gp_debug_fail_alloc_after(int k);
+
+/* Library build tag (static string). */
+GPFAGP_API const char* gp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPFAGP_H */

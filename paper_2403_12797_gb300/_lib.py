@@ -1,0 +1,277 @@
+"""ctypes binding of ``libgpfagp.so`` (the C ABI declared in ``include/gpfagp.h``).
+
+Argument marshalling only: every step of fit and predict runs in the
+library's CUDA kernels. Arrays may be numpy float64 (host pointers; the
+library copies) or torch float64 CUDA tensors (device pointers; the call
+runs on torch's current stream). Loading fails loudly if the library has
+not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_ENODEV = 0, -1, -2, -3, -4, -5, -6
+PREC = {"fp64": 0, "bf16x3": 3}
+FIELD = {"L": 1, "c": 2, "b": 3, "d": 4}
+
+HEADER = os.path.join(_build.ROOT, "include", "gpfagp.h")
+
+_lib: Optional[C.CDLL] = None
+
+
+class GPError(RuntimeError):
+    def __init__(self, status: int, detail: int, where: str):
+        self.status = status
+        self.detail = detail
+        super().__init__(f"{where}: {strerror(status)} (status {status}, detail {detail})")
+
+
+class FitArgs(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("y", C.c_void_p), ("N", C.c_int64), ("p", C.c_int),
+                ("n", C.c_int), ("eps", C.c_double), ("alpha", C.c_double), ("sigma2", C.c_double)]
+
+
+class PredictArgs(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("Xs", C.c_void_p), ("Ns", C.c_int64),
+                ("mean", C.c_void_p), ("var", C.c_void_p)]
+
+
+def declared_symbols() -> List[str]:
+    """Names of the entry points declared in include/gpfagp.h."""
+    txt = open(HEADER).read()
+    return re.findall(r"GPFAGP_API\s+[\w\s\*]+?\b(gp_\w+)\s*\(", txt)
+
+
+def lib(build: bool = True) -> C.CDLL:
+    """Load (building first if stale and ``build``) the shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libgpfagp.so not found at {path}: build it with "
+                          "python -m paper_2403_12797_gb300.build")
+    L = C.CDLL(path)
+    vp, i64, d, i = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    sig = {
+        "gp_fit": (vp, [vp, vp, i64, i, i, d, d, d]),
+        "gp_predict": (i, [vp, vp, i64, vp, vp]),
+        "gp_free": (None, [vp]),
+        "gp_last_error": (i, []),
+        "gp_last_error_detail": (i64, []),
+        "gp_strerror": (C.c_char_p, [i]),
+        "gp_fit_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
+        "gp_predict_ex": (i, [vp, vp, i64, vp, vp, vp, i]),
+        "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "gp_model_read": (i, [vp, i, vp]),
+        "gp_gram_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, vp, i]),
+        "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
+        "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
+        "gp_debug_fail_alloc_after": (None, [i]),
+        "gp_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return lib().gp_strerror(int(status)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != GP_OK:
+        raise GPError(rc, int(lib().gp_last_error_detail()), where)
+
+
+# ------------------------------------------------------------------ array marshalling
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _host(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a) -> int:
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_of(a, stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream)
+    if _is_torch(a):
+        import torch
+        return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _prep_xy(X, y):
+    """Returns (X, y, N, p, dev) with X (N,p) and y (N,) float64, host or device."""
+    if _is_torch(X):
+        import torch
+        if X.dtype != torch.float64 or not X.is_cuda or not X.is_contiguous():
+            raise TypeError("device inputs must be contiguous float64 CUDA tensors")
+        if X.dim() == 1:
+            X = X.reshape(-1, 1)
+        if y is not None and (y.dtype != torch.float64 or not y.is_cuda or not y.is_contiguous()):
+            raise TypeError("device inputs must be contiguous float64 CUDA tensors")
+        return X, y, int(X.shape[0]), int(X.shape[1]), 1
+    X = np.asarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    X = np.ascontiguousarray(X)
+    yy = None if y is None else _host(y).reshape(-1)
+    return X, yy, int(X.shape[0]), int(X.shape[1]), 0
+
+
+# ------------------------------------------------------------------ public API
+
+class Model:
+    """A fitted decomposed-kernel GP (owns a gp_model handle)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+        M, p, n, prec = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().gp_model_info(self._h, C.byref(M), C.byref(p), C.byref(n), C.byref(prec)),
+               "gp_model_info")
+        self.M, self.p, self.n, self.prec = int(M.value), int(p.value), int(n.value), int(prec.value)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value or 0
+
+    def predict(self, Xs, var: bool = True, mean_out=None, var_out=None, stream=None):
+        """Predictive mean (and variance) at Xs; returns (mean, var or None)."""
+        Xs, _, Ns, p, dev = _prep_xy(Xs, None)
+        if p != self.p:
+            raise ValueError(f"Xs has {p} columns, model has p={self.p}")
+        if dev:
+            import torch
+            mean = mean_out if mean_out is not None else torch.empty(Ns, dtype=torch.float64, device=Xs.device)
+            vv = (var_out if var_out is not None else torch.empty(Ns, dtype=torch.float64, device=Xs.device)) if var else None
+        else:
+            mean = mean_out if mean_out is not None else np.empty(Ns)
+            vv = (var_out if var_out is not None else np.empty(Ns)) if var else None
+        rc = lib().gp_predict_ex(self._h, C.c_void_p(_ptr(Xs)), Ns, C.c_void_p(_ptr(mean)),
+                                 C.c_void_p(_ptr(vv)) if vv is not None else None,
+                                 _stream_of(Xs, stream), dev)
+        _check(rc, "gp_predict_ex")
+        return mean, vv
+
+    def read(self, field: str) -> np.ndarray:
+        """Host copy of a fitted quantity: 'L' (M x M), 'c', 'b' or 'd' (M)."""
+        out = np.empty((self.M, self.M) if field == "L" else self.M)
+        _check(lib().gp_model_read(self._h, FIELD[field], out.ctypes.data), "gp_model_read")
+        return out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().gp_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "bf16x3",
+        stream=None) -> Model:
+    """Fit (Sec. 2.2, M x M form) on host numpy arrays or device tensors."""
+    X, y, N, p, dev = _prep_xy(X, y)
+    out = C.c_void_p()
+    rc = lib().gp_fit_ex(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),
+                         float(alpha), float(sigma2), PREC[prec], _stream_of(X, stream), dev,
+                         C.byref(out))
+    _check(rc, "gp_fit_ex")
+    return Model(out.value)
+
+
+def fit_north_star(X, y, n, eps, alpha, sigma2) -> Model:
+    """The plain ``gp_fit`` entry point (host arrays, mixed precision, default stream)."""
+    X, y, N, p, _ = _prep_xy(X, y)
+    h = lib().gp_fit(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),
+                     float(alpha), float(sigma2))
+    if not h:
+        _check(int(lib().gp_last_error()), "gp_fit")
+    return Model(h)
+
+
+def gram(X, y, n: int, eps: float, alpha: float, prec: str = "fp64", stream=None):
+    """G = Phi^T Phi (M x M) and b = Phi^T y as float64 (host arrays in, host arrays out)."""
+    X, y, N, p, dev = _prep_xy(X, y)
+    M = int(n) ** p
+    if dev:
+        import torch
+        G = torch.empty((M, M), dtype=torch.float64, device=X.device)
+        b = torch.empty(M, dtype=torch.float64, device=X.device)
+    else:
+        G = np.empty((M, M))
+        b = np.empty(M)
+    rc = lib().gp_gram_ex(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),
+                          float(alpha), PREC[prec], C.c_void_p(_ptr(G)), C.c_void_p(_ptr(b)),
+                          _stream_of(X, stream), dev)
+    _check(rc, "gp_gram_ex")
+    return G, b
+
+
+def fit_batch(problems: Sequence[Tuple], prec: str = "bf16x3", stream=None) -> List[Model]:
+    """Fit many independent problems; each item is (X, y, n, eps, alpha, sigma2)."""
+    cnt = len(problems)
+    args = (FitArgs * cnt)()
+    keep = []
+    dev = 0
+    for i, (X, y, n, eps, alpha, sigma2) in enumerate(problems):
+        X, y, N, p, dev = _prep_xy(X, y)
+        keep.append((X, y))
+        args[i] = FitArgs(_ptr(X), _ptr(y), N, p, int(n), float(eps), float(alpha), float(sigma2))
+    outs = (C.c_void_p * cnt)()
+    st = _stream_of(keep[0][0], stream) if cnt else None
+    rc = lib().gp_fit_batch(cnt, args, PREC[prec], st, dev, outs)
+    models = [Model(o) if o else None for o in outs]
+    if rc != GP_OK:
+        for m in models:
+            if m is not None:
+                m.free()
+        _check(rc, "gp_fit_batch")
+    return models
+
+
+def predict_batch(reqs: Sequence[Tuple], stream=None):
+    """Batched predict on device tensors; each item is (model, Xs, mean_out, var_out or None)."""
+    cnt = len(reqs)
+    args = (PredictArgs * cnt)()
+    for i, (m, Xs, mo, vo) in enumerate(reqs):
+        args[i] = PredictArgs(m.handle, _ptr(Xs), int(Xs.shape[0]), _ptr(mo),
+                              _ptr(vo) if vo is not None else None)
+    st = stream
+    if st is None and cnt:
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+    _check(lib().gp_predict_batch(cnt, args, st), "gp_predict_batch")
+
+
+def debug_fail_alloc_after(k: int):
+    lib().gp_debug_fail_alloc_after(int(k))
+
+
+def version() -> str:
+    return lib().gp_version().decode()

@@ -1,0 +1,518 @@
+// gp_api.cu -- the C ABI (include/gpfagp.h): argument checks, device memory,
+// and the order of kernel launches for fit and predict.
+//
+// fit (Sec. 2.2 in the M x M form):
+//   eigenfunction tables (Eq. 14-16) -> fused Phi generation + Gram
+//   (Phi^T Phi, Phi^T y) -> split reduction + A = G + sigma^2 Lambda^{-1}
+//   -> A = L L^T -> W = L^{-1} -> c = A^{-1} b with float64 refinement
+// predict (Eq. 11-12, diagonal): tables of X* -> fused Phi_* generation,
+//   mean = Phi_* c, var = sigma^2 rowsum((Phi_* W^T)^2).
+#include "gp_kernels.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+struct gp_model {
+    int device;
+    int prec;
+    GpShape shape;          // N / Npad of the training set (informational)
+    double eps, alpha, sigma2;
+    double* L;              // M x M lower Cholesky factor of A
+    double* W;              // M x M, L^{-1}
+    double* c;              // M, A^{-1} b
+    double* b;              // M, Phi^T y
+    double* d;              // M, sigma^2 / lambda_m (clamped)
+    uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_BF16X3 only)
+};
+
+namespace {
+
+thread_local int g_err = GP_OK;
+thread_local int64_t g_detail = 0;
+std::atomic<int> g_fail_after{0};
+std::mutex g_pool_mu;
+std::vector<int> g_pool_ready;
+
+int set_err(int code, int64_t detail = 0) {
+    g_err = code;
+    g_detail = detail;
+    return code;
+}
+
+int cuda_err(cudaError_t e) { return set_err(GP_ECUDA, (int64_t)e); }
+
+// Keep the stream-ordered pool's memory across calls (no release at every
+// synchronisation), so repeated fits and predicts do not remap memory.
+void prepare_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d : g_pool_ready)
+        if (d == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_ready.push_back(dev);
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    int k = g_fail_after.load();
+    while (k > 0) {
+        if (g_fail_after.compare_exchange_weak(k, k - 1)) {
+            if (k == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    if (bytes == 0) bytes = 16;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+// Frees every registered pointer on the stream when it goes out of scope.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void* p : ptrs)
+            if (p) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    int get(T** p, size_t count) {
+        void* v = nullptr;
+        cudaError_t e = dev_alloc(&v, count * sizeof(T), s);
+        if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)(count * sizeof(T)));
+        if (e != cudaSuccess) return cuda_err(e);
+        ptrs.push_back(v);
+        *p = (T*)v;
+        return GP_OK;
+    }
+};
+
+int check_device(int* dev_out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_err(GP_ENODEV, (int64_t)e);
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return set_err(GP_ENODEV, major * 10 + minor);
+    prepare_pool(dev);
+    *dev_out = dev;
+    return GP_OK;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+int check_hyper(int64_t N, int p, int n, double eps, double alpha, double sigma2) {
+    if (N < 1 || p < 1 || p > GP_PMAX || n < 1) return set_err(GP_EINVAL, 1);
+    if (!finite_pos(eps) || !finite_pos(alpha) || !finite_pos(sigma2)) return set_err(GP_EINVAL, 2);
+    double M = pow((double)n, (double)p);
+    if (M > (double)GP_MAX_M) return set_err(GP_EINVAL, 3);
+    return GP_OK;
+}
+
+// log lambda_k, k = 0..n-1 (Eq. 16 with delta^2 of Eq. 14, rho^2 reading)
+void log_eigenvalues(int n, double eps, double alpha, double* out) {
+    const double beta = pow(1.0 + (2.0 * eps / alpha) * (2.0 * eps / alpha), 0.25);
+    const double delta2 = alpha * alpha * (beta * beta - 1.0) / 2.0;
+    const double D = alpha * alpha + delta2 + eps * eps;
+    for (int k = 0; k < n; ++k) out[k] = 0.5 * log(alpha * alpha / D) + k * log(eps * eps / D);
+}
+
+template <typename T>
+__global__ void pad_y_kernel(const double* __restrict__ y, int64_t N, int64_t Npad, T* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < Npad) out[i] = i < N ? (T)y[i] : T(0);
+}
+
+int read_status(GpStatus* st, cudaStream_t s) {
+    GpStatus h;
+    cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (h.code != GP_OK) return set_err(h.code, h.detail);
+    return GP_OK;
+}
+
+// Split the (padded) rows so that tile pairs x splits fill the GPU.
+void choose_splits(int npairs, int64_t Npad, int target_ctas, int* nsplit, int64_t* rps) {
+    int64_t want = (target_ctas + npairs - 1) / npairs;
+    int64_t maxs = Npad / 256;  // at least 256 rows per split
+    if (want > maxs) want = maxs;
+    if (want < 1) want = 1;
+    if (want > 65535) want = 65535;
+    int64_t r = gp_round_up((Npad + want - 1) / want, 128);
+    *rps = r;
+    *nsplit = (int)((Npad + r - 1) / r);
+}
+
+int num_sms(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// The fused Gram step: A (M x M) = Phi^T Phi [+ diag(d)], b = Phi^T y.
+// X, y are device pointers.
+int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const double* yd,
+                const double* d, double* A, double* b, GpStatus* st, cudaStream_t stream) {
+    Scratch sc(stream);
+    int rc;
+    if (prec == GP_PREC_FP64) {
+        double *tab, *ypad, *Gpart, *bpart;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
+        const int T = s.Mpad / SYRK64_TM;
+        const int npairs = T * (T + 1) / 2;
+        int nsplit;
+        int64_t rps;
+        choose_splits(npairs, s.Npad, 4 * num_sms(dev), &nsplit, &rps);
+        if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRK64_TM * SYRK64_TM))) return rc;
+        if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
+        launch_eig_tables_f64(s, Xd, yd, tab, st, stream);
+        pad_y_kernel<double><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
+        cudaError_t e = launch_syrk64(s, tab, ypad, nsplit, rps, Gpart, bpart, stream);
+        if (e != cudaSuccess) return cuda_err(e);
+        launch_assemble_f64(Gpart, bpart, nsplit, SYRK64_TM, s.Mpad, s.M, d, A, b, stream);
+    } else {
+        float *tab, *ypad, *Gpart, *bpart;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
+        const int T = s.Mpad / SYRKTC_TM;
+        const int npairs = T * (T + 1) / 2;
+        int nsplit;
+        int64_t rps;
+        choose_splits(npairs, s.Npad, num_sms(dev), &nsplit, &rps);
+        if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
+        if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
+        launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
+        pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
+        cudaError_t e = launch_syrk_tc(s, tab, ypad, nsplit, rps, Gpart, bpart, st, stream);
+        if (e != cudaSuccess) return cuda_err(e);
+        launch_assemble_f32(Gpart, bpart, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e);
+    return GP_OK;
+}
+
+int tile_of(int prec) { return prec == GP_PREC_FP64 ? SYRK64_TM : SYRKTC_TM; }
+
+int check_prec(int prec) {
+    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3) return set_err(GP_EINVAL, 4);
+    return GP_OK;
+}
+
+void free_model(gp_model* h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    void* ps[] = {h->L, h->W, h->c, h->b, h->d, h->Wpack};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+int model_alloc(gp_model* h, size_t bytes, void** p, cudaStream_t s) {
+    cudaError_t e = dev_alloc(p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)bytes);
+    if (e != cudaSuccess) return cuda_err(e);
+    return GP_OK;
+}
+
+}  // namespace
+
+int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile) {
+    memset(s, 0, sizeof(*s));
+    s->N = N;
+    s->Npad = gp_round_up(N > 0 ? N : 1, 128);
+    s->p = p;
+    s->n = n;
+    int64_t M = 1;
+    for (int j = 0; j < p; ++j) M *= n;
+    s->M = (int)M;
+    s->Mpad = (int)gp_round_up(M, tile);
+    int64_t st = 1;
+    for (int j = p - 1; j >= 0; --j) {
+        s->stride[j] = (int)st;
+        st *= n;
+    }
+    const double beta = pow(1.0 + (2.0 * eps / alpha) * (2.0 * eps / alpha), 0.25);
+    s->alpha_beta = alpha * beta;
+    s->delta2 = alpha * alpha * (beta * beta - 1.0) / 2.0;
+    s->sqrt_beta = sqrt(beta);
+    return GP_OK;
+}
+
+extern "C" {
+
+GPFAGP_API const char* gp_version(void) { return "gpfagp 0.1 sm_103a"; }
+
+GPFAGP_API int gp_last_error(void) { return g_err; }
+GPFAGP_API int64_t gp_last_error_detail(void) { return g_detail; }
+
+GPFAGP_API const char* gp_strerror(int status) {
+    switch (status) {
+        case GP_OK: return "ok";
+        case GP_EINVAL: return "invalid argument";
+        case GP_ENOMEM: return "device allocation failed";
+        case GP_ENOTPD: return "matrix A is not positive definite";
+        case GP_ECUDA: return "CUDA runtime error";
+        case GP_ETIMEOUT: return "bounded device wait timed out";
+        case GP_ENODEV: return "no sm_103 device";
+        default: return "unknown status";
+    }
+}
+
+GPFAGP_API void gp_debug_fail_alloc_after(int k) { g_fail_after.store(k > 0 ? k : 0); }
+
+GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                          double alpha, int prec, double* G, double* b, void* cuda_stream,
+                          int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!X || !y || !G || !b) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, 1.0))) return rc;
+    if ((rc = check_prec(prec))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    GpShape s;
+    gp_fill_shape(&s, N, p, n, eps, alpha, tile_of(prec));
+    Scratch sc(stream);
+    const double *Xd = X, *yd = y;
+    double *Gd = G, *bd = b;
+    GpStatus* st;
+    if ((rc = sc.get(&st, 1))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    if (!dev_ptrs) {
+        double *xx, *yy;
+        if ((rc = sc.get(&xx, (size_t)N * p))) return rc;
+        if ((rc = sc.get(&yy, (size_t)N))) return rc;
+        if ((rc = sc.get(&Gd, (size_t)s.M * s.M))) return rc;
+        if ((rc = sc.get(&bd, (size_t)s.M))) return rc;
+        cudaMemcpyAsync(xx, X, sizeof(double) * N * p, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+        yd = yy;
+    }
+    if ((rc = gram_device(s, prec, dev, Xd, yd, nullptr, Gd, bd, st, stream))) return rc;
+    if (!dev_ptrs) {
+        cudaMemcpyAsync(G, Gd, sizeof(double) * s.M * s.M, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(b, bd, sizeof(double) * s.M, cudaMemcpyDeviceToHost, stream);
+    }
+    return read_status(st, stream);
+}
+
+GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                         double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                         gp_model** out) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!out) return set_err(GP_EINVAL, 0);
+    *out = nullptr;
+    if (!X || !y) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
+    if ((rc = check_prec(prec))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    gp_model* h = new gp_model();
+    memset(h, 0, sizeof(*h));
+    h->device = dev;
+    h->prec = prec;
+    h->eps = eps;
+    h->alpha = alpha;
+    h->sigma2 = sigma2;
+    gp_fill_shape(&h->shape, N, p, n, eps, alpha, tile_of(prec));
+    const GpShape& s = h->shape;
+    const int M = s.M;
+
+    Scratch sc(stream);
+    auto fail = [&](int code) {
+        int64_t det = g_detail;
+        cudaStreamSynchronize(stream);
+        free_model(h);
+        set_err(code, det);
+        return code;
+    };
+    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->L, stream))) return fail(rc);
+    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->W, stream))) return fail(rc);
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->c, stream))) return fail(rc);
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->b, stream))) return fail(rc);
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return fail(rc);
+    if (prec == GP_PREC_BF16X3) {
+        if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return fail(rc);
+    }
+    GpStatus* st;
+    double *A, *loglam, *work;
+    if ((rc = sc.get(&st, 1))) return fail(rc);
+    if ((rc = sc.get(&A, (size_t)M * M))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return fail(rc);
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+
+    const double *Xd = X, *yd = y;
+    if (!dev_ptrs) {
+        double *xx, *yy;
+        if ((rc = sc.get(&xx, (size_t)N * p))) return fail(rc);
+        if ((rc = sc.get(&yy, (size_t)N))) return fail(rc);
+        cudaMemcpyAsync(xx, X, sizeof(double) * N * p, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+        yd = yy;
+    }
+    std::vector<double> ll(n);
+    log_eigenvalues(n, eps, alpha, ll.data());
+    cudaMemcpyAsync(loglam, ll.data(), sizeof(double) * n, cudaMemcpyHostToDevice, stream);
+    launch_noise_diag(s, loglam, sigma2, h->d, stream);
+
+    if ((rc = gram_device(s, prec, dev, Xd, yd, h->d, A, h->b, st, stream))) return fail(rc);
+    cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
+    cudaError_t e = launch_cholesky(h->L, M, st, stream);
+    if (e == cudaSuccess) e = launch_tri_inverse(h->L, h->W, M, st, stream);
+    if (e == cudaSuccess) e = launch_solve_refine(A, h->W, h->b, h->c, work, M, 2, st, stream);
+    if (e == cudaSuccess && prec == GP_PREC_BF16X3) {
+        launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail(cuda_err(e));
+    if ((rc = read_status(st, stream))) return fail(rc);
+    *out = h;
+    return GP_OK;
+}
+
+GPFAGP_API gp_model* gp_fit(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                            double alpha, double sigma2) {
+    gp_model* h = nullptr;
+    gp_fit_ex(X, y, N, p, n, eps, alpha, sigma2, GP_PREC_BF16X3, nullptr, 0, &h);
+    return h;
+}
+
+GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, double* mean,
+                             double* var, void* cuda_stream, int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!h || Ns < 0) return set_err(GP_EINVAL, 0);
+    if (Ns == 0) return GP_OK;
+    if (!Xs || !mean) return set_err(GP_EINVAL, 0);
+    if ((rc = check_device(&dev))) return rc;
+    if (dev != h->device) return set_err(GP_EINVAL, 5);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    GpShape s = h->shape;
+    s.N = Ns;
+    s.Npad = gp_round_up(Ns, 128);
+    Scratch sc(stream);
+    GpStatus* st;
+    if ((rc = sc.get(&st, 1))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    const double* Xd = Xs;
+    double *md = mean, *vd = var;
+    if (!dev_ptrs) {
+        double* xx;
+        if ((rc = sc.get(&xx, (size_t)Ns * s.p))) return rc;
+        if ((rc = sc.get(&md, (size_t)Ns))) return rc;
+        if (var && (rc = sc.get(&vd, (size_t)Ns))) return rc;
+        cudaMemcpyAsync(xx, Xs, sizeof(double) * Ns * s.p, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+    }
+    cudaError_t e;
+    if (h->prec == GP_PREC_FP64) {
+        double *tab, *part;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&part, predict64_part_elems(s.Npad, s.M)))) return rc;
+        launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
+        e = launch_predict64(s, tab, h->W, h->c, h->sigma2, part, md, vd, stream);
+    } else {
+        float* tab;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
+        e = launch_predict_tc(s, tab, h->Wpack, h->c, h->sigma2, md, vd, st, stream);
+    }
+    if (e != cudaSuccess) return cuda_err(e);
+    if (!dev_ptrs) {
+        cudaMemcpyAsync(mean, md, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+        if (var) cudaMemcpyAsync(var, vd, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+    }
+    return read_status(st, stream);
+}
+
+GPFAGP_API int gp_predict(const gp_model* h, const double* Xs, int64_t Ns, double* mean, double* var) {
+    return gp_predict_ex(h, Xs, Ns, mean, var, nullptr, 0);
+}
+
+GPFAGP_API void gp_free(gp_model* h) { free_model(h); }
+
+GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec) {
+    if (!h) return set_err(GP_EINVAL, 0);
+    if (M) *M = h->shape.M;
+    if (p) *p = h->shape.p;
+    if (n) *n = h->shape.n;
+    if (prec) *prec = h->prec;
+    return GP_OK;
+}
+
+GPFAGP_API int gp_model_read(const gp_model* h, int field, double* dst) {
+    set_err(GP_OK);
+    if (!h || !dst) return set_err(GP_EINVAL, 0);
+    const size_t M = (size_t)h->shape.M;
+    const double* src = nullptr;
+    size_t cnt = M;
+    switch (field) {
+        case GP_FIELD_L: src = h->L; cnt = M * M; break;
+        case GP_FIELD_C: src = h->c; break;
+        case GP_FIELD_B: src = h->b; break;
+        case GP_FIELD_D: src = h->d; break;
+        default: return set_err(GP_EINVAL, field);
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_err(e);
+    return GP_OK;
+}
+
+GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* cuda_stream,
+                            int dev_ptrs, gp_model** out) {
+    set_err(GP_OK);
+    if (count < 0 || (count > 0 && (!args || !out))) return set_err(GP_EINVAL, 0);
+    int first = GP_OK;
+    int64_t first_idx = 0;
+    for (int i = 0; i < count; ++i) {
+        const gp_fit_args& a = args[i];
+        int rc = gp_fit_ex(a.X, a.y, a.N, a.p, a.n, a.eps, a.alpha, a.sigma2, prec, cuda_stream,
+                           dev_ptrs, &out[i]);
+        if (rc != GP_OK && first == GP_OK) {
+            first = rc;
+            first_idx = i;
+        }
+    }
+    if (first != GP_OK) return set_err(first, first_idx);
+    return GP_OK;
+}
+
+GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream) {
+    set_err(GP_OK);
+    if (count < 0 || (count > 0 && !args)) return set_err(GP_EINVAL, 0);
+    for (int i = 0; i < count; ++i) {
+        const gp_predict_args& a = args[i];
+        int rc = gp_predict_ex(a.model, a.Xs, a.Ns, a.mean, a.var, cuda_stream, 1);
+        if (rc != GP_OK) return set_err(rc, i);
+    }
+    return GP_OK;
+}
+
+}  // extern "C"

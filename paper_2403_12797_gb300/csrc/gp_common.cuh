@@ -1,0 +1,123 @@
+// gp_common.cuh -- shared definitions of the GB300 decomposed-kernel GP library.
+//
+// Host/device structures for one problem, the device status word, the
+// eigenfunction-table window of a column tile (Sec. 2.3, Eq. 18-19: a
+// column of Phi is a product of one table row per input dimension), and
+// error-handling helpers. Nothing here launches a kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gpfagp.h"
+
+#define GP_PMAX 32           // largest supported input dimension p
+
+// ---------------------------------------------------------------------------
+// Device status word: written by kernels, read back once per call by the host.
+// ---------------------------------------------------------------------------
+struct GpStatus {
+    int32_t code;            // GP_OK or a negative status
+    int32_t pad;
+    int64_t detail;          // pivot column, timeout site, ...
+};
+
+__device__ __forceinline__ void gp_set_status(GpStatus* st, int code, int64_t detail) {
+    // first error wins
+    if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
+}
+
+// ---------------------------------------------------------------------------
+// One problem's shape and SE eigen-parameters (Eq. 14-16), computed on the
+// host in float64 and passed by value to kernels.
+// ---------------------------------------------------------------------------
+struct GpShape {
+    int64_t N;               // data rows (training or test points)
+    int64_t Npad;            // rows of the eigenfunction tables (multiple of 128)
+    int     p, n;            // input dimensions, eigenfunctions per dimension
+    int     M;               // n^p
+    int     Mpad;            // M rounded up to the tile size of the kernel in use
+    int     stride[GP_PMAX]; // n^(p-1-j): column m has digit (m / stride[j]) % n
+    double  alpha_beta;      // rho * beta   (Hermite argument scale, Eq. 15)
+    double  delta2;          // delta^2      (envelope exponent, Eq. 15)
+    double  sqrt_beta;       // gamma_1 = sqrt(beta)
+};
+
+// ---------------------------------------------------------------------------
+// Table window of a tile of consecutive columns [m0, m0 + TW).
+//
+// Each column of Phi multiplies one eigenfunction table row per dimension.
+// For dimension j, the digits of consecutive columns are consecutive values
+// mod n, so a tile needs count_j <= n rows of dimension j starting at digit
+// first_j (mod n). Window row r = base_j + ((digit - first_j) mod n).
+// ---------------------------------------------------------------------------
+struct TileWindow {
+    int nrows;
+    int base[GP_PMAX];
+    int first[GP_PMAX];
+    int count[GP_PMAX];
+};
+
+__host__ __device__ inline void tile_window(const GpShape& s, int m0, int TW, TileWindow* w) {
+    int m1 = m0 + TW;
+    if (m1 > s.M) m1 = s.M;
+    int rows = 0;
+    for (int j = 0; j < s.p; ++j) {
+        int st = s.stride[j];
+        int f = (m0 / st) % s.n;
+        int cnt = 0;
+        if (m1 > m0) {
+            long span = (long)((m1 - 1) / st) - (long)(m0 / st) + 1;
+            cnt = span < s.n ? (int)span : s.n;
+        }
+        w->base[j] = rows;
+        w->first[j] = f;
+        w->count[j] = cnt;
+        rows += cnt;
+    }
+    w->nrows = rows;
+}
+
+// window row of dimension j for column m (m inside the tile)
+__host__ __device__ inline int window_row(const GpShape& s, const TileWindow& w, int j, int m) {
+    int d = (m / s.stride[j]) % s.n;
+    int pos = d - w.first[j];
+    if (pos < 0) pos += s.n;
+    return w.base[j] + pos;
+}
+
+// global table row (dimension j, digit) for window row r
+__host__ __device__ inline int window_table_row(const GpShape& s, const TileWindow& w, int r) {
+    int j = 0;
+    while (j + 1 < s.p && r >= w.base[j + 1]) ++j;
+    int d = w.first[j] + (r - w.base[j]);
+    if (d >= s.n) d -= s.n;
+    return j * s.n + d;
+}
+
+// lower-triangular tile pair index q -> (I, J), I >= J, q = I(I+1)/2 + J
+__host__ __device__ inline void tri_pair(int q, int* I, int* J) {
+    int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    while (i * (i + 1) / 2 > q) --i;
+    *I = i;
+    *J = q - i * (i + 1) / 2;
+}
+
+// largest window (table rows) over the column tiles of width TW
+static inline int gp_max_window_rows(const GpShape& s, int TW) {
+    int mx = 1;
+    for (int m0 = 0; m0 < s.M; m0 += TW) {
+        TileWindow w;
+        tile_window(s, m0, TW, &w);
+        if (w.nrows > mx) mx = w.nrows;
+    }
+    return mx;
+}
+
+static inline int64_t gp_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// Host-side helpers implemented in gp_api.cu
+// ---------------------------------------------------------------------------
+int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile);

@@ -1,0 +1,73 @@
+// gp_kernels.cuh -- launchers of the library's CUDA kernels (host side).
+#pragma once
+
+#include "gp_common.cuh"
+
+// ---- eigenfunction tables (gp_tables.cu) ------------------------------------
+void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
+                           GpStatus* st, cudaStream_t stream);
+void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
+                           GpStatus* st, cudaStream_t stream);
+
+// ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
+// Tile 64 x 64, lower-triangular tile pairs x N splits.
+constexpr int SYRK64_TM = 64;
+constexpr int SYRK64_BK = 16;
+size_t syrk64_smem_bytes(const GpShape& s);
+cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypad, int nsplit,
+                          int64_t rows_per_split, double* Gpart, double* bpart, cudaStream_t stream);
+
+// ---- bf16x3 tensor-core Gram (gp_syrk_tc.cu) ---------------------------------
+constexpr int SYRKTC_TM = 128;
+constexpr int SYRKTC_BK = 32;
+size_t syrktc_smem_bytes(const GpShape& s);
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const float* ypad, int nsplit,
+                           int64_t rows_per_split, float* Gpart, float* bpart, GpStatus* st,
+                           cudaStream_t stream);
+
+// ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
+// A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);
+// b = sum_s bpart[s]. d may be NULL (plain Gram).
+void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
+                         int M, const double* d, double* A, double* b, cudaStream_t stream);
+void launch_assemble_f32(const float* Gpart, const float* bpart, int nsplit, int tile, int Mpad,
+                         int M, const double* d, double* A, double* b, cudaStream_t stream);
+// d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)
+void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
+                       cudaStream_t stream);
+
+// ---- float64 factorisation and solves (gp_chol.cu) ----------------------------
+constexpr int CHOL_NB = 64;
+// In-place lower Cholesky of the M x M row-major matrix L (upper part ignored,
+// then zeroed). Non-positive pivot -> status GP_ENOTPD, detail = column.
+cudaError_t launch_cholesky(double* L, int M, GpStatus* st, cudaStream_t stream);
+// W = L^{-1} (lower, M x M row-major); W's upper part is zeroed.
+cudaError_t launch_tri_inverse(const double* L, double* W, int M, GpStatus* st,
+                               cudaStream_t stream);
+// c = A^{-1} b through W = L^{-1}: c = W^T (W b), then `refine` steps of
+// c += W^T W (b - A c) with the float64 residual.
+cudaError_t launch_solve_refine(const double* A, const double* W, const double* b, double* c,
+                                double* work, int M, int refine, const GpStatus* st,
+                                cudaStream_t stream);
+size_t solve_refine_work_elems(int M);
+
+// ---- float64 predict (gp_predict64.cu) -----------------------------------------
+constexpr int PRED64_TT = 64;   // test points per CTA
+constexpr int PRED64_TK = 64;   // columns of Z = Phi_* W^T per CTA
+size_t predict64_part_elems(int64_t Ns, int M);
+cudaError_t launch_predict64(const GpShape& s, const double* tab, const double* W, const double* c,
+                             double sigma2, double* part, double* mean, double* var,
+                             cudaStream_t stream);
+
+// ---- bf16x3 tensor-core predict (gp_predict_tc.cu) ------------------------------
+constexpr int PREDTC_TT = 128;  // test points per CTA (MMA M)
+constexpr int PREDTC_BK = 32;   // Phi_* columns per pipeline stage (MMA K chunk)
+constexpr int PREDTC_KB = 128;  // rows of W per MMA (MMA N)
+constexpr int PREDTC_SUPER = 4; // MMA N-blocks held in TMEM at once (4 x 128 = 512 columns)
+// Pack W = L^{-1} (float64, M x M) into the bf16 hi/lo blocked operand layout.
+size_t predtc_wpack_bytes(int M);
+void launch_pack_w_bf16x3(const double* W, int M, uint16_t* Wpack, cudaStream_t stream);
+size_t predtc_smem_bytes(const GpShape& s);
+cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
+                              const double* c, double sigma2, double* mean, double* var,
+                              GpStatus* st, cudaStream_t stream);

@@ -1,0 +1,79 @@
+// gp_tables.cu -- per-dimension eigenfunction tables (Sec. 2.3, Eq. 14-15).
+//
+// For every point i and input dimension j the kernel evaluates the n SE
+// eigenfunctions phi_k(x_ij) = gamma_k exp(-delta^2 x^2) H_{k-1}(rho beta x)
+// through the normalised Hermite recurrence (the quantity gamma_{k+1} H_k(t)
+// satisfies q_{k+1} = sqrt(2/(k+1)) t q_k - sqrt(k/(k+1)) q_{k-1},
+// q_0 = sqrt(beta), q_1 = sqrt(2) t q_0), so nothing overflows for large n.
+//
+// Layout: T[(j * n + k) * Npad + i], rows i >= N are zero. A column of Phi
+// (Eq. 19) is the product of one row per dimension of this table, formed
+// later inside the contraction kernels: Phi itself is never stored.
+#include "gp_kernels.cuh"
+
+#include <math.h>
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T gp_exp(T v);
+template <>
+__device__ __forceinline__ float gp_exp<float>(float v) { return expf(v); }
+template <>
+__device__ __forceinline__ double gp_exp<double>(double v) { return exp(v); }
+
+template <typename T>
+__device__ __forceinline__ T gp_sqrt(T v);
+template <>
+__device__ __forceinline__ float gp_sqrt<float>(float v) { return sqrtf(v); }
+template <>
+__device__ __forceinline__ double gp_sqrt<double>(double v) { return sqrt(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double* __restrict__ X,
+                                                         const double* __restrict__ y,
+                                                         T* __restrict__ tab, GpStatus* st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= s.Npad) return;
+    T* out = tab + (int64_t)j * s.n * s.Npad + i;
+    if (i >= s.N) {
+        for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
+        return;
+    }
+    const double xd = X[i * s.p + j];
+    if (!isfinite(xd) || (j == 0 && y != nullptr && !isfinite(y[i]))) {
+        gp_set_status(st, GP_EINVAL, i);
+        for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
+        return;
+    }
+    const T x = (T)xd;
+    const T t = (T)s.alpha_beta * x;
+    T q0 = (T)s.sqrt_beta * gp_exp<T>(-(T)s.delta2 * x * x);
+    out[0] = q0;
+    if (s.n == 1) return;
+    T q1 = gp_sqrt<T>(T(2)) * t * q0;
+    out[s.Npad] = q1;
+    for (int k = 1; k + 1 < s.n; ++k) {
+        const T a = gp_sqrt<T>(T(2) / T(k + 1));
+        const T b = gp_sqrt<T>(T(k) / T(k + 1));
+        const T q2 = a * t * q1 - b * q0;
+        out[(int64_t)(k + 1) * s.Npad] = q2;
+        q0 = q1;
+        q1 = q2;
+    }
+}
+
+}  // namespace
+
+void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
+                           GpStatus* st, cudaStream_t stream) {
+    dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
+    eig_tables_kernel<double><<<grid, 256, 0, stream>>>(s, X, y, tab, st);
+}
+
+void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
+                           GpStatus* st, cudaStream_t stream) {
+    dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
+    eig_tables_kernel<float><<<grid, 256, 0, stream>>>(s, X, y, tab, st);
+}

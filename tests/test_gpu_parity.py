@@ -1,0 +1,165 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances (relative L2 unless stated):
+  fp64 mode:    Gram 1e-12 (Frobenius), mean and variance 1e-10;
+  bf16x3 mode:  Gram 3e-5 (Frobenius; each product carries <= 3*2^-18
+                relative error from the dropped lo*lo term and the bf16
+                rounding of lo), mean 1e-4, variance 1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import fagp as O
+from paper_2403_12797_gb300 import _lib
+from paper_2403_12797_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(G=1e-12, mean=1e-10, var=1e-10),
+       "bf16x3": dict(G=3e-5, mean=1e-4, var=1e-3)}
+
+GRAM_CASES = [
+    # (seed, N, p, n): ragged N, M not a multiple of the tile, several tiles, wrap of digits
+    (1, 1000, 1, 10),
+    (2, 777, 2, 7),
+    (3, 3000, 3, 5),
+    (4, 513, 2, 20),
+    (5, 2000, 4, 3),
+    (6, 100, 1, 1),
+    (7, 1, 2, 3),
+    (8, 4099, 1, 300),
+    (9, 1500, 3, 6),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("seed,N,p,n", GRAM_CASES)
+def test_gram_matches_oracle(prec, seed, N, p, n):
+    pr = W.random_problem(seed, N, 1, p, n, eps=1.1, alpha=0.9)
+    G, b = _lib.gram(pr.X, pr.y, n, pr.eps, pr.alpha, prec=prec)
+    Go, bo = O.gram(pr.X, pr.y, n, pr.eps, pr.alpha)
+    assert O.relerr(G, Go) < TOL[prec]["G"]
+    assert O.relerr(b, bo) < max(TOL[prec]["G"], 1e-12) * 10
+    np.testing.assert_array_equal(G, G.T)
+
+
+def _fit_predict(pr, prec, var=True):
+    m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    mean, v = m.predict(pr.Xs, var=var)
+    return m, mean, v
+
+
+def _oracle(pr):
+    mdl = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    return mdl, O.predict(mdl, pr.Xs)
+
+
+def _small_cases():
+    out = [W.workload1(), W.workload2(N=20_000, Ns=3_000)]
+    w3 = W.workload3(N=20_000, Ns=1_000)
+    w3.n = 8          # M = 512: several 128-wide tiles, ragged test tile
+    out.append(w3)
+    out.append(W.random_problem(21, 5_000, 333, 4, 4, eps=0.8, alpha=1.2, sigma2=0.02))
+    out.append(W.random_problem(22, 300, 129, 1, 40, eps=1.0, alpha=1.0, sigma2=0.01))
+    out.append(W.random_problem(23, 1, 7, 2, 3))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("case", range(6))
+def test_fit_predict_matches_oracle(prec, case):
+    pr = _small_cases()[case]
+    m, mean, var = _fit_predict(pr, prec)
+    mdl, (mo, vo) = _oracle(pr)
+    assert O.relerr(mean, mo) < TOL[prec]["mean"], (O.relerr(mean, mo), pr.name)
+    assert O.relerr(var, vo) < TOL[prec]["var"], (O.relerr(var, vo), pr.name)
+    if prec == "fp64":
+        assert O.relerr(m.read("L"), mdl["L"]) < 1e-10
+        assert O.relerr(m.read("c"), mdl["c"]) < 1e-9
+        assert O.relerr(m.read("b"), mdl["b"]) < 1e-12
+    np.testing.assert_allclose(m.read("d"), mdl["d"], rtol=1e-13)
+    m.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_workload2_full_size(prec):
+    pr = W.workload2()
+    m, mean, var = _fit_predict(pr, prec)
+    _, (mo, vo) = _oracle(pr)
+    assert O.relerr(mean, mo) < TOL[prec]["mean"], O.relerr(mean, mo)
+    assert O.relerr(var, vo) < TOL[prec]["var"], O.relerr(var, vo)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_fit_is_deterministic_and_device_path_matches_host(prec):
+    import torch
+    pr = W.workload2(N=30_000, Ns=2_000)
+    m1, mean1, var1 = _fit_predict(pr, prec)
+    m2, mean2, var2 = _fit_predict(pr, prec)
+    np.testing.assert_array_equal(mean1, mean2)
+    np.testing.assert_array_equal(var1, var2)
+    Xd = torch.from_numpy(pr.X).cuda()
+    yd = torch.from_numpy(pr.y).cuda()
+    Xsd = torch.from_numpy(pr.Xs).cuda()
+    m3 = _lib.fit(Xd, yd, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    mean3, var3 = m3.predict(Xsd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(mean3.cpu().numpy(), mean1)
+    np.testing.assert_array_equal(var3.cpu().numpy(), var1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_predict_edge_sizes(prec):
+    pr = W.workload1()
+    m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    mdl = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    mean, var = m.predict(np.zeros((0, 1)))
+    assert mean.shape == (0,)
+    for Ns in (1, 127, 128, 129):
+        Xs = pr.Xs[:Ns]
+        mean, var = m.predict(Xs)
+        mo, vo = O.predict(mdl, Xs)
+        assert O.relerr(mean, mo) < TOL[prec]["mean"]
+        assert O.relerr(var, vo) < TOL[prec]["var"]
+    mean_only, none = m.predict(pr.Xs, var=False)
+    assert none is None
+    mean_full, _ = m.predict(pr.Xs)
+    np.testing.assert_array_equal(mean_only, mean_full)
+
+
+def test_north_star_entry_point():
+    pr = W.workload1()
+    m = _lib.fit_north_star(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    mean, var = np.empty(pr.Ns), np.empty(pr.Ns)
+    rc = _lib.lib().gp_predict(m._h, pr.Xs.ctypes.data, pr.Ns, mean.ctypes.data, var.ctypes.data)
+    assert rc == _lib.GP_OK
+    _, (mo, vo) = _oracle(pr)
+    assert O.relerr(mean, mo) < 1e-4 and O.relerr(var, vo) < 1e-3
+
+
+def test_nan_input_is_rejected_on_device():
+    pr = W.workload1()
+    X = pr.X.copy()
+    X[17, 0] = np.nan
+    with pytest.raises(_lib.GPError) as e:
+        _lib.fit(X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="fp64")
+    assert e.value.status == _lib.GP_EINVAL and e.value.detail == 17
+    y = pr.y.copy()
+    y[5] = np.inf
+    with pytest.raises(_lib.GPError) as e:
+        _lib.fit(pr.X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="bf16x3")
+    assert e.value.status == _lib.GP_EINVAL
+
+
+def test_allocation_failure_reports_enomem_then_recovers():
+    pr = W.workload1()
+    for k in (1, 3, 6):
+        _lib.debug_fail_alloc_after(k)
+        with pytest.raises(_lib.GPError) as e:
+            _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+        assert e.value.status == _lib.GP_ENOMEM
+    _lib.debug_fail_alloc_after(0)
+    m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    mean, _ = m.predict(pr.Xs)
+    assert np.isfinite(mean).all()
