@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the decomposed-kernel GP hot path on GB300.
+
+One step = one full fit (eigenfunction tables, fused Phi generation + Gram
+on the tensor cores, split reduction and assembly of A, float64 Cholesky,
+inverse, solve + refinement, operand packing) followed by one full predict
+(mean and variance) of the p=2, n=20 (M=400) workload: N=200,000 training
+points, 50,000 test points. Inputs are resident in device memory when the
+timed region starts; L2 is flushed (256 MiB write) between timed steps.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fit+predict points/s at M=n^p; serve p50/p99 ms; mixed vs FP64 GPU at err ≤1e-4"
+UNIT = "points/s"
+WORKLOAD = ("p=2, n=20 (M=400), N=200,000 train x~U[-1,1]^2, y=sin(3x1)cos(2x2)+0.05 noise, "
+            "50,000 test points, eps=1, alpha=0.8, sigma2=0.0025")
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 float64 rate (no measured figure available)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"],
+                    src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_file: str, name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (matching sha256 prefix), else None."""
+    src = os.path.join(ROOT, "paper_2403_12797_gb300", "csrc", kernel_file)
+    prof = os.path.join(ROOT, "profiles", f"{name}.md")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        txt = open(prof).read()
+    except Exception:
+        return None
+    m_h = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+    m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_h or not m_t or m_h.group(1) != h:
+        return None
+    return float(m_t.group(1))
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import fagp as O
+    from paper_2403_12797_gb300 import workloads as W
+    pr = W.workload2()
+    # bounded sample of the workload: a quarter of the training and test points
+    Ns_, Nt_ = pr.N // 4, pr.Ns // 4
+    X, y, Xs = pr.X[:Ns_], pr.y[:Ns_], pr.Xs[:Nt_]
+
+    def step():
+        m = O.fit(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+        O.predict(m, Xs)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = (Ns_ + Nt_) / dt
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": f"{Ns_} train + {Nt_} test points per step"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"first {Ns_} train and {Nt_} test points of the workload"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2403_12797_gb300 import _lib
+    from paper_2403_12797_gb300 import build as _build
+    from paper_2403_12797_gb300 import workloads as W
+
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    L = _lib.lib()
+    L.gp_kernel_launches.restype = __import__("ctypes").c_int64
+    L.gp_profile_query.argtypes = [__import__("ctypes").c_char_p, __import__("ctypes").c_void_p,
+                                   __import__("ctypes").c_void_p]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    pr = W.workload2()
+    dev = torch.device("cuda", local)
+    X = torch.from_numpy(pr.X).to(dev)
+    y = torch.from_numpy(pr.y).to(dev)
+    Xs = torch.from_numpy(pr.Xs).to(dev)
+    mean = torch.empty(pr.Ns, dtype=torch.float64, device=dev)
+    var = torch.empty(pr.Ns, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        m = _lib.fit(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+        m.predict(Xs, mean_out=mean, var_out=var)
+        m.free()
+
+    prec = args.prec
+    for _ in range(args.warmup):
+        step(prec)
+    barrier()
+
+    import ctypes as C
+    L.gp_profile_reset()
+    L.gp_profile_enable(1)
+    launches0 = L.gp_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(prec)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop()
+    launches = L.gp_kernel_launches() - launches0
+    L.gp_profile_enable(0)
+    groups = {}
+    for g in ("eig_tables", "syrk_tc", "syrk64", "assemble", "cholesky", "tri_inverse",
+              "solve_refine", "pack_w", "predict_tc", "predict64"):
+        n_, ms_ = C.c_int64(), C.c_double()
+        if L.gp_profile_query(g.encode(), C.byref(n_), C.byref(ms_)) == 0:
+            groups[g] = {"launches": n_.value, "total_ms": ms_.value}
+
+    t_step = sum(times) / len(times)
+    t_all = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    t_max_ms = float(t_all.item())
+    points = (pr.N + pr.Ns) * args.steps * world
+    value = points / (t_max_ms / 1e3)
+
+    # ---- roofline of the dominant kernel group (device time inside the timed steps)
+    pk = peaks()
+    M, N, Ns = pr.M, pr.N, pr.Ns
+    work = {
+        "syrk_tc": ("tensor", N * M * (M + 1) + 2 * N * M, pk["bf16"], "TFLOP/s", "gp_syrk_tc.cu"),
+        "predict_tc": ("tensor", Ns * M * (M + 1) + 4 * Ns * M, pk["bf16"], "TFLOP/s", "gp_predict_tc.cu"),
+        "cholesky": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_chol.cu"),
+        "tri_inverse": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_chol.cu"),
+        "eig_tables": ("hbm", (N + Ns) * 2 * 8 + (N + Ns) * 2 * pr.n * 4, pk["hbm"], "GB/s", "gp_tables.cu"),
+    }
+    total_dev = sum(g["total_ms"] for g in groups.values()) or 1.0
+    shares = {k: round(v["total_ms"] / total_dev, 4) for k, v in groups.items()}
+    dom = max((k for k in groups if k in work), key=lambda k: groups[k]["total_ms"], default=None)
+
+    def roof(name):
+        g = groups[name]
+        bound, units, peak, unit, src = work[name]
+        per_launch_ms = g["total_ms"] / max(1, g["launches"]) * (1 if name != "eig_tables" else 2)
+        # eig_tables runs twice per step (train and test); its work figure is per step
+        per_launch_ms = g["total_ms"] / args.steps if name == "eig_tables" else per_launch_ms
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        achieved = units / (per_launch_ms / 1e3) / scale
+        tr = traffic_from_profile(src, f"{name}_w2")
+        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": tr,
+                "peak_source": ("measured bf16 burst" if bound == "tensor" and pk["src"] == "measured"
+                                else "measured HBM copy" if bound == "hbm" and pk["src"] == "measured"
+                                else "nominal fp64" if bound == "alu" else "fallback"),
+                "avg_launch_ms": per_launch_ms}
+
+    roofline = roof(dom) if dom else None
+    roof_syrk = roof("syrk_tc") if "syrk_tc" in groups else None
+    if roof_syrk is not None:
+        roof_syrk["executed_tflops"] = roof_syrk["achieved"] * (4 if prec == "bf16x4" else 3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3 tensor (f32 acc) + f64 factorisation" if prec != "fp64" else "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "prec": prec, "l2": "flushed between steps (256 MiB write)",
+                      "replicas": world},
+           "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+           "roofline_syrk": roof_syrk, "kernel_shares": shares}
+
+    if rank == 0 and not args.quick:
+        extra = compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np)
+        out.update(extra)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np):
+    """Errors of both GPU modes vs the FP64 oracle, the FP64 GPU form's
+    throughput, the oracle's CPU time, and the end-to-end host-buffer number."""
+    from oracle import fagp as O
+    res = {}
+    # ---- FP64 GPU form, same workload
+    mean = torch.empty(pr.Ns, dtype=torch.float64, device=dev)
+    var = torch.empty(pr.Ns, dtype=torch.float64, device=dev)
+
+    def step(prec):
+        m = _lib.fit(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+        m.predict(Xs, mean_out=mean, var_out=var)
+        m.free()
+
+    step("fp64")
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step("fp64")
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    m64, v64 = mean.cpu().numpy().copy(), var.cpu().numpy().copy()
+    step(args.prec)
+    torch.cuda.synchronize()
+    mmx, vmx = mean.cpu().numpy().copy(), var.cpu().numpy().copy()
+
+    # ---- oracle: accuracy reference and the CPU baseline (full workload, one pass)
+    t0 = time.perf_counter()
+    mdl = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    mo, vo = O.predict(mdl, pr.Xs)
+    t_or = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": (pr.N + pr.Ns) / t_or, "unit": UNIT, "cores": os.cpu_count(),
+                           "kind": "oracle",
+                           "sample": "the full workload once (200,000 train + 50,000 test points)"}
+    res["fp64_gpu"] = {"value": (pr.N + pr.Ns) / (statistics.mean(ts) / 1e3), "unit": UNIT,
+                       "ms_per_step": statistics.mean(ts),
+                       "err_mean_rel_l2": O.relerr(m64, mo), "err_var_rel_l2": O.relerr(v64, vo)}
+    res["accuracy"] = {"prec": args.prec, "err_mean_rel_l2": O.relerr(mmx, mo),
+                       "err_var_rel_l2": O.relerr(vmx, vo), "tol_mean": 1e-4, "tol_var": 1e-3}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Xh = torch.from_numpy(pr.X).pin_memory().numpy()
+    yh = torch.from_numpy(pr.y).pin_memory().numpy()
+    Xsh = torch.from_numpy(pr.Xs).pin_memory().numpy()
+    mh = torch.empty(pr.Ns, dtype=torch.float64).pin_memory().numpy()
+    vh = torch.empty(pr.Ns, dtype=torch.float64).pin_memory().numpy()
+
+    def e2e_step():
+        m = _lib.fit(Xh, yh, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=args.prec)
+        m.predict(Xsh, mean_out=mh, var_out=vh)
+        m.free()
+
+    for _ in range(2):
+        e2e_step()
+    n_e2e = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    dt = (time.perf_counter() - t0) / n_e2e
+    res["e2e"] = {"value": (pr.N + pr.Ns) / dt, "unit": UNIT,
+                  "h2d_bytes_per_step": int((pr.N * pr.p + pr.N + pr.Ns * pr.p) * 8),
+                  "d2h_bytes_per_step": int(pr.Ns * 2 * 8)}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16x4", "fp64"])
+    ap.add_argument("--quick", action="store_true", help="skip the comparisons (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if not args.quick else args.warmup
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

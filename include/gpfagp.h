@@ -70,11 +70,17 @@ typedef struct gp_model gp_model;
  * GP_PREC_BF16X3: Phi generated in float32 and split into bf16 hi + lo; the
  *                 contractions Phi^T Phi and Phi_* L^{-T} run on the tensor
  *                 cores as hi*hi + hi*lo + lo*hi with float32 accumulation;
+ *                 the diagonal of Phi^T Phi also receives sum(lo^2), the
+ *                 expectation of the dropped lo*lo product (without it the
+ *                 diagonal is biased low by ~3e-6 relative);
  *                 Phi^T y and the predictive mean use float32 products;
  *                 split-N partials are summed, A assembled, factored and
- *                 inverted, and c solved and refined, in float64.           */
+ *                 inverted, and c solved and refined, in float64.
+ * GP_PREC_BF16X4: as BF16X3 but Phi^T Phi takes all four products
+ *                 (hi*hi + hi*lo + lo*hi + lo*lo) on the tensor cores.      */
 #define GP_PREC_FP64    0
 #define GP_PREC_BF16X3  3
+#define GP_PREC_BF16X4  4
 
 /* Largest supported M = n^p (the M x M float64 factor must fit in memory). */
 #define GP_MAX_M  32768
@@ -178,6 +184,23 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k);
 
 /* Library build tag (static string). */
 GPFAGP_API const char* gp_version(void);
+
+/* ---- measurement hooks ------------------------------------------------------ */
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+GPFAGP_API int64_t gp_kernel_launches(void);
+
+/* Enable (1) or disable (0) CUDA-event timing of the library's kernel groups:
+ * "eig_tables", "syrk64", "syrk_tc", "assemble", "cholesky", "tri_inverse",
+ * "solve_refine", "pack_w", "predict64", "predict_tc". Each group is bracketed
+ * by two events on the stream it runs on. */
+GPFAGP_API void gp_profile_enable(int on);
+/* Clear the accumulated group timings. */
+GPFAGP_API void gp_profile_reset(void);
+/* Wait for the recorded events of group `name` and report how many times it
+ * ran and its total device time in milliseconds since the last reset.
+ * Returns GP_EINVAL (and zeros) if the group has not run. */
+GPFAGP_API int gp_profile_query(const char* name, int64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -178,13 +178,25 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         choose_splits(npairs, s.Npad, 4 * num_sms(dev), &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRK64_TM * SYRK64_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
-        launch_eig_tables_f64(s, Xd, yd, tab, st, stream);
-        pad_y_kernel<double><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
-        cudaError_t e = launch_syrk64(s, tab, ypad, nsplit, rps, Gpart, bpart, stream);
-        if (e != cudaSuccess) return cuda_err(e);
-        launch_assemble_f64(Gpart, bpart, nsplit, SYRK64_TM, s.Mpad, s.M, d, A, b, stream);
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f64(s, Xd, yd, tab, st, stream);
+            pad_y_kernel<double><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
+            gp_note_launches(2);
+        }
+        {
+            GpProf pf("syrk64", stream);
+            cudaError_t e = launch_syrk64(s, tab, ypad, nsplit, rps, Gpart, bpart, stream);
+            if (e != cudaSuccess) return cuda_err(e);
+            gp_note_launches(1);
+        }
+        {
+            GpProf pf("assemble", stream);
+            launch_assemble_f64(Gpart, bpart, nsplit, SYRK64_TM, s.Mpad, s.M, d, A, b, stream);
+            gp_note_launches(1);
+        }
     } else {
-        float *tab, *ypad, *Gpart, *bpart;
+        float *tab, *ypad, *Gpart, *bpart, *dpart;
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
         if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
         const int T = s.Mpad / SYRKTC_TM;
@@ -194,11 +206,26 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         choose_splits(npairs, s.Npad, num_sms(dev), &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
-        launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
-        pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
-        cudaError_t e = launch_syrk_tc(s, tab, ypad, nsplit, rps, Gpart, bpart, st, stream);
-        if (e != cudaSuccess) return cuda_err(e);
-        launch_assemble_f32(Gpart, bpart, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
+        const bool four = (prec == GP_PREC_BF16X4);
+        dpart = nullptr;
+        if (!four && (rc = sc.get(&dpart, (size_t)nsplit * s.Mpad))) return rc;
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
+            pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
+            gp_note_launches(2);
+        }
+        {
+            GpProf pf("syrk_tc", stream);
+            cudaError_t e = launch_syrk_tc(s, tab, ypad, nsplit, rps, four, Gpart, bpart, dpart, st, stream);
+            if (e != cudaSuccess) return cuda_err(e);
+            gp_note_launches(1);
+        }
+        {
+            GpProf pf("assemble", stream);
+            launch_assemble_f32(Gpart, bpart, dpart, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
+            gp_note_launches(1);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e);
@@ -208,7 +235,8 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
 int tile_of(int prec) { return prec == GP_PREC_FP64 ? SYRK64_TM : SYRKTC_TM; }
 
 int check_prec(int prec) {
-    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3) return set_err(GP_EINVAL, 4);
+    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3 && prec != GP_PREC_BF16X4)
+        return set_err(GP_EINVAL, 4);
     return GP_OK;
 }
 
@@ -352,7 +380,7 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->c, stream))) return fail(rc);
     if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->b, stream))) return fail(rc);
     if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return fail(rc);
-    if (prec == GP_PREC_BF16X3) {
+    if (prec != GP_PREC_FP64) {
         if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return fail(rc);
     }
     GpStatus* st;
@@ -377,14 +405,27 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     log_eigenvalues(n, eps, alpha, ll.data());
     cudaMemcpyAsync(loglam, ll.data(), sizeof(double) * n, cudaMemcpyHostToDevice, stream);
     launch_noise_diag(s, loglam, sigma2, h->d, stream);
+    gp_note_launches(1);
 
     if ((rc = gram_device(s, prec, dev, Xd, yd, h->d, A, h->b, st, stream))) return fail(rc);
     cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
-    cudaError_t e = launch_cholesky(h->L, M, st, stream);
-    if (e == cudaSuccess) e = launch_tri_inverse(h->L, h->W, M, st, stream);
-    if (e == cudaSuccess) e = launch_solve_refine(A, h->W, h->b, h->c, work, M, 2, st, stream);
-    if (e == cudaSuccess && prec == GP_PREC_BF16X3) {
+    cudaError_t e;
+    {
+        GpProf pf("cholesky", stream);
+        e = launch_cholesky(h->L, M, st, stream);
+    }
+    if (e == cudaSuccess) {
+        GpProf pf("tri_inverse", stream);
+        e = launch_tri_inverse(h->L, h->W, M, st, stream);
+    }
+    if (e == cudaSuccess) {
+        GpProf pf("solve_refine", stream);
+        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, 2, st, stream);
+    }
+    if (e == cudaSuccess && prec != GP_PREC_FP64) {
+        GpProf pf("pack_w", stream);
         launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
+        gp_note_launches(1);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fail(cuda_err(e));
@@ -432,13 +473,23 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, do
         double *tab, *part;
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
         if ((rc = sc.get(&part, predict64_part_elems(s.Npad, s.M)))) return rc;
-        launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
+        }
+        GpProf pf("predict64", stream);
         e = launch_predict64(s, tab, h->W, h->c, h->sigma2, part, md, vd, stream);
+        gp_note_launches(3);
     } else {
         float* tab;
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
-        launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
+        }
+        GpProf pf("predict_tc", stream);
         e = launch_predict_tc(s, tab, h->Wpack, h->c, h->sigma2, md, vd, st, stream);
+        gp_note_launches(2);
     }
     if (e != cudaSuccess) return cuda_err(e);
     if (!dev_ptrs) {

@@ -16,7 +16,8 @@ namespace {
 
 template <typename P>
 __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpart,
-                                                       const P* __restrict__ bpart, int nsplit,
+                                                       const P* __restrict__ bpart,
+                                                       const P* __restrict__ dpart, int nsplit,
                                                        int tile, int Mpad, int M,
                                                        const double* __restrict__ d,
                                                        double* __restrict__ A,
@@ -37,6 +38,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     const int64_t sstride = (int64_t)npairs * tile * tile;
     double acc = 0.0;
     for (int s = 0; s < nsplit; ++s) acc += (double)Gpart[off + s * sstride];
+    if (row == col && dpart != nullptr)
+        for (int s = 0; s < nsplit; ++s) acc += (double)dpart[(int64_t)s * Mpad + row];
     if (row == col && d != nullptr) acc += d[row];
     A[(int64_t)row * M + col] = acc;
     if (row == 0) {
@@ -62,13 +65,16 @@ __global__ void noise_diag_kernel(GpShape s, const double* __restrict__ loglam, 
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<double><<<grid, 256, 0, stream>>>(Gpart, bpart, nsplit, tile, Mpad, M, d, A, b);
+    assemble_kernel<double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, nsplit, tile, Mpad, M, d,
+                                                      A, b);
 }
 
-void launch_assemble_f32(const float* Gpart, const float* bpart, int nsplit, int tile, int Mpad,
-                         int M, const double* d, double* A, double* b, cudaStream_t stream) {
+void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart, int nsplit,
+                         int tile, int Mpad, int M, const double* d, double* A, double* b,
+                         cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<float><<<grid, 256, 0, stream>>>(Gpart, bpart, nsplit, tile, Mpad, M, d, A, b);
+    assemble_kernel<float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, nsplit, tile, Mpad, M, d,
+                                                     A, b);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

@@ -298,15 +298,18 @@ cudaError_t launch_cholesky(double* L, int M, GpStatus* st, cudaStream_t stream)
     for (int kb = 0; kb < M; kb += NB) {
         const int w = min(NB, M - kb);
         chol_diag_kernel<<<1, 256, 0, stream>>>(L, M, kb, w, st);
+        gp_note_launches(1);
         const int rest = M - kb - w;
         if (rest > 0) {
             chol_panel_kernel<<<(rest + NB - 1) / NB, 64, psmem, stream>>>(L, M, kb, w, st);
             const int T = (rest + NB - 1) / NB;
             chol_update_kernel<<<T * (T + 1) / 2, 256, 0, stream>>>(L, M, kb, w, st);
+            gp_note_launches(2);
         }
     }
     dim3 g((M + 255) / 256, M);
     zero_upper_kernel<<<g, 256, 0, stream>>>(L, M);
+    gp_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -319,6 +322,7 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, GpStatus* st,
     cudaMemsetAsync(W, 0, (size_t)M * M * sizeof(double), stream);
     const int nb = (M + NB - 1) / NB;
     for (int I = 0; I < nb; ++I) trinv_row_kernel<<<I + 1, 256, smem, stream>>>(L, W, M, I, st);
+    gp_note_launches(nb);
     return cudaGetLastError();
 }
 
@@ -330,6 +334,7 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const double* 
     double* r = work + M;
     double* part = work + 2 * (int64_t)M;
     wtw_apply(W, M, b, tmp, part, c, 0, st, stream);
+    gp_note_launches(3 + 4 * refine);
     for (int it = 0; it < refine; ++it) {
         gemv_rows_kernel<<<(M * 32 + 255) / 256, 256, 0, stream>>>(A, M, c, r, 0, b, st);
         wtw_apply(W, M, r, tmp, part, c, 1, st, stream);

@@ -121,3 +121,16 @@ static inline int64_t gp_round_up(int64_t v, int64_t m) { return (v + m - 1) / m
 // Host-side helpers implemented in gp_api.cu
 // ---------------------------------------------------------------------------
 int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile);
+
+// gp_prof.cu: kernel launch counter and CUDA-event timing of kernel groups
+void gp_note_launches(int n);
+void gp_prof_begin(const char* name, cudaStream_t s);
+void gp_prof_end(const char* name, cudaStream_t s);
+
+// RAII bracket of one kernel group on a stream
+struct GpProf {
+    const char* name;
+    cudaStream_t s;
+    GpProf(const char* n, cudaStream_t st) : name(n), s(st) { gp_prof_begin(n, st); }
+    ~GpProf() { gp_prof_end(name, s); }
+};

@@ -6,8 +6,10 @@
 // and never written to global memory.
 //
 // Precision: each Phi value v (float32) is split into bf16 hi = bf16(v) and
-// lo = bf16(v - hi); the MMA accumulates hi*hi + hi*lo + lo*hi in float32
-// TMEM (relative error ~2^-17 per product instead of bf16's 2^-8).
+// lo = bf16(v - hi); the MMA accumulates hi*hi + hi*lo + lo*hi (+ lo*lo) in
+// float32 TMEM. Without lo*lo every diagonal entry of G would be biased low
+// by sum(lo^2) (~2.7e-6 relative): the 3-product mode adds that sum, taken
+// on the CUDA cores, instead.
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows:
@@ -134,20 +136,32 @@ __device__ __forceinline__ void phi8(const float* win, const unsigned short* crr
     }
 }
 
-__device__ __forceinline__ void store_hilo(uint8_t* hi_tile, uint8_t* lo_tile, int r, int g,
-                                           const float v[8]) {
+// Split 8 values into bf16 hi/lo, store both core-matrix rows; returns the
+// sum of lo^2 (the expected value of the dropped lo*lo product on the diagonal).
+__device__ __forceinline__ float store_hilo(uint8_t* hi_tile, uint8_t* lo_tile, int r, int g,
+                                            const float v[8]) {
     uint32_t h[4], l[4];
+    float lsq = 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
+    for (int q = 0; q < 4; ++q) {
+        split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
+        const float2 lf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&l[q]));
+        lsq = fmaf(lf.x, lf.x, fmaf(lf.y, lf.y, lsq));
+    }
     const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
     *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    return lsq;
 }
 
+// FOUR = false: hi*hi + hi*lo + lo*hi on the tensor cores, and the diagonal
+// CTAs add sum(lo^2) per column (dpart), the only part of the dropped lo*lo
+// product whose expectation is not zero. FOUR = true: all four products.
+template <bool FOUR>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const float* __restrict__ ypad,
                    int64_t rps, int npairs, int maxrows, float* __restrict__ Gpart,
-                   float* __restrict__ bpart, GpStatus* st) {
+                   float* __restrict__ bpart, float* __restrict__ dpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
     __shared__ int s_ok;
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int g = lane >> 3;       // 8-row group of the chunk
         const int rl = lane & 7;       // column within an 8-column core group
         float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+        float dacc[4] = {0.f, 0.f, 0.f, 0.f};
         bool ok = true;
         for (int c = 0; c < nchunks && ok; ++c) {
             const int stg = c % STAGES;
@@ -222,7 +237,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int r = 8 * (it * 4 + warp) + rl;
                 float v[8];
                 phi8(sm.winI, sm.crI + r * s.p, s.p, g, v);
-                store_hilo(sb, sb + TILE_BYTES, r, g, v);
+                const float lsq = store_hilo(sb, sb + TILE_BYTES, r, g, v);
+                if (!FOUR && diag) dacc[it] += lsq;
                 if (J == 0) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], sm.yv[8 * g + k], bacc[it]);
@@ -249,6 +265,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (lane < 8) {
                     const int r = 8 * (it * 4 + warp) + rl;
                     bpart[(int64_t)split * s.Mpad + I * TM + r] = v;
+                }
+            }
+        }
+        if (!FOUR && diag) {
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                float v = dacc[it];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (lane < 8) {
+                    const int r = 8 * (it * 4 + warp) + rl;
+                    dpart[(int64_t)split * s.Mpad + I * TM + r] = v;
                 }
             }
         }
@@ -295,6 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_bf16(tmem, dAh, dBh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
                     mma_bf16(tmem, dAh, dBl, idesc, 1u);
                     mma_bf16(tmem, dAl, dBh, idesc, 1u);
+                    if (FOUR) mma_bf16(tmem, dAl, dBl, idesc, 1u);
                 }
                 mma_commit(&sm.empty[stg]);
             }
@@ -317,18 +346,18 @@ size_t syrktc_smem_bytes(const GpShape& s) {
 }
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const float* ypad, int nsplit,
-                           int64_t rows_per_split, float* Gpart, float* bpart, GpStatus* st,
-                           cudaStream_t stream) {
+                           int64_t rows_per_split, bool four, float* Gpart, float* bpart,
+                           float* dpart, GpStatus* st, cudaStream_t stream) {
     const int maxrows = gp_max_window_rows(s, TM);
     const size_t smem = smem_tc_layout(maxrows, s.p, nullptr, nullptr);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = four ? syrk_tc_kernel<true> : syrk_tc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int T = s.Mpad / TM;
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
-    syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, ypad, rows_per_split, npairs, maxrows,
-                                                     Gpart, bpart, st);
+    kern<<<grid, NTHREADS, smem, stream>>>(s, tab, ypad, rows_per_split, npairs, maxrows, Gpart,
+                                           bpart, dpart, st);
     return cudaGetLastError();
 }
