@@ -67,20 +67,21 @@ typedef struct gp_model gp_model;
 
 /* ---- precision modes ---------------------------------------------------- */
 /* GP_PREC_FP64:   every step in float64 on the CUDA cores.
- * GP_PREC_BF16X3: Phi generated in float32 and split into bf16 hi + lo; the
- *                 contractions Phi^T Phi and Phi_* L^{-T} run on the tensor
- *                 cores as hi*hi + hi*lo + lo*hi with float32 accumulation;
- *                 the diagonal of Phi^T Phi also receives sum(lo^2), the
- *                 expectation of the dropped lo*lo product (without it the
- *                 diagonal is biased low by ~3e-6 relative);
+ * GP_PREC_BF16X3: Phi generated in float32; the contractions run on the
+ *                 tensor cores as three bf16 products:
+ *                 - Phi^T Phi: each column is scaled by a power of two and
+ *                   split into two 8-bit integer slices s1 + s2/256 (exact in
+ *                   bf16); s1*s1 and s1*s2 + s2*s1 are summed EXACTLY in
+ *                   float32 TMEM for 512-row blocks and the blocks are added
+ *                   in float32 with round-to-nearest; the diagonal receives
+ *                   the dropped sum of s2^2 / 2^16;
+ *                 - Phi_* L^{-T} (variance): bf16 hi/lo split of both
+ *                   operands, hi*hi + hi*lo + lo*hi in float32;
  *                 Phi^T y and the predictive mean use float32 products;
  *                 split-N partials are summed, A assembled, factored and
- *                 inverted, and c solved and refined, in float64.
- * GP_PREC_BF16X4: as BF16X3 but Phi^T Phi takes all four products
- *                 (hi*hi + hi*lo + lo*hi + lo*lo) on the tensor cores.      */
+ *                 inverted, and c solved and refined, in float64.          */
 #define GP_PREC_FP64    0
 #define GP_PREC_BF16X3  3
-#define GP_PREC_BF16X4  4
 
 /* Largest supported M = n^p (the M x M float64 factor must fit in memory). */
 #define GP_MAX_M  32768

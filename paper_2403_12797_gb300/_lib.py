@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_ENODEV = 0, -1, -2, -3, -4, -5, -6
-PREC = {"fp64": 0, "bf16x3": 3, "bf16x4": 4}
+PREC = {"fp64": 0, "bf16x3": 3}
 FIELD = {"L": 1, "c": 2, "b": 3, "d": 4}
 
 HEADER = os.path.join(_build.ROOT, "include", "gpfagp.h")

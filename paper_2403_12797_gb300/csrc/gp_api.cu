@@ -206,24 +206,29 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         choose_splits(npairs, s.Npad, num_sms(dev), &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
-        const bool four = (prec == GP_PREC_BF16X4);
-        dpart = nullptr;
-        if (!four && (rc = sc.get(&dpart, (size_t)nsplit * s.Mpad))) return rc;
+        if ((rc = sc.get(&dpart, (size_t)nsplit * s.Mpad))) return rc;
+        unsigned int* tmax;
+        int* colexp;
+        if ((rc = sc.get(&tmax, (size_t)s.p * s.n))) return rc;
+        if ((rc = sc.get(&colexp, (size_t)s.Mpad))) return rc;
         {
             GpProf pf("eig_tables", stream);
             launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
             pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
-            gp_note_launches(2);
+            launch_table_absmax(s, tab, tmax, stream);
+            gp_note_launches(3);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tab, ypad, nsplit, rps, four, Gpart, bpart, dpart, st, stream);
+            cudaError_t e = launch_syrk_tc(s, tab, tmax, ypad, nsplit, rps, Gpart, bpart, dpart, colexp,
+                                           st, stream);
             if (e != cudaSuccess) return cuda_err(e);
             gp_note_launches(1);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_f32(Gpart, bpart, dpart, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
+            launch_assemble_f32(Gpart, bpart, dpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b,
+                                stream);
             gp_note_launches(1);
         }
     }
@@ -235,7 +240,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
 int tile_of(int prec) { return prec == GP_PREC_FP64 ? SYRK64_TM : SYRKTC_TM; }
 
 int check_prec(int prec) {
-    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3 && prec != GP_PREC_BF16X4)
+    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3)
         return set_err(GP_EINVAL, 4);
     return GP_OK;
 }

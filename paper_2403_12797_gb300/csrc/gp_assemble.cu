@@ -17,7 +17,8 @@ namespace {
 template <typename P>
 __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpart,
                                                        const P* __restrict__ bpart,
-                                                       const P* __restrict__ dpart, int nsplit,
+                                                       const P* __restrict__ dpart,
+                                                       const int* __restrict__ colexp, int nsplit,
                                                        int tile, int Mpad, int M,
                                                        const double* __restrict__ d,
                                                        double* __restrict__ A,
@@ -27,11 +28,9 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     if (col >= M) return;
     const int T = Mpad / tile;
     const int npairs = T * (T + 1) / 2;
-    int r = row, c = col;
-    if (r / tile < c / tile) {
-        r = col;
-        c = row;
-    }
+    // read the lower-triangle element (r >= c), so A is exactly symmetric
+    const int r = row >= col ? row : col;
+    const int c = row >= col ? col : row;
     const int I = r / tile, J = c / tile;
     const int q = I * (I + 1) / 2 + J;
     const int64_t off = (int64_t)q * tile * tile + (int64_t)(r % tile) * tile + (c % tile);
@@ -40,6 +39,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     for (int s = 0; s < nsplit; ++s) acc += (double)Gpart[off + s * sstride];
     if (row == col && dpart != nullptr)
         for (int s = 0; s < nsplit; ++s) acc += (double)dpart[(int64_t)s * Mpad + row];
+    if (colexp != nullptr) acc = ldexp(acc, colexp[r] + colexp[c] - 14);
     if (row == col && d != nullptr) acc += d[row];
     A[(int64_t)row * M + col] = acc;
     if (row == 0) {
@@ -65,16 +65,16 @@ __global__ void noise_diag_kernel(GpShape s, const double* __restrict__ loglam, 
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, nsplit, tile, Mpad, M, d,
-                                                      A, b);
+    assemble_kernel<double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, nullptr, nsplit, tile,
+                                                      Mpad, M, d, A, b);
 }
 
-void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart, int nsplit,
-                         int tile, int Mpad, int M, const double* d, double* A, double* b,
-                         cudaStream_t stream) {
+void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart,
+                         const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
+                         double* A, double* b, cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, nsplit, tile, Mpad, M, d,
-                                                     A, b);
+    assemble_kernel<float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, colexp, nsplit, tile, Mpad,
+                                                     M, d, A, b);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

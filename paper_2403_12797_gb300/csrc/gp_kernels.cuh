@@ -9,6 +9,9 @@ void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, d
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream);
 
+// tmax[j*n + k] = max_i |tab[j][k][i]| (float bits); zeroes tmax first.
+void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmax, cudaStream_t stream);
+
 // ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
 // Tile 64 x 64, lower-triangular tile pairs x N splits.
 constexpr int SYRK64_TM = 64;
@@ -21,21 +24,25 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
 constexpr int SYRKTC_TM = 128;
 constexpr int SYRKTC_BK = 32;
 size_t syrktc_smem_bytes(const GpShape& s);
-// four = false: 3 products + diagonal sum(lo^2) into dpart (nsplit x Mpad);
-// four = true: 4 products (dpart unused).
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const float* ypad, int nsplit,
-                           int64_t rows_per_split, bool four, float* Gpart, float* bpart,
-                           float* dpart, GpStatus* st, cudaStream_t stream);
+// Gpart holds column-scaled partial tiles (units 2^(14 - E_m - E_m')), dpart
+// the scaled diagonal corrections (nsplit x Mpad), colexp[m] = E_m (Mpad),
+// bpart the unscaled Phi^T y partials.
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
+                           const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
+                           float* bpart, float* dpart, int* colexp, GpStatus* st,
+                           cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);
 // b = sum_s bpart[s]. d may be NULL (plain Gram).
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream);
-// dpart (nullable): per-split diagonal corrections added to A[m][m].
-void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart, int nsplit,
-                         int tile, int Mpad, int M, const double* d, double* A, double* b,
-                         cudaStream_t stream);
+// dpart (nullable): per-split diagonal corrections added to the scaled
+// diagonal; colexp (nullable): per-column exponents, A[m][m'] is the split
+// sum times 2^(E_m + E_m' - 14).
+void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart,
+                         const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
+                         double* A, double* b, cudaStream_t stream);
 // d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
                        cudaStream_t stream);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       double* __restrict__ mean, double* __restrict__ var, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wv;
-    __shared__ int s_ok;
+    __shared__ int s_ok[2];
     char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     SmemP sm;
     smem_p_layout(maxrows, s.p, base, &sm);
@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         double macc = 0.0, vacc = 0.0;
         bool ok = true;
         int gc = 0;
+        int nbc = 0;
         for (int sup = 0; sup < nsuper && ok; ++sup) {
             const int b0 = sup * SUPER;
             const int nblk = min(SUPER, nblocks - b0);
@@ -146,16 +147,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 named_bar_sync(1, NPROD);
                 for (int r = 0; r < wv.nrows; ++r)
                     sm.win[r * TT + t] = __ldg(tab + (int64_t)sm.tr[r] * s.Npad + t0 + t);
+                // one thread waits and broadcasts; the two flags alternate so a
+                // flag is rewritten only after every reader passed a later barrier
+                const int slot = nbc++ & 1;
                 if (tid == 0) {
                     int fine = 1;
                     if (gc >= STAGES && !mbar_wait(&sm.empty[stg], ((gc / STAGES) - 1) & 1)) {
                         gp_set_status(st, GP_ETIMEOUT, 11);
                         fine = 0;
                     }
-                    s_ok = fine;
+                    s_ok[slot] = fine;
                 }
                 named_bar_sync(1, NPROD);
-                if (!s_ok) {
+                if (!s_ok[slot]) {
                     ok = false;
                     break;
                 }
@@ -195,13 +199,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!ok) break;
             // epilogue of this super-tile: rows of Z from TMEM. One thread
             // waits and broadcasts, so all producers take the same branch.
+            const int slot = nbc++ & 1;
             if (tid == 0) {
                 int fine = mbar_wait(sm.accf, sup & 1) ? 1 : 0;
                 if (!fine) gp_set_status(st, GP_ETIMEOUT, 12);
-                s_ok = fine;
+                s_ok[slot] = fine;
             }
             named_bar_sync(1, NPROD);
-            const bool got = s_ok != 0;
+            const bool got = s_ok[slot] != 0;
             tc_fence_after();
             if (got) {
                 for (int bb = 0; bb < nblk; ++bb) {

@@ -1,57 +1,78 @@
-// gp_syrk_tc.cu -- fused Phi generation + bf16x3 tensor-core Gram (tcgen05, TMEM).
+// gp_syrk_tc.cu -- fused Phi generation + exact-sum bf16 tensor-core Gram (tcgen05, TMEM).
 //
 // Computes G = Phi^T Phi and b = Phi^T y over the N training rows (the
 // products of Lambda-bar and of W in Sec. 2.2). Phi (Eq. 19) is generated in
 // shared memory, chunk by chunk, from the per-dimension eigenfunction tables
 // and never written to global memory.
 //
-// Precision: each Phi value v (float32) is split into bf16 hi = bf16(v) and
-// lo = bf16(v - hi); the MMA accumulates hi*hi + hi*lo + lo*hi (+ lo*lo) in
-// float32 TMEM. Without lo*lo every diagonal entry of G would be biased low
-// by sum(lo^2) (~2.7e-6 relative): the 3-product mode adds that sum, taken
-// on the CUDA cores, instead.
+// Precision. The tensor cores' float32 accumulation truncates, so a long
+// sum in TMEM drifts low by ~2e-8 per accumulate step; over the thousands of
+// steps of a large N that bias (~1e-4 relative on the diagonal of G) is
+// amplified by the conditioning of A into percent-level errors of the
+// posterior. This kernel therefore makes every tensor-core sum EXACT:
+//   * each column m is scaled by 2^(7 - E_m), where 2^(E_m) bounds |Phi[:, m]|
+//     (the product of the per-dimension table maxima), so |Phi * 2^(7-E_m)| <= 128;
+//   * the scaled value w is split into integers s1 = rint(w) and
+//     s2 = rint((w - s1) * 256), both in [-128, 128] and exact in bf16;
+//   * acc1 += s1 s1' and acc2 += s1 s2' + s2 s1' are integer sums below 2^24,
+//     exact in float32, for blocks of 512 rows;
+//   * after each block the producers add acc1 + acc2 / 256 into float32
+//     registers (round to nearest: unbiased), while the MMAs fill the other
+//     TMEM buffer (two buffers x 256 columns = all 512 TMEM columns).
+// The dropped s2 s2' / 2^16 term has zero mean off the diagonal; on the
+// diagonal its sum (sum of s2^2, exact on the CUDA cores) is added back
+// (dpart). Representation error: |w - s1 - s2/256| <= 2^-9 (<= 2^-16 of the
+// column bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows:
 //   warps 0-3  producers: copy the tables' window rows for the chunk into
-//              shared memory, form the Phi tiles of column tiles I and J in
-//              the K-major core-matrix layout (8 columns x 16 bytes), split
-//              them into hi/lo and publish the pipeline stage; the CTAs with
-//              J == 0 also accumulate b_I = Phi_I^T y and reduce it with warp
-//              shuffles. After the last chunk they are the epilogue: TMEM ->
-//              registers -> float32 partial tile in global memory.
+//              shared memory, form Phi for column tiles I and J in the K-major
+//              core-matrix layout (8 columns x 16 bytes), split, publish the
+//              stage; J == 0 CTAs also accumulate b_I = Phi_I^T y (float32,
+//              warp-shuffle reduction). They drain TMEM and write the
+//              (scaled) partial tile at the end.
 //   warp 4     allocates TMEM and issues the MMAs (one elected lane):
-//              6 x (128 x 128 x 16) per 32-row chunk; tcgen05.commit frees
-//              the stage.
-// Split partials are summed in float64 by gp_assemble.cu.
+//              3 x (128 x 128 x 16) per 16 rows; tcgen05.commit frees stages
+//              and signals finished blocks.
+// Split partials are summed and unscaled in float64 by gp_assemble.cu.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
 
 namespace {
 
-constexpr int TM = SYRKTC_TM;         // 128
-constexpr int BK = SYRKTC_BK;         // 32 data rows per chunk
+constexpr int TM = SYRKTC_TM;              // 128
+constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
 constexpr int STAGES = 4;
-constexpr int WSTRIDE = BK + 4;       // floats per window row (bank-conflict padding)
-constexpr int TILE_BYTES = TM * BK * 2;  // one bf16 operand tile: 8 KB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr uint32_t LBO = 128;         // K-adjacent core matrices
-constexpr uint32_t SBO = (BK / 8) * 128;  // 8-row groups
-constexpr int NPROD = 128;
+constexpr int BLOCK_CHUNKS = 16;           // 512 rows per exact TMEM block
+constexpr int WSTRIDE = BK + 4;            // floats per window row (bank-conflict padding)
+constexpr int TILE_BYTES = TM * BK * 2;    // one bf16 operand tile: 8 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A s2, B s1, B s2
+constexpr uint32_t LBO = 128;              // K-adjacent core matrices
+constexpr uint32_t SBO = (BK / 8) * 128;   // 8-row groups
+constexpr int NPROD = 256;                 // 8 producer warps
+constexpr int NPW = NPROD / 32;
+constexpr int IT = (TM / 8) / NPW;         // 8-column core groups per producer warp
+constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain
+constexpr int MMA_WARP = NPW;
 constexpr int NTHREADS = NPROD + 32;
+constexpr uint32_t TMEM_COLS = 512;        // 2 buffers x (acc1 | acc2)
 
 struct SmemTC {
-    uint8_t* stage;      // STAGES x STAGE_BYTES (1024-aligned)
-    float* winI;         // maxrows x WSTRIDE
+    uint8_t* stage;       // STAGES x STAGE_BYTES (1024-aligned)
+    float* winI;          // maxrows x WSTRIDE
     float* winJ;
-    float* yv;           // BK
+    float* yv;            // BK
+    float* scI;           // TM column scales 2^(7 - E)
+    float* scJ;
     int* trI;
     int* trJ;
     unsigned short* crI;  // TM x p
     unsigned short* crJ;
-    uint64_t* full;      // STAGES
-    uint64_t* empty;     // STAGES
-    uint64_t* accf;      // 1
+    uint64_t* full;       // STAGES
+    uint64_t* empty;      // STAGES
+    uint64_t* accf;       // 2: block finished in TMEM buffer u
+    uint64_t* drained;    // 2: TMEM buffer u has been read back
     uint32_t* tmem_base;
 };
 
@@ -67,19 +88,24 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base,
     size_t oWI = take(sizeof(float) * maxrows * WSTRIDE, 16);
     size_t oWJ = take(sizeof(float) * maxrows * WSTRIDE, 16);
     size_t oY = take(sizeof(float) * BK, 16);
+    size_t oSI = take(sizeof(float) * TM, 16);
+    size_t oSJ = take(sizeof(float) * TM, 16);
     size_t oTI = take(sizeof(int) * maxrows, 16);
     size_t oTJ = take(sizeof(int) * maxrows, 16);
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
     size_t oCJ = take(sizeof(unsigned short) * TM * p, 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
-    size_t oA = take(sizeof(uint64_t), 8);
+    size_t oA = take(sizeof(uint64_t) * 2, 8);
+    size_t oD = take(sizeof(uint64_t) * 2, 8);
     size_t oT = take(sizeof(uint32_t), 8);
     if (L) {
         L->stage = (uint8_t*)(base + oS);
         L->winI = (float*)(base + oWI);
         L->winJ = (float*)(base + oWJ);
         L->yv = (float*)(base + oY);
+        L->scI = (float*)(base + oSI);
+        L->scJ = (float*)(base + oSJ);
         L->trI = (int*)(base + oTI);
         L->trJ = (int*)(base + oTJ);
         L->crI = (unsigned short*)(base + oCI);
@@ -87,18 +113,40 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base,
         L->full = (uint64_t*)(base + oF);
         L->empty = (uint64_t*)(base + oE);
         L->accf = (uint64_t*)(base + oA);
+        L->drained = (uint64_t*)(base + oD);
         L->tmem_base = (uint32_t*)(base + oT);
     }
     return off + 1024;  // slack for aligning the dynamic base
 }
 
-__device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0, int* tr,
-                           unsigned short* cr, int tid, int nthr) {
+// exponent e with |x| < 2^e (0 for x == 0)
+__device__ __forceinline__ int bound_exp(unsigned int bits) {
+    int e = 0;
+    frexpf(__uint_as_float(bits), &e);
+    return e;
+}
+
+// Window rows, column -> window-row map, and column scales of one tile.
+__device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0,
+                           const unsigned int* __restrict__ tmax, int* tr, unsigned short* cr,
+                           float* sc, int* colexp_out, int tid, int nthr) {
     for (int r = tid; r < w.nrows; r += nthr) tr[r] = window_table_row(s, w, r);
     for (int e = tid; e < TM * s.p; e += nthr) {
         int c = e / s.p, j = e % s.p;
         int m = m0 + c;
         cr[e] = (unsigned short)(m < s.M ? window_row(s, w, j, m) : 0xFFFF);
+    }
+    for (int c = tid; c < TM; c += nthr) {
+        const int m = m0 + c;
+        if (m >= s.M) {
+            sc[c] = 0.f;
+            continue;
+        }
+        int E = 0;
+        for (int j = 0; j < s.p; ++j) E += bound_exp(tmax[j * s.n + (m / s.stride[j]) % s.n]);
+        if (E < -100) E = -100;
+        sc[c] = ldexpf(1.f, 7 - E);
+        if (colexp_out) colexp_out[m] = E;
     }
 }
 
@@ -114,7 +162,7 @@ __device__ __forceinline__ void load_window(const GpShape& s, const float* __res
     }
 }
 
-// Phi values of column r (window rows cr[r*p..]) for data rows 8g..8g+7 of the chunk.
+// Phi values of column r (window rows crr[0..p)) for data rows 8g..8g+7 of the chunk.
 __device__ __forceinline__ void phi8(const float* win, const unsigned short* crr, int p, int g,
                                      float v[8]) {
     if (crr[0] == 0xFFFF) {
@@ -136,35 +184,40 @@ __device__ __forceinline__ void phi8(const float* win, const unsigned short* crr
     }
 }
 
-// Split 8 values into bf16 hi/lo, store both core-matrix rows; returns the
-// sum of lo^2 (the expected value of the dropped lo*lo product on the diagonal).
-__device__ __forceinline__ float store_hilo(uint8_t* hi_tile, uint8_t* lo_tile, int r, int g,
-                                            const float v[8]) {
-    uint32_t h[4], l[4];
-    float lsq = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-        const float2 lf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&l[q]));
-        lsq = fmaf(lf.x, lf.x, fmaf(lf.y, lf.y, lsq));
-    }
-    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
-    *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    return lsq;
+__device__ __forceinline__ uint32_t pack_bf16x2_exact(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // exact: |a|, |b| <= 128 integers
+    return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// FOUR = false: hi*hi + hi*lo + lo*hi on the tensor cores, and the diagonal
-// CTAs add sum(lo^2) per column (dpart), the only part of the dropped lo*lo
-// product whose expectation is not zero. FOUR = true: all four products.
-template <bool FOUR>
+// Scale 8 values by sc, split into integer slices s1, s2, store both
+// core-matrix rows; returns sum(s2^2).
+__device__ __forceinline__ float store_slices(uint8_t* s1_tile, uint8_t* s2_tile, int r, int g,
+                                              const float v[8], float sc) {
+    uint32_t h[4], l[4];
+    float dsq = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;
+        const float a0 = rintf(w0), a1 = rintf(w1);
+        const float b0 = rintf((w0 - a0) * 256.f), b1 = rintf((w1 - a1) * 256.f);
+        h[q] = pack_bf16x2_exact(a0, a1);
+        l[q] = pack_bf16x2_exact(b0, b1);
+        dsq = fmaf(b0, b0, fmaf(b1, b1, dsq));
+    }
+    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
+    *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(s2_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    return dsq;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
-    syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const float* __restrict__ ypad,
-                   int64_t rps, int npairs, int maxrows, float* __restrict__ Gpart,
-                   float* __restrict__ bpart, float* __restrict__ dpart, GpStatus* st) {
+    syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmax,
+                   const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows,
+                   float* __restrict__ Gpart, float* __restrict__ bpart, float* __restrict__ dpart,
+                   int* __restrict__ colexp, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
-    __shared__ int s_ok;
+    __shared__ int s_ok[2];
     char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     SmemTC sm;
     smem_tc_layout(maxrows, s.p, base, &sm);
@@ -180,6 +233,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int64_t r1 = r0 + rps;
     if (r1 > s.Npad) r1 = s.Npad;
     const int nchunks = r0 < r1 ? (int)((r1 - r0) / BK) : 0;
+    const int nblocks = (nchunks + BLOCK_CHUNKS - 1) / BLOCK_CHUNKS;
 
     if (tid == 0) {
         tile_window(s, I * TM, TM, &wI);
@@ -188,27 +242,72 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.full[i], NPROD);
             mbar_init(&sm.empty[i], 1);
         }
-        mbar_init(sm.accf, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.accf[i], 1);
+            mbar_init(&sm.drained[i], NPROD);
+        }
         mbar_fence_init();
     }
-    if (warp == 4) tmem_alloc(sm.tmem_base, TM);
+    if (warp == MMA_WARP) tmem_alloc(sm.tmem_base, TMEM_COLS);
     __syncthreads();
     if (tid < NPROD) {
-        setup_tile(s, wI, I * TM, sm.trI, sm.crI, tid, NPROD);
-        if (!diag) setup_tile(s, wJ, J * TM, sm.trJ, sm.crJ, tid, NPROD);
+        setup_tile(s, wI, I * TM, tmax, sm.trI, sm.crI, sm.scI, (J == 0 && split == 0) ? colexp : nullptr,
+                   tid, NPROD);
+        if (!diag) setup_tile(s, wJ, J * TM, tmax, sm.trJ, sm.crJ, sm.scJ, nullptr, tid, NPROD);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_base;
 
-    if (warp < 4) {
+    if (warp < NPW) {
         // ------------------------------------------------------------ producers
         const int g = lane >> 3;       // 8-row group of the chunk
         const int rl = lane & 7;       // column within an 8-column core group
-        float bacc[4] = {0.f, 0.f, 0.f, 0.f};
-        float dacc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (tile rows)
+        const int half = warp >> 2;    // tile columns CPT*half ..
+        float bacc[IT], dacc[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) bacc[it] = dacc[it] = 0.f;
+        float gacc[CPT];               // this thread's part of its tile row
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) gacc[i] = 0.f;
         bool ok = true;
+
+        // One thread waits and broadcasts, so every producer takes the same
+        // path. Successive calls alternate between two flags: a flag is
+        // rewritten only after the barrier of the following call, which every
+        // reader of its previous value has passed.
+        int nbc = 0;
+        auto bcast_wait = [&](uint64_t* bar, uint32_t parity, int site) -> bool {
+            const int slot = nbc++ & 1;
+            if (tid == 0) {
+                int fine = mbar_wait(bar, parity) ? 1 : 0;
+                if (!fine) gp_set_status(st, GP_ETIMEOUT, site);
+                s_ok[slot] = fine;
+            }
+            named_bar_sync(1, NPROD);
+            return s_ok[slot] != 0;
+        };
+        auto drain = [&](int d) -> bool {
+            const int u = d & 1;
+            if (!bcast_wait(&sm.accf[u], (d >> 1) & 1, 4)) return false;
+            tc_fence_after();
+            const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + half * CPT;
+#pragma unroll
+            for (int ch = 0; ch < CPT / 16; ++ch) {
+                float a1[16], a2[16];
+                tmem_ld16(tmem + lrow + ch * 16, a1);
+                tmem_ld16(tmem + lrow + 128 + ch * 16, a2);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) gacc[ch * 16 + i] += fmaf(a2[i], 1.f / 256.f, a1[i]);
+            }
+            tc_fence_before();
+            mbar_arrive(&sm.drained[u]);
+            return true;
+        };
+
+        int next_drain = 0;
         for (int c = 0; c < nchunks && ok; ++c) {
             const int stg = c % STAGES;
             const int64_t i0 = r0 + (int64_t)c * BK;
@@ -216,29 +315,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             load_window(s, tab, sm.trI, wI.nrows, i0, sm.winI, tid);
             if (!diag) load_window(s, tab, sm.trJ, wJ.nrows, i0, sm.winJ, tid);
             if (tid < BK) sm.yv[tid] = ypad[i0 + tid];
-            // one thread waits for the stage to be released by the MMAs and
-            // broadcasts the outcome, so every producer leaves the loop together
-            if (tid == 0) {
-                int fine = 1;
-                if (c >= STAGES && !mbar_wait(&sm.empty[stg], ((c / STAGES) - 1) & 1)) {
-                    gp_set_status(st, GP_ETIMEOUT, 1);
-                    fine = 0;
+            if (c >= STAGES) {
+                if (!bcast_wait(&sm.empty[stg], ((c / STAGES) - 1) & 1, 1)) {
+                    ok = false;
+                    break;
                 }
-                s_ok = fine;
-            }
-            named_bar_sync(1, NPROD);
-            if (!s_ok) {
-                ok = false;
-                break;
+            } else {
+                named_bar_sync(1, NPROD);
             }
             uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
 #pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                const int r = 8 * (it * 4 + warp) + rl;
+            for (int it = 0; it < IT; ++it) {
+                const int r = 8 * (it * NPW + warp) + rl;
                 float v[8];
                 phi8(sm.winI, sm.crI + r * s.p, s.p, g, v);
-                const float lsq = store_hilo(sb, sb + TILE_BYTES, r, g, v);
-                if (!FOUR && diag) dacc[it] += lsq;
+                const float dsq = store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[r]);
+                if (diag) dacc[it] += dsq;
                 if (J == 0) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], sm.yv[8 * g + k], bacc[it]);
@@ -246,56 +338,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (!diag) {
 #pragma unroll
-                for (int it = 0; it < 4; ++it) {
-                    const int r = 8 * (it * 4 + warp) + rl;
+                for (int it = 0; it < IT; ++it) {
+                    const int r = 8 * (it * NPW + warp) + rl;
                     float v[8];
                     phi8(sm.winJ, sm.crJ + r * s.p, s.p, g, v);
-                    store_hilo(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v);
+                    store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, sm.scJ[r]);
                 }
             }
             fence_proxy_async_smem();
             mbar_arrive(&sm.full[stg]);
+            // drain a finished block once STAGES chunks of the next one are queued
+            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) - 1 + STAGES <= c) {
+                if (!drain(next_drain)) {
+                    ok = false;
+                    break;
+                }
+                ++next_drain;
+            }
+        }
+        while (ok && next_drain < nblocks) {
+            if (!drain(next_drain)) ok = false;
+            ++next_drain;
         }
         if (J == 0) {
 #pragma unroll
-            for (int it = 0; it < 4; ++it) {
+            for (int it = 0; it < IT; ++it) {
                 float v = bacc[it];
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (lane < 8) {
-                    const int r = 8 * (it * 4 + warp) + rl;
-                    bpart[(int64_t)split * s.Mpad + I * TM + r] = v;
-                }
+                if (lane < 8) bpart[(int64_t)split * s.Mpad + I * TM + 8 * (it * NPW + warp) + rl] = v;
             }
         }
-        if (!FOUR && diag) {
+        if (diag) {
 #pragma unroll
-            for (int it = 0; it < 4; ++it) {
+            for (int it = 0; it < IT; ++it) {
                 float v = dacc[it];
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (lane < 8) {
-                    const int r = 8 * (it * 4 + warp) + rl;
-                    dpart[(int64_t)split * s.Mpad + I * TM + r] = v;
-                }
+                if (lane < 8)
+                    dpart[(int64_t)split * s.Mpad + I * TM + 8 * (it * NPW + warp) + rl] = v * (1.f / 65536.f);
             }
         }
-        // ------------------------------------------------------------ epilogue
-        bool got = ok && mbar_wait(sm.accf, 0);
-        if (!got && ok) gp_set_status(st, GP_ETIMEOUT, 2);
-        got = __all_sync(0xffffffffu, got);  // tcgen05.ld is warp-collective
-        tc_fence_after();
-        if (got) {
-            const int row = warp * 32 + lane;
-            float* out = Gpart + ((int64_t)split * npairs + q) * (TM * TM) + (int64_t)row * TM;
-#pragma unroll 1
-            for (int ch = 0; ch < TM / 32; ++ch) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
-                float4* o4 = reinterpret_cast<float4*>(out + ch * 32);
+        if (ok) {
+            const int row = quarter * 32 + lane;
+            float4* o4 = reinterpret_cast<float4*>(Gpart + ((int64_t)split * npairs + q) * (TM * TM) +
+                                                   (int64_t)row * TM + half * CPT);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) o4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-            }
+            for (int k = 0; k < CPT / 4; ++k)
+                o4[k] = make_float4(gacc[4 * k], gacc[4 * k + 1], gacc[4 * k + 2], gacc[4 * k + 3]);
         }
     } else {
         // ------------------------------------------------------------ MMA issuer
@@ -304,38 +394,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sbase = smem_u32(sm.stage);
             for (int c = 0; c < nchunks; ++c) {
                 const int stg = c % STAGES;
+                const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS, u = d & 1;
+                if (cb == 0 && d >= 2 && !mbar_wait(&sm.drained[u], ((d >> 1) - 1) & 1)) {
+                    gp_set_status(st, GP_ETIMEOUT, 5);
+                    break;
+                }
                 if (!mbar_wait(&sm.full[stg], (c / STAGES) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 3);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_hi = sbase + stg * STAGE_BYTES;
-                const uint32_t a_lo = a_hi + TILE_BYTES;
-                const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TILE_BYTES;
-                const uint32_t b_lo = diag ? a_lo : a_hi + 3 * TILE_BYTES;
+                const uint32_t acc1 = tmem + (uint32_t)u * 256;
+                const uint32_t acc2 = acc1 + 128;
+                const uint32_t a1 = sbase + stg * STAGE_BYTES;
+                const uint32_t a2 = a1 + TILE_BYTES;
+                const uint32_t b1 = diag ? a1 : a1 + 2 * TILE_BYTES;
+                const uint32_t b2 = diag ? a2 : a1 + 3 * TILE_BYTES;
 #pragma unroll
                 for (int ks = 0; ks < BK / 16; ++ks) {
                     const uint32_t ko = ks * 2 * LBO;
-                    const uint64_t dAh = smem_desc(a_hi + ko, LBO, SBO);
-                    const uint64_t dAl = smem_desc(a_lo + ko, LBO, SBO);
-                    const uint64_t dBh = smem_desc(b_hi + ko, LBO, SBO);
-                    const uint64_t dBl = smem_desc(b_lo + ko, LBO, SBO);
-                    mma_bf16(tmem, dAh, dBh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem, dAh, dBl, idesc, 1u);
-                    mma_bf16(tmem, dAl, dBh, idesc, 1u);
-                    if (FOUR) mma_bf16(tmem, dAl, dBl, idesc, 1u);
+                    const uint64_t dA1 = smem_desc(a1 + ko, LBO, SBO);
+                    const uint64_t dA2 = smem_desc(a2 + ko, LBO, SBO);
+                    const uint64_t dB1 = smem_desc(b1 + ko, LBO, SBO);
+                    const uint64_t dB2 = smem_desc(b2 + ko, LBO, SBO);
+                    const uint32_t acc = (cb > 0 || ks > 0) ? 1u : 0u;
+                    mma_bf16(acc1, dA1, dB1, idesc, acc);
+                    mma_bf16(acc2, dA1, dB2, idesc, acc);
+                    mma_bf16(acc2, dA2, dB1, idesc, 1u);
                 }
                 mma_commit(&sm.empty[stg]);
+                if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(&sm.accf[u]);
             }
-            mma_commit(sm.accf);
         }
         __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         tc_fence_after();
-        tmem_dealloc(tmem, TM);
+        tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
@@ -345,19 +442,20 @@ size_t syrktc_smem_bytes(const GpShape& s) {
     return smem_tc_layout(gp_max_window_rows(s, TM), s.p, nullptr, nullptr);
 }
 
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const float* ypad, int nsplit,
-                           int64_t rows_per_split, bool four, float* Gpart, float* bpart,
-                           float* dpart, GpStatus* st, cudaStream_t stream) {
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
+                           const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
+                           float* bpart, float* dpart, int* colexp, GpStatus* st,
+                           cudaStream_t stream) {
     const int maxrows = gp_max_window_rows(s, TM);
     const size_t smem = smem_tc_layout(maxrows, s.p, nullptr, nullptr);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    auto kern = four ? syrk_tc_kernel<true> : syrk_tc_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const int T = s.Mpad / TM;
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
-    kern<<<grid, NTHREADS, smem, stream>>>(s, tab, ypad, rows_per_split, npairs, maxrows, Gpart,
-                                           bpart, dpart, st);
+    syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmax, ypad, rows_per_split, npairs,
+                                                     maxrows, Gpart, bpart, dpart, colexp, st);
     return cudaGetLastError();
 }

@@ -17,8 +17,7 @@ from paper_2403_12797_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": dict(G=1e-12, mean=1e-10, var=1e-10),
-       "bf16x3": dict(G=3e-5, mean=1e-4, var=1e-3),
-       "bf16x4": dict(G=3e-5, mean=1e-4, var=1e-3)}
+       "bf16x3": dict(G=3e-5, mean=1e-4, var=1e-3)}
 
 GRAM_CASES = [
     # (seed, N, p, n): ragged N, M not a multiple of the tile, several tiles, wrap of digits
@@ -34,7 +33,7 @@ GRAM_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("seed,N,p,n", GRAM_CASES)
 def test_gram_matches_oracle(prec, seed, N, p, n):
     pr = W.random_problem(seed, N, 1, p, n, eps=1.1, alpha=0.9)
@@ -67,7 +66,7 @@ def _small_cases():
     return out
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("case", range(6))
 def test_fit_predict_matches_oracle(prec, case):
     pr = _small_cases()[case]
@@ -83,7 +82,7 @@ def test_fit_predict_matches_oracle(prec, case):
     m.free()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_workload2_full_size(prec):
     pr = W.workload2()
     m, mean, var = _fit_predict(pr, prec)
