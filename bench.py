@@ -283,7 +283,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16x3 tensor (f32 acc) + f64 factorisation" if prec != "fp64" else "f64",
+           "dtype": "bf16 tensor (f32 acc, exact blocks) + f64 factorisation" if prec != "fp64" else "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "prec": prec, "l2": "flushed between steps (256 MiB write)",
                       "replicas": world},
@@ -374,7 +374,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--quick", action="store_true", help="skip the comparisons (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.quick else args.warmup

@@ -66,22 +66,22 @@ typedef struct gp_model gp_model;
 #define GP_ENODEV   (-6)  /* no usable sm_103 device                           */
 
 /* ---- precision modes ---------------------------------------------------- */
-/* GP_PREC_FP64:   every step in float64 on the CUDA cores.
- * GP_PREC_BF16X3: Phi generated in float32; the contractions run on the
- *                 tensor cores as three bf16 products:
- *                 - Phi^T Phi: each column is scaled by a power of two and
- *                   split into two 8-bit integer slices s1 + s2/256 (exact in
- *                   bf16); s1*s1 and s1*s2 + s2*s1 are summed EXACTLY in
- *                   float32 TMEM for 512-row blocks and the blocks are added
- *                   in float32 with round-to-nearest; the diagonal receives
- *                   the dropped sum of s2^2 / 2^16;
- *                 - Phi_* L^{-T} (variance): bf16 hi/lo split of both
- *                   operands, hi*hi + hi*lo + lo*hi in float32;
- *                 Phi^T y and the predictive mean use float32 products;
- *                 split-N partials are summed, A assembled, factored and
- *                 inverted, and c solved and refined, in float64.          */
-#define GP_PREC_FP64    0
-#define GP_PREC_BF16X3  3
+/* GP_PREC_FP64:  every step in float64 on the CUDA cores.
+ * GP_PREC_MIXED: Phi generated in float32; the contractions run on the
+ *                tensor cores with bf16 operands:
+ *                - Phi^T Phi: each column is scaled by a power of two so that
+ *                  |w| <= 128 and split into the integer s1 = rint(w) (exact
+ *                  in bf16) and lo = bf16(w - s1); s1*s1' is summed EXACTLY
+ *                  in float32 TMEM over 512-row blocks, s1*lo' + lo*s1' +
+ *                  lo*lo' beside it; blocks are added in float32 with
+ *                  round-to-nearest (no truncation drift);
+ *                - Phi_* L^{-T} (variance): bf16 hi/lo split of both
+ *                  operands, hi*hi + hi*lo + lo*hi in float32;
+ *                Phi^T y and the predictive mean use float32 products;
+ *                split-N partials are summed, A assembled, factored and
+ *                inverted, and c solved and refined, in float64.           */
+#define GP_PREC_FP64   0
+#define GP_PREC_MIXED  3
 
 /* Largest supported M = n^p (the M x M float64 factor must fit in memory). */
 #define GP_MAX_M  32768
@@ -89,7 +89,7 @@ typedef struct gp_model gp_model;
 /* ---- spec entry points -------------------------------------------- */
 
 /* Fit the posterior of Sec. 2.2 on host arrays X (N x p) and y (N), in the
- * GP_PREC_BF16X3 mode on the current device and the legacy default stream.
+ * GP_PREC_MIXED mode on the current device and the legacy default stream.
  * Returns a model handle, or NULL on failure (gp_last_error() tells why). */
 GPFAGP_API gp_model* gp_fit(const double* X, const double* y, int64_t N, int p, int n,
                             double eps, double alpha, double sigma2);

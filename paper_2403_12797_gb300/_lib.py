@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_ENODEV = 0, -1, -2, -3, -4, -5, -6
-PREC = {"fp64": 0, "bf16x3": 3}
+PREC = {"fp64": 0, "mixed": 3}
 FIELD = {"L": 1, "c": 2, "b": 3, "d": 4}
 
 HEADER = os.path.join(_build.ROOT, "include", "gpfagp.h")
@@ -193,7 +193,7 @@ class Model:
             pass
 
 
-def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "bf16x3",
+def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "mixed",
         stream=None) -> Model:
     """Fit (Sec. 2.2, M x M form) on host numpy arrays or device tensors."""
     X, y, N, p, dev = _prep_xy(X, y)
@@ -233,7 +233,7 @@ def gram(X, y, n: int, eps: float, alpha: float, prec: str = "fp64", stream=None
     return G, b
 
 
-def fit_batch(problems: Sequence[Tuple], prec: str = "bf16x3", stream=None) -> List[Model]:
+def fit_batch(problems: Sequence[Tuple], prec: str = "mixed", stream=None) -> List[Model]:
     """Fit many independent problems; each item is (X, y, n, eps, alpha, sigma2)."""
     cnt = len(problems)
     args = (FitArgs * cnt)()

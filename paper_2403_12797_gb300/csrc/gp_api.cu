@@ -28,7 +28,7 @@ struct gp_model {
     double* c;              // M, A^{-1} b
     double* b;              // M, Phi^T y
     double* d;              // M, sigma^2 / lambda_m (clamped)
-    uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_BF16X3 only)
+    uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
 };
 
 namespace {
@@ -196,7 +196,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             gp_note_launches(1);
         }
     } else {
-        float *tab, *ypad, *Gpart, *bpart, *dpart;
+        float *tab, *ypad, *Gpart, *bpart;
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
         if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
         const int T = s.Mpad / SYRKTC_TM;
@@ -206,7 +206,6 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         choose_splits(npairs, s.Npad, num_sms(dev), &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
-        if ((rc = sc.get(&dpart, (size_t)nsplit * s.Mpad))) return rc;
         unsigned int* tmax;
         int* colexp;
         if ((rc = sc.get(&tmax, (size_t)s.p * s.n))) return rc;
@@ -220,14 +219,14 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tab, tmax, ypad, nsplit, rps, Gpart, bpart, dpart, colexp,
-                                           st, stream);
+            cudaError_t e = launch_syrk_tc(s, tab, tmax, ypad, nsplit, rps, Gpart, bpart, colexp, st,
+                                           stream);
             if (e != cudaSuccess) return cuda_err(e);
             gp_note_launches(1);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_f32(Gpart, bpart, dpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b,
+            launch_assemble_f32(Gpart, bpart, nullptr, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b,
                                 stream);
             gp_note_launches(1);
         }
@@ -240,7 +239,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
 int tile_of(int prec) { return prec == GP_PREC_FP64 ? SYRK64_TM : SYRKTC_TM; }
 
 int check_prec(int prec) {
-    if (prec != GP_PREC_FP64 && prec != GP_PREC_BF16X3)
+    if (prec != GP_PREC_FP64 && prec != GP_PREC_MIXED)
         return set_err(GP_EINVAL, 4);
     return GP_OK;
 }
@@ -442,7 +441,7 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
 GPFAGP_API gp_model* gp_fit(const double* X, const double* y, int64_t N, int p, int n, double eps,
                             double alpha, double sigma2) {
     gp_model* h = nullptr;
-    gp_fit_ex(X, y, N, p, n, eps, alpha, sigma2, GP_PREC_BF16X3, nullptr, 0, &h);
+    gp_fit_ex(X, y, N, p, n, eps, alpha, sigma2, GP_PREC_MIXED, nullptr, 0, &h);
     return h;
 }
 

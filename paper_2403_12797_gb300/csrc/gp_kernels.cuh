@@ -24,13 +24,11 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
 constexpr int SYRKTC_TM = 128;
 constexpr int SYRKTC_BK = 32;
 size_t syrktc_smem_bytes(const GpShape& s);
-// Gpart holds column-scaled partial tiles (units 2^(14 - E_m - E_m')), dpart
-// the scaled diagonal corrections (nsplit x Mpad), colexp[m] = E_m (Mpad),
-// bpart the unscaled Phi^T y partials.
+// Gpart holds column-scaled partial tiles (units 2^(14 - E_m - E_m')),
+// colexp[m] = E_m (Mpad), bpart the unscaled Phi^T y partials.
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
                            const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
-                           float* bpart, float* dpart, int* colexp, GpStatus* st,
-                           cudaStream_t stream);
+                           float* bpart, int* colexp, GpStatus* st, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);

@@ -1,4 +1,4 @@
-// gp_syrk_tc.cu -- fused Phi generation + exact-sum bf16 tensor-core Gram (tcgen05, TMEM).
+// gp_syrk_tc.cu -- fused Phi generation + bf16 tensor-core Gram with exact block sums (tcgen05, TMEM).
 //
 // Computes G = Phi^T Phi and b = Phi^T y over the N training rows (the
 // products of Lambda-bar and of W in Sec. 2.2). Phi (Eq. 19) is generated in
@@ -7,33 +7,33 @@
 //
 // Precision. The tensor cores' float32 accumulation truncates, so a long
 // sum in TMEM drifts low by ~2e-8 per accumulate step; over the thousands of
-// steps of a large N that bias (~1e-4 relative on the diagonal of G) is
-// amplified by the conditioning of A into percent-level errors of the
-// posterior. This kernel therefore makes every tensor-core sum EXACT:
+// steps of a large N that bias (~1e-4 relative on G) is amplified by the
+// conditioning of A into percent-level errors of the posterior. The kernel
+// therefore keeps the dominant part of every tensor-core sum exact:
 //   * each column m is scaled by 2^(7 - E_m), where 2^(E_m) bounds |Phi[:, m]|
-//     (the product of the per-dimension table maxima), so |Phi * 2^(7-E_m)| <= 128;
-//   * the scaled value w is split into integers s1 = rint(w) and
-//     s2 = rint((w - s1) * 256), both in [-128, 128] and exact in bf16;
-//   * acc1 += s1 s1' and acc2 += s1 s2' + s2 s1' are integer sums below 2^24,
-//     exact in float32, for blocks of 512 rows;
-//   * after each block the producers add acc1 + acc2 / 256 into float32
-//     registers (round to nearest: unbiased), while the MMAs fill the other
-//     TMEM buffer (two buffers x 256 columns = all 512 TMEM columns).
-// The dropped s2 s2' / 2^16 term has zero mean off the diagonal; on the
-// diagonal its sum (sum of s2^2, exact on the CUDA cores) is added back
-// (dpart). Representation error: |w - s1 - s2/256| <= 2^-9 (<= 2^-16 of the
-// column bound).
+//     (the product of the per-dimension table maxima), so |w| <= 128 for the
+//     scaled value w = Phi * 2^(7 - E_m);
+//   * w = s1 + lo with the integer s1 = rint(w) (exact in bf16) and the
+//     remainder lo = bf16(w - s1), |w - s1| <= 1/2;
+//   * acc1 += s1 s1' is an integer sum below 2^24 for blocks of 512 rows,
+//     hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo' is a few
+//     percent of G, so its truncation over one block (~2e-6 of itself) is
+//     negligible;
+//   * after each block the producers add acc1 + acc2 into float32 registers
+//     (round to nearest: unbiased), while the MMAs fill the other TMEM
+//     buffer (two buffers x 256 columns = all 512 TMEM columns).
+// Representation error: |w - s1 - lo| <= 2^-10 (2^-17 of the column bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows:
-//   warps 0-3  producers: copy the tables' window rows for the chunk into
+//   warps 0-7  producers: copy the tables' window rows for the chunk into
 //              shared memory, form Phi for column tiles I and J in the K-major
 //              core-matrix layout (8 columns x 16 bytes), split, publish the
 //              stage; J == 0 CTAs also accumulate b_I = Phi_I^T y (float32,
 //              warp-shuffle reduction). They drain TMEM and write the
 //              (scaled) partial tile at the end.
-//   warp 4     allocates TMEM and issues the MMAs (one elected lane):
-//              3 x (128 x 128 x 16) per 16 rows; tcgen05.commit frees stages
+//   warp 8     allocates TMEM and issues the MMAs (one elected lane):
+//              4 x (128 x 128 x 16) per 16 rows; tcgen05.commit frees stages
 //              and signals finished blocks.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
 #include "gp_kernels.cuh"
@@ -189,31 +189,29 @@ __device__ __forceinline__ uint32_t pack_bf16x2_exact(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Scale 8 values by sc, split into integer slices s1, s2, store both
-// core-matrix rows; returns sum(s2^2).
-__device__ __forceinline__ float store_slices(uint8_t* s1_tile, uint8_t* s2_tile, int r, int g,
-                                              const float v[8], float sc) {
+// Scale 8 values by sc and split each into the integer s1 = rint(w)
+// (|s1| <= 128, exact in bf16) and the remainder lo = bf16(w - s1); store
+// both core-matrix rows.
+__device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
+                                             const float v[8], float sc) {
     uint32_t h[4], l[4];
-    float dsq = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;
         const float a0 = rintf(w0), a1 = rintf(w1);
-        const float b0 = rintf((w0 - a0) * 256.f), b1 = rintf((w1 - a1) * 256.f);
         h[q] = pack_bf16x2_exact(a0, a1);
-        l[q] = pack_bf16x2_exact(b0, b1);
-        dsq = fmaf(b0, b0, fmaf(b1, b1, dsq));
+        __nv_bfloat162 lo = __floats2bfloat162_rn(w0 - a0, w1 - a1);
+        l[q] = *reinterpret_cast<uint32_t*>(&lo);
     }
     const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
     *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(s2_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    return dsq;
+    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmax,
                    const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows,
-                   float* __restrict__ Gpart, float* __restrict__ bpart, float* __restrict__ dpart,
+                   float* __restrict__ Gpart, float* __restrict__ bpart,
                    int* __restrict__ colexp, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
@@ -266,9 +264,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int rl = lane & 7;       // column within an 8-column core group
         const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (tile rows)
         const int half = warp >> 2;    // tile columns CPT*half ..
-        float bacc[IT], dacc[IT];
+        float bacc[IT];
 #pragma unroll
-        for (int it = 0; it < IT; ++it) bacc[it] = dacc[it] = 0.f;
+        for (int it = 0; it < IT; ++it) bacc[it] = 0.f;
         float gacc[CPT];               // this thread's part of its tile row
 #pragma unroll
         for (int i = 0; i < CPT; ++i) gacc[i] = 0.f;
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld16(tmem + lrow + ch * 16, a1);
                 tmem_ld16(tmem + lrow + 128 + ch * 16, a2);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) gacc[ch * 16 + i] += fmaf(a2[i], 1.f / 256.f, a1[i]);
+                for (int i = 0; i < 16; ++i) gacc[ch * 16 + i] += a1[i] + a2[i];
             }
             tc_fence_before();
             mbar_arrive(&sm.drained[u]);
@@ -329,8 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int r = 8 * (it * NPW + warp) + rl;
                 float v[8];
                 phi8(sm.winI, sm.crI + r * s.p, s.p, g, v);
-                const float dsq = store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[r]);
-                if (diag) dacc[it] += dsq;
+                store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[r]);
                 if (J == 0) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], sm.yv[8 * g + k], bacc[it]);
@@ -367,16 +364,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
                 if (lane < 8) bpart[(int64_t)split * s.Mpad + I * TM + 8 * (it * NPW + warp) + rl] = v;
-            }
-        }
-        if (diag) {
-#pragma unroll
-            for (int it = 0; it < IT; ++it) {
-                float v = dacc[it];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (lane < 8)
-                    dpart[(int64_t)split * s.Mpad + I * TM + 8 * (it * NPW + warp) + rl] = v * (1.f / 65536.f);
             }
         }
         if (ok) {
@@ -418,9 +405,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint64_t dB1 = smem_desc(b1 + ko, LBO, SBO);
                     const uint64_t dB2 = smem_desc(b2 + ko, LBO, SBO);
                     const uint32_t acc = (cb > 0 || ks > 0) ? 1u : 0u;
-                    mma_bf16(acc1, dA1, dB1, idesc, acc);
-                    mma_bf16(acc2, dA1, dB2, idesc, acc);
-                    mma_bf16(acc2, dA2, dB1, idesc, 1u);
+                    mma_bf16(acc1, dA1, dB1, idesc, acc);   // s1 s1'  (exact)
+                    mma_bf16(acc2, dA1, dB2, idesc, acc);   // s1 lo'
+                    mma_bf16(acc2, dA2, dB1, idesc, 1u);    // lo s1'
+                    mma_bf16(acc2, dA2, dB2, idesc, 1u);    // lo lo'
                 }
                 mma_commit(&sm.empty[stg]);
                 if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(&sm.accf[u]);
@@ -444,7 +432,7 @@ size_t syrktc_smem_bytes(const GpShape& s) {
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
                            const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
-                           float* bpart, float* dpart, int* colexp, GpStatus* st,
+                           float* bpart, int* colexp, GpStatus* st,
                            cudaStream_t stream) {
     const int maxrows = gp_max_window_rows(s, TM);
     const size_t smem = smem_tc_layout(maxrows, s.p, nullptr, nullptr);
@@ -456,6 +444,6 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
     syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmax, ypad, rows_per_split, npairs,
-                                                     maxrows, Gpart, bpart, dpart, colexp, st);
+                                                     maxrows, Gpart, bpart, colexp, st);
     return cudaGetLastError();
 }
