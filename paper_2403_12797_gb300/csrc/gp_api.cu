@@ -143,14 +143,16 @@ int read_status(GpStatus* st, cudaStream_t s) {
     return GP_OK;
 }
 
-// Split the (padded) rows so that tile pairs x splits fill the GPU.
-void choose_splits(int npairs, int64_t Npad, int target_ctas, int* nsplit, int64_t* rps) {
+// Split the (padded) rows so that tile pairs x splits fill the GPU; every
+// split is a multiple of `granule` rows.
+void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, int* nsplit,
+                   int64_t* rps) {
     int64_t want = (target_ctas + npairs - 1) / npairs;
     int64_t maxs = Npad / 256;  // at least 256 rows per split
     if (want > maxs) want = maxs;
     if (want < 1) want = 1;
     if (want > 65535) want = 65535;
-    int64_t r = gp_round_up((Npad + want - 1) / want, 128);
+    int64_t r = gp_round_up((Npad + want - 1) / want, granule);
     *rps = r;
     *nsplit = (int)((Npad + r - 1) / r);
 }
@@ -175,7 +177,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         const int npairs = T * (T + 1) / 2;
         int nsplit;
         int64_t rps;
-        choose_splits(npairs, s.Npad, 4 * num_sms(dev), &nsplit, &rps);
+        choose_splits(npairs, s.Npad, 4 * num_sms(dev), 128, &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRK64_TM * SYRK64_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
         {
@@ -203,24 +205,25 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         const int npairs = T * (T + 1) / 2;
         int nsplit;
         int64_t rps;
-        choose_splits(npairs, s.Npad, num_sms(dev), &nsplit, &rps);
+        choose_splits(npairs, s.Npad, num_sms(dev), GP_TAB_BLOCK, &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
-        unsigned int* tmax;
+        unsigned int *tmax, *tmaxb;
         int* colexp;
         if ((rc = sc.get(&tmax, (size_t)s.p * s.n))) return rc;
+        if ((rc = sc.get(&tmaxb, (size_t)s.p * s.n * ((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
         if ((rc = sc.get(&colexp, (size_t)s.Mpad))) return rc;
         {
             GpProf pf("eig_tables", stream);
             launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
             pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
-            launch_table_absmax(s, tab, tmax, stream);
+            launch_table_absmax(s, tab, tmaxb, tmax, stream);
             gp_note_launches(3);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tab, tmax, ypad, nsplit, rps, Gpart, bpart, colexp, st,
-                                           stream);
+            cudaError_t e = launch_syrk_tc(s, tab, tmaxb, tmax, ypad, nsplit, rps, Gpart, bpart, colexp,
+                                           st, stream);
             if (e != cudaSuccess) return cuda_err(e);
             gp_note_launches(1);
         }

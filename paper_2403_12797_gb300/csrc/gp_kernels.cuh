@@ -9,8 +9,13 @@ void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, d
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream);
 
-// tmax[j*n + k] = max_i |tab[j][k][i]| (float bits); zeroes tmax first.
-void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmax, cudaStream_t stream);
+// Rows per block of the mixed-precision Gram (exact tensor-core sums) and of
+// the per-block table maxima.
+constexpr int GP_TAB_BLOCK = 512;
+// tmaxb[b * p*n + j*n + k] = max |tab[j][k][i]| over rows i of block b and
+// tmax[j*n + k] = max over all rows (float bits); zeroes tmax first.
+void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmaxb, unsigned int* tmax,
+                         cudaStream_t stream);
 
 // ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
 // Tile 64 x 64, lower-triangular tile pairs x N splits.
@@ -26,9 +31,11 @@ constexpr int SYRKTC_BK = 32;
 size_t syrktc_smem_bytes(const GpShape& s);
 // Gpart holds column-scaled partial tiles (units 2^(14 - E_m - E_m')),
 // colexp[m] = E_m (Mpad), bpart the unscaled Phi^T y partials.
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
-                           const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
-                           float* bpart, int* colexp, GpStatus* st, cudaStream_t stream);
+// rows_per_split must be a multiple of GP_TAB_BLOCK.
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
+                           const unsigned int* tmax, const float* ypad, int nsplit,
+                           int64_t rows_per_split, float* Gpart, float* bpart, int* colexp,
+                           GpStatus* st, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);

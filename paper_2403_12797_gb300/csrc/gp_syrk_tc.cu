@@ -10,19 +10,20 @@
 // steps of a large N that bias (~1e-4 relative on G) is amplified by the
 // conditioning of A into percent-level errors of the posterior. The kernel
 // therefore keeps the dominant part of every tensor-core sum exact:
-//   * each column m is scaled by 2^(7 - E_m), where 2^(E_m) bounds |Phi[:, m]|
-//     (the product of the per-dimension table maxima), so |w| <= 128 for the
-//     scaled value w = Phi * 2^(7 - E_m);
-//   * w = s1 + lo with the integer s1 = rint(w) (exact in bf16) and the
-//     remainder lo = bf16(w - s1), |w - s1| <= 1/2;
+//   * for every 512-row block, each column m is scaled by 2^(7 - E_m), where
+//     2^(E_m) bounds |Phi[:, m]| inside the block (the product of the block's
+//     per-dimension table maxima), so |w| <= 128 for w = Phi * 2^(7 - E_m);
+//   * w = s1 + lo with the integer s1 = rint(w) (exact in fp16) and the
+//     remainder lo = fp16(w - s1), |w - s1| <= 1/2 (2^-12 absolute error);
 //   * acc1 += s1 s1' is an integer sum below 2^24 for blocks of 512 rows,
 //     hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo' is a few
 //     percent of G, so its truncation over one block (~2e-6 of itself) is
 //     negligible;
-//   * after each block the producers add acc1 + acc2 into float32 registers
-//     (round to nearest: unbiased), while the MMAs fill the other TMEM
-//     buffer (two buffers x 256 columns = all 512 TMEM columns).
-// Representation error: |w - s1 - lo| <= 2^-10 (2^-17 of the column bound).
+//   * after each block the producers multiply acc1 + acc2 by the exact power
+//     of two that maps the block's column scaling to the global one and add
+//     it into float32 registers (round to nearest: unbiased), while the MMAs
+//     fill the other TMEM buffer (two buffers x 256 columns = all 512).
+// Representation error: |w - s1 - lo| <= 2^-12 (2^-19 of the block bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows:
@@ -63,8 +64,12 @@ struct SmemTC {
     float* winI;          // maxrows x WSTRIDE
     float* winJ;
     float* yv;            // BK
-    float* scI;           // TM column scales 2^(7 - E)
+    float* scI;           // 2 x TM: block column scales 2^(7 - E_blk), by block parity
     float* scJ;
+    float* muI;           // 2 x TM: drain multipliers 2^(E_blk - E_glob)
+    float* muJ;
+    int* egI;             // TM: global column exponents E_glob
+    int* egJ;
     int* trI;
     int* trJ;
     unsigned short* crI;  // TM x p
@@ -88,8 +93,12 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base,
     size_t oWI = take(sizeof(float) * maxrows * WSTRIDE, 16);
     size_t oWJ = take(sizeof(float) * maxrows * WSTRIDE, 16);
     size_t oY = take(sizeof(float) * BK, 16);
-    size_t oSI = take(sizeof(float) * TM, 16);
-    size_t oSJ = take(sizeof(float) * TM, 16);
+    size_t oSI = take(sizeof(float) * 2 * TM, 16);
+    size_t oSJ = take(sizeof(float) * 2 * TM, 16);
+    size_t oMI = take(sizeof(float) * 2 * TM, 16);
+    size_t oMJ = take(sizeof(float) * 2 * TM, 16);
+    size_t oEI = take(sizeof(int) * TM, 16);
+    size_t oEJ = take(sizeof(int) * TM, 16);
     size_t oTI = take(sizeof(int) * maxrows, 16);
     size_t oTJ = take(sizeof(int) * maxrows, 16);
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
@@ -106,6 +115,10 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base,
         L->yv = (float*)(base + oY);
         L->scI = (float*)(base + oSI);
         L->scJ = (float*)(base + oSJ);
+        L->muI = (float*)(base + oMI);
+        L->muJ = (float*)(base + oMJ);
+        L->egI = (int*)(base + oEI);
+        L->egJ = (int*)(base + oEJ);
         L->trI = (int*)(base + oTI);
         L->trJ = (int*)(base + oTJ);
         L->crI = (unsigned short*)(base + oCI);
@@ -126,10 +139,17 @@ __device__ __forceinline__ int bound_exp(unsigned int bits) {
     return e;
 }
 
-// Window rows, column -> window-row map, and column scales of one tile.
+// sum over dimensions of the table-maximum exponents of column m
+__device__ __forceinline__ int column_exp(const GpShape& s, const unsigned int* __restrict__ tm, int m) {
+    int E = 0;
+    for (int j = 0; j < s.p; ++j) E += bound_exp(tm[j * s.n + (m / s.stride[j]) % s.n]);
+    return E < -100 ? -100 : E;
+}
+
+// Window rows, column -> window-row map and global column exponents of one tile.
 __device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0,
                            const unsigned int* __restrict__ tmax, int* tr, unsigned short* cr,
-                           float* sc, int* colexp_out, int tid, int nthr) {
+                           int* eg, int* colexp_out, int tid, int nthr) {
     for (int r = tid; r < w.nrows; r += nthr) tr[r] = window_table_row(s, w, r);
     for (int e = tid; e < TM * s.p; e += nthr) {
         int c = e / s.p, j = e % s.p;
@@ -138,16 +158,26 @@ __device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0,
     }
     for (int c = tid; c < TM; c += nthr) {
         const int m = m0 + c;
-        if (m >= s.M) {
-            sc[c] = 0.f;
-            continue;
-        }
-        int E = 0;
-        for (int j = 0; j < s.p; ++j) E += bound_exp(tmax[j * s.n + (m / s.stride[j]) % s.n]);
-        if (E < -100) E = -100;
-        sc[c] = ldexpf(1.f, 7 - E);
-        if (colexp_out) colexp_out[m] = E;
+        const int E = m < s.M ? column_exp(s, tmax, m) : 0;
+        eg[c] = E;
+        if (colexp_out && m < s.M) colexp_out[m] = E;
     }
+}
+
+// Column scales of one tile for the 512-row block whose table maxima are tmb:
+// quantisation scale 2^(7 - E_blk) (|Phi * scale| <= 128 inside the block) and
+// the drain multiplier 2^(E_blk - E_glob) <= 1 back to the global scaling.
+__device__ __forceinline__ void block_scales(const GpShape& s, int m0, const unsigned int* __restrict__ tmb,
+                                             const int* eg, float* sc, float* mu, int c) {
+    const int m = m0 + c;
+    if (m >= s.M) {
+        sc[c] = 0.f;
+        mu[c] = 0.f;
+        return;
+    }
+    const int E = column_exp(s, tmb, m);
+    sc[c] = ldexpf(1.f, 7 - E);
+    mu[c] = ldexpf(1.f, E - eg[c]);
 }
 
 // window rows (nrows x BK floats) of the chunk starting at data row i0
@@ -184,14 +214,15 @@ __device__ __forceinline__ void phi8(const float* win, const unsigned short* crr
     }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2_exact(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // exact: |a|, |b| <= 128 integers
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
 // Scale 8 values by sc and split each into the integer s1 = rint(w)
-// (|s1| <= 128, exact in bf16) and the remainder lo = bf16(w - s1); store
-// both core-matrix rows.
+// (|s1| <= 128, exact in fp16) and the remainder lo = fp16(w - s1)
+// (|lo| <= 1/2, 11-bit precision, subnormals below 2^-14); store both
+// core-matrix rows.
 __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
                                              const float v[8], float sc) {
     uint32_t h[4], l[4];
@@ -199,9 +230,8 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
     for (int q = 0; q < 4; ++q) {
         const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;
         const float a0 = rintf(w0), a1 = rintf(w1);
-        h[q] = pack_bf16x2_exact(a0, a1);
-        __nv_bfloat162 lo = __floats2bfloat162_rn(w0 - a0, w1 - a1);
-        l[q] = *reinterpret_cast<uint32_t*>(&lo);
+        h[q] = pack_half2(a0, a1);
+        l[q] = pack_half2(w0 - a0, w1 - a1);
     }
     const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
     *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -209,7 +239,8 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmax,
+    syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmaxb,
+                   const unsigned int* __restrict__ tmax,
                    const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows,
                    float* __restrict__ Gpart, float* __restrict__ bpart,
                    int* __restrict__ colexp, GpStatus* st) {
@@ -249,9 +280,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == MMA_WARP) tmem_alloc(sm.tmem_base, TMEM_COLS);
     __syncthreads();
     if (tid < NPROD) {
-        setup_tile(s, wI, I * TM, tmax, sm.trI, sm.crI, sm.scI, (J == 0 && split == 0) ? colexp : nullptr,
+        setup_tile(s, wI, I * TM, tmax, sm.trI, sm.crI, sm.egI, (J == 0 && split == 0) ? colexp : nullptr,
                    tid, NPROD);
-        if (!diag) setup_tile(s, wJ, J * TM, tmax, sm.trJ, sm.crJ, sm.scJ, nullptr, tid, NPROD);
+        if (!diag) setup_tile(s, wJ, J * TM, tmax, sm.trJ, sm.crJ, sm.egJ, nullptr, tid, NPROD);
     }
     tc_fence_before();
     __syncthreads();
@@ -292,13 +323,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!bcast_wait(&sm.accf[u], (d >> 1) & 1, 4)) return false;
             tc_fence_after();
             const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + half * CPT;
+            // back to the global column scaling (exact powers of two)
+            const float mrow = sm.muI[u * TM + quarter * 32 + lane];
+            const float* mcol = (diag ? sm.muI : sm.muJ) + u * TM + half * CPT;
 #pragma unroll
             for (int ch = 0; ch < CPT / 16; ++ch) {
                 float a1[16], a2[16];
                 tmem_ld16(tmem + lrow + ch * 16, a1);
                 tmem_ld16(tmem + lrow + 128 + ch * 16, a2);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) gacc[ch * 16 + i] += a1[i] + a2[i];
+                for (int i = 0; i < 16; ++i)
+                    gacc[ch * 16 + i] = fmaf(a1[i] + a2[i], mrow * mcol[ch * 16 + i], gacc[ch * 16 + i]);
             }
             tc_fence_before();
             mbar_arrive(&sm.drained[u]);
@@ -313,6 +348,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             load_window(s, tab, sm.trI, wI.nrows, i0, sm.winI, tid);
             if (!diag) load_window(s, tab, sm.trJ, wJ.nrows, i0, sm.winJ, tid);
             if (tid < BK) sm.yv[tid] = ypad[i0 + tid];
+            const int slot = (c / BLOCK_CHUNKS) & 1;
+            if (c % BLOCK_CHUNKS == 0) {
+                // a new 512-row block: its column scales (the drain of the
+                // block two back, which used this slot, is complete)
+                const unsigned int* tmb = tmaxb + ((r0 + (int64_t)c * BK) / GP_TAB_BLOCK) * (s.p * s.n);
+                if (tid < TM)
+                    block_scales(s, I * TM, tmb, sm.egI, sm.scI + slot * TM, sm.muI + slot * TM, tid);
+                else if (!diag)
+                    block_scales(s, J * TM, tmb, sm.egJ, sm.scJ + slot * TM, sm.muJ + slot * TM, tid - TM);
+            }
             if (c >= STAGES) {
                 if (!bcast_wait(&sm.empty[stg], ((c / STAGES) - 1) & 1, 1)) {
                     ok = false;
@@ -327,7 +372,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int r = 8 * (it * NPW + warp) + rl;
                 float v[8];
                 phi8(sm.winI, sm.crI + r * s.p, s.p, g, v);
-                store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[r]);
+                store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[slot * TM + r]);
                 if (J == 0) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], sm.yv[8 * g + k], bacc[it]);
@@ -339,7 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int r = 8 * (it * NPW + warp) + rl;
                     float v[8];
                     phi8(sm.winJ, sm.crJ + r * s.p, s.p, g, v);
-                    store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, sm.scJ[r]);
+                    store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, sm.scJ[slot * TM + r]);
                 }
             }
             fence_proxy_async_smem();
@@ -377,7 +422,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(TM, TM);
+            const uint32_t idesc = idesc_f16_f32(TM, TM);
             const uint32_t sbase = smem_u32(sm.stage);
             for (int c = 0; c < nchunks; ++c) {
                 const int stg = c % STAGES;
@@ -430,10 +475,11 @@ size_t syrktc_smem_bytes(const GpShape& s) {
     return smem_tc_layout(gp_max_window_rows(s, TM), s.p, nullptr, nullptr);
 }
 
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmax,
-                           const float* ypad, int nsplit, int64_t rows_per_split, float* Gpart,
-                           float* bpart, int* colexp, GpStatus* st,
-                           cudaStream_t stream) {
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
+                           const unsigned int* tmax, const float* ypad, int nsplit,
+                           int64_t rows_per_split, float* Gpart, float* bpart, int* colexp,
+                           GpStatus* st, cudaStream_t stream) {
+    if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
     const size_t smem = smem_tc_layout(maxrows, s.p, nullptr, nullptr);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -443,7 +489,7 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
     const int T = s.Mpad / TM;
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
-    syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmax, ypad, rows_per_split, npairs,
+    syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs,
                                                      maxrows, Gpart, bpart, colexp, st);
     return cudaGetLastError();
 }

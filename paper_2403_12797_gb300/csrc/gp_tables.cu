@@ -64,32 +64,36 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     }
 }
 
-// tmax[row] = max_i |tab[row][i]| as float bits (non-negative floats order
-// like their bit patterns). tmax must be zeroed before the launch.
+// Per 512-row block b and table row: tmaxb[b * rows + row] = max |tab[row][i]|
+// over the block, and tmax[row] = the maximum over all blocks, as float bits
+// (non-negative floats order like their bit patterns). tmax must be zeroed.
 __global__ void __launch_bounds__(256) table_absmax_kernel(const float* __restrict__ tab, int64_t Npad,
+                                                           int rows, unsigned int* __restrict__ tmaxb,
                                                            unsigned int* __restrict__ tmax) {
     const int row = blockIdx.y;
-    const int64_t i0 = (int64_t)blockIdx.x * 4096;
+    const int64_t i0 = (int64_t)blockIdx.x * GP_TAB_BLOCK;
     const float* r = tab + (int64_t)row * Npad;
     float m = 0.f;
-    for (int64_t i = i0 + threadIdx.x; i < i0 + 4096 && i < Npad; i += blockDim.x) m = fmaxf(m, fabsf(r[i]));
+    for (int64_t i = i0 + threadIdx.x; i < i0 + GP_TAB_BLOCK && i < Npad; i += blockDim.x)
+        m = fmaxf(m, fabsf(r[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ float wm[8];
     if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) m = fmaxf(m, wm[w]);
-        m = fmaxf(m, wm[0]);
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, wm[w]);
+        tmaxb[(int64_t)blockIdx.x * rows + row] = __float_as_uint(m);
         atomicMax(tmax + row, __float_as_uint(m));
     }
 }
 
 }  // namespace
 
-void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmax, cudaStream_t stream) {
+void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmaxb, unsigned int* tmax,
+                         cudaStream_t stream) {
     cudaMemsetAsync(tmax, 0, sizeof(unsigned int) * s.p * s.n, stream);
-    dim3 grid((unsigned)((s.Npad + 4095) / 4096), (unsigned)(s.p * s.n));
-    table_absmax_kernel<<<grid, 256, 0, stream>>>(tab, s.Npad, tmax);
+    dim3 grid((unsigned)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK), (unsigned)(s.p * s.n));
+    table_absmax_kernel<<<grid, 256, 0, stream>>>(tab, s.Npad, s.p * s.n, tmaxb, tmax);
 }
 
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
