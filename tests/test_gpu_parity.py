@@ -74,7 +74,15 @@ def test_fit_predict_matches_oracle(prec, case):
     pr = _small_cases()[case]
     m, mean, var = _fit_predict(pr, prec)
     mdl, (mo, vo) = _oracle(pr)
-    assert O.relerr(mean, mo) < TOL[prec]["mean"], (O.relerr(mean, mo), pr.name)
+    tol_mean = TOL[prec]["mean"]
+    if prec == "mixed" and pr.N == 1:
+        # One training point: G = phi phi^T has no rows to average over, so
+        # each entry keeps the full <= 2^-16 relative error of one product
+        # of two mixed-precision Phi values, and for this problem the mean
+        # amplifies relative errors of G by ~30 (checked on the oracle):
+        # 30 * 2^-16 = 4.6e-4.
+        tol_mean = 1e-3
+    assert O.relerr(mean, mo) < tol_mean, (O.relerr(mean, mo), pr.name)
     assert O.relerr(var, vo) < TOL[prec]["var"], (O.relerr(var, vo), pr.name)
     if prec == "fp64":
         assert O.relerr(m.read("L"), mdl["L"]) < 1e-10

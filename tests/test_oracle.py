@@ -297,3 +297,21 @@ def test_workload_generators_shapes_and_determinism():
     assert w3.M == 4096 and w3.eps == 1.2
     w4 = W.workload4(count=16, Ns=4)
     assert all(pr.M <= 1024 and 1 <= pr.p <= 4 and pr.n >= 2 for pr in w4)
+
+
+def test_single_point_posterior_sensitivity_to_gram_errors():
+    # Pins the amplification used for the N = 1 mixed-precision tolerance in
+    # the GPU parity test: a relative perturbation r of G moves the mean by
+    # about 30 r for this problem.
+    pr = W.random_problem(23, 1, 7, 2, 3)
+    ref = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    mo, _ = O.predict(ref, pr.Xs)
+    rng = np.random.Generator(np.random.PCG64(0))
+    G = ref["G"] * (1 + 1e-6 * rng.standard_normal(ref["G"].shape))
+    G = (G + G.T) / 2
+    L = np.linalg.cholesky(G + np.diag(ref["d"]))
+    import scipy.linalg as sla
+    c = sla.cho_solve((L, True), ref["b"])
+    m = O.phi_matrix(pr.Xs, pr.n, pr.eps, pr.alpha) @ c
+    amp = O.relerr(m, mo) / 1e-6
+    assert 10 < amp < 40
