@@ -143,6 +143,31 @@ GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, in
                           double eps, double alpha, int prec, double* G, double* b,
                           void* cuda_stream, int dev_ptrs);
 
+/* ---- allocation-free Gram ------------------------------------------------- */
+
+/* Size of the library's fixed device scratch array used by gp_gram_static. */
+#define GP_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* gp_gram_ex in GP_PREC_FP64 mode for callers that cannot allocate device
+ * memory during the call (a fixed, pre-carved memory budget, a real-time
+ * loop that must not enter the allocator, an allocator hook that must not
+ * be re-entered). The paper has no counterpart: this is a deployment
+ * variant of the Gram step. It calls no cudaMalloc/cudaFree (nor any
+ * allocating library routine): its scratch (tables, partial tiles, status)
+ * lives in one static device array of GP_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.
+ *   X (N x p), y (N): device inputs; G (M x M) and b (M): device outputs,
+ *   same layout and meaning as gp_gram_ex. Returns after the results are
+ *   written (the status word is read back).
+ * Errors: GP_EINVAL for bad arguments and for problems whose scratch would
+ * exceed GP_STATIC_SCRATCH_BYTES (gp_last_error_detail() = the bytes needed).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any
+ * stream capture. Every call shares the one array, so calls that overlap on
+ * the GPU race; serialise them. */
+GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p, int n,
+                              double eps, double alpha, double* G, double* b, void* cuda_stream);
+
 /* ---- batched fit -------------------------------------------------------- */
 
 /* One independent problem of a batched fit. Pointer kind as in the call. */

@@ -72,6 +72,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "gp_model_read": (i, [vp, i, vp]),
         "gp_gram_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, vp, i]),
+        "gp_gram_static": (i, [vp, vp, i64, i, i, d, d, vp, vp, vp]),
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
         "gp_debug_fail_alloc_after": (None, [i]),

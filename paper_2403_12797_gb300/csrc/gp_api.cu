@@ -350,6 +350,19 @@ GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, in
     return read_status(st, stream);
 }
 
+GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                              double alpha, double* G, double* b, void* cuda_stream) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!X || !y || !G || !b) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, 1.0))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    int64_t detail = 0;
+    rc = gp_static_gram(X, y, N, p, n, eps, alpha, G, b, (cudaStream_t)cuda_stream, &detail);
+    if (rc != GP_OK) return set_err(rc, detail);
+    return GP_OK;
+}
+
 GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
                          double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
                          gp_model** out) {

@@ -52,6 +52,11 @@ void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dp
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
                        cudaStream_t stream);
 
+// ---- allocation-free float64 Gram (gp_static.cu) --------------------------------
+// Device pointers only; returns a GP_* status, *detail as in gp_last_error_detail.
+int gp_static_gram(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                   double alpha, double* G, double* b, cudaStream_t stream, int64_t* detail);
+
 // ---- float64 factorisation and solves (gp_chol.cu) ----------------------------
 constexpr int CHOL_NB = 64;
 // In-place lower Cholesky of the M x M row-major matrix L (upper part ignored,
