@@ -44,7 +44,8 @@ namespace {
 
 constexpr int TM = SYRKTC_TM;              // 128
 constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
+constexpr int WBUF = 3;                    // table-window ring (chunks prefetched ahead)
 constexpr int BLOCK_CHUNKS = 16;           // 512 rows per exact TMEM block
 constexpr int WSTRIDE = BK + 4;            // floats per window row (bank-conflict padding)
 constexpr int TILE_BYTES = TM * BK * 2;    // one bf16 operand tile: 8 KB
@@ -61,9 +62,9 @@ constexpr uint32_t TMEM_COLS = 512;        // 2 buffers x (acc1 | acc2)
 
 struct SmemTC {
     uint8_t* stage;       // STAGES x STAGE_BYTES (1024-aligned)
-    float* winI;          // maxrows x WSTRIDE
+    float* winI;          // WBUF x maxrows x WSTRIDE
     float* winJ;
-    float* yv;            // BK
+    float* yv;            // WBUF x BK
     float* scI;           // 2 x TM: block column scales 2^(7 - E_blk), by block parity
     float* scJ;
     float* muI;           // 2 x TM: drain multipliers 2^(E_blk - E_glob)
@@ -81,7 +82,7 @@ struct SmemTC {
     uint32_t* tmem_base;
 };
 
-__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base, SmemTC* L) {
+__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, char* base, SmemTC* L) {
     size_t off = 0;
     auto take = [&](size_t bytes, size_t align) {
         off = (off + align - 1) / align * align;
@@ -89,10 +90,10 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, char* base,
         off += bytes;
         return o;
     };
-    size_t oS = take((size_t)STAGES * STAGE_BYTES, 1024);
-    size_t oWI = take(sizeof(float) * maxrows * WSTRIDE, 16);
-    size_t oWJ = take(sizeof(float) * maxrows * WSTRIDE, 16);
-    size_t oY = take(sizeof(float) * BK, 16);
+    size_t oS = take((size_t)nst * STAGE_BYTES, 1024);
+    size_t oWI = take(sizeof(float) * WBUF * maxrows * WSTRIDE, 16);
+    size_t oWJ = take(sizeof(float) * WBUF * maxrows * WSTRIDE, 16);
+    size_t oY = take(sizeof(float) * WBUF * BK, 16);
     size_t oSI = take(sizeof(float) * 2 * TM, 16);
     size_t oSJ = take(sizeof(float) * 2 * TM, 16);
     size_t oMI = take(sizeof(float) * 2 * TM, 16);
@@ -180,15 +181,15 @@ __device__ __forceinline__ void block_scales(const GpShape& s, int m0, const uns
     mu[c] = ldexpf(1.f, E - eg[c]);
 }
 
-// window rows (nrows x BK floats) of the chunk starting at data row i0
-__device__ __forceinline__ void load_window(const GpShape& s, const float* __restrict__ tab,
-                                            const int* tr, int nrows, int64_t i0, float* win,
-                                            int tid) {
+// Start the asynchronous copy of the window rows (nrows x BK floats) of the
+// chunk starting at data row i0 into win (16-byte cp.async per thread).
+__device__ __forceinline__ void load_window_async(const GpShape& s, const float* __restrict__ tab,
+                                                  const int* tr, int nrows, int64_t i0, float* win,
+                                                  int tid) {
     const int nv = nrows * (BK / 4);
     for (int e = tid; e < nv; e += NPROD) {
         const int r = e / (BK / 4), v = e % (BK / 4);
-        const float4 x = __ldg(reinterpret_cast<const float4*>(tab + (int64_t)tr[r] * s.Npad + i0) + v);
-        *reinterpret_cast<float4*>(win + r * WSTRIDE + 4 * v) = x;
+        cp_async16(win + r * WSTRIDE + 4 * v, tab + (int64_t)tr[r] * s.Npad + i0 + 4 * v);
     }
 }
 
@@ -241,7 +242,7 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmaxb,
                    const unsigned int* __restrict__ tmax,
-                   const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows,
+                   const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows, int nst,
                    float* __restrict__ Gpart, float* __restrict__ bpart,
                    int* __restrict__ colexp, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ int s_ok[2];
     char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     SmemTC sm;
-    smem_tc_layout(maxrows, s.p, base, &sm);
+    smem_tc_layout(maxrows, s.p, nst, base, &sm);
 
     const int q = blockIdx.x, split = blockIdx.y;
     int I, J;
@@ -340,14 +341,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             return true;
         };
 
+        // table windows are prefetched WBUF-1 chunks ahead into a ring
+        const int wsz = maxrows * WSTRIDE;
+        auto prefetch = [&](int cc) {
+            if (cc < nchunks) {
+                const int buf = cc % WBUF;
+                const int64_t i0 = r0 + (int64_t)cc * BK;
+                load_window_async(s, tab, sm.trI, wI.nrows, i0, sm.winI + buf * wsz, tid);
+                if (!diag) load_window_async(s, tab, sm.trJ, wJ.nrows, i0, sm.winJ + buf * wsz, tid);
+                if (tid < BK / 4) cp_async16(sm.yv + buf * BK + 4 * tid, ypad + i0 + 4 * tid);
+            }
+            cp_async_commit();  // one group per chunk, possibly empty
+        };
+        prefetch(0);
+        prefetch(1);
+
         int next_drain = 0;
         for (int c = 0; c < nchunks && ok; ++c) {
-            const int stg = c % STAGES;
-            const int64_t i0 = r0 + (int64_t)c * BK;
-            named_bar_sync(1, NPROD);  // previous chunk's windows are consumed
-            load_window(s, tab, sm.trI, wI.nrows, i0, sm.winI, tid);
-            if (!diag) load_window(s, tab, sm.trJ, wJ.nrows, i0, sm.winJ, tid);
-            if (tid < BK) sm.yv[tid] = ypad[i0 + tid];
+            const int stg = c % nst;
+            const int buf = c % WBUF;
+            named_bar_sync(1, NPROD);  // chunk c-1's windows are consumed: its buffer is free
+            prefetch(c + 2);
+            cp_async_wait<2>();        // this thread's copies for chunk c have landed
+            const float* winI = sm.winI + buf * wsz;
+            const float* winJ = sm.winJ + buf * wsz;
+            const float* yv = sm.yv + buf * BK;
             const int slot = (c / BLOCK_CHUNKS) & 1;
             if (c % BLOCK_CHUNKS == 0) {
                 // a new 512-row block: its column scales (the drain of the
@@ -358,8 +376,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 else if (!diag)
                     block_scales(s, J * TM, tmb, sm.egJ, sm.scJ + slot * TM, sm.muJ + slot * TM, tid - TM);
             }
-            if (c >= STAGES) {
-                if (!bcast_wait(&sm.empty[stg], ((c / STAGES) - 1) & 1, 1)) {
+            if (c >= nst) {
+                if (!bcast_wait(&sm.empty[stg], ((c / nst) - 1) & 1, 1)) {
                     ok = false;
                     break;
                 }
@@ -371,11 +389,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int it = 0; it < IT; ++it) {
                 const int r = 8 * (it * NPW + warp) + rl;
                 float v[8];
-                phi8(sm.winI, sm.crI + r * s.p, s.p, g, v);
+                phi8(winI, sm.crI + r * s.p, s.p, g, v);
                 store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[slot * TM + r]);
                 if (J == 0) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], sm.yv[8 * g + k], bacc[it]);
+                    for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], yv[8 * g + k], bacc[it]);
                 }
             }
             if (!diag) {
@@ -383,14 +401,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int it = 0; it < IT; ++it) {
                     const int r = 8 * (it * NPW + warp) + rl;
                     float v[8];
-                    phi8(sm.winJ, sm.crJ + r * s.p, s.p, g, v);
+                    phi8(winJ, sm.crJ + r * s.p, s.p, g, v);
                     store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, sm.scJ[slot * TM + r]);
                 }
             }
             fence_proxy_async_smem();
             mbar_arrive(&sm.full[stg]);
-            // drain a finished block once STAGES chunks of the next one are queued
-            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) - 1 + STAGES <= c) {
+            // drain a finished block once nst chunks of the next one are queued
+            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) - 1 + nst <= c) {
                 if (!drain(next_drain)) {
                     ok = false;
                     break;
@@ -402,6 +420,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!drain(next_drain)) ok = false;
             ++next_drain;
         }
+        cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (J == 0) {
 #pragma unroll
             for (int it = 0; it < IT; ++it) {
@@ -425,13 +444,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t idesc = idesc_f16_f32(TM, TM);
             const uint32_t sbase = smem_u32(sm.stage);
             for (int c = 0; c < nchunks; ++c) {
-                const int stg = c % STAGES;
+                const int stg = c % nst;
                 const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS, u = d & 1;
                 if (cb == 0 && d >= 2 && !mbar_wait(&sm.drained[u], ((d >> 1) - 1) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 5);
                     break;
                 }
-                if (!mbar_wait(&sm.full[stg], (c / STAGES) & 1)) {
+                if (!mbar_wait(&sm.full[stg], (c / nst) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 3);
                     break;
                 }
@@ -469,10 +488,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// deepest pipeline (<= STAGES) whose shared memory fits one CTA; 0 if none
+int syrk_tc_stages(const GpShape& s, int maxrows, size_t* smem) {
+    for (int nst = STAGES; nst >= 2; --nst) {
+        *smem = smem_tc_layout(maxrows, s.p, nst, nullptr, nullptr);
+        if (*smem <= 227 * 1024) return nst;
+    }
+    return 0;
+}
+
 }  // namespace
 
 size_t syrktc_smem_bytes(const GpShape& s) {
-    return smem_tc_layout(gp_max_window_rows(s, TM), s.p, nullptr, nullptr);
+    size_t smem = 0;
+    syrk_tc_stages(s, gp_max_window_rows(s, TM), &smem);
+    return smem;
 }
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
@@ -481,8 +511,9 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
                            GpStatus* st, cudaStream_t stream) {
     if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
-    const size_t smem = smem_tc_layout(maxrows, s.p, nullptr, nullptr);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    size_t smem = 0;
+    const int nst = syrk_tc_stages(s, maxrows, &smem);
+    if (nst == 0) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -490,6 +521,6 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
     syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs,
-                                                     maxrows, Gpart, bpart, colexp, st);
+                                                     maxrows, nst, Gpart, bpart, colexp, st);
     return cudaGetLastError();
 }
