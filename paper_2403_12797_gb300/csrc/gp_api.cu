@@ -147,8 +147,8 @@ int read_status(GpStatus* st, cudaStream_t s) {
 // split is a multiple of `granule` rows.
 void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, int* nsplit,
                    int64_t* rps) {
-    int64_t want = (target_ctas + npairs - 1) / npairs;
-    int64_t maxs = Npad / 256;  // at least 256 rows per split
+    int64_t want = target_ctas / npairs;  // never more CTAs than one wave
+    int64_t maxs = Npad / 256;            // at least 256 rows per split
     if (want > maxs) want = maxs;
     if (want < 1) want = 1;
     if (want > 65535) want = 65535;
@@ -409,6 +409,9 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if ((rc = sc.get(&A, (size_t)M * M))) return fail(rc);
     if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
     if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return fail(rc);
+    const bool fp32_inverse = (prec != GP_PREC_FP64);
+    unsigned char* fwork;
+    if ((rc = sc.get(&fwork, factor_work_bytes(M, fp32_inverse)))) return fail(rc);
     cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
 
     const double *Xd = X, *yd = y;
@@ -432,15 +435,15 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     cudaError_t e;
     {
         GpProf pf("cholesky", stream);
-        e = launch_cholesky(h->L, M, st, stream);
+        e = launch_cholesky(h->L, M, st, fwork, stream);
     }
     if (e == cudaSuccess) {
         GpProf pf("tri_inverse", stream);
-        e = launch_tri_inverse(h->L, h->W, M, st, stream);
+        e = launch_tri_inverse(h->L, h->W, M, fp32_inverse, st, fwork, stream);
     }
     if (e == cudaSuccess) {
         GpProf pf("solve_refine", stream);
-        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, 2, st, stream);
+        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st, stream);
     }
     if (e == cudaSuccess && prec != GP_PREC_FP64) {
         GpProf pf("pack_w", stream);

@@ -57,13 +57,16 @@ void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, do
 int gp_static_gram(const double* X, const double* y, int64_t N, int p, int n, double eps,
                    double alpha, double* G, double* b, cudaStream_t stream, int64_t* detail);
 
-// ---- float64 factorisation and solves (gp_chol.cu) ----------------------------
-constexpr int CHOL_NB = 64;
+// ---- factorisation (gp_factor.cu) and solves (gp_chol.cu) ----------------------
+// Device workspace (bytes) for launch_cholesky and launch_tri_inverse.
+size_t factor_work_bytes(int M, bool fp32_inverse);
 // In-place lower Cholesky of the M x M row-major matrix L (upper part ignored,
-// then zeroed). Non-positive pivot -> status GP_ENOTPD, detail = column.
-cudaError_t launch_cholesky(double* L, int M, GpStatus* st, cudaStream_t stream);
-// W = L^{-1} (lower, M x M row-major); W's upper part is zeroed.
-cudaError_t launch_tri_inverse(const double* L, double* W, int M, GpStatus* st,
+// then zeroed), float64, one cooperative launch. Non-positive pivot ->
+// status GP_ENOTPD, detail = column.
+cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream);
+// W = L^{-1} (lower, M x M row-major, upper part zeroed), computed in float32
+// (fp32 = true) or float64 arithmetic, one cooperative launch.
+cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
                                cudaStream_t stream);
 // c = A^{-1} b through W = L^{-1}: c = W^T (W b), then `refine` steps of
 // c += W^T W (b - A c) with the float64 residual.
