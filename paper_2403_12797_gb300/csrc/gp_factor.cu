@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(NT) trinv_coop_kernel(const double* __restrict
     const int64_t total = (int64_t)M * M;
     for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)gridDim.x * NT) {
         const int i = (int)(e / M), j = (int)(e % M);
-        if (j <= i) R[e] = (i == j) ? T(1) : T(0);
-        else W[e] = 0.0;
+        R[e] = (i == j) ? T(1) : T(0);  // whole matrix: diagonal blocks are read in full
+        if (j > i) W[e] = 0.0;
     }
     if (!grid_sync(gb, st)) return;
     for (int I = 0; I < nb; ++I) {
