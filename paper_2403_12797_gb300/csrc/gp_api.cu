@@ -29,6 +29,7 @@ struct gp_model {
     double* b;              // M, Phi^T y
     double* d;              // M, sigma^2 / lambda_m (clamped)
     uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
+    int* cinfo;             // chunk table of the tensor-core predict (GP_PREC_MIXED only)
 };
 
 namespace {
@@ -253,7 +254,7 @@ void free_model(gp_model* h) {
     cudaGetDevice(&cur);
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    void* ps[] = {h->L, h->W, h->c, h->b, h->d, h->Wpack};
+    void* ps[] = {h->L, h->W, h->c, h->b, h->d, h->Wpack, h->cinfo};
     for (void* p : ps)
         if (p) cudaFree(p);
     cudaSetDevice(cur);
@@ -402,6 +403,8 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return fail(rc);
     if (prec != GP_PREC_FP64) {
         if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return fail(rc);
+        if ((rc = model_alloc(h, sizeof(int) * predtc_cinfo_ints(s), (void**)&h->cinfo, stream)))
+            return fail(rc);
     }
     GpStatus* st;
     double *A, *loglam, *work;
@@ -450,6 +453,14 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
         launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
         gp_note_launches(1);
         e = cudaGetLastError();
+    }
+    std::vector<int> cinfo_host;
+    if (e == cudaSuccess && prec != GP_PREC_FP64) {
+        cinfo_host.resize(predtc_cinfo_ints(s));
+        predtc_build_cinfo(s, cinfo_host.data());
+        // the host vector lives until the status read below synchronises the stream
+        e = cudaMemcpyAsync(h->cinfo, cinfo_host.data(), sizeof(int) * cinfo_host.size(),
+                            cudaMemcpyHostToDevice, stream);
     }
     if (e != cudaSuccess) return fail(cuda_err(e));
     if ((rc = read_status(st, stream))) return fail(rc);
@@ -511,7 +522,7 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, do
             launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
         }
         GpProf pf("predict_tc", stream);
-        e = launch_predict_tc(s, tab, h->Wpack, h->c, h->sigma2, md, vd, st, stream);
+        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->c, h->sigma2, md, vd, st, stream);
         gp_note_launches(2);
     }
     if (e != cudaSuccess) return cuda_err(e);

@@ -9,10 +9,12 @@
 // algorithm step by step, separated by grid barriers whose waits are bounded
 // (GP_ETIMEOUT after GP_WAIT_NS; nothing can hang):
 //
-//   Cholesky (float64, right-looking, 32-column panels), per step k:
-//     A  CTA 0 factors the 32 x 32 diagonal block;
-//     B  one warp per row below it solves x L_kk^T = a (lane j owns x_j);
-//     C  16 x 16 tiles of the trailing lower triangle subtract L_ik L_jk^T.
+//   Cholesky (float64, right-looking, 32-column panels, look-ahead), per step k:
+//     B  one warp per row below the factored diagonal block solves
+//        x L_kk^T = a (lane j owns x_j);
+//     C  16 x 16 tiles of the trailing lower triangle subtract L_ik L_jk^T;
+//        CTA 0 updates the next diagonal block's tiles first and factors it
+//        (32 x 32, in shared memory) while the other CTAs finish C.
 //   A non-positive or NaN pivot sets GP_ENOTPD (detail = column); every CTA
 //   sees it after the next barrier and returns.
 //
@@ -48,20 +50,22 @@ __device__ bool grid_sync(GridBar* gb, GpStatus* st) {
     __syncthreads();
     if (threadIdx.x == 0) {
         s_fail = 0;
-        volatile unsigned int* vgen = &gb->gen;
-        const unsigned int g = *vgen;
+        unsigned int g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gb->gen) : "memory");
         __threadfence();
         const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
         if (arrived == gridDim.x) {
             gb->count = 0u;
             __threadfence();
-            atomicAdd(&gb->gen, 1u);
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->gen) : "memory");
         } else {
             const uint64_t t0 = globaltimer_ns();
             uint32_t it = 0;
-            while (*vgen == g) {
-                __nanosleep(64);
-                if ((++it & 63u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) {
+            while (true) {
+                unsigned int cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&gb->gen) : "memory");
+                if (cur != g) break;
+                if ((++it & 1023u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) {
                     gp_set_status(st, GP_ETIMEOUT, 100);
                     s_fail = 1;
                     break;
@@ -78,58 +82,85 @@ __device__ __forceinline__ int status_code(const GpStatus* st) { return *(volati
 
 // ---------------------------------------------------------------- Cholesky
 
+// Factor the w x w diagonal block at (kb, kb) in shared memory (one CTA).
+__device__ void chol_diag_block(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
+                                double (*a)[CB + 1]) {
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < w * w; e += NT) {
+        const int i = e / w, j = e % w;
+        a[i][j] = (j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        if (tid == 0) {
+            const double piv = a[j][j];
+            if (!(piv > 0.0) || !isfinite(piv)) {
+                bad = 1;
+                gp_set_status(st, GP_ENOTPD, kb + j);
+            } else {
+                a[j][j] = sqrt(piv);
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        const double djj = a[j][j];
+        for (int i = j + 1 + tid; i < w; i += NT) a[i][j] /= djj;
+        __syncthreads();
+        const int r = w - j - 1;
+        for (int e = tid; e < r * r; e += NT) {
+            const int i = j + 1 + e / r, l = j + 1 + e % r;
+            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        }
+        __syncthreads();
+    }
+    if (!bad)
+        for (int e = tid; e < w * w; e += NT) {
+            const int i = e / w, j = e % w;
+            if (j <= i) L[(int64_t)(kb + i) * M + kb + j] = a[i][j];
+        }
+    __syncthreads();
+}
+
+// L[r0.., c0..] -= L[r0.., kb..kb+w) L[c0.., kb..kb+w)^T on one 16 x 16 lower tile.
+__device__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
+                                 double (*ti)[CB + 1], double (*tj)[CB + 1]) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < UT * w; e += NT) {
+        const int r = e / w, l = e % w;
+        ti[r][l] = (r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+        tj[r][l] = (c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+    }
+    __syncthreads();
+    const int ty = tid / UT, tx = tid % UT;
+    double s = 0.0;
+    for (int l = 0; l < w; ++l) s = fma(ti[ty][l], tj[tx][l], s);
+    const int i = r0 + ty, j = c0 + tx;
+    if (i < M && j <= i) L[(int64_t)i * M + j] -= s;
+    __syncthreads();
+}
+
+// Right-looking Cholesky with look-ahead: while the other CTAs apply step
+// k's trailing update, CTA 0 updates the tiles of the next diagonal block
+// first and factors it, so each step costs two grid barriers.
 __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
                                                        GridBar* gb) {
     __shared__ double a[CB][CB + 1];
     __shared__ double ti[UT][CB + 1];
     __shared__ double tj[UT][CB + 1];
-    __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = (M + CB - 1) / CB;
+    const int G = gridDim.x;
+    if (blockIdx.x == 0) chol_diag_block(L, M, 0, min(CB, M), st, a);
+    if (!grid_sync(gb, st)) return;
+    if (status_code(st) != 0) return;
     for (int k = 0; k < nb; ++k) {
         const int kb = k * CB, w = min(CB, M - kb);
         const int rest = M - kb - w;
-        // ---- A: diagonal block
-        if (blockIdx.x == 0) {
-            if (tid == 0) bad = 0;
-            for (int e = tid; e < w * w; e += NT) {
-                const int i = e / w, j = e % w;
-                a[i][j] = (j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
-            }
-            __syncthreads();
-            for (int j = 0; j < w; ++j) {
-                if (tid == 0) {
-                    const double piv = a[j][j];
-                    if (!(piv > 0.0) || !isfinite(piv)) {
-                        bad = 1;
-                        gp_set_status(st, GP_ENOTPD, kb + j);
-                    } else {
-                        a[j][j] = sqrt(piv);
-                    }
-                }
-                __syncthreads();
-                if (bad) break;
-                const double djj = a[j][j];
-                for (int i = j + 1 + tid; i < w; i += NT) a[i][j] /= djj;
-                __syncthreads();
-                const int r = w - j - 1;
-                for (int e = tid; e < r * r; e += NT) {
-                    const int i = j + 1 + e / r, l = j + 1 + e % r;
-                    if (l <= i) a[i][l] -= a[i][j] * a[l][j];
-                }
-                __syncthreads();
-            }
-            if (!bad)
-                for (int e = tid; e < w * w; e += NT) {
-                    const int i = e / w, j = e % w;
-                    if (j <= i) L[(int64_t)(kb + i) * M + kb + j] = a[i][j];
-                }
-        }
-        if (!grid_sync(gb, st)) return;
-        if (status_code(st) != 0) return;
         if (rest == 0) break;
         // ---- B: panel rows, one warp per row
-        const int rows_here = (int)gridDim.x * (NT / 32);
+        const int rows_here = G * (NT / 32);
         if ((int)blockIdx.x * (NT / 32) < rest) {
             for (int e = tid; e < w * w; e += NT) {
                 const int i = e / w, j = e % w;
@@ -142,40 +173,43 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
                 const double av = lane < w ? row[lane] : 0.0;
                 double acc = 0.0, x = 0.0;
                 for (int l = 0; l < w; ++l) {
-                    double xl = 0.0;
                     if (lane == l) x = (av - acc) / a[l][l];
-                    xl = __shfl_sync(0xffffffffu, x, l);
+                    const double xl = __shfl_sync(0xffffffffu, x, l);
                     if (lane > l && lane < w) acc = fma(xl, a[lane][l], acc);
                 }
                 if (lane < w) row[lane] = x;
             }
+            __syncthreads();
         }
         if (!grid_sync(gb, st)) return;
-        // ---- C: trailing update on 16 x 16 lower tiles
+        // ---- C: trailing update; CTA 0 takes the next diagonal block's tiles and factors it
         const int ntr = (rest + UT - 1) / UT;
         const int ntiles = ntr * (ntr + 1) / 2;
-        const int ty = tid / UT, tx = tid % UT;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            int I, J;
-            tri_pair(t, &I, &J);
-            const int r0 = kb + w + I * UT, c0 = kb + w + J * UT;
-            for (int e = tid; e < UT * w; e += NT) {
-                const int r = e / w, l = e % w;
-                ti[r][l] = (r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
-                tj[r][l] = (c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+        const int wn = min(CB, rest);              // width of the next diagonal block
+        const int nd = (wn + UT - 1) / UT;
+        const int ndiag = nd * (nd + 1) / 2;       // its tiles come first in tile order
+        if (blockIdx.x == 0) {
+            for (int t = 0; t < ndiag; ++t) {
+                int I, J;
+                tri_pair(t, &I, &J);
+                chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
             }
-            __syncthreads();
-            double s = 0.0;
-            for (int l = 0; l < w; ++l) s = fma(ti[ty][l], tj[tx][l], s);
-            const int i = r0 + ty, j = c0 + tx;
-            if (i < M && j <= i) L[(int64_t)i * M + j] -= s;
-            __syncthreads();
+            chol_diag_block(L, M, kb + w, wn, st, a);
         }
+        const int first = (G > 1) ? (int)blockIdx.x - 1 : 0;
+        const int stride = (G > 1) ? G - 1 : 1;
+        if (G == 1 || blockIdx.x > 0)
+            for (int t = ndiag + first; t < ntiles; t += stride) {
+                int I, J;
+                tri_pair(t, &I, &J);
+                chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
+            }
         if (!grid_sync(gb, st)) return;
+        if (status_code(st) != 0) return;
     }
     // upper triangle = 0
     const int64_t total = (int64_t)M * M;
-    for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)gridDim.x * NT) {
+    for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)G * NT) {
         const int i = (int)(e / M), j = (int)(e % M);
         if (j > i) L[e] = 0.0;
     }

@@ -92,6 +92,9 @@ constexpr int PREDTC_SUPER = 4; // MMA N-blocks held in TMEM at once (4 x 128 = 
 size_t predtc_wpack_bytes(int M);
 void launch_pack_w_bf16x3(const double* W, int M, uint16_t* Wpack, cudaStream_t stream);
 size_t predtc_smem_bytes(const GpShape& s);
+// Chunk table of the predict kernel (ints): built once per fitted model.
+size_t predtc_cinfo_ints(const GpShape& s);
+void predtc_build_cinfo(const GpShape& s, int* out);
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
-                              const double* c, double sigma2, double* mean, double* var,
-                              GpStatus* st, cudaStream_t stream);
+                              const int* cinfo, const double* c, double sigma2, double* mean,
+                              double* var, GpStatus* st, cudaStream_t stream);

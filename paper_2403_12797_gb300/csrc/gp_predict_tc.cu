@@ -34,12 +34,12 @@ constexpr uint32_t LBO = 128;
 constexpr uint32_t SBO = (BK / 8) * 128;     // 512
 constexpr int NPROD = 128;
 constexpr int NTHREADS = NPROD + 64;
+constexpr int WBUF = 3;                      // window ring: chunks prefetched two ahead
 
 struct SmemP {
     uint8_t* stage;
-    float* win;               // maxrows x TT
-    int* tr;                  // maxrows
-    unsigned short* cr;       // BK x p
+    float* win;               // WBUF x maxrows x TT: window rows of the prefetched chunks
+    int* cr;                  // WBUF x crp4: column -> window-row map of those chunks
     uint64_t* full;           // producers' Phi_* tile is ready (count NPROD)
     uint64_t* wfull;          // the W bulk copy has landed (count 1 + tx bytes)
     uint64_t* empty;
@@ -48,7 +48,7 @@ struct SmemP {
     uint32_t* tmem_base;
 };
 
-__host__ __device__ inline size_t smem_p_layout(int maxrows, int p, char* base, SmemP* L) {
+__host__ __device__ inline size_t smem_p_layout(int maxrows, int crp4, char* base, SmemP* L) {
     size_t off = 0;
     auto take = [&](size_t bytes, size_t align) {
         off = (off + align - 1) / align * align;
@@ -57,9 +57,8 @@ __host__ __device__ inline size_t smem_p_layout(int maxrows, int p, char* base, 
         return o;
     };
     size_t oS = take((size_t)STAGES * STAGE_BYTES, 1024);
-    size_t oW = take(sizeof(float) * maxrows * TT, 16);
-    size_t oT = take(sizeof(int) * maxrows, 16);
-    size_t oC = take(sizeof(unsigned short) * BK * p, 16);
+    size_t oW = take(sizeof(float) * WBUF * maxrows * TT, 16);
+    size_t oC = take(sizeof(int) * WBUF * crp4, 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
     size_t oX = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
@@ -69,8 +68,7 @@ __host__ __device__ inline size_t smem_p_layout(int maxrows, int p, char* base, 
     if (L) {
         L->stage = (uint8_t*)(base + oS);
         L->win = (float*)(base + oW);
-        L->tr = (int*)(base + oT);
-        L->cr = (unsigned short*)(base + oC);
+        L->cr = (int*)(base + oC);
         L->full = (uint64_t*)(base + oF);
         L->wfull = (uint64_t*)(base + oX);
         L->empty = (uint64_t*)(base + oE);
@@ -90,14 +88,17 @@ __host__ __device__ inline int super_chunks(int M, int b0, int nblk) {
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     predict_tc_kernel(GpShape s, const float* __restrict__ tab, const uint8_t* __restrict__ Wpack,
-                      const double* __restrict__ cvec, double sigma2, int maxrows,
-                      double* __restrict__ mean, double* __restrict__ var, GpStatus* st) {
+                      const int* __restrict__ cinfo, int maxrows, const double* __restrict__ cvec,
+                      double sigma2, double* __restrict__ mean, double* __restrict__ var,
+                      GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
-    __shared__ TileWindow wv;
     __shared__ int s_ok[2];
     char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int maxrows4 = (maxrows + 3) & ~3;
+    const int crp4 = (BK * s.p + 3) & ~3;
+    const int cstride = 4 + maxrows4 + crp4;
     SmemP sm;
-    smem_p_layout(maxrows, s.p, base, &sm);
+    smem_p_layout(maxrows, crp4, base, &sm);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t t0 = (int64_t)blockIdx.x * TT;
@@ -128,6 +129,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         int gc = 0;
         int nbc = 0;
+        const int wsz = maxrows * TT;
+        // prefetch cursor over the (super-tile, chunk) sequence, WBUF-1 chunks ahead
+        int pf_sup = 0, pf_c = 0, pf_q = 0;
+        auto prefetch_next = [&]() {
+            if (pf_sup < nsuper) {
+                const int buf = pf_q % WBUF;
+                const int* ci = cinfo + (int64_t)pf_c * cstride;
+                const int nrows = __ldg(ci);
+                for (int e = tid; e < nrows * (TT / 4); e += NPROD) {
+                    const int r = e / (TT / 4), v = e % (TT / 4);
+                    const int row = __ldg(ci + 4 + r);
+                    cp_async16(sm.win + buf * wsz + r * TT + 4 * v, tab + (int64_t)row * s.Npad + t0 + 4 * v);
+                }
+                for (int e = tid; e < crp4 / 4; e += NPROD)
+                    cp_async16(sm.cr + buf * crp4 + 4 * e, ci + 4 + maxrows4 + 4 * e);
+                if (++pf_c >= super_chunks(s.M, pf_sup * SUPER, min(SUPER, nblocks - pf_sup * SUPER))) {
+                    ++pf_sup;
+                    pf_c = 0;
+                }
+            }
+            cp_async_commit();  // one group per chunk, possibly empty
+            ++pf_q;
+        };
+        prefetch_next();
+        prefetch_next();
         for (int sup = 0; sup < nsuper && ok; ++sup) {
             const int b0 = sup * SUPER;
             const int nblk = min(SUPER, nblocks - b0);
@@ -135,20 +161,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool last = (sup == nsuper - 1);
             for (int c = 0; c < nch; ++c, ++gc) {
                 const int stg = gc % STAGES;
-                named_bar_sync(1, NPROD);
-                if (tid == 0) tile_window(s, c * BK, BK, &wv);
-                named_bar_sync(1, NPROD);
-                for (int r = tid; r < wv.nrows; r += NPROD) sm.tr[r] = window_table_row(s, wv, r);
-                for (int e = tid; e < BK * s.p; e += NPROD) {
-                    const int cc = e / s.p, j = e % s.p;
-                    const int m = c * BK + cc;
-                    sm.cr[e] = (unsigned short)(m < s.M ? window_row(s, wv, j, m) : 0xFFFF);
-                }
-                named_bar_sync(1, NPROD);
-                for (int r = 0; r < wv.nrows; ++r)
-                    sm.win[r * TT + t] = __ldg(tab + (int64_t)sm.tr[r] * s.Npad + t0 + t);
-                // one thread waits and broadcasts; the two flags alternate so a
-                // flag is rewritten only after every reader passed a later barrier
+                const int buf = gc % WBUF;
+                cp_async_wait<1>();  // this thread's copies for chunk gc have landed
+                // One barrier per chunk (one thread waits for the stage and
+                // broadcasts; the two flags alternate so a flag is rewritten
+                // only after every reader passed a later barrier): all copies
+                // of chunk gc are visible and chunk gc-1 has been consumed.
                 const int slot = nbc++ & 1;
                 if (tid == 0) {
                     int fine = 1;
@@ -163,6 +181,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     ok = false;
                     break;
                 }
+                prefetch_next();
+                const float* win = sm.win + buf * wsz;
+                const int* cr = sm.cr + buf * crp4;
                 uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
                 float mpart = 0.f;
 #pragma unroll
@@ -170,11 +191,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float v[8];
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
-                        const unsigned short* crr = sm.cr + (g * 8 + kk) * s.p;
+                        const int* crr = cr + (g * 8 + kk) * s.p;
                         float x = 0.f;
-                        if (crr[0] != 0xFFFF) {
-                            x = sm.win[crr[0] * TT + t];
-                            for (int j = 1; j < s.p; ++j) x *= sm.win[crr[j] * TT + t];
+                        if (crr[0] >= 0) {
+                            x = win[crr[0] * TT + t];
+                            for (int j = 1; j < s.p; ++j) x *= win[crr[j] * TT + t];
                         }
                         v[kk] = x;
                     }
@@ -228,6 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 break;
             }
         }
+        cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (ok && t0 + t < s.N) {
             mean[t0 + t] = macc;
             if (var) var[t0 + t] = sigma2 * vacc;
@@ -362,21 +384,53 @@ void launch_pack_w_bf16x3(const double* W, int M, uint16_t* Wpack, cudaStream_t 
     pack_w_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(W, M, Mpad, (uint8_t*)Wpack);
 }
 
+namespace {
+int predtc_maxrows(const GpShape& s) { return gp_max_window_rows(s, BK); }
+int predtc_cstride(const GpShape& s) {
+    return 4 + ((predtc_maxrows(s) + 3) & ~3) + ((BK * s.p + 3) & ~3);
+}
+}  // namespace
+
+size_t predtc_cinfo_ints(const GpShape& s) {
+    return (size_t)((s.M + BK - 1) / BK) * predtc_cstride(s);
+}
+
+// Per 32-column chunk c of Phi_*: [nrows, 0, 0, 0][table row of each window
+// row][window row of (column, dimension), -1 beyond M], padded to 16 bytes.
+void predtc_build_cinfo(const GpShape& s, int* out) {
+    const int maxrows4 = (predtc_maxrows(s) + 3) & ~3;
+    const int cs = predtc_cstride(s);
+    const int nch = (s.M + BK - 1) / BK;
+    for (int c = 0; c < nch; ++c) {
+        int* ci = out + (size_t)c * cs;
+        for (int i = 0; i < cs; ++i) ci[i] = 0;
+        TileWindow w;
+        tile_window(s, c * BK, BK, &w);
+        ci[0] = w.nrows;
+        for (int r = 0; r < w.nrows; ++r) ci[4 + r] = window_table_row(s, w, r);
+        for (int cc = 0; cc < BK; ++cc)
+            for (int j = 0; j < s.p; ++j) {
+                const int m = c * BK + cc;
+                ci[4 + maxrows4 + cc * s.p + j] = m < s.M ? window_row(s, w, j, m) : -1;
+            }
+    }
+}
+
 size_t predtc_smem_bytes(const GpShape& s) {
-    return smem_p_layout(gp_max_window_rows(s, BK), s.p, nullptr, nullptr);
+    return smem_p_layout(predtc_maxrows(s), (BK * s.p + 3) & ~3, nullptr, nullptr);
 }
 
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
-                              const double* c, double sigma2, double* mean, double* var,
-                              GpStatus* st, cudaStream_t stream) {
-    const int maxrows = gp_max_window_rows(s, BK);
-    const size_t smem = smem_p_layout(maxrows, s.p, nullptr, nullptr);
+                              const int* cinfo, const double* c, double sigma2, double* mean,
+                              double* var, GpStatus* st, cudaStream_t stream) {
+    const int maxrows = predtc_maxrows(s);
+    const size_t smem = predtc_smem_bytes(s);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(predict_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(s.Npad / TT);
-    predict_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, c, sigma2,
-                                                        maxrows, mean, var, st);
+    predict_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, cinfo, maxrows,
+                                                        c, sigma2, mean, var, st);
     return cudaGetLastError();
 }

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         auto bcast_wait = [&](uint64_t* bar, uint32_t parity, int site) -> bool {
             const int slot = nbc++ & 1;
             if (tid == 0) {
-                int fine = mbar_wait(bar, parity) ? 1 : 0;
+                int fine = (bar == nullptr || mbar_wait(bar, parity)) ? 1 : 0;
                 if (!fine) gp_set_status(st, GP_ETIMEOUT, site);
                 s_ok[slot] = fine;
             }
@@ -360,9 +360,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < nchunks && ok; ++c) {
             const int stg = c % nst;
             const int buf = c % WBUF;
-            named_bar_sync(1, NPROD);  // chunk c-1's windows are consumed: its buffer is free
-            prefetch(c + 2);
-            cp_async_wait<2>();        // this thread's copies for chunk c have landed
+            cp_async_wait<1>();        // this thread's copies for chunk c have landed
             const float* winI = sm.winI + buf * wsz;
             const float* winJ = sm.winJ + buf * wsz;
             const float* yv = sm.yv + buf * BK;
@@ -376,14 +374,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 else if (!diag)
                     block_scales(s, J * TM, tmb, sm.egJ, sm.scJ + slot * TM, sm.muJ + slot * TM, tid - TM);
             }
-            if (c >= nst) {
-                if (!bcast_wait(&sm.empty[stg], ((c / nst) - 1) & 1, 1)) {
-                    ok = false;
-                    break;
-                }
-            } else {
-                named_bar_sync(1, NPROD);
+            // One barrier per chunk: every thread's copies of chunk c are
+            // visible, chunk c-1 is consumed (its window buffer may be
+            // refilled), and the pipeline stage has been released by the MMAs.
+            if (!bcast_wait(c >= nst ? &sm.empty[stg] : nullptr, ((c / nst) - 1) & 1, 1)) {
+                ok = false;
+                break;
             }
+            prefetch(c + 2);
             uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
 #pragma unroll
             for (int it = 0; it < IT; ++it) {

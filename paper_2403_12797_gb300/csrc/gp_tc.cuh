@@ -60,15 +60,28 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Hardware-suspended wait (returns when the phase completes or after a
+// bounded, implementation-defined time).
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     uint32_t it = 0;
     while (true) {
-        if (mbar_test(bar, parity)) return true;
-        if (++it > 16) __nanosleep(64);
-        if ((it & 255u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) return false;
+        if (mbar_try(bar, parity)) return true;
+        if ((++it & 15u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) return false;
     }
 }
 
