@@ -57,7 +57,7 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int nch, int M
     y[j] = accumulate ? y[j] + s : s;
 }
 
-constexpr int LT_CHUNK = 128;
+constexpr int LT_CHUNK = 32;
 
 // y = W^T (W v)  using tmp (M) and part (ceil(M/LT_CHUNK) * M)
 void wtw_apply(const double* W, int M, const double* v, double* tmp, double* part, double* y,

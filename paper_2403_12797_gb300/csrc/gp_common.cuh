@@ -97,7 +97,9 @@ __host__ __device__ inline int window_table_row(const GpShape& s, const TileWind
 
 // lower-triangular tile pair index q -> (I, J), I >= J, q = I(I+1)/2 + J
 __host__ __device__ inline void tri_pair(int q, int* I, int* J) {
-    int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    // float estimate (double square roots are slow on the device), corrected below
+    int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    if (i < 0) i = 0;
     while ((i + 1) * (i + 2) / 2 <= q) ++i;
     while (i * (i + 1) / 2 > q) --i;
     *I = i;

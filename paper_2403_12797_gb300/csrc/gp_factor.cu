@@ -37,6 +37,7 @@ constexpr int CB = 32;  // Cholesky panel width
 constexpr int UT = 16;  // Cholesky trailing-update tile
 constexpr int IB = 32;  // inverse block size
 constexpr int NT = 256; // threads per CTA
+constexpr int NHELP = 16; // CTAs sharing the next diagonal block's update
 
 struct GridBar {
     unsigned int count;
@@ -78,59 +79,244 @@ __device__ bool grid_sync(GridBar* gb, GpStatus* st) {
     return s_fail == 0;
 }
 
+// 1 / x in float64 with three dependent FMAs instead of a division, for
+// 2^-1022 <= x < 2^1021 (biased exponent 1..2044; callers check the range):
+// the seed is the single-precision reciprocal (rcp.approx.f32) of x's leading
+// 23 mantissa bits, rescaled by x's exponent, and one step of Halley's
+// third-order iteration r <- r (1 + e + e^2), e = 1 - x r, takes its relative
+// error from about 2^-22 to below the float64 rounding level (within one ulp
+// of the rounded quotient). There is no division fallback on purpose: the
+// compiler would evaluate it on every call.
+__device__ __forceinline__ double fast_rcp(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int E = (hi >> 20) & 0x7ff;
+    const float m = __int_as_float(0x3F800000 | ((hi & 0xFFFFF) << 3) | ((unsigned)lo >> 29));
+    float rm;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rm) : "f"(m));
+    const int rb = __float_as_int(rm);
+    const int shi = ((((rb >> 23) & 0xff) - 127 + 1023) << 20) | ((rb & 0x7FFFFF) >> 3);
+    const int slo = rb << 29;
+    double r = __hiloint2double(shi - ((E - 1023) << 20), slo);
+    const double e = fma(-x, r, 1.0);
+    r = fma(r, fma(e, e, e), r);
+    return r;
+}
+
 __device__ __forceinline__ int status_code(const GpStatus* st) { return *(volatile const int*)&st->code; }
 
 // ---------------------------------------------------------------- Cholesky
 
-// Factor the w x w diagonal block at (kb, kb) in shared memory (one CTA).
-__device__ void chol_diag_block(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
-                                double (*a)[CB + 1]) {
-    __shared__ int bad;
-    const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    for (int e = tid; e < w * w; e += NT) {
-        const int i = e / w, j = e % w;
-        a[i][j] = (j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
+// Cholesky workspace header: the grid barrier, the counter of finished
+// next-diagonal-block updates, then (from byte 256) 1 / L_jj for every j.
+struct CholWork {
+    GridBar bar;
+    unsigned int helped;
+};
+constexpr int CHOL_RSD_OFFSET = 256;
+
+constexpr int PSLOT = 4;  // pivot slots (the owner of pivot j reuses the slot of pivot j - 4)
+
+struct PotrfSmem {
+    uint64_t full[PSLOT];   // slot s holds pivot j (j mod PSLOT = s): arrives when u and r are written
+    uint64_t empty[PSLOT];  // every warp arrives once it has applied that pivot to its columns
+    double u[PSLOT][CB];    // pivot column j after steps < j (lane i: a_ij)
+    double l[PSLOT][CB];    // multipliers a_ij / d_j (i > j; 0 elsewhere)
+    double r[PSLOT];        // 1 / d_j
+    double d[CB];       // pivots d_j
+    double s[CB];       // sqrt(d_j)
+    double rs[CB];      // 1 / sqrt(d_j)
+    int bad;
+    int fail;
+};
+
+// Named barriers of the pivot chain: U(s) hands the pivot column of slot s,
+// R(s) its reciprocal, from the owner of pivot j to the owner of pivot j + 1.
+constexpr int POTRF_BAR_U = 1;           // ids 1..PSLOT
+constexpr int POTRF_BAR_R = 1 + PSLOT;   // ids PSLOT+1..2 PSLOT
+
+// col[q] (column warp + 8q) -= l[lane] u[column] for the owned columns m > mlo.
+__device__ __forceinline__ void potrf_apply(double (&col)[4], const double* l, const double* u, int mlo,
+                                            int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double lv = l[lane];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = warp + 8 * q;
+        if (m > mlo && m < w) col[q] = fma(-lv, u[m], col[q]);
+    }
+}
+
+// The owner of pivot j publishes column j (already updated by all earlier
+// pivots) and then its reciprocal. A pivot outside [2^-1022, 2^1021) -- zero,
+// negative, NaN, or beyond any value a Gram matrix plus the clamped noise
+// diagonal reaches -- is checked on the high word (no float64 instruction),
+// recorded as not positive definite and replaced by NaN, so control flow
+// never depends on the data.
+__device__ __forceinline__ void potrf_publish(double v, int j, int w, int kb, GpStatus* st, PotrfSmem& sm,
+                                              bool handoff) {
+    const int lane = threadIdx.x & 31;
+    const int sl = j % PSLOT;
+    sm.u[sl][lane] = v;
+    __syncwarp();
+    if (handoff) named_bar_arrive(POTRF_BAR_U + sl, 64);
+    const double piv = __shfl_sync(0xffffffffu, v, j);
+    const int hi = __double2hiint(piv);
+    const bool ok = hi >= 0x00100000 && hi < 0x7FD00000;
+    const double r = ok ? fast_rcp(piv) : __longlong_as_double(0x7FF8000000000000ll);
+    if (lane == 0) {
+        sm.r[sl] = r;
+        sm.d[j] = piv;
+        if (!ok) {
+            sm.bad = 1;
+            gp_set_status(st, GP_ENOTPD, kb + j);
+        }
+    }
+    __syncwarp();
+    if (handoff) named_bar_arrive(POTRF_BAR_R + sl, 64);
+    // the multipliers, once, for every warp that applies this pivot
+    sm.l[sl][lane] = (lane > j && lane < w) ? v * r : 0.0;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.full[sl]);
+}
+
+// Factor the w x w diagonal block at (kb, kb) in place (one CTA, w <= 32).
+// Right-looking L D L^T elimination in registers: lane i holds row i, warp
+// q owns columns q, q + 8, q + 16, q + 24, and pivot j subtracts
+// (a_ij / d_j) a_mj from every later column m. The critical path is the chain
+// of pivots, so it is cut to one reciprocal and one FMA per pivot: the owner
+// of pivot j publishes column j before forming 1 / d_j, the owner of pivot
+// j + 1 multiplies a_ij a_{j+1,j} meanwhile and, once the reciprocal arrives,
+// finishes its column with one FMA and publishes it in turn. These handoffs
+// use pairs of named barriers; the other warps follow through PSLOT pivot
+// slots guarded by mbarriers (bounded waits), applying each pivot to their
+// columns off the critical path. The owner of pivot j + 2 applies pivot j
+// to that column alone and the rest of its columns after its own turn, so it
+// is never late for the chain. Every warp runs the same sequence of
+// barrier operations whatever the data, so nothing can wait for an arrival
+// that never comes. At the end L_jj = sqrt(d_j), L_ij = a_ij / sqrt(d_j) and
+// rsd[kb + j] = 1 / L_jj. Returns false on a non-positive pivot (GP_ENOTPD)
+// or an expired wait (GP_ETIMEOUT).
+__device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
+                                           double* __restrict__ rsd, PotrfSmem& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double col[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = warp + 8 * q;
+        col[q] = (m < w && lane < w && lane >= m) ? L[(int64_t)(kb + lane) * M + kb + m] : 0.0;
+    }
+    if (tid == 0) {
+        sm.bad = 0;
+        sm.fail = 0;
+        for (int q = 0; q < PSLOT; ++q) {
+            mbar_init(&sm.full[q], 1);
+            mbar_init(&sm.empty[q], NT / 32);
+        }
+        mbar_fence_init();
     }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        if (tid == 0) {
-            const double piv = a[j][j];
-            if (!(piv > 0.0) || !isfinite(piv)) {
-                bad = 1;
-                gp_set_status(st, GP_ENOTPD, kb + j);
-            } else {
-                a[j][j] = sqrt(piv);
+    if (warp == 0) potrf_publish(col[0], 0, w, kb, st, sm, w > 1);
+    int pend = -1;  // pivot this warp has applied to its next pivot column only
+    for (int j = 0; j + 1 < w; ++j) {
+        const int sl = j % PSLOT, jn = j + 1, sn = jn % PSLOT;
+        if (warp == (jn & 7)) {
+            // ---- the pivot chain: finish column jn and publish it
+            named_bar_sync(POTRF_BAR_U + sl, 64);
+            const double p = sm.u[sl][lane] * sm.u[sl][jn];
+            // slot sn last held pivot jn - PSLOT: every warp must be done with it
+            if (jn >= PSLOT && !*(volatile int*)&sm.fail &&
+                !mbar_wait(&sm.empty[sn], (uint32_t)(jn / PSLOT - 1) & 1u)) {
+                if (lane == 0) {
+                    sm.fail = 1;
+                    gp_set_status(st, GP_ETIMEOUT, 103);
+                }
             }
+            named_bar_sync(POTRF_BAR_R + sl, 64);
+            const double r = sm.r[sl];
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q == (jn >> 3)) {
+                    col[q] = fma(-p, r, col[q]);
+                    v = col[q];
+                }
+            potrf_publish(v, jn, w, kb, st, sm, jn + 1 < w);
+            // then the rest of this warp's columns (all > jn): pivot j - 1 if put
+            // off, and pivot j
+            if (pend >= 0) {
+                const int sp = pend % PSLOT;
+                potrf_apply(col, sm.l[sp], sm.u[sp], jn, w);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[sp]);
+                pend = -1;
+            }
+            // pivot j's multipliers were written after its reciprocal's handoff
+            if (!*(volatile int*)&sm.fail && !mbar_wait(&sm.full[sl], (uint32_t)(j / PSLOT) & 1u)) {
+                if (lane == 0) {
+                    sm.fail = 1;
+                    gp_set_status(st, GP_ETIMEOUT, 104);
+                }
+            }
+            potrf_apply(col, sm.l[sl], sm.u[sl], jn, w);
+        } else {
+            // ---- follow pivot j
+            if (!*(volatile int*)&sm.fail && !mbar_wait(&sm.full[sl], (uint32_t)(j / PSLOT) & 1u)) {
+                if (lane == 0) {
+                    sm.fail = 1;
+                    gp_set_status(st, GP_ETIMEOUT, 102);
+                }
+            }
+            const int jnn = jn + 1;
+            if (jnn < w && warp == (jnn & 7)) {
+                // owner of the next pivot: column jnn now, the others after its turn
+                const double lv = sm.l[sl][lane];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q == (jnn >> 3)) col[q] = fma(-lv, sm.u[sl][jnn], col[q]);
+                pend = j;
+                continue;  // its empty arrival for pivot j comes with the deferred update
+            }
+            potrf_apply(col, sm.l[sl], sm.u[sl], j, w);
         }
-        __syncthreads();
-        if (bad) break;
-        const double djj = a[j][j];
-        for (int i = j + 1 + tid; i < w; i += NT) a[i][j] /= djj;
-        __syncthreads();
-        const int r = w - j - 1;
-        for (int e = tid; e < r * r; e += NT) {
-            const int i = j + 1 + e / r, l = j + 1 + e % r;
-            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
-        }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[sl]);
     }
-    if (!bad)
-        for (int e = tid; e < w * w; e += NT) {
-            const int i = e / w, j = e % w;
-            if (j <= i) L[(int64_t)(kb + i) * M + kb + j] = a[i][j];
-        }
     __syncthreads();
+    if (sm.bad || sm.fail) return false;  // uniform: read after the barrier
+    if (tid < w) {
+        const double sq = sqrt(sm.d[tid]);
+        const double rs = 1.0 / sq;
+        sm.s[tid] = sq;
+        sm.rs[tid] = rs;
+        rsd[kb + tid] = rs;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = warp + 8 * q;
+        if (m < w && lane < w && lane >= m)
+            L[(int64_t)(kb + lane) * M + kb + m] = (lane == m) ? sm.s[m] : col[q] * sm.rs[m];
+    }
+    __syncthreads();
+    return true;
 }
 
 // L[r0.., c0..] -= L[r0.., kb..kb+w) L[c0.., kb..kb+w)^T on one 16 x 16 lower tile.
 __device__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
                                  double (*ti)[CB + 1], double (*tj)[CB + 1]) {
     const int tid = threadIdx.x;
-    for (int e = tid; e < UT * w; e += NT) {
-        const int r = e / w, l = e % w;
-        ti[r][l] = (r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
-        tj[r][l] = (c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+    double vi[UT * CB / NT], vj[UT * CB / NT];
+#pragma unroll
+    for (int q = 0; q < UT * CB / NT; ++q) {  // all loads in flight before the stores
+        const int e = tid + q * NT, r = e / CB, l = e % CB;
+        vi[q] = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+        vj[q] = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < UT * CB / NT; ++q) {
+        const int e = tid + q * NT;
+        ti[e / CB][e % CB] = vi[q];
+        tj[e / CB][e % CB] = vj[q];
     }
     __syncthreads();
     const int ty = tid / UT, tx = tid % UT;
@@ -141,60 +327,140 @@ __device__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, i
     __syncthreads();
 }
 
-// Right-looking Cholesky with look-ahead: while the other CTAs apply step
-// k's trailing update, CTA 0 updates the tiles of the next diagonal block
-// first and factors it, so each step costs two grid barriers.
+// Share `part` of `nparts` of the next diagonal block's update
+// L[r0 + I][r0 + J] -= sum_l L[r0 + I][kb + l] L[r0 + J][kb + l] (J <= I < wn,
+// r0 = kb + w): four threads per entry, each summing every fourth l.
+__device__ void chol_next_diag(double* __restrict__ L, int M, int kb, int w, int wn, int part,
+                               int nparts, double (*P)[CB + 1]) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int r0 = kb + w;
+    double v[CB * CB / NT];
+#pragma unroll
+    for (int q = 0; q < CB * CB / NT; ++q) {
+        const int e = tid + q * NT, r = e / CB, l = e % CB;
+        v[q] = (r < wn && l < w) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < CB * CB / NT; ++q) {
+        const int e = tid + q * NT;
+        P[e / CB][e % CB] = v[q];
+    }
+    __syncthreads();
+    const int npairs = wn * (wn + 1) / 2;
+    const int quarter = tid & 3;
+    const unsigned gmask = 0xFu << (lane & ~3);
+    for (int p = part + nparts * (tid >> 2); p < npairs; p += nparts * (NT / 4)) {
+        int I, J;
+        tri_pair(p, &I, &J);
+        double s = 0.0;
+        for (int l = quarter; l < w; l += 4) s = fma(P[I][l], P[J][l], s);
+        s += __shfl_xor_sync(gmask, s, 1);
+        s += __shfl_xor_sync(gmask, s, 2);
+        if (quarter == 0) L[(int64_t)(r0 + I) * M + r0 + J] -= s;
+    }
+    __syncthreads();
+}
+
+// Right-looking blocked Cholesky with look-ahead. Step k:
+//   B  every CTA solves its panel rows (row rr on CTA rr mod G), one warp a row;
+//   -- grid barrier --
+//   C  CTAs 1..NHELP update the next diagonal block (a share each) and count
+//      themselves done; CTA 0 waits for the count and factors that block while
+//      CTAs 1..G-1 apply the rest of the trailing update;
+//   -- grid barrier --
 __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
-                                                       GridBar* gb) {
+                                                       CholWork* cw) {
     __shared__ double a[CB][CB + 1];
     __shared__ double ti[UT][CB + 1];
     __shared__ double tj[UT][CB + 1];
+    __shared__ double rdiag[CB];
+    __shared__ PotrfSmem sm;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = (M + CB - 1) / CB;
     const int G = gridDim.x;
-    if (blockIdx.x == 0) chol_diag_block(L, M, 0, min(CB, M), st, a);
+    const int nh = (G > 1) ? min(NHELP, G - 1) : 1;
+    double* rsd = (double*)((char*)cw + CHOL_RSD_OFFSET);
+    GridBar* gb = &cw->bar;
+    if (blockIdx.x == 0) chol_potrf(L, M, 0, min(CB, M), st, rsd, sm);
     if (!grid_sync(gb, st)) return;
     if (status_code(st) != 0) return;
     for (int k = 0; k < nb; ++k) {
         const int kb = k * CB, w = min(CB, M - kb);
         const int rest = M - kb - w;
         if (rest == 0) break;
-        // ---- B: panel rows, one warp per row
-        const int rows_here = G * (NT / 32);
-        if ((int)blockIdx.x * (NT / 32) < rest) {
-            for (int e = tid; e < w * w; e += NT) {
-                const int i = e / w, j = e % w;
-                a[i][j] = (j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
+        // ---- B: panel rows, x L_kk^T = a (lane j owns x_j). With s_j = 1 / L_jj,
+        // x_j = a_j s_j - sum_{l<j} x_l (L_jl s_j): lane j holds the scaled row of
+        // L_kk in registers, and each step is one shuffle and one FMA.
+        if ((int)blockIdx.x < rest) {
+            double v[CB * CB / NT];
+#pragma unroll
+            for (int q = 0; q < CB * CB / NT; ++q) {
+                const int e = tid + q * NT, i = e / CB, j = e % CB;
+                v[q] = (i < w && j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
             }
+#pragma unroll
+            for (int q = 0; q < CB * CB / NT; ++q) {
+                const int e = tid + q * NT;
+                a[e / CB][e % CB] = v[q];
+            }
+            if (tid < CB) rdiag[tid] = tid < w ? rsd[kb + tid] : 0.0;
             __syncthreads();
-            for (int rr = blockIdx.x * (NT / 32) + warp; rr < rest; rr += rows_here) {
-                const int i = kb + w + rr;
-                double* row = L + (int64_t)i * M + kb;
-                const double av = lane < w ? row[lane] : 0.0;
-                double acc = 0.0, x = 0.0;
-                for (int l = 0; l < w; ++l) {
-                    if (lane == l) x = (av - acc) / a[l][l];
-                    const double xl = __shfl_sync(0xffffffffu, x, l);
-                    if (lane > l && lane < w) acc = fma(xl, a[lane][l], acc);
+            const double rd = rdiag[lane];
+            double ls[CB];
+#pragma unroll
+            for (int l = 0; l < CB; ++l) ls[l] = a[lane][l] * rd;
+            for (int rr = blockIdx.x + G * warp; rr < rest; rr += G * (NT / 32)) {
+                double* row = L + (int64_t)(kb + w + rr) * M + kb;
+                double acc = lane < w ? row[lane] * rd : 0.0;
+#pragma unroll
+                for (int l = 0; l < CB; ++l) {
+                    if (l < w) {
+                        const double xl = __shfl_sync(0xffffffffu, acc, l);
+                        if (lane > l) acc = fma(-xl, ls[l], acc);
+                    }
                 }
-                if (lane < w) row[lane] = x;
+                if (lane < w) row[lane] = acc;
             }
             __syncthreads();
         }
         if (!grid_sync(gb, st)) return;
-        // ---- C: trailing update; CTA 0 takes the next diagonal block's tiles and factors it
+        // ---- C
+        const int wn = min(CB, rest);              // width of the next diagonal block
         const int ntr = (rest + UT - 1) / UT;
         const int ntiles = ntr * (ntr + 1) / 2;
-        const int wn = min(CB, rest);              // width of the next diagonal block
         const int nd = (wn + UT - 1) / UT;
-        const int ndiag = nd * (nd + 1) / 2;       // its tiles come first in tile order
-        if (blockIdx.x == 0) {
-            for (int t = 0; t < ndiag; ++t) {
-                int I, J;
-                tri_pair(t, &I, &J);
-                chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
+        const int ndiag = nd * (nd + 1) / 2;       // tiles of the next diagonal block come first
+        const bool helper = (G == 1) || ((int)blockIdx.x >= 1 && (int)blockIdx.x <= nh);
+        if (helper) {
+            chol_next_diag(L, M, kb, w, wn, G == 1 ? 0 : (int)blockIdx.x - 1, nh, a);
+            if (G > 1 && tid == 0) {
+                __threadfence();
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&cw->helped) : "memory");
             }
-            chol_diag_block(L, M, kb + w, wn, st, a);
+        }
+        if (blockIdx.x == 0) {
+            if (G > 1) {
+                if (tid == 0) {
+                    s_fail = 0;
+                    const unsigned int target = (unsigned)nh * (unsigned)(k + 1);
+                    const uint64_t t0 = globaltimer_ns();
+                    uint32_t it = 0;
+                    while (true) {
+                        unsigned int cur;
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&cw->helped) : "memory");
+                        if (cur >= target) break;
+                        if ((++it & 1023u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) {
+                            gp_set_status(st, GP_ETIMEOUT, 101);
+                            s_fail = 1;
+                            break;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (s_fail) return;
+            }
+            chol_potrf(L, M, kb + w, wn, st, rsd, sm);
         }
         const int first = (G > 1) ? (int)blockIdx.x - 1 : 0;
         const int stride = (G > 1) ? G - 1 : 1;
@@ -306,6 +572,139 @@ __global__ void __launch_bounds__(NT) trinv_coop_kernel(const double* __restrict
     }
 }
 
+// float32 inverse by column strips (M <= STRIP_MAX_M). Block column J of W
+// depends on no other block column, so after one grid barrier (the diagonal
+// block inverses D_I) each CTA walks its strips down the rows with no further
+// synchronisation:
+//   W_IJ = D_I (delta_IJ I - sum_{J <= K < I} L_IK W_KJ).
+// The strip's finished blocks stay in shared memory (M x 32 float32), and the
+// K sum streams L in chunks of SKC columns whose global loads are issued one
+// chunk ahead, into registers, while the current chunk is multiplied.
+constexpr int SKC = 128;
+constexpr int STRIP_MAX_M = 1024;
+constexpr int SPF = IB * SKC / NT;  // chunk elements per thread
+
+size_t strip_smem_bytes(int M) {
+    return sizeof(float) * ((size_t)M * IB + (size_t)IB * (SKC + 1) + 2 * IB * (IB + 1));
+}
+
+__global__ void __launch_bounds__(NT) trinv_strip_kernel(const double* __restrict__ L,
+                                                         double* __restrict__ W, int M,
+                                                         float* __restrict__ Dinv, GpStatus* st,
+                                                         GridBar* gb) {
+    extern __shared__ __align__(16) float smem_f[];
+    float* sS = smem_f;                               // [M][IB]   the strip
+    float (*sL)[SKC + 1] = (float (*)[SKC + 1])(sS + (size_t)M * IB);
+    float (*sa)[IB + 1] = (float (*)[IB + 1])(&sL[IB][0]);
+    float (*sb)[IB + 1] = sa + IB;
+    const int tid = threadIdx.x;
+    const int nb = (M + IB - 1) / IB;
+    // ---- 0: D_I = L_II^{-1}
+    for (int I = blockIdx.x; I < nb; I += gridDim.x) {
+        const int r0 = I * IB, wI = min(IB, M - r0);
+        float v[IB * IB / NT];
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT, i = e / IB, j = e % IB;
+            v[q] = (i < wI && j <= i) ? (float)L[(int64_t)(r0 + i) * M + r0 + j] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT;
+            sa[e / IB][e % IB] = v[q];
+            sb[e / IB][e % IB] = 0.0f;
+        }
+        __syncthreads();
+        if (tid < wI) {
+            const int j = tid;
+            sb[j][j] = 1.0f / sa[j][j];
+            for (int i = j + 1; i < wI; ++i) {
+                float s = 0.0f;
+                for (int k = j; k < i; ++k) s = fmaf(sa[i][k], sb[k][j], s);
+                sb[i][j] = -s / sa[i][i];
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < IB * IB; e += NT) Dinv[(int64_t)I * IB * IB + e] = sb[e / IB][e % IB];
+        __syncthreads();
+    }
+    if (!grid_sync(gb, st)) return;
+    // ---- 1: strips
+    const int ty = tid >> 3, tx = (tid & 7) * 4;
+    for (int J = blockIdx.x; J < nb; J += gridDim.x) {
+        const int c0 = J * IB, wJ = min(IB, M - c0);
+        for (int e = tid; e < c0 * IB; e += NT) {  // rows above the strip's diagonal block
+            const int i = e / IB, j = e % IB;
+            if (j < wJ) W[(int64_t)i * M + c0 + j] = 0.0;
+        }
+        // chunk prefetch: (pI, pkc) is the next chunk to be consumed
+        int pI = J + 1, pkc = c0;
+        float pf[SPF];
+        auto load_chunk = [&](int I, int kc) {
+            const int r0 = I * IB, wI = min(IB, M - r0);
+#pragma unroll
+            for (int q = 0; q < SPF; ++q) {
+                const int e = tid + q * NT, i = e / SKC, l = e % SKC;
+                pf[q] = (i < wI && kc + l < r0) ? (float)L[(int64_t)(r0 + i) * M + kc + l] : 0.0f;
+            }
+        };
+        if (pI < nb) load_chunk(pI, pkc);
+        for (int I = J; I < nb; ++I) {
+            const int r0 = I * IB, wI = min(IB, M - r0);
+            float acc[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = (I == J && ty == tx + c) ? 1.0f : 0.0f;
+            for (int kc = c0; kc < r0; kc += SKC) {
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < SPF; ++q) {
+                    const int e = tid + q * NT;
+                    sL[e / SKC][e % SKC] = pf[q];
+                }
+                __syncthreads();
+                if (pkc + SKC < pI * IB) {
+                    pkc += SKC;
+                } else {
+                    ++pI;
+                    pkc = c0;
+                }
+                if (pI < nb) load_chunk(pI, pkc);
+                const int kn = min(SKC, r0 - kc);
+                const float* srow = sS + (size_t)kc * IB + tx;
+                for (int l = 0; l < kn; ++l) {
+                    const float av = sL[ty][l];
+                    const float4 w4 = *reinterpret_cast<const float4*>(srow + (size_t)l * IB);
+                    acc[0] = fmaf(-av, w4.x, acc[0]);
+                    acc[1] = fmaf(-av, w4.y, acc[1]);
+                    acc[2] = fmaf(-av, w4.z, acc[2]);
+                    acc[3] = fmaf(-av, w4.w, acc[3]);
+                }
+            }
+            float dv[IB * IB / NT];
+#pragma unroll
+            for (int q = 0; q < IB * IB / NT; ++q) dv[q] = Dinv[(int64_t)I * IB * IB + tid + q * NT];
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sb[ty][tx + c] = acc[c];
+#pragma unroll
+            for (int q = 0; q < IB * IB / NT; ++q) {
+                const int e = tid + q * NT;
+                sa[e / IB][e % IB] = dv[q];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float o = 0.0f;
+                for (int l = 0; l <= ty; ++l) o = fmaf(sa[ty][l], sb[l][tx + c], o);
+                const bool ok = ty < wI && tx + c < wJ;
+                if (r0 + ty < M) sS[(size_t)(r0 + ty) * IB + tx + c] = ok ? o : 0.0f;
+                if (ok) W[(int64_t)(r0 + ty) * M + c0 + tx + c] = (double)o;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int coop_grid(const void* kern, int dev) {
     int sms = 1, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -319,16 +718,18 @@ int coop_grid(const void* kern, int dev) {
 size_t factor_work_bytes(int M, bool fp32_inverse) {
     const size_t nb = (M + IB - 1) / IB;
     const size_t el = fp32_inverse ? sizeof(float) : sizeof(double);
-    return 256 + el * ((size_t)M * M + nb * IB * IB);
+    const size_t inv = el * ((size_t)M * M + nb * IB * IB);
+    const size_t chol = sizeof(double) * (size_t)M;  // 1 / L_jj
+    return CHOL_RSD_OFFSET + (inv > chol ? inv : chol);
 }
 
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
-    GridBar* gb = (GridBar*)work;
-    cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
+    CholWork* cw = (CholWork*)work;
+    cudaMemsetAsync(cw, 0, CHOL_RSD_OFFSET, stream);
     dim3 grid((unsigned)coop_grid((const void*)chol_coop_kernel, dev)), block(NT);
-    void* args[] = {&L, &M, &st, &gb};
+    void* args[] = {&L, &M, &st, &cw};
     gp_note_launches(1);
     return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, grid, block, args, 0, stream);
 }
@@ -342,13 +743,24 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
     char* base = (char*)work + 256;
     const size_t nb = (M + IB - 1) / IB;
     gp_note_launches(1);
+    if (fp32 && M <= STRIP_MAX_M) {
+        float* D = (float*)base;
+        const void* k = (const void*)trinv_strip_kernel;
+        const size_t smem = strip_smem_bytes(M);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        dim3 grid((unsigned)sms), block(NT);
+        void* args[] = {(void*)&L, &W, &M, &D, &st, &gb};
+        (void)nb;
+        return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
+    }
     if (fp32) {
         float* R = (float*)base;
         float* D = R + (size_t)M * M;
         const void* k = (const void*)trinv_coop_kernel<float>;
         dim3 grid((unsigned)coop_grid(k, dev)), block(NT);
         void* args[] = {(void*)&L, &W, &M, &R, &D, &st, &gb};
-        (void)nb;
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
     double* R = (double*)base;

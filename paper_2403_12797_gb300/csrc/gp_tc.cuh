@@ -89,6 +89,13 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Producer side of a named barrier: counts this warp's threads and continues;
+// shared-memory writes made before it are visible to the threads that
+// complete named_bar_sync on the same barrier.
+__device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // ---------------------------------------------------------------- proxies / fences
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
