@@ -27,13 +27,14 @@
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows:
-//   warps 0-7  producers: copy the tables' window rows for the chunk into
-//              shared memory, form Phi for column tiles I and J in the K-major
-//              core-matrix layout (8 columns x 16 bytes), split, publish the
-//              stage; J == 0 CTAs also accumulate b_I = Phi_I^T y (float32,
-//              warp-shuffle reduction). They drain TMEM and write the
-//              (scaled) partial tile at the end.
-//   warp 8     allocates TMEM and issues the MMAs (one elected lane):
+//   warps 0-15 producers (one 8-column core group each): copy the tables'
+//              window rows for the chunk into shared memory, form Phi for
+//              column tiles I and J in the K-major core-matrix layout
+//              (8 columns x 16 bytes), split, publish the stage; J == 0 CTAs
+//              also accumulate b_I = Phi_I^T y (float32, warp-shuffle
+//              reduction). They drain TMEM and write the (scaled) partial
+//              tile at the end.
+//   warp 16    allocates TMEM and issues the MMAs (one elected lane):
 //              4 x (128 x 128 x 16) per 16 rows; tcgen05.commit frees stages
 //              and signals finished blocks.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
@@ -52,10 +53,9 @@ constexpr int TILE_BYTES = TM * BK * 2;    // one bf16 operand tile: 8 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A s2, B s1, B s2
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
 constexpr uint32_t SBO = (BK / 8) * 128;   // 8-row groups
-constexpr int NPROD = 256;                 // 8 producer warps
+constexpr int NPROD = 512;                 // 16 producer warps: one 8-column core group each
 constexpr int NPW = NPROD / 32;
-constexpr int IT = (TM / 8) / NPW;         // 8-column core groups per producer warp
-constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain
+constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain (32)
 constexpr int MMA_WARP = NPW;
 constexpr int NTHREADS = NPROD + 32;
 constexpr uint32_t TMEM_COLS = 512;        // 2 buffers x (acc1 | acc2)
@@ -193,25 +193,37 @@ __device__ __forceinline__ void load_window_async(const GpShape& s, const float*
     }
 }
 
-// Phi values of column r (window rows crr[0..p)) for data rows 8g..8g+7 of the chunk.
-__device__ __forceinline__ void phi8(const float* win, const unsigned short* crr, int p, int g,
-                                     float v[8]) {
-    if (crr[0] == 0xFFFF) {
+// Phi values of one column for data rows 8g..8g+7 of the chunk: the product
+// over dimensions of the column's window rows, whose float offsets woff[j]
+// (window row x WSTRIDE) are held in registers; woff[0] < 0 marks a padding
+// column (m >= M). P = 0 takes p at run time and the offsets from the
+// column's window-row map crr in shared memory.
+template <int P>
+__device__ __forceinline__ void phi8(const float* win, const int* woff, const unsigned short* crr, int p,
+                                     int g, float v[8]) {
+    const int o0 = (P > 0) ? woff[0] : (crr[0] == 0xFFFF ? -1 : crr[0] * WSTRIDE);
+    if (o0 < 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = 0.f;
         return;
     }
     {
-        const float4* w = reinterpret_cast<const float4*>(win + crr[0] * WSTRIDE + 8 * g);
+        const float4* w = reinterpret_cast<const float4*>(win + o0 + 8 * g);
         float4 a = w[0], b = w[1];
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     }
-    for (int j = 1; j < p; ++j) {
-        const float4* w = reinterpret_cast<const float4*>(win + crr[j] * WSTRIDE + 8 * g);
+    auto mul_row = [&](int oj) {
+        const float4* w = reinterpret_cast<const float4*>(win + oj + 8 * g);
         float4 a = w[0], b = w[1];
         v[0] *= a.x; v[1] *= a.y; v[2] *= a.z; v[3] *= a.w;
         v[4] *= b.x; v[5] *= b.y; v[6] *= b.z; v[7] *= b.w;
+    };
+    if constexpr (P > 0) {
+#pragma unroll
+        for (int j = 1; j < P; ++j) mul_row(woff[j]);
+    } else {
+        for (int j = 1; j < p; ++j) mul_row(crr[j] * WSTRIDE);
     }
 }
 
@@ -223,22 +235,36 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 // Scale 8 values by sc and split each into the integer s1 = rint(w)
 // (|s1| <= 128, exact in fp16) and the remainder lo = fp16(w - s1)
 // (|lo| <= 1/2, 11-bit precision, subnormals below 2^-14); store both
-// core-matrix rows.
+// core-matrix rows. The float-to-integer rounding and float16 packing
+// instructions run at a fraction of the FMA rate, so s1 avoids both: adding
+// 1.5 * 2^23 rounds w to the nearest integer k (ties to even) in the low
+// mantissa bits of t, the integer k + 1152 has the float16 bit pattern
+// 0x6480 + k (exponent 2^10), and one exact half2 subtraction of 1152 leaves
+// k. Only the remainder takes a float16 conversion.
 __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
                                              const float v[8], float sc) {
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    const __half2 k1152 = __floats2half2_rn(1152.0f, 1152.0f);
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;
-        const float a0 = rintf(w0), a1 = rintf(w1);
-        h[q] = pack_half2(a0, a1);
-        l[q] = pack_half2(w0 - a0, w1 - a1);
+        const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;  // exact: sc is a power of two
+        const float t0 = __fadd_rn(w0, kMagic), t1 = __fadd_rn(w1, kMagic);
+        const float a0 = __fsub_rn(t0, kMagic), a1 = __fsub_rn(t1, kMagic);
+        const uint32_t b0 = (uint32_t)__float_as_int(t0) - 0x4B400000u + 0x6480u;
+        const uint32_t b1 = (uint32_t)__float_as_int(t1) - 0x4B400000u + 0x6480u;
+        const uint32_t raw = __byte_perm(b0, b1, 0x5410);
+        const __half2 k2 = __hsub2(*reinterpret_cast<const __half2*>(&raw), k1152);
+        h[q] = *reinterpret_cast<const uint32_t*>(&k2);
+        l[q] = pack_half2(__fsub_rn(w0, a0), __fsub_rn(w1, a1));
     }
     const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
     *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise.
+template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmaxb,
                    const unsigned int* __restrict__ tmax,
@@ -292,13 +318,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (warp < NPW) {
         // ------------------------------------------------------------ producers
-        const int g = lane >> 3;       // 8-row group of the chunk
-        const int rl = lane & 7;       // column within an 8-column core group
-        const int quarter = warp & 3;  // TMEM lanes 32*quarter.. (tile rows)
-        const int half = warp >> 2;    // tile columns CPT*half ..
-        float bacc[IT];
+        // generation: this thread's tile column r (core group = warp), data rows 8g..8g+7
+        const int g = lane >> 3;
+        const int rl = lane & 7;
+        const int r = 8 * warp + rl;
+        // drain: TMEM lanes 32*quarter.. (tile rows), tile columns CPT*cgrp ..
+        const int quarter = warp & 3;
+        const int cgrp = warp >> 2;
+        int woffI[P > 0 ? P : 1], woffJ[P > 0 ? P : 1];
+        if constexpr (P > 0) {
 #pragma unroll
-        for (int it = 0; it < IT; ++it) bacc[it] = 0.f;
+            for (int j = 0; j < P; ++j) {
+                const unsigned short ci = sm.crI[r * s.p + j];
+                woffI[j] = (j == 0 && ci == 0xFFFF) ? -1 : ci * WSTRIDE;
+                const unsigned short cj = diag ? ci : sm.crJ[r * s.p + j];
+                woffJ[j] = (j == 0 && cj == 0xFFFF) ? -1 : cj * WSTRIDE;
+            }
+        }
+        float bacc = 0.f;
         float gacc[CPT];               // this thread's part of its tile row
 #pragma unroll
         for (int i = 0; i < CPT; ++i) gacc[i] = 0.f;
@@ -323,10 +360,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int u = d & 1;
             if (!bcast_wait(&sm.accf[u], (d >> 1) & 1, 4)) return false;
             tc_fence_after();
-            const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + half * CPT;
+            const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + cgrp * CPT;
             // back to the global column scaling (exact powers of two)
             const float mrow = sm.muI[u * TM + quarter * 32 + lane];
-            const float* mcol = (diag ? sm.muI : sm.muJ) + u * TM + half * CPT;
+            const float* mcol = (diag ? sm.muI : sm.muJ) + u * TM + cgrp * CPT;
 #pragma unroll
             for (int ch = 0; ch < CPT / 16; ++ch) {
                 float a1[16], a2[16];
@@ -357,6 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         prefetch(1);
 
         int next_drain = 0;
+        float scI = 0.f, scJ = 0.f;
         for (int c = 0; c < nchunks && ok; ++c) {
             const int stg = c % nst;
             const int buf = c % WBUF;
@@ -365,13 +403,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const float* winJ = sm.winJ + buf * wsz;
             const float* yv = sm.yv + buf * BK;
             const int slot = (c / BLOCK_CHUNKS) & 1;
-            if (c % BLOCK_CHUNKS == 0) {
+            const bool newblk = (c % BLOCK_CHUNKS == 0);
+            if (newblk) {
                 // a new 512-row block: its column scales (the drain of the
                 // block two back, which used this slot, is complete)
                 const unsigned int* tmb = tmaxb + ((r0 + (int64_t)c * BK) / GP_TAB_BLOCK) * (s.p * s.n);
                 if (tid < TM)
                     block_scales(s, I * TM, tmb, sm.egI, sm.scI + slot * TM, sm.muI + slot * TM, tid);
-                else if (!diag)
+                else if (!diag && tid < 2 * TM)
                     block_scales(s, J * TM, tmb, sm.egJ, sm.scJ + slot * TM, sm.muJ + slot * TM, tid - TM);
             }
             // One barrier per chunk: every thread's copies of chunk c are
@@ -381,27 +420,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = false;
                 break;
             }
+            if (newblk) {
+                scI = sm.scI[slot * TM + r];
+                scJ = diag ? scI : sm.scJ[slot * TM + r];
+            }
             prefetch(c + 2);
             uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
-#pragma unroll
-            for (int it = 0; it < IT; ++it) {
-                const int r = 8 * (it * NPW + warp) + rl;
+            {
                 float v[8];
-                phi8(winI, sm.crI + r * s.p, s.p, g, v);
-                store_slices(sb, sb + TILE_BYTES, r, g, v, sm.scI[slot * TM + r]);
+                phi8<P>(winI, woffI, sm.crI + r * s.p, s.p, g, v);
+                store_slices(sb, sb + TILE_BYTES, r, g, v, scI);
                 if (J == 0) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) bacc[it] = fmaf(v[k], yv[8 * g + k], bacc[it]);
+                    for (int k = 0; k < 8; ++k) bacc = fmaf(v[k], yv[8 * g + k], bacc);
                 }
             }
             if (!diag) {
-#pragma unroll
-                for (int it = 0; it < IT; ++it) {
-                    const int r = 8 * (it * NPW + warp) + rl;
-                    float v[8];
-                    phi8(winJ, sm.crJ + r * s.p, s.p, g, v);
-                    store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, sm.scJ[slot * TM + r]);
-                }
+                float v[8];
+                phi8<P>(winJ, woffJ, sm.crJ + r * s.p, s.p, g, v);
+                store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, scJ);
             }
             fence_proxy_async_smem();
             mbar_arrive(&sm.full[stg]);
@@ -420,18 +457,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (J == 0) {
-#pragma unroll
-            for (int it = 0; it < IT; ++it) {
-                float v = bacc[it];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (lane < 8) bpart[(int64_t)split * s.Mpad + I * TM + 8 * (it * NPW + warp) + rl] = v;
-            }
+            float v = bacc;
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (lane < 8) bpart[(int64_t)split * s.Mpad + I * TM + r] = v;
         }
         if (ok) {
             const int row = quarter * 32 + lane;
             float4* o4 = reinterpret_cast<float4*>(Gpart + ((int64_t)split * npairs + q) * (TM * TM) +
-                                                   (int64_t)row * TM + half * CPT);
+                                                   (int64_t)row * TM + cgrp * CPT);
 #pragma unroll
             for (int k = 0; k < CPT / 4; ++k)
                 o4[k] = make_float4(gacc[4 * k], gacc[4 * k + 1], gacc[4 * k + 2], gacc[4 * k + 3]);
@@ -512,13 +546,21 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
     size_t smem = 0;
     const int nst = syrk_tc_stages(s, maxrows, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     const int T = s.Mpad / TM;
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
-    syrk_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs,
-                                                     maxrows, nst, Gpart, bpart, colexp, st);
-    return cudaGetLastError();
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs, maxrows,
+                                               nst, Gpart, bpart, colexp, st);
+        return cudaGetLastError();
+    };
+    switch (s.p) {
+        case 1: return go(syrk_tc_kernel<1>);
+        case 2: return go(syrk_tc_kernel<2>);
+        case 3: return go(syrk_tc_kernel<3>);
+        case 4: return go(syrk_tc_kernel<4>);
+        default: return go(syrk_tc_kernel<0>);
+    }
 }
