@@ -278,12 +278,14 @@ def run_ours(args):
     roofline = roof(dom) if dom else None
     roof_syrk = roof("syrk_tc") if "syrk_tc" in groups else None
     if roof_syrk is not None:
-        roof_syrk["executed_tflops"] = roof_syrk["achieved"] * 3
+        # four fp16 products per pair of Phi values (s1 s1', s1 lo', lo s1', lo lo')
+        roof_syrk["executed_tflops"] = roof_syrk["achieved"] * 4
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16 tensor (f32 acc, exact blocks) + f64 factorisation" if prec != "fp64" else "f64",
+           "dtype": ("f16 tensor (integer + remainder slices, f32 acc in exact 512-row blocks) "
+                     "+ f64 factorisation") if prec != "fp64" else "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "prec": prec, "l2": "flushed between steps (256 MiB write)",
                       "replicas": world},

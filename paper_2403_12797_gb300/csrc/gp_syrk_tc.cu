@@ -244,19 +244,20 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
                                              const float v[8], float sc) {
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-    const __half2 k1152 = __floats2half2_rn(1152.0f, 1152.0f);
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float w0 = v[2 * q] * sc, w1 = v[2 * q + 1] * sc;  // exact: sc is a power of two
-        const float t0 = __fadd_rn(w0, kMagic), t1 = __fadd_rn(w1, kMagic);
+        // v * sc is exact (sc is a power of two), so one rounding each: t rounds
+        // v sc + 1.5 2^23 to an integer, a = rint(v sc), lo = v sc - a exactly
+        const float t0 = __fmaf_rn(v[2 * q], sc, kMagic), t1 = __fmaf_rn(v[2 * q + 1], sc, kMagic);
         const float a0 = __fsub_rn(t0, kMagic), a1 = __fsub_rn(t1, kMagic);
         const uint32_t b0 = (uint32_t)__float_as_int(t0) - 0x4B400000u + 0x6480u;
         const uint32_t b1 = (uint32_t)__float_as_int(t1) - 0x4B400000u + 0x6480u;
         const uint32_t raw = __byte_perm(b0, b1, 0x5410);
-        const __half2 k2 = __hsub2(*reinterpret_cast<const __half2*>(&raw), k1152);
-        h[q] = *reinterpret_cast<const uint32_t*>(&k2);
-        l[q] = pack_half2(__fsub_rn(w0, a0), __fsub_rn(w1, a1));
+        uint32_t k2;
+        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(k2) : "r"(raw), "r"(0x64806480u));  // - (1152, 1152)
+        h[q] = k2;
+        l[q] = pack_half2(__fmaf_rn(v[2 * q], sc, -a0), __fmaf_rn(v[2 * q + 1], sc, -a1));
     }
     const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
     *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);

@@ -60,28 +60,31 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Hardware-suspended wait (returns when the phase completes or after a
-// bounded, implementation-defined time).
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+// Hardware-suspended wait: the thread sleeps until the phase completes (it
+// wakes as fast as a polling loop would see the completion) or until about
+// `ns` nanoseconds have passed, so a waiting thread issues no instructions
+// that the working warps of its scheduler could use.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
         : "memory");
     return ok != 0;
 }
 
 // Wait for the phase with the given parity to complete; false on timeout.
+// The first suspended try normally returns with the phase complete; the
+// clock (a slow special-register read) is consulted only after that.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (mbar_test(bar, parity)) return true;
+    if (mbar_try(bar, parity, 1000000u)) return true;
     const uint64_t t0 = globaltimer_ns();
-    uint32_t it = 0;
     while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if ((++it & 15u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) return false;
+        if (mbar_try(bar, parity, 1000000u)) return true;
+        if (globaltimer_ns() - t0 > GP_WAIT_NS) return false;
     }
 }
 
@@ -223,8 +226,18 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc)
                  : "memory");
 }
+// Arrive on bar once every cp.async this thread has issued so far has landed
+// (the arrival is not counted in advance: the barrier's expected count must
+// include it).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until every cp.async of this thread has completed
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 // wait until at most N of this thread's committed groups are still pending
 template <int N>

@@ -32,6 +32,8 @@ GRAM_CASES = [
     (7, 1, 2, 3),
     (8, 4099, 1, 300),
     (9, 1500, 3, 6),
+    (10, 600, 5, 2),    # p > 4: the run-time-p generation path
+    (11, 700, 6, 3),    # p > 4 with several column tiles (M = 729)
 ]
 
 
