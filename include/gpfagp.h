@@ -179,14 +179,33 @@ typedef struct gp_fit_args {
     double eps, alpha, sigma2;
 } gp_fit_args;
 
-/* Fit `count` independent problems of uneven N, p and n. The contraction of
- * all problems runs as ONE persistent launch over a shared work list; the
- * float64 factorisations run batched. out[i] receives problem i's model
- * (or NULL); the return value is GP_OK when every problem succeeded, else
- * the first failing problem's status (gp_last_error_detail() = its index).
- * Each model is the same as the one gp_fit_ex would produce on its own. */
+/* Fit `count` independent problems of uneven N, p and n (and precision
+ * `prec` for all) side by side.
+ *   - Inputs, model buffers and the shape-only tables are staged first.
+ *   - The launch plan comes from an autotuner: each problem's Gram gets a
+ *     share of k waves of the GPU in proportion to its contraction work, with
+ *     k in {1, 2, 4} chosen once per distinct batch (multiset of p, n, N
+ *     rounded to a power of two) by timing the batch's Gram steps on the
+ *     device; the choice is cached for the process.
+ *   - Every problem's fit is enqueued on one of up to 8 streams and the whole
+ *     batch is captured into ONE CUDA graph and launched once; if the driver
+ *     refuses to capture or instantiate it, the same launches run directly on
+ *     the streams (gp_batch_info reports which).
+ *   - All statuses are read back once at the end.
+ * out[i] receives problem i's model, or NULL if it failed; the return value
+ * is GP_OK when every problem succeeded, else the first failing problem's
+ * status with gp_last_error_detail() = its index. X, y are device pointers
+ * when dev_ptrs != 0, else host pointers (copied during the call). Each
+ * model equals the one gp_fit_ex computes for the same problem up to the
+ * order of the Gram's split sums (the autotuned split count), i.e. within
+ * the precision mode's tolerance. Blocks until the batch has run. */
 GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec,
                             void* cuda_stream, int dev_ptrs, gp_model** out);
+
+/* Of the last gp_fit_batch on this thread: *used_graph = 1 if the batch ran
+ * as one captured graph (0 if directly on streams), *tuned_k = the Gram
+ * budget factor of its plan. Either pointer may be NULL. */
+GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k);
 
 /* One predict request of a batched predict. */
 typedef struct gp_predict_args {
@@ -197,9 +216,13 @@ typedef struct gp_predict_args {
     double* var;       /* Ns, or NULL */
 } gp_predict_args;
 
-/* Run `count` predict requests against (possibly different) models as one
- * persistent launch per precision mode. Device pointers only. Each result
- * is bitwise the same as gp_predict_ex on that request alone. */
+/* Run `count` predict requests against (possibly different) models side by
+ * side: each request's kernels are enqueued on one of up to 8 streams
+ * behind `cuda_stream` (no host synchronisation in between), then the call
+ * waits once and reads every request's status. Device pointers only. Each
+ * result is bitwise the same as gp_predict_ex on that request alone (the
+ * same kernels with the same launch configuration). Returns the first
+ * failing request's status (detail = its index). */
 GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream);
 
 /* ---- test hooks ----------------------------------------------------------- */

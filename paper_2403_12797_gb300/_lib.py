@@ -75,6 +75,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_gram_static": (i, [vp, vp, i64, i, i, d, d, vp, vp, vp]),
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
+        "gp_batch_info": (i, [C.POINTER(i), C.POINTER(i)]),
         "gp_debug_fail_alloc_after": (None, [i]),
         "gp_version": (C.c_char_p, []),
     }
@@ -254,6 +255,13 @@ def fit_batch(problems: Sequence[Tuple], prec: str = "mixed", stream=None) -> Li
                 m.free()
         _check(rc, "gp_fit_batch")
     return models
+
+
+def batch_info() -> Tuple[int, int]:
+    """(used_graph, tuned_k) of this thread's last fit_batch."""
+    g, k = C.c_int(), C.c_int()
+    lib().gp_batch_info(C.byref(g), C.byref(k))
+    return g.value, k.value
 
 
 def predict_batch(reqs: Sequence[Tuple], stream=None):

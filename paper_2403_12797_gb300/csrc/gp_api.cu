@@ -14,8 +14,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 struct gp_model {
@@ -167,7 +170,8 @@ int num_sms(int dev) {
 // The fused Gram step: A (M x M) = Phi^T Phi [+ diag(d)], b = Phi^T y.
 // X, y are device pointers.
 int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const double* yd,
-                const double* d, double* A, double* b, GpStatus* st, cudaStream_t stream) {
+                const double* d, double* A, double* b, GpStatus* st, cudaStream_t stream,
+                int target_ctas = 0) {
     Scratch sc(stream);
     int rc;
     if (prec == GP_PREC_FP64) {
@@ -178,7 +182,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         const int npairs = T * (T + 1) / 2;
         int nsplit;
         int64_t rps;
-        choose_splits(npairs, s.Npad, 4 * num_sms(dev), 128, &nsplit, &rps);
+        choose_splits(npairs, s.Npad, target_ctas > 0 ? target_ctas : 4 * num_sms(dev), 128, &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRK64_TM * SYRK64_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
         {
@@ -206,7 +210,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         const int npairs = T * (T + 1) / 2;
         int nsplit;
         int64_t rps;
-        choose_splits(npairs, s.Npad, num_sms(dev), GP_TAB_BLOCK, &nsplit, &rps);
+        choose_splits(npairs, s.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), GP_TAB_BLOCK, &nsplit, &rps);
         if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
@@ -266,6 +270,262 @@ int model_alloc(gp_model* h, size_t bytes, void** p, cudaStream_t s) {
     if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)bytes);
     if (e != cudaSuccess) return cuda_err(e);
     return GP_OK;
+}
+
+gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, double alpha, double sigma2) {
+    gp_model* h = new gp_model();
+    memset(h, 0, sizeof(*h));
+    h->device = dev;
+    h->prec = prec;
+    h->eps = eps;
+    h->alpha = alpha;
+    h->sigma2 = sigma2;
+    gp_fill_shape(&h->shape, N, p, n, eps, alpha, tile_of(prec));
+    return h;
+}
+
+// The model's own device buffers (kept until gp_free).
+int fit_alloc(gp_model* h, cudaStream_t stream) {
+    const int M = h->shape.M;
+    int rc;
+    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->L, stream))) return rc;
+    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->W, stream))) return rc;
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->c, stream))) return rc;
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->b, stream))) return rc;
+    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return rc;
+    if (h->prec != GP_PREC_FP64) {
+        if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return rc;
+        if ((rc = model_alloc(h, sizeof(int) * predtc_cinfo_ints(h->shape), (void**)&h->cinfo, stream)))
+            return rc;
+    }
+    return GP_OK;
+}
+
+// Host inputs of one fit that its asynchronous copies read: kept alive by
+// the caller until the stream (or graph) has run.
+struct FitStage {
+    std::vector<double> loglam;
+    std::vector<int> cinfo;
+};
+
+// Copy the shape-only inputs (log eigenvalues, and the predict chunk table
+// into the model) to the device.
+int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream) {
+    const GpShape& s = h->shape;
+    stage.loglam.resize(s.n);
+    log_eigenvalues(s.n, h->eps, h->alpha, stage.loglam.data());
+    cudaError_t e = cudaMemcpyAsync(loglam_d, stage.loglam.data(), sizeof(double) * s.n,
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && h->prec != GP_PREC_FP64) {
+        stage.cinfo.resize(predtc_cinfo_ints(s));
+        predtc_build_cinfo(s, stage.cinfo.data());
+        e = cudaMemcpyAsync(h->cinfo, stage.cinfo.data(), sizeof(int) * stage.cinfo.size(),
+                            cudaMemcpyHostToDevice, stream);
+    }
+    return e == cudaSuccess ? GP_OK : cuda_err(e);
+}
+
+// Every device step of one fit, enqueued on `stream` with no host
+// synchronisation (so that it can be captured into a graph). Inputs are
+// device pointers; scratch comes from `sc` (stream-ordered); errors found on
+// the device land in *st.
+int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
+                int gram_ctas, Scratch& sc, cudaStream_t stream) {
+    const GpShape& s = h->shape;
+    const int M = s.M;
+    const int prec = h->prec;
+    int rc;
+    double *A, *work;
+    if ((rc = sc.get(&A, (size_t)M * M))) return rc;
+    if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return rc;
+    const bool fp32_inverse = (prec != GP_PREC_FP64);
+    unsigned char* fwork;
+    if ((rc = sc.get(&fwork, factor_work_bytes(M, fp32_inverse)))) return rc;
+    launch_noise_diag(s, loglam_d, h->sigma2, h->d, stream);
+    gp_note_launches(1);
+    if ((rc = gram_device(s, prec, h->device, Xd, yd, h->d, A, h->b, st, stream, gram_ctas))) return rc;
+    cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
+    cudaError_t e;
+    {
+        GpProf pf("cholesky", stream);
+        e = launch_cholesky(h->L, M, st, fwork, stream);
+    }
+    if (e == cudaSuccess) {
+        GpProf pf("tri_inverse", stream);
+        e = launch_tri_inverse(h->L, h->W, M, fp32_inverse, st, fwork, stream);
+    }
+    if (e == cudaSuccess) {
+        GpProf pf("solve_refine", stream);
+        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st, stream);
+    }
+    if (e == cudaSuccess && prec != GP_PREC_FP64) {
+        GpProf pf("pack_w", stream);
+        launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
+        gp_note_launches(1);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? GP_OK : cuda_err(e);
+}
+
+// Every device step of one predict (tables of X*, then mean and variance),
+// enqueued on `stream` without host synchronisation. Device pointers only.
+int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md, double* vd, GpStatus* st,
+                    Scratch& sc, cudaStream_t stream) {
+    GpShape s = h->shape;
+    s.N = Ns;
+    s.Npad = gp_round_up(Ns, 128);
+    int rc;
+    cudaError_t e;
+    if (h->prec == GP_PREC_FP64) {
+        double *tab, *part;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&part, predict64_part_elems(s.Npad, s.M)))) return rc;
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
+        }
+        GpProf pf("predict64", stream);
+        e = launch_predict64(s, tab, h->W, h->c, h->sigma2, part, md, vd, stream);
+        gp_note_launches(3);
+    } else {
+        float* tab;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        {
+            GpProf pf("eig_tables", stream);
+            launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
+        }
+        GpProf pf("predict_tc", stream);
+        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->c, h->sigma2, md, vd, st, stream);
+        gp_note_launches(2);
+    }
+    return e == cudaSuccess ? GP_OK : cuda_err(e);
+}
+
+// ---------------------------------------------------------------- batches
+
+// Streams that run the problems of one batch side by side (created per call).
+struct StreamSet {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    explicit StreamSet(int k) {
+        st.resize(k);
+        ev.resize(k + 1);
+        for (int i = 0; i < k; ++i) cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+        for (int i = 0; i <= k; ++i) cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    }
+    ~StreamSet() {
+        for (cudaStream_t s : st) cudaStreamDestroy(s);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    // every stream waits for the work already on `origin`
+    void fork(cudaStream_t origin) {
+        cudaEventRecord(ev.back(), origin);
+        for (cudaStream_t s : st) cudaStreamWaitEvent(s, ev.back(), 0);
+    }
+    // `origin` waits for every stream
+    void join(cudaStream_t origin) {
+        for (size_t i = 0; i < st.size(); ++i) {
+            cudaEventRecord(ev[i], st[i]);
+            cudaStreamWaitEvent(origin, ev[i], 0);
+        }
+    }
+};
+
+// Gram CTA budget of problem i for the budget factor k: k waves of the GPU
+// shared out in proportion to each problem's contraction work.
+std::vector<int> gram_budgets(const std::vector<gp_model*>& hs, int k, int sms) {
+    std::vector<double> w(hs.size());
+    double tot = 0.0;
+    for (size_t i = 0; i < hs.size(); ++i) {
+        const GpShape& s = hs[i]->shape;
+        const int T = s.Mpad / tile_of(hs[i]->prec);
+        w[i] = (double)s.Npad * (double)(T * (T + 1) / 2);
+        tot += w[i];
+    }
+    std::vector<int> out(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) {
+        const double c = (double)k * sms * (tot > 0 ? w[i] / tot : 1.0);
+        out[i] = c < 1.0 ? 1 : (int)(c + 0.5);
+    }
+    return out;
+}
+
+// The autotuner: for each distinct batch (multiset of p, n, N rounded to a
+// power of two, precision) the Gram budget factor k in {1, 2, 4} is chosen
+// once by timing the batch's Gram steps under each value on the device; the
+// choice is cached for the process.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+thread_local int g_batch_graph = 0;
+thread_local int g_batch_k = 0;
+
+std::string batch_signature(const std::vector<gp_model*>& hs) {
+    std::vector<std::string> parts;
+    for (gp_model* h : hs) {
+        int lg = 0;
+        while ((int64_t)1 << (lg + 1) <= h->shape.N) ++lg;
+        char buf[64];
+        snprintf(buf, sizeof(buf), "%d.%d.%d.%d", h->shape.p, h->shape.n, lg, h->prec);
+        parts.push_back(buf);
+    }
+    std::sort(parts.begin(), parts.end());
+    std::string sig;
+    for (auto& x : parts) sig += x + ";";
+    return sig;
+}
+
+int tune_batch(const std::vector<gp_model*>& hs, const std::vector<const double*>& Xd,
+               const std::vector<const double*>& yd, GpStatus* sts, StreamSet& ss, cudaStream_t origin,
+               int sms) {
+    const std::string sig = batch_signature(hs);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(sig);
+        if (it != g_tune.end()) return it->second;
+    }
+    int best = 1;
+    float best_ms = 1e30f;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const int cand[3] = {1, 2, 4};
+    for (int k : cand) {
+        const std::vector<int> bud = gram_budgets(hs, k, sms);
+        cudaEventRecord(t0, origin);
+        ss.fork(origin);
+        int rc = GP_OK;
+        {
+            std::vector<Scratch*> scs;
+            for (size_t i = 0; i < hs.size() && rc == GP_OK; ++i) {
+                cudaStream_t s = ss.st[i % ss.st.size()];
+                Scratch* sc = new Scratch(s);
+                scs.push_back(sc);
+                const GpShape& sh = hs[i]->shape;
+                double *A, *b;
+                if ((rc = sc->get(&A, (size_t)sh.M * sh.M))) break;
+                if ((rc = sc->get(&b, (size_t)sh.M))) break;
+                rc = gram_device(sh, hs[i]->prec, hs[i]->device, Xd[i], yd[i], nullptr, A, b, &sts[i], s,
+                                 bud[i]);
+            }
+            for (Scratch* sc : scs) delete sc;
+        }
+        ss.join(origin);
+        cudaEventRecord(t1, origin);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (rc != GP_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaMemsetAsync(sts, 0, sizeof(GpStatus) * hs.size(), origin);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[sig] = best;
+    return best;
 }
 
 }  // namespace
@@ -377,18 +637,9 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if ((rc = check_device(&dev))) return rc;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    gp_model* h = new gp_model();
-    memset(h, 0, sizeof(*h));
-    h->device = dev;
-    h->prec = prec;
-    h->eps = eps;
-    h->alpha = alpha;
-    h->sigma2 = sigma2;
-    gp_fill_shape(&h->shape, N, p, n, eps, alpha, tile_of(prec));
-    const GpShape& s = h->shape;
-    const int M = s.M;
-
+    gp_model* h = new_model(dev, prec, N, p, n, eps, alpha, sigma2);
     Scratch sc(stream);
+    FitStage stage;
     auto fail = [&](int code) {
         int64_t det = g_detail;
         cudaStreamSynchronize(stream);
@@ -396,27 +647,12 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
         set_err(code, det);
         return code;
     };
-    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->L, stream))) return fail(rc);
-    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->W, stream))) return fail(rc);
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->c, stream))) return fail(rc);
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->b, stream))) return fail(rc);
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return fail(rc);
-    if (prec != GP_PREC_FP64) {
-        if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return fail(rc);
-        if ((rc = model_alloc(h, sizeof(int) * predtc_cinfo_ints(s), (void**)&h->cinfo, stream)))
-            return fail(rc);
-    }
+    if ((rc = fit_alloc(h, stream))) return fail(rc);
     GpStatus* st;
-    double *A, *loglam, *work;
+    double* loglam;
     if ((rc = sc.get(&st, 1))) return fail(rc);
-    if ((rc = sc.get(&A, (size_t)M * M))) return fail(rc);
     if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
-    if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return fail(rc);
-    const bool fp32_inverse = (prec != GP_PREC_FP64);
-    unsigned char* fwork;
-    if ((rc = sc.get(&fwork, factor_work_bytes(M, fp32_inverse)))) return fail(rc);
     cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
-
     const double *Xd = X, *yd = y;
     if (!dev_ptrs) {
         double *xx, *yy;
@@ -427,42 +663,9 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
         Xd = xx;
         yd = yy;
     }
-    std::vector<double> ll(n);
-    log_eigenvalues(n, eps, alpha, ll.data());
-    cudaMemcpyAsync(loglam, ll.data(), sizeof(double) * n, cudaMemcpyHostToDevice, stream);
-    launch_noise_diag(s, loglam, sigma2, h->d, stream);
-    gp_note_launches(1);
-
-    if ((rc = gram_device(s, prec, dev, Xd, yd, h->d, A, h->b, st, stream))) return fail(rc);
-    cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
-    cudaError_t e;
-    {
-        GpProf pf("cholesky", stream);
-        e = launch_cholesky(h->L, M, st, fwork, stream);
-    }
-    if (e == cudaSuccess) {
-        GpProf pf("tri_inverse", stream);
-        e = launch_tri_inverse(h->L, h->W, M, fp32_inverse, st, fwork, stream);
-    }
-    if (e == cudaSuccess) {
-        GpProf pf("solve_refine", stream);
-        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st, stream);
-    }
-    if (e == cudaSuccess && prec != GP_PREC_FP64) {
-        GpProf pf("pack_w", stream);
-        launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
-        gp_note_launches(1);
-        e = cudaGetLastError();
-    }
-    std::vector<int> cinfo_host;
-    if (e == cudaSuccess && prec != GP_PREC_FP64) {
-        cinfo_host.resize(predtc_cinfo_ints(s));
-        predtc_build_cinfo(s, cinfo_host.data());
-        // the host vector lives until the status read below synchronises the stream
-        e = cudaMemcpyAsync(h->cinfo, cinfo_host.data(), sizeof(int) * cinfo_host.size(),
-                            cudaMemcpyHostToDevice, stream);
-    }
-    if (e != cudaSuccess) return fail(cuda_err(e));
+    if ((rc = fit_stage(h, stage, loglam, stream))) return fail(rc);
+    if ((rc = fit_compute(h, Xd, yd, loglam, st, 0, sc, stream))) return fail(rc);
+    // the staged host vectors live until this read synchronises the stream
     if ((rc = read_status(st, stream))) return fail(rc);
     *out = h;
     return GP_OK;
@@ -485,9 +688,6 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, do
     if ((rc = check_device(&dev))) return rc;
     if (dev != h->device) return set_err(GP_EINVAL, 5);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
-    GpShape s = h->shape;
-    s.N = Ns;
-    s.Npad = gp_round_up(Ns, 128);
     Scratch sc(stream);
     GpStatus* st;
     if ((rc = sc.get(&st, 1))) return rc;
@@ -496,36 +696,13 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, do
     double *md = mean, *vd = var;
     if (!dev_ptrs) {
         double* xx;
-        if ((rc = sc.get(&xx, (size_t)Ns * s.p))) return rc;
+        if ((rc = sc.get(&xx, (size_t)Ns * h->shape.p))) return rc;
         if ((rc = sc.get(&md, (size_t)Ns))) return rc;
         if (var && (rc = sc.get(&vd, (size_t)Ns))) return rc;
-        cudaMemcpyAsync(xx, Xs, sizeof(double) * Ns * s.p, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(xx, Xs, sizeof(double) * Ns * h->shape.p, cudaMemcpyHostToDevice, stream);
         Xd = xx;
     }
-    cudaError_t e;
-    if (h->prec == GP_PREC_FP64) {
-        double *tab, *part;
-        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
-        if ((rc = sc.get(&part, predict64_part_elems(s.Npad, s.M)))) return rc;
-        {
-            GpProf pf("eig_tables", stream);
-            launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
-        }
-        GpProf pf("predict64", stream);
-        e = launch_predict64(s, tab, h->W, h->c, h->sigma2, part, md, vd, stream);
-        gp_note_launches(3);
-    } else {
-        float* tab;
-        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
-        {
-            GpProf pf("eig_tables", stream);
-            launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
-        }
-        GpProf pf("predict_tc", stream);
-        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->c, h->sigma2, md, vd, st, stream);
-        gp_note_launches(2);
-    }
-    if (e != cudaSuccess) return cuda_err(e);
+    if ((rc = predict_compute(h, Xd, Ns, md, vd, st, sc, stream))) return rc;
     if (!dev_ptrs) {
         cudaMemcpyAsync(mean, md, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
         if (var) cudaMemcpyAsync(var, vd, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
@@ -573,30 +750,187 @@ GPFAGP_API int gp_model_read(const gp_model* h, int field, double* dst) {
 GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* cuda_stream,
                             int dev_ptrs, gp_model** out) {
     set_err(GP_OK);
+    g_batch_graph = 0;
+    g_batch_k = 0;
+    int rc, dev;
     if (count < 0 || (count > 0 && (!args || !out))) return set_err(GP_EINVAL, 0);
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    if (count == 0) return GP_OK;
+    if ((rc = check_prec(prec))) return rc;
+    for (int i = 0; i < count; ++i) {
+        const gp_fit_args& a = args[i];
+        if (!a.X || !a.y) return set_err(GP_EINVAL, i);
+        if (check_hyper(a.N, a.p, a.n, a.eps, a.alpha, a.sigma2)) return set_err(GP_EINVAL, i);
+    }
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t origin = (cudaStream_t)cuda_stream;
+    const int sms = num_sms(dev);
+
+    // models, inputs on the device, shape-only inputs: all before any capture
+    std::vector<gp_model*> hs(count, nullptr);
+    std::vector<FitStage> stages(count);
+    std::vector<const double*> Xd(count), yd(count);
+    Scratch keep(origin);  // inputs and statuses, freed after the batch has run
+    GpStatus* sts = nullptr;
+    auto fail_all = [&](int code, int idx) {
+        int64_t det = g_detail;
+        cudaStreamSynchronize(origin);
+        for (gp_model* h : hs) free_model(h);
+        set_err(code, idx >= 0 ? idx : det);
+        return code;
+    };
+    if ((rc = keep.get(&sts, (size_t)count))) return fail_all(rc, -1);
+    cudaMemsetAsync(sts, 0, sizeof(GpStatus) * count, origin);
+    std::vector<double*> loglam(count);
+    for (int i = 0; i < count; ++i) {
+        const gp_fit_args& a = args[i];
+        hs[i] = new_model(dev, prec, a.N, a.p, a.n, a.eps, a.alpha, a.sigma2);
+        if ((rc = fit_alloc(hs[i], origin))) return fail_all(rc, i);
+        if ((rc = keep.get(&loglam[i], (size_t)a.n))) return fail_all(rc, i);
+        if ((rc = fit_stage(hs[i], stages[i], loglam[i], origin))) return fail_all(rc, i);
+        Xd[i] = a.X;
+        yd[i] = a.y;
+        if (!dev_ptrs) {
+            double *xx, *yy;
+            if ((rc = keep.get(&xx, (size_t)a.N * a.p))) return fail_all(rc, i);
+            if ((rc = keep.get(&yy, (size_t)a.N))) return fail_all(rc, i);
+            cudaMemcpyAsync(xx, a.X, sizeof(double) * a.N * a.p, cudaMemcpyHostToDevice, origin);
+            cudaMemcpyAsync(yy, a.y, sizeof(double) * a.N, cudaMemcpyHostToDevice, origin);
+            Xd[i] = xx;
+            yd[i] = yy;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(origin);  // staged host inputs have been read
+    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
+
+    StreamSet ss(count < 8 ? count : 8);
+    const int k = tune_batch(hs, Xd, yd, sts, ss, origin, sms);
+    g_batch_k = k;
+    const std::vector<int> bud = gram_budgets(hs, k, sms);
+
+    // enqueue every problem's fit, problem i on stream i mod S
+    auto enqueue_all = [&]() -> int {
+        ss.fork(origin);
+        int first = GP_OK;
+        std::vector<Scratch*> scs;
+        for (int i = 0; i < count && first == GP_OK; ++i) {
+            cudaStream_t s = ss.st[i % ss.st.size()];
+            Scratch* sc = new Scratch(s);
+            scs.push_back(sc);
+            first = fit_compute(hs[i], Xd[i], yd[i], loglam[i], &sts[i], bud[i], *sc, s);
+        }
+        for (Scratch* sc : scs) delete sc;  // scratch frees are stream-ordered
+        ss.join(origin);
+        return first;
+    };
+
+    // One graph for the whole batch; if capturing or instantiating it is
+    // refused, the same launches run directly on the streams.
+    const int prof = gp_prof_suspend();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ran = false;
+    if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const int erc = enqueue_all();
+        const cudaError_t ce = cudaStreamEndCapture(origin, &graph);
+        if (erc == GP_OK && ce == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess &&
+            cudaGraphLaunch(exec, origin) == cudaSuccess) {
+            ran = true;
+            g_batch_graph = 1;
+        }
+        if (!ran) {
+            (void)cudaGetLastError();
+            set_err(GP_OK);
+        }
+    } else {
+        (void)cudaGetLastError();
+    }
+    if (!ran) {
+        rc = enqueue_all();
+        if (rc != GP_OK) {
+            gp_prof_resume(prof);
+            return fail_all(rc, -1);
+        }
+    }
+    e = cudaStreamSynchronize(origin);
+    gp_prof_resume(prof);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
+
+    std::vector<GpStatus> hst(count);
+    e = cudaMemcpy(hst.data(), sts, sizeof(GpStatus) * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
     int first = GP_OK;
     int64_t first_idx = 0;
     for (int i = 0; i < count; ++i) {
-        const gp_fit_args& a = args[i];
-        int rc = gp_fit_ex(a.X, a.y, a.N, a.p, a.n, a.eps, a.alpha, a.sigma2, prec, cuda_stream,
-                           dev_ptrs, &out[i]);
-        if (rc != GP_OK && first == GP_OK) {
-            first = rc;
-            first_idx = i;
+        if (hst[i].code != GP_OK) {
+            if (first == GP_OK) {
+                first = hst[i].code;
+                first_idx = i;
+            }
+            free_model(hs[i]);
+            hs[i] = nullptr;
         }
+        out[i] = hs[i];
     }
     if (first != GP_OK) return set_err(first, first_idx);
+    return GP_OK;
+}
+
+GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k) {
+    if (used_graph) *used_graph = g_batch_graph;
+    if (tuned_k) *tuned_k = g_batch_k;
     return GP_OK;
 }
 
 GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream) {
     set_err(GP_OK);
     if (count < 0 || (count > 0 && !args)) return set_err(GP_EINVAL, 0);
+    if (count == 0) return GP_OK;
+    int rc, dev;
     for (int i = 0; i < count; ++i) {
         const gp_predict_args& a = args[i];
-        int rc = gp_predict_ex(a.model, a.Xs, a.Ns, a.mean, a.var, cuda_stream, 1);
-        if (rc != GP_OK) return set_err(rc, i);
+        if (!a.model || a.Ns < 0 || (a.Ns > 0 && (!a.Xs || !a.mean))) return set_err(GP_EINVAL, i);
     }
+    if ((rc = check_device(&dev))) return rc;
+    for (int i = 0; i < count; ++i)
+        if (args[i].model->device != dev) return set_err(GP_EINVAL, i);
+    cudaStream_t origin = (cudaStream_t)cuda_stream;
+    Scratch keep(origin);
+    GpStatus* sts;
+    if ((rc = keep.get(&sts, (size_t)count))) return rc;
+    cudaMemsetAsync(sts, 0, sizeof(GpStatus) * count, origin);
+    StreamSet ss(count < 8 ? count : 8);
+    ss.fork(origin);
+    int first = GP_OK;
+    int64_t first_idx = 0;
+    {
+        std::vector<Scratch*> scs;
+        for (int i = 0; i < count; ++i) {
+            const gp_predict_args& a = args[i];
+            if (a.Ns == 0) continue;
+            cudaStream_t s = ss.st[i % ss.st.size()];
+            Scratch* sc = new Scratch(s);
+            scs.push_back(sc);
+            rc = predict_compute(a.model, a.Xs, a.Ns, a.mean, a.var, &sts[i], *sc, s);
+            if (rc != GP_OK && first == GP_OK) {
+                first = rc;
+                first_idx = i;
+            }
+        }
+        for (Scratch* sc : scs) delete sc;
+    }
+    ss.join(origin);
+    cudaError_t e = cudaStreamSynchronize(origin);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (first != GP_OK) return set_err(first, first_idx);
+    std::vector<GpStatus> hst(count);
+    e = cudaMemcpy(hst.data(), sts, sizeof(GpStatus) * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e);
+    for (int i = 0; i < count; ++i)
+        if (hst[i].code != GP_OK) return set_err(hst[i].code, i);
     return GP_OK;
 }
 

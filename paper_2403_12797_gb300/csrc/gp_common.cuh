@@ -128,6 +128,8 @@ int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha,
 void gp_note_launches(int n);
 void gp_prof_begin(const char* name, cudaStream_t s);
 void gp_prof_end(const char* name, cudaStream_t s);
+int gp_prof_suspend();
+void gp_prof_resume(int state);
 
 // RAII bracket of one kernel group on a stream
 struct GpProf {

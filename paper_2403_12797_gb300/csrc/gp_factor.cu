@@ -723,12 +723,24 @@ size_t factor_work_bytes(int M, bool fp32_inverse) {
     return CHOL_RSD_OFFSET + (inv > chol ? inv : chol);
 }
 
+// CTAs for the Cholesky of an M x M matrix: about two trailing-update tiles
+// per CTA in the first step (one CTA when there is none), at most one per SM,
+// so that small problems -- e.g. the many problems of a batch running side by
+// side -- do not claim the whole GPU.
+int chol_grid(int M, int dev) {
+    if (M <= CB) return 1;
+    const int T = (M - CB + UT - 1) / UT;
+    const int want = (T * (T + 1) / 2 + 1) / 2;
+    const int g = coop_grid((const void*)chol_coop_kernel, dev);
+    return want < 2 ? 2 : (want > g ? g : want);
+}
+
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
     CholWork* cw = (CholWork*)work;
     cudaMemsetAsync(cw, 0, CHOL_RSD_OFFSET, stream);
-    dim3 grid((unsigned)coop_grid((const void*)chol_coop_kernel, dev)), block(NT);
+    dim3 grid((unsigned)chol_grid(M, dev)), block(NT);
     void* args[] = {&L, &M, &st, &cw};
     gp_note_launches(1);
     return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, grid, block, args, 0, stream);
@@ -750,9 +762,8 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int sms = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        dim3 grid((unsigned)sms), block(NT);
+        dim3 grid((unsigned)((int)nb < sms ? (int)nb : sms)), block(NT);  // one CTA per strip
         void* args[] = {(void*)&L, &W, &M, &D, &st, &gb};
-        (void)nb;
         return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
     }
     if (fp32) {

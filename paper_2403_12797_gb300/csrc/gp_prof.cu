@@ -58,6 +58,11 @@ void drain_locked() {
 
 void gp_note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Switch the group timing off (returning its previous state) and back on:
+// work that is captured into a graph is not timed.
+int gp_prof_suspend() { return g_prof_on.exchange(0); }
+void gp_prof_resume(int state) { g_prof_on.store(state); }
+
 void gp_prof_begin(const char* name, cudaStream_t s) {
     if (!g_prof_on.load()) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);

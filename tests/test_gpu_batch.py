@@ -1,0 +1,97 @@
+"""Batched fit (one captured graph, autotuned Gram budgets) and batched predict.
+
+The batch is a small instance of the uneven-shape batched workload (p in
+1..4, M <= 256, N log-uniform up to 20,000). Every batched model is checked
+against the FP64 oracle with the precision mode's tolerances, batched
+predicts against single predicts bitwise, and a failing member against its
+index.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fagp as O
+from paper_2403_12797_gb300 import _lib
+from paper_2403_12797_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(mean=1e-10, var=1e-10), "mixed": dict(mean=1e-4, var=1e-3)}
+
+
+def _batch(count=16, seed_offset=0):
+    return W.workload4(count=count, Ns=300, N_hi=20_000, M_max=256, seed_offset=seed_offset)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_fit_batch_matches_oracle(prec):
+    probs = _batch()
+    models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs], prec=prec)
+    used_graph, k = _lib.batch_info()
+    assert k in (1, 2, 4)
+    assert used_graph in (0, 1)
+    try:
+        for pr, m in zip(probs, models):
+            assert m is not None
+            mean, var = m.predict(pr.Xs)
+            mdl = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+            mo, vo = O.predict(mdl, pr.Xs)
+            assert O.relerr(mean, mo) < TOL[prec]["mean"], (pr.name, O.relerr(mean, mo))
+            assert O.relerr(var, vo) < TOL[prec]["var"], (pr.name, O.relerr(var, vo))
+    finally:
+        for m in models:
+            m.free()
+
+
+def test_fit_batch_agrees_with_single_fits():
+    probs = _batch(count=6, seed_offset=7)
+    models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs], prec="fp64")
+    try:
+        for pr, m in zip(probs, models):
+            s = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="fp64")
+            try:
+                # same arithmetic up to the order of the Gram's split sums
+                assert O.relerr(m.read("L"), s.read("L")) < 1e-12
+                assert O.relerr(m.read("c"), s.read("c")) < 1e-9
+            finally:
+                s.free()
+    finally:
+        for m in models:
+            m.free()
+
+
+def test_fit_batch_reports_failing_member():
+    probs = _batch(count=5, seed_offset=3)
+    bad = 2
+    ys = [pr.y.copy() for pr in probs]
+    ys[bad][7] = np.nan
+    with pytest.raises(_lib.GPError) as ei:
+        _lib.fit_batch([(pr.X, y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr, y in zip(probs, ys)])
+    assert ei.value.status == _lib.GP_EINVAL
+    assert ei.value.detail == bad
+
+
+def test_predict_batch_bitwise_equals_single():
+    probs = _batch(count=3, seed_offset=11)
+    dev = torch.device("cuda", 0)
+    for prec in ("mixed", "fp64"):
+        models = [_lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec) for pr in probs]
+        try:
+            reqs, singles = [], []
+            rng = np.random.default_rng(5)
+            for r in range(9):
+                m, pr = models[r % 3], probs[r % 3]
+                ns = int(rng.choice([1, 17, 129, 300]))
+                Xs = torch.from_numpy(pr.Xs[:ns].copy()).to(dev)
+                mo = torch.empty(ns, dtype=torch.float64, device=dev)
+                vo = torch.empty(ns, dtype=torch.float64, device=dev)
+                reqs.append((m, Xs, mo, vo))
+                singles.append(m.predict(pr.Xs[:ns]))
+            _lib.predict_batch(reqs)
+            torch.cuda.synchronize()
+            for (m, Xs, mo, vo), (ms, vs) in zip(reqs, singles):
+                np.testing.assert_array_equal(mo.cpu().numpy(), ms)
+                np.testing.assert_array_equal(vo.cpu().numpy(), vs)
+        finally:
+            for m in models:
+                m.free()
