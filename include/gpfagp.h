@@ -225,6 +225,58 @@ typedef struct gp_predict_args {
  * failing request's status (detail = its index). */
 GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream);
 
+/* ---- request server (continuous batching over resident models) ----------- */
+
+/* A server keeps fitted models resident on the device and runs predict and
+ * refit requests on `slots` CUDA streams from a worker thread. Requests queue
+ * in arrival order; the queue head is admitted as soon as a slot is free and
+ * its scratch-memory estimate fits under the budget (always, when nothing is
+ * running), so requests that arrive while others run start as room frees up
+ * and the admitted ones overlap on the device. Every request runs exactly the
+ * kernels of gp_predict_ex / gp_fit_ex with the same launch plans, so its
+ * result does not depend on the mix it ran in. Host buffers are staged
+ * through pinned memory; the caller keeps them alive until gp_server_wait
+ * has returned for the request. A refit fits a new model on the resident
+ * model's p, n, eps, alpha, sigma2 and precision and swaps it in at
+ * completion; predicts admitted before the swap finish on the old model,
+ * which is freed after them. gp_server_add_model hands the model to the
+ * server: the caller must not free it; gp_server_destroy frees every model
+ * the server holds. gp_server_model returns the model currently serving an
+ * id (valid until the next refit of that id completes or the server is
+ * destroyed). */
+typedef struct gp_server gp_server;
+
+typedef struct gp_server_report {
+    int64_t predicts_done;  /* finished predict requests (GP_OK)            */
+    int64_t refits_done;    /* finished refits                              */
+    int64_t points;         /* test points of the finished predicts         */
+    double p50_ms, p99_ms, max_ms;  /* predict latency, submit to results   */
+    double wall_s;          /* first submit to last completion              */
+    double points_per_s;    /* points / wall_s                              */
+    int peak_inflight;      /* most requests running at once               */
+} gp_server_report;
+
+/* slots: 1..64 concurrent requests; mem_budget_bytes: scratch budget
+ * (<= 0: half the free device memory at creation). */
+GPFAGP_API int gp_server_create(int slots, int64_t mem_budget_bytes, gp_server** out);
+/* Register (and hand over) a fitted model; *model_id identifies it in requests. */
+GPFAGP_API int gp_server_add_model(gp_server* s, gp_model* m, int* model_id);
+/* The model currently serving model_id (changes when a refit completes). */
+GPFAGP_API gp_model* gp_server_model(gp_server* s, int model_id);
+/* Queue a predict of Ns >= 1 host rows Xs (Ns x p); mean (and var, or NULL)
+ * are host outputs of Ns doubles, written before gp_server_wait returns. */
+GPFAGP_API int gp_server_submit_predict(gp_server* s, int model_id, const double* Xs, int64_t Ns,
+                                        double* mean, double* var, int64_t* req_id);
+/* Queue a refit of model_id on N host rows X (N x p), y (N). */
+GPFAGP_API int gp_server_submit_refit(gp_server* s, int model_id, const double* X, const double* y,
+                                      int64_t N, int64_t* req_id);
+/* Wait for a request (timeout_s <= 0: no limit); returns its status
+ * (GP_ETIMEOUT if the limit passed first; the request stays queued). */
+GPFAGP_API int gp_server_wait(gp_server* s, int64_t req_id, double timeout_s);
+GPFAGP_API int gp_server_stats(gp_server* s, gp_server_report* out);
+/* Finish every queued request, then stop the worker and release the streams. */
+GPFAGP_API void gp_server_destroy(gp_server* s);
+
 /* ---- test hooks ----------------------------------------------------------- */
 
 /* Make the k-th device allocation from now fail with GP_ENOMEM (k >= 1);

@@ -33,6 +33,12 @@ class GPError(RuntimeError):
         super().__init__(f"{where}: {strerror(status)} (status {status}, detail {detail})")
 
 
+class ServerReport(C.Structure):
+    _fields_ = [("predicts_done", C.c_int64), ("refits_done", C.c_int64), ("points", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("wall_s", C.c_double), ("points_per_s", C.c_double), ("peak_inflight", C.c_int)]
+
+
 class FitArgs(C.Structure):
     _fields_ = [("X", C.c_void_p), ("y", C.c_void_p), ("N", C.c_int64), ("p", C.c_int),
                 ("n", C.c_int), ("eps", C.c_double), ("alpha", C.c_double), ("sigma2", C.c_double)]
@@ -76,6 +82,14 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
         "gp_batch_info": (i, [C.POINTER(i), C.POINTER(i)]),
+        "gp_server_create": (i, [i, i64, C.POINTER(vp)]),
+        "gp_server_add_model": (i, [vp, vp, C.POINTER(i)]),
+        "gp_server_model": (vp, [vp, i]),
+        "gp_server_submit_predict": (i, [vp, i, vp, i64, vp, vp, C.POINTER(i64)]),
+        "gp_server_submit_refit": (i, [vp, i, vp, vp, i64, C.POINTER(i64)]),
+        "gp_server_wait": (i, [vp, i64, d]),
+        "gp_server_stats": (i, [vp, C.POINTER(ServerReport)]),
+        "gp_server_destroy": (None, [vp]),
         "gp_debug_fail_alloc_after": (None, [i]),
         "gp_version": (C.c_char_p, []),
     }
@@ -183,6 +197,12 @@ class Model:
         _check(lib().gp_model_read(self._h, FIELD[field], out.ctypes.data), "gp_model_read")
         return out
 
+    def disown(self) -> int:
+        """Give up the handle without freeing it (its new owner frees it)."""
+        h = self.handle
+        self._h = C.c_void_p(0)
+        return h
+
     def free(self):
         if self._h is not None and self._h.value:
             lib().gp_free(self._h)
@@ -284,3 +304,74 @@ def debug_fail_alloc_after(k: int):
 
 def version() -> str:
     return lib().gp_version().decode()
+
+
+# ------------------------------------------------------------------ request server
+
+class Server:
+    """Resident models behind a request server (gp_server_* in the C ABI).
+
+    ``add_model`` hands a fitted Model to the server (the Model object is
+    emptied); ``submit_predict`` / ``submit_refit`` return a ticket for
+    ``wait``. Inputs are host (numpy) arrays kept alive by the ticket.
+    """
+
+    def __init__(self, slots: int = 8, mem_budget: int = 0):
+        h = C.c_void_p()
+        _check(lib().gp_server_create(int(slots), int(mem_budget), C.byref(h)), "gp_server_create")
+        self.handle = h.value
+        self._p = {}
+
+    def add_model(self, model: "Model") -> int:
+        mid = C.c_int()
+        _check(lib().gp_server_add_model(self.handle, C.c_void_p(model.handle), C.byref(mid)),
+               "gp_server_add_model")
+        self._p[mid.value] = model.p
+        model.disown()  # the server frees it
+        return mid.value
+
+    def submit_predict(self, model_id: int, Xs, var: bool = True):
+        Xs = np.ascontiguousarray(np.asarray(Xs, dtype=np.float64))
+        if Xs.ndim == 1:
+            Xs = Xs[:, None]
+        ns = Xs.shape[0]
+        mean = np.empty(ns)
+        v = np.empty(ns) if var else None
+        rid = C.c_int64()
+        _check(lib().gp_server_submit_predict(self.handle, int(model_id), Xs.ctypes.data, ns, mean.ctypes.data,
+                                              v.ctypes.data if v is not None else None, C.byref(rid)),
+               "gp_server_submit_predict")
+        return {"id": rid.value, "kind": "predict", "keep": (Xs,), "out": (mean, v)}
+
+    def submit_refit(self, model_id: int, X, y):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+        if X.ndim == 1:
+            X = X[:, None]
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        rid = C.c_int64()
+        _check(lib().gp_server_submit_refit(self.handle, int(model_id), X.ctypes.data, y.ctypes.data,
+                                            X.shape[0], C.byref(rid)), "gp_server_submit_refit")
+        return {"id": rid.value, "kind": "refit", "keep": (X, y), "out": None}
+
+    def wait(self, ticket, timeout: float = 0.0):
+        _check(lib().gp_server_wait(self.handle, ticket["id"], float(timeout)), "gp_server_wait")
+        return ticket["out"]
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(lib().gp_server_stats(self.handle, C.byref(r)), "gp_server_stats")
+        return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def model_handle(self, model_id: int):
+        return lib().gp_server_model(self.handle, int(model_id))
+
+    def close(self):
+        if self.handle:
+            lib().gp_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -7,7 +7,7 @@
 //   -> A = L L^T -> W = L^{-1} -> c = A^{-1} b with float64 refinement
 // predict (Eq. 11-12, diagonal): tables of X* -> fused Phi_* generation,
 //   mean = Phi_* c, var = sigma^2 rowsum((Phi_* W^T)^2).
-#include "gp_kernels.cuh"
+#include "gp_internal.cuh"
 
 #include <math.h>
 #include <stdio.h>
@@ -21,21 +21,8 @@
 #include <string>
 #include <vector>
 
-struct gp_model {
-    int device;
-    int prec;
-    GpShape shape;          // N / Npad of the training set (informational)
-    double eps, alpha, sigma2;
-    double* L;              // M x M lower Cholesky factor of A
-    double* W;              // M x M, L^{-1}
-    double* c;              // M, A^{-1} b
-    double* b;              // M, Phi^T y
-    double* d;              // M, sigma^2 / lambda_m (clamped)
-    uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
-    int* cinfo;             // chunk table of the tensor-core predict (GP_PREC_MIXED only)
-};
 
-namespace {
+namespace gpi {
 
 thread_local int g_err = GP_OK;
 thread_local int64_t g_detail = 0;
@@ -43,7 +30,7 @@ std::atomic<int> g_fail_after{0};
 std::mutex g_pool_mu;
 std::vector<int> g_pool_ready;
 
-int set_err(int code, int64_t detail = 0) {
+int set_err(int code, int64_t detail) {
     g_err = code;
     g_detail = detail;
     return code;
@@ -80,26 +67,6 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     return cudaMallocAsync(p, bytes, s);
 }
 
-// Frees every registered pointer on the stream when it goes out of scope.
-struct Scratch {
-    cudaStream_t s;
-    std::vector<void*> ptrs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    ~Scratch() {
-        for (void* p : ptrs)
-            if (p) cudaFreeAsync(p, s);
-    }
-    template <typename T>
-    int get(T** p, size_t count) {
-        void* v = nullptr;
-        cudaError_t e = dev_alloc(&v, count * sizeof(T), s);
-        if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)(count * sizeof(T)));
-        if (e != cudaSuccess) return cuda_err(e);
-        ptrs.push_back(v);
-        *p = (T*)v;
-        return GP_OK;
-    }
-};
 
 int check_device(int* dev_out) {
     int dev = 0;
@@ -301,12 +268,6 @@ int fit_alloc(gp_model* h, cudaStream_t stream) {
     return GP_OK;
 }
 
-// Host inputs of one fit that its asynchronous copies read: kept alive by
-// the caller until the stream (or graph) has run.
-struct FitStage {
-    std::vector<double> loglam;
-    std::vector<int> cinfo;
-};
 
 // Copy the shape-only inputs (log eigenvalues, and the predict chunk table
 // into the model) to the device.
@@ -528,7 +489,9 @@ int tune_batch(const std::vector<gp_model*>& hs, const std::vector<const double*
     return best;
 }
 
-}  // namespace
+}  // namespace gpi
+
+using namespace gpi;
 
 int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile) {
     memset(s, 0, sizeof(*s));

@@ -1,0 +1,77 @@
+// gp_internal.cuh -- library-internal interface shared by the C ABI
+// (gp_api.cu) and the request server (gp_server.cu): the model record,
+// stream-ordered scratch memory, and the enqueue-only fit and predict steps.
+#pragma once
+
+#include "gp_kernels.cuh"
+
+#include <vector>
+
+struct gp_model {
+    int device;
+    int prec;
+    GpShape shape;          // N / Npad of the training set (informational)
+    double eps, alpha, sigma2;
+    double* L;              // M x M lower Cholesky factor of A
+    double* W;              // M x M, L^{-1}
+    double* c;              // M, A^{-1} b
+    double* b;              // M, Phi^T y
+    double* d;              // M, sigma^2 / lambda_m (clamped)
+    uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
+    int* cinfo;             // chunk table of the tensor-core predict (GP_PREC_MIXED only)
+};
+
+namespace gpi {
+
+// thread-local status of the last ABI call (gp_last_error / _detail)
+int set_err(int code, int64_t detail = 0);
+int cuda_err(cudaError_t e);
+// stream-ordered allocation (honours gp_debug_fail_alloc_after)
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+
+// Frees every registered pointer on the stream when it goes out of scope.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void* p : ptrs)
+            if (p) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    int get(T** p, size_t count) {
+        void* v = nullptr;
+        cudaError_t e = dev_alloc(&v, count * sizeof(T), s);
+        if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)(count * sizeof(T)));
+        if (e != cudaSuccess) return cuda_err(e);
+        ptrs.push_back(v);
+        *p = (T*)v;
+        return GP_OK;
+    }
+};
+
+int check_device(int* dev_out);
+int num_sms(int dev);
+int tile_of(int prec);
+void free_model(gp_model* h);
+
+gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, double alpha, double sigma2);
+// the model's own device buffers
+int fit_alloc(gp_model* h, cudaStream_t stream);
+
+// Host inputs of one fit that its asynchronous copies read: kept alive by
+// the caller until the stream (or graph) has run.
+struct FitStage {
+    std::vector<double> loglam;
+    std::vector<int> cinfo;
+};
+
+// shape-only inputs to the device (log eigenvalues; predict chunk table into the model)
+int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream);
+// every device step of a fit / of a predict, enqueued without host synchronisation
+int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
+                int gram_ctas, Scratch& sc, cudaStream_t stream);
+int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md, double* vd, GpStatus* st,
+                    Scratch& sc, cudaStream_t stream);
+
+}  // namespace gpi
