@@ -295,6 +295,9 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         extra = compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np)
         out.update(extra)
+        if not args.no_extras:
+            out["batched_fit"] = batched_fit_bench(_lib, torch, dev)
+            out["serving"] = serving_bench(_lib, torch, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -370,6 +373,92 @@ def compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np):
     return res
 
 
+def batched_fit_bench(_lib, torch, dev):
+    """The batched-fit workload: 256 independent GPs of uneven shape fitted by
+    one gp_fit_batch (inputs resident on the device), against the same fits
+    one after another."""
+    from paper_2403_12797_gb300 import workloads as W
+    probs = W.workload4(count=256, Ns=1)
+    items = [(torch.from_numpy(pr.X).to(dev), torch.from_numpy(pr.y).to(dev), pr.n, pr.eps, pr.alpha,
+              pr.sigma2) for pr in probs]
+    points = sum(pr.X.shape[0] for pr in probs)
+    for m in _lib.fit_batch(items):  # tunes the plan for this batch, warms the pool
+        m.free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    models = _lib.fit_batch(items)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    graph, k = _lib.batch_info()
+    for m in models:
+        m.free()
+    t0 = time.perf_counter()
+    for it in items:
+        _lib.fit(*it).free()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    return {"workload": "256 GPs: N log-uniform [1e3, 2e5], p in {1,2,3,4}, M = n^p <= 1024, "
+                        "mixed precision, inputs on the device",
+            "points": points, "ms": t_batch * 1e3, "points_per_s": points / t_batch,
+            "sequential_ms": t_seq * 1e3, "sequential_points_per_s": points / t_seq,
+            "speedup": t_seq / t_batch, "one_graph": bool(graph), "tuned_k": k}
+
+
+def serving_bench(_lib, torch, dev):
+    """The serving workload: 64 resident models (p in {2,3,4}, M <= 2048, N up
+    to 5e5, fitted by one batched fit); a closed-loop burst gives the
+    saturating request rate, then open-loop Poisson streams at 50 % and 80 %
+    of it (predict sizes log-uniform on [1, 65536], 5 % refits with N
+    log-uniform on [1e4, 5e5]) give p50/p99 latency and throughput."""
+    from paper_2403_12797_gb300 import workloads as W
+    mods = W.workload5_models(count=64)
+    models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in mods])
+    n_esc = sum(1 for m in models if m.gram_fp64)
+    out = {"workload": "64 resident models: p in {2,3,4}, M <= 2048, N log-uniform [1e4, 5e5]; "
+                       "predict sizes log-uniform [1, 65536], 5 % refits (N log-uniform [1e4, 5e5])",
+           "models_fit_points": sum(pr.X.shape[0] for pr in mods),
+           "models_gram_fp64": n_esc}
+    with _lib.Server(slots=8) as srv:
+        ids = [srv.add_model(m) for m in models]
+        # closed loop: a burst of the same request mix (5 % refits) submitted at once
+        burst = W.workload5_stream(mods, 200, 1e9, refit_frac=0.05, seed=1)
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        tk = [srv.submit_refit(ids[r.model], r.refit.X, r.refit.y) if r.kind == "refit"
+              else srv.submit_predict(ids[r.model], r.Xs) for r in burst]
+        for t in tk:
+            srv.wait(t, timeout=600.0)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        sat_rate = len(burst) / wall
+        out["saturation"] = {"requests_per_s": sat_rate, "points_per_s": st["points_per_s"],
+                             "refits": st["refits_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                             "peak_inflight": st["peak_inflight"]}
+        out["refits_gram_fp64"] = sum(1 for i in ids if _lib.lib().gp_model_flags(srv.model_handle(i)) & 1)
+        for frac in (0.5, 0.8):
+            rate = frac * sat_rate
+            stream = W.workload5_stream(mods, max(20, int(rate * 3.0)), rate, refit_frac=0.05, seed=2)
+            srv.reset_stats()
+            t0 = time.perf_counter()
+            tk = []
+            for r in stream:
+                delay = r.t_arrive - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                if r.kind == "refit":
+                    tk.append(srv.submit_refit(ids[r.model], r.refit.X, r.refit.y))
+                else:
+                    tk.append(srv.submit_predict(ids[r.model], r.Xs))
+            for t in tk:
+                srv.wait(t, timeout=600.0)
+            st = srv.stats()
+            out[f"load_{int(frac * 100)}"] = {
+                "offered_requests_per_s": rate, "requests": len(stream),
+                "refits": st["refits_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "points_per_s": st["points_per_s"], "peak_inflight": st["peak_inflight"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,6 +467,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--quick", action="store_true", help="skip the comparisons (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-fit and serving measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.quick else args.warmup
     if args.impl == "reference":

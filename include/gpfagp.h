@@ -105,6 +105,9 @@ GPFAGP_API void gp_free(gp_model* h);
 
 GPFAGP_API int gp_last_error(void);
 GPFAGP_API int64_t gp_last_error_detail(void);
+/* For GP_ECUDA: the library step whose CUDA call failed (static string,
+ * "" otherwise). */
+GPFAGP_API const char* gp_last_error_where(void);
 GPFAGP_API const char* gp_strerror(int status);
 
 /* ---- extended entry points ---------------------------------------------- */
@@ -122,6 +125,16 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
 
 /* Model shape and mode: any output pointer may be NULL. */
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
+
+/* Model flags: GP_MODEL_GRAM_FP64 when a mixed-precision fit recomputed its
+ * Gram in float64. The mixed Gram keeps its 512-row block sums exact but
+ * sums blocks in float32; when A = G + sigma^2 Lambda^{-1} is conditioned
+ * beyond what that carries (large N with a small noise variance) the
+ * float64 Cholesky meets a non-positive pivot, and the fit (gp_fit_ex,
+ * gp_fit_batch, server refits) then redoes the Gram with the float64 kernel
+ * and factors again instead of failing. */
+#define GP_MODEL_GRAM_FP64 1
+GPFAGP_API int gp_model_flags(const gp_model* h);
 
 /* Copy a fitted quantity of the model to host memory, in float64.
  *   GP_FIELD_L: the Cholesky factor L (M x M row-major, lower; upper = 0)
@@ -171,6 +184,18 @@ GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p
 /* ---- batched fit -------------------------------------------------------- */
 
 /* One independent problem of a batched fit. Pointer kind as in the call. */
+/* Fit from a given Gram: G = Phi^T Phi (M x M, full symmetric, row-major,
+ * float64) and b = Phi^T y (M) of N training rows -- e.g. the sums of the
+ * per-GPU Grams of a row-sharded training set after one all-reduce (each
+ * rank then factors the same A). Continues the fit exactly as gp_fit_ex does
+ * after its Gram step: A = G + sigma^2 Lambda^{-1} (Eq. 11, 16), Cholesky,
+ * W = L^{-1}, c with float64 refinement. G and b are device pointers when
+ * dev_ptrs != 0, else host pointers; they are copied, not kept. Errors as
+ * gp_fit_ex (GP_ENOTPD when G + diag(d) is not positive definite). */
+GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p, int n, double eps,
+                              double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                              gp_model** out);
+
 typedef struct gp_fit_args {
     const double* X;   /* N x p */
     const double* y;   /* N     */
@@ -274,6 +299,8 @@ GPFAGP_API int gp_server_submit_refit(gp_server* s, int model_id, const double* 
  * (GP_ETIMEOUT if the limit passed first; the request stays queued). */
 GPFAGP_API int gp_server_wait(gp_server* s, int64_t req_id, double timeout_s);
 GPFAGP_API int gp_server_stats(gp_server* s, gp_server_report* out);
+/* Start a new measurement window (requests still running are not counted). */
+GPFAGP_API int gp_server_reset_stats(gp_server* s);
 /* Finish every queued request, then stop the worker and release the streams. */
 GPFAGP_API void gp_server_destroy(gp_server* s);
 
@@ -282,6 +309,10 @@ GPFAGP_API void gp_server_destroy(gp_server* s);
 /* Make the k-th device allocation from now fail with GP_ENOMEM (k >= 1);
  * k = 0 disarms. For error-path tests. */
 GPFAGP_API void gp_debug_fail_alloc_after(int k);
+
+/* Make the next k mixed-precision fits report a non-positive pivot on their
+ * first attempt (k = 0 disarms), to exercise the float64 escalation. */
+GPFAGP_API void gp_debug_force_escalation(int k);
 
 /* Library build tag (static string). */
 GPFAGP_API const char* gp_version(void);

@@ -72,6 +72,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_free": (None, [vp]),
         "gp_last_error": (i, []),
         "gp_last_error_detail": (i64, []),
+        "gp_last_error_where": (C.c_char_p, []),
         "gp_strerror": (C.c_char_p, [i]),
         "gp_fit_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_predict_ex": (i, [vp, vp, i64, vp, vp, vp, i]),
@@ -82,6 +83,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
         "gp_batch_info": (i, [C.POINTER(i), C.POINTER(i)]),
+        "gp_fit_gram_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_server_create": (i, [i, i64, C.POINTER(vp)]),
         "gp_server_add_model": (i, [vp, vp, C.POINTER(i)]),
         "gp_server_model": (vp, [vp, i]),
@@ -90,7 +92,10 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_server_wait": (i, [vp, i64, d]),
         "gp_server_stats": (i, [vp, C.POINTER(ServerReport)]),
         "gp_server_destroy": (None, [vp]),
+        "gp_server_reset_stats": (i, [vp]),
         "gp_debug_fail_alloc_after": (None, [i]),
+        "gp_debug_force_escalation": (None, [i]),
+        "gp_model_flags": (i, [vp]),
         "gp_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -107,7 +112,8 @@ def strerror(status: int) -> str:
 
 def _check(rc: int, where: str):
     if rc != GP_OK:
-        raise GPError(rc, int(lib().gp_last_error_detail()), where)
+        w = lib().gp_last_error_where().decode()
+        raise GPError(rc, int(lib().gp_last_error_detail()), where + (f" [{w}]" if w else ""))
 
 
 # ------------------------------------------------------------------ array marshalling
@@ -197,6 +203,11 @@ class Model:
         _check(lib().gp_model_read(self._h, FIELD[field], out.ctypes.data), "gp_model_read")
         return out
 
+    @property
+    def gram_fp64(self) -> bool:
+        """True if this mixed-precision fit recomputed its Gram in float64."""
+        return bool(lib().gp_model_flags(self._h) & 1)
+
     def disown(self) -> int:
         """Give up the handle without freeing it (its new owner frees it)."""
         h = self.handle
@@ -224,6 +235,18 @@ def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "mixe
                          float(alpha), float(sigma2), PREC[prec], _stream_of(X, stream), dev,
                          C.byref(out))
     _check(rc, "gp_fit_ex")
+    return Model(out.value)
+
+
+def fit_gram(G, b, N: int, p: int, n: int, eps: float, alpha: float, sigma2: float,
+             prec: str = "mixed") -> Model:
+    """Fit from a given float64 Gram G = Phi^T Phi (M x M) and b = Phi^T y of N rows (host arrays)."""
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    out = C.c_void_p()
+    rc = lib().gp_fit_gram_ex(G.ctypes.data, b.ctypes.data, int(N), int(p), int(n), float(eps), float(alpha),
+                              float(sigma2), PREC[prec], None, 0, C.byref(out))
+    _check(rc, "gp_fit_gram_ex")
     return Model(out.value)
 
 
@@ -298,6 +321,10 @@ def predict_batch(reqs: Sequence[Tuple], stream=None):
     _check(lib().gp_predict_batch(cnt, args, st), "gp_predict_batch")
 
 
+def debug_force_escalation(k: int):
+    lib().gp_debug_force_escalation(int(k))
+
+
 def debug_fail_alloc_after(k: int):
     lib().gp_debug_fail_alloc_after(int(k))
 
@@ -361,6 +388,9 @@ class Server:
         r = ServerReport()
         _check(lib().gp_server_stats(self.handle, C.byref(r)), "gp_server_stats")
         return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def reset_stats(self):
+        _check(lib().gp_server_reset_stats(self.handle), "gp_server_reset_stats")
 
     def model_handle(self, model_id: int):
         return lib().gp_server_model(self.handle, int(model_id))

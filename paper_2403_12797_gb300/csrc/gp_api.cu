@@ -36,7 +36,12 @@ int set_err(int code, int64_t detail) {
     return code;
 }
 
-int cuda_err(cudaError_t e) { return set_err(GP_ECUDA, (int64_t)e); }
+thread_local const char* g_where = "";
+
+int cuda_err(cudaError_t e, const char* where) {
+    g_where = where;
+    return set_err(GP_ECUDA, (int64_t)e);
+}
 
 // Keep the stream-ordered pool's memory across calls (no release at every
 // synchronisation), so repeated fits and predicts do not remap memory.
@@ -109,7 +114,7 @@ int read_status(GpStatus* st, cudaStream_t s) {
     GpStatus h;
     cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "status read");
     if (h.code != GP_OK) return set_err(h.code, h.detail);
     return GP_OK;
 }
@@ -161,7 +166,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         {
             GpProf pf("syrk64", stream);
             cudaError_t e = launch_syrk64(s, tab, ypad, nsplit, rps, Gpart, bpart, stream);
-            if (e != cudaSuccess) return cuda_err(e);
+            if (e != cudaSuccess) return cuda_err(e, "syrk64 launch");
             gp_note_launches(1);
         }
         {
@@ -170,7 +175,9 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             gp_note_launches(1);
         }
     } else {
-        float *tab, *ypad, *Gpart, *bpart;
+        float *tab, *ypad;
+        float2* Gpart;
+        double* bpart;
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
         if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
         const int T = s.Mpad / SYRKTC_TM;
@@ -196,18 +203,17 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             GpProf pf("syrk_tc", stream);
             cudaError_t e = launch_syrk_tc(s, tab, tmaxb, tmax, ypad, nsplit, rps, Gpart, bpart, colexp,
                                            st, stream);
-            if (e != cudaSuccess) return cuda_err(e);
+            if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
             gp_note_launches(1);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_f32(Gpart, bpart, nullptr, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b,
-                                stream);
+            launch_assemble_scaled(Gpart, bpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
             gp_note_launches(1);
         }
     }
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "Gram step");
     return GP_OK;
 }
 
@@ -235,7 +241,7 @@ void free_model(gp_model* h) {
 int model_alloc(gp_model* h, size_t bytes, void** p, cudaStream_t s) {
     cudaError_t e = dev_alloc(p, bytes, s);
     if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)bytes);
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "model allocation");
     return GP_OK;
 }
 
@@ -283,15 +289,33 @@ int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t strea
         e = cudaMemcpyAsync(h->cinfo, stage.cinfo.data(), sizeof(int) * stage.cinfo.size(),
                             cudaMemcpyHostToDevice, stream);
     }
-    return e == cudaSuccess ? GP_OK : cuda_err(e);
+    return e == cudaSuccess ? GP_OK : cuda_err(e, "shape-input copies");
+}
+
+int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
+               cudaStream_t stream);
+
+__global__ void add_diag_kernel(double* __restrict__ A, const double* __restrict__ d, int M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) A[(int64_t)i * M + i] += d[i];
 }
 
 // Every device step of one fit, enqueued on `stream` with no host
 // synchronisation (so that it can be captured into a graph). Inputs are
 // device pointers; scratch comes from `sc` (stream-ordered); errors found on
 // the device land in *st.
+// Test hook: the next k mixed-precision fits report a non-positive pivot on
+// their first attempt (exercises the float64 escalation).
+std::atomic<int> g_force_escalate{0};
+
+bool mixed_escalates(const gp_model* h, int code) {
+    return h->prec == GP_PREC_MIXED && code == GP_ENOTPD && !(h->flags & GP_MODEL_GRAM_FP64);
+}
+
+__global__ void force_notpd_kernel(GpStatus* st) { gp_set_status(st, GP_ENOTPD, 0); }
+
 int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
-                int gram_ctas, Scratch& sc, cudaStream_t stream) {
+                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec) {
     const GpShape& s = h->shape;
     const int M = s.M;
     const int prec = h->prec;
@@ -304,7 +328,25 @@ int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* l
     if ((rc = sc.get(&fwork, factor_work_bytes(M, fp32_inverse)))) return rc;
     launch_noise_diag(s, loglam_d, h->sigma2, h->d, stream);
     gp_note_launches(1);
-    if ((rc = gram_device(s, prec, h->device, Xd, yd, h->d, A, h->b, st, stream, gram_ctas))) return rc;
+    const int gp_ = gram_prec < 0 ? prec : gram_prec;
+    if (gp_ == GP_PREC_FP64 && prec != GP_PREC_FP64) h->flags |= GP_MODEL_GRAM_FP64;
+    if ((rc = gram_device(s, gp_, h->device, Xd, yd, h->d, A, h->b, st, stream, gram_ctas))) return rc;
+    if (prec == GP_PREC_MIXED && gp_ == GP_PREC_MIXED) {
+        int k = g_force_escalate.load();
+        while (k > 0 && !g_force_escalate.compare_exchange_weak(k, k - 1)) {
+        }
+        if (k > 0) force_notpd_kernel<<<1, 1, 0, stream>>>(st);
+    }
+    return fit_factor(h, A, work, fwork, st, stream);
+}
+
+// The factorisation steps of a fit from the assembled A (device, M x M, kept
+// for the refinement residual): L, W = L^{-1}, c, and the predict operand.
+int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
+               cudaStream_t stream) {
+    const int M = h->shape.M;
+    const int prec = h->prec;
+    const bool fp32_inverse = (prec != GP_PREC_FP64);
     cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
     cudaError_t e;
     {
@@ -325,7 +367,7 @@ int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* l
         gp_note_launches(1);
         e = cudaGetLastError();
     }
-    return e == cudaSuccess ? GP_OK : cuda_err(e);
+    return e == cudaSuccess ? GP_OK : cuda_err(e, "factorisation or solve launch");
 }
 
 // Every device step of one predict (tables of X*, then mean and variance),
@@ -359,7 +401,7 @@ int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md,
         e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->c, h->sigma2, md, vd, st, stream);
         gp_note_launches(2);
     }
-    return e == cudaSuccess ? GP_OK : cuda_err(e);
+    return e == cudaSuccess ? GP_OK : cuda_err(e, "predict launch");
 }
 
 // ---------------------------------------------------------------- batches
@@ -522,6 +564,8 @@ GPFAGP_API const char* gp_version(void) { return "gpfagp 0.1 sm_103a"; }
 GPFAGP_API int gp_last_error(void) { return g_err; }
 GPFAGP_API int64_t gp_last_error_detail(void) { return g_detail; }
 
+GPFAGP_API const char* gp_last_error_where(void) { return g_err == GP_ECUDA ? g_where : ""; }
+
 GPFAGP_API const char* gp_strerror(int status) {
     switch (status) {
         case GP_OK: return "ok";
@@ -536,6 +580,10 @@ GPFAGP_API const char* gp_strerror(int status) {
 }
 
 GPFAGP_API void gp_debug_fail_alloc_after(int k) { g_fail_after.store(k > 0 ? k : 0); }
+
+GPFAGP_API void gp_debug_force_escalation(int k) { g_force_escalate.store(k > 0 ? k : 0); }
+
+GPFAGP_API int gp_model_flags(const gp_model* h) { return h ? h->flags : 0; }
 
 GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
                           double alpha, int prec, double* G, double* b, void* cuda_stream,
@@ -629,6 +677,61 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if ((rc = fit_stage(h, stage, loglam, stream))) return fail(rc);
     if ((rc = fit_compute(h, Xd, yd, loglam, st, 0, sc, stream))) return fail(rc);
     // the staged host vectors live until this read synchronises the stream
+    rc = read_status(st, stream);
+    if (mixed_escalates(h, rc)) {
+        // the mixed Gram was not accurate enough for this A: redo it in float64
+        set_err(GP_OK);
+        cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+        Scratch sc2(stream);
+        if ((rc = fit_compute(h, Xd, yd, loglam, st, 0, sc2, stream, GP_PREC_FP64))) return fail(rc);
+        rc = read_status(st, stream);
+    }
+    if (rc) return fail(rc);
+    *out = h;
+    return GP_OK;
+}
+
+GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p, int n, double eps,
+                              double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                              gp_model** out) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!out) return set_err(GP_EINVAL, 0);
+    *out = nullptr;
+    if (!G || !b) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
+    if ((rc = check_prec(prec))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    gp_model* h = new_model(dev, prec, N, p, n, eps, alpha, sigma2);
+    const int M = h->shape.M;
+    Scratch sc(stream);
+    FitStage stage;
+    auto fail = [&](int code) {
+        int64_t det = g_detail;
+        cudaStreamSynchronize(stream);
+        free_model(h);
+        set_err(code, det);
+        return code;
+    };
+    if ((rc = fit_alloc(h, stream))) return fail(rc);
+    GpStatus* st;
+    double *loglam, *A, *work;
+    unsigned char* fwork;
+    if ((rc = sc.get(&st, 1))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    if ((rc = sc.get(&A, (size_t)M * M))) return fail(rc);
+    if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return fail(rc);
+    if ((rc = sc.get(&fwork, factor_work_bytes(M, prec != GP_PREC_FP64)))) return fail(rc);
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    const cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyAsync(A, G, sizeof(double) * M * M, kind, stream);
+    cudaMemcpyAsync(h->b, b, sizeof(double) * M, kind, stream);
+    if ((rc = fit_stage(h, stage, loglam, stream))) return fail(rc);
+    launch_noise_diag(h->shape, loglam, sigma2, h->d, stream);
+    add_diag_kernel<<<(M + 255) / 256, 256, 0, stream>>>(A, h->d, M);
+    gp_note_launches(2);
+    if ((rc = fit_factor(h, A, work, fwork, st, stream))) return fail(rc);
     if ((rc = read_status(st, stream))) return fail(rc);
     *out = h;
     return GP_OK;
@@ -706,7 +809,7 @@ GPFAGP_API int gp_model_read(const gp_model* h, int field, double* dst) {
     cudaSetDevice(h->device);
     cudaError_t e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyDeviceToHost);
     cudaSetDevice(cur);
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "model read");
     return GP_OK;
 }
 
@@ -726,7 +829,24 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
         if (check_hyper(a.N, a.p, a.n, a.eps, a.alpha, a.sigma2)) return set_err(GP_EINVAL, i);
     }
     if ((rc = check_device(&dev))) return rc;
+    // The legacy default stream cannot be captured: the batch then runs on a
+    // stream of its own, ordered after the work already queued there.
+    struct OwnStream {
+        cudaStream_t s = nullptr;
+        ~OwnStream() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } own;
     cudaStream_t origin = (cudaStream_t)cuda_stream;
+    if (origin == nullptr) {
+        cudaEvent_t ev;
+        cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaEventRecord(ev, nullptr);
+        cudaStreamWaitEvent(own.s, ev, 0);
+        cudaEventDestroy(ev);
+        origin = own.s;
+    }
     const int sms = num_sms(dev);
 
     // models, inputs on the device, shape-only inputs: all before any capture
@@ -764,7 +884,7 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
         }
     }
     cudaError_t e = cudaStreamSynchronize(origin);  // staged host inputs have been read
-    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
+    if (e != cudaSuccess) return fail_all(cuda_err(e, "batch input staging"), -1);
 
     StreamSet ss(count < 8 ? count : 8);
     const int k = tune_batch(hs, Xd, yd, sts, ss, origin, sms);
@@ -820,11 +940,23 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
     gp_prof_resume(prof);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
+    if (e != cudaSuccess) return fail_all(cuda_err(e, "batch synchronise"), -1);
 
     std::vector<GpStatus> hst(count);
     e = cudaMemcpy(hst.data(), sts, sizeof(GpStatus) * count, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail_all(cuda_err(e), -1);
+    if (e != cudaSuccess) return fail_all(cuda_err(e, "batch status read"), -1);
+    // members whose mixed Gram was not accurate enough: float64 Gram, one by one
+    for (int i = 0; i < count; ++i) {
+        if (!mixed_escalates(hs[i], hst[i].code)) continue;
+        cudaMemsetAsync(&sts[i], 0, sizeof(GpStatus), origin);
+        Scratch sc2(origin);
+        rc = fit_compute(hs[i], Xd[i], yd[i], loglam[i], &sts[i], 0, sc2, origin, GP_PREC_FP64);
+        if (rc != GP_OK) return fail_all(rc, i);
+        e = cudaMemcpyAsync(&hst[i], &sts[i], sizeof(GpStatus), cudaMemcpyDeviceToHost, origin);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(origin);
+        if (e != cudaSuccess) return fail_all(cuda_err(e, "batch status read"), -1);
+    }
+    set_err(GP_OK);
     int first = GP_OK;
     int64_t first_idx = 0;
     for (int i = 0; i < count; ++i) {
@@ -887,11 +1019,11 @@ GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cu
     }
     ss.join(origin);
     cudaError_t e = cudaStreamSynchronize(origin);
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "batch synchronise");
     if (first != GP_OK) return set_err(first, first_idx);
     std::vector<GpStatus> hst(count);
     e = cudaMemcpy(hst.data(), sts, sizeof(GpStatus) * count, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_err(e);
+    if (e != cudaSuccess) return cuda_err(e, "batch status read");
     for (int i = 0; i < count; ++i)
         if (hst[i].code != GP_OK) return set_err(hst[i].code, i);
     return GP_OK;

@@ -14,10 +14,15 @@
 
 namespace {
 
-template <typename P>
+// a partial value as float64 (float pairs hold hi + lo)
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float2 v) { return (double)v.x + (double)v.y; }
+
+template <typename P, typename PB = P>
 __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpart,
-                                                       const P* __restrict__ bpart,
-                                                       const P* __restrict__ dpart,
+                                                       const PB* __restrict__ bpart,
+                                                       const PB* __restrict__ dpart,
                                                        const int* __restrict__ colexp, int nsplit,
                                                        int tile, int Mpad, int M,
                                                        const double* __restrict__ d,
@@ -36,15 +41,15 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     const int64_t off = (int64_t)q * tile * tile + (int64_t)(r % tile) * tile + (c % tile);
     const int64_t sstride = (int64_t)npairs * tile * tile;
     double acc = 0.0;
-    for (int s = 0; s < nsplit; ++s) acc += (double)Gpart[off + s * sstride];
+    for (int s = 0; s < nsplit; ++s) acc += to_f64(Gpart[off + s * sstride]);
     if (row == col && dpart != nullptr)
-        for (int s = 0; s < nsplit; ++s) acc += (double)dpart[(int64_t)s * Mpad + row];
+        for (int s = 0; s < nsplit; ++s) acc += to_f64(dpart[(int64_t)s * Mpad + row]);
     if (colexp != nullptr) acc = ldexp(acc, colexp[r] + colexp[c] - 14);
     if (row == col && d != nullptr) acc += d[row];
     A[(int64_t)row * M + col] = acc;
     if (row == 0) {
         double bb = 0.0;
-        for (int s = 0; s < nsplit; ++s) bb += (double)bpart[(int64_t)s * Mpad + col];
+        for (int s = 0; s < nsplit; ++s) bb += to_f64(bpart[(int64_t)s * Mpad + col]);
         b[col] = bb;
     }
 }
@@ -65,7 +70,7 @@ __global__ void noise_diag_kernel(GpShape s, const double* __restrict__ loglam, 
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, nullptr, nsplit, tile,
+    assemble_kernel<double, double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, nullptr, nsplit, tile,
                                                       Mpad, M, d, A, b);
 }
 
@@ -73,8 +78,16 @@ void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dp
                          const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
                          double* A, double* b, cudaStream_t stream) {
     dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, colexp, nsplit, tile, Mpad,
+    assemble_kernel<float, float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, colexp, nsplit, tile, Mpad,
                                                      M, d, A, b);
+}
+
+void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
+                            int tile, int Mpad, int M, const double* d, double* A, double* b,
+                            cudaStream_t stream) {
+    dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
+    assemble_kernel<float2, double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, colexp, nsplit, tile,
+                                                              Mpad, M, d, A, b);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

@@ -124,6 +124,22 @@ static inline int64_t gp_round_up(int64_t v, int64_t m) { return (v + m - 1) / m
 // ---------------------------------------------------------------------------
 int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile);
 
+// Let `kern` use as much dynamic shared memory as the device allows next to
+// its static shared memory. Always the same value, so it can be set before
+// every launch in any order (captured graphs and concurrent launches of the
+// same kernel with different sizes see one limit); each launch's own size
+// is checked against it at launch.
+inline cudaError_t gp_allow_max_smem(const void* kern) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 // gp_prof.cu: kernel launch counter and CUDA-event timing of kernel groups
 void gp_note_launches(int n);
 void gp_prof_begin(const char* name, cudaStream_t s);

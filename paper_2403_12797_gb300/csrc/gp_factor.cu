@@ -759,7 +759,7 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
         float* D = (float*)base;
         const void* k = (const void*)trinv_strip_kernel;
         const size_t smem = strip_smem_bytes(M);
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        gp_allow_max_smem((const void*)k);
         int sms = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         dim3 grid((unsigned)((int)nb < sms ? (int)nb : sms)), block(NT);  // one CTA per strip

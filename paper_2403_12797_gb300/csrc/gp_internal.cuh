@@ -19,13 +19,15 @@ struct gp_model {
     double* d;              // M, sigma^2 / lambda_m (clamped)
     uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
     int* cinfo;             // chunk table of the tensor-core predict (GP_PREC_MIXED only)
+    int flags;              // GP_MODEL_GRAM_FP64: Gram recomputed in float64 (mixed mode)
 };
 
 namespace gpi {
 
 // thread-local status of the last ABI call (gp_last_error / _detail)
 int set_err(int code, int64_t detail = 0);
-int cuda_err(cudaError_t e);
+// GP_ECUDA with detail = the CUDA error code; `where` names the failing step
+int cuda_err(cudaError_t e, const char* where = "");
 // stream-ordered allocation (honours gp_debug_fail_alloc_after)
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 
@@ -43,7 +45,7 @@ struct Scratch {
         void* v = nullptr;
         cudaError_t e = dev_alloc(&v, count * sizeof(T), s);
         if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)(count * sizeof(T)));
-        if (e != cudaSuccess) return cuda_err(e);
+        if (e != cudaSuccess) return cuda_err(e, "scratch allocation");
         ptrs.push_back(v);
         *p = (T*)v;
         return GP_OK;
@@ -69,8 +71,13 @@ struct FitStage {
 // shape-only inputs to the device (log eigenvalues; predict chunk table into the model)
 int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream);
 // every device step of a fit / of a predict, enqueued without host synchronisation
+// gram_prec: precision of the Gram step (-1: the model's); the mixed mode
+// escalates to GP_PREC_FP64 after a non-positive pivot (see mixed_escalates)
 int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
-                int gram_ctas, Scratch& sc, cudaStream_t stream);
+                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec = -1);
+// whether a fit that ended with `code` is redone with the float64 Gram: a
+// mixed-precision fit whose Cholesky met a non-positive pivot
+bool mixed_escalates(const gp_model* h, int code);
 int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md, double* vd, GpStatus* st,
                     Scratch& sc, cudaStream_t stream);
 

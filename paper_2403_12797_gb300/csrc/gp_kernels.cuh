@@ -29,12 +29,13 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
 constexpr int SYRKTC_TM = 128;
 constexpr int SYRKTC_BK = 32;
 size_t syrktc_smem_bytes(const GpShape& s);
-// Gpart holds column-scaled partial tiles (units 2^(14 - E_m - E_m')),
-// colexp[m] = E_m (Mpad), bpart the unscaled Phi^T y partials.
+// Gpart holds column-scaled partial tiles as float pairs hi + lo (units
+// 2^(14 - E_m - E_m')),
+// colexp[m] = E_m (Mpad), bpart the unscaled float64 Phi^T y partials.
 // rows_per_split must be a multiple of GP_TAB_BLOCK.
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
                            const unsigned int* tmax, const float* ypad, int nsplit,
-                           int64_t rows_per_split, float* Gpart, float* bpart, int* colexp,
+                           int64_t rows_per_split, float2* Gpart, double* bpart, int* colexp,
                            GpStatus* st, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
@@ -48,6 +49,10 @@ void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, i
 void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart,
                          const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
                          double* A, double* b, cudaStream_t stream);
+// float-pair partials of the tensor-core Gram: A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
+void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
+                            int tile, int Mpad, int M, const double* d, double* A, double* b,
+                            cudaStream_t stream);
 // d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
                        cudaStream_t stream);

@@ -126,8 +126,7 @@ cudaError_t launch_predict64(const GpShape& s, const double* tab, const double* 
     const size_t smem = sizeof(double) * ((size_t)maxrows * TT + TT * (CK + 1) + CK * TK) +
                         sizeof(int) * maxrows + sizeof(unsigned short) * CK * s.p + 16;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(predict64_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = gp_allow_max_smem((const void*)predict64_kernel);
         if (e != cudaSuccess) return e;
     }
     const int nkt = (s.M + TK - 1) / TK;

@@ -425,9 +425,8 @@ cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t
                               double* var, GpStatus* st, cudaStream_t stream) {
     const int maxrows = predtc_maxrows(s);
     const size_t smem = predtc_smem_bytes(s);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(predict_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > (227 - 2) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
+    cudaError_t e = gp_allow_max_smem((const void*)predict_tc_kernel);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(s.Npad / TT);
     predict_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, cinfo, maxrows,

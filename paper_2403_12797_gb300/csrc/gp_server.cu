@@ -94,6 +94,11 @@ struct Request {
     Scratch* sc = nullptr;
     GpStatus* st = nullptr;
     FitStage stage;
+    // refit: staged device inputs, and the float64-Gram retry
+    double* xd = nullptr;
+    double* ll = nullptr;
+    Scratch* sc2 = nullptr;
+    bool escalated = false;
 };
 
 }  // namespace
@@ -194,12 +199,35 @@ int launch_request(gp_server* S, Request* r, int slot) {
         if ((rc = r->sc->get(&ll, (size_t)s.n))) return rc;
         cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
         const double* yd = xd + (size_t)r->N * s.p;
+        r->xd = xd;
+        r->ll = ll;
         if ((rc = fit_stage(h, r->stage, ll, st))) return rc;
         if ((rc = fit_compute(h, xd, yd, ll, r->st, 0, *r->sc, st))) return rc;
         cudaMemcpyAsync((char*)pin.p + in, r->st, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
     }
     cudaEventRecord(S->done_ev[slot], st);
     return GP_OK;
+}
+
+// A refit whose mixed Gram met a non-positive pivot: redo the fit on the same
+// slot with the float64 Gram (its staged inputs are still on the device).
+// Returns false if the retry could not be enqueued.
+bool escalate_refit(gp_server* S, Request* r) {
+    const int slot = r->slot;
+    cudaStream_t st = S->streams[slot];
+    const GpShape& s = r->fresh->shape;
+    r->escalated = true;
+    r->sc2 = new Scratch(st);
+    GpStatus* st2;
+    if (r->sc2->get(&st2, 1)) return false;
+    cudaMemsetAsync(st2, 0, sizeof(GpStatus), st);
+    const double* yd = r->xd + (size_t)r->N * s.p;
+    if (fit_compute(r->fresh, r->xd, yd, r->ll, st2, 0, *r->sc2, st, GP_PREC_FP64)) return false;
+    const size_t in = (size_t)r->N * (s.p + 1) * 8;
+    cudaMemcpyAsync((char*)S->pin[slot].p + in, st2, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(S->done_ev[slot], st);
+    r->st = st2;
+    return true;
 }
 
 // Request r has completed (or failed to launch): results out, accounting (lock held).
@@ -225,11 +253,15 @@ void finish_request(gp_server* S, Request* r, int launch_rc) {
         } else {
             memcpy(&hs, (const char*)pin.p + (size_t)r->N * (S->models[r->model].model->shape.p + 1) * 8,
                    sizeof(hs));
+            if (!r->escalated && mixed_escalates(r->fresh, hs.code) && escalate_refit(S, r))
+                return;  // still running: finished when the retry completes
         }
         code = hs.code;
     }
     delete r->sc;  // stream-ordered frees behind the finished work
     r->sc = nullptr;
+    delete r->sc2;
+    r->sc2 = nullptr;
     r->status = code;
     S->slot_req[r->slot] = nullptr;
     S->mem_used -= r->bytes;
@@ -475,6 +507,18 @@ GPFAGP_API int gp_server_stats(gp_server* S, gp_server_report* out) {
         out->wall_s = ms_between(S->first_submit, S->last_end) / 1e3;
         out->points_per_s = out->wall_s > 0 ? (double)S->points / out->wall_s : 0.0;
     }
+    return GP_OK;
+}
+
+GPFAGP_API int gp_server_reset_stats(gp_server* S) {
+    set_err(GP_OK);
+    if (!S) return set_err(GP_EINVAL, 0);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->lat_ms.clear();
+    S->points = 0;
+    S->refits_done = 0;
+    S->peak_inflight = S->inflight;
+    S->have_first = false;
     return GP_OK;
 }
 

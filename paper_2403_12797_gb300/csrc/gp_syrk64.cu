@@ -172,8 +172,7 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
     int T = s.Mpad / TM;
     int npairs = T * (T + 1) / 2;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(syrk64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = gp_allow_max_smem((const void*)syrk64_kernel);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)npairs, (unsigned)nsplit);

@@ -21,8 +21,12 @@
 //     negligible;
 //   * after each block the producers multiply acc1 + acc2 by the exact power
 //     of two that maps the block's column scaling to the global one and add
-//     it into float32 registers (round to nearest: unbiased), while the MMAs
-//     fill the other TMEM buffer (two buffers x 256 columns = all 512).
+//     it into float32 registers; every FLUSH_BLOCKS blocks those are folded
+//     into the split's partial tile of float pairs (hi + lo, an exact
+//     two-sum, ~46 bits), while the MMAs fill the other
+//     TMEM buffer (two buffers x 256 columns = all 512); summing the blocks
+//     in float32 instead would lose ~1e-6 of G over a million rows, enough
+//     to make a strongly conditioned A indefinite.
 // Representation error: |w - s1 - lo| <= 2^-12 (2^-19 of the block bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
@@ -48,6 +52,7 @@ constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WBUF = 3;                    // table-window ring (chunks prefetched ahead)
 constexpr int BLOCK_CHUNKS = 16;           // 512 rows per exact TMEM block
+constexpr int FLUSH_BLOCKS = 4;            // blocks summed in float32 registers between flushes
 constexpr int WSTRIDE = BK + 4;            // floats per window row (bank-conflict padding)
 constexpr int TILE_BYTES = TM * BK * 2;    // one bf16 operand tile: 8 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A s2, B s1, B s2
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmaxb,
                    const unsigned int* __restrict__ tmax,
                    const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows, int nst,
-                   float* __restrict__ Gpart, float* __restrict__ bpart,
+                   float2* __restrict__ Gpart, double* __restrict__ bpart,
                    int* __restrict__ colexp, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
@@ -336,10 +341,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 woffJ[j] = (j == 0 && cj == 0xFFFF) ? -1 : cj * WSTRIDE;
             }
         }
+        // b: float32 within a block, float64 across blocks
         float bacc = 0.f;
-        float gacc[CPT];               // this thread's part of its tile row
+        double bsum = 0.0;
+        // This thread's part of its tile row: blocks are summed in float32
+        // registers (gacc) for FLUSH_BLOCKS blocks, then folded into the
+        // split's partial tile, kept as unevaluated float pairs hi + lo
+        // (~46-bit sums), by an exact two-sum in float32 arithmetic
+        // (read-modify-write of memory only this thread touches, resident in
+        // L2). The long sums over blocks thus lose nothing that matters, while
+        // staying off the slow float64 pipe and off the drain's critical path
+        // most of the time.
+        float2* grow = Gpart + ((int64_t)split * npairs + q) * (TM * TM) +
+                       (int64_t)(quarter * 32 + lane) * TM + cgrp * CPT;
+        float gacc[CPT];
 #pragma unroll
         for (int i = 0; i < CPT; ++i) gacc[i] = 0.f;
+        bool flushed = false;
+        auto flush = [&]() {
+            // hi + v = s + e exactly (Knuth's two-sum); lo collects e
+            auto add2 = [](float& hi, float& lo, float v) {
+                const float s = __fadd_rn(hi, v);
+                const float t = __fsub_rn(s, hi);
+                const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, t)), __fsub_rn(v, t));
+                hi = s;
+                lo = __fadd_rn(lo, e);
+            };
+            float4* g4 = reinterpret_cast<float4*>(grow);  // (hi, lo) of two elements
+#pragma unroll
+            for (int k = 0; k < CPT / 2; ++k) {
+                float4 o = flushed ? g4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                add2(o.x, o.y, gacc[2 * k]);
+                add2(o.z, o.w, gacc[2 * k + 1]);
+                g4[k] = o;
+                gacc[2 * k] = 0.f;
+                gacc[2 * k + 1] = 0.f;
+            }
+            flushed = true;
+        };
         bool ok = true;
 
         // One thread waits and broadcasts, so every producer takes the same
@@ -376,6 +415,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_before();
             mbar_arrive(&sm.drained[u]);
+            if ((d + 1) % FLUSH_BLOCKS == 0 || d + 1 == nblocks) flush();
             return true;
         };
 
@@ -406,6 +446,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int slot = (c / BLOCK_CHUNKS) & 1;
             const bool newblk = (c % BLOCK_CHUNKS == 0);
             if (newblk) {
+                bsum += (double)bacc;
+                bacc = 0.f;
                 // a new 512-row block: its column scales (the drain of the
                 // block two back, which used this slot, is complete)
                 const unsigned int* tmb = tmaxb + ((r0 + (int64_t)c * BK) / GP_TAB_BLOCK) * (s.p * s.n);
@@ -458,18 +500,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (J == 0) {
-            float v = bacc;
+            double v = bsum + (double)bacc;
             v += __shfl_xor_sync(0xffffffffu, v, 8);
             v += __shfl_xor_sync(0xffffffffu, v, 16);
             if (lane < 8) bpart[(int64_t)split * s.Mpad + I * TM + r] = v;
         }
-        if (ok) {
-            const int row = quarter * 32 + lane;
-            float4* o4 = reinterpret_cast<float4*>(Gpart + ((int64_t)split * npairs + q) * (TM * TM) +
-                                                   (int64_t)row * TM + cgrp * CPT);
+        if (nblocks == 0) {  // a split without rows: its partial tile is zero
 #pragma unroll
-            for (int k = 0; k < CPT / 4; ++k)
-                o4[k] = make_float4(gacc[4 * k], gacc[4 * k + 1], gacc[4 * k + 2], gacc[4 * k + 3]);
+            for (int k = 0; k < CPT; ++k) grow[k] = make_float2(0.f, 0.f);
         }
     } else {
         // ------------------------------------------------------------ MMA issuer
@@ -521,11 +559,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// deepest pipeline (<= STAGES) whose shared memory fits one CTA; 0 if none
+// deepest pipeline (<= STAGES) whose dynamic shared memory fits one CTA next
+// to the kernel's static shared memory (tile windows and flags, under 2 KB);
+// 0 if none
 int syrk_tc_stages(const GpShape& s, int maxrows, size_t* smem) {
+    constexpr size_t kDynamicBudget = (227 - 2) * 1024;
     for (int nst = STAGES; nst >= 2; --nst) {
         *smem = smem_tc_layout(maxrows, s.p, nst, nullptr, nullptr);
-        if (*smem <= 227 * 1024) return nst;
+        if (*smem <= kDynamicBudget) return nst;
     }
     return 0;
 }
@@ -540,7 +581,7 @@ size_t syrktc_smem_bytes(const GpShape& s) {
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
                            const unsigned int* tmax, const float* ypad, int nsplit,
-                           int64_t rows_per_split, float* Gpart, float* bpart, int* colexp,
+                           int64_t rows_per_split, float2* Gpart, double* bpart, int* colexp,
                            GpStatus* st, cudaStream_t stream) {
     if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
@@ -551,7 +592,7 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned in
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
     auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = gp_allow_max_smem((const void*)kern);
         if (e != cudaSuccess) return e;
         kern<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs, maxrows,
                                                nst, Gpart, bpart, colexp, st);

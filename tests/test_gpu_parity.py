@@ -175,3 +175,59 @@ def test_allocation_failure_reports_enomem_then_recovers():
     m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
     mean, _ = m.predict(pr.Xs)
     assert np.isfinite(mean).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fit_from_gram_and_two_shards(prec):
+    """gp_fit_gram_ex continues a fit from a given Gram: from the whole Gram it
+    agrees with gp_fit_ex, and from the sum of two row-block Grams (the
+    all-reduce of a two-GPU fit, emulated on one GPU) it matches the oracle."""
+    from paper_2403_12797_gb300 import dist as D
+    pr = W.workload2(N=30_000, Ns=2_000)
+    G, b = _lib.gram(pr.X, pr.y, pr.n, pr.eps, pr.alpha, prec=prec)
+    mg = _lib.fit_gram(G, b, pr.X.shape[0], 2, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    mf = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    Gs, bs = np.zeros_like(G), np.zeros_like(b)
+    for r in range(2):
+        i0, i1 = D.row_partition(pr.X.shape[0], 2, r, granule=512)
+        g, bb = _lib.gram(pr.X[i0:i1], pr.y[i0:i1], pr.n, pr.eps, pr.alpha, prec=prec)
+        Gs += g
+        bs += bb
+    ms = _lib.fit_gram(Gs, bs, pr.X.shape[0], 2, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+    try:
+        mean_g, var_g = mg.predict(pr.Xs)
+        mean_f, var_f = mf.predict(pr.Xs)
+        assert O.relerr(mean_g, mean_f) < 1e-12 and O.relerr(var_g, var_f) < 1e-12
+        mdl, (mo, vo) = _oracle(pr)
+        mean_s, var_s = ms.predict(pr.Xs)
+        assert O.relerr(mean_s, mo) < TOL[prec]["mean"]
+        assert O.relerr(var_s, vo) < TOL[prec]["var"]
+    finally:
+        mg.free()
+        mf.free()
+        ms.free()
+
+
+def test_mixed_fit_escalates_to_fp64_gram():
+    """A mixed fit whose Cholesky meets a non-positive pivot redoes its Gram in
+    float64 (forced here through the test hook): the model is flagged and
+    matches the oracle to the float64 Gram's accuracy in the mean."""
+    pr = W.workload2(N=20_000, Ns=1_000)
+    _lib.debug_force_escalation(1)
+    try:
+        m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="mixed")
+    finally:
+        _lib.debug_force_escalation(0)
+    try:
+        assert m.gram_fp64
+        mean, var = m.predict(pr.Xs)
+        mdl, (mo, vo) = _oracle(pr)
+        assert O.relerr(mean, mo) < 1e-6
+        assert O.relerr(var, vo) < TOL["mixed"]["var"]
+    finally:
+        m.free()
+    plain = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="mixed")
+    try:
+        assert not plain.gram_fp64
+    finally:
+        plain.free()
