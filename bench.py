@@ -251,8 +251,8 @@ def run_ours(args):
     work = {
         "syrk_tc": ("tensor", N * M * (M + 1) + 2 * N * M, pk["bf16"], "TFLOP/s", "gp_syrk_tc.cu"),
         "predict_tc": ("tensor", Ns * M * (M + 1) + 4 * Ns * M, pk["bf16"], "TFLOP/s", "gp_predict_tc.cu"),
-        "cholesky": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_chol.cu"),
-        "tri_inverse": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_chol.cu"),
+        "cholesky": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_factor.cu"),
+        "tri_inverse": ("alu", M ** 3 / 3, FP64_PEAK_TFLOPS, "TFLOP/s", "gp_factor.cu"),
         "eig_tables": ("hbm", (N + Ns) * 2 * 8 + (N + Ns) * 2 * pr.n * 4, pk["hbm"], "GB/s", "gp_tables.cu"),
     }
     total_dev = sum(g["total_ms"] for g in groups.values()) or 1.0
