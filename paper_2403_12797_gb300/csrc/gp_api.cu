@@ -363,7 +363,7 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
     }
     if (e == cudaSuccess && prec != GP_PREC_FP64) {
         GpProf pf("pack_w", stream);
-        launch_pack_w_bf16x3(h->W, M, h->Wpack, stream);
+        launch_pack_w_bf16x3(h->W, h->c, M, h->Wpack, stream);
         gp_note_launches(1);
         e = cudaGetLastError();
     }
@@ -398,7 +398,7 @@ int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md,
             launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
         }
         GpProf pf("predict_tc", stream);
-        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->c, h->sigma2, md, vd, st, stream);
+        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->sigma2, md, vd, st, stream);
         gp_note_launches(2);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "predict launch");

@@ -93,13 +93,13 @@ constexpr int PREDTC_TT = 128;  // test points per CTA (MMA M)
 constexpr int PREDTC_BK = 32;   // Phi_* columns per pipeline stage (MMA K chunk)
 constexpr int PREDTC_KB = 128;  // rows of W per MMA (MMA N)
 constexpr int PREDTC_SUPER = 4; // MMA N-blocks held in TMEM at once (4 x 128 = 512 columns)
-// Pack W = L^{-1} (float64, M x M) into the bf16 hi/lo blocked operand layout.
 size_t predtc_wpack_bytes(int M);
-void launch_pack_w_bf16x3(const double* W, int M, uint16_t* Wpack, cudaStream_t stream);
+// Pack W = L^{-1} and c into the predict kernel's operands: bf16 hi/lo blocks of W, then c in float32.
+void launch_pack_w_bf16x3(const double* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream);
 size_t predtc_smem_bytes(const GpShape& s);
 // Chunk table of the predict kernel (ints): built once per fitted model.
 size_t predtc_cinfo_ints(const GpShape& s);
 void predtc_build_cinfo(const GpShape& s, int* out);
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
-                              const int* cinfo, const double* c, double sigma2, double* mean,
-                              double* var, GpStatus* st, cudaStream_t stream);
+                              const int* cinfo, double sigma2, double* mean, double* var,
+                              GpStatus* st, cudaStream_t stream);

@@ -5,18 +5,24 @@
 //
 // CTA = 128 test points. Z = Phi_* W^T (128 x M) is accumulated in TMEM 512
 // columns at a time ("super-tile" of four 128-column blocks of W's rows).
-// For every 32-column chunk of Phi_*:
-//   warps 0-3  producers: load the test points' table window rows, form the
-//              Phi_* chunk (float32), add its contribution to the mean
-//              (float32 products, float64 running sum), split it into bf16
-//              hi/lo in the K-major core-matrix layout and publish it;
-//   warp 5     loads the matching packed hi/lo blocks of W with one bulk
-//              (TMA) copy per chunk;
+// For every 32-column chunk of Phi_* a pipeline stage holds the chunk's
+// table window (the rows phi_d(x*_{.j}) its columns touch, for the CTA's
+// test points), the chunk's column -> window-row map, the packed hi/lo
+// blocks of W, and the generated hi/lo tile of Phi_*:
+//   warp 5     (all lanes) copies the window rows, the map and the W blocks
+//              with 1-D bulk (TMA) copies that complete on one mbarrier;
+//   warps 0-3  producers: form the Phi_* chunk in float32 (one test point
+//              per thread, p a compile-time constant for p <= 4), add its
+//              contribution to the mean (float32 products with a float32
+//              copy of c, float64 running sum), split it into bf16 hi/lo in
+//              the K-major core-matrix layout and publish it;
 //   warp 4     issues hi*hi + hi*lo + lo*hi MMAs (M=128, N=128, K=16) into
 //              each block's TMEM accumulator, skipping blocks where W is zero
 //              (W is lower triangular).
 // After a super-tile, warps 0-3 read their rows of Z from TMEM and add the
-// squares into the variance.
+// squares into the variance. Every wait is bounded; a warp decides with a
+// vote, so tcgen05 loads stay warp-uniform and no CTA-wide barrier is left
+// waiting for a warp that gave up.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
 
@@ -29,54 +35,24 @@ constexpr int SUPER = PREDTC_SUPER; // 4 blocks in TMEM
 constexpr int STAGES = 2;
 constexpr int A_BYTES = TT * BK * 2;         // 8 KB per hi or lo tile
 constexpr int WB_BYTES = KB * BK * 2;        // 8 KB per hi or lo block of W
-constexpr int STAGE_BYTES = 2 * A_BYTES + SUPER * 2 * WB_BYTES;  // 80 KB
+constexpr int WIN_OFF = 2 * A_BYTES + SUPER * 2 * WB_BYTES;  // 80 KB: window after A and W
 constexpr uint32_t LBO = 128;
 constexpr uint32_t SBO = (BK / 8) * 128;     // 512
 constexpr int NPROD = 128;
 constexpr int NTHREADS = NPROD + 64;
-constexpr int WBUF = 3;                      // window ring: chunks prefetched two ahead
+constexpr unsigned FULLMASK = 0xffffffffu;
 
-struct SmemP {
-    uint8_t* stage;
-    float* win;               // WBUF x maxrows x TT: window rows of the prefetched chunks
-    int* cr;                  // WBUF x crp4: column -> window-row map of those chunks
-    uint64_t* full;           // producers' Phi_* tile is ready (count NPROD)
-    uint64_t* wfull;          // the W bulk copy has landed (count 1 + tx bytes)
-    uint64_t* empty;
-    uint64_t* accf;
-    uint64_t* tfree;
-    uint32_t* tmem_base;
-};
+// Stage: [A hi | A lo | W blocks (hi, lo) x SUPER | window (maxrows + 1 rows
+// of TT floats; the last row is zero) | column map (crp4 ints)], 1 KB aligned.
+__host__ __device__ inline uint32_t stage_bytes(int maxrows, int crp4) {
+    const uint32_t end = WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4 + (uint32_t)crp4 * 4;
+    return (end + 1023u) & ~1023u;
+}
+__host__ __device__ inline uint32_t map_off(int maxrows) { return WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4; }
 
-__host__ __device__ inline size_t smem_p_layout(int maxrows, int crp4, char* base, SmemP* L) {
-    size_t off = 0;
-    auto take = [&](size_t bytes, size_t align) {
-        off = (off + align - 1) / align * align;
-        size_t o = off;
-        off += bytes;
-        return o;
-    };
-    size_t oS = take((size_t)STAGES * STAGE_BYTES, 1024);
-    size_t oW = take(sizeof(float) * WBUF * maxrows * TT, 16);
-    size_t oC = take(sizeof(int) * WBUF * crp4, 16);
-    size_t oF = take(sizeof(uint64_t) * STAGES, 8);
-    size_t oX = take(sizeof(uint64_t) * STAGES, 8);
-    size_t oE = take(sizeof(uint64_t) * STAGES, 8);
-    size_t oA = take(sizeof(uint64_t), 8);
-    size_t oR = take(sizeof(uint64_t), 8);
-    size_t oM = take(sizeof(uint32_t), 8);
-    if (L) {
-        L->stage = (uint8_t*)(base + oS);
-        L->win = (float*)(base + oW);
-        L->cr = (int*)(base + oC);
-        L->full = (uint64_t*)(base + oF);
-        L->wfull = (uint64_t*)(base + oX);
-        L->empty = (uint64_t*)(base + oE);
-        L->accf = (uint64_t*)(base + oA);
-        L->tfree = (uint64_t*)(base + oR);
-        L->tmem_base = (uint32_t*)(base + oM);
-    }
-    return off + 1024;
+// barriers after the stages: full[S], wfull[S], empty[S], accf, tfree, tmem base
+__host__ __device__ inline size_t smem_bytes(int maxrows, int crp4) {
+    return 1024 + (size_t)STAGES * stage_bytes(maxrows, crp4) + 8 * (3 * STAGES + 2) + 8;
 }
 
 // number of 32-column chunks of Phi_* that meet the blocks b0 .. b0+nblk-1
@@ -86,19 +62,60 @@ __host__ __device__ inline int super_chunks(int M, int b0, int nblk) {
     return (mend + BK - 1) / BK;
 }
 
+// Phi_* of eight columns for test point t: column kk is the product of the
+// window entries at the P float offsets map[kk * P + j] (+ t).
+template <int P>
+__device__ __forceinline__ void gen8(const float* win, const int* map, int p, int t, float* v) {
+    if constexpr (P > 0) {
+        int o[8 * P];
+#pragma unroll
+        for (int q = 0; q < 2 * P; ++q) {
+            const int4 w = reinterpret_cast<const int4*>(map)[q];
+            o[4 * q] = w.x;
+            o[4 * q + 1] = w.y;
+            o[4 * q + 2] = w.z;
+            o[4 * q + 3] = w.w;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            float x = win[o[kk * P] + t];
+#pragma unroll
+            for (int j = 1; j < P; ++j) x *= win[o[kk * P + j] + t];
+            v[kk] = x;
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            float x = win[map[kk * p] + t];
+            for (int j = 1; j < p; ++j) x *= win[map[kk * p + j] + t];
+            v[kk] = x;
+        }
+    }
+}
+
+template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     predict_tc_kernel(GpShape s, const float* __restrict__ tab, const uint8_t* __restrict__ Wpack,
-                      const int* __restrict__ cinfo, int maxrows, const double* __restrict__ cvec,
+                      const float* __restrict__ cf, const int* __restrict__ cinfo, int maxrows,
                       double sigma2, double* __restrict__ mean, double* __restrict__ var,
                       GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
-    __shared__ int s_ok[2];
-    char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1 KB alignment by offsetting the shared array itself (keeps the
+    // shared state space visible to the compiler)
+    char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int p = P > 0 ? P : s.p;
     const int maxrows4 = (maxrows + 3) & ~3;
-    const int crp4 = (BK * s.p + 3) & ~3;
+    const int crp4 = (BK * p + 3) & ~3;
     const int cstride = 4 + maxrows4 + crp4;
-    SmemP sm;
-    smem_p_layout(maxrows, crp4, base, &sm);
+    const uint32_t SB = stage_bytes(maxrows, crp4);
+    const uint32_t MAPO = map_off(maxrows);
+    uint8_t* stage = (uint8_t*)base;
+    uint64_t* full = (uint64_t*)(base + (size_t)STAGES * SB);
+    uint64_t* wfull = full + STAGES;
+    uint64_t* empty = wfull + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint64_t* tfree = accf + 1;
+    uint32_t* tmem_base = (uint32_t*)(tfree + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t t0 = (int64_t)blockIdx.x * TT;
@@ -108,19 +125,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (tid == 0) {
         for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&sm.full[i], NPROD);
-            mbar_init(&sm.wfull[i], 1);
-            mbar_init(&sm.empty[i], 1);
+            mbar_init(&full[i], NPROD);
+            mbar_init(&wfull[i], 1);
+            mbar_init(&empty[i], 1);
         }
-        mbar_init(sm.accf, 1);
-        mbar_init(sm.tfree, NPROD);
+        mbar_init(accf, 1);
+        mbar_init(tfree, NPROD);
         mbar_fence_init();
     }
-    if (warp == 4) tmem_alloc(sm.tmem_base, 512);
+    // the zero window row of every stage (columns beyond M map to it)
+    if (tid < NPROD)
+        for (int i = 0; i < STAGES; ++i)
+            reinterpret_cast<float*>(stage + (size_t)i * SB + WIN_OFF)[maxrows * TT + tid] = 0.f;
+    if (warp == 4) tmem_alloc(tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *sm.tmem_base;
+    const uint32_t tmem = *tmem_base;
 
     if (warp < 4) {
         // ------------------------------------------------------------ producers + epilogue
@@ -128,32 +149,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         double macc = 0.0, vacc = 0.0;
         bool ok = true;
         int gc = 0;
-        int nbc = 0;
-        const int wsz = maxrows * TT;
-        // prefetch cursor over the (super-tile, chunk) sequence, WBUF-1 chunks ahead
-        int pf_sup = 0, pf_c = 0, pf_q = 0;
-        auto prefetch_next = [&]() {
-            if (pf_sup < nsuper) {
-                const int buf = pf_q % WBUF;
-                const int* ci = cinfo + (int64_t)pf_c * cstride;
-                const int nrows = __ldg(ci);
-                for (int e = tid; e < nrows * (TT / 4); e += NPROD) {
-                    const int r = e / (TT / 4), v = e % (TT / 4);
-                    const int row = __ldg(ci + 4 + r);
-                    cp_async16(sm.win + buf * wsz + r * TT + 4 * v, tab + (int64_t)row * s.Npad + t0 + 4 * v);
-                }
-                for (int e = tid; e < crp4 / 4; e += NPROD)
-                    cp_async16(sm.cr + buf * crp4 + 4 * e, ci + 4 + maxrows4 + 4 * e);
-                if (++pf_c >= super_chunks(s.M, pf_sup * SUPER, min(SUPER, nblocks - pf_sup * SUPER))) {
-                    ++pf_sup;
-                    pf_c = 0;
-                }
-            }
-            cp_async_commit();  // one group per chunk, possibly empty
-            ++pf_q;
-        };
-        prefetch_next();
-        prefetch_next();
         for (int sup = 0; sup < nsuper && ok; ++sup) {
             const int b0 = sup * SUPER;
             const int nblk = min(SUPER, nblocks - b0);
@@ -161,50 +156,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool last = (sup == nsuper - 1);
             for (int c = 0; c < nch; ++c, ++gc) {
                 const int stg = gc % STAGES;
-                const int buf = gc % WBUF;
-                cp_async_wait<1>();  // this thread's copies for chunk gc have landed
-                // One barrier per chunk (one thread waits for the stage and
-                // broadcasts; the two flags alternate so a flag is rewritten
-                // only after every reader passed a later barrier): all copies
-                // of chunk gc are visible and chunk gc-1 has been consumed.
-                const int slot = nbc++ & 1;
-                if (tid == 0) {
-                    int fine = 1;
-                    if (gc >= STAGES && !mbar_wait(&sm.empty[stg], ((gc / STAGES) - 1) & 1)) {
-                        gp_set_status(st, GP_ETIMEOUT, 11);
-                        fine = 0;
-                    }
-                    s_ok[slot] = fine;
-                }
-                named_bar_sync(1, NPROD);
-                if (!s_ok[slot]) {
+                // the stage's A tile is free (MMAs of chunk gc - STAGES done)
+                // and its window and map have landed
+                bool w = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
+                w = w && mbar_wait(&wfull[stg], (gc / STAGES) & 1);
+                if (!__all_sync(FULLMASK, w)) {
+                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 11);
                     ok = false;
                     break;
                 }
-                prefetch_next();
-                const float* win = sm.win + buf * wsz;
-                const int* cr = sm.cr + buf * crp4;
-                uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
+                uint8_t* sb = stage + (size_t)stg * SB;
+                const float* win = reinterpret_cast<const float*>(sb + WIN_OFF);
+                const int* map = reinterpret_cast<const int*>(sb + MAPO);
                 float mpart = 0.f;
 #pragma unroll
                 for (int g = 0; g < BK / 8; ++g) {
                     float v[8];
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const int* crr = cr + (g * 8 + kk) * s.p;
-                        float x = 0.f;
-                        if (crr[0] >= 0) {
-                            x = win[crr[0] * TT + t];
-                            for (int j = 1; j < s.p; ++j) x *= win[crr[j] * TT + t];
-                        }
-                        v[kk] = x;
-                    }
+                    gen8<P>(win, map + g * 8 * p, p, t, v);
                     if (last) {
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const int m = c * BK + g * 8 + kk;
-                            if (m < s.M) mpart = fmaf(v[kk], (float)__ldg(cvec + m), mpart);
-                        }
+                        const float4 ca = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8));
+                        const float4 cb = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8 + 4));
+                        mpart = fmaf(v[0], ca.x, mpart);
+                        mpart = fmaf(v[1], ca.y, mpart);
+                        mpart = fmaf(v[2], ca.z, mpart);
+                        mpart = fmaf(v[3], ca.w, mpart);
+                        mpart = fmaf(v[4], cb.x, mpart);
+                        mpart = fmaf(v[5], cb.y, mpart);
+                        mpart = fmaf(v[6], cb.z, mpart);
+                        mpart = fmaf(v[7], cb.w, mpart);
                     }
                     uint32_t h[4], l[4];
 #pragma unroll
@@ -213,43 +192,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<uint4*>(sb + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                macc += (double)mpart;
+                if (last) macc += (double)mpart;
                 fence_proxy_async_smem();
-                mbar_arrive(&sm.full[stg]);
+                mbar_arrive(&full[stg]);
             }
             if (!ok) break;
-            // epilogue of this super-tile: rows of Z from TMEM. One thread
-            // waits and broadcasts, so all producers take the same branch.
-            const int slot = nbc++ & 1;
-            if (tid == 0) {
-                int fine = mbar_wait(sm.accf, sup & 1) ? 1 : 0;
-                if (!fine) gp_set_status(st, GP_ETIMEOUT, 12);
-                s_ok[slot] = fine;
-            }
-            named_bar_sync(1, NPROD);
-            const bool got = s_ok[slot] != 0;
-            tc_fence_after();
-            if (got) {
-                for (int bb = 0; bb < nblk; ++bb) {
-#pragma unroll 1
-                    for (int ch = 0; ch < KB / 32; ++ch) {
-                        float v[32];
-                        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + bb * KB + ch * 32, v);
-                        float q = 0.f;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) q = fmaf(v[i], v[i], q);
-                        vacc += (double)q;
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(sm.tfree);
+            // epilogue of this super-tile: rows of Z from TMEM
+            const bool got = __all_sync(FULLMASK, mbar_wait(accf, sup & 1));
             if (!got) {
+                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 12);
                 ok = false;
                 break;
             }
+            tc_fence_after();
+            for (int bb = 0; bb < nblk; ++bb) {
+#pragma unroll 1
+                for (int ch = 0; ch < KB / 32; ++ch) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + bb * KB + ch * 32, v);
+                    float q = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) q = fmaf(v[i], v[i], q);
+                    vacc += (double)q;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tfree);
         }
-        cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (ok && t0 + t < s.N) {
             mean[t0 + t] = macc;
             if (var) var[t0 + t] = sigma2 * vacc;
@@ -258,28 +227,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(TT, KB);
-            const uint32_t sbase = smem_u32(sm.stage);
+            const uint32_t sbase = smem_u32(stage);
             int gc = 0;
             bool ok = true;
             for (int sup = 0; sup < nsuper && ok; ++sup) {
                 const int b0 = sup * SUPER;
                 const int nblk = min(SUPER, nblocks - b0);
                 const int nch = super_chunks(s.M, b0, nblk);
-                if (sup > 0 && !mbar_wait(sm.tfree, (sup - 1) & 1)) {
+                if (sup > 0 && !mbar_wait(tfree, (sup - 1) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 13);
                     break;
                 }
                 tc_fence_after();
                 for (int c = 0; c < nch; ++c, ++gc) {
                     const int stg = gc % STAGES;
-                    if (!mbar_wait(&sm.full[stg], (gc / STAGES) & 1) ||
-                        !mbar_wait(&sm.wfull[stg], (gc / STAGES) & 1)) {
+                    if (!mbar_wait(&full[stg], (gc / STAGES) & 1) ||
+                        !mbar_wait(&wfull[stg], (gc / STAGES) & 1)) {
                         gp_set_status(st, GP_ETIMEOUT, 14);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_hi = sbase + stg * STAGE_BYTES;
+                    const uint32_t a_hi = sbase + stg * SB;
                     const uint32_t a_lo = a_hi + A_BYTES;
                     const uint32_t wbase = a_hi + 2 * A_BYTES;
                     for (int bb = 0; bb < nblk; ++bb) {
@@ -299,39 +268,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             mma_bf16(d, dAl, dBh, idesc, 1u);
                         }
                     }
-                    mma_commit(&sm.empty[stg]);
+                    mma_commit(&empty[stg]);
                 }
-                mma_commit(sm.accf);
+                mma_commit(accf);
             }
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------------------ W loader (TMA)
-        if (lane == 0) {
-            int gc = 0;
-            bool ok = true;
-            for (int sup = 0; sup < nsuper && ok; ++sup) {
-                const int b0 = sup * SUPER;
-                const int nblk = min(SUPER, nblocks - b0);
-                const int nch = super_chunks(s.M, b0, nblk);
-                for (int c = 0; c < nch; ++c, ++gc) {
-                    const int stg = gc % STAGES;
-                    if (gc >= STAGES && !mbar_wait(&sm.empty[stg], ((gc / STAGES) - 1) & 1)) {
-                        gp_set_status(st, GP_ETIMEOUT, 15);
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t bytes = (uint32_t)nblk * 2 * WB_BYTES;
-                    uint8_t* dst = sm.stage + (size_t)stg * STAGE_BYTES + 2 * A_BYTES;
-                    const uint8_t* src = Wpack + ((size_t)c * KBtot + b0) * 2 * WB_BYTES;
-                    mbar_arrive_expect_tx(&sm.wfull[stg], bytes);
-                    bulk_g2s(dst, src, bytes, &sm.wfull[stg]);
+        // ------------------------------------------------------------ loader (bulk copies, all lanes)
+        int gc = 0;
+        bool ok = true;
+        for (int sup = 0; sup < nsuper && ok; ++sup) {
+            const int b0 = sup * SUPER;
+            const int nblk = min(SUPER, nblocks - b0);
+            const int nch = super_chunks(s.M, b0, nblk);
+            for (int c = 0; c < nch; ++c, ++gc) {
+                const int stg = gc % STAGES;
+                const int* ci = cinfo + (int64_t)c * cstride;
+                const int nrows = __ldg(ci);
+                // table rows of this lane's window rows (read before the wait)
+                const int row0 = lane < nrows ? __ldg(ci + 4 + lane) : 0;
+                const bool e = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
+                if (!__all_sync(FULLMASK, e)) {
+                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 15);
+                    ok = false;
+                    break;
+                }
+                uint8_t* sb = stage + (size_t)stg * SB;
+                const uint32_t wbytes = (uint32_t)nblk * 2 * WB_BYTES;
+                if (lane == 0)
+                    mbar_arrive_expect_tx(&wfull[stg], wbytes + (uint32_t)nrows * TT * 4 + (uint32_t)crp4 * 4);
+                __syncwarp();
+                if (lane == 0)
+                    bulk_g2s(sb + 2 * A_BYTES, Wpack + ((size_t)c * KBtot + b0) * 2 * WB_BYTES, wbytes,
+                             &wfull[stg]);
+                if (lane == 1) bulk_g2s(sb + MAPO, ci + 4 + maxrows4, (uint32_t)crp4 * 4, &wfull[stg]);
+                for (int r = lane; r < nrows; r += 32) {
+                    const int row = r < 32 ? row0 : __ldg(ci + 4 + r);
+                    bulk_g2s(sb + WIN_OFF + (size_t)r * TT * 4, tab + (int64_t)row * s.Npad + t0, TT * 4,
+                             &wfull[stg]);
                 }
             }
-            // before leaving, wait (bounded) for the copies this thread issued
-            for (int g = gc - STAGES; g < gc; ++g)
-                if (g >= 0) mbar_wait(&sm.wfull[g % STAGES], (g / STAGES) & 1);
         }
+        // before leaving, wait (bounded) for the copies this warp issued
+        for (int g = gc - STAGES; g < gc; ++g)
+            if (g >= 0) mbar_wait(&wfull[g % STAGES], (g / STAGES) & 1);
         __syncwarp();
     }
     tc_fence_before();
@@ -344,12 +325,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // W (M x M float64, lower) -> packed bf16 hi/lo blocks: for chunk c (32
 // columns m) and block b (128 rows k), hi then lo, each 128 x 32 in the
-// K-major core-matrix layout of the MMA's B operand.
-__global__ void pack_w_kernel(const double* __restrict__ W, int M, int Mpad, uint8_t* __restrict__ out) {
+// K-major core-matrix layout of the MMA's B operand. Thread idx < Mpad also
+// writes the float32 copy of c (zero beyond M) that follows the blocks.
+__global__ void pack_w_kernel(const double* __restrict__ W, const double* __restrict__ cvec, int M,
+                              int Mpad, uint8_t* __restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int KBt = Mpad / KB;
     const int nch = Mpad / BK;
     const int64_t total = (int64_t)nch * KBt * KB * (BK / 8);
+    if (idx < Mpad) {
+        float* cf = reinterpret_cast<float*>(out + (size_t)4 * Mpad * Mpad);
+        cf[idx] = idx < M ? (float)cvec[idx] : 0.f;
+    }
     if (idx >= total) return;
     const int g = (int)(idx % (BK / 8));
     const int r = (int)((idx / (BK / 8)) % KB);
@@ -373,15 +360,16 @@ __global__ void pack_w_kernel(const double* __restrict__ W, int M, int Mpad, uin
 
 }  // namespace
 
+// packed hi/lo blocks of W (4 Mpad^2 bytes), then c in float32 (Mpad floats)
 size_t predtc_wpack_bytes(int M) {
     const size_t Mpad = (size_t)gp_round_up(M, KB);
-    return 4 * Mpad * Mpad;
+    return 4 * Mpad * Mpad + 4 * Mpad;
 }
 
-void launch_pack_w_bf16x3(const double* W, int M, uint16_t* Wpack, cudaStream_t stream) {
+void launch_pack_w_bf16x3(const double* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream) {
     const int Mpad = (int)gp_round_up(M, KB);
     const int64_t total = (int64_t)(Mpad / BK) * (Mpad / KB) * KB * (BK / 8);
-    pack_w_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(W, M, Mpad, (uint8_t*)Wpack);
+    pack_w_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(W, c, M, Mpad, (uint8_t*)Wpack);
 }
 
 namespace {
@@ -396,9 +384,11 @@ size_t predtc_cinfo_ints(const GpShape& s) {
 }
 
 // Per 32-column chunk c of Phi_*: [nrows, 0, 0, 0][table row of each window
-// row][window row of (column, dimension), -1 beyond M], padded to 16 bytes.
+// row][float offset (window row x TT) of each (column, dimension); columns
+// beyond M point at the zero row maxrows], padded to 16 bytes.
 void predtc_build_cinfo(const GpShape& s, int* out) {
-    const int maxrows4 = (predtc_maxrows(s) + 3) & ~3;
+    const int maxrows = predtc_maxrows(s);
+    const int maxrows4 = (maxrows + 3) & ~3;
     const int cs = predtc_cstride(s);
     const int nch = (s.M + BK - 1) / BK;
     for (int c = 0; c < nch; ++c) {
@@ -411,25 +401,40 @@ void predtc_build_cinfo(const GpShape& s, int* out) {
         for (int cc = 0; cc < BK; ++cc)
             for (int j = 0; j < s.p; ++j) {
                 const int m = c * BK + cc;
-                ci[4 + maxrows4 + cc * s.p + j] = m < s.M ? window_row(s, w, j, m) : -1;
+                ci[4 + maxrows4 + cc * s.p + j] = (m < s.M ? window_row(s, w, j, m) : maxrows) * TT;
             }
     }
 }
 
 size_t predtc_smem_bytes(const GpShape& s) {
-    return smem_p_layout(predtc_maxrows(s), (BK * s.p + 3) & ~3, nullptr, nullptr);
+    return smem_bytes(predtc_maxrows(s), (BK * s.p + 3) & ~3);
 }
 
-cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
-                              const int* cinfo, const double* c, double sigma2, double* mean,
-                              double* var, GpStatus* st, cudaStream_t stream) {
+namespace {
+template <int P>
+cudaError_t predict_tc_launch(const GpShape& s, const float* tab, const uint16_t* Wpack, const int* cinfo,
+                              double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream) {
     const int maxrows = predtc_maxrows(s);
     const size_t smem = predtc_smem_bytes(s);
     if (smem > (227 - 2) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
-    cudaError_t e = gp_allow_max_smem((const void*)predict_tc_kernel);
+    cudaError_t e = gp_allow_max_smem((const void*)predict_tc_kernel<P>);
     if (e != cudaSuccess) return e;
+    const size_t Mpad = (size_t)gp_round_up(s.M, KB);
+    const float* cf = reinterpret_cast<const float*>((const uint8_t*)Wpack + 4 * Mpad * Mpad);
     const unsigned grid = (unsigned)(s.Npad / TT);
-    predict_tc_kernel<<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, cinfo, maxrows,
-                                                        c, sigma2, mean, var, st);
+    predict_tc_kernel<P><<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, cf, cinfo, maxrows,
+                                                           sigma2, mean, var, st);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack, const int* cinfo,
+                              double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream) {
+    switch (s.p) {
+        case 1: return predict_tc_launch<1>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
+        case 2: return predict_tc_launch<2>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
+        case 3: return predict_tc_launch<3>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
+        case 4: return predict_tc_launch<4>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
+        default: return predict_tc_launch<0>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
+    }
 }
