@@ -175,11 +175,10 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             gp_note_launches(1);
         }
     } else {
-        float *tab, *ypad;
+        float* tabc;
         float2* Gpart;
         double* bpart;
-        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
-        if ((rc = sc.get(&ypad, (size_t)s.Npad))) return rc;
+        if ((rc = sc.get(&tabc, syrktc_table_floats(s)))) return rc;
         const int T = s.Mpad / SYRKTC_TM;
         const int npairs = T * (T + 1) / 2;
         int nsplit;
@@ -189,22 +188,23 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
         int* colexp;
+        signed char* ebx;
         if ((rc = sc.get(&tmax, (size_t)s.p * s.n))) return rc;
         if ((rc = sc.get(&tmaxb, (size_t)s.p * s.n * ((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
         if ((rc = sc.get(&colexp, (size_t)s.Mpad))) return rc;
+        if ((rc = sc.get(&ebx, syrktc_ebx_bytes(s)))) return rc;
         {
             GpProf pf("eig_tables", stream);
-            launch_eig_tables_f32(s, Xd, yd, tab, st, stream);
-            pad_y_kernel<float><<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(yd, s.N, s.Npad, ypad);
-            launch_table_absmax(s, tab, tmaxb, tmax, stream);
-            gp_note_launches(3);
+            launch_eig_tables_chunked(s, Xd, yd, tabc, st, stream);
+            launch_table_absmax(s, tabc, tmaxb, tmax, stream);
+            gp_note_launches(2);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tab, tmaxb, tmax, ypad, nsplit, rps, Gpart, bpart, colexp,
+            cudaError_t e = launch_syrk_tc(s, tabc, tmaxb, tmax, nsplit, rps, Gpart, bpart, colexp, ebx,
                                            st, stream);
             if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
-            gp_note_launches(1);
+            gp_note_launches(2);
         }
         {
             GpProf pf("assemble", stream);

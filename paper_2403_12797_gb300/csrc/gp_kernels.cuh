@@ -3,6 +3,9 @@
 
 #include "gp_common.cuh"
 
+constexpr int SYRKTC_TM = 128;  // tile of the mixed-precision Gram
+constexpr int SYRKTC_BK = 32;   // rows per pipeline chunk of it
+
 // ---- eigenfunction tables (gp_tables.cu) ------------------------------------
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
                            GpStatus* st, cudaStream_t stream);
@@ -12,9 +15,16 @@ void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, f
 // Rows per block of the mixed-precision Gram (exact tensor-core sums) and of
 // the per-block table maxima.
 constexpr int GP_TAB_BLOCK = 512;
-// tmaxb[b * p*n + j*n + k] = max |tab[j][k][i]| over rows i of block b and
+// Chunk-major float32 table of the mixed-precision Gram: chunk q of 32 rows
+// holds table row R = j*n + k at tabc[q*RC + R*SYRKTC_WS + i%32] and y in row
+// p*n, RC = (p*n + 1) * SYRKTC_WS (row stride 36 floats, 4 of them zero).
+constexpr int SYRKTC_WS = 36;
+size_t syrktc_table_floats(const GpShape& s);
+void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
+                               GpStatus* st, cudaStream_t stream);
+// tmaxb[b * p*n + j*n + k] = max |tabc row j*n+k| over rows i of block b and
 // tmax[j*n + k] = max over all rows (float bits); zeroes tmax first.
-void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmaxb, unsigned int* tmax,
+void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmaxb, unsigned int* tmax,
                          cudaStream_t stream);
 
 // ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
@@ -26,16 +36,16 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
                           int64_t rows_per_split, double* Gpart, double* bpart, cudaStream_t stream);
 
 // ---- bf16x3 tensor-core Gram (gp_syrk_tc.cu) ---------------------------------
-constexpr int SYRKTC_TM = 128;
-constexpr int SYRKTC_BK = 32;
 size_t syrktc_smem_bytes(const GpShape& s);
+// bytes of the per-block column exponents the launch needs (ebx argument)
+size_t syrktc_ebx_bytes(const GpShape& s);
 // Gpart holds column-scaled partial tiles as float pairs hi + lo (units
 // 2^(14 - E_m - E_m')),
-// colexp[m] = E_m (Mpad), bpart the unscaled float64 Phi^T y partials.
-// rows_per_split must be a multiple of GP_TAB_BLOCK.
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
-                           const unsigned int* tmax, const float* ypad, int nsplit,
-                           int64_t rows_per_split, float2* Gpart, double* bpart, int* colexp,
+// colexp[m] = E_m (Mpad, written here), bpart the unscaled float64 Phi^T y
+// partials. rows_per_split must be a multiple of GP_TAB_BLOCK.
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
+                           const unsigned int* tmax, int nsplit, int64_t rows_per_split,
+                           float2* Gpart, double* bpart, int* colexp, signed char* ebx,
                            GpStatus* st, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------

@@ -30,17 +30,23 @@
 // Representation error: |w - s1 - lo| <= 2^-12 (2^-19 of the block bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
-// of the rows:
-//   warps 0-15 producers (one 8-column core group each): copy the tables'
-//              window rows for the chunk into shared memory, form Phi for
+// of the rows, pipelined over chunks of 32 rows through nst stages:
+//   warp 17    (all lanes) copies the chunk's table window -- the tile's
+//              rows of the chunk-major table, at most two contiguous ranges
+//              per dimension and tile, plus y -- with 1-D bulk (TMA) copies
+//              that complete on the stage's mbarrier;
+//   warps 0-15 producers (one 8-column core group each): form Phi for
 //              column tiles I and J in the K-major core-matrix layout
-//              (8 columns x 16 bytes), split, publish the stage; J == 0 CTAs
-//              also accumulate b_I = Phi_I^T y (float32, warp-shuffle
-//              reduction). They drain TMEM and write the (scaled) partial
-//              tile at the end.
+//              (8 columns x 16 bytes) from the window, split, publish the
+//              stage; J == 0 CTAs also accumulate b_I = Phi_I^T y (float32,
+//              warp-shuffle reduction). They drain TMEM after each block
+//              and write the (scaled) partial tile at the end.
 //   warp 16    allocates TMEM and issues the MMAs (one elected lane):
 //              4 x (128 x 128 x 16) per 16 rows; tcgen05.commit frees stages
-//              and signals finished blocks.
+//              (A tiles and windows) and signals finished blocks.
+// Every warp waits on mbarriers by itself (bounded, decided by a warp vote):
+// there is no CTA-wide barrier inside the pipeline. The block exponents E_m
+// per 512-row block and the global ones come from a small kernel run first.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
@@ -49,43 +55,40 @@ namespace {
 
 constexpr int TM = SYRKTC_TM;              // 128
 constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
+constexpr int WS = SYRKTC_WS;              // floats per window row (36: bank-conflict padding)
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
-constexpr int WBUF = 3;                    // table-window ring (chunks prefetched ahead)
-constexpr int BLOCK_CHUNKS = 16;           // 512 rows per exact TMEM block
+constexpr int BLOCK_CHUNKS = GP_TAB_BLOCK / BK;  // 16 chunks = 512 rows per exact TMEM block
 constexpr int FLUSH_BLOCKS = 4;            // blocks summed in float32 registers between flushes
-constexpr int WSTRIDE = BK + 4;            // floats per window row (bank-conflict padding)
-constexpr int TILE_BYTES = TM * BK * 2;    // one bf16 operand tile: 8 KB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A s2, B s1, B s2
+constexpr int TILE_BYTES = TM * BK * 2;    // one 16-bit operand tile: 8 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A lo, B s1, B lo
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
 constexpr uint32_t SBO = (BK / 8) * 128;   // 8-row groups
 constexpr int NPROD = 512;                 // 16 producer warps: one 8-column core group each
 constexpr int NPW = NPROD / 32;
 constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain (32)
 constexpr int MMA_WARP = NPW;
-constexpr int NTHREADS = NPROD + 32;
+constexpr int NTHREADS = NPROD + 64;
 constexpr uint32_t TMEM_COLS = 512;        // 2 buffers x (acc1 | acc2)
+constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct SmemTC {
-    uint8_t* stage;       // STAGES x STAGE_BYTES (1024-aligned)
-    float* winI;          // WBUF x maxrows x WSTRIDE
-    float* winJ;
-    float* yv;            // WBUF x BK
-    float* scI;           // 2 x TM: block column scales 2^(7 - E_blk), by block parity
-    float* scJ;
-    float* muI;           // 2 x TM: drain multipliers 2^(E_blk - E_glob)
-    float* muJ;
+    uint8_t* stage;       // nst x STAGE_BYTES (1024-aligned)
+    float* win;           // nst x (2 maxrows + 1) x WS: windows of tiles I, J and y
     int* egI;             // TM: global column exponents E_glob
     int* egJ;
-    int* trI;
-    int* trJ;
-    unsigned short* crI;  // TM x p
+    unsigned short* crI;  // TM x p: window row of (column, dimension)
     unsigned short* crJ;
-    uint64_t* full;       // STAGES
-    uint64_t* empty;      // STAGES
+    int* rng;             // copy ranges (table row, rows, window row), 3 ints each
+    uint64_t* full;       // STAGES: producers' tiles published (count NPROD)
+    uint64_t* tfull;      // STAGES: window landed (count 1 + tx bytes)
+    uint64_t* empty;      // STAGES: MMAs of the stage done
     uint64_t* accf;       // 2: block finished in TMEM buffer u
     uint64_t* drained;    // 2: TMEM buffer u has been read back
     uint32_t* tmem_base;
 };
+
+__host__ __device__ inline int max_ranges(int p) { return 4 * p + 1; }
+__host__ __device__ inline int win_floats(int maxrows) { return (2 * maxrows + 1) * WS; }
 
 __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, char* base, SmemTC* L) {
     size_t off = 0;
@@ -96,40 +99,28 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, ch
         return o;
     };
     size_t oS = take((size_t)nst * STAGE_BYTES, 1024);
-    size_t oWI = take(sizeof(float) * WBUF * maxrows * WSTRIDE, 16);
-    size_t oWJ = take(sizeof(float) * WBUF * maxrows * WSTRIDE, 16);
-    size_t oY = take(sizeof(float) * WBUF * BK, 16);
-    size_t oSI = take(sizeof(float) * 2 * TM, 16);
-    size_t oSJ = take(sizeof(float) * 2 * TM, 16);
-    size_t oMI = take(sizeof(float) * 2 * TM, 16);
-    size_t oMJ = take(sizeof(float) * 2 * TM, 16);
+    size_t oW = take(sizeof(float) * nst * win_floats(maxrows), 16);
     size_t oEI = take(sizeof(int) * TM, 16);
     size_t oEJ = take(sizeof(int) * TM, 16);
-    size_t oTI = take(sizeof(int) * maxrows, 16);
-    size_t oTJ = take(sizeof(int) * maxrows, 16);
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
     size_t oCJ = take(sizeof(unsigned short) * TM * p, 16);
+    size_t oR = take(sizeof(int) * 3 * max_ranges(p), 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
+    size_t oX = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
     size_t oA = take(sizeof(uint64_t) * 2, 8);
     size_t oD = take(sizeof(uint64_t) * 2, 8);
     size_t oT = take(sizeof(uint32_t), 8);
     if (L) {
         L->stage = (uint8_t*)(base + oS);
-        L->winI = (float*)(base + oWI);
-        L->winJ = (float*)(base + oWJ);
-        L->yv = (float*)(base + oY);
-        L->scI = (float*)(base + oSI);
-        L->scJ = (float*)(base + oSJ);
-        L->muI = (float*)(base + oMI);
-        L->muJ = (float*)(base + oMJ);
+        L->win = (float*)(base + oW);
         L->egI = (int*)(base + oEI);
         L->egJ = (int*)(base + oEJ);
-        L->trI = (int*)(base + oTI);
-        L->trJ = (int*)(base + oTJ);
         L->crI = (unsigned short*)(base + oCI);
         L->crJ = (unsigned short*)(base + oCJ);
+        L->rng = (int*)(base + oR);
         L->full = (uint64_t*)(base + oF);
+        L->tfull = (uint64_t*)(base + oX);
         L->empty = (uint64_t*)(base + oE);
         L->accf = (uint64_t*)(base + oA);
         L->drained = (uint64_t*)(base + oD);
@@ -152,61 +143,57 @@ __device__ __forceinline__ int column_exp(const GpShape& s, const unsigned int* 
     return E < -100 ? -100 : E;
 }
 
-// Window rows, column -> window-row map and global column exponents of one tile.
-__device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0,
-                           const unsigned int* __restrict__ tmax, int* tr, unsigned short* cr,
-                           int* eg, int* colexp_out, int tid, int nthr) {
-    for (int r = tid; r < w.nrows; r += nthr) tr[r] = window_table_row(s, w, r);
-    for (int e = tid; e < TM * s.p; e += nthr) {
-        int c = e / s.p, j = e % s.p;
-        int m = m0 + c;
-        cr[e] = (unsigned short)(m < s.M ? window_row(s, w, j, m) : 0xFFFF);
-    }
-    for (int c = tid; c < TM; c += nthr) {
-        const int m = m0 + c;
-        const int E = m < s.M ? column_exp(s, tmax, m) : 0;
-        eg[c] = E;
-        if (colexp_out && m < s.M) colexp_out[m] = E;
+// Column exponents: ebx[b * Mpad + m] = E_m of 512-row block b (b < nblk),
+// colexp[m] = the global E_m (blockIdx.y == nblk); 0 for padding columns.
+__global__ void colexp_kernel(GpShape s, const unsigned int* __restrict__ tmaxb,
+                              const unsigned int* __restrict__ tmax, int nblk, int* __restrict__ colexp,
+                              signed char* __restrict__ ebx) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= s.Mpad) return;
+    const int b = blockIdx.y;
+    if (b == nblk) {
+        colexp[m] = m < s.M ? column_exp(s, tmax, m) : 0;
+    } else {
+        const int E = m < s.M ? column_exp(s, tmaxb + (int64_t)b * s.p * s.n, m) : 0;
+        ebx[(int64_t)b * s.Mpad + m] = (signed char)(E > 127 ? 127 : E);
     }
 }
 
-// Column scales of one tile for the 512-row block whose table maxima are tmb:
-// quantisation scale 2^(7 - E_blk) (|Phi * scale| <= 128 inside the block) and
-// the drain multiplier 2^(E_blk - E_glob) <= 1 back to the global scaling.
-__device__ __forceinline__ void block_scales(const GpShape& s, int m0, const unsigned int* __restrict__ tmb,
-                                             const int* eg, float* sc, float* mu, int c) {
-    const int m = m0 + c;
-    if (m >= s.M) {
-        sc[c] = 0.f;
-        mu[c] = 0.f;
-        return;
-    }
-    const int E = column_exp(s, tmb, m);
-    sc[c] = ldexpf(1.f, 7 - E);
-    mu[c] = ldexpf(1.f, E - eg[c]);
-}
+// 2^k for -126 <= k <= 127, exactly
+__device__ __forceinline__ float pow2i(int k) { return __int_as_float((127 + k) << 23); }
 
-// Start the asynchronous copy of the window rows (nrows x BK floats) of the
-// chunk starting at data row i0 into win (16-byte cp.async per thread).
-__device__ __forceinline__ void load_window_async(const GpShape& s, const float* __restrict__ tab,
-                                                  const int* tr, int nrows, int64_t i0, float* win,
-                                                  int tid) {
-    const int nv = nrows * (BK / 4);
-    for (int e = tid; e < nv; e += NPROD) {
-        const int r = e / (BK / 4), v = e % (BK / 4);
-        cp_async16(win + r * WSTRIDE + 4 * v, tab + (int64_t)tr[r] * s.Npad + i0 + 4 * v);
+// Copy ranges of one tile's window (thread 0): dimension j's window rows
+// are the digits first .. first+count-1 (mod n), i.e. at most two
+// contiguous runs of table rows j*n + digit.
+__device__ int tile_ranges(const GpShape& s, const TileWindow& w, int dst0, int* rng, int nr) {
+    for (int j = 0; j < s.p; ++j) {
+        const int cnt = w.count[j];
+        if (cnt <= 0) continue;
+        const int first = w.first[j];
+        const int run = min(cnt, s.n - first);
+        rng[3 * nr] = j * s.n + first;
+        rng[3 * nr + 1] = run;
+        rng[3 * nr + 2] = dst0 + w.base[j];
+        ++nr;
+        if (cnt > run) {
+            rng[3 * nr] = j * s.n;
+            rng[3 * nr + 1] = cnt - run;
+            rng[3 * nr + 2] = dst0 + w.base[j] + run;
+            ++nr;
+        }
     }
+    return nr;
 }
 
 // Phi values of one column for data rows 8g..8g+7 of the chunk: the product
 // over dimensions of the column's window rows, whose float offsets woff[j]
-// (window row x WSTRIDE) are held in registers; woff[0] < 0 marks a padding
+// (window row x WS) are held in registers; woff[0] < 0 marks a padding
 // column (m >= M). P = 0 takes p at run time and the offsets from the
 // column's window-row map crr in shared memory.
 template <int P>
 __device__ __forceinline__ void phi8(const float* win, const int* woff, const unsigned short* crr, int p,
                                      int g, float v[8]) {
-    const int o0 = (P > 0) ? woff[0] : (crr[0] == 0xFFFF ? -1 : crr[0] * WSTRIDE);
+    const int o0 = (P > 0) ? woff[0] : (crr[0] == 0xFFFF ? -1 : crr[0] * WS);
     if (o0 < 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = 0.f;
@@ -228,7 +215,7 @@ __device__ __forceinline__ void phi8(const float* win, const int* woff, const un
 #pragma unroll
         for (int j = 1; j < P; ++j) mul_row(woff[j]);
     } else {
-        for (int j = 1; j < p; ++j) mul_row(crr[j] * WSTRIDE);
+        for (int j = 1; j < p; ++j) mul_row(crr[j] * WS);
     }
 }
 
@@ -272,15 +259,13 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
 // P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise.
 template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    syrk_tc_kernel(GpShape s, const float* __restrict__ tab, const unsigned int* __restrict__ tmaxb,
-                   const unsigned int* __restrict__ tmax,
-                   const float* __restrict__ ypad, int64_t rps, int npairs, int maxrows, int nst,
-                   float2* __restrict__ Gpart, double* __restrict__ bpart,
-                   int* __restrict__ colexp, GpStatus* st) {
+    syrk_tc_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
+                   const int* __restrict__ colexp, int64_t rps, int npairs, int maxrows, int nst,
+                   float2* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
-    __shared__ int s_ok[2];
-    char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ int s_nrng;
+    char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     SmemTC sm;
     smem_tc_layout(maxrows, s.p, nst, base, &sm);
 
@@ -296,12 +281,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (r1 > s.Npad) r1 = s.Npad;
     const int nchunks = r0 < r1 ? (int)((r1 - r0) / BK) : 0;
     const int nblocks = (nchunks + BLOCK_CHUNKS - 1) / BLOCK_CHUNKS;
+    const int64_t RC = (int64_t)(s.p * s.n + 1) * WS;  // floats per table chunk
+    const int wsz = win_floats(maxrows);
 
     if (tid == 0) {
         tile_window(s, I * TM, TM, &wI);
         tile_window(s, J * TM, TM, &wJ);
+        int nr = tile_ranges(s, wI, 0, sm.rng, 0);
+        const int nwin0 = diag ? wI.nrows : wI.nrows + wJ.nrows;
+        if (!diag) nr = tile_ranges(s, wJ, wI.nrows, sm.rng, nr);
+        sm.rng[3 * nr] = s.p * s.n;  // y
+        sm.rng[3 * nr + 1] = 1;
+        sm.rng[3 * nr + 2] = nwin0;
+        s_nrng = nr + 1;
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&sm.full[i], NPROD);
+            mbar_init(&sm.tfull[i], 1);
             mbar_init(&sm.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -312,15 +307,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     if (warp == MMA_WARP) tmem_alloc(sm.tmem_base, TMEM_COLS);
     __syncthreads();
-    if (tid < NPROD) {
-        setup_tile(s, wI, I * TM, tmax, sm.trI, sm.crI, sm.egI, (J == 0 && split == 0) ? colexp : nullptr,
-                   tid, NPROD);
-        if (!diag) setup_tile(s, wJ, J * TM, tmax, sm.trJ, sm.crJ, sm.egJ, nullptr, tid, NPROD);
+    for (int e = tid; e < TM * s.p; e += NTHREADS) {
+        const int c = e / s.p, j = e % s.p;
+        const int mi = I * TM + c, mj = J * TM + c;
+        sm.crI[e] = (unsigned short)(mi < s.M ? window_row(s, wI, j, mi) : 0xFFFF);
+        sm.crJ[e] = (unsigned short)(mj < s.M ? window_row(s, wJ, j, mj) : 0xFFFF);
+    }
+    for (int c = tid; c < TM; c += NTHREADS) {
+        sm.egI[c] = colexp[I * TM + c];
+        sm.egJ[c] = colexp[J * TM + c];
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_base;
+    const int nrowsI = wI.nrows;
+    const int nwin = (diag ? nrowsI : nrowsI + wJ.nrows) + 1;
 
     if (warp < NPW) {
         // ------------------------------------------------------------ producers
@@ -331,16 +333,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // drain: TMEM lanes 32*quarter.. (tile rows), tile columns CPT*cgrp ..
         const int quarter = warp & 3;
         const int cgrp = warp >> 2;
+        const unsigned short* crrI = sm.crI + r * s.p;
+        const unsigned short* crrJ = (diag ? sm.crI : sm.crJ) + r * s.p;
         int woffI[P > 0 ? P : 1], woffJ[P > 0 ? P : 1];
         if constexpr (P > 0) {
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const unsigned short ci = sm.crI[r * s.p + j];
-                woffI[j] = (j == 0 && ci == 0xFFFF) ? -1 : ci * WSTRIDE;
-                const unsigned short cj = diag ? ci : sm.crJ[r * s.p + j];
-                woffJ[j] = (j == 0 && cj == 0xFFFF) ? -1 : cj * WSTRIDE;
+                const unsigned short ci = crrI[j], cj = crrJ[j];
+                woffI[j] = (j == 0 && ci == 0xFFFF) ? -1 : ci * WS;
+                woffJ[j] = (j == 0 && cj == 0xFFFF) ? -1 : cj * WS;
             }
         }
+        const int jwin = diag ? 0 : nrowsI * WS;  // tile J's window inside the stage window
+        const int ywin = (nwin - 1) * WS;
         // b: float32 within a block, float64 across blocks
         float bacc = 0.f;
         double bsum = 0.0;
@@ -380,38 +385,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             flushed = true;
         };
         bool ok = true;
-
-        // One thread waits and broadcasts, so every producer takes the same
-        // path. Successive calls alternate between two flags: a flag is
-        // rewritten only after the barrier of the following call, which every
-        // reader of its previous value has passed.
-        int nbc = 0;
-        auto bcast_wait = [&](uint64_t* bar, uint32_t parity, int site) -> bool {
-            const int slot = nbc++ & 1;
-            if (tid == 0) {
-                int fine = (bar == nullptr || mbar_wait(bar, parity)) ? 1 : 0;
-                if (!fine) gp_set_status(st, GP_ETIMEOUT, site);
-                s_ok[slot] = fine;
-            }
-            named_bar_sync(1, NPROD);
-            return s_ok[slot] != 0;
-        };
+        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
         auto drain = [&](int d) -> bool {
             const int u = d & 1;
-            if (!bcast_wait(&sm.accf[u], (d >> 1) & 1, 4)) return false;
+            if (!__all_sync(FULLMASK, mbar_wait(&sm.accf[u], (d >> 1) & 1))) {
+                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 4);
+                return false;
+            }
             tc_fence_after();
             const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + cgrp * CPT;
-            // back to the global column scaling (exact powers of two)
-            const float mrow = sm.muI[u * TM + quarter * 32 + lane];
-            const float* mcol = (diag ? sm.muI : sm.muJ) + u * TM + cgrp * CPT;
+            // back to the global column scaling: 2^(E_blk - E_glob) (exact powers of two)
+            const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
+            const int row = quarter * 32 + lane;
+            const float mrow = ldexpf(1.f, (int)eb[I * TM + row] - sm.egI[row]);
+            const signed char* ebc = eb + J * TM + cgrp * CPT;
+            const int* egc = (diag ? sm.egI : sm.egJ) + cgrp * CPT;
 #pragma unroll
             for (int ch = 0; ch < CPT / 16; ++ch) {
+                const int4 e4 = *reinterpret_cast<const int4*>(ebc + ch * 16);
+                const int ew[4] = {e4.x, e4.y, e4.z, e4.w};
                 float a1[16], a2[16];
                 tmem_ld16(tmem + lrow + ch * 16, a1);
                 tmem_ld16(tmem + lrow + 128 + ch * 16, a2);
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    gacc[ch * 16 + i] = fmaf(a1[i] + a2[i], mrow * mcol[ch * 16 + i], gacc[ch * 16 + i]);
+                for (int i = 0; i < 16; ++i) {
+                    const int eblk = (int)(signed char)(ew[i >> 2] >> (8 * (i & 3)));
+                    const float mc = ldexpf(1.f, eblk - egc[ch * 16 + i]);
+                    gacc[ch * 16 + i] = fmaf(a1[i] + a2[i], mrow * mc, gacc[ch * 16 + i]);
+                }
             }
             tc_fence_before();
             mbar_arrive(&sm.drained[u]);
@@ -419,68 +420,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             return true;
         };
 
-        // table windows are prefetched WBUF-1 chunks ahead into a ring
-        const int wsz = maxrows * WSTRIDE;
-        auto prefetch = [&](int cc) {
-            if (cc < nchunks) {
-                const int buf = cc % WBUF;
-                const int64_t i0 = r0 + (int64_t)cc * BK;
-                load_window_async(s, tab, sm.trI, wI.nrows, i0, sm.winI + buf * wsz, tid);
-                if (!diag) load_window_async(s, tab, sm.trJ, wJ.nrows, i0, sm.winJ + buf * wsz, tid);
-                if (tid < BK / 4) cp_async16(sm.yv + buf * BK + 4 * tid, ypad + i0 + 4 * tid);
-            }
-            cp_async_commit();  // one group per chunk, possibly empty
-        };
-        prefetch(0);
-        prefetch(1);
-
+        const int mI = I * TM + r, mJ = J * TM + r;
+        // block exponents of this thread's columns, loaded one block ahead
+        int eI = 0, eJ = 0;
+        if (nblocks > 0) {
+            eI = ebx[(int64_t)blk0 * s.Mpad + mI];
+            eJ = ebx[(int64_t)blk0 * s.Mpad + mJ];
+        }
         int next_drain = 0;
         float scI = 0.f, scJ = 0.f;
         for (int c = 0; c < nchunks && ok; ++c) {
             const int stg = c % nst;
-            const int buf = c % WBUF;
-            cp_async_wait<1>();        // this thread's copies for chunk c have landed
-            const float* winI = sm.winI + buf * wsz;
-            const float* winJ = sm.winJ + buf * wsz;
-            const float* yv = sm.yv + buf * BK;
-            const int slot = (c / BLOCK_CHUNKS) & 1;
-            const bool newblk = (c % BLOCK_CHUNKS == 0);
-            if (newblk) {
-                bsum += (double)bacc;
-                bacc = 0.f;
-                // a new 512-row block: its column scales (the drain of the
-                // block two back, which used this slot, is complete)
-                const unsigned int* tmb = tmaxb + ((r0 + (int64_t)c * BK) / GP_TAB_BLOCK) * (s.p * s.n);
-                if (tid < TM)
-                    block_scales(s, I * TM, tmb, sm.egI, sm.scI + slot * TM, sm.muI + slot * TM, tid);
-                else if (!diag && tid < 2 * TM)
-                    block_scales(s, J * TM, tmb, sm.egJ, sm.scJ + slot * TM, sm.muJ + slot * TM, tid - TM);
-            }
-            // One barrier per chunk: every thread's copies of chunk c are
-            // visible, chunk c-1 is consumed (its window buffer may be
-            // refilled), and the pipeline stage has been released by the MMAs.
-            if (!bcast_wait(c >= nst ? &sm.empty[stg] : nullptr, ((c / nst) - 1) & 1, 1)) {
+            // the stage's A tiles are free (MMAs of chunk c - nst done) and
+            // its window has landed
+            bool w = c < nst || mbar_wait(&sm.empty[stg], ((c / nst) - 1) & 1);
+            w = w && mbar_wait(&sm.tfull[stg], (c / nst) & 1);
+            if (!__all_sync(FULLMASK, w)) {
+                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 1);
                 ok = false;
                 break;
             }
-            if (newblk) {
-                scI = sm.scI[slot * TM + r];
-                scJ = diag ? scI : sm.scJ[slot * TM + r];
+            if (c % BLOCK_CHUNKS == 0) {
+                bsum += (double)bacc;
+                bacc = 0.f;
+                // a new 512-row block: quantisation scales 2^(7 - E_blk)
+                scI = pow2i(7 - eI);
+                scJ = pow2i(7 - eJ);
+                const int nb = c / BLOCK_CHUNKS + 1;
+                if (nb < nblocks) {
+                    eI = ebx[(int64_t)(blk0 + nb) * s.Mpad + mI];
+                    eJ = ebx[(int64_t)(blk0 + nb) * s.Mpad + mJ];
+                }
             }
-            prefetch(c + 2);
+            const float* win = sm.win + stg * wsz;
             uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
             {
                 float v[8];
-                phi8<P>(winI, woffI, sm.crI + r * s.p, s.p, g, v);
+                phi8<P>(win, woffI, crrI, s.p, g, v);
                 store_slices(sb, sb + TILE_BYTES, r, g, v, scI);
                 if (J == 0) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) bacc = fmaf(v[k], yv[8 * g + k], bacc);
+                    const float4* y4 = reinterpret_cast<const float4*>(win + ywin + 8 * g);
+                    const float4 ya = y4[0], yb = y4[1];
+                    bacc = fmaf(v[0], ya.x, bacc);
+                    bacc = fmaf(v[1], ya.y, bacc);
+                    bacc = fmaf(v[2], ya.z, bacc);
+                    bacc = fmaf(v[3], ya.w, bacc);
+                    bacc = fmaf(v[4], yb.x, bacc);
+                    bacc = fmaf(v[5], yb.y, bacc);
+                    bacc = fmaf(v[6], yb.z, bacc);
+                    bacc = fmaf(v[7], yb.w, bacc);
                 }
             }
             if (!diag) {
                 float v[8];
-                phi8<P>(winJ, woffJ, sm.crJ + r * s.p, s.p, g, v);
+                phi8<P>(win + jwin, woffJ, crrJ, s.p, g, v);
                 store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, scJ);
             }
             fence_proxy_async_smem();
@@ -498,7 +491,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!drain(next_drain)) ok = false;
             ++next_drain;
         }
-        cp_async_wait<0>();  // no copy of this thread may still be in flight at exit
         if (J == 0) {
             double v = bsum + (double)bacc;
             v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -509,7 +501,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int k = 0; k < CPT; ++k) grow[k] = make_float2(0.f, 0.f);
         }
-    } else {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16_f32(TM, TM);
@@ -550,6 +542,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
         __syncwarp();
+    } else {
+        // ------------------------------------------------------------ window loader (bulk copies)
+        const int nr = s_nrng;
+        const uint32_t wbytes = (uint32_t)nwin * WS * 4;
+        int c = 0;
+        for (; c < nchunks; ++c) {
+            const int stg = c % nst;
+            const bool e = c < nst || mbar_wait(&sm.empty[stg], ((c / nst) - 1) & 1);
+            if (!__all_sync(FULLMASK, e)) {
+                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 6);
+                break;
+            }
+            if (lane == 0) mbar_arrive_expect_tx(&sm.tfull[stg], wbytes);
+            __syncwarp();
+            const float* src = tabc + ((r0 + (int64_t)c * BK) / BK) * RC;
+            float* dst = sm.win + stg * wsz;
+            for (int k = lane; k < nr; k += 32)
+                bulk_g2s(dst + sm.rng[3 * k + 2] * WS, src + (int64_t)sm.rng[3 * k] * WS,
+                         (uint32_t)sm.rng[3 * k + 1] * WS * 4, &sm.tfull[stg]);
+        }
+        // before leaving, wait (bounded) for the copies this warp issued
+        for (int k = c - nst; k < c; ++k)
+            if (k >= 0) mbar_wait(&sm.tfull[k % nst], (k / nst) & 1);
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -579,23 +595,30 @@ size_t syrktc_smem_bytes(const GpShape& s) {
     return smem;
 }
 
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tab, const unsigned int* tmaxb,
-                           const unsigned int* tmax, const float* ypad, int nsplit,
-                           int64_t rows_per_split, float2* Gpart, double* bpart, int* colexp,
+size_t syrktc_ebx_bytes(const GpShape& s) {
+    return (size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * (size_t)s.Mpad;
+}
+
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
+                           const unsigned int* tmax, int nsplit, int64_t rows_per_split,
+                           float2* Gpart, double* bpart, int* colexp, signed char* ebx,
                            GpStatus* st, cudaStream_t stream) {
     if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
     size_t smem = 0;
     const int nst = syrk_tc_stages(s, maxrows, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
+    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
+    colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
+        s, tmaxb, tmax, nblk, colexp, ebx);
     const int T = s.Mpad / TM;
     const int npairs = T * (T + 1) / 2;
     dim3 grid((unsigned)npairs, (unsigned)nsplit);
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = gp_allow_max_smem((const void*)kern);
         if (e != cudaSuccess) return e;
-        kern<<<grid, NTHREADS, smem, stream>>>(s, tab, tmaxb, tmax, ypad, rows_per_split, npairs, maxrows,
-                                               nst, Gpart, bpart, colexp, st);
+        kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, rows_per_split, npairs, maxrows, nst,
+                                               Gpart, bpart, st);
         return cudaGetLastError();
     };
     switch (s.p) {

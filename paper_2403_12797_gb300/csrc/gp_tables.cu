@@ -6,7 +6,8 @@
 // satisfies q_{k+1} = sqrt(2/(k+1)) t q_k - sqrt(k/(k+1)) q_{k-1},
 // q_0 = sqrt(beta), q_1 = sqrt(2) t q_0), so nothing overflows for large n.
 //
-// Layout: T[(j * n + k) * Npad + i], rows i >= N are zero. A column of Phi
+// Layouts: T[(j * n + k) * Npad + i] (float64 Gram, predictions), or chunk-major
+// for the mixed-precision Gram (below); rows i >= N are zero. A column of Phi
 // (Eq. 19) is the product of one row per dimension of this table, formed
 // later inside the contraction kernels: Phi itself is never stored.
 #include "gp_kernels.cuh"
@@ -64,18 +65,71 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     }
 }
 
-// Per 512-row block b and table row: tmaxb[b * rows + row] = max |tab[row][i]|
-// over the block, and tmax[row] = the maximum over all blocks, as float bits
-// (non-negative floats order like their bit patterns). tmax must be zeroed.
+// The same recurrence, written in the chunk-major layout of the mixed-precision
+// Gram: for chunk q = i / 32 of the rows, table row R = j * n + k at
+// T[q * RC + R * WS + i % 32] (WS = 36 floats, the last 4 zero) and y in row
+// R = p * n, RC = (p * n + 1) * WS. One chunk's rows of every table row are
+// thus one contiguous block that a single bulk copy can move.
+__global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, const double* __restrict__ X,
+                                                                 const double* __restrict__ y,
+                                                                 float* __restrict__ tab, GpStatus* st) {
+    constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= s.Npad) return;
+    const int rows = s.p * s.n + 1;
+    float* chunk = tab + (i / CW) * (int64_t)rows * WS;
+    const int k0 = (int)(i % CW);
+    float* out = chunk + (int64_t)j * s.n * WS + k0;
+    if (k0 < WS - CW) {  // zero the padding of this thread's share of the rows
+        for (int k = 0; k < s.n; ++k) out[k * WS + CW] = 0.f;
+        if (j == 0) chunk[(int64_t)(rows - 1) * WS + CW + k0] = 0.f;
+    }
+    bool zero = i >= s.N;
+    double xd = 0.0;
+    if (!zero) {
+        xd = X[i * s.p + j];
+        if (!isfinite(xd) || (j == 0 && y != nullptr && !isfinite(y[i]))) {
+            gp_set_status(st, GP_EINVAL, i);
+            zero = true;
+        }
+    }
+    if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : (float)y[i];
+    if (zero) {
+        for (int k = 0; k < s.n; ++k) out[k * WS] = 0.f;
+        return;
+    }
+    const float x = (float)xd;
+    const float t = (float)s.alpha_beta * x;
+    float q0 = (float)s.sqrt_beta * expf(-(float)s.delta2 * x * x);
+    out[0] = q0;
+    if (s.n == 1) return;
+    float q1 = sqrtf(2.f) * t * q0;
+    out[WS] = q1;
+    for (int k = 1; k + 1 < s.n; ++k) {
+        const float a = sqrtf(2.f / (float)(k + 1));
+        const float b = sqrtf((float)k / (float)(k + 1));
+        const float q2 = a * t * q1 - b * q0;
+        out[(k + 1) * WS] = q2;
+        q0 = q1;
+        q1 = q2;
+    }
+}
+
+// Per 512-row block b and table row R: tmaxb[b * rows + R] = max |T[R][i]|
+// over the block (chunk-major layout above), and tmax[R] = the maximum over
+// all blocks, as float bits (non-negative floats order like their bit
+// patterns). tmax must be zeroed.
 __global__ void __launch_bounds__(256) table_absmax_kernel(const float* __restrict__ tab, int64_t Npad,
                                                            int rows, unsigned int* __restrict__ tmaxb,
                                                            unsigned int* __restrict__ tmax) {
+    constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
     const int row = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * GP_TAB_BLOCK;
-    const float* r = tab + (int64_t)row * Npad;
+    const int64_t RC = (int64_t)(rows + 1) * WS;
     float m = 0.f;
     for (int64_t i = i0 + threadIdx.x; i < i0 + GP_TAB_BLOCK && i < Npad; i += blockDim.x)
-        m = fmaxf(m, fabsf(r[i]));
+        m = fmaxf(m, fabsf(tab[(i / CW) * RC + (int64_t)row * WS + i % CW]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ float wm[8];
     if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
@@ -89,11 +143,11 @@ __global__ void __launch_bounds__(256) table_absmax_kernel(const float* __restri
 
 }  // namespace
 
-void launch_table_absmax(const GpShape& s, const float* tab, unsigned int* tmaxb, unsigned int* tmax,
+void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmaxb, unsigned int* tmax,
                          cudaStream_t stream) {
     cudaMemsetAsync(tmax, 0, sizeof(unsigned int) * s.p * s.n, stream);
     dim3 grid((unsigned)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK), (unsigned)(s.p * s.n));
-    table_absmax_kernel<<<grid, 256, 0, stream>>>(tab, s.Npad, s.p * s.n, tmaxb, tmax);
+    table_absmax_kernel<<<grid, 256, 0, stream>>>(tabc, s.Npad, s.p * s.n, tmaxb, tmax);
 }
 
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
@@ -106,4 +160,14 @@ void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, f
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
     eig_tables_kernel<float><<<grid, 256, 0, stream>>>(s, X, y, tab, st);
+}
+
+size_t syrktc_table_floats(const GpShape& s) {
+    return (size_t)(s.Npad / SYRKTC_BK) * (size_t)(s.p * s.n + 1) * SYRKTC_WS;
+}
+
+void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
+                               GpStatus* st, cudaStream_t stream) {
+    dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
+    eig_tables_chunked_kernel<<<grid, 256, 0, stream>>>(s, X, y, tabc, st);
 }
