@@ -34,7 +34,8 @@
 //   warp 17    (all lanes) copies the chunk's table window -- the tile's
 //              rows of the chunk-major table, at most two contiguous ranges
 //              per dimension and tile, plus y -- with 1-D bulk (TMA) copies
-//              that complete on the stage's mbarrier;
+//              into a ring of up to 8 window slots, each released by the
+//              producer warps once they have read it;
 //   warps 0-15 producers (one 8-column core group each): form Phi for
 //              column tiles I and J in the K-major core-matrix layout
 //              (8 columns x 16 bytes) from the window, split, publish the
@@ -57,6 +58,7 @@ constexpr int TM = SYRKTC_TM;              // 128
 constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
 constexpr int WS = SYRKTC_WS;              // floats per window row (36: bank-conflict padding)
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
+constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
 constexpr int BLOCK_CHUNKS = GP_TAB_BLOCK / BK;  // 16 chunks = 512 rows per exact TMEM block
 constexpr int FLUSH_BLOCKS = 4;            // blocks summed in float32 registers between flushes
 constexpr int TILE_BYTES = TM * BK * 2;    // one 16-bit operand tile: 8 KB
@@ -73,15 +75,16 @@ constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct SmemTC {
     uint8_t* stage;       // nst x STAGE_BYTES (1024-aligned)
-    float* win;           // nst x (2 maxrows + 1) x WS: windows of tiles I, J and y
+    float* win;           // nwr x (2 maxrows + 1) x WS: windows of tiles I, J and y
     int* egI;             // TM: global column exponents E_glob
     int* egJ;
     unsigned short* crI;  // TM x p: window row of (column, dimension)
     unsigned short* crJ;
     int* rng;             // copy ranges (table row, rows, window row), 3 ints each
     uint64_t* full;       // STAGES: producers' tiles published (count NPROD)
-    uint64_t* tfull;      // STAGES: window landed (count 1 + tx bytes)
     uint64_t* empty;      // STAGES: MMAs of the stage done
+    uint64_t* tfull;      // WRMAX: window landed (count 1 + tx bytes)
+    uint64_t* wempty;     // WRMAX: every producer warp has read the window (count NPW)
     uint64_t* accf;       // 2: block finished in TMEM buffer u
     uint64_t* drained;    // 2: TMEM buffer u has been read back
     uint32_t* tmem_base;
@@ -90,7 +93,7 @@ struct SmemTC {
 __host__ __device__ inline int max_ranges(int p) { return 4 * p + 1; }
 __host__ __device__ inline int win_floats(int maxrows) { return (2 * maxrows + 1) * WS; }
 
-__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, char* base, SmemTC* L) {
+__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, int nwr, char* base, SmemTC* L) {
     size_t off = 0;
     auto take = [&](size_t bytes, size_t align) {
         off = (off + align - 1) / align * align;
@@ -99,15 +102,16 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, ch
         return o;
     };
     size_t oS = take((size_t)nst * STAGE_BYTES, 1024);
-    size_t oW = take(sizeof(float) * nst * win_floats(maxrows), 16);
+    size_t oW = take(sizeof(float) * nwr * win_floats(maxrows), 16);
     size_t oEI = take(sizeof(int) * TM, 16);
     size_t oEJ = take(sizeof(int) * TM, 16);
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
     size_t oCJ = take(sizeof(unsigned short) * TM * p, 16);
     size_t oR = take(sizeof(int) * 3 * max_ranges(p), 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
-    size_t oX = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
+    size_t oX = take(sizeof(uint64_t) * WRMAX, 8);
+    size_t oY = take(sizeof(uint64_t) * WRMAX, 8);
     size_t oA = take(sizeof(uint64_t) * 2, 8);
     size_t oD = take(sizeof(uint64_t) * 2, 8);
     size_t oT = take(sizeof(uint32_t), 8);
@@ -120,8 +124,9 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, ch
         L->crJ = (unsigned short*)(base + oCJ);
         L->rng = (int*)(base + oR);
         L->full = (uint64_t*)(base + oF);
-        L->tfull = (uint64_t*)(base + oX);
         L->empty = (uint64_t*)(base + oE);
+        L->tfull = (uint64_t*)(base + oX);
+        L->wempty = (uint64_t*)(base + oY);
         L->accf = (uint64_t*)(base + oA);
         L->drained = (uint64_t*)(base + oD);
         L->tmem_base = (uint32_t*)(base + oT);
@@ -161,6 +166,9 @@ __global__ void colexp_kernel(GpShape s, const unsigned int* __restrict__ tmaxb,
 
 // 2^k for -126 <= k <= 127, exactly
 __device__ __forceinline__ float pow2i(int k) { return __int_as_float((127 + k) << 23); }
+// 2^k for k <= 0, flushed to 0 below 2^-126 (a block whose column bound is
+// that far below the column's global bound adds nothing representable)
+__device__ __forceinline__ float pow2_down(int k) { return k < -126 ? 0.f : __int_as_float((127 + k) << 23); }
 
 // Copy ranges of one tile's window (thread 0): dimension j's window rows
 // are the digits first .. first+count-1 (mod n), i.e. at most two
@@ -260,14 +268,14 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
 template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
-                   const int* __restrict__ colexp, int64_t rps, int npairs, int maxrows, int nst,
+                   const int* __restrict__ colexp, int64_t rps, int npairs, int maxrows, int nst, int nwr,
                    float2* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
     __shared__ int s_nrng;
     char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     SmemTC sm;
-    smem_tc_layout(maxrows, s.p, nst, base, &sm);
+    smem_tc_layout(maxrows, s.p, nst, nwr, base, &sm);
 
     const int q = blockIdx.x, split = blockIdx.y;
     int I, J;
@@ -296,8 +304,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         s_nrng = nr + 1;
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&sm.full[i], NPROD);
-            mbar_init(&sm.tfull[i], 1);
             mbar_init(&sm.empty[i], 1);
+        }
+        for (int i = 0; i < WRMAX; ++i) {
+            mbar_init(&sm.tfull[i], 1);
+            mbar_init(&sm.wempty[i], NPW);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&sm.accf[i], 1);
@@ -397,21 +408,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // back to the global column scaling: 2^(E_blk - E_glob) (exact powers of two)
             const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
             const int row = quarter * 32 + lane;
-            const float mrow = ldexpf(1.f, (int)eb[I * TM + row] - sm.egI[row]);
+            const float mrow = pow2_down((int)eb[I * TM + row] - sm.egI[row]);
             const signed char* ebc = eb + J * TM + cgrp * CPT;
             const int* egc = (diag ? sm.egI : sm.egJ) + cgrp * CPT;
 #pragma unroll
-            for (int ch = 0; ch < CPT / 16; ++ch) {
-                const int4 e4 = *reinterpret_cast<const int4*>(ebc + ch * 16);
-                const int ew[4] = {e4.x, e4.y, e4.z, e4.w};
-                float a1[16], a2[16];
-                tmem_ld16(tmem + lrow + ch * 16, a1);
-                tmem_ld16(tmem + lrow + 128 + ch * 16, a2);
+            for (int ch = 0; ch < CPT / 8; ++ch) {
+                const int2 e2 = *reinterpret_cast<const int2*>(ebc + ch * 8);
+                float a1[8], a2[8];
+                tmem_ld8(tmem + lrow + ch * 8, a1);
+                tmem_ld8(tmem + lrow + 128 + ch * 8, a2);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int eblk = (int)(signed char)(ew[i >> 2] >> (8 * (i & 3)));
-                    const float mc = ldexpf(1.f, eblk - egc[ch * 16 + i]);
-                    gacc[ch * 16 + i] = fmaf(a1[i] + a2[i], mrow * mc, gacc[ch * 16 + i]);
+                for (int i = 0; i < 8; ++i) {
+                    const int eblk = (int)(signed char)((i < 4 ? e2.x : e2.y) >> (8 * (i & 3)));
+                    const float mc = pow2_down(eblk - egc[ch * 8 + i]);
+                    gacc[ch * 8 + i] = fmaf(a1[i] + a2[i], mrow * mc, gacc[ch * 8 + i]);
                 }
             }
             tc_fence_before();
@@ -429,12 +439,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         int next_drain = 0;
         float scI = 0.f, scJ = 0.f;
+        // ring positions of chunk c: stage stg (phase sph = (c / nst) & 1) and
+        // window slot wsl (phase wph = (c / nwr) & 1), advanced without division
+        int stg = 0, sph = 0, wsl = 0, wph = 0;
         for (int c = 0; c < nchunks && ok; ++c) {
-            const int stg = c % nst;
             // the stage's A tiles are free (MMAs of chunk c - nst done) and
-            // its window has landed
-            bool w = c < nst || mbar_wait(&sm.empty[stg], ((c / nst) - 1) & 1);
-            w = w && mbar_wait(&sm.tfull[stg], (c / nst) & 1);
+            // the chunk's window has landed
+            bool w = c < nst || mbar_wait(&sm.empty[stg], sph ^ 1);
+            w = w && mbar_wait(&sm.tfull[wsl], wph);
             if (!__all_sync(FULLMASK, w)) {
                 if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 1);
                 ok = false;
@@ -452,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     eJ = ebx[(int64_t)(blk0 + nb) * s.Mpad + mJ];
                 }
             }
-            const float* win = sm.win + stg * wsz;
+            const float* win = sm.win + wsl * wsz;
             uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
             {
                 float v[8];
@@ -476,8 +488,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 phi8<P>(win + jwin, woffJ, crrJ, s.p, g, v);
                 store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, scJ);
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
             fence_proxy_async_smem();
             mbar_arrive(&sm.full[stg]);
+            if (++stg == nst) {
+                stg = 0;
+                sph ^= 1;
+            }
+            if (++wsl == nwr) {
+                wsl = 0;
+                wph ^= 1;
+            }
             // drain a finished block once nst chunks of the next one are queued
             while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) - 1 + nst <= c) {
                 if (!drain(next_drain)) {
@@ -506,14 +528,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = idesc_f16_f32(TM, TM);
             const uint32_t sbase = smem_u32(sm.stage);
+            int stg = 0, sph = 0;
             for (int c = 0; c < nchunks; ++c) {
-                const int stg = c % nst;
                 const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS, u = d & 1;
                 if (cb == 0 && d >= 2 && !mbar_wait(&sm.drained[u], ((d >> 1) - 1) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 5);
                     break;
                 }
-                if (!mbar_wait(&sm.full[stg], (c / nst) & 1)) {
+                if (!mbar_wait(&sm.full[stg], sph)) {
                     gp_set_status(st, GP_ETIMEOUT, 3);
                     break;
                 }
@@ -539,6 +561,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 mma_commit(&sm.empty[stg]);
                 if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(&sm.accf[u]);
+                if (++stg == nst) {
+                    stg = 0;
+                    sph ^= 1;
+                }
             }
         }
         __syncwarp();
@@ -546,25 +572,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ window loader (bulk copies)
         const int nr = s_nrng;
         const uint32_t wbytes = (uint32_t)nwin * WS * 4;
-        int c = 0;
+        // this lane's copy range (at most one per lane: 4p + 1 <= 32 ranges for p <= 7)
+        int rdst = 0, rsrc = 0, rlen = 0;
+        for (int k = lane; k < nr; k += 32) {
+            rdst = sm.rng[3 * k + 2] * WS;
+            rsrc = sm.rng[3 * k] * WS;
+            rlen = sm.rng[3 * k + 1] * WS * 4;
+        }
+        const bool multi = nr > 32;
+        int c = 0, wsl = 0, wph = 0;
         for (; c < nchunks; ++c) {
-            const int stg = c % nst;
-            const bool e = c < nst || mbar_wait(&sm.empty[stg], ((c / nst) - 1) & 1);
+            // the window slot is free: every producer warp has read chunk c - nwr
+            const bool e = c < nwr || mbar_wait(&sm.wempty[wsl], wph ^ 1);
             if (!__all_sync(FULLMASK, e)) {
                 if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 6);
                 break;
             }
-            if (lane == 0) mbar_arrive_expect_tx(&sm.tfull[stg], wbytes);
+            if (lane == 0) mbar_arrive_expect_tx(&sm.tfull[wsl], wbytes);
             __syncwarp();
             const float* src = tabc + ((r0 + (int64_t)c * BK) / BK) * RC;
-            float* dst = sm.win + stg * wsz;
-            for (int k = lane; k < nr; k += 32)
-                bulk_g2s(dst + sm.rng[3 * k + 2] * WS, src + (int64_t)sm.rng[3 * k] * WS,
-                         (uint32_t)sm.rng[3 * k + 1] * WS * 4, &sm.tfull[stg]);
+            float* dst = sm.win + wsl * wsz;
+            if (!multi) {
+                if (lane < nr) bulk_g2s(dst + rdst, src + rsrc, (uint32_t)rlen, &sm.tfull[wsl]);
+            } else {
+                for (int k = lane; k < nr; k += 32)
+                    bulk_g2s(dst + sm.rng[3 * k + 2] * WS, src + (int64_t)sm.rng[3 * k] * WS,
+                             (uint32_t)sm.rng[3 * k + 1] * WS * 4, &sm.tfull[wsl]);
+            }
+            if (++wsl == nwr) {
+                wsl = 0;
+                wph ^= 1;
+            }
         }
         // before leaving, wait (bounded) for the copies this warp issued
-        for (int k = c - nst; k < c; ++k)
-            if (k >= 0) mbar_wait(&sm.tfull[k % nst], (k / nst) & 1);
+        for (int k = c - nwr; k < c; ++k)
+            if (k >= 0) mbar_wait(&sm.tfull[k % nwr], (k / nwr) & 1);
         __syncwarp();
     }
     tc_fence_before();
@@ -575,15 +617,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// deepest pipeline (<= STAGES) whose dynamic shared memory fits one CTA next
-// to the kernel's static shared memory (tile windows and flags, under 2 KB);
-// 0 if none
-int syrk_tc_stages(const GpShape& s, int maxrows, size_t* smem) {
+// deepest pipeline (<= STAGES operand stages, then <= WRMAX window slots)
+// whose dynamic shared memory fits one CTA next to the kernel's static shared
+// memory (tile windows and flags, under 2 KB); 0 if none
+int syrk_tc_stages(const GpShape& s, int maxrows, int* nwr, size_t* smem) {
     constexpr size_t kDynamicBudget = (227 - 2) * 1024;
-    for (int nst = STAGES; nst >= 2; --nst) {
-        *smem = smem_tc_layout(maxrows, s.p, nst, nullptr, nullptr);
-        if (*smem <= kDynamicBudget) return nst;
-    }
+    for (int nst = STAGES; nst >= 2; --nst)
+        for (int w = WRMAX; w >= 2; --w) {
+            *smem = smem_tc_layout(maxrows, s.p, nst, w, nullptr, nullptr);
+            if (*smem <= kDynamicBudget) {
+                *nwr = w;
+                return nst;
+            }
+        }
     return 0;
 }
 
@@ -591,7 +637,8 @@ int syrk_tc_stages(const GpShape& s, int maxrows, size_t* smem) {
 
 size_t syrktc_smem_bytes(const GpShape& s) {
     size_t smem = 0;
-    syrk_tc_stages(s, gp_max_window_rows(s, TM), &smem);
+    int nwr = 0;
+    syrk_tc_stages(s, gp_max_window_rows(s, TM), &nwr, &smem);
     return smem;
 }
 
@@ -606,7 +653,8 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
     if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
     size_t smem = 0;
-    const int nst = syrk_tc_stages(s, maxrows, &smem);
+    int nwr = 0;
+    const int nst = syrk_tc_stages(s, maxrows, &nwr, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
     colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
@@ -618,7 +666,7 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
         cudaError_t e = gp_allow_max_smem((const void*)kern);
         if (e != cudaSuccess) return e;
         kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, rows_per_split, npairs, maxrows, nst,
-                                               Gpart, bpart, st);
+                                               nwr, Gpart, bpart, st);
         return cudaGetLastError();
     };
     switch (s.p) {
