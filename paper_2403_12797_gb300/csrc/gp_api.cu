@@ -359,7 +359,8 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
     }
     if (e == cudaSuccess) {
         GpProf pf("solve_refine", stream);
-        e = launch_solve_refine(A, h->W, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st, stream);
+        e = launch_solve_refine(A, h->W, fwork, fp32_inverse, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st,
+                                stream);
     }
     if (e == cudaSuccess && prec != GP_PREC_FP64) {
         GpProf pf("pack_w", stream);

@@ -18,18 +18,16 @@
 //   A non-positive or NaN pivot sets GP_ENOTPD (detail = column); every CTA
 //   sees it after the next barrier and returns.
 //
-//   W = L^{-1} (right-looking block forward substitution on R = I, 32-row
-//   blocks), in float32 or float64 arithmetic:
-//     0  invert every 32 x 32 diagonal block (D_I = L_II^{-1}); R = I;
-//     for each block row I:  1  W_IJ = D_I R_IJ        (J <= I)
-//                            2  R_KJ -= L_KI W_IJ      (K > I, J <= I)
-//   The mixed-precision fit uses float32 here: W feeds the bf16 hi/lo
-//   variance contraction, and as the preconditioner of c = A^{-1} b its
-//   error is removed by the float64 iterative refinement.
+//   W = L^{-1} by recursive doubling over 32-row blocks (below), in float32
+//   or float64 arithmetic. The mixed-precision fit uses float32 here: W
+//   feeds the bf16 hi/lo variance contraction, and as the preconditioner of
+//   c = A^{-1} b its error is removed by the float64 iterative refinement.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
 
 #include <math.h>
+
+#include <algorithm>
 
 namespace {
 
@@ -46,34 +44,37 @@ struct GridBar {
 
 // Bounded grid-wide barrier for a cooperative launch. Returns false (and
 // sets GP_ETIMEOUT) if the other CTAs do not arrive within GP_WAIT_NS.
+// `count` only grows (zeroed before the launch): the arrivals at the k-th
+// barrier are numbers k G .. k G + G - 1, so a CTA learns from its own
+// arrival number which total ends the barrier. The arrival is a release
+// and the wait an acquire at GPU scope; together with the CTA barriers on
+// both sides they order every thread's writes before the barrier with every
+// thread's reads after it.
 __device__ bool grid_sync(GridBar* gb, GpStatus* st) {
     __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
         s_fail = 0;
-        unsigned int g;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gb->gen) : "memory");
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            gb->count = 0u;
-            __threadfence();
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->gen) : "memory");
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            uint32_t it = 0;
-            while (true) {
-                unsigned int cur;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&gb->gen) : "memory");
-                if (cur != g) break;
-                if ((++it & 1023u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) {
+        unsigned int old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+        const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+        uint64_t t0 = 0;
+        uint32_t it = 0;
+        while (true) {
+            unsigned int cur;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&gb->count) : "memory");
+            if ((int)(cur - target) >= 0) break;
+            if ((++it & 255u) == 0) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > GP_WAIT_NS) {
                     gp_set_status(st, GP_ETIMEOUT, 100);
                     s_fail = 1;
                     break;
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return s_fail == 0;
@@ -114,175 +115,98 @@ struct CholWork {
 };
 constexpr int CHOL_RSD_OFFSET = 256;
 
-constexpr int PSLOT = 4;  // pivot slots (the owner of pivot j reuses the slot of pivot j - 4)
-
 struct PotrfSmem {
-    uint64_t full[PSLOT];   // slot s holds pivot j (j mod PSLOT = s): arrives when u and r are written
-    uint64_t empty[PSLOT];  // every warp arrives once it has applied that pivot to its columns
-    double u[PSLOT][CB];    // pivot column j after steps < j (lane i: a_ij)
-    double l[PSLOT][CB];    // multipliers a_ij / d_j (i > j; 0 elsewhere)
-    double r[PSLOT];        // 1 / d_j
-    double d[CB];       // pivots d_j
-    double s[CB];       // sqrt(d_j)
-    double rs[CB];      // 1 / sqrt(d_j)
+    double a[CB][CB + 1];                  // the block: lower part updated in place
+    double l[2][CB];                       // multipliers a_ij / d_j of the last two pivots
+    double d[CB];                          // pivots d_j
+    double s[CB];                          // sqrt(d_j)
+    double rs[CB];                         // 1 / sqrt(d_j)
+    unsigned short tri[CB * (CB + 1) / 2]; // lower entries (i << 8 | m), columns in decreasing order
     int bad;
-    int fail;
 };
 
-// Named barriers of the pivot chain: U(s) hands the pivot column of slot s,
-// R(s) its reciprocal, from the owner of pivot j to the owner of pivot j + 1.
-constexpr int POTRF_BAR_U = 1;           // ids 1..PSLOT
-constexpr int POTRF_BAR_R = 1 + PSLOT;   // ids PSLOT+1..2 PSLOT
+// Named barriers of the pivot loop: PUB(j & 1) -- pivot j is published;
+// DONE(j & 1) -- the followers have applied pivot j. Alternating ids keep
+// an arrival for pivot j + 1 off a barrier that pivot j still occupies.
+constexpr int POTRF_BAR_PUB = 1;   // ids 1, 2
+constexpr int POTRF_BAR_DONE = 3;  // ids 3, 4
+constexpr int POTRF_FOLLOW = 192;  // follower threads: warps 1-3 and 5-7
+constexpr int POTRF_BAR_N = 32 + POTRF_FOLLOW;
 
-// col[q] (column warp + 8q) -= l[lane] u[column] for the owned columns m > mlo.
-__device__ __forceinline__ void potrf_apply(double (&col)[4], const double* l, const double* u, int mlo,
-                                            int w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double lv = l[lane];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int m = warp + 8 * q;
-        if (m > mlo && m < w) col[q] = fma(-lv, u[m], col[q]);
-    }
-}
-
-// The owner of pivot j publishes column j (already updated by all earlier
-// pivots) and then its reciprocal. A pivot outside [2^-1022, 2^1021) -- zero,
-// negative, NaN, or beyond any value a Gram matrix plus the clamped noise
-// diagonal reaches -- is checked on the high word (no float64 instruction),
-// recorded as not positive definite and replaced by NaN, so control flow
-// never depends on the data.
-__device__ __forceinline__ void potrf_publish(double v, int j, int w, int kb, GpStatus* st, PotrfSmem& sm,
-                                              bool handoff) {
-    const int lane = threadIdx.x & 31;
-    const int sl = j % PSLOT;
-    sm.u[sl][lane] = v;
-    __syncwarp();
-    if (handoff) named_bar_arrive(POTRF_BAR_U + sl, 64);
-    const double piv = __shfl_sync(0xffffffffu, v, j);
-    const int hi = __double2hiint(piv);
-    const bool ok = hi >= 0x00100000 && hi < 0x7FD00000;
-    const double r = ok ? fast_rcp(piv) : __longlong_as_double(0x7FF8000000000000ll);
-    if (lane == 0) {
-        sm.r[sl] = r;
-        sm.d[j] = piv;
-        if (!ok) {
-            sm.bad = 1;
-            gp_set_status(st, GP_ENOTPD, kb + j);
-        }
-    }
-    __syncwarp();
-    if (handoff) named_bar_arrive(POTRF_BAR_R + sl, 64);
-    // the multipliers, once, for every warp that applies this pivot
-    sm.l[sl][lane] = (lane > j && lane < w) ? v * r : 0.0;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&sm.full[sl]);
-}
-
-// Factor the w x w diagonal block at (kb, kb) in place (one CTA, w <= 32).
-// Right-looking L D L^T elimination in registers: lane i holds row i, warp
-// q owns columns q, q + 8, q + 16, q + 24, and pivot j subtracts
-// (a_ij / d_j) a_mj from every later column m. The critical path is the chain
-// of pivots, so it is cut to one reciprocal and one FMA per pivot: the owner
-// of pivot j publishes column j before forming 1 / d_j, the owner of pivot
-// j + 1 multiplies a_ij a_{j+1,j} meanwhile and, once the reciprocal arrives,
-// finishes its column with one FMA and publishes it in turn. These handoffs
-// use pairs of named barriers; the other warps follow through PSLOT pivot
-// slots guarded by mbarriers (bounded waits), applying each pivot to their
-// columns off the critical path. The owner of pivot j + 2 applies pivot j
-// to that column alone and the rest of its columns after its own turn, so it
-// is never late for the chain. Every warp runs the same sequence of
-// barrier operations whatever the data, so nothing can wait for an arrival
-// that never comes. At the end L_jj = sqrt(d_j), L_ij = a_ij / sqrt(d_j) and
-// rsd[kb + j] = 1 / L_jj. Returns false on a non-positive pivot (GP_ENOTPD)
-// or an expired wait (GP_ETIMEOUT).
+// Factor the w x w diagonal block at (kb, kb) in place (one CTA, w <= 32),
+// right-looking L D L^T in shared memory. The pivot chain runs in warp 0
+// alone (lane i = row i, the current pivot column in a register): for pivot
+// j it broadcasts d_j, forms 1 / d_j (fast_rcp) and the multipliers
+// l_ij = a_ij / d_j, publishes them, and applies pivot j to column j + 1
+// itself, so that column is the next pivot column one FMA later. Warps 1-3
+// and 5-7 (the three other schedulers; warp 4 shares warp 0's float64 pipe
+// and stays idle) apply pivot j to the columns m >= j + 2, one lower-triangle
+// entry per thread from a packed table, so no float64 lane is spent on rows
+// above the diagonal; the chain waits for them only before it reads the
+// next column. Control flow does not depend on the data: a pivot outside
+// [2^-1022, 2^1021) (zero, negative, NaN, beyond any value a Gram matrix plus
+// the clamped noise diagonal reaches) is checked on its high word, recorded
+// as GP_ENOTPD and replaced by NaN. At the end L_jj = sqrt(d_j),
+// L_ij = a_ij / sqrt(d_j) and rsd[kb + j] = 1 / L_jj.
 __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
                                            double* __restrict__ rsd, PotrfSmem& sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double col[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int m = warp + 8 * q;
-        col[q] = (m < w && lane < w && lane >= m) ? L[(int64_t)(kb + lane) * M + kb + m] : 0.0;
+    for (int e = tid; e < CB * CB; e += NT) {
+        const int i = e / CB, m = e % CB;
+        sm.a[i][m] = (i < w && m <= i) ? L[(int64_t)(kb + i) * M + kb + m] : 0.0;
     }
-    if (tid == 0) {
-        sm.bad = 0;
-        sm.fail = 0;
-        for (int q = 0; q < PSLOT; ++q) {
-            mbar_init(&sm.full[q], 1);
-            mbar_init(&sm.empty[q], NT / 32);
+    if (tid < w) {  // column m's entries start after those of the columns > m
+        const int m = tid;
+        const int st0 = (w - m - 1) * (w - m) / 2;
+        for (int i = m; i < w; ++i) sm.tri[st0 + i - m] = (unsigned short)((i << 8) | m);
+    }
+    if (tid == 0) sm.bad = 0;
+    __syncthreads();
+    if (warp == 0) {
+        double col = sm.a[lane][0];
+        for (int j = 0; j < w; ++j) {
+            // column j is final (every pivot < j applied)
+            sm.a[lane][j] = col;
+            const double piv = __shfl_sync(0xffffffffu, col, j);
+            const int hi = __double2hiint(piv);
+            const bool ok = hi >= 0x00100000 && hi < 0x7FD00000;
+            const double r = ok ? fast_rcp(piv) : __longlong_as_double(0x7FF8000000000000ll);
+            const double l = (lane > j && lane < w) ? col * r : 0.0;
+            sm.l[j & 1][lane] = l;
+            if (lane == 0) {
+                sm.d[j] = piv;
+                if (!ok) {
+                    sm.bad = 1;
+                    gp_set_status(st, GP_ENOTPD, kb + j);
+                }
+            }
+            __syncwarp();
+            named_bar_arrive(POTRF_BAR_PUB + (j & 1), POTRF_BAR_N);
+            if (j + 1 < w) {
+                // the followers have applied pivot j - 1 to the columns >= j + 1
+                if (j >= 1) named_bar_sync(POTRF_BAR_DONE + ((j - 1) & 1), POTRF_BAR_N);
+                const double u = __shfl_sync(0xffffffffu, col, j + 1);  // a_{j+1, j}
+                col = fma(-l, u, sm.a[lane][j + 1]);
+            }
         }
-        mbar_fence_init();
+        for (int q = (w > 2 ? w - 2 : 0); q < w; ++q) named_bar_sync(POTRF_BAR_DONE + (q & 1), POTRF_BAR_N);
+    } else if (warp != 4) {
+        const int ft = (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
+        for (int j = 0; j < w; ++j) {
+            named_bar_sync(POTRF_BAR_PUB + (j & 1), POTRF_BAR_N);
+            const int T = w - j - 2;
+            const int cnt = T > 0 ? T * (T + 1) / 2 : 0;  // entries of the columns m >= j + 2
+            const double* lj = sm.l[j & 1];
+            for (int e = ft; e < cnt; e += POTRF_FOLLOW) {
+                const unsigned v = sm.tri[e];
+                const int i = (int)(v >> 8), m = (int)(v & 255u);
+                sm.a[i][m] = fma(-lj[i], sm.a[m][j], sm.a[i][m]);
+            }
+            named_bar_arrive(POTRF_BAR_DONE + (j & 1), POTRF_BAR_N);
+        }
     }
     __syncthreads();
-    if (warp == 0) potrf_publish(col[0], 0, w, kb, st, sm, w > 1);
-    int pend = -1;  // pivot this warp has applied to its next pivot column only
-    for (int j = 0; j + 1 < w; ++j) {
-        const int sl = j % PSLOT, jn = j + 1, sn = jn % PSLOT;
-        if (warp == (jn & 7)) {
-            // ---- the pivot chain: finish column jn and publish it
-            named_bar_sync(POTRF_BAR_U + sl, 64);
-            const double p = sm.u[sl][lane] * sm.u[sl][jn];
-            // slot sn last held pivot jn - PSLOT: every warp must be done with it
-            if (jn >= PSLOT && !*(volatile int*)&sm.fail &&
-                !mbar_wait(&sm.empty[sn], (uint32_t)(jn / PSLOT - 1) & 1u)) {
-                if (lane == 0) {
-                    sm.fail = 1;
-                    gp_set_status(st, GP_ETIMEOUT, 103);
-                }
-            }
-            named_bar_sync(POTRF_BAR_R + sl, 64);
-            const double r = sm.r[sl];
-            double v = 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q == (jn >> 3)) {
-                    col[q] = fma(-p, r, col[q]);
-                    v = col[q];
-                }
-            potrf_publish(v, jn, w, kb, st, sm, jn + 1 < w);
-            // then the rest of this warp's columns (all > jn): pivot j - 1 if put
-            // off, and pivot j
-            if (pend >= 0) {
-                const int sp = pend % PSLOT;
-                potrf_apply(col, sm.l[sp], sm.u[sp], jn, w);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.empty[sp]);
-                pend = -1;
-            }
-            // pivot j's multipliers were written after its reciprocal's handoff
-            if (!*(volatile int*)&sm.fail && !mbar_wait(&sm.full[sl], (uint32_t)(j / PSLOT) & 1u)) {
-                if (lane == 0) {
-                    sm.fail = 1;
-                    gp_set_status(st, GP_ETIMEOUT, 104);
-                }
-            }
-            potrf_apply(col, sm.l[sl], sm.u[sl], jn, w);
-        } else {
-            // ---- follow pivot j
-            if (!*(volatile int*)&sm.fail && !mbar_wait(&sm.full[sl], (uint32_t)(j / PSLOT) & 1u)) {
-                if (lane == 0) {
-                    sm.fail = 1;
-                    gp_set_status(st, GP_ETIMEOUT, 102);
-                }
-            }
-            const int jnn = jn + 1;
-            if (jnn < w && warp == (jnn & 7)) {
-                // owner of the next pivot: column jnn now, the others after its turn
-                const double lv = sm.l[sl][lane];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q == (jnn >> 3)) col[q] = fma(-lv, sm.u[sl][jnn], col[q]);
-                pend = j;
-                continue;  // its empty arrival for pivot j comes with the deferred update
-            }
-            potrf_apply(col, sm.l[sl], sm.u[sl], j, w);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.empty[sl]);
-    }
-    __syncthreads();
-    if (sm.bad || sm.fail) return false;  // uniform: read after the barrier
+    if (sm.bad) return false;  // uniform: read after the barrier
     if (tid < w) {
         const double sq = sqrt(sm.d[tid]);
         const double rs = 1.0 / sq;
@@ -291,11 +215,9 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
         rsd[kb + tid] = rs;
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int m = warp + 8 * q;
-        if (m < w && lane < w && lane >= m)
-            L[(int64_t)(kb + lane) * M + kb + m] = (lane == m) ? sm.s[m] : col[q] * sm.rs[m];
+    for (int e = tid; e < CB * CB; e += NT) {
+        const int i = e / CB, m = e % CB;
+        if (i < w && m <= i) L[(int64_t)(kb + i) * M + kb + m] = (i == m) ? sm.s[m] : sm.a[i][m] * sm.rs[m];
     }
     __syncthreads();
     return true;
@@ -483,225 +405,216 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
 
 // ---------------------------------------------------------------- W = L^{-1}
 
+// W = L^{-1} by recursive doubling over 32-row blocks, in float32 (mixed
+// precision) or float64 arithmetic. With L = [L11 0; L21 L22] the inverse is
+// [W11 0; W21 W22], W21 = -W22 (L21 W11): the diagonal blocks' inverses D_I
+// come first (level 0), and each level h = 32, 64, 128, ... joins every
+// aligned pair of h-row blocks with two tiled GEMM phases over all CTAs,
+//   A:  X[S][F]  = L[S][F] W[F][F]     (W[F][F] lower triangular)
+//   B:  W[S][F]  = -W[S][S] X[S][F]    (W[S][S] lower triangular),
+// F = the first h rows of the pair, S the rest. A grid barrier separates the
+// phases, so an M x M inverse takes 2 ceil(log2(M / 32)) + 1 phases whose
+// tiles run side by side, instead of a walk down the block rows.
+
+// 32 x 32 tile of C (+)= sum_{k in [k0, k1)} A[r0 + i][k] B[k][c0 + j] (rows
+// and columns beyond M read as zero), each thread four outputs of row ty;
+// the next chunk's global loads are in flight while one is multiplied.
 template <typename T>
-__device__ __forceinline__ T tload(const double* p) { return (T)(*p); }
-
-template <typename T>
-__global__ void __launch_bounds__(NT) trinv_coop_kernel(const double* __restrict__ L,
-                                                        double* __restrict__ W, int M,
-                                                        T* __restrict__ R, T* __restrict__ Dinv,
-                                                        GpStatus* st, GridBar* gb) {
-    __shared__ T sa[IB][IB + 1];
-    __shared__ T sb[IB][IB + 1];
-    const int tid = threadIdx.x;
-    const int nb = (M + IB - 1) / IB;
-    const int ty = tid / IB, tx = tid % IB;   // 8 x 32 threads: rows ty + 8q
-    // ---- 0: diagonal block inverses, R = I (lower), W = 0 above the diagonal
-    for (int I = blockIdx.x; I < nb; I += gridDim.x) {
-        const int r0 = I * IB, wI = min(IB, M - r0);
-        for (int e = tid; e < IB * IB; e += NT) {
-            const int i = e / IB, j = e % IB;
-            sa[i][j] = (i < wI && j <= i) ? tload<T>(L + (int64_t)(r0 + i) * M + r0 + j) : T(0);
-            sb[i][j] = T(0);
-        }
-        __syncthreads();
-        if (tid < wI) {  // column j of L_II^{-1} by forward substitution
-            const int j = tid;
-            sb[j][j] = T(1) / sa[j][j];
-            for (int i = j + 1; i < wI; ++i) {
-                T s = T(0);
-                for (int k = j; k < i; ++k) s += sa[i][k] * sb[k][j];
-                sb[i][j] = -s / sa[i][i];
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < IB * IB; e += NT) Dinv[(int64_t)I * IB * IB + e] = sb[e / IB][e % IB];
-        __syncthreads();
-    }
-    const int64_t total = (int64_t)M * M;
-    for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)gridDim.x * NT) {
-        const int i = (int)(e / M), j = (int)(e % M);
-        R[e] = (i == j) ? T(1) : T(0);  // whole matrix: diagonal blocks are read in full
-        if (j > i) W[e] = 0.0;
-    }
-    if (!grid_sync(gb, st)) return;
-    for (int I = 0; I < nb; ++I) {
-        const int r0 = I * IB, wI = min(IB, M - r0);
-        // ---- 1: W_IJ = D_I R_IJ, J <= I
-        for (int J = blockIdx.x; J <= I; J += gridDim.x) {
-            const int c0 = J * IB, wJ = min(IB, M - c0);
-            for (int e = tid; e < IB * IB; e += NT) {
-                const int i = e / IB, j = e % IB;
-                sa[i][j] = Dinv[(int64_t)I * IB * IB + e];
-                sb[i][j] = (i < wI && j < wJ) ? R[(int64_t)(r0 + i) * M + c0 + j] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < IB / 8; ++q) {
-                const int i = ty + 8 * q;
-                T s = T(0);
-                for (int k = 0; k <= i; ++k) s += sa[i][k] * sb[k][tx];
-                if (i < wI && tx < wJ) W[(int64_t)(r0 + i) * M + c0 + tx] = (double)s;
-            }
-            __syncthreads();
-        }
-        if (!grid_sync(gb, st)) return;
-        // ---- 2: R_KJ -= L_KI W_IJ, K > I, J <= I
-        const int nK = nb - I - 1, nJ = I + 1;
-        for (int t = blockIdx.x; t < nK * nJ; t += gridDim.x) {
-            const int K = I + 1 + t / nJ, J = t % nJ;
-            const int k0 = K * IB, wK = min(IB, M - k0);
-            const int c0 = J * IB, wJ = min(IB, M - c0);
-            for (int e = tid; e < IB * IB; e += NT) {
-                const int i = e / IB, j = e % IB;
-                sa[i][j] = (i < wK && j < wI) ? tload<T>(L + (int64_t)(k0 + i) * M + r0 + j) : T(0);
-                sb[i][j] = (i < wI && j < wJ) ? (T)W[(int64_t)(r0 + i) * M + c0 + j] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < IB / 8; ++q) {
-                const int i = ty + 8 * q;
-                T s = T(0);
-#pragma unroll 8
-                for (int k = 0; k < IB; ++k) s += sa[i][k] * sb[k][tx];
-                if (i < wK && tx < wJ) R[(int64_t)(k0 + i) * M + c0 + tx] -= s;
-            }
-            __syncthreads();
-        }
-        if (!grid_sync(gb, st)) return;
-    }
-}
-
-// float32 inverse by column strips (M <= STRIP_MAX_M). Block column J of W
-// depends on no other block column, so after one grid barrier (the diagonal
-// block inverses D_I) each CTA walks its strips down the rows with no further
-// synchronisation:
-//   W_IJ = D_I (delta_IJ I - sum_{J <= K < I} L_IK W_KJ).
-// The strip's finished blocks stay in shared memory (M x 32 float32), and the
-// K sum streams L in chunks of SKC columns whose global loads are issued one
-// chunk ahead, into registers, while the current chunk is multiplied.
-constexpr int SKC = 128;
-constexpr int STRIP_MAX_M = 1024;
-constexpr int SPF = IB * SKC / NT;  // chunk elements per thread
-
-size_t strip_smem_bytes(int M) {
-    return sizeof(float) * ((size_t)M * IB + (size_t)IB * (SKC + 1) + 2 * IB * (IB + 1));
-}
-
-__global__ void __launch_bounds__(NT) trinv_strip_kernel(const double* __restrict__ L,
-                                                         double* __restrict__ W, int M,
-                                                         float* __restrict__ Dinv, GpStatus* st,
-                                                         GridBar* gb) {
-    extern __shared__ __align__(16) float smem_f[];
-    float* sS = smem_f;                               // [M][IB]   the strip
-    float (*sL)[SKC + 1] = (float (*)[SKC + 1])(sS + (size_t)M * IB);
-    float (*sa)[IB + 1] = (float (*)[IB + 1])(&sL[IB][0]);
-    float (*sb)[IB + 1] = sa + IB;
-    const int tid = threadIdx.x;
-    const int nb = (M + IB - 1) / IB;
-    // ---- 0: D_I = L_II^{-1}
-    for (int I = blockIdx.x; I < nb; I += gridDim.x) {
-        const int r0 = I * IB, wI = min(IB, M - r0);
-        float v[IB * IB / NT];
+__device__ __forceinline__ void tile_mm(const T* __restrict__ A, const T* __restrict__ B, int M, int r0,
+                                        int c0, int k0, int k1, T (&acc)[4], T (*sa)[IB + 1],
+                                        T (*sb)[IB + 1]) {
+    const int tid = threadIdx.x, ty = tid >> 3, tx = (tid & 7) * 4;
+    T va[IB * IB / NT], vb[IB * IB / NT];
+    auto load = [&](int kc) {
 #pragma unroll
         for (int q = 0; q < IB * IB / NT; ++q) {
             const int e = tid + q * NT, i = e / IB, j = e % IB;
-            v[q] = (i < wI && j <= i) ? (float)L[(int64_t)(r0 + i) * M + r0 + j] : 0.0f;
+            va[q] = (r0 + i < M && kc + j < M) ? A[(int64_t)(r0 + i) * M + kc + j] : T(0);
+            vb[q] = (kc + i < M && c0 + j < M) ? B[(int64_t)(kc + i) * M + c0 + j] : T(0);
         }
+    };
+    if (k0 < k1) load(k0);
+    for (int kc = k0; kc < k1; kc += IB) {
+        __syncthreads();
 #pragma unroll
         for (int q = 0; q < IB * IB / NT; ++q) {
             const int e = tid + q * NT;
-            sa[e / IB][e % IB] = v[q];
-            sb[e / IB][e % IB] = 0.0f;
+            sa[e / IB][e % IB] = va[q];
+            sb[e / IB][e % IB] = vb[q];
         }
         __syncthreads();
-        if (tid < wI) {
+        if (kc + IB < k1) load(kc + IB);
+#pragma unroll 8
+        for (int l = 0; l < IB; ++l) {
+            const T av = sa[ty][l];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = fma(av, sb[l][tx + c], acc[c]);
+        }
+    }
+    __syncthreads();
+}
+
+// Lt: L in the arithmetic type T (converted here when T is float; L itself
+// when T is double); Wt: W in T (W itself when T is double); X: M x M scratch.
+template <typename T>
+__global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict__ L, double* __restrict__ W,
+                                                       int M, T* __restrict__ Lt, T* __restrict__ Wt,
+                                                       T* __restrict__ X, GpStatus* st, GridBar* gb) {
+    __shared__ T sa[IB][IB + 1];
+    __shared__ T sb[IB][IB + 1];
+    __shared__ T rd[IB];
+    const int tid = threadIdx.x, ty = tid >> 3, tx = (tid & 7) * 4;
+    const int nb = (M + IB - 1) / IB;
+    const int G = gridDim.x;
+    constexpr bool conv = sizeof(T) != sizeof(double);
+    // ---- level 0: L in T, zero upper triangles, D_I = L_II^{-1}
+    const int64_t total = (int64_t)M * M;
+    for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)G * NT) {
+        const int i = (int)(e / M), j = (int)(e % M);
+        if (j > i) {
+            W[e] = 0.0;
+            if (conv) Wt[e] = T(0);
+        } else if (conv) {
+            Lt[e] = (T)L[e];
+        }
+    }
+    for (int I = blockIdx.x; I < nb; I += G) {
+        const int r0 = I * IB, wI = min(IB, M - r0);
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT, i = e / IB, j = e % IB;
+            sa[i][j] = (i < wI && j <= i) ? (T)L[(int64_t)(r0 + i) * M + r0 + j] : T(0);
+            sb[i][j] = T(0);
+        }
+        __syncthreads();
+        if (tid < wI) rd[tid] = T(1) / sa[tid][tid];
+        __syncthreads();
+        if (tid < wI) {  // column j of L_II^{-1} by forward substitution
             const int j = tid;
-            sb[j][j] = 1.0f / sa[j][j];
+            sb[j][j] = rd[j];
             for (int i = j + 1; i < wI; ++i) {
-                float s = 0.0f;
-                for (int k = j; k < i; ++k) s = fmaf(sa[i][k], sb[k][j], s);
-                sb[i][j] = -s / sa[i][i];
+                T s = T(0);
+                for (int k = j; k < i; ++k) s = fma(sa[i][k], sb[k][j], s);
+                sb[i][j] = -s * rd[i];
             }
         }
         __syncthreads();
-        for (int e = tid; e < IB * IB; e += NT) Dinv[(int64_t)I * IB * IB + e] = sb[e / IB][e % IB];
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT, i = e / IB, j = e % IB;
+            if (i < wI && j < wI && j <= i) {
+                const int64_t o = (int64_t)(r0 + i) * M + r0 + j;
+                W[o] = (double)sb[i][j];
+                if (conv) Wt[o] = sb[i][j];
+            }
+        }
         __syncthreads();
     }
     if (!grid_sync(gb, st)) return;
-    // ---- 1: strips
-    const int ty = tid >> 3, tx = (tid & 7) * 4;
-    for (int J = blockIdx.x; J < nb; J += gridDim.x) {
-        const int c0 = J * IB, wJ = min(IB, M - c0);
-        for (int e = tid; e < c0 * IB; e += NT) {  // rows above the strip's diagonal block
-            const int i = e / IB, j = e % IB;
-            if (j < wJ) W[(int64_t)i * M + c0 + j] = 0.0;
+    const T* Lr = conv ? Lt : reinterpret_cast<const T*>(L);
+    for (int h = IB; h < M; h *= 2) {
+        const int hb = h / IB;                     // blocks per half
+        const int ng = (M + 2 * h - 1) / (2 * h);  // pairs at this level
+        const int ntile = ng * hb * hb;            // (S block, F block) tiles, full pairs
+        // ---- A: X[S][F] = L[S][F] W[F][F]
+        for (int t = blockIdx.x; t < ntile; t += G) {
+            const int g = t / (hb * hb), si = (t / hb) % hb, fj = t % hb;
+            const int F0 = g * 2 * h, S0 = F0 + h;
+            const int r0 = S0 + si * IB, c0 = F0 + fj * IB;
+            if (r0 >= M) continue;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            tile_mm<T>(Lr, Wt, M, r0, c0, c0, S0, acc, sa, sb);  // W[k][c0..] = 0 for k < c0
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (r0 + ty < M) X[(int64_t)(r0 + ty) * M + c0 + tx + c] = acc[c];
         }
-        // chunk prefetch: (pI, pkc) is the next chunk to be consumed
-        int pI = J + 1, pkc = c0;
-        float pf[SPF];
-        auto load_chunk = [&](int I, int kc) {
-            const int r0 = I * IB, wI = min(IB, M - r0);
-#pragma unroll
-            for (int q = 0; q < SPF; ++q) {
-                const int e = tid + q * NT, i = e / SKC, l = e % SKC;
-                pf[q] = (i < wI && kc + l < r0) ? (float)L[(int64_t)(r0 + i) * M + kc + l] : 0.0f;
-            }
-        };
-        if (pI < nb) load_chunk(pI, pkc);
-        for (int I = J; I < nb; ++I) {
-            const int r0 = I * IB, wI = min(IB, M - r0);
-            float acc[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] = (I == J && ty == tx + c) ? 1.0f : 0.0f;
-            for (int kc = c0; kc < r0; kc += SKC) {
-                __syncthreads();
-#pragma unroll
-                for (int q = 0; q < SPF; ++q) {
-                    const int e = tid + q * NT;
-                    sL[e / SKC][e % SKC] = pf[q];
-                }
-                __syncthreads();
-                if (pkc + SKC < pI * IB) {
-                    pkc += SKC;
-                } else {
-                    ++pI;
-                    pkc = c0;
-                }
-                if (pI < nb) load_chunk(pI, pkc);
-                const int kn = min(SKC, r0 - kc);
-                const float* srow = sS + (size_t)kc * IB + tx;
-                for (int l = 0; l < kn; ++l) {
-                    const float av = sL[ty][l];
-                    const float4 w4 = *reinterpret_cast<const float4*>(srow + (size_t)l * IB);
-                    acc[0] = fmaf(-av, w4.x, acc[0]);
-                    acc[1] = fmaf(-av, w4.y, acc[1]);
-                    acc[2] = fmaf(-av, w4.z, acc[2]);
-                    acc[3] = fmaf(-av, w4.w, acc[3]);
-                }
-            }
-            float dv[IB * IB / NT];
-#pragma unroll
-            for (int q = 0; q < IB * IB / NT; ++q) dv[q] = Dinv[(int64_t)I * IB * IB + tid + q * NT];
-            __syncthreads();
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sb[ty][tx + c] = acc[c];
-#pragma unroll
-            for (int q = 0; q < IB * IB / NT; ++q) {
-                const int e = tid + q * NT;
-                sa[e / IB][e % IB] = dv[q];
-            }
-            __syncthreads();
+        if (!grid_sync(gb, st)) return;
+        // ---- B: W[S][F] = -W[S][S] X[S][F]
+        for (int t = blockIdx.x; t < ntile; t += G) {
+            const int g = t / (hb * hb), si = (t / hb) % hb, fj = t % hb;
+            const int F0 = g * 2 * h, S0 = F0 + h;
+            const int r0 = S0 + si * IB, c0 = F0 + fj * IB;
+            if (r0 >= M) continue;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            tile_mm<T>(Wt, X, M, r0, c0, S0, min(r0 + IB, M), acc, sa, sb);  // W[r][k] = 0 for k > r
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float o = 0.0f;
-                for (int l = 0; l <= ty; ++l) o = fmaf(sa[ty][l], sb[l][tx + c], o);
-                const bool ok = ty < wI && tx + c < wJ;
-                if (r0 + ty < M) sS[(size_t)(r0 + ty) * IB + tx + c] = ok ? o : 0.0f;
-                if (ok) W[(int64_t)(r0 + ty) * M + c0 + tx + c] = (double)o;
+                const int64_t o = (int64_t)(r0 + ty) * M + c0 + tx + c;
+                if (r0 + ty < M) {
+                    W[o] = (double)(-acc[c]);
+                    if (conv) Wt[o] = -acc[c];
+                }
             }
         }
-        __syncthreads();
+        if (!grid_sync(gb, st)) return;
+    }
+}
+
+// ---------------------------------------------------------------- c = A^{-1} b
+
+// c = W^T (W b), then `refine` steps of c += W^T W (b - A c): the residual
+// and c in float64; the products with W in T (float32 for the mixed fit,
+// whose W is float32-accurate, so float32 products lose nothing the
+// refinement would keep). One cooperative launch, a grid barrier between
+// phases:
+//   Wv   warp per row i:                 t_i = sum_{j <= i} W_ij v_j
+//   WTt  CTA per 32-column block, 8 row lanes: c_j (+)= sum_{i >= j} W_ij t_i
+//   res  warp per row i (float64):       r_i = b_i - sum_j A_ij c_j
+// W's upper triangle is stored as zero, so full row segments are read.
+template <typename T>
+__global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict__ A, const T* __restrict__ W,
+                                                        const double* __restrict__ b, double* __restrict__ c,
+                                                        T* __restrict__ t, T* __restrict__ r, int M, int refine,
+                                                        GpStatus* st, GridBar* gb) {
+    __shared__ T red[NT / 32][IB + 1];
+    if (status_code(st) != 0) return;  // set before this launch: every CTA leaves
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    const int nb = (M + IB - 1) / IB;
+    auto w_apply = [&](const T* v) {
+        for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
+            const T* row = W + (int64_t)i * M;
+            T s = T(0);
+            for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) t[i] = s;
+        }
+    };
+    auto wt_apply = [&](bool accumulate) {
+        for (int J = blockIdx.x; J < nb; J += G) {
+            const int j = J * IB + lane;
+            T s = T(0);
+            if (j < M)
+                for (int i = J * IB + warp; i < M; i += NT / 32) s = fma(W[(int64_t)i * M + j], t[i], s);
+            red[warp][lane] = s;
+            __syncthreads();
+            if (warp == 0 && j < M) {
+                T v = T(0);
+#pragma unroll
+                for (int w = 0; w < NT / 32; ++w) v += red[w][lane];
+                c[j] = (accumulate ? c[j] : 0.0) + (double)v;
+            }
+            __syncthreads();
+        }
+    };
+    for (int i = blockIdx.x * NT + tid; i < M; i += G * NT) r[i] = (T)b[i];
+    if (!grid_sync(gb, st)) return;
+    w_apply(r);
+    if (!grid_sync(gb, st)) return;
+    wt_apply(false);
+    for (int it = 0; it < refine; ++it) {
+        if (!grid_sync(gb, st)) return;
+        for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
+            const double* row = A + (int64_t)i * M;
+            double s = 0.0;
+            for (int j = lane; j < M; j += 32) s = fma(row[j], c[j], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) r[i] = (T)(b[i] - s);
+        }
+        if (!grid_sync(gb, st)) return;
+        w_apply(r);
+        if (!grid_sync(gb, st)) return;
+        wt_apply(true);
     }
 }
 
@@ -716,9 +629,8 @@ int coop_grid(const void* kern, int dev) {
 }  // namespace
 
 size_t factor_work_bytes(int M, bool fp32_inverse) {
-    const size_t nb = (M + IB - 1) / IB;
-    const size_t el = fp32_inverse ? sizeof(float) : sizeof(double);
-    const size_t inv = el * ((size_t)M * M + nb * IB * IB);
+    // inverse: L and W in float32 plus X (mixed), or X alone (float64)
+    const size_t inv = fp32_inverse ? 3 * sizeof(float) * (size_t)M * M : sizeof(double) * (size_t)M * M;
     const size_t chol = sizeof(double) * (size_t)M;  // 1 / L_jj
     return CHOL_RSD_OFFSET + (inv > chol ? inv : chol);
 }
@@ -752,32 +664,60 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
     cudaGetDevice(&dev);
     GridBar* gb = (GridBar*)work;
     cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
-    char* base = (char*)work + 256;
-    const size_t nb = (M + IB - 1) / IB;
+    char* base = (char*)work + CHOL_RSD_OFFSET;
+    const int nb = (M + IB - 1) / IB;
+    // enough CTAs for the widest phase (the last level's tiles) and level 0
+    int hmax = IB;
+    while (hmax * 2 < M) hmax *= 2;
+    const int hb = hmax / IB;
+    const int want = std::max(nb, ((M + 2 * hmax - 1) / (2 * hmax)) * hb * hb);
     gp_note_launches(1);
-    if (fp32 && M <= STRIP_MAX_M) {
-        float* D = (float*)base;
-        const void* k = (const void*)trinv_strip_kernel;
-        const size_t smem = strip_smem_bytes(M);
-        gp_allow_max_smem((const void*)k);
-        int sms = 1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        dim3 grid((unsigned)((int)nb < sms ? (int)nb : sms)), block(NT);  // one CTA per strip
-        void* args[] = {(void*)&L, &W, &M, &D, &st, &gb};
-        return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
-    }
+    const size_t M2 = (size_t)M * M;
     if (fp32) {
-        float* R = (float*)base;
-        float* D = R + (size_t)M * M;
-        const void* k = (const void*)trinv_coop_kernel<float>;
-        dim3 grid((unsigned)coop_grid(k, dev)), block(NT);
-        void* args[] = {(void*)&L, &W, &M, &R, &D, &st, &gb};
+        float* Lt = (float*)base;
+        float* Wt = Lt + M2;
+        float* X = Wt + M2;
+        const void* k = (const void*)trinv_rec_kernel<float>;
+        dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+        void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &st, &gb};
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
-    double* R = (double*)base;
-    double* D = R + (size_t)M * M;
-    const void* k = (const void*)trinv_coop_kernel<double>;
-    dim3 grid((unsigned)coop_grid(k, dev)), block(NT);
-    void* args[] = {(void*)&L, &W, &M, &R, &D, &st, &gb};
+    double* Lt = nullptr;
+    double* Wt = W;
+    double* X = (double*)base;
+    const void* k = (const void*)trinv_rec_kernel<double>;
+    dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+    void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &st, &gb};
+    return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
+}
+
+size_t solve_refine_work_elems(int M) {
+    return 32 + 2 * (size_t)M;  // grid barrier (256 bytes), t, r
+}
+
+cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
+                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    GridBar* gb = (GridBar*)work;
+    cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
+    const int nb = (M + IB - 1) / IB;
+    const int want = std::max(nb, (M + NT / 32 - 1) / (NT / 32));
+    gp_note_launches(1);
+    if (fp32) {
+        // the float32 W left in the inverse's workspace
+        const float* Wf = (const float*)((const char*)fwork + CHOL_RSD_OFFSET) + (size_t)M * M;
+        float* t = (float*)(work + 32);
+        float* r = t + M;
+        const void* k = (const void*)solve_coop_kernel<float>;
+        dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+        void* args[] = {(void*)&A, (void*)&Wf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
+        return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
+    }
+    double* t = work + 32;
+    double* r = t + M;
+    const void* k = (const void*)solve_coop_kernel<double>;
+    dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+    void* args[] = {(void*)&A, (void*)&W, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
     return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }

@@ -72,7 +72,7 @@ void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, do
 int gp_static_gram(const double* X, const double* y, int64_t N, int p, int n, double eps,
                    double alpha, double* G, double* b, cudaStream_t stream, int64_t* detail);
 
-// ---- factorisation (gp_factor.cu) and solves (gp_chol.cu) ----------------------
+// ---- factorisation, inverse and solve (gp_factor.cu) ---------------------------
 // Device workspace (bytes) for launch_cholesky and launch_tri_inverse.
 size_t factor_work_bytes(int M, bool fp32_inverse);
 // In-place lower Cholesky of the M x M row-major matrix L (upper part ignored,
@@ -84,10 +84,11 @@ cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStre
 cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
                                cudaStream_t stream);
 // c = A^{-1} b through W = L^{-1}: c = W^T (W b), then `refine` steps of
-// c += W^T W (b - A c) with the float64 residual.
-cudaError_t launch_solve_refine(const double* A, const double* W, const double* b, double* c,
-                                double* work, int M, int refine, const GpStatus* st,
-                                cudaStream_t stream);
+// c += W^T W (b - A c) with the float64 residual, one cooperative launch.
+// fp32: the products use the float32 W that launch_tri_inverse left in
+// fwork (its workspace); otherwise W itself.
+cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
+                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream);
 size_t solve_refine_work_elems(int M);
 
 // ---- float64 predict (gp_predict64.cu) -----------------------------------------

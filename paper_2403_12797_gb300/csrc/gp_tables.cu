@@ -16,6 +16,9 @@
 
 namespace {
 
+// up to this n the recurrence coefficients are staged in shared memory
+constexpr int COEF_SMEM_N = 2048;
+
 template <typename T>
 __device__ __forceinline__ T gp_exp(T v);
 template <>
@@ -34,6 +37,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double* __restrict__ X,
                                                          const double* __restrict__ y,
                                                          T* __restrict__ tab, GpStatus* st) {
+    // recurrence coefficients sqrt(2/(k+1)), sqrt(k/(k+1)), once per block
+    extern __shared__ __align__(16) unsigned char coef_raw[];
+    T* ca = reinterpret_cast<T*>(coef_raw);
+    T* cb = ca + s.n;
+    const bool staged = s.n <= COEF_SMEM_N;
+    if (staged) {
+        for (int k = threadIdx.x; k < s.n; k += blockDim.x) {
+            ca[k] = gp_sqrt<T>(T(2) / T(k + 1));
+            cb[k] = gp_sqrt<T>(T(k) / T(k + 1));
+        }
+        __syncthreads();
+    }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= s.Npad) return;
@@ -56,8 +71,8 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     T q1 = gp_sqrt<T>(T(2)) * t * q0;
     out[s.Npad] = q1;
     for (int k = 1; k + 1 < s.n; ++k) {
-        const T a = gp_sqrt<T>(T(2) / T(k + 1));
-        const T b = gp_sqrt<T>(T(k) / T(k + 1));
+        const T a = staged ? ca[k] : gp_sqrt<T>(T(2) / T(k + 1));
+        const T b = staged ? cb[k] : gp_sqrt<T>(T(k) / T(k + 1));
         const T q2 = a * t * q1 - b * q0;
         out[(int64_t)(k + 1) * s.Npad] = q2;
         q0 = q1;
@@ -74,6 +89,17 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
                                                                  const double* __restrict__ y,
                                                                  float* __restrict__ tab, GpStatus* st) {
     constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
+    extern __shared__ __align__(16) unsigned char coef_raw[];
+    float* ca = reinterpret_cast<float*>(coef_raw);
+    float* cb = ca + s.n;
+    const bool staged = s.n <= COEF_SMEM_N;
+    if (staged) {
+        for (int k = threadIdx.x; k < s.n; k += blockDim.x) {
+            ca[k] = sqrtf(2.f / (float)(k + 1));
+            cb[k] = sqrtf((float)k / (float)(k + 1));
+        }
+        __syncthreads();
+    }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= s.Npad) return;
@@ -107,8 +133,8 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     float q1 = sqrtf(2.f) * t * q0;
     out[WS] = q1;
     for (int k = 1; k + 1 < s.n; ++k) {
-        const float a = sqrtf(2.f / (float)(k + 1));
-        const float b = sqrtf((float)k / (float)(k + 1));
+        const float a = staged ? ca[k] : sqrtf(2.f / (float)(k + 1));
+        const float b = staged ? cb[k] : sqrtf((float)k / (float)(k + 1));
         const float q2 = a * t * q1 - b * q0;
         out[(k + 1) * WS] = q2;
         q0 = q1;
@@ -141,6 +167,11 @@ __global__ void __launch_bounds__(256) table_absmax_kernel(const float* __restri
     }
 }
 
+template <typename T>
+size_t coef_bytes(const GpShape& s) {
+    return s.n <= COEF_SMEM_N ? 2 * sizeof(T) * (size_t)s.n : 0;
+}
+
 }  // namespace
 
 void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmaxb, unsigned int* tmax,
@@ -153,13 +184,13 @@ void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmax
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<double><<<grid, 256, 0, stream>>>(s, X, y, tab, st);
+    eig_tables_kernel<double><<<grid, 256, coef_bytes<double>(s), stream>>>(s, X, y, tab, st);
 }
 
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<float><<<grid, 256, 0, stream>>>(s, X, y, tab, st);
+    eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tab, st);
 }
 
 size_t syrktc_table_floats(const GpShape& s) {
@@ -169,5 +200,5 @@ size_t syrktc_table_floats(const GpShape& s) {
 void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
                                GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_chunked_kernel<<<grid, 256, 0, stream>>>(s, X, y, tabc, st);
+    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, st);
 }
