@@ -289,7 +289,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": ("f16 tensor (integer + remainder slices, f32 acc in exact 512-row blocks) "
+           "dtype": ("f16 tensor (integer + remainder slices, f32 acc in exact 1024-row blocks) "
                      "+ f64 factorisation") if prec != "fp64" else "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "prec": prec, "l2": "flushed between steps (256 MiB write)",

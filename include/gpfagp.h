@@ -71,10 +71,10 @@ typedef struct gp_model gp_model;
  *                tensor cores with bf16 operands:
  *                - Phi^T Phi: each column is scaled by a power of two so that
  *                  |w| <= 128 and split into the integer s1 = rint(w) (exact
- *                  in bf16) and lo = bf16(w - s1); s1*s1' is summed EXACTLY
- *                  in float32 TMEM over 512-row blocks, s1*lo' + lo*s1' +
- *                  lo*lo' beside it; blocks are added in float32 with
- *                  round-to-nearest (no truncation drift);
+ *                  in fp16) and lo = fp16(w - s1); s1*s1' is summed EXACTLY
+ *                  in float32 TMEM over 1024-row blocks, s1*lo' + lo*s1' +
+ *                  lo*lo' beside it; blocks are folded into float pairs
+ *                  hi + lo by an exact two-sum (no truncation drift);
  *                - Phi_* L^{-T} (variance): bf16 hi/lo split of both
  *                  operands, hi*hi + hi*lo + lo*hi in float32;
  *                Phi^T y and the predictive mean use float32 products;
@@ -127,8 +127,8 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
 
 /* Model flags: GP_MODEL_GRAM_FP64 when a mixed-precision fit recomputed its
- * Gram in float64. The mixed Gram keeps its 512-row block sums exact but
- * sums blocks in float32; when A = G + sigma^2 Lambda^{-1} is conditioned
+ * Gram in float64. The mixed Gram keeps its 1024-row block sums exact and
+ * folds the blocks into ~46-bit float pairs; when A = G + sigma^2 Lambda^{-1} is conditioned
  * beyond what that carries (large N with a small noise variance) the
  * float64 Cholesky meets a non-positive pivot, and the fit (gp_fit_ex,
  * gp_fit_batch, server refits) then redoes the Gram with the float64 kernel

@@ -14,7 +14,7 @@ void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, f
 
 // Rows per block of the mixed-precision Gram (exact tensor-core sums) and of
 // the per-block table maxima.
-constexpr int GP_TAB_BLOCK = 512;
+constexpr int GP_TAB_BLOCK = 1024;
 // Chunk-major float32 table of the mixed-precision Gram: chunk q of 32 rows
 // holds table row R = j*n + k at tabc[q*RC + R*SYRKTC_WS + i%32] and y in row
 // p*n, RC = (p*n + 1) * SYRKTC_WS (row stride 36 floats, 4 of them zero).

@@ -10,23 +10,25 @@
 // steps of a large N that bias (~1e-4 relative on G) is amplified by the
 // conditioning of A into percent-level errors of the posterior. The kernel
 // therefore keeps the dominant part of every tensor-core sum exact:
-//   * for every 512-row block, each column m is scaled by 2^(7 - E_m), where
+//   * for every 1024-row block, each column m is scaled by 2^(7 - E_m), where
 //     2^(E_m) bounds |Phi[:, m]| inside the block (the product of the block's
 //     per-dimension table maxima), so |w| <= 128 for w = Phi * 2^(7 - E_m);
 //   * w = s1 + lo with the integer s1 = rint(w) (exact in fp16) and the
 //     remainder lo = fp16(w - s1), |w - s1| <= 1/2 (2^-12 absolute error);
-//   * acc1 += s1 s1' is an integer sum below 2^24 for blocks of 512 rows,
-//     hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo' is a few
+//   * acc1 += s1 s1' is an integer sum of magnitude at most 1024 * 128^2 =
+//     2^24 over a block, hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo' is a few
 //     percent of G, so its truncation over one block (~2e-6 of itself) is
 //     negligible;
 //   * after each block the producers multiply acc1 + acc2 by the exact power
 //     of two that maps the block's column scaling to the global one and add
-//     it into float32 registers; every FLUSH_BLOCKS blocks those are folded
-//     into the split's partial tile of float pairs (hi + lo, an exact
-//     two-sum, ~46 bits), while the MMAs fill the other
-//     TMEM buffer (two buffers x 256 columns = all 512); summing the blocks
-//     in float32 instead would lose ~1e-6 of G over a million rows, enough
-//     to make a strongly conditioned A indefinite.
+//     it into a float32 sum held in TMEM (columns 256-383, beside acc1 and
+//     acc2); every FLUSH_BLOCKS blocks that sum is folded into the split's
+//     partial tile, kept as unevaluated float pairs hi + lo (an exact
+//     two-sum, ~46 bits) in L2-resident memory that only the folding thread
+//     touches. Summing the blocks in float32 instead would lose ~1e-6 of G
+//     over a million rows, enough to make a strongly conditioned A
+//     indefinite. With 1024-row blocks a drain is rare, so the accumulators
+//     are single-buffered: the MMAs of the next block wait for it.
 // Representation error: |w - s1 - lo| <= 2^-12 (2^-19 of the block bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
@@ -47,7 +49,7 @@
 //              (A tiles and windows) and signals finished blocks.
 // Every warp waits on mbarriers by itself (bounded, decided by a warp vote):
 // there is no CTA-wide barrier inside the pipeline. The block exponents E_m
-// per 512-row block and the global ones come from a small kernel run first.
+// per 1024-row block and the global ones come from a small kernel run first.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
@@ -59,8 +61,9 @@ constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
 constexpr int WS = SYRKTC_WS;              // floats per window row (36: bank-conflict padding)
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
-constexpr int BLOCK_CHUNKS = GP_TAB_BLOCK / BK;  // 16 chunks = 512 rows per exact TMEM block
-constexpr int FLUSH_BLOCKS = 4;            // blocks summed in float32 registers between flushes
+constexpr int BLOCK_CHUNKS = GP_TAB_BLOCK / BK;  // 32 chunks = 1024 rows per exact TMEM block
+constexpr int B_FOLD = 16;                 // chunks between float64 folds of b (512 rows)
+constexpr int FLUSH_BLOCKS = 4;            // blocks summed in the TMEM float32 sum between flushes
 constexpr int TILE_BYTES = TM * BK * 2;    // one 16-bit operand tile: 8 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A lo, B s1, B lo
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
@@ -70,7 +73,7 @@ constexpr int NPW = NPROD / 32;
 constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain (32)
 constexpr int MMA_WARP = NPW;
 constexpr int NTHREADS = NPROD + 64;
-constexpr uint32_t TMEM_COLS = 512;        // 2 buffers x (acc1 | acc2)
+constexpr uint32_t TMEM_COLS = 512;        // acc1 | acc2 | float32 block sum | unused
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct SmemTC {
@@ -85,8 +88,8 @@ struct SmemTC {
     uint64_t* empty;      // STAGES: MMAs of the stage done
     uint64_t* tfull;      // WRMAX: window landed (count 1 + tx bytes)
     uint64_t* wempty;     // WRMAX: every producer warp has read the window (count NPW)
-    uint64_t* accf;       // 2: block finished in TMEM buffer u
-    uint64_t* drained;    // 2: TMEM buffer u has been read back
+    uint64_t* accf;       // the block's MMAs are done (acc1, acc2 final)
+    uint64_t* drained;    // acc1 and acc2 have been read back (count NPROD)
     uint32_t* tmem_base;
 };
 
@@ -148,7 +151,7 @@ __device__ __forceinline__ int column_exp(const GpShape& s, const unsigned int* 
     return E < -100 ? -100 : E;
 }
 
-// Column exponents: ebx[b * Mpad + m] = E_m of 512-row block b (b < nblk),
+// Column exponents: ebx[b * Mpad + m] = E_m of 1024-row block b (b < nblk),
 // colexp[m] = the global E_m (blockIdx.y == nblk); 0 for padding columns.
 __global__ void colexp_kernel(GpShape s, const unsigned int* __restrict__ tmaxb,
                               const unsigned int* __restrict__ tmax, int nblk, int* __restrict__ colexp,
@@ -310,10 +313,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.tfull[i], 1);
             mbar_init(&sm.wempty[i], NPW);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&sm.accf[i], 1);
-            mbar_init(&sm.drained[i], NPROD);
-        }
+        mbar_init(sm.accf, 1);
+        mbar_init(sm.drained, NPROD);
         mbar_fence_init();
     }
     if (warp == MMA_WARP) tmem_alloc(sm.tmem_base, TMEM_COLS);
@@ -360,73 +361,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // b: float32 within a block, float64 across blocks
         float bacc = 0.f;
         double bsum = 0.0;
-        // This thread's part of its tile row: blocks are summed in float32
-        // registers (gacc) for FLUSH_BLOCKS blocks, then folded into the
-        // split's partial tile, kept as unevaluated float pairs hi + lo
-        // (~46-bit sums), by an exact two-sum in float32 arithmetic
-        // (read-modify-write of memory only this thread touches, resident in
-        // L2). The long sums over blocks thus lose nothing that matters, while
-        // staying off the slow float64 pipe and off the drain's critical path
-        // most of the time.
+        // This thread's part of its tile row in the split's partial tile:
+        // (hi, lo) float pairs of CPT columns.
         float2* grow = Gpart + ((int64_t)split * npairs + q) * (TM * TM) +
                        (int64_t)(quarter * 32 + lane) * TM + cgrp * CPT;
-        float gacc[CPT];
-#pragma unroll
-        for (int i = 0; i < CPT; ++i) gacc[i] = 0.f;
-        bool flushed = false;
-        auto flush = [&]() {
-            // hi + v = s + e exactly (Knuth's two-sum); lo collects e
-            auto add2 = [](float& hi, float& lo, float v) {
-                const float s = __fadd_rn(hi, v);
-                const float t = __fsub_rn(s, hi);
-                const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, t)), __fsub_rn(v, t));
-                hi = s;
-                lo = __fadd_rn(lo, e);
-            };
-            float4* g4 = reinterpret_cast<float4*>(grow);  // (hi, lo) of two elements
-#pragma unroll
-            for (int k = 0; k < CPT / 2; ++k) {
-                float4 o = flushed ? g4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                add2(o.x, o.y, gacc[2 * k]);
-                add2(o.z, o.w, gacc[2 * k + 1]);
-                g4[k] = o;
-                gacc[2 * k] = 0.f;
-                gacc[2 * k + 1] = 0.f;
-            }
-            flushed = true;
-        };
+        bool flushed = false;  // the partial tile holds a first fold
         bool ok = true;
         const int blk0 = (int)(r0 / GP_TAB_BLOCK);
+        const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + cgrp * CPT;  // lanes, first column
         auto drain = [&](int d) -> bool {
-            const int u = d & 1;
-            if (!__all_sync(FULLMASK, mbar_wait(&sm.accf[u], (d >> 1) & 1))) {
+            if (!__all_sync(FULLMASK, mbar_wait(sm.accf, d & 1))) {
                 if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 4);
                 return false;
             }
             tc_fence_after();
-            const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + (uint32_t)u * 256 + cgrp * CPT;
             // back to the global column scaling: 2^(E_blk - E_glob) (exact powers of two)
             const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
             const int row = quarter * 32 + lane;
             const float mrow = pow2_down((int)eb[I * TM + row] - sm.egI[row]);
             const signed char* ebc = eb + J * TM + cgrp * CPT;
             const int* egc = (diag ? sm.egI : sm.egJ) + cgrp * CPT;
-#pragma unroll
+            const bool fresh = (d % FLUSH_BLOCKS == 0);                  // the TMEM sum is empty
+            const bool fold = ((d + 1) % FLUSH_BLOCKS == 0 || d + 1 == nblocks);
+            float4* g4 = reinterpret_cast<float4*>(grow);  // (hi, lo) of two columns
+            // hi + v = s + e exactly (Knuth's two-sum); lo collects e
+            auto add2 = [](float& hi, float& lo, float v) {
+                const float sum = __fadd_rn(hi, v);
+                const float t = __fsub_rn(sum, hi);
+                const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, t)), __fsub_rn(v, t));
+                hi = sum;
+                lo = __fadd_rn(lo, e);
+            };
+#pragma unroll 1
             for (int ch = 0; ch < CPT / 8; ++ch) {
                 const int2 e2 = *reinterpret_cast<const int2*>(ebc + ch * 8);
-                float a1[8], a2[8];
+                float a1[8], a2[8], g[8];
                 tmem_ld8(tmem + lrow + ch * 8, a1);
                 tmem_ld8(tmem + lrow + 128 + ch * 8, a2);
+                if (!fresh) tmem_ld8(tmem + lrow + 256 + ch * 8, g);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int eblk = (int)(signed char)((i < 4 ? e2.x : e2.y) >> (8 * (i & 3)));
                     const float mc = pow2_down(eblk - egc[ch * 8 + i]);
-                    gacc[ch * 8 + i] = fmaf(a1[i] + a2[i], mrow * mc, gacc[ch * 8 + i]);
+                    g[i] = fmaf(a1[i] + a2[i], mrow * mc, fresh ? 0.f : g[i]);
+                }
+                if (fold) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float4 o = flushed ? g4[ch * 4 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        add2(o.x, o.y, g[2 * k]);
+                        add2(o.z, o.w, g[2 * k + 1]);
+                        g4[ch * 4 + k] = o;
+                    }
+                } else {
+                    tmem_st8(tmem + lrow + 256 + ch * 8, g);
                 }
             }
+            if (fold) flushed = true;
+            tmem_wait_st();
             tc_fence_before();
-            mbar_arrive(&sm.drained[u]);
-            if ((d + 1) % FLUSH_BLOCKS == 0 || d + 1 == nblocks) flush();
+            mbar_arrive(sm.drained);
             return true;
         };
 
@@ -452,10 +446,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = false;
                 break;
             }
-            if (c % BLOCK_CHUNKS == 0) {
+            if (c % B_FOLD == 0) {
                 bsum += (double)bacc;
                 bacc = 0.f;
-                // a new 512-row block: quantisation scales 2^(7 - E_blk)
+            }
+            if (c % BLOCK_CHUNKS == 0) {
+                // a new 1024-row block: quantisation scales 2^(7 - E_blk)
                 scI = pow2i(7 - eI);
                 scJ = pow2i(7 - eJ);
                 const int nb = c / BLOCK_CHUNKS + 1;
@@ -500,8 +496,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 wsl = 0;
                 wph ^= 1;
             }
-            // drain a finished block once nst chunks of the next one are queued
-            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) - 1 + nst <= c) {
+            // drain a finished block once one chunk of the next one is queued
+            // (its MMAs are normally done by then; the next block's wait for it)
+            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) <= c) {
                 if (!drain(next_drain)) {
                     ok = false;
                     break;
@@ -530,8 +527,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sbase = smem_u32(sm.stage);
             int stg = 0, sph = 0;
             for (int c = 0; c < nchunks; ++c) {
-                const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS, u = d & 1;
-                if (cb == 0 && d >= 2 && !mbar_wait(&sm.drained[u], ((d >> 1) - 1) & 1)) {
+                const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS;
+                // the accumulators of block d - 1 have been read back
+                if (cb == 0 && d >= 1 && !mbar_wait(sm.drained, (d - 1) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 5);
                     break;
                 }
@@ -540,8 +538,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t acc1 = tmem + (uint32_t)u * 256;
-                const uint32_t acc2 = acc1 + 128;
+                const uint32_t acc1 = tmem;
+                const uint32_t acc2 = tmem + 128;
                 const uint32_t a1 = sbase + stg * STAGE_BYTES;
                 const uint32_t a2 = a1 + TILE_BYTES;
                 const uint32_t b1 = diag ? a1 : a1 + 2 * TILE_BYTES;
@@ -560,7 +558,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_bf16(acc2, dA2, dB2, idesc, 1u);    // lo lo'
                 }
                 mma_commit(&sm.empty[stg]);
-                if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(&sm.accf[u]);
+                if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(sm.accf);
                 if (++stg == nst) {
                     stg = 0;
                     sph ^= 1;

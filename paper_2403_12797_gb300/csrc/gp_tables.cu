@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     }
 }
 
-// Per 512-row block b and table row R: tmaxb[b * rows + R] = max |T[R][i]|
+// Per GP_TAB_BLOCK-row block b and table row R: tmaxb[b * rows + R] = max |T[R][i]|
 // over the block (chunk-major layout above), and tmax[R] = the maximum over
 // all blocks, as float bits (non-negative floats order like their bit
 // patterns). tmax must be zeroed.
