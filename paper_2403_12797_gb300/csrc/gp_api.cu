@@ -119,18 +119,34 @@ int read_status(GpStatus* st, cudaStream_t s) {
     return GP_OK;
 }
 
-// Split the (padded) rows so that tile pairs x splits fill the GPU; every
-// split is a multiple of `granule` rows.
+// Split the (padded) rows among CTAs: every split is a multiple of `granule`
+// rows, and the split count minimises (waves of tile pairs x splits over
+// `target_ctas` resident CTAs) x (rows per split + a fixed cost of one block
+// of rows per CTA: pipeline fill, drain, partial tile) -- the time of the
+// longest CTA chain -- preferring fewer splits on ties (less partial-tile
+// memory to reduce), within eight waves. E.g. 528 tile pairs on 152 CTAs:
+// one split takes 4 waves of the whole row range, two splits 7 waves of half
+// of it.
 void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, int* nsplit,
                    int64_t* rps) {
-    int64_t want = target_ctas / npairs;  // never more CTAs than one wave
-    int64_t maxs = Npad / 256;            // at least 256 rows per split
-    if (want > maxs) want = maxs;
-    if (want < 1) want = 1;
-    if (want > 65535) want = 65535;
-    int64_t r = gp_round_up((Npad + want - 1) / want, granule);
-    *rps = r;
-    *nsplit = (int)((Npad + r - 1) / r);
+    if (target_ctas < 1) target_ctas = 1;
+    int64_t maxs = Npad / 256;  // at least 256 rows per split
+    if (maxs < 1) maxs = 1;
+    if (maxs > 4096) maxs = 4096;
+    int64_t best_r = gp_round_up(Npad, granule), best_cost = -1;
+    for (int64_t want = 1; want <= maxs; ++want) {
+        const int64_t r = gp_round_up((Npad + want - 1) / want, granule);
+        const int64_t ns = (Npad + r - 1) / r;
+        const int64_t waves = (npairs * ns + target_ctas - 1) / target_ctas;
+        if (ns > 1 && ns * npairs > 8 * (int64_t)target_ctas) break;
+        const int64_t cost = waves * (r + 1024);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_r = r;
+        }
+    }
+    *rps = best_r;
+    *nsplit = (int)((Npad + best_r - 1) / best_r);
 }
 
 int num_sms(int dev) {

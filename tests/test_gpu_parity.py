@@ -103,6 +103,37 @@ def test_workload2_full_size(prec):
     assert O.relerr(var, vo) < TOL[prec]["var"], O.relerr(var, vo)
 
 
+def test_workload3_full_size_gram_sampled():
+    """The M = 4096, N = 2,000,000 workload at full size, mixed precision, in
+    the launch configuration the fit uses: 200 sampled entries of G = Phi^T Phi
+    (40 of them diagonal) and 50 of b = Phi^T y against dot products of the
+    oracle's eigenfunction columns (Eq. 19), computed one by one.
+
+    Bound: each Phi value is represented within 2^-19 of its 1024-row block
+    bound B (integer + fp16 remainder split), so
+    |dG_ac| <= 2^-19 sum_i (B_a |Phi_ic| + B_c |Phi_ia|), i.e. relative to
+    |Phi_a| |Phi_c| at most 2^-19 (B_a sqrt(N)/|Phi_a| + B_c sqrt(N)/|Phi_c|);
+    the columns' peak-to-RMS ratios stay below 10 here, giving 4e-5. The
+    block sums add ~1e-7 of G (truncation of the float32 remainder sums)."""
+    pr = W.workload3()
+    M = pr.n ** 3
+    G, b = _lib.gram(pr.X, pr.y, pr.n, pr.eps, pr.alpha, prec="mixed")
+    E = [O.eigenfunctions_1d(pr.X[:, j], pr.n, pr.eps, pr.alpha) for j in range(3)]
+    idx = O.multi_index(pr.n, 3)
+
+    def col(m):
+        return E[0][:, idx[m, 0]] * E[1][:, idx[m, 1]] * E[2][:, idx[m, 2]]
+
+    rng = np.random.default_rng(5)
+    pairs = rng.integers(0, M, size=(200, 2))
+    pairs[:40, 1] = pairs[:40, 0]
+    errs = [abs(G[a, c] - float(col(a) @ col(c))) / np.sqrt(G[a, a] * G[c, c]) for a, c in pairs]
+    assert max(errs) < 4e-5, max(errs)
+    ynorm = float(np.sqrt(pr.y @ pr.y))
+    berr = [abs(b[k] - float(col(k) @ pr.y)) / (np.sqrt(G[k, k]) * ynorm) for k in rng.integers(0, M, size=50)]
+    assert max(berr) < 4e-5, max(berr)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_fit_is_deterministic_and_device_path_matches_host(prec):
     import torch
