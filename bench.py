@@ -295,7 +295,10 @@ def run_ours(args):
            "config": {"workload": WORKLOAD, "prec": prec, "l2": "flushed between steps (256 MiB write)",
                       "replicas": world},
            "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-           "roofline_syrk": roof_syrk, "kernel_shares": shares}
+           "roofline_syrk": roof_syrk, "kernel_shares": shares,
+           # device time of the kernel groups per step; the rest of ms_per_step is the
+           # host's turnaround inside the API calls (status reads, the fit -> predict handoff)
+           "device_busy_ms_per_step": sum(g["total_ms"] for g in groups.values()) / args.steps}
 
     if rank == 0 and not args.quick:
         extra = compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np)

@@ -111,9 +111,13 @@ __global__ void pad_y_kernel(const double* __restrict__ y, int64_t N, int64_t Np
 }
 
 int read_status(GpStatus* st, cudaStream_t s) {
-    GpStatus h;
-    cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    PinnedBlock pb = pinned_get(sizeof(GpStatus));
+    GpStatus local;
+    GpStatus* hp = pb.p ? (GpStatus*)pb.p : &local;
+    cudaError_t e = cudaMemcpyAsync(hp, st, sizeof(GpStatus), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const GpStatus h = *hp;
+    if (pb.p) pinned_put(pb);
     if (e != cudaSuccess) return cuda_err(e, "status read");
     if (h.code != GP_OK) return set_err(h.code, h.detail);
     return GP_OK;
@@ -247,7 +251,7 @@ void free_model(gp_model* h) {
     cudaGetDevice(&cur);
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    void* ps[] = {h->L, h->W, h->c, h->b, h->d, h->Wpack, h->cinfo};
+    void* ps[] = {h->block};
     for (void* p : ps)
         if (p) cudaFree(p);
     cudaSetDevice(cur);
@@ -274,36 +278,78 @@ gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, doub
 }
 
 // The model's own device buffers (kept until gp_free).
+// The model's device buffers, carved from one allocation (kept until gp_free).
 int fit_alloc(gp_model* h, cudaStream_t stream) {
-    const int M = h->shape.M;
+    const size_t M = (size_t)h->shape.M;
+    const bool tc = h->prec != GP_PREC_FP64;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t sizes[7] = {sizeof(double) * M * M, sizeof(double) * M * M, sizeof(double) * M,
+                             sizeof(double) * M,     sizeof(double) * M,
+                             tc ? predtc_wpack_bytes((int)M) : 0,
+                             tc ? sizeof(int) * predtc_cinfo_ints(h->shape) : 0};
+    size_t total = 0;
+    for (size_t b : sizes) total += al(b);
     int rc;
-    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->L, stream))) return rc;
-    if ((rc = model_alloc(h, sizeof(double) * M * M, (void**)&h->W, stream))) return rc;
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->c, stream))) return rc;
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->b, stream))) return rc;
-    if ((rc = model_alloc(h, sizeof(double) * M, (void**)&h->d, stream))) return rc;
-    if (h->prec != GP_PREC_FP64) {
-        if ((rc = model_alloc(h, predtc_wpack_bytes(M), (void**)&h->Wpack, stream))) return rc;
-        if ((rc = model_alloc(h, sizeof(int) * predtc_cinfo_ints(h->shape), (void**)&h->cinfo, stream)))
-            return rc;
+    if ((rc = model_alloc(h, total, &h->block, stream))) return rc;
+    char* p = (char*)h->block;
+    void** dst[7] = {(void**)&h->L, (void**)&h->W, (void**)&h->c, (void**)&h->b,
+                     (void**)&h->d, (void**)&h->Wpack, (void**)&h->cinfo};
+    for (int i = 0; i < 7; ++i) {
+        *dst[i] = sizes[i] ? (void*)p : nullptr;
+        p += al(sizes[i]);
     }
     return GP_OK;
 }
 
+// ---------------------------------------------------------------- pinned staging pool
+
+namespace {
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_pin_free;  // capacity -> block
+}  // namespace
+
+PinnedBlock pinned_get(size_t bytes) {
+    size_t cap = 4096;
+    while (cap < bytes) cap *= 2;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        auto it = g_pin_free.lower_bound(cap);
+        if (it != g_pin_free.end() && it->first <= 4 * cap) {
+            PinnedBlock b{it->second, it->first};
+            g_pin_free.erase(it);
+            return b;
+        }
+    }
+    PinnedBlock b;
+    if (cudaHostAlloc(&b.p, cap, cudaHostAllocPortable) == cudaSuccess) {
+        b.cap = cap;
+    } else {
+        cudaGetLastError();
+        b.p = nullptr;
+    }
+    return b;
+}
+
+void pinned_put(PinnedBlock b) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.emplace(b.cap, b.p);
+}
 
 // Copy the shape-only inputs (log eigenvalues, and the predict chunk table
-// into the model) to the device.
+// into the model) to the device, from pinned staging memory.
 int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream) {
     const GpShape& s = h->shape;
-    stage.loglam.resize(s.n);
-    log_eigenvalues(s.n, h->eps, h->alpha, stage.loglam.data());
-    cudaError_t e = cudaMemcpyAsync(loglam_d, stage.loglam.data(), sizeof(double) * s.n,
-                                    cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && h->prec != GP_PREC_FP64) {
-        stage.cinfo.resize(predtc_cinfo_ints(s));
-        predtc_build_cinfo(s, stage.cinfo.data());
-        e = cudaMemcpyAsync(h->cinfo, stage.cinfo.data(), sizeof(int) * stage.cinfo.size(),
-                            cudaMemcpyHostToDevice, stream);
+    const size_t nci = h->prec != GP_PREC_FP64 ? predtc_cinfo_ints(s) : 0;
+    const size_t lbytes = sizeof(double) * (size_t)s.n;
+    stage.buf = pinned_get(lbytes + sizeof(int) * nci);
+    if (!stage.buf.p) return set_err(GP_ENOMEM, (int64_t)(lbytes + sizeof(int) * nci));
+    double* ll = (double*)stage.buf.p;
+    log_eigenvalues(s.n, h->eps, h->alpha, ll);
+    cudaError_t e = cudaMemcpyAsync(loglam_d, ll, lbytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && nci > 0) {
+        int* ci = (int*)((char*)stage.buf.p + lbytes);
+        predtc_build_cinfo(s, ci);
+        e = cudaMemcpyAsync(h->cinfo, ci, sizeof(int) * nci, cudaMemcpyHostToDevice, stream);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "shape-input copies");
 }

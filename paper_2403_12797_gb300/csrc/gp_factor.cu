@@ -28,6 +28,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace {
 
@@ -618,12 +621,24 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
     }
 }
 
+// CTAs of a cooperative launch of `kern` (one per SM), cached per kernel and
+// device: the occupancy query costs more host time than the launch itself.
 int coop_grid(const void* kern, int dev) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({kern, dev});
+        if (it != cache.end()) return it->second;
+    }
     int sms = 1, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
     if (occ < 1) occ = 1;
-    return sms * (occ < 2 ? occ : 1);
+    const int g = sms * (occ < 2 ? occ : 1);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[{kern, dev}] = g;
+    return g;
 }
 
 }  // namespace

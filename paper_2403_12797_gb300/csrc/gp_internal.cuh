@@ -20,6 +20,7 @@ struct gp_model {
     uint16_t* Wpack;        // bf16 hi/lo operand layout of W (GP_PREC_MIXED only)
     int* cinfo;             // chunk table of the tensor-core predict (GP_PREC_MIXED only)
     int flags;              // GP_MODEL_GRAM_FP64: Gram recomputed in float64 (mixed mode)
+    void* block;            // the one device allocation the buffers above are carved from
 };
 
 namespace gpi {
@@ -31,10 +32,16 @@ int cuda_err(cudaError_t e, const char* where = "");
 // stream-ordered allocation (honours gp_debug_fail_alloc_after)
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 
-// Frees every registered pointer on the stream when it goes out of scope.
+// Stream-ordered scratch: requests are carved (256-byte aligned) from chunks
+// of at least 1 MiB, so a fit makes a few allocations instead of one per
+// buffer; every chunk is freed on the stream when the object goes out of
+// scope.
 struct Scratch {
+    static constexpr size_t kChunk = (size_t)1 << 20;
     cudaStream_t s;
-    std::vector<void*> ptrs;
+    std::vector<void*> ptrs;  // chunks
+    char* cur = nullptr;
+    size_t left = 0;
     explicit Scratch(cudaStream_t st) : s(st) {}
     ~Scratch() {
         for (void* p : ptrs)
@@ -42,12 +49,25 @@ struct Scratch {
     }
     template <typename T>
     int get(T** p, size_t count) {
-        void* v = nullptr;
-        cudaError_t e = dev_alloc(&v, count * sizeof(T), s);
-        if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)(count * sizeof(T)));
-        if (e != cudaSuccess) return cuda_err(e, "scratch allocation");
-        ptrs.push_back(v);
-        *p = (T*)v;
+        size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        if (bytes > left) {
+            const size_t sz = bytes > kChunk ? bytes : kChunk;
+            void* v = nullptr;
+            cudaError_t e = dev_alloc(&v, sz, s);
+            if (e == cudaErrorMemoryAllocation) return set_err(GP_ENOMEM, (int64_t)sz);
+            if (e != cudaSuccess) return cuda_err(e, "scratch allocation");
+            ptrs.push_back(v);
+            if (bytes >= kChunk) {  // a large request takes its chunk alone
+                *p = (T*)v;
+                return GP_OK;
+            }
+            cur = (char*)v;
+            left = sz;
+        }
+        *p = (T*)cur;
+        cur += bytes;
+        left -= bytes;
         return GP_OK;
     }
 };
@@ -63,9 +83,27 @@ int fit_alloc(gp_model* h, cudaStream_t stream);
 
 // Host inputs of one fit that its asynchronous copies read: kept alive by
 // the caller until the stream (or graph) has run.
+// Page-locked host memory from a process-wide pool (allocated on first need,
+// reused afterwards): copies from it are asynchronous, where a copy from
+// pageable memory first waits for the whole stream.
+struct PinnedBlock {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+PinnedBlock pinned_get(size_t bytes);  // p == nullptr if the allocation failed
+void pinned_put(PinnedBlock b);
+
+// Host staging of a fit's shape-only inputs, in pinned memory that stays
+// valid until the object is destroyed (after the stream has been synchronised
+// or the captured graph has run).
 struct FitStage {
-    std::vector<double> loglam;
-    std::vector<int> cinfo;
+    PinnedBlock buf;
+    FitStage() = default;
+    FitStage(const FitStage&) = delete;
+    FitStage& operator=(const FitStage&) = delete;
+    ~FitStage() {
+        if (buf.p) pinned_put(buf);
+    }
 };
 
 // shape-only inputs to the device (log eigenvalues; predict chunk table into the model)
