@@ -215,8 +215,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         if ((rc = sc.get(&ebx, syrktc_ebx_bytes(s)))) return rc;
         {
             GpProf pf("eig_tables", stream);
-            launch_eig_tables_chunked(s, Xd, yd, tabc, st, stream);
-            launch_table_absmax(s, tabc, tmaxb, tmax, stream);
+            launch_eig_tables_chunked(s, Xd, yd, tabc, tmaxb, tmax, st, stream);
             gp_note_launches(2);
         }
         {

@@ -121,6 +121,8 @@ constexpr int CHOL_RSD_OFFSET = 256;
 struct PotrfSmem {
     double a[CB][CB + 1];                  // the block: lower part updated in place
     double l[2][CB];                       // multipliers a_ij / d_j of the last two pivots
+    double pu[2][CB];                      // a_ij a_{j+1,j} of the last two pivots
+    double r[2];                           // 1 / d_j of the last two pivots
     double d[CB];                          // pivots d_j
     double s[CB];                          // sqrt(d_j)
     double rs[CB];                         // 1 / sqrt(d_j)
@@ -128,29 +130,40 @@ struct PotrfSmem {
     int bad;
 };
 
-// Named barriers of the pivot loop: PUB(j & 1) -- pivot j is published;
-// DONE(j & 1) -- the followers have applied pivot j. Alternating ids keep
-// an arrival for pivot j + 1 off a barrier that pivot j still occupies.
-constexpr int POTRF_BAR_PUB = 1;   // ids 1, 2
-constexpr int POTRF_BAR_DONE = 3;  // ids 3, 4
-constexpr int POTRF_FOLLOW = 192;  // follower threads: warps 1-3 and 5-7
-constexpr int POTRF_BAR_N = 32 + POTRF_FOLLOW;
+// Named barriers of the pivot loop, each a pair used alternately (pivot j
+// takes id + (j & 1)), so an arrival for pivot j + 1 never lands on a barrier
+// that pivot j still occupies:
+//   COL   chain -> helper     column j is final (in shared memory)
+//   PU    helper -> chain     a_ij a_{j+1,j} is ready
+//   R     chain -> helper     1 / d_j is ready
+//   PUB   helper -> followers the multipliers of pivot j are ready
+//   DONE  followers -> chain  pivot j has been applied to the columns >= j + 2
+constexpr int POTRF_BAR_COL = 1;
+constexpr int POTRF_BAR_PU = 3;
+constexpr int POTRF_BAR_R = 5;
+constexpr int POTRF_BAR_PUB = 7;
+constexpr int POTRF_BAR_DONE = 9;
+constexpr int POTRF_FOLLOW = 160;  // follower threads: warps 2, 3, 5, 6, 7
+constexpr int POTRF_PAIR_N = 64;                 // chain + helper
+constexpr int POTRF_FOLLOW_N = 32 + POTRF_FOLLOW; // (helper or chain) + followers
 
 // Factor the w x w diagonal block at (kb, kb) in place (one CTA, w <= 32),
-// right-looking L D L^T in shared memory. The pivot chain runs in warp 0
-// alone (lane i = row i, the current pivot column in a register): for pivot
-// j it broadcasts d_j, forms 1 / d_j (fast_rcp) and the multipliers
-// l_ij = a_ij / d_j, publishes them, and applies pivot j to column j + 1
-// itself, so that column is the next pivot column one FMA later. Warps 1-3
-// and 5-7 (the three other schedulers; warp 4 shares warp 0's float64 pipe
-// and stays idle) apply pivot j to the columns m >= j + 2, one lower-triangle
-// entry per thread from a packed table, so no float64 lane is spent on rows
-// above the diagonal; the chain waits for them only before it reads the
-// next column. Control flow does not depend on the data: a pivot outside
-// [2^-1022, 2^1021) (zero, negative, NaN, beyond any value a Gram matrix plus
-// the clamped noise diagonal reaches) is checked on its high word, recorded
-// as GP_ENOTPD and replaced by NaN. At the end L_jj = sqrt(d_j),
-// L_ij = a_ij / sqrt(d_j) and rsd[kb + j] = 1 / L_jj.
+// right-looking L D L^T in shared memory. Every float64 warp instruction
+// holds its scheduler's float64 pipe for 64 cycles, so the pivot chain gets a
+// scheduler to itself and as few of them as possible: warp 0 (lane i = row i,
+// the current pivot column in a register) broadcasts d_j, forms 1 / d_j
+// (fast_rcp, three FMAs) and applies pivot j to column j + 1 with one FMA,
+// using a_ij a_{j+1,j} that warp 1 (the helper, another scheduler) formed
+// meanwhile; the helper then forms the multipliers l_ij = a_ij / d_j for the
+// followers. Warps 2, 3 and 5-7 (the other schedulers; warp 4 shares warp
+// 0's float64 pipe and stays idle) apply pivot j to the columns m >= j + 2,
+// one lower-triangle entry per thread from a packed table, so no float64 lane
+// is spent on rows above the diagonal; the chain waits for them only before
+// it reads the next column. Control flow does not depend on the data: a
+// pivot outside [2^-1022, 2^1021) (zero, negative, NaN, beyond any value a
+// Gram matrix plus the clamped noise diagonal reaches) is checked on its
+// high word, recorded as GP_ENOTPD and replaced by NaN. At the end
+// L_jj = sqrt(d_j), L_ij = a_ij / sqrt(d_j) and rsd[kb + j] = 1 / L_jj.
 __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
                                            double* __restrict__ rsd, PotrfSmem& sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -166,17 +179,18 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     if (tid == 0) sm.bad = 0;
     __syncthreads();
     if (warp == 0) {
+        // ---- the pivot chain
         double col = sm.a[lane][0];
         for (int j = 0; j < w; ++j) {
-            // column j is final (every pivot < j applied)
-            sm.a[lane][j] = col;
+            sm.a[lane][j] = col;  // column j is final (every pivot < j applied)
+            __syncwarp();
+            named_bar_arrive(POTRF_BAR_COL + (j & 1), POTRF_PAIR_N);
             const double piv = __shfl_sync(0xffffffffu, col, j);
             const int hi = __double2hiint(piv);
             const bool ok = hi >= 0x00100000 && hi < 0x7FD00000;
             const double r = ok ? fast_rcp(piv) : __longlong_as_double(0x7FF8000000000000ll);
-            const double l = (lane > j && lane < w) ? col * r : 0.0;
-            sm.l[j & 1][lane] = l;
             if (lane == 0) {
+                sm.r[j & 1] = r;
                 sm.d[j] = piv;
                 if (!ok) {
                     sm.bad = 1;
@@ -184,19 +198,35 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
                 }
             }
             __syncwarp();
-            named_bar_arrive(POTRF_BAR_PUB + (j & 1), POTRF_BAR_N);
+            named_bar_arrive(POTRF_BAR_R + (j & 1), POTRF_PAIR_N);
             if (j + 1 < w) {
+                named_bar_sync(POTRF_BAR_PU + (j & 1), POTRF_PAIR_N);
                 // the followers have applied pivot j - 1 to the columns >= j + 1
-                if (j >= 1) named_bar_sync(POTRF_BAR_DONE + ((j - 1) & 1), POTRF_BAR_N);
-                const double u = __shfl_sync(0xffffffffu, col, j + 1);  // a_{j+1, j}
-                col = fma(-l, u, sm.a[lane][j + 1]);
+                if (j >= 1) named_bar_sync(POTRF_BAR_DONE + ((j - 1) & 1), POTRF_FOLLOW_N);
+                col = fma(-sm.pu[j & 1][lane], r, sm.a[lane][j + 1]);
             }
         }
-        for (int q = (w > 2 ? w - 2 : 0); q < w; ++q) named_bar_sync(POTRF_BAR_DONE + (q & 1), POTRF_BAR_N);
-    } else if (warp != 4) {
-        const int ft = (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
+        for (int q = (w > 2 ? w - 2 : 0); q < w; ++q) named_bar_sync(POTRF_BAR_DONE + (q & 1), POTRF_FOLLOW_N);
+    } else if (warp == 1) {
+        // ---- the helper: a_ij a_{j+1,j} for the chain, then the multipliers
         for (int j = 0; j < w; ++j) {
-            named_bar_sync(POTRF_BAR_PUB + (j & 1), POTRF_BAR_N);
+            named_bar_sync(POTRF_BAR_COL + (j & 1), POTRF_PAIR_N);
+            const double cj = sm.a[lane][j];
+            const bool below = lane > j && lane < w;
+            if (j + 1 < w) {
+                sm.pu[j & 1][lane] = below ? cj * sm.a[j + 1][j] : 0.0;
+                __syncwarp();
+                named_bar_arrive(POTRF_BAR_PU + (j & 1), POTRF_PAIR_N);
+            }
+            named_bar_sync(POTRF_BAR_R + (j & 1), POTRF_PAIR_N);
+            sm.l[j & 1][lane] = below ? cj * sm.r[j & 1] : 0.0;
+            __syncwarp();
+            named_bar_arrive(POTRF_BAR_PUB + (j & 1), POTRF_FOLLOW_N);
+        }
+    } else if (warp != 4) {
+        const int ft = (warp < 4 ? warp - 2 : warp - 3) * 32 + lane;
+        for (int j = 0; j < w; ++j) {
+            named_bar_sync(POTRF_BAR_PUB + (j & 1), POTRF_FOLLOW_N);
             const int T = w - j - 2;
             const int cnt = T > 0 ? T * (T + 1) / 2 : 0;  // entries of the columns m >= j + 2
             const double* lj = sm.l[j & 1];
@@ -205,7 +235,7 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
                 const int i = (int)(v >> 8), m = (int)(v & 255u);
                 sm.a[i][m] = fma(-lj[i], sm.a[m][j], sm.a[i][m]);
             }
-            named_bar_arrive(POTRF_BAR_DONE + (j & 1), POTRF_BAR_N);
+            named_bar_arrive(POTRF_BAR_DONE + (j & 1), POTRF_FOLLOW_N);
         }
     }
     __syncthreads();

@@ -21,11 +21,9 @@ constexpr int GP_TAB_BLOCK = 1024;
 constexpr int SYRKTC_WS = 36;
 size_t syrktc_table_floats(const GpShape& s);
 void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
-                               GpStatus* st, cudaStream_t stream);
-// tmaxb[b * p*n + j*n + k] = max |tabc row j*n+k| over rows i of block b and
-// tmax[j*n + k] = max over all rows (float bits); zeroes tmax first.
-void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmaxb, unsigned int* tmax,
-                         cudaStream_t stream);
+                               unsigned int* tmaxb, unsigned int* tmax, GpStatus* st, cudaStream_t stream);
+// (also fills) tmaxb[b * p*n + j*n + k] = max |tabc row j*n+k| over rows i of
+// block b, and tmax[j*n + k] = the maximum over all rows (float bits).
 
 // ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
 // Tile 64 x 64, lower-triangular tile pairs x N splits.

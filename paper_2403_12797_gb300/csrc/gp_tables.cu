@@ -84,10 +84,14 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
 // Gram: for chunk q = i / 32 of the rows, table row R = j * n + k at
 // T[q * RC + R * WS + i % 32] (WS = 36 floats, the last 4 zero) and y in row
 // R = p * n, RC = (p * n + 1) * WS. One chunk's rows of every table row are
-// thus one contiguous block that a single bulk copy can move.
+// thus one contiguous block that a single bulk copy can move. Each warp (32
+// rows of one chunk, hence of one GP_TAB_BLOCK-row block) also folds the
+// maxima |T[R][i]| of its rows into tmaxb[block][R] (float bits, zeroed
+// before): the bounds of the Gram's per-block column scaling.
 __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, const double* __restrict__ X,
                                                                  const double* __restrict__ y,
-                                                                 float* __restrict__ tab, GpStatus* st) {
+                                                                 float* __restrict__ tab,
+                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st) {
     constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
     extern __shared__ __align__(16) unsigned char coef_raw[];
     float* ca = reinterpret_cast<float*>(coef_raw);
@@ -102,11 +106,12 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
-    if (i >= s.Npad) return;
+    if (i >= s.Npad) return;  // whole warps: Npad is a multiple of 128
     const int rows = s.p * s.n + 1;
     float* chunk = tab + (i / CW) * (int64_t)rows * WS;
     const int k0 = (int)(i % CW);
     float* out = chunk + (int64_t)j * s.n * WS + k0;
+    unsigned int* bmax = tmaxb + (i / GP_TAB_BLOCK) * (int64_t)(s.p * s.n) + (int64_t)j * s.n;
     if (k0 < WS - CW) {  // zero the padding of this thread's share of the rows
         for (int k = 0; k < s.n; ++k) out[k * WS + CW] = 0.f;
         if (j == 0) chunk[(int64_t)(rows - 1) * WS + CW + k0] = 0.f;
@@ -121,49 +126,46 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
         }
     }
     if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : (float)y[i];
-    if (zero) {
-        for (int k = 0; k < s.n; ++k) out[k * WS] = 0.f;
-        return;
-    }
-    const float x = (float)xd;
+    // every lane runs the whole recurrence (rows beyond N or with bad input
+    // are zero from q0 on), so the warp reductions see all 32 lanes
+    auto emit = [&](int k, float v) {
+        out[k * WS] = v;
+        float m = fabsf(v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(bmax + k, __float_as_uint(m));
+    };
+    const float x = zero ? 0.f : (float)xd;
     const float t = (float)s.alpha_beta * x;
-    float q0 = (float)s.sqrt_beta * expf(-(float)s.delta2 * x * x);
-    out[0] = q0;
+    float q0 = zero ? 0.f : (float)s.sqrt_beta * expf(-(float)s.delta2 * x * x);
+    emit(0, q0);
     if (s.n == 1) return;
     float q1 = sqrtf(2.f) * t * q0;
-    out[WS] = q1;
+    emit(1, q1);
     for (int k = 1; k + 1 < s.n; ++k) {
         const float a = staged ? ca[k] : sqrtf(2.f / (float)(k + 1));
         const float b = staged ? cb[k] : sqrtf((float)k / (float)(k + 1));
         const float q2 = a * t * q1 - b * q0;
-        out[(k + 1) * WS] = q2;
+        emit(k + 1, q2);
         q0 = q1;
         q1 = q2;
     }
 }
 
-// Per GP_TAB_BLOCK-row block b and table row R: tmaxb[b * rows + R] = max |T[R][i]|
-// over the block (chunk-major layout above), and tmax[R] = the maximum over
-// all blocks, as float bits (non-negative floats order like their bit
-// patterns). tmax must be zeroed.
-__global__ void __launch_bounds__(256) table_absmax_kernel(const float* __restrict__ tab, int64_t Npad,
-                                                           int rows, unsigned int* __restrict__ tmaxb,
-                                                           unsigned int* __restrict__ tmax) {
-    constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
-    const int row = blockIdx.y;
-    const int64_t i0 = (int64_t)blockIdx.x * GP_TAB_BLOCK;
-    const int64_t RC = (int64_t)(rows + 1) * WS;
-    float m = 0.f;
-    for (int64_t i = i0 + threadIdx.x; i < i0 + GP_TAB_BLOCK && i < Npad; i += blockDim.x)
-        m = fmaxf(m, fabsf(tab[(i / CW) * RC + (int64_t)row * WS + i % CW]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wm[8];
+// tmax[R] = max over blocks b of tmaxb[b][R] (one CTA per table row R).
+__global__ void __launch_bounds__(256) table_gmax_kernel(const unsigned int* __restrict__ tmaxb, int rows,
+                                                         int nblk, unsigned int* __restrict__ tmax) {
+    __shared__ unsigned int wm[8];
+    const int R = blockIdx.x;
+    unsigned int m = 0u;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) m = max(m, tmaxb[(int64_t)b * rows + R]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 0; w < 8; ++w) m = fmaxf(m, wm[w]);
-        tmaxb[(int64_t)blockIdx.x * rows + row] = __float_as_uint(m);
-        atomicMax(tmax + row, __float_as_uint(m));
+        for (int w = 0; w < 8; ++w) m = max(m, wm[w]);
+        tmax[R] = m;
     }
 }
 
@@ -173,13 +175,6 @@ size_t coef_bytes(const GpShape& s) {
 }
 
 }  // namespace
-
-void launch_table_absmax(const GpShape& s, const float* tabc, unsigned int* tmaxb, unsigned int* tmax,
-                         cudaStream_t stream) {
-    cudaMemsetAsync(tmax, 0, sizeof(unsigned int) * s.p * s.n, stream);
-    dim3 grid((unsigned)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK), (unsigned)(s.p * s.n));
-    table_absmax_kernel<<<grid, 256, 0, stream>>>(tabc, s.Npad, s.p * s.n, tmaxb, tmax);
-}
 
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
                            GpStatus* st, cudaStream_t stream) {
@@ -198,7 +193,11 @@ size_t syrktc_table_floats(const GpShape& s) {
 }
 
 void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
-                               GpStatus* st, cudaStream_t stream) {
+                               unsigned int* tmaxb, unsigned int* tmax, GpStatus* st, cudaStream_t stream) {
+    const int rows = s.p * s.n;
+    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
+    cudaMemsetAsync(tmaxb, 0, sizeof(unsigned int) * (size_t)rows * nblk, stream);
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, st);
+    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, tmaxb, st);
+    table_gmax_kernel<<<(unsigned)rows, 256, 0, stream>>>(tmaxb, rows, nblk, tmax);
 }
