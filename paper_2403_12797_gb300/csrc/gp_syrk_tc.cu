@@ -57,17 +57,23 @@
 namespace {
 
 constexpr int TM = SYRKTC_TM;              // 128
-constexpr int BK = SYRKTC_BK;              // 32 data rows per chunk
+constexpr int CW = SYRKTC_BK;              // 32 rows per table chunk
 constexpr int WS = SYRKTC_WS;              // floats per window row (36: bank-conflict padding)
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
-constexpr int BLOCK_CHUNKS = GP_TAB_BLOCK / BK;  // 32 chunks = 1024 rows per exact TMEM block
-constexpr int B_FOLD = 16;                 // chunks between float64 folds of b (512 rows)
 constexpr int FLUSH_BLOCKS = 4;            // blocks summed in the TMEM float32 sum between flushes
-constexpr int TILE_BYTES = TM * BK * 2;    // one 16-bit operand tile: 8 KB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A s1, A lo, B s1, B lo
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
-constexpr uint32_t SBO = (BK / 8) * 128;   // 8-row groups
+// A pipeline stage holds H table chunks (KS = 32 H rows; H = 2 unless the
+// windows of two chunks do not fit): per-stage costs -- waits, arrivals, the
+// MMA issue -- are paid once per KS rows.
+template <int H> struct StageGeom {
+    static constexpr int KS = CW * H;                     // rows per stage
+    static constexpr int TILE = TM * KS * 2;              // one 16-bit operand tile
+    static constexpr int BYTES = 4 * TILE;                // A s1, A lo, B s1, B lo
+    static constexpr uint32_t SBO = (KS / 8) * 128;       // 8-row groups
+    static constexpr int BLOCK = GP_TAB_BLOCK / KS;       // stages per exact 1024-row TMEM block
+    static constexpr int BFOLD = 512 / KS;                // stages between float64 folds of b
+};
 constexpr int NPROD = 512;                 // 16 producer warps: one 8-column core group each
 constexpr int NPW = NPROD / 32;
 constexpr int CPT = TM / (NPW / 4);        // tile columns per thread in the TMEM drain (32)
@@ -77,8 +83,8 @@ constexpr uint32_t TMEM_COLS = 512;        // acc1 | acc2 | float32 block sum | 
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct SmemTC {
-    uint8_t* stage;       // nst x STAGE_BYTES (1024-aligned)
-    float* win;           // nwr x (2 maxrows + 1) x WS: windows of tiles I, J and y
+    uint8_t* stage;       // nst x StageGeom<H>::BYTES (1024-aligned)
+    float* win;           // nwr x H x (2 maxrows + 1) x WS: windows of tiles I, J and y, per chunk
     int* egI;             // TM: global column exponents E_glob
     int* egJ;
     unsigned short* crI;  // TM x p: window row of (column, dimension)
@@ -96,7 +102,8 @@ struct SmemTC {
 __host__ __device__ inline int max_ranges(int p) { return 4 * p + 1; }
 __host__ __device__ inline int win_floats(int maxrows) { return (2 * maxrows + 1) * WS; }
 
-__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, int nwr, char* base, SmemTC* L) {
+__host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, int nwr, int H, char* base,
+                                                  SmemTC* L) {
     size_t off = 0;
     auto take = [&](size_t bytes, size_t align) {
         off = (off + align - 1) / align * align;
@@ -104,8 +111,8 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, in
         off += bytes;
         return o;
     };
-    size_t oS = take((size_t)nst * STAGE_BYTES, 1024);
-    size_t oW = take(sizeof(float) * nwr * win_floats(maxrows), 16);
+    size_t oS = take((size_t)nst * 4 * TM * (CW * H) * 2, 1024);
+    size_t oW = take(sizeof(float) * nwr * H * win_floats(maxrows), 16);
     size_t oEI = take(sizeof(int) * TM, 16);
     size_t oEJ = take(sizeof(int) * TM, 16);
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
@@ -244,6 +251,7 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 // mantissa bits of t, the integer k + 1152 has the float16 bit pattern
 // 0x6480 + k (exponent 2^10), and one exact half2 subtraction of 1152 leaves
 // k. Only the remainder takes a float16 conversion.
+template <uint32_t SBO>
 __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
                                              const float v[8], float sc) {
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
@@ -267,8 +275,9 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise.
-template <int P>
+// P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise;
+// H = table chunks per pipeline stage.
+template <int P, int H>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
                    const int* __restrict__ colexp, int64_t rps, int npairs, int maxrows, int nst, int nwr,
@@ -278,7 +287,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ int s_nrng;
     char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     SmemTC sm;
-    smem_tc_layout(maxrows, s.p, nst, nwr, base, &sm);
+    smem_tc_layout(maxrows, s.p, nst, nwr, H, base, &sm);
+    using GM = StageGeom<H>;
 
     const int q = blockIdx.x, split = blockIdx.y;
     int I, J;
@@ -290,10 +300,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t r0 = (int64_t)split * rps;
     int64_t r1 = r0 + rps;
     if (r1 > s.Npad) r1 = s.Npad;
-    const int nchunks = r0 < r1 ? (int)((r1 - r0) / BK) : 0;
-    const int nblocks = (nchunks + BLOCK_CHUNKS - 1) / BLOCK_CHUNKS;
+    // pipeline stages of KS rows (split boundaries are multiples of 1024
+    // rows and Npad of 128, so KS divides every split)
+    const int nchunks = r0 < r1 ? (int)((r1 - r0) / GM::KS) : 0;
+    const int nblocks = (nchunks + GM::BLOCK - 1) / GM::BLOCK;
     const int64_t RC = (int64_t)(s.p * s.n + 1) * WS;  // floats per table chunk
-    const int wsz = win_floats(maxrows);
+    const int wsz1 = win_floats(maxrows);                // one chunk's window
+    const int wsz = H * wsz1;                            // one window slot
 
     if (tid == 0) {
         tile_window(s, I * TM, TM, &wI);
@@ -446,43 +459,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = false;
                 break;
             }
-            if (c % B_FOLD == 0) {
+            if (c % GM::BFOLD == 0) {
                 bsum += (double)bacc;
                 bacc = 0.f;
             }
-            if (c % BLOCK_CHUNKS == 0) {
+            if (c % GM::BLOCK == 0) {
                 // a new 1024-row block: quantisation scales 2^(7 - E_blk)
                 scI = pow2i(7 - eI);
                 scJ = pow2i(7 - eJ);
-                const int nb = c / BLOCK_CHUNKS + 1;
+                const int nb = c / GM::BLOCK + 1;
                 if (nb < nblocks) {
                     eI = ebx[(int64_t)(blk0 + nb) * s.Mpad + mI];
                     eJ = ebx[(int64_t)(blk0 + nb) * s.Mpad + mJ];
                 }
             }
-            const float* win = sm.win + wsl * wsz;
-            uint8_t* sb = sm.stage + (size_t)stg * STAGE_BYTES;
-            {
-                float v[8];
-                phi8<P>(win, woffI, crrI, s.p, g, v);
-                store_slices(sb, sb + TILE_BYTES, r, g, v, scI);
-                if (J == 0) {
-                    const float4* y4 = reinterpret_cast<const float4*>(win + ywin + 8 * g);
-                    const float4 ya = y4[0], yb = y4[1];
-                    bacc = fmaf(v[0], ya.x, bacc);
-                    bacc = fmaf(v[1], ya.y, bacc);
-                    bacc = fmaf(v[2], ya.z, bacc);
-                    bacc = fmaf(v[3], ya.w, bacc);
-                    bacc = fmaf(v[4], yb.x, bacc);
-                    bacc = fmaf(v[5], yb.y, bacc);
-                    bacc = fmaf(v[6], yb.z, bacc);
-                    bacc = fmaf(v[7], yb.w, bacc);
+            uint8_t* sb = sm.stage + (size_t)stg * GM::BYTES;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float* win = sm.win + wsl * wsz + h * wsz1;  // chunk h of the stage
+                const int kg = 4 * h + g;                          // K group of these 8 rows
+                {
+                    float v[8];
+                    phi8<P>(win, woffI, crrI, s.p, g, v);
+                    store_slices<GM::SBO>(sb, sb + GM::TILE, r, kg, v, scI);
+                    if (J == 0) {
+                        const float4* y4 = reinterpret_cast<const float4*>(win + ywin + 8 * g);
+                        const float4 ya = y4[0], yb = y4[1];
+                        bacc = fmaf(v[0], ya.x, bacc);
+                        bacc = fmaf(v[1], ya.y, bacc);
+                        bacc = fmaf(v[2], ya.z, bacc);
+                        bacc = fmaf(v[3], ya.w, bacc);
+                        bacc = fmaf(v[4], yb.x, bacc);
+                        bacc = fmaf(v[5], yb.y, bacc);
+                        bacc = fmaf(v[6], yb.z, bacc);
+                        bacc = fmaf(v[7], yb.w, bacc);
+                    }
                 }
-            }
-            if (!diag) {
-                float v[8];
-                phi8<P>(win + jwin, woffJ, crrJ, s.p, g, v);
-                store_slices(sb + 2 * TILE_BYTES, sb + 3 * TILE_BYTES, r, g, v, scJ);
+                if (!diag) {
+                    float v[8];
+                    phi8<P>(win + jwin, woffJ, crrJ, s.p, g, v);
+                    store_slices<GM::SBO>(sb + 2 * GM::TILE, sb + 3 * GM::TILE, r, kg, v, scJ);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             // drain a finished block once one chunk of the next one is queued
             // (its MMAs are normally done by then; the next block's wait for it)
-            while (next_drain < nblocks && min((next_drain + 1) * BLOCK_CHUNKS, nchunks) <= c) {
+            while (next_drain < nblocks && min((next_drain + 1) * GM::BLOCK, nchunks) <= c) {
                 if (!drain(next_drain)) {
                     ok = false;
                     break;
@@ -527,7 +544,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sbase = smem_u32(sm.stage);
             int stg = 0, sph = 0;
             for (int c = 0; c < nchunks; ++c) {
-                const int d = c / BLOCK_CHUNKS, cb = c % BLOCK_CHUNKS;
+                const int d = c / GM::BLOCK, cb = c % GM::BLOCK;
                 // the accumulators of block d - 1 have been read back
                 if (cb == 0 && d >= 1 && !mbar_wait(sm.drained, (d - 1) & 1)) {
                     gp_set_status(st, GP_ETIMEOUT, 5);
@@ -540,17 +557,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t acc1 = tmem;
                 const uint32_t acc2 = tmem + 128;
-                const uint32_t a1 = sbase + stg * STAGE_BYTES;
-                const uint32_t a2 = a1 + TILE_BYTES;
-                const uint32_t b1 = diag ? a1 : a1 + 2 * TILE_BYTES;
-                const uint32_t b2 = diag ? a2 : a1 + 3 * TILE_BYTES;
+                const uint32_t a1 = sbase + stg * GM::BYTES;
+                const uint32_t a2 = a1 + GM::TILE;
+                const uint32_t b1 = diag ? a1 : a1 + 2 * GM::TILE;
+                const uint32_t b2 = diag ? a2 : a1 + 3 * GM::TILE;
 #pragma unroll
-                for (int ks = 0; ks < BK / 16; ++ks) {
+                for (int ks = 0; ks < GM::KS / 16; ++ks) {
                     const uint32_t ko = ks * 2 * LBO;
-                    const uint64_t dA1 = smem_desc(a1 + ko, LBO, SBO);
-                    const uint64_t dA2 = smem_desc(a2 + ko, LBO, SBO);
-                    const uint64_t dB1 = smem_desc(b1 + ko, LBO, SBO);
-                    const uint64_t dB2 = smem_desc(b2 + ko, LBO, SBO);
+                    const uint64_t dA1 = smem_desc(a1 + ko, LBO, GM::SBO);
+                    const uint64_t dA2 = smem_desc(a2 + ko, LBO, GM::SBO);
+                    const uint64_t dB1 = smem_desc(b1 + ko, LBO, GM::SBO);
+                    const uint64_t dB2 = smem_desc(b2 + ko, LBO, GM::SBO);
                     const uint32_t acc = (cb > 0 || ks > 0) ? 1u : 0u;
                     mma_bf16(acc1, dA1, dB1, idesc, acc);   // s1 s1'  (exact)
                     mma_bf16(acc2, dA1, dB2, idesc, acc);   // s1 lo'
@@ -558,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_bf16(acc2, dA2, dB2, idesc, 1u);    // lo lo'
                 }
                 mma_commit(&sm.empty[stg]);
-                if (cb == BLOCK_CHUNKS - 1 || c == nchunks - 1) mma_commit(sm.accf);
+                if (cb == GM::BLOCK - 1 || c == nchunks - 1) mma_commit(sm.accf);
                 if (++stg == nst) {
                     stg = 0;
                     sph ^= 1;
@@ -569,7 +586,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
         // ------------------------------------------------------------ window loader (bulk copies)
         const int nr = s_nrng;
-        const uint32_t wbytes = (uint32_t)nwin * WS * 4;
+        const uint32_t wbytes = (uint32_t)(H * nwin * WS * 4);
         // this lane's copy range (at most one per lane: 4p + 1 <= 32 ranges for p <= 7)
         int rdst = 0, rsrc = 0, rlen = 0;
         for (int k = lane; k < nr; k += 32) {
@@ -588,14 +605,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (lane == 0) mbar_arrive_expect_tx(&sm.tfull[wsl], wbytes);
             __syncwarp();
-            const float* src = tabc + ((r0 + (int64_t)c * BK) / BK) * RC;
-            float* dst = sm.win + wsl * wsz;
-            if (!multi) {
-                if (lane < nr) bulk_g2s(dst + rdst, src + rsrc, (uint32_t)rlen, &sm.tfull[wsl]);
-            } else {
-                for (int k = lane; k < nr; k += 32)
-                    bulk_g2s(dst + sm.rng[3 * k + 2] * WS, src + (int64_t)sm.rng[3 * k] * WS,
-                             (uint32_t)sm.rng[3 * k + 1] * WS * 4, &sm.tfull[wsl]);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float* src = tabc + ((r0 + (int64_t)c * GM::KS) / CW + h) * RC;
+                float* dst = sm.win + wsl * wsz + h * wsz1;
+                if (!multi) {
+                    if (lane < nr) bulk_g2s(dst + rdst, src + rsrc, (uint32_t)rlen, &sm.tfull[wsl]);
+                } else {
+                    for (int k = lane; k < nr; k += 32)
+                        bulk_g2s(dst + sm.rng[3 * k + 2] * WS, src + (int64_t)sm.rng[3 * k] * WS,
+                                 (uint32_t)sm.rng[3 * k + 1] * WS * 4, &sm.tfull[wsl]);
+                }
             }
             if (++wsl == nwr) {
                 wsl = 0;
@@ -615,19 +635,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// deepest pipeline (<= STAGES operand stages, then <= WRMAX window slots)
-// whose dynamic shared memory fits one CTA next to the kernel's static shared
-// memory (tile windows and flags, under 2 KB); 0 if none
-int syrk_tc_stages(const GpShape& s, int maxrows, int* nwr, size_t* smem) {
+// Pipeline shape: two table chunks per stage when two operand stages and two
+// window slots of two chunks fit, else one; then the deepest pipeline (<=
+// STAGES operand stages, then <= WRMAX window slots) whose dynamic shared
+// memory fits one CTA next to the kernel's static shared memory (tile
+// windows and flags, under 2 KB). Returns the operand stages (0 if nothing
+// fits).
+int syrk_tc_stages(const GpShape& s, int maxrows, int* H, int* nwr, size_t* smem) {
     constexpr size_t kDynamicBudget = (227 - 2) * 1024;
-    for (int nst = STAGES; nst >= 2; --nst)
-        for (int w = WRMAX; w >= 2; --w) {
-            *smem = smem_tc_layout(maxrows, s.p, nst, w, nullptr, nullptr);
-            if (*smem <= kDynamicBudget) {
-                *nwr = w;
-                return nst;
+    for (int h = 2; h >= 1; --h)
+        for (int nst = STAGES; nst >= 2; --nst)
+            for (int w = WRMAX; w >= 2; --w) {
+                *smem = smem_tc_layout(maxrows, s.p, nst, w, h, nullptr, nullptr);
+                if (*smem <= kDynamicBudget) {
+                    *H = h;
+                    *nwr = w;
+                    return nst;
+                }
             }
-        }
     return 0;
 }
 
@@ -635,8 +660,8 @@ int syrk_tc_stages(const GpShape& s, int maxrows, int* nwr, size_t* smem) {
 
 size_t syrktc_smem_bytes(const GpShape& s) {
     size_t smem = 0;
-    int nwr = 0;
-    syrk_tc_stages(s, gp_max_window_rows(s, TM), &nwr, &smem);
+    int nwr = 0, H = 0;
+    syrk_tc_stages(s, gp_max_window_rows(s, TM), &H, &nwr, &smem);
     return smem;
 }
 
@@ -648,11 +673,11 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
                            const unsigned int* tmax, int nsplit, int64_t rows_per_split,
                            float2* Gpart, double* bpart, int* colexp, signed char* ebx,
                            GpStatus* st, cudaStream_t stream) {
-    if (rows_per_split % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
+    if (rows_per_split % GP_TAB_BLOCK != 0 || s.Npad % (2 * CW) != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
     size_t smem = 0;
-    int nwr = 0;
-    const int nst = syrk_tc_stages(s, maxrows, &nwr, &smem);
+    int nwr = 0, H = 1;
+    const int nst = syrk_tc_stages(s, maxrows, &H, &nwr, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
     colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
@@ -667,11 +692,20 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
                                                nwr, Gpart, bpart, st);
         return cudaGetLastError();
     };
+    if (H == 2) {
+        switch (s.p) {
+            case 1: return go(syrk_tc_kernel<1, 2>);
+            case 2: return go(syrk_tc_kernel<2, 2>);
+            case 3: return go(syrk_tc_kernel<3, 2>);
+            case 4: return go(syrk_tc_kernel<4, 2>);
+            default: return go(syrk_tc_kernel<0, 2>);
+        }
+    }
     switch (s.p) {
-        case 1: return go(syrk_tc_kernel<1>);
-        case 2: return go(syrk_tc_kernel<2>);
-        case 3: return go(syrk_tc_kernel<3>);
-        case 4: return go(syrk_tc_kernel<4>);
-        default: return go(syrk_tc_kernel<0>);
+        case 1: return go(syrk_tc_kernel<1, 1>);
+        case 2: return go(syrk_tc_kernel<2, 1>);
+        case 3: return go(syrk_tc_kernel<3, 1>);
+        case 4: return go(syrk_tc_kernel<4, 1>);
+        default: return go(syrk_tc_kernel<0, 1>);
     }
 }
