@@ -6,8 +6,9 @@
 // Eq. 16, evaluated in log space and clamped at 1e200 so that eigenvalues
 // that underflow stay finite.
 //
-// The partial Gram tiles of the N splits are summed in float64 in split
-// order, so the result does not depend on scheduling.
+// The partial Gram tiles of the N splits are summed in split order (float64
+// for the float64 Gram, float pairs for the mixed one), so the result does
+// not depend on scheduling.
 #include "gp_kernels.cuh"
 
 #include <math.h>
@@ -15,9 +16,7 @@
 namespace {
 
 // a partial value as float64 (float pairs hold hi + lo)
-__device__ __forceinline__ double to_f64(float v) { return (double)v; }
 __device__ __forceinline__ double to_f64(double v) { return v; }
-__device__ __forceinline__ double to_f64(float2 v) { return (double)v.x + (double)v.y; }
 
 template <typename P, typename PB = P>
 __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpart,
@@ -54,6 +53,74 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     }
 }
 
+// The mixed-precision Gram's assembly, per 32 x 32 block (bi >= bj) of the
+// lower triangle of A: the float-pair partial tiles of the splits (column-
+// scaled by 2^(7 - E_m)) are read coalesced along their rows, summed in split
+// order as an unevaluated float pair (exact two-sum, ~46 bits), converted to
+// float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
+// block is written to A and, through shared memory, transposed into the
+// upper triangle (A is exactly symmetric). Diagonal blocks also sum b.
+__global__ void __launch_bounds__(256) assemble_scaled_kernel(const float2* __restrict__ Gpart,
+                                                              const double* __restrict__ bpart,
+                                                              const int* __restrict__ colexp, int nsplit,
+                                                              int Mpad, int M, const double* __restrict__ d,
+                                                              double* __restrict__ A, double* __restrict__ b) {
+    constexpr int TT = 128, B = 32;
+    __shared__ double t[B][B + 1];
+    int bi, bj;
+    tri_pair(blockIdx.x, &bi, &bj);
+    const int r0 = bi * B, c0 = bj * B;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int T = Mpad / TT;
+    const int64_t sstride = (int64_t)(T * (T + 1) / 2) * TT * TT;
+    auto add2 = [](float& hi, float& lo, float v) {  // hi + v = s + e exactly; lo collects e
+        const float sum = __fadd_rn(hi, v);
+        const float tt = __fsub_rn(sum, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, tt)), __fsub_rn(v, tt));
+        hi = sum;
+        lo = __fadd_rn(lo, e);
+    };
+#pragma unroll
+    for (int k = 0; k < B / 8; ++k) {
+        const int r = r0 + ty + 8 * k, c = c0 + tx;
+        double v = 0.0;
+        if (r < M && c < M && c <= r) {
+            const int I = r / TT, J = c / TT;
+            const int64_t off = (int64_t)(I * (I + 1) / 2 + J) * TT * TT + (int64_t)(r % TT) * TT + (c % TT);
+            float hi = 0.f, lo = 0.f;
+            for (int sp = 0; sp < nsplit; ++sp) {
+                const float2 g = Gpart[off + sp * sstride];
+                add2(hi, lo, g.x);
+                lo = __fadd_rn(lo, g.y);
+            }
+            const int e = colexp[r] + colexp[c] - 14;  // |e| well inside float64's exponent range
+            v = ((double)hi + (double)lo) * __hiloint2double((e + 1023) << 20, 0);
+            if (r == c && d != nullptr) v += d[r];
+            A[(int64_t)r * M + c] = v;
+        }
+        t[ty + 8 * k][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < B / 8; ++k) {
+        const int rr = ty + 8 * k;  // row of the transposed block (a column of the lower block)
+        if (bi != bj) {
+            const int row = c0 + rr, col = r0 + tx;
+            if (row < M && col < M) A[(int64_t)row * M + col] = t[tx][rr];
+        } else if (tx > rr && r0 + rr < M && c0 + tx < M) {
+            A[(int64_t)(r0 + rr) * M + c0 + tx] = t[tx][rr];
+        }
+    }
+    if (bi == bj && threadIdx.x < B) {
+        const int col = c0 + threadIdx.x;
+        if (col < M) {
+            double bb = 0.0;
+            for (int sp = 0; sp < nsplit; ++sp) bb += bpart[(int64_t)sp * Mpad + col];
+            b[col] = bb;
+        }
+    }
+}
+
 __global__ void noise_diag_kernel(GpShape s, const double* __restrict__ loglam, double log_sigma2,
                                   double* __restrict__ d) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,20 +141,13 @@ void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, i
                                                       Mpad, M, d, A, b);
 }
 
-void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart,
-                         const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
-                         double* A, double* b, cudaStream_t stream) {
-    dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<float, float><<<grid, 256, 0, stream>>>(Gpart, bpart, dpart, colexp, nsplit, tile, Mpad,
-                                                     M, d, A, b);
-}
-
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream) {
-    dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
-    assemble_kernel<float2, double><<<grid, 256, 0, stream>>>(Gpart, bpart, nullptr, colexp, nsplit, tile,
-                                                              Mpad, M, d, A, b);
+    (void)tile;  // the tensor-core Gram's tiles are 128 x 128
+    const int nb = (M + 31) / 32;
+    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, 0, stream>>>(Gpart, bpart, colexp, nsplit, Mpad,
+                                                                             M, d, A, b);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

@@ -489,10 +489,13 @@ __device__ __forceinline__ void tile_mm(const T* __restrict__ A, const T* __rest
 
 // Lt: L in the arithmetic type T (converted here when T is float; L itself
 // when T is double); Wt: W in T (W itself when T is double); X: M x M scratch.
+// At the end WT (Lt's buffer when T is float, X's when T is double) holds
+// W^T in T, for the solve's W^T t.
 template <typename T>
 __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict__ L, double* __restrict__ W,
                                                        int M, T* __restrict__ Lt, T* __restrict__ Wt,
-                                                       T* __restrict__ X, GpStatus* st, GridBar* gb) {
+                                                       T* __restrict__ X, T* __restrict__ WT, GpStatus* st,
+                                                       GridBar* gb) {
     __shared__ T sa[IB][IB + 1];
     __shared__ T sb[IB][IB + 1];
     __shared__ T rd[IB];
@@ -581,6 +584,25 @@ __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict_
         }
         if (!grid_sync(gb, st)) return;
     }
+    // ---- W^T (in T) by 32 x 32 blocks through shared memory
+    const int nb2 = nb * nb;
+    for (int t = blockIdx.x; t < nb2; t += G) {
+        const int bi = t / nb, bj = t % nb;
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT, i = e / IB, j = e % IB;
+            const int r = bi * IB + i, c = bj * IB + j;
+            sa[i][j] = (r < M && c < M) ? Wt[(int64_t)r * M + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < IB * IB / NT; ++q) {
+            const int e = tid + q * NT, i = e / IB, j = e % IB;
+            const int r = bj * IB + i, c = bi * IB + j;
+            if (r < M && c < M) WT[(int64_t)r * M + c] = sa[j][i];
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- c = A^{-1} b
@@ -589,21 +611,19 @@ __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict_
 // and c in float64; the products with W in T (float32 for the mixed fit,
 // whose W is float32-accurate, so float32 products lose nothing the
 // refinement would keep). One cooperative launch, a grid barrier between
-// phases:
-//   Wv   warp per row i:                 t_i = sum_{j <= i} W_ij v_j
-//   WTt  CTA per 32-column block, 8 row lanes: c_j (+)= sum_{i >= j} W_ij t_i
-//   res  warp per row i (float64):       r_i = b_i - sum_j A_ij c_j
-// W's upper triangle is stored as zero, so full row segments are read.
+// phases, every phase a warp per row:
+//   Wv   t_i = sum_{j <= i} W_ij v_j
+//   WTt  c_j (+)= sum_{i >= j} (W^T)_ji t_i     (W^T from the inverse)
+//   res  r_i = b_i - sum_j A_ij c_j              (float64)
 template <typename T>
 __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict__ A, const T* __restrict__ W,
-                                                        const double* __restrict__ b, double* __restrict__ c,
-                                                        T* __restrict__ t, T* __restrict__ r, int M, int refine,
-                                                        GpStatus* st, GridBar* gb) {
-    __shared__ T red[NT / 32][IB + 1];
+                                                        const T* __restrict__ WT, const double* __restrict__ b,
+                                                        double* __restrict__ c, T* __restrict__ t,
+                                                        T* __restrict__ r, int M, int refine, GpStatus* st,
+                                                        GridBar* gb) {
     if (status_code(st) != 0) return;  // set before this launch: every CTA leaves
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x;
-    const int nb = (M + IB - 1) / IB;
     auto w_apply = [&](const T* v) {
         for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
             const T* row = W + (int64_t)i * M;
@@ -614,20 +634,12 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
         }
     };
     auto wt_apply = [&](bool accumulate) {
-        for (int J = blockIdx.x; J < nb; J += G) {
-            const int j = J * IB + lane;
+        for (int j = blockIdx.x * (NT / 32) + warp; j < M; j += G * (NT / 32)) {
+            const T* row = WT + (int64_t)j * M;
             T s = T(0);
-            if (j < M)
-                for (int i = J * IB + warp; i < M; i += NT / 32) s = fma(W[(int64_t)i * M + j], t[i], s);
-            red[warp][lane] = s;
-            __syncthreads();
-            if (warp == 0 && j < M) {
-                T v = T(0);
-#pragma unroll
-                for (int w = 0; w < NT / 32; ++w) v += red[w][lane];
-                c[j] = (accumulate ? c[j] : 0.0) + (double)v;
-            }
-            __syncthreads();
+            for (int i = j + lane; i < M; i += 32) s = fma(row[i], t[i], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) c[j] = (accumulate ? c[j] : 0.0) + (double)s;
         }
     };
     for (int i = blockIdx.x * NT + tid; i < M; i += G * NT) r[i] = (T)b[i];
@@ -722,17 +734,19 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
         float* Lt = (float*)base;
         float* Wt = Lt + M2;
         float* X = Wt + M2;
+        float* WT = Lt;  // L in float is no longer needed once W is complete
         const void* k = (const void*)trinv_rec_kernel<float>;
         dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-        void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &st, &gb};
+        void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &WT, &st, &gb};
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
     double* Lt = nullptr;
     double* Wt = W;
     double* X = (double*)base;
+    double* WT = X;  // X is free after the last level
     const void* k = (const void*)trinv_rec_kernel<double>;
     dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-    void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &st, &gb};
+    void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &WT, &st, &gb};
     return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }
 
@@ -746,23 +760,25 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const void* fw
     cudaGetDevice(&dev);
     GridBar* gb = (GridBar*)work;
     cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
-    const int nb = (M + IB - 1) / IB;
-    const int want = std::max(nb, (M + NT / 32 - 1) / (NT / 32));
+    const int want = (M + NT / 32 - 1) / (NT / 32);
     gp_note_launches(1);
+    const char* fbase = (const char*)fwork + CHOL_RSD_OFFSET;
     if (fp32) {
-        // the float32 W left in the inverse's workspace
-        const float* Wf = (const float*)((const char*)fwork + CHOL_RSD_OFFSET) + (size_t)M * M;
+        // the float32 W and W^T left in the inverse's workspace
+        const float* WTf = (const float*)fbase;
+        const float* Wf = WTf + (size_t)M * M;
         float* t = (float*)(work + 32);
         float* r = t + M;
         const void* k = (const void*)solve_coop_kernel<float>;
         dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-        void* args[] = {(void*)&A, (void*)&Wf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
+        void* args[] = {(void*)&A, (void*)&Wf, (void*)&WTf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
+    const double* WTd = (const double*)fbase;
     double* t = work + 32;
     double* r = t + M;
     const void* k = (const void*)solve_coop_kernel<double>;
     dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-    void* args[] = {(void*)&A, (void*)&W, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
+    void* args[] = {(void*)&A, (void*)&W, (void*)&WTd, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
     return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }

@@ -51,12 +51,6 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
 // b = sum_s bpart[s]. d may be NULL (plain Gram).
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream);
-// dpart (nullable): per-split diagonal corrections added to the scaled
-// diagonal; colexp (nullable): per-column exponents, A[m][m'] is the split
-// sum times 2^(E_m + E_m' - 14).
-void launch_assemble_f32(const float* Gpart, const float* bpart, const float* dpart,
-                         const int* colexp, int nsplit, int tile, int Mpad, int M, const double* d,
-                         double* A, double* b, cudaStream_t stream);
 // float-pair partials of the tensor-core Gram: A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
