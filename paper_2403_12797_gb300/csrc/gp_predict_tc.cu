@@ -9,18 +9,20 @@
 // table window (the rows phi_d(x*_{.j}) its columns touch, for the CTA's
 // test points), the chunk's column -> window-row map, the packed hi/lo
 // blocks of W, and the generated hi/lo tile of Phi_*:
-//   warp 5     (all lanes) copies the window rows, the map and the W blocks
+//   warp 9     (all lanes) copies the window rows, the map and the W blocks
 //              with 1-D bulk (TMA) copies that complete on one mbarrier;
-//   warps 0-3  producers: form the Phi_* chunk in float32 (one test point
-//              per thread, p a compile-time constant for p <= 4), add its
+//   warps 0-7  producers, two threads per test point (warps 0-3 and 4-7
+//              each take half of the chunk's columns): form the Phi_* chunk
+//              in float32 (p a compile-time constant for p <= 4), add its
 //              contribution to the mean (float32 products with a float32
 //              copy of c, float64 running sum), split it into bf16 hi/lo in
 //              the K-major core-matrix layout and publish it;
-//   warp 4     issues hi*hi + hi*lo + lo*hi MMAs (M=128, N=128, K=16) into
+//   warp 8     issues hi*hi + hi*lo + lo*hi MMAs (M=128, N=128, K=16) into
 //              each block's TMEM accumulator, skipping blocks where W is zero
 //              (W is lower triangular).
-// After a super-tile, warps 0-3 read their rows of Z from TMEM and add the
-// squares into the variance. Every wait is bounded; a warp decides with a
+// After a super-tile, the producers read their rows of Z from TMEM (each
+// half every other 32 columns) and add the squares into the variance; the
+// two halves' sums meet in shared memory at the end. Every wait is bounded; a warp decides with a
 // vote, so tcgen05 loads stay warp-uniform and no CTA-wide barrier is left
 // waiting for a warp that gave up.
 #include "gp_kernels.cuh"
@@ -38,8 +40,10 @@ constexpr int WB_BYTES = KB * BK * 2;        // 8 KB per hi or lo block of W
 constexpr int WIN_OFF = 2 * A_BYTES + SUPER * 2 * WB_BYTES;  // 80 KB: window after A and W
 constexpr uint32_t LBO = 128;
 constexpr uint32_t SBO = (BK / 8) * 128;     // 512
-constexpr int NPROD = 128;
-constexpr int NTHREADS = NPROD + 64;
+constexpr int NPROD = 2 * TT;                // two producer threads per test point (8 warps)
+constexpr int NPW = NPROD / 32;
+constexpr int MMA_W = NPW;                   // warp 8: MMA issuer
+constexpr int NTHREADS = NPROD + 64;         // + warp 9: loader
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 // Stage: [A hi | A lo | W blocks (hi, lo) x SUPER | window (maxrows + 1 rows
@@ -134,19 +138,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_fence_init();
     }
     // the zero window row of every stage (columns beyond M map to it)
-    if (tid < NPROD)
+    if (tid < TT)
         for (int i = 0; i < STAGES; ++i)
             reinterpret_cast<float*>(stage + (size_t)i * SB + WIN_OFF)[maxrows * TT + tid] = 0.f;
-    if (warp == 4) tmem_alloc(tmem_base, 512);
+    if (warp == MMA_W) tmem_alloc(tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
+    // the two producer threads of a test point combine their sums here
+    __shared__ double comb_m[TT], comb_v[TT];
+    __shared__ int comb_ok[TT];
+    const int t = tid & (TT - 1);     // test point (and TMEM lane) of a producer thread
+    const int hf = tid / TT;          // its half of every 32-column chunk
+    double macc = 0.0, vacc = 0.0;
+    bool pok = false;
 
-    if (warp < 4) {
+    if (warp < NPW) {
         // ------------------------------------------------------------ producers + epilogue
-        const int t = tid;
-        double macc = 0.0, vacc = 0.0;
         bool ok = true;
         int gc = 0;
         for (int sup = 0; sup < nsuper && ok; ++sup) {
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int* map = reinterpret_cast<const int*>(sb + MAPO);
                 float mpart = 0.f;
 #pragma unroll
-                for (int g = 0; g < BK / 8; ++g) {
+                for (int g = 2 * hf; g < 2 * hf + 2; ++g) {
                     float v[8];
                     gen8<P>(win, map + g * 8 * p, p, t, v);
                     if (last) {
@@ -207,9 +216,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             for (int bb = 0; bb < nblk; ++bb) {
 #pragma unroll 1
-                for (int ch = 0; ch < KB / 32; ++ch) {
+                for (int ch = hf; ch < KB / 32; ch += 2) {  // this half's 32-column pieces
                     float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + bb * KB + ch * 32, v);
+                    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + bb * KB + ch * 32, v);
                     float q = 0.f;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) q = fmaf(v[i], v[i], q);
@@ -219,11 +228,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_before();
             mbar_arrive(tfree);
         }
-        if (ok && t0 + t < s.N) {
-            mean[t0 + t] = macc;
-            if (var) var[t0 + t] = sigma2 * vacc;
+        pok = ok;
+        if (hf == 1) {
+            comb_m[t] = macc;
+            comb_v[t] = vacc;
+            comb_ok[t] = ok ? 1 : 0;
         }
-    } else if (warp == 4) {
+    } else if (warp == MMA_W) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(TT, KB);
@@ -317,9 +328,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == MMA_W) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
+    }
+    if (tid < TT && pok && comb_ok[t] && t0 + t < s.N) {
+        mean[t0 + t] = macc + comb_m[t];
+        if (var) var[t0 + t] = sigma2 * (vacc + comb_v[t]);
     }
 }
 
@@ -416,7 +431,7 @@ cudaError_t predict_tc_launch(const GpShape& s, const float* tab, const uint16_t
                               double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream) {
     const int maxrows = predtc_maxrows(s);
     const size_t smem = predtc_smem_bytes(s);
-    if (smem > (227 - 2) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
+    if (smem > (227 - 4) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
     cudaError_t e = gp_allow_max_smem((const void*)predict_tc_kernel<P>);
     if (e != cudaSuccess) return e;
     const size_t Mpad = (size_t)gp_round_up(s.M, KB);
