@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
 // float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
 // block is written to A and, through shared memory, transposed into the
 // upper triangle (A is exactly symmetric). Diagonal blocks also sum b.
-__global__ void __launch_bounds__(256) assemble_scaled_kernel(const float2* __restrict__ Gpart,
+__global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __restrict__ Gpart,
                                                               const double* __restrict__ bpart,
                                                               const int* __restrict__ colexp, int nsplit,
                                                               int Mpad, int M, const double* __restrict__ d,
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) assemble_scaled_kernel(const float2* __re
     int bi, bj;
     tri_pair(blockIdx.x, &bi, &bj);
     const int r0 = bi * B, c0 = bj * B;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // one element per thread
     const int T = Mpad / TT;
     const int64_t sstride = (int64_t)(T * (T + 1) / 2) * TT * TT;
     auto add2 = [](float& hi, float& lo, float v) {  // hi + v = s + e exactly; lo collects e
@@ -80,9 +80,8 @@ __global__ void __launch_bounds__(256) assemble_scaled_kernel(const float2* __re
         hi = sum;
         lo = __fadd_rn(lo, e);
     };
-#pragma unroll
-    for (int k = 0; k < B / 8; ++k) {
-        const int r = r0 + ty + 8 * k, c = c0 + tx;
+    {
+        const int r = r0 + ty, c = c0 + tx;
         double v = 0.0;
         if (r < M && c < M && c <= r) {
             const int I = r / TT, J = c / TT;
@@ -98,12 +97,11 @@ __global__ void __launch_bounds__(256) assemble_scaled_kernel(const float2* __re
             if (r == c && d != nullptr) v += d[r];
             A[(int64_t)r * M + c] = v;
         }
-        t[ty + 8 * k][tx] = v;
+        t[ty][tx] = v;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < B / 8; ++k) {
-        const int rr = ty + 8 * k;  // row of the transposed block (a column of the lower block)
+    {
+        const int rr = ty;  // row of the transposed block (a column of the lower block)
         if (bi != bj) {
             const int row = c0 + rr, col = r0 + tx;
             if (row < M && col < M) A[(int64_t)row * M + col] = t[tx][rr];
@@ -146,8 +144,8 @@ void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int*
                             cudaStream_t stream) {
     (void)tile;  // the tensor-core Gram's tiles are 128 x 128
     const int nb = (M + 31) / 32;
-    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, 0, stream>>>(Gpart, bpart, colexp, nsplit, Mpad,
-                                                                             M, d, A, b);
+    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(Gpart, bpart, colexp, nsplit, Mpad,
+                                                                              M, d, A, b);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
