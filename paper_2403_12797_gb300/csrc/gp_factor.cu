@@ -450,38 +450,46 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
 // tiles run side by side, instead of a walk down the block rows.
 
 // 32 x 32 tile of C (+)= sum_{k in [k0, k1)} A[r0 + i][k] B[k][c0 + j] (rows
-// and columns beyond M read as zero), each thread four outputs of row ty;
-// the next chunk's global loads are in flight while one is multiplied.
+// and columns beyond M read as zero), each thread four outputs of row ty.
+// The global loads of up to KBATCH 32-wide K chunks are all issued before the
+// first of them is multiplied, so a tile pays the L2 latency once per batch
+// instead of once per chunk.
+constexpr int KBATCH = 8;
 template <typename T>
 __device__ __forceinline__ void tile_mm(const T* __restrict__ A, const T* __restrict__ B, int M, int r0,
                                         int c0, int k0, int k1, T (&acc)[4], T (*sa)[IB + 1],
                                         T (*sb)[IB + 1]) {
     const int tid = threadIdx.x, ty = tid >> 3, tx = (tid & 7) * 4;
-    T va[IB * IB / NT], vb[IB * IB / NT];
-    auto load = [&](int kc) {
+    for (int kb = k0; kb < k1; kb += IB * KBATCH) {
+        T va[KBATCH][IB * IB / NT], vb[KBATCH][IB * IB / NT];
 #pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT, i = e / IB, j = e % IB;
-            va[q] = (r0 + i < M && kc + j < M) ? A[(int64_t)(r0 + i) * M + kc + j] : T(0);
-            vb[q] = (kc + i < M && c0 + j < M) ? B[(int64_t)(kc + i) * M + c0 + j] : T(0);
-        }
-    };
-    if (k0 < k1) load(k0);
-    for (int kc = k0; kc < k1; kc += IB) {
-        __syncthreads();
+        for (int u = 0; u < KBATCH; ++u) {
+            const int kc = kb + u * IB;
 #pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT;
-            sa[e / IB][e % IB] = va[q];
-            sb[e / IB][e % IB] = vb[q];
+            for (int q = 0; q < IB * IB / NT; ++q) {
+                const int e = tid + q * NT, i = e / IB, j = e % IB;
+                const bool in = kc < k1;
+                va[u][q] = (in && r0 + i < M && kc + j < M) ? A[(int64_t)(r0 + i) * M + kc + j] : T(0);
+                vb[u][q] = (in && kc + i < M && c0 + j < M) ? B[(int64_t)(kc + i) * M + c0 + j] : T(0);
+            }
         }
-        __syncthreads();
-        if (kc + IB < k1) load(kc + IB);
+#pragma unroll
+        for (int u = 0; u < KBATCH; ++u) {
+            if (kb + u * IB >= k1) break;  // uniform across the CTA
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < IB * IB / NT; ++q) {
+                const int e = tid + q * NT;
+                sa[e / IB][e % IB] = va[u][q];
+                sb[e / IB][e % IB] = vb[u][q];
+            }
+            __syncthreads();
 #pragma unroll 8
-        for (int l = 0; l < IB; ++l) {
-            const T av = sa[ty][l];
+            for (int l = 0; l < IB; ++l) {
+                const T av = sa[ty][l];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] = fma(av, sb[l][tx + c], acc[c]);
+                for (int c = 0; c < 4; ++c) acc[c] = fma(av, sb[l][tx + c], acc[c]);
+            }
         }
     }
     __syncthreads();
@@ -523,16 +531,23 @@ __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict_
             sb[i][j] = T(0);
         }
         __syncthreads();
-        if (tid < wI) rd[tid] = T(1) / sa[tid][tid];
+        if (tid < IB) rd[tid] = tid < wI ? T(1) / sa[tid][tid] : T(0);
         __syncthreads();
-        if (tid < wI) {  // column j of L_II^{-1} by forward substitution
+        if (tid < IB) {
+            // column j of L_II^{-1} by forward substitution, held in registers
+            // (x[k] = 0 above the diagonal, so every row sums over all k < i;
+            // rows and columns beyond wI come out zero through rd = 0)
             const int j = tid;
-            sb[j][j] = rd[j];
-            for (int i = j + 1; i < wI; ++i) {
-                T s = T(0);
-                for (int k = j; k < i; ++k) s = fma(sa[i][k], sb[k][j], s);
-                sb[i][j] = -s * rd[i];
+            T x[IB];
+#pragma unroll
+            for (int i = 0; i < IB; ++i) {
+                T sum = T(0);
+#pragma unroll
+                for (int k = 0; k < i; ++k) sum = fma(sa[i][k], x[k], sum);
+                x[i] = i < j ? T(0) : (i == j ? rd[i] : -sum * rd[i]);
             }
+#pragma unroll
+            for (int i = 0; i < IB; ++i) sb[i][j] = x[i];
         }
         __syncthreads();
 #pragma unroll
@@ -624,21 +639,32 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
     if (status_code(st) != 0) return;  // set before this launch: every CTA leaves
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x;
+    // row . vector over [lo, hi) by one warp, eight loads per lane in flight
+    auto dotrow = [&](const T* row, const T* v, int lo, int hi) -> T {
+        T s = T(0);
+        for (int j0 = lo; j0 < hi; j0 += 32 * 8) {
+            T a[8], x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u + lane;
+                a[u] = j < hi ? row[j] : T(0);
+                x[u] = j < hi ? v[j] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s = fma(a[u], x[u], s);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        return s;
+    };
     auto w_apply = [&](const T* v) {
         for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
-            const T* row = W + (int64_t)i * M;
-            T s = T(0);
-            for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const T s = dotrow(W + (int64_t)i * M, v, 0, i + 1);
             if (lane == 0) t[i] = s;
         }
     };
     auto wt_apply = [&](bool accumulate) {
         for (int j = blockIdx.x * (NT / 32) + warp; j < M; j += G * (NT / 32)) {
-            const T* row = WT + (int64_t)j * M;
-            T s = T(0);
-            for (int i = j + lane; i < M; i += 32) s = fma(row[i], t[i], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const T s = dotrow(WT + (int64_t)j * M, t, j, M);
             if (lane == 0) c[j] = (accumulate ? c[j] : 0.0) + (double)s;
         }
     };
@@ -652,7 +678,17 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
         for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
             const double* row = A + (int64_t)i * M;
             double s = 0.0;
-            for (int j = lane; j < M; j += 32) s = fma(row[j], c[j], s);
+            for (int j0 = 0; j0 < M; j0 += 32 * 8) {
+                double a[8], x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + 32 * u + lane;
+                    a[u] = j < M ? row[j] : 0.0;
+                    x[u] = j < M ? c[j] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = fma(a[u], x[u], s);
+            }
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) r[i] = (T)(b[i] - s);
         }
