@@ -282,7 +282,9 @@ int fit_alloc(gp_model* h, cudaStream_t stream) {
     const size_t M = (size_t)h->shape.M;
     const bool tc = h->prec != GP_PREC_FP64;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t sizes[7] = {sizeof(double) * M * M, sizeof(double) * M * M, sizeof(double) * M,
+    // W = L^{-1} in float64 only for the float64 fit (the mixed one keeps
+    // its float32 W packed for the predict kernel)
+    const size_t sizes[7] = {sizeof(double) * M * M, tc ? 0 : sizeof(double) * M * M, sizeof(double) * M,
                              sizeof(double) * M,     sizeof(double) * M,
                              tc ? predtc_wpack_bytes((int)M) : 0,
                              tc ? sizeof(int) * predtc_cinfo_ints(h->shape) : 0};
@@ -425,7 +427,7 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
     }
     if (e == cudaSuccess && prec != GP_PREC_FP64) {
         GpProf pf("pack_w", stream);
-        launch_pack_w_bf16x3(h->W, h->c, M, h->Wpack, stream);
+        launch_pack_w_bf16x3(tri_inverse_fp32_w(fwork, M), h->c, M, h->Wpack, stream);
         gp_note_launches(1);
         e = cudaGetLastError();
     }

@@ -18,7 +18,7 @@
 //   A non-positive or NaN pivot sets GP_ENOTPD (detail = column); every CTA
 //   sees it after the next barrier and returns.
 //
-//   W = L^{-1} by recursive doubling over 32-row blocks (below), in float32
+//   W = L^{-1} by recursive doubling over diagonal blocks (below), in float32
 //   or float64 arithmetic. The mixed-precision fit uses float32 here: W
 //   feeds the bf16 hi/lo variance contraction, and as the preconditioner of
 //   c = A^{-1} b its error is removed by the float64 iterative refinement.
@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -257,7 +258,7 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
 }
 
 // L[r0.., c0..] -= L[r0.., kb..kb+w) L[c0.., kb..kb+w)^T on one 16 x 16 lower tile.
-__device__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
+__device__ __forceinline__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
                                  double (*ti)[CB + 1], double (*tj)[CB + 1]) {
     const int tid = threadIdx.x;
     double vi[UT * CB / NT], vj[UT * CB / NT];
@@ -285,7 +286,7 @@ __device__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, i
 // Share `part` of `nparts` of the next diagonal block's update
 // L[r0 + I][r0 + J] -= sum_l L[r0 + I][kb + l] L[r0 + J][kb + l] (J <= I < wn,
 // r0 = kb + w): four threads per entry, each summing every fourth l.
-__device__ void chol_next_diag(double* __restrict__ L, int M, int kb, int w, int wn, int part,
+__device__ __forceinline__ void chol_next_diag(double* __restrict__ L, int M, int kb, int w, int wn, int part,
                                int nparts, double (*P)[CB + 1]) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int r0 = kb + w;
@@ -438,132 +439,429 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
 
 // ---------------------------------------------------------------- W = L^{-1}
 
-// W = L^{-1} by recursive doubling over 32-row blocks, in float32 (mixed
-// precision) or float64 arithmetic. With L = [L11 0; L21 L22] the inverse is
-// [W11 0; W21 W22], W21 = -W22 (L21 W11): the diagonal blocks' inverses D_I
-// come first (level 0), and each level h = 32, 64, 128, ... joins every
-// aligned pair of h-row blocks with two tiled GEMM phases over all CTAs,
+// W = L^{-1} by recursive doubling, in float32 (mixed precision) or float64
+// arithmetic. With L = [L11 0; L21 L22] the inverse is [W11 0; W21 W22],
+// W21 = -W22 (L21 W11). Level 0 inverts the LB-row diagonal blocks of L, one
+// per CTA and entirely in shared memory (its own doubling over 32-row
+// blocks, separated by CTA barriers only); each level h = LB, 2 LB, ... then
+// joins every aligned pair of h-row blocks with two tiled GEMM phases over
+// all CTAs,
 //   A:  X[S][F]  = L[S][F] W[F][F]     (W[F][F] lower triangular)
 //   B:  W[S][F]  = -W[S][S] X[S][F]    (W[S][S] lower triangular),
 // F = the first h rows of the pair, S the rest. A grid barrier separates the
-// phases, so an M x M inverse takes 2 ceil(log2(M / 32)) + 1 phases whose
-// tiles run side by side, instead of a walk down the block rows.
+// phases, so an M x M inverse takes 2 ceil(log2(M / LB)) + 1 phases whose
+// tiles run side by side. Every phase also stores the transposes of the
+// blocks it completes, so W^T is ready when the last phase ends.
+// float64 -> float32, rounded to nearest even, in integer arithmetic: on
+// GB300 the conversion instruction runs on the float64 pipe (64 cycles per
+// warp instruction per scheduler), integer operations do not. A normal
+// result takes the top 23 mantissa bits plus the rounding of the 29 below
+// (a carry moves into the exponent, and to infinity at the top); tiny
+// results become subnormal or zero, large ones infinity, NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu, sgn = hi & 0x80000000u;
+    if (e - 897u < 254u || e == 0u) {  // float exponent 1 .. 254 before rounding, or zero
+        const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rem = lo & 0x1FFFFFFFu;
+        const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+        return __uint_as_float(e == 0u ? sgn : sgn | ((((e - 896u) << 23) | m) + up));
+    }
+    if (e == 0x7FFu) return __uint_as_float(sgn | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x00400000u : 0u));
+    if (e > 1150u) return __uint_as_float(sgn | 0x7F800000u);
+    // |x| < 2^-126: q = round(x 2^149) = round(sig 2^(e - 926)), sig with its hidden bit
+    const int sh = 926 - (int)e;
+    if (e == 0u || sh > 63) return __uint_as_float(sgn);
+    const uint64_t sig = (1ull << 52) | ((uint64_t)(hi & 0xFFFFFu) << 32) | lo;
+    uint64_t q = sig >> sh;
+    const uint64_t rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    return __uint_as_float(sgn | (uint32_t)q);
+}
+__device__ __forceinline__ float to_t(double x, float*) { return d2f_rn(x); }
+__device__ __forceinline__ double to_t(double x, double*) { return x; }
 
-// 32 x 32 tile of C (+)= sum_{k in [k0, k1)} A[r0 + i][k] B[k][c0 + j] (rows
-// and columns beyond M read as zero), each thread four outputs of row ty.
-// The global loads of up to KBATCH 32-wide K chunks are all issued before the
-// first of them is multiplied, so a tile pays the L2 latency once per batch
-// instead of once per chunk.
-constexpr int KBATCH = 8;
 template <typename T>
-__device__ __forceinline__ void tile_mm(const T* __restrict__ A, const T* __restrict__ B, int M, int r0,
-                                        int c0, int k0, int k1, T (&acc)[4], T (*sa)[IB + 1],
-                                        T (*sb)[IB + 1]) {
-    const int tid = threadIdx.x, ty = tid >> 3, tx = (tid & 7) * 4;
-    for (int kb = k0; kb < k1; kb += IB * KBATCH) {
-        T va[KBATCH][IB * IB / NT], vb[KBATCH][IB * IB / NT];
+struct InvGeom;
+// A level-0 CTA moves its whole block through one SM, whose own share of
+// the L2 bandwidth is small (tens of bytes per clock), so the blocks are kept
+// at 64 rows: more CTAs, each with less to move, and one more grid-wide level.
+template <>
+struct InvGeom<float> {
+    static constexpr int LB = 64;   // rows of a level-0 block
+    static constexpr int LD = 68;   // row stride of its shared-memory copies
+    static constexpr int XD = 36;   // row stride of its X scratch
+};
+template <>
+struct InvGeom<double> {
+    static constexpr int LB = 64;
+    static constexpr int LD = 66;
+    static constexpr int XD = 34;
+};
+// level 0's buffers, or the 8192-element staging of tile_mm4 if larger
+template <typename T>
+constexpr size_t trinv_smem_bytes() {
+    using G = InvGeom<T>;
+    const size_t l0 = 2 * (size_t)G::LB * G::LD + (size_t)(G::LB / 2) * G::XD + G::LB;
+    return sizeof(T) * (l0 > 8192 ? l0 : 8192);
+}
+
+// four consecutive elements, 16-byte aligned, in shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Warp-task k of round m for warp w when 8 warps deal the tasks, sorted by
+// decreasing cost, in alternating directions (0..7, 7..0, ...), so that
+// every warp's total is about the same.
+__device__ __forceinline__ int snake_task(int w, int m) { return 8 * m + ((m & 1) ? 7 - w : w); }
+
+// One level h = H of the doubling inside a level-0 block (shared memory):
+//   A  X[S][F] = L[S][F] W[F][F]: a warp-task is 32 rows of sX (lane = row)
+//      and one column quad j4, so its trip count k = j4 .. H - 1 (W[F][F] is
+//      zero above the diagonal) is the same on every lane;
+//   B  W[S][F] = -W[S][S] X[S][F]: a warp-task is 32 / (H / 4) adjacent rows
+//      (lanes across the rows' column quads), k = 0 .. the last row's index
+//      (W[S][S] is zero above the diagonal).
+// Both take k in steps of four with 16-byte loads.
+template <typename T, int H>
+__device__ __forceinline__ void trinv_level0_pairs(const T* sL, T* sW, T* sX) {
+    constexpr int LB = InvGeom<T>::LB, LD = InvGeom<T>::LD, XD = InvGeom<T>::XD;
+    constexpr int Q = H / 4;                  // column quads of a pair
+    constexpr int NP = LB / (2 * H);          // pairs
+    constexpr int NRG = LB / 64;              // 32-row groups of sX
+    constexpr int NA = NRG * Q;               // A warp-tasks
+    constexpr int R = 32 / Q;                 // rows of a B warp-task
+    constexpr int NRB = H / R;                // B warp-tasks per pair
+    constexpr int NB = NP * NRB;
+    static_assert(NA % 8 == 0 || NA < 8, "A tasks");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int m = 0; m * 8 < NA; ++m) {
+        const int k = snake_task(warp, m);
+        if (k >= NA) continue;
+        const int jq = k / NRG, rg = k % NRG;  // cost H - 4 jq, decreasing in k
+        const int gi = rg * 32 + lane, g = gi / H, i = gi % H, j4 = jq * 4;
+        const int F0 = 2 * g * H, S0 = F0 + H;
+        const T* lrow = sL + (S0 + i) * LD + F0;
+        const T* wcol = sW + F0 * LD + F0 + j4;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int k0 = j4; k0 < H; k0 += 4) {
+            T l4[4];
+            ld4(lrow + k0, l4);
 #pragma unroll
-        for (int u = 0; u < KBATCH; ++u) {
-            const int kc = kb + u * IB;
+            for (int kk = 0; kk < 4; ++kk) {
+                T w4[4];
+                ld4(wcol + (k0 + kk) * LD, w4);
 #pragma unroll
-            for (int q = 0; q < IB * IB / NT; ++q) {
-                const int e = tid + q * NT, i = e / IB, j = e % IB;
-                const bool in = kc < k1;
-                va[u][q] = (in && r0 + i < M && kc + j < M) ? A[(int64_t)(r0 + i) * M + kc + j] : T(0);
-                vb[u][q] = (in && kc + i < M && c0 + j < M) ? B[(int64_t)(kc + i) * M + c0 + j] : T(0);
+                for (int c = 0; c < 4; ++c) acc[c] = fma(l4[kk], w4[c], acc[c]);
+            }
+        }
+        st4(sX + gi * XD + j4, acc);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int m = 0; m * 8 < NB; ++m) {
+        const int k = snake_task(warp, m);
+        if (k >= NB) continue;
+        const int g = k % NP, rb = NRB - 1 - k / NP;  // cost ~ rb, decreasing in k
+        const int i = rb * R + lane / Q, j4 = (lane % Q) * 4, imax = rb * R + R - 1;
+        const int F0 = 2 * g * H, S0 = F0 + H;
+        const T* wrow = sW + (S0 + i) * LD + S0;
+        const T* xcol = sX + g * H * XD + j4;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int k0 = 0; k0 <= imax; k0 += 4) {
+            T w4[4];
+            ld4(wrow + k0, w4);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                T x4[4];
+                ld4(xcol + (k0 + kk) * XD, x4);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] = fma(w4[kk], x4[c], acc[c]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < KBATCH; ++u) {
-            if (kb + u * IB >= k1) break;  // uniform across the CTA
-            __syncthreads();
+        for (int c = 0; c < 4; ++c) acc[c] = -acc[c];
+        st4(sW + (S0 + i) * LD + F0 + j4, acc);
+    }
+    __syncthreads();
+}
+
+// Level 0 for the diagonal block of rows R0 .. R0 + wB - 1 (wB <= LB): its
+// inverse in sW (LB x LB, stride LD, zero above the diagonal and beyond wB)
+// from the block of L, read into sL in T. Diagonal 32-row blocks by forward
+// substitution (one warp per block, lane j forms column j in registers),
+// then the pairs of h-row blocks, h = 32, 64, .. LB / 2.
+template <typename T>
+__device__ __forceinline__ void trinv_level0(const double* __restrict__ L, int M, int R0, int wB, T* sL, T* sW, T* sX,
+                             T* srd) {
+    constexpr int LB = InvGeom<T>::LB, LD = InvGeom<T>::LD;
+    constexpr int RPW = LB / 8, SLOTS = LB / 64, RB = 8;  // rows per warp, double2 per lane and row
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the lower triangle of the block of L in T, rows warp + 8 t, 16-byte
+    // loads, RB rows' loads in flight; sW = 0
+#pragma unroll 1
+    for (int t0 = 0; t0 < RPW; t0 += RB) {
+        double2 v[RB][SLOTS];
 #pragma unroll
-            for (int q = 0; q < IB * IB / NT; ++q) {
-                const int e = tid + q * NT;
-                sa[e / IB][e % IB] = va[u][q];
-                sb[e / IB][e % IB] = vb[u][q];
+        for (int t = 0; t < RB; ++t) {
+            const int i = warp + 8 * (t0 + t);
+#pragma unroll
+            for (int sl = 0; sl < SLOTS; ++sl) {
+                const int j = 64 * sl + 2 * lane;
+                const double* src = L + (int64_t)(R0 + i) * M + R0 + j;
+                // rows of L are 16-byte aligned only when M and R0 are even:
+                // take the pair as two loads otherwise
+                if (i < wB && j <= i) {
+                    if (((M | R0) & 1) == 0) {
+                        v[t][sl] = *reinterpret_cast<const double2*>(src);
+                        if (j + 1 > i) v[t][sl].y = 0.0;
+                    } else {
+                        v[t][sl].x = src[0];
+                        v[t][sl].y = j + 1 <= i ? src[1] : 0.0;
+                    }
+                } else {
+                    v[t][sl] = make_double2(0.0, 0.0);
+                }
             }
-            __syncthreads();
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int i = warp + 8 * (t0 + t);
+#pragma unroll
+            for (int sl = 0; sl < SLOTS; ++sl) {
+                const int j = 64 * sl + 2 * lane;
+                sL[i * LD + j] = to_t(v[t][sl].x, (T*)nullptr);
+                sL[i * LD + j + 1] = to_t(v[t][sl].y, (T*)nullptr);
+                sW[i * LD + j] = T(0);
+                sW[i * LD + j + 1] = T(0);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < LB) srd[tid] = tid < wB ? T(1) / sL[tid * LD + tid] : T(0);
+    __syncthreads();
+    if (warp < LB / IB) {
+        // x[k] = 0 above the diagonal, so every row sums over all k < i; rows
+        // and columns from wB on come out zero through srd = 0
+        const int D0 = warp * IB;
+        const T* a = sL + D0 * LD + D0;
+        T x[IB];
+#pragma unroll
+        for (int i = 0; i < IB; ++i) {
+            T sum = T(0);
+#pragma unroll
+            for (int k = 0; k < i; ++k) sum = fma(a[i * LD + k], x[k], sum);
+            const T r = srd[D0 + i];
+            x[i] = i < lane ? T(0) : (i == lane ? r : -sum * r);
+        }
+#pragma unroll
+        for (int i = 0; i < IB; ++i) sW[(D0 + i) * LD + D0 + lane] = x[i];
+    }
+    __syncthreads();
+    trinv_level0_pairs<T, 32>(sL, sW, sX);
+    if constexpr (LB > 64) trinv_level0_pairs<T, 64>(sL, sW, sX);
+}
+
+// 32 x 32 tile acc = sum over the 32-wide K chunks kc = k0, k0 + 32, .. < k1
+// of A[r0 + i][kc + j] B[kc + j][c0 + l] (rows, columns and k from M on read
+// as zero), returned as in a 256-thread layout: thread t holds row t / 8,
+// columns 4 (t % 8) .. + 3. Four groups of 64 threads take every fourth
+// chunk; each thread forms a 4 x 4 block of its group's partial tile from
+// two 16-byte shared-memory reads per k (a column of A, staged transposed,
+// and a row of B), and the partial tiles are summed through shared memory.
+// The transposed A chunk keeps 4-element groups contiguous and XOR-swizzles
+// them by k / 4 (group (i / 4) ^ (k / 4 % 8)), so that the staging stores
+// and the reads are free of bank conflicts. Float operands with M % 4 == 0
+// are fetched 16 bytes a lane (an SM sustains several times more bytes per
+// clock from 16-byte loads than from 4-byte ones); otherwise element-wise.
+// Up to KB2 chunks per group are in registers before the first is used.
+// sm: 8192 elements of T.
+constexpr int KB2 = 2;
+__device__ __forceinline__ void group_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ int at_idx(int k, int i) {
+    return k * IB + ((((i >> 2) ^ ((k >> 2) & 7)) << 2) | (i & 3));
+}
+template <typename T, bool VEC>
+__device__ __forceinline__ void tile_mm4_run(const T* __restrict__ A, const T* __restrict__ B, int M, int r0,
+                                             int c0, int k0, int k1, T (&acc)[4][4], T* At, T* Bs) {
+    const int tid = threadIdx.x, grp = tid >> 6, t = tid & 63, w = t >> 5, l = t & 31;
+    const int ty4 = t >> 3, tx4 = t & 7;
+    constexpr int NL = VEC ? 4 : 16;  // loads of each operand per thread and chunk
+    using V = typename std::conditional<VEC, float4, T>::type;
+    const int nch = k1 > k0 ? (k1 - k0 + IB - 1) / IB : 0;
+    for (int cb = 0; cb < nch; cb += 4 * KB2) {
+        V va[KB2][NL], vb[KB2][NL];
+#pragma unroll
+        for (int u = 0; u < KB2; ++u) {
+            const int ch = cb + grp + 4 * u;
+            const int kc = k0 + ch * IB;
+            const bool in = ch < nch;
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                if constexpr (VEC) {
+                    // 4 rows x 128 bytes a warp: row (l / 8) + 4 (2 q + w), 16 bytes at 4 (l % 8)
+                    const int i = (l >> 3) + 4 * (2 * q + w), j = 4 * (l & 7);
+                    va[u][q] = (in && r0 + i < M && kc + j < M)
+                                   ? *reinterpret_cast<const float4*>(A + (int64_t)(r0 + i) * M + kc + j)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    vb[u][q] = (in && kc + i < M && c0 + j < M)
+                                   ? *reinterpret_cast<const float4*>(B + (int64_t)(kc + i) * M + c0 + j)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    // A: row (l % 4) + 4 (2 (q / 4) + w), k 4 (l / 4) + q % 4; B: k 2 q + w, column l
+                    const int i = (l & 3) + 4 * (2 * (q >> 2) + w), j = 4 * (l >> 2) + (q & 3);
+                    va[u][q] = (in && r0 + i < M && kc + j < M) ? A[(int64_t)(r0 + i) * M + kc + j] : T(0);
+                    const int bi = 2 * q + w;
+                    vb[u][q] = (in && kc + bi < M && c0 + l < M) ? B[(int64_t)(kc + bi) * M + c0 + l] : T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KB2; ++u) {
+            if (cb + grp + 4 * u >= nch) break;  // uniform within the group
+            group_bar(1 + grp);                   // the group's last chunk is consumed
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                if constexpr (VEC) {
+                    const int i = (l >> 3) + 4 * (2 * q + w), j = 4 * (l & 7);
+                    At[at_idx(j, i)] = va[u][q].x;
+                    At[at_idx(j + 1, i)] = va[u][q].y;
+                    At[at_idx(j + 2, i)] = va[u][q].z;
+                    At[at_idx(j + 3, i)] = va[u][q].w;
+                    *reinterpret_cast<float4*>(Bs + i * IB + j) = vb[u][q];
+                } else {
+                    const int i = (l & 3) + 4 * (2 * (q >> 2) + w), j = 4 * (l >> 2) + (q & 3);
+                    At[at_idx(j, i)] = va[u][q];
+                    Bs[(2 * q + w) * IB + l] = vb[u][q];
+                }
+            }
+            group_bar(1 + grp);
 #pragma unroll 8
-            for (int l = 0; l < IB; ++l) {
-                const T av = sa[ty][l];
+            for (int k = 0; k < IB; ++k) {
+                T a4[4], b4[4];
+                ld4(At + at_idx(k, 4 * ty4), a4);
+                ld4(Bs + k * IB + 4 * tx4, b4);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[c] = fma(av, sb[l][tx + c], acc[c]);
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fma(a4[r], b4[c], acc[r][c]);
             }
         }
+    }
+}
+template <typename T>
+__device__ __forceinline__ void tile_mm4(const T* __restrict__ A, const T* __restrict__ B, int M, int r0, int c0,
+                                         int k0, int k1, T (&out)[4], T* sm) {
+    const int tid = threadIdx.x, grp = tid >> 6, t = tid & 63;
+    const int ty4 = t >> 3, tx4 = t & 7;
+    T acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+    T* At = sm + grp * 2 * IB * IB;
+    T* Bs = At + IB * IB;
+    if (sizeof(T) == 4 && (M & 3) == 0) {
+        if constexpr (sizeof(T) == 4) tile_mm4_run<T, true>(A, B, M, r0, c0, k0, k1, acc, At, Bs);
+    } else {
+        tile_mm4_run<T, false>(A, B, M, r0, c0, k0, k1, acc, At, Bs);
+    }
+    __syncthreads();
+    // partial tiles red[grp][row][col] (stride 33) over the staging buffers
+    T* red = sm + grp * IB * (IB + 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) red[(4 * ty4 + r) * (IB + 1) + 4 * tx4 + c] = acc[r][c];
+    __syncthreads();
+    const int ry = tid >> 3, rx = (tid & 7) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        T v = T(0);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) v += sm[g * IB * (IB + 1) + ry * (IB + 1) + rx + c];
+        out[c] = v;
     }
     __syncthreads();
 }
 
 // Lt: L in the arithmetic type T (converted here when T is float; L itself
-// when T is double); Wt: W in T (W itself when T is double); X: M x M scratch.
+// when T is double); Wt: the result W in T (the float64 output itself when T
+// is double; the float32 fit keeps no float64 copy); X: M x M scratch.
 // At the end WT (Lt's buffer when T is float, X's when T is double) holds
-// W^T in T, for the solve's W^T t.
+// W^T in T on and above the diagonal, for the solve's W^T t; below it, WT is
+// whatever the buffer held (the parts of L and X the phases used).
 template <typename T>
-__global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict__ L, double* __restrict__ W,
-                                                       int M, T* __restrict__ Lt, T* __restrict__ Wt,
+__global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict__ L, int M,
+                                                       T* __restrict__ Lt, T* __restrict__ Wt,
                                                        T* __restrict__ X, T* __restrict__ WT, GpStatus* st,
                                                        GridBar* gb) {
+    constexpr int LB = InvGeom<T>::LB, LD = InvGeom<T>::LD, XD = InvGeom<T>::XD;
     __shared__ T sa[IB][IB + 1];
-    __shared__ T sb[IB][IB + 1];
-    __shared__ T rd[IB];
-    const int tid = threadIdx.x, ty = tid >> 3, tx = (tid & 7) * 4;
-    const int nb = (M + IB - 1) / IB;
+    extern __shared__ __align__(16) unsigned char inv_raw[];
+    T* sdyn = reinterpret_cast<T*>(inv_raw);  // level 0, then the tile products
+    T* sL = sdyn;
+    T* sW = sL + LB * LD;
+    T* sX = sW + LB * LD;
+    T* srd = sX + (LB / 2) * XD;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, ty = tid >> 3, tx = (tid & 7) * 4;
     const int G = gridDim.x;
     constexpr bool conv = sizeof(T) != sizeof(double);
-    // ---- level 0: L in T, zero upper triangles, D_I = L_II^{-1}
-    const int64_t total = (int64_t)M * M;
-    for (int64_t e = (int64_t)blockIdx.x * NT + tid; e < total; e += (int64_t)G * NT) {
-        const int i = (int)(e / M), j = (int)(e % M);
-        if (j > i) {
-            W[e] = 0.0;
-            if (conv) Wt[e] = T(0);
-        } else if (conv) {
-            Lt[e] = (T)L[e];
-        }
-    }
-    for (int I = blockIdx.x; I < nb; I += G) {
-        const int r0 = I * IB, wI = min(IB, M - r0);
-#pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT, i = e / IB, j = e % IB;
-            sa[i][j] = (i < wI && j <= i) ? (T)L[(int64_t)(r0 + i) * M + r0 + j] : T(0);
-            sb[i][j] = T(0);
-        }
-        __syncthreads();
-        if (tid < IB) rd[tid] = tid < wI ? T(1) / sa[tid][tid] : T(0);
-        __syncthreads();
-        if (tid < IB) {
-            // column j of L_II^{-1} by forward substitution, held in registers
-            // (x[k] = 0 above the diagonal, so every row sums over all k < i;
-            // rows and columns beyond wI come out zero through rd = 0)
-            const int j = tid;
-            T x[IB];
-#pragma unroll
-            for (int i = 0; i < IB; ++i) {
-                T sum = T(0);
-#pragma unroll
-                for (int k = 0; k < i; ++k) sum = fma(sa[i][k], x[k], sum);
-                x[i] = i < j ? T(0) : (i == j ? rd[i] : -sum * rd[i]);
+    // ---- level 0: diagonal LB blocks (CTAs 0 .. nlb - 1), and outside them
+    // zeros above the diagonal and L in T below it (the other CTAs, if any)
+    const int nlb = (M + LB - 1) / LB;
+    for (int b = blockIdx.x; b < nlb; b += G) {
+        const int R0 = b * LB, wB = min(LB, M - R0);
+        trinv_level0<T>(L, M, R0, wB, sL, sW, sX, srd);
+        // the lower triangle of W and Wt (row i = warp + 8 t), and W^T above
+        // the diagonal (row c, lanes across r >= c; the column reads of sW
+        // cost a 4-way bank conflict, less than staging 32 x 32 transposes)
+        for (int i = warp; i < wB; i += NT / 32) {
+            for (int j = lane; j <= i; j += 32) {
+                const int64_t o = (int64_t)(R0 + i) * M + R0 + j;
+                Wt[o] = sW[i * LD + j];
             }
-#pragma unroll
-            for (int i = 0; i < IB; ++i) sb[i][j] = x[i];
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT, i = e / IB, j = e % IB;
-            if (i < wI && j < wI && j <= i) {
-                const int64_t o = (int64_t)(r0 + i) * M + r0 + j;
-                W[o] = (double)sb[i][j];
-                if (conv) Wt[o] = sb[i][j];
-            }
+        for (int c = warp; c < wB; c += NT / 32) {
+            for (int r = c + lane; r < wB; r += 32) WT[(int64_t)(R0 + c) * M + R0 + r] = sW[r * LD + c];
         }
         __syncthreads();
     }
+    {
+        // CTAs nlb .. G - 1 (all, if there are no more than nlb): zeros above
+        // the diagonal, L in T below the level-0 blocks
+        const int c0 = G > nlb ? nlb : 0, nc = G - c0;
+        if (blockIdx.x >= c0) {
+            for (int i = (blockIdx.x - c0) * (NT / 32) + warp; i < M; i += nc * (NT / 32)) {
+                const int bi = i / LB;
+                const int64_t ro = (int64_t)i * M;
+                for (int j = lane; j < M; j += 32) {
+                    if (j > i) {
+                        Wt[ro + j] = T(0);
+                    } else if (conv && j / LB < bi) {
+                        Lt[ro + j] = to_t(L[ro + j], (T*)nullptr);
+                    }
+                }
+            }
+        }
+    }
+    if (LB >= M) return;
     if (!grid_sync(gb, st)) return;
     const T* Lr = conv ? Lt : reinterpret_cast<const T*>(L);
-    for (int h = IB; h < M; h *= 2) {
+    for (int h = LB; h < M; h *= 2) {
         const int hb = h / IB;                     // blocks per half
         const int ng = (M + 2 * h - 1) / (2 * h);  // pairs at this level
         const int ntile = ng * hb * hb;            // (S block, F block) tiles, full pairs
@@ -574,49 +872,35 @@ __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict_
             const int r0 = S0 + si * IB, c0 = F0 + fj * IB;
             if (r0 >= M) continue;
             T acc[4] = {T(0), T(0), T(0), T(0)};
-            tile_mm<T>(Lr, Wt, M, r0, c0, c0, S0, acc, sa, sb);  // W[k][c0..] = 0 for k < c0
+            tile_mm4<T>(Lr, Wt, M, r0, c0, c0, S0, acc, sdyn);  // W[k][c0..] = 0 for k < c0
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if (r0 + ty < M) X[(int64_t)(r0 + ty) * M + c0 + tx + c] = acc[c];
         }
         if (!grid_sync(gb, st)) return;
-        // ---- B: W[S][F] = -W[S][S] X[S][F]
+        // ---- B: W[S][F] = -W[S][S] X[S][F], and its transpose into WT[F][S]
         for (int t = blockIdx.x; t < ntile; t += G) {
             const int g = t / (hb * hb), si = (t / hb) % hb, fj = t % hb;
             const int F0 = g * 2 * h, S0 = F0 + h;
             const int r0 = S0 + si * IB, c0 = F0 + fj * IB;
             if (r0 >= M) continue;
             T acc[4] = {T(0), T(0), T(0), T(0)};
-            tile_mm<T>(Wt, X, M, r0, c0, S0, min(r0 + IB, M), acc, sa, sb);  // W[r][k] = 0 for k > r
+            tile_mm4<T>(Wt, X, M, r0, c0, S0, min(r0 + IB, M), acc, sdyn);  // W[r][k] = 0 for k > r
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int64_t o = (int64_t)(r0 + ty) * M + c0 + tx + c;
-                if (r0 + ty < M) {
-                    W[o] = (double)(-acc[c]);
-                    if (conv) Wt[o] = -acc[c];
-                }
+                if (r0 + ty < M) Wt[o] = -acc[c];
+                sa[tx + c][ty] = -acc[c];
             }
-        }
-        if (!grid_sync(gb, st)) return;
-    }
-    // ---- W^T (in T) by 32 x 32 blocks through shared memory
-    const int nb2 = nb * nb;
-    for (int t = blockIdx.x; t < nb2; t += G) {
-        const int bi = t / nb, bj = t % nb;
+            __syncthreads();
 #pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT, i = e / IB, j = e % IB;
-            const int r = bi * IB + i, c = bj * IB + j;
-            sa[i][j] = (r < M && c < M) ? Wt[(int64_t)r * M + c] : T(0);
+            for (int q = 0; q < IB * IB / NT; ++q) {
+                const int e = tid + q * NT, i = e / IB, j = e % IB;
+                if (r0 + j < M) WT[(int64_t)(c0 + i) * M + r0 + j] = sa[i][j];
+            }
+            // the next tile_mm4's barriers order these reads before sa is written again
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < IB * IB / NT; ++q) {
-            const int e = tid + q * NT, i = e / IB, j = e % IB;
-            const int r = bj * IB + i, c = bi * IB + j;
-            if (r < M && c < M) WT[(int64_t)r * M + c] = sa[j][i];
-        }
-        __syncthreads();
+        if (2 * h < M && !grid_sync(gb, st)) return;
     }
 }
 
@@ -699,9 +983,10 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
     }
 }
 
-// CTAs of a cooperative launch of `kern` (one per SM), cached per kernel and
+// CTAs of a cooperative launch of `kern` (one per SM) with `smem` bytes of
+// dynamic shared memory (allowed beyond 48 KB here), cached per kernel and
 // device: the occupancy query costs more host time than the launch itself.
-int coop_grid(const void* kern, int dev) {
+int coop_grid(const void* kern, int dev, size_t smem = 0) {
     static std::mutex mu;
     static std::map<std::pair<const void*, int>, int> cache;
     {
@@ -711,7 +996,8 @@ int coop_grid(const void* kern, int dev) {
     }
     int sms = 1, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
     if (occ < 1) occ = 1;
     const int g = sms * (occ < 2 ? occ : 1);
     std::lock_guard<std::mutex> lk(mu);
@@ -751,6 +1037,19 @@ cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStre
     return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, grid, block, args, 0, stream);
 }
 
+namespace {
+// widest phase of the inverse: the diagonal blocks of level 0, or the tiles
+// of the last level's pairs
+int trinv_want(int M, int LB) {
+    const int nlb = (M + LB - 1) / LB;
+    if (LB >= M) return nlb;
+    int hmax = LB;
+    while (hmax * 2 < M) hmax *= 2;
+    const int hb = hmax / IB;
+    return std::max(nlb, ((M + 2 * hmax - 1) / (2 * hmax)) * hb * hb);
+}
+}  // namespace
+
 cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
                                cudaStream_t stream) {
     int dev = 0;
@@ -758,32 +1057,32 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
     GridBar* gb = (GridBar*)work;
     cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
     char* base = (char*)work + CHOL_RSD_OFFSET;
-    const int nb = (M + IB - 1) / IB;
-    // enough CTAs for the widest phase (the last level's tiles) and level 0
-    int hmax = IB;
-    while (hmax * 2 < M) hmax *= 2;
-    const int hb = hmax / IB;
-    const int want = std::max(nb, ((M + 2 * hmax - 1) / (2 * hmax)) * hb * hb);
     gp_note_launches(1);
     const size_t M2 = (size_t)M * M;
     if (fp32) {
         float* Lt = (float*)base;
         float* Wt = Lt + M2;
         float* X = Wt + M2;
-        float* WT = Lt;  // L in float is no longer needed once W is complete
+        float* WT = Lt;  // W^T goes where L in float is no longer read
         const void* k = (const void*)trinv_rec_kernel<float>;
-        dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-        void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &WT, &st, &gb};
-        return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
+        const size_t smem = trinv_smem_bytes<float>();
+        dim3 grid((unsigned)std::min(trinv_want(M, InvGeom<float>::LB), coop_grid(k, dev, smem))), block(NT);
+        void* args[] = {(void*)&L, &M, &Lt, &Wt, &X, &WT, &st, &gb};
+        return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
     }
     double* Lt = nullptr;
     double* Wt = W;
     double* X = (double*)base;
-    double* WT = X;  // X is free after the last level
+    double* WT = X;  // above the diagonal, where X is never used
     const void* k = (const void*)trinv_rec_kernel<double>;
-    dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-    void* args[] = {(void*)&L, &W, &M, &Lt, &Wt, &X, &WT, &st, &gb};
-    return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
+    const size_t smem = trinv_smem_bytes<double>();
+    dim3 grid((unsigned)std::min(trinv_want(M, InvGeom<double>::LB), coop_grid(k, dev, smem))), block(NT);
+    void* args[] = {(void*)&L, &M, &Lt, &Wt, &X, &WT, &st, &gb};
+    return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
+}
+
+const float* tri_inverse_fp32_w(const void* work, int M) {
+    return (const float*)((const char*)work + CHOL_RSD_OFFSET) + (size_t)M * M;
 }
 
 size_t solve_refine_work_elems(int M) {

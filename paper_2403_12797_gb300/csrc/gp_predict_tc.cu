@@ -338,11 +338,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// W (M x M float64, lower) -> packed bf16 hi/lo blocks: for chunk c (32
+// W (M x M float32, lower) -> packed bf16 hi/lo blocks: for chunk c (32
 // columns m) and block b (128 rows k), hi then lo, each 128 x 32 in the
 // K-major core-matrix layout of the MMA's B operand. Thread idx < Mpad also
 // writes the float32 copy of c (zero beyond M) that follows the blocks.
-__global__ void pack_w_kernel(const double* __restrict__ W, const double* __restrict__ cvec, int M,
+__global__ void pack_w_kernel(const float* __restrict__ W, const double* __restrict__ cvec, int M,
                               int Mpad, uint8_t* __restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int KBt = Mpad / KB;
@@ -362,7 +362,7 @@ __global__ void pack_w_kernel(const double* __restrict__ W, const double* __rest
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
         const int m = c * BK + g * 8 + kk;
-        v[kk] = (k < M && m < M && m <= k) ? (float)W[(int64_t)k * M + m] : 0.f;
+        v[kk] = (k < M && m < M && m <= k) ? W[(int64_t)k * M + m] : 0.f;
     }
     uint32_t h[4], l[4];
 #pragma unroll
@@ -381,7 +381,7 @@ size_t predtc_wpack_bytes(int M) {
     return 4 * Mpad * Mpad + 4 * Mpad;
 }
 
-void launch_pack_w_bf16x3(const double* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream) {
+void launch_pack_w_bf16x3(const float* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream) {
     const int Mpad = (int)gp_round_up(M, KB);
     const int64_t total = (int64_t)(Mpad / BK) * (Mpad / KB) * KB * (BK / 8);
     pack_w_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(W, c, M, Mpad, (uint8_t*)Wpack);

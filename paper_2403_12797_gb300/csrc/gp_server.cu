@@ -149,7 +149,7 @@ size_t refit_bytes(const gp_model* m, int64_t N, int sms) {
     const size_t Npad = (size_t)gp_round_up(N, 128);
     const size_t M = (size_t)s.M;
     size_t b = (size_t)N * (s.p + 1) * 8;                        // X, y
-    b += 2 * M * M * 8 + 5 * M * 8;                               // new model: L, W, c, b, d
+    b += (m->prec == GP_PREC_FP64 ? 2 : 1) * M * M * 8 + 5 * M * 8; // new model: L, W (float64 fit), c, b, d
     if (m->prec != GP_PREC_FP64) b += predtc_wpack_bytes((int)M) + predtc_cinfo_ints(s) * 4;
     b += M * M * 8 + solve_refine_work_elems((int)M) * 8 + factor_work_bytes((int)M, true);
     b += (size_t)s.p * s.n * Npad * 8 + Npad * 8;                 // tables, padded y

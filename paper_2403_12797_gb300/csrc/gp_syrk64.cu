@@ -58,7 +58,7 @@ __host__ __device__ inline size_t smem64_layout(int maxrows, int p, char* base, 
     return off;
 }
 
-__device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0, int* tr,
+__device__ __forceinline__ void setup_tile(const GpShape& s, const TileWindow& w, int m0, int* tr,
                            unsigned short* cr) {
     for (int r = threadIdx.x; r < w.nrows; r += blockDim.x) tr[r] = window_table_row(s, w, r);
     for (int e = threadIdx.x; e < TM * s.p; e += blockDim.x) {
@@ -68,7 +68,7 @@ __device__ void setup_tile(const GpShape& s, const TileWindow& w, int m0, int* t
     }
 }
 
-__device__ void load_window(const GpShape& s, const double* __restrict__ tab, const int* tr,
+__device__ __forceinline__ void load_window(const GpShape& s, const double* __restrict__ tab, const int* tr,
                             int nrows, int64_t i0, double* win) {
     for (int e = threadIdx.x; e < nrows * BK; e += blockDim.x) {
         int r = e / BK, k = e % BK;
@@ -76,7 +76,7 @@ __device__ void load_window(const GpShape& s, const double* __restrict__ tab, co
     }
 }
 
-__device__ void gen_phi(const GpShape& s, const double* win, const unsigned short* cr, int m0,
+__device__ __forceinline__ void gen_phi(const GpShape& s, const double* win, const unsigned short* cr, int m0,
                         double* phi) {
     for (int e = threadIdx.x; e < BK * TM; e += blockDim.x) {
         int c = e % TM, k = e / TM;

@@ -247,24 +247,25 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 // (|lo| <= 1/2, 11-bit precision, subnormals below 2^-14); store both
 // core-matrix rows. The float-to-integer rounding and float16 packing
 // instructions run at a fraction of the FMA rate, so s1 avoids both: adding
-// 1.5 * 2^23 rounds w to the nearest integer k (ties to even) in the low
-// mantissa bits of t, the integer k + 1152 has the float16 bit pattern
-// 0x6480 + k (exponent 2^10), and one exact half2 subtraction of 1152 leaves
-// k. Only the remainder takes a float16 conversion.
+// the magic K = 1.5 * 2^23 + 0x6480 (still in [2^23, 2^24), where floats
+// are the integers) rounds w to the nearest integer k (ties to even), and
+// the low 16 bits of the sum t are then 0x6480 + k -- the float16 bit
+// pattern of 1152 + k (exponent 2^10) -- for |k| <= 128, with no carry out
+// of the half word. One byte permute packs two of them and one exact half2
+// subtraction of 1152 leaves k. Only the remainder takes a float16
+// conversion.
 template <uint32_t SBO>
 __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
                                              const float v[8], float sc) {
-    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr float kMagic = 12608640.0f;  // 1.5 * 2^23 + 0x6480
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         // v * sc is exact (sc is a power of two), so one rounding each: t rounds
-        // v sc + 1.5 2^23 to an integer, a = rint(v sc), lo = v sc - a exactly
+        // v sc + K to an integer, a = rint(v sc), lo = v sc - a exactly
         const float t0 = __fmaf_rn(v[2 * q], sc, kMagic), t1 = __fmaf_rn(v[2 * q + 1], sc, kMagic);
         const float a0 = __fsub_rn(t0, kMagic), a1 = __fsub_rn(t1, kMagic);
-        const uint32_t b0 = (uint32_t)__float_as_int(t0) - 0x4B400000u + 0x6480u;
-        const uint32_t b1 = (uint32_t)__float_as_int(t1) - 0x4B400000u + 0x6480u;
-        const uint32_t raw = __byte_perm(b0, b1, 0x5410);
+        const uint32_t raw = __byte_perm((uint32_t)__float_as_int(t0), (uint32_t)__float_as_int(t1), 0x5410);
         uint32_t k2;
         asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(k2) : "r"(raw), "r"(0x64806480u));  // - (1152, 1152)
         h[q] = k2;

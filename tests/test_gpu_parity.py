@@ -67,11 +67,17 @@ def _small_cases():
     out.append(W.random_problem(21, 5_000, 333, 4, 4, eps=0.8, alpha=1.2, sigma2=0.02))
     out.append(W.random_problem(22, 300, 129, 1, 40, eps=1.0, alpha=1.0, sigma2=0.01))
     out.append(W.random_problem(23, 1, 7, 2, 3))
+    # odd M across the inverse's diagonal blocks (128 rows in float32, 64 in
+    # float64) and its doubling levels: one block plus one row, a ragged
+    # second block, several levels
+    out.append(W.random_problem(24, 3_000, 200, 1, 129, eps=1.0, alpha=1.0, sigma2=0.02))
+    out.append(W.random_problem(25, 4_000, 200, 1, 201, eps=1.0, alpha=1.0, sigma2=0.02))
+    out.append(W.random_problem(26, 6_000, 200, 3, 7, eps=0.9, alpha=1.1, sigma2=0.02))
     return out
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(9))
 def test_fit_predict_matches_oracle(prec, case):
     pr = _small_cases()[case]
     m, mean, var = _fit_predict(pr, prec)
