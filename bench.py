@@ -202,8 +202,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(prec):
-        m = _lib.fit(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
-        m.predict(Xs, mean_out=mean, var_out=var)
+        # fit and predict through the one-call entry point (the same kernels
+        # as fit() then predict(), without the host round trip between them)
+        m, _, _ = _lib.fit_predict(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, Xs, prec=prec,
+                                   mean_out=mean, var_out=var)
         m.free()
 
     prec = args.prec
@@ -323,8 +325,8 @@ def compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np):
     var = torch.empty(pr.Ns, dtype=torch.float64, device=dev)
 
     def step(prec):
-        m = _lib.fit(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
-        m.predict(Xs, mean_out=mean, var_out=var)
+        m, _, _ = _lib.fit_predict(X, y, pr.n, pr.eps, pr.alpha, pr.sigma2, Xs, prec=prec,
+                                   mean_out=mean, var_out=var)
         m.free()
 
     step("fp64")
@@ -351,8 +353,8 @@ def compare_and_baselines(args, pr, X, y, Xs, dev, stream, _lib, torch, np):
     vh = torch.empty(pr.Ns, dtype=torch.float64).pin_memory().numpy()
 
     def e2e_step():
-        m = _lib.fit(Xh, yh, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=args.prec)
-        m.predict(Xsh, mean_out=mh, var_out=vh)
+        m, _, _ = _lib.fit_predict(Xh, yh, pr.n, pr.eps, pr.alpha, pr.sigma2, Xsh, prec=args.prec,
+                                   mean_out=mh, var_out=vh)
         m.free()
 
     for _ in range(max(3, args.warmup)):

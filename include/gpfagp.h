@@ -123,6 +123,20 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
 GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
                              double* mean, double* var, void* cuda_stream, int dev_ptrs);
 
+/* gp_fit_ex followed by gp_predict_ex on the fitted model (Sec. 2.2 and
+ * Eq. 8-9, the same kernels), with the prediction enqueued right behind the
+ * fit and a single status read at the end, so the device does not wait for
+ * the host between the two. Arguments as in gp_fit_ex (X, y, N, ...,
+ * dev_ptrs, out) and gp_predict_ex (Xs, Ns, mean, var; var may be NULL);
+ * every pointer is of the kind dev_ptrs names. A mixed fit that the float64
+ * Gram must redo (see gp_model_flags) is redone, and its prediction with it.
+ * On GP_OK *out receives the model and mean/var hold the prediction; on
+ * error *out is NULL and mean/var are unspecified. */
+GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, int p, int n,
+                                 double eps, double alpha, double sigma2, int prec,
+                                 const double* Xs, int64_t Ns, double* mean, double* var,
+                                 void* cuda_stream, int dev_ptrs, gp_model** out);
+
 /* Model shape and mode: any output pointer may be NULL. */
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
 

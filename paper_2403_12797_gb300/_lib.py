@@ -76,6 +76,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_strerror": (C.c_char_p, [i]),
         "gp_fit_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_predict_ex": (i, [vp, vp, i64, vp, vp, vp, i]),
+        "gp_fit_predict_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i64, vp, vp, vp, i, C.POINTER(vp)]),
         "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "gp_model_read": (i, [vp, i, vp]),
         "gp_gram_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, vp, i]),
@@ -224,6 +225,33 @@ class Model:
             self.free()
         except Exception:
             pass
+
+
+def fit_predict(X, y, n: int, eps: float, alpha: float, sigma2: float, Xs, prec: str = "mixed",
+                var: bool = True, mean_out=None, var_out=None, stream=None):
+    """fit(X, y, ...) then Model.predict(Xs) in one library call: the
+    prediction is enqueued behind the fit with one status read at the end.
+    Returns (model, mean, var or None); all arrays host or all device."""
+    X, y, N, p, dev = _prep_xy(X, y)
+    Xs, _, Ns, ps, devs = _prep_xy(Xs, None)
+    if ps != p:
+        raise ValueError(f"Xs has {ps} columns, X has {p}")
+    if devs != dev:
+        raise TypeError("X and Xs must both be host arrays or both device tensors")
+    if dev:
+        import torch
+        mean = mean_out if mean_out is not None else torch.empty(Ns, dtype=torch.float64, device=Xs.device)
+        vv = (var_out if var_out is not None else torch.empty(Ns, dtype=torch.float64, device=Xs.device)) if var else None
+    else:
+        mean = mean_out if mean_out is not None else np.empty(Ns)
+        vv = (var_out if var_out is not None else np.empty(Ns)) if var else None
+    out = C.c_void_p()
+    rc = lib().gp_fit_predict_ex(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),
+                                 float(alpha), float(sigma2), PREC[prec], C.c_void_p(_ptr(Xs)), Ns,
+                                 C.c_void_p(_ptr(mean)), C.c_void_p(_ptr(vv)) if vv is not None else None,
+                                 _stream_of(X, stream), dev, C.byref(out))
+    _check(rc, "gp_fit_predict_ex")
+    return Model(out.value), mean, vv
 
 
 def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "mixed",

@@ -755,6 +755,91 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     return GP_OK;
 }
 
+namespace {
+// The device steps of a predict on a fitted model into device or host
+// outputs (host: staged through scratch and copied back on the stream).
+int predict_enqueue(const gp_model* h, const double* Xs, int64_t Ns, double* mean, double* var, int dev_ptrs,
+                    GpStatus* st, Scratch& sc, cudaStream_t stream) {
+    if (Ns == 0) return GP_OK;
+    const double* Xd = Xs;
+    double *md = mean, *vd = var;
+    int rc;
+    if (!dev_ptrs) {
+        double* xx;
+        if ((rc = sc.get(&xx, (size_t)Ns * h->shape.p))) return rc;
+        if ((rc = sc.get(&md, (size_t)Ns))) return rc;
+        if (var && (rc = sc.get(&vd, (size_t)Ns))) return rc;
+        cudaMemcpyAsync(xx, Xs, sizeof(double) * Ns * h->shape.p, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+    }
+    if ((rc = predict_compute(h, Xd, Ns, md, vd, st, sc, stream))) return rc;
+    if (!dev_ptrs) {
+        cudaMemcpyAsync(mean, md, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+        if (var) cudaMemcpyAsync(var, vd, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+    }
+    return GP_OK;
+}
+}  // namespace
+
+GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                                 double alpha, double sigma2, int prec, const double* Xs, int64_t Ns,
+                                 double* mean, double* var, void* cuda_stream, int dev_ptrs, gp_model** out) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!out) return set_err(GP_EINVAL, 0);
+    *out = nullptr;
+    if (!X || !y || Ns < 0 || (Ns > 0 && (!Xs || !mean))) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
+    if ((rc = check_prec(prec))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    gp_model* h = new_model(dev, prec, N, p, n, eps, alpha, sigma2);
+    Scratch sc(stream);
+    FitStage stage;
+    auto fail = [&](int code) {
+        int64_t det = g_detail;
+        cudaStreamSynchronize(stream);
+        free_model(h);
+        set_err(code, det);
+        return code;
+    };
+    if ((rc = fit_alloc(h, stream))) return fail(rc);
+    GpStatus* st;
+    double* loglam;
+    if ((rc = sc.get(&st, 1))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    const double *Xd = X, *yd = y;
+    if (!dev_ptrs) {
+        double *xx, *yy;
+        if ((rc = sc.get(&xx, (size_t)N * p))) return fail(rc);
+        if ((rc = sc.get(&yy, (size_t)N))) return fail(rc);
+        cudaMemcpyAsync(xx, X, sizeof(double) * N * p, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+        yd = yy;
+    }
+    if ((rc = fit_stage(h, stage, loglam, stream))) return fail(rc);
+    if ((rc = fit_compute(h, Xd, yd, loglam, st, 0, sc, stream))) return fail(rc);
+    // the predict reads the model the fit leaves; if the fit failed, what it
+    // computes is discarded below
+    if ((rc = predict_enqueue(h, Xs, Ns, mean, var, dev_ptrs, st, sc, stream))) return fail(rc);
+    // the staged host vectors live until this read synchronises the stream
+    rc = read_status(st, stream);
+    if (mixed_escalates(h, rc)) {
+        set_err(GP_OK);
+        cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+        Scratch sc2(stream);
+        if ((rc = fit_compute(h, Xd, yd, loglam, st, 0, sc2, stream, GP_PREC_FP64))) return fail(rc);
+        if ((rc = predict_enqueue(h, Xs, Ns, mean, var, dev_ptrs, st, sc2, stream))) return fail(rc);
+        rc = read_status(st, stream);
+    }
+    if (rc) return fail(rc);
+    *out = h;
+    return GP_OK;
+}
+
 GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p, int n, double eps,
                               double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
                               gp_model** out) {

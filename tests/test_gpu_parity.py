@@ -159,6 +159,52 @@ def test_fit_is_deterministic_and_device_path_matches_host(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fit_predict_in_one_call_matches_separate_calls(prec):
+    """gp_fit_predict_ex runs the same kernels as gp_fit_ex + gp_predict_ex,
+    only without the host round trip between them: bit-identical results on
+    host and device pointers, with and without the float64 Gram redo."""
+    import torch
+    pr = W.workload2(N=30_000, Ns=2_000)
+    m1, mean1, var1 = _fit_predict(pr, prec)
+    m2, mean2, var2 = _lib.fit_predict(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, pr.Xs, prec=prec)
+    np.testing.assert_array_equal(mean2, mean1)
+    np.testing.assert_array_equal(var2, var1)
+    np.testing.assert_array_equal(m2.read("c"), m1.read("c"))
+    m2.free()
+    Xd, yd, Xsd = (torch.from_numpy(a).cuda() for a in (pr.X, pr.y, pr.Xs))
+    m3, mean3, var3 = _lib.fit_predict(Xd, yd, pr.n, pr.eps, pr.alpha, pr.sigma2, Xsd, prec=prec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(mean3.cpu().numpy(), mean1)
+    np.testing.assert_array_equal(var3.cpu().numpy(), var1)
+    # mean only, and no test points
+    m4, mean4, none = _lib.fit_predict(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, pr.Xs, prec=prec, var=False)
+    assert none is None
+    np.testing.assert_array_equal(mean4, mean1)
+    m5, mean5, var5 = _lib.fit_predict(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, pr.Xs[:0], prec=prec)
+    assert mean5.shape == (0,) and var5.shape == (0,)
+    np.testing.assert_array_equal(m5.read("c"), m1.read("c"))
+    for m in (m1, m3, m4, m5):
+        m.free()
+    if prec == "mixed":
+        _lib.debug_force_escalation(1)
+        try:
+            me, meane, vare = _lib.fit_predict(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, pr.Xs, prec=prec)
+        finally:
+            _lib.debug_force_escalation(0)
+        _lib.debug_force_escalation(1)
+        try:
+            mf = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+        finally:
+            _lib.debug_force_escalation(0)
+        meanf, varf = mf.predict(pr.Xs)
+        assert me.gram_fp64 and mf.gram_fp64
+        np.testing.assert_array_equal(meane, meanf)
+        np.testing.assert_array_equal(vare, varf)
+        me.free()
+        mf.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_predict_edge_sizes(prec):
     pr = W.workload1()
     m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
