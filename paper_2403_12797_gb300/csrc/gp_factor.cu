@@ -111,12 +111,17 @@ __device__ __forceinline__ int status_code(const GpStatus* st) { return *(volati
 
 // ---------------------------------------------------------------- Cholesky
 
-// Cholesky workspace header: the grid barrier, the counter of finished
-// next-diagonal-block updates, then (from byte 256) 1 / L_jj for every j.
+// Workspace header (256 bytes, zeroed by launch_cholesky with one memset):
+// the Cholesky's grid barrier and its counter of finished next-diagonal-block
+// updates, then the grid barriers of the inverse (byte 64) and of the solve
+// (byte 128), which run after it on the same workspace; from byte 256 on,
+// 1 / L_jj for every j, then the inverse's buffers.
 struct CholWork {
     GridBar bar;
     unsigned int helped;
 };
+constexpr int TRINV_BAR_OFFSET = 64;
+constexpr int SOLVE_BAR_OFFSET = 128;
 constexpr int CHOL_RSD_OFFSET = 256;
 
 struct PotrfSmem {
@@ -1054,8 +1059,7 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
                                cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
-    GridBar* gb = (GridBar*)work;
-    cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
+    GridBar* gb = (GridBar*)((char*)work + TRINV_BAR_OFFSET);  // zeroed by launch_cholesky
     char* base = (char*)work + CHOL_RSD_OFFSET;
     gp_note_launches(1);
     const size_t M2 = (size_t)M * M;
@@ -1086,15 +1090,14 @@ const float* tri_inverse_fp32_w(const void* work, int M) {
 }
 
 size_t solve_refine_work_elems(int M) {
-    return 32 + 2 * (size_t)M;  // grid barrier (256 bytes), t, r
+    return 32 + 2 * (size_t)M;  // 256 bytes unused (alignment), t, r
 }
 
 cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
                                 double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
-    GridBar* gb = (GridBar*)work;
-    cudaMemsetAsync(gb, 0, sizeof(GridBar), stream);
+    GridBar* gb = (GridBar*)((char*)const_cast<void*>(fwork) + SOLVE_BAR_OFFSET);  // zeroed by launch_cholesky
     const int want = (M + NT / 32 - 1) / (NT / 32);
     gp_note_launches(1);
     const char* fbase = (const char*)fwork + CHOL_RSD_OFFSET;

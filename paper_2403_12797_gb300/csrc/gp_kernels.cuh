@@ -69,7 +69,9 @@ int gp_static_gram(const double* X, const double* y, int64_t N, int p, int n, do
 size_t factor_work_bytes(int M, bool fp32_inverse);
 // In-place lower Cholesky of the M x M row-major matrix L (upper part ignored,
 // then zeroed), float64, one cooperative launch. Non-positive pivot ->
-// status GP_ENOTPD, detail = column.
+// status GP_ENOTPD, detail = column. It zeroes the workspace header, which
+// holds the grid barriers of launch_tri_inverse and launch_solve_refine too:
+// those two run after it, on the same workspace.
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream);
 // W = L^{-1} (lower, M x M row-major, upper part zeroed), one cooperative
 // launch: in float64 into W (fp32 = false), or in float32 into the workspace

@@ -128,12 +128,11 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : (float)y[i];
     // every lane runs the whole recurrence (rows beyond N or with bad input
     // are zero from q0 on), so the warp reductions see all 32 lanes
+    // (|v| as bits orders like |v|, so one integer warp reduction gives the maximum)
     auto emit = [&](int k, float v) {
         out[k * WS] = v;
-        float m = fabsf(v);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(bmax + k, __float_as_uint(m));
+        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v)));
+        if ((threadIdx.x & 31) == 0) atomicMax(bmax + k, m);
     };
     const float x = zero ? 0.f : (float)xd;
     const float t = (float)s.alpha_beta * x;
