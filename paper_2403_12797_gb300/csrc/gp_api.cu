@@ -161,9 +161,14 @@ int num_sms(int dev) {
 
 // The fused Gram step: A (M x M) = Phi^T Phi [+ diag(d)], b = Phi^T y.
 // X, y are device pointers.
+// ex (optional, the fit's): the noise diagonal ex->dout from ex->loglam, and
+// A's lower triangle in ex->L. The mixed assembly does both in its kernel
+// (*l_written = true); the float64 path launches the diagonal kernel first and
+// leaves L to the caller.
 int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const double* yd,
                 const double* d, double* A, double* b, GpStatus* st, cudaStream_t stream,
-                int target_ctas = 0) {
+                int target_ctas = 0, const AssembleExtra* ex = nullptr, bool* l_written = nullptr) {
+    if (l_written) *l_written = false;
     Scratch sc(stream);
     int rc;
     if (prec == GP_PREC_FP64) {
@@ -191,6 +196,11 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("assemble", stream);
+            if (ex != nullptr) {
+                launch_noise_diag(*ex->shape, ex->loglam, ex->sigma2, ex->dout, stream);
+                d = ex->dout;
+                gp_note_launches(1);
+            }
             launch_assemble_f64(Gpart, bpart, nsplit, SYRK64_TM, s.Mpad, s.M, d, A, b, stream);
             gp_note_launches(1);
         }
@@ -227,8 +237,9 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_scaled(Gpart, bpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream);
+            launch_assemble_scaled(Gpart, bpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
+            if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -356,7 +367,7 @@ int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t strea
 }
 
 int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
-               cudaStream_t stream);
+               cudaStream_t stream, bool l_ready = false);
 
 __global__ void add_diag_kernel(double* __restrict__ A, const double* __restrict__ d, int M) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,28 +400,32 @@ int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* l
     const bool fp32_inverse = (prec != GP_PREC_FP64);
     unsigned char* fwork;
     if ((rc = sc.get(&fwork, factor_work_bytes(M, fp32_inverse)))) return rc;
-    launch_noise_diag(s, loglam_d, h->sigma2, h->d, stream);
-    gp_note_launches(1);
     const int gp_ = gram_prec < 0 ? prec : gram_prec;
     if (gp_ == GP_PREC_FP64 && prec != GP_PREC_FP64) h->flags |= GP_MODEL_GRAM_FP64;
-    if ((rc = gram_device(s, gp_, h->device, Xd, yd, h->d, A, h->b, st, stream, gram_ctas))) return rc;
+    // the noise diagonal d (Eq. 16, 20) and the Cholesky's copy of A come out
+    // of the assembly
+    const AssembleExtra ex{&s, loglam_d, h->sigma2, h->d, h->L};
+    bool l_written = false;
+    if ((rc = gram_device(s, gp_, h->device, Xd, yd, nullptr, A, h->b, st, stream, gram_ctas, &ex, &l_written)))
+        return rc;
     if (prec == GP_PREC_MIXED && gp_ == GP_PREC_MIXED) {
         int k = g_force_escalate.load();
         while (k > 0 && !g_force_escalate.compare_exchange_weak(k, k - 1)) {
         }
         if (k > 0) force_notpd_kernel<<<1, 1, 0, stream>>>(st);
     }
-    return fit_factor(h, A, work, fwork, st, stream);
+    return fit_factor(h, A, work, fwork, st, stream, l_written);
 }
 
 // The factorisation steps of a fit from the assembled A (device, M x M, kept
 // for the refinement residual): L, W = L^{-1}, c, and the predict operand.
+// l_ready: h->L already holds A's lower triangle.
 int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
-               cudaStream_t stream) {
+               cudaStream_t stream, bool l_ready) {
     const int M = h->shape.M;
     const int prec = h->prec;
     const bool fp32_inverse = (prec != GP_PREC_FP64);
-    cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
+    if (!l_ready) cudaMemcpyAsync(h->L, A, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, stream);
     cudaError_t e;
     {
         GpProf pf("cholesky", stream);

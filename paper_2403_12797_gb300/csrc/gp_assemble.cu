@@ -60,17 +60,54 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
 // float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
 // block is written to A and, through shared memory, transposed into the
 // upper triangle (A is exactly symmetric). Diagonal blocks also sum b.
+// d_m = sigma2 / lambda_m = exp(log sigma2 - sum_j log lambda_{m_j}) (Eq. 16,
+// 20), clamped at 1e200
+__device__ __forceinline__ double noise_diag_entry(const GpShape& s, const double* __restrict__ loglam,
+                                                   double log_sigma2, int m) {
+    double ll = 0.0;
+    for (int j = 0; j < s.p; ++j) ll += loglam[(m / s.stride[j]) % s.n];
+    const double logd = log_sigma2 - ll;
+    const double lclamp = 460.51701859880913680;  // log(1e200)
+    return logd >= lclamp ? 1e200 : exp(logd);
+}
+
+// With loglam given, the diagonal of A gets d_m computed here (and stored in
+// dout) instead of read from d; with L given, the lower triangle of A is also
+// written there (the Cholesky's input), which saves a separate copy.
 __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __restrict__ Gpart,
                                                               const double* __restrict__ bpart,
                                                               const int* __restrict__ colexp, int nsplit,
                                                               int Mpad, int M, const double* __restrict__ d,
-                                                              double* __restrict__ A, double* __restrict__ b) {
+                                                              double* __restrict__ A, double* __restrict__ b,
+                                                              GpShape sh, const double* __restrict__ loglam,
+                                                              double log_sigma2, double* __restrict__ dout,
+                                                              double* __restrict__ Lc) {
     constexpr int TT = 128, B = 32;
     __shared__ double t[B][B + 1];
+    __shared__ double sd[B];
     int bi, bj;
     tri_pair(blockIdx.x, &bi, &bj);
     const int r0 = bi * B, c0 = bj * B;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // one element per thread
+    if (bi == bj) {
+        // the block's diagonal entries of d, all by warp 0 (a float64
+        // instruction costs its scheduler the same for one lane as for 32,
+        // so one entry in each of 32 warps would cost 32 times as much)
+        if (threadIdx.x < B) {
+            const int r = r0 + threadIdx.x;
+            double dr = 0.0;
+            if (r < M) {
+                if (loglam != nullptr) {
+                    dr = noise_diag_entry(sh, loglam, log_sigma2, r);
+                    dout[r] = dr;
+                } else if (d != nullptr) {
+                    dr = d[r];
+                }
+            }
+            sd[threadIdx.x] = dr;
+        }
+        __syncthreads();
+    }
     const int T = Mpad / TT;
     const int64_t sstride = (int64_t)(T * (T + 1) / 2) * TT * TT;
     auto add2 = [](float& hi, float& lo, float v) {  // hi + v = s + e exactly; lo collects e
@@ -94,8 +131,9 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __r
             }
             const int e = colexp[r] + colexp[c] - 14;  // |e| well inside float64's exponent range
             v = ((double)hi + (double)lo) * __hiloint2double((e + 1023) << 20, 0);
-            if (r == c && d != nullptr) v += d[r];
+            if (r == c) v += sd[ty];
             A[(int64_t)r * M + c] = v;
+            if (Lc != nullptr) Lc[(int64_t)r * M + c] = v;
         }
         t[ty][tx] = v;
     }
@@ -123,11 +161,7 @@ __global__ void noise_diag_kernel(GpShape s, const double* __restrict__ loglam, 
                                   double* __restrict__ d) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= s.M) return;
-    double ll = 0.0;
-    for (int j = 0; j < s.p; ++j) ll += loglam[(m / s.stride[j]) % s.n];
-    const double logd = log_sigma2 - ll;
-    const double lclamp = 460.51701859880913680;  // log(1e200)
-    d[m] = logd >= lclamp ? 1e200 : exp(logd);
+    d[m] = noise_diag_entry(s, loglam, log_sigma2, m);
 }
 
 }  // namespace
@@ -141,11 +175,22 @@ void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, i
 
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, const AssembleExtra* ex) {
     (void)tile;  // the tensor-core Gram's tiles are 128 x 128
     const int nb = (M + 31) / 32;
-    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(Gpart, bpart, colexp, nsplit, Mpad,
-                                                                              M, d, A, b);
+    GpShape sh{};
+    const double* loglam = nullptr;
+    double lsig = 0.0;
+    double *dout = nullptr, *Lc = nullptr;
+    if (ex != nullptr) {
+        sh = *ex->shape;
+        loglam = ex->loglam;
+        lsig = log(ex->sigma2);
+        dout = ex->dout;
+        Lc = ex->L;
+    }
+    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
+        Gpart, bpart, colexp, nsplit, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

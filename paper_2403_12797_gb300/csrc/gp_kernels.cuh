@@ -51,10 +51,20 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
 // b = sum_s bpart[s]. d may be NULL (plain Gram).
 void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, int tile, int Mpad,
                          int M, const double* d, double* A, double* b, cudaStream_t stream);
+// Optional extras of the fit's assembly: the noise diagonal d_m computed in
+// the kernel (from loglam and sigma2, stored to dout and added to A's
+// diagonal; d is then ignored), and a copy of A's lower triangle written to L.
+struct AssembleExtra {
+    const GpShape* shape;
+    const double* loglam;
+    double sigma2;
+    double* dout;
+    double* L;
+};
 // float-pair partials of the tensor-core Gram: A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const AssembleExtra* ex = nullptr);
 // d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
                        cudaStream_t stream);
