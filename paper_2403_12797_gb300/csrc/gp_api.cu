@@ -437,14 +437,9 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
     }
     if (e == cudaSuccess) {
         GpProf pf("solve_refine", stream);
+        // a mixed fit's solve also packs the predict operand (W and c)
         e = launch_solve_refine(A, h->W, fwork, fp32_inverse, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st,
-                                stream);
-    }
-    if (e == cudaSuccess && prec != GP_PREC_FP64) {
-        GpProf pf("pack_w", stream);
-        launch_pack_w_bf16x3(tri_inverse_fp32_w(fwork, M), h->c, M, h->Wpack, stream);
-        gp_note_launches(1);
-        e = cudaGetLastError();
+                                stream, prec != GP_PREC_FP64 ? h->Wpack : nullptr);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "factorisation or solve launch");
 }

@@ -919,12 +919,17 @@ __global__ void __launch_bounds__(NT) trinv_rec_kernel(const double* __restrict_
 //   Wv   t_i = sum_{j <= i} W_ij v_j
 //   WTt  c_j (+)= sum_{i >= j} (W^T)_ji t_i     (W^T from the inverse)
 //   res  r_i = b_i - sum_j A_ij c_j              (float64)
+//
+// A mixed fit (Wpack != NULL) also leaves the predict kernel's operands: the
+// packed bf16 hi/lo blocks of the float32 W, written in the first phase (W is
+// complete before this launch), and c in float32 after them, written with
+// the final c.
 template <typename T>
 __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict__ A, const T* __restrict__ W,
                                                         const T* __restrict__ WT, const double* __restrict__ b,
                                                         double* __restrict__ c, T* __restrict__ t,
                                                         T* __restrict__ r, int M, int refine, GpStatus* st,
-                                                        GridBar* gb) {
+                                                        GridBar* gb, uint8_t* __restrict__ Wpack, int Mpad) {
     if (status_code(st) != 0) return;  // set before this launch: every CTA leaves
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x;
@@ -951,17 +956,32 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
             if (lane == 0) t[i] = s;
         }
     };
-    auto wt_apply = [&](bool accumulate) {
+    float* cf = Wpack != nullptr ? reinterpret_cast<float*>(Wpack + (size_t)4 * Mpad * Mpad) : nullptr;
+    auto wt_apply = [&](bool accumulate, bool last) {
         for (int j = blockIdx.x * (NT / 32) + warp; j < M; j += G * (NT / 32)) {
             const T s = dotrow(WT + (int64_t)j * M, t, j, M);
-            if (lane == 0) c[j] = (accumulate ? c[j] : 0.0) + (double)s;
+            if (lane == 0) {
+                const double cj = (accumulate ? c[j] : 0.0) + (double)s;
+                c[j] = cj;
+                if constexpr (sizeof(T) == 4) {
+                    if (last && cf != nullptr) cf[j] = (float)cj;
+                }
+            }
         }
     };
     for (int i = blockIdx.x * NT + tid; i < M; i += G * NT) r[i] = (T)b[i];
+    if constexpr (sizeof(T) == 4) {
+        if (Wpack != nullptr) {
+            const int64_t items = pack_w_items(Mpad);
+            for (int64_t i = (int64_t)blockIdx.x * NT + tid; i < items; i += (int64_t)G * NT)
+                pack_w_item(W, M, Mpad, Wpack, i);
+            for (int i = M + blockIdx.x * NT + tid; i < Mpad; i += G * NT) cf[i] = 0.f;
+        }
+    }
     if (!grid_sync(gb, st)) return;
     w_apply(r);
     if (!grid_sync(gb, st)) return;
-    wt_apply(false);
+    wt_apply(false, refine == 0);
     for (int it = 0; it < refine; ++it) {
         if (!grid_sync(gb, st)) return;
         for (int i = blockIdx.x * (NT / 32) + warp; i < M; i += G * (NT / 32)) {
@@ -984,7 +1004,7 @@ __global__ void __launch_bounds__(NT) solve_coop_kernel(const double* __restrict
         if (!grid_sync(gb, st)) return;
         w_apply(r);
         if (!grid_sync(gb, st)) return;
-        wt_apply(true);
+        wt_apply(true, it + 1 == refine);
     }
 }
 
@@ -1085,16 +1105,15 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
     return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
 }
 
-const float* tri_inverse_fp32_w(const void* work, int M) {
-    return (const float*)((const char*)work + CHOL_RSD_OFFSET) + (size_t)M * M;
-}
-
 size_t solve_refine_work_elems(int M) {
     return 32 + 2 * (size_t)M;  // 256 bytes unused (alignment), t, r
 }
 
 cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
-                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream) {
+                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream,
+                                uint16_t* Wpack) {
+    uint8_t* wp = fp32 ? reinterpret_cast<uint8_t*>(Wpack) : nullptr;
+    int Mpad = (int)gp_round_up(M, PREDTC_KB);
     int dev = 0;
     cudaGetDevice(&dev);
     GridBar* gb = (GridBar*)((char*)const_cast<void*>(fwork) + SOLVE_BAR_OFFSET);  // zeroed by launch_cholesky
@@ -1109,7 +1128,7 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const void* fw
         float* r = t + M;
         const void* k = (const void*)solve_coop_kernel<float>;
         dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-        void* args[] = {(void*)&A, (void*)&Wf, (void*)&WTf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
+        void* args[] = {(void*)&A, (void*)&Wf, (void*)&WTf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb, &wp, &Mpad};
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
     const double* WTd = (const double*)fbase;
@@ -1117,6 +1136,6 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const void* fw
     double* r = t + M;
     const void* k = (const void*)solve_coop_kernel<double>;
     dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
-    void* args[] = {(void*)&A, (void*)&W, (void*)&WTd, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb};
+    void* args[] = {(void*)&A, (void*)&W, (void*)&WTd, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb, &wp, &Mpad};
     return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }

@@ -85,17 +85,19 @@ size_t factor_work_bytes(int M, bool fp32_inverse);
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream);
 // W = L^{-1} (lower, M x M row-major, upper part zeroed), one cooperative
 // launch: in float64 into W (fp32 = false), or in float32 into the workspace
-// (fp32 = true; W is not written and may be NULL), where
-// tri_inverse_fp32_w(work, M) finds it, and the solve its transpose.
+// (fp32 = true; W is not written and may be NULL), where the solve finds it
+// and its transpose.
 cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
                                cudaStream_t stream);
-const float* tri_inverse_fp32_w(const void* work, int M);
 // c = A^{-1} b through W = L^{-1}: c = W^T (W b), then `refine` steps of
 // c += W^T W (b - A c) with the float64 residual, one cooperative launch.
 // fp32: the products use the float32 W that launch_tri_inverse left in
 // fwork (its workspace); otherwise W itself.
+// fp32 with Wpack != NULL: also the predict kernel's operands into Wpack
+// (predtc_wpack_bytes), from the float32 W and the final c.
 cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
-                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream);
+                                double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream,
+                                uint16_t* Wpack = nullptr);
 size_t solve_refine_work_elems(int M);
 
 // ---- float64 predict (gp_predict64.cu) -----------------------------------------
@@ -112,8 +114,9 @@ constexpr int PREDTC_BK = 32;   // Phi_* columns per pipeline stage (MMA K chunk
 constexpr int PREDTC_KB = 128;  // rows of W per MMA (MMA N)
 constexpr int PREDTC_SUPER = 4; // MMA N-blocks held in TMEM at once (4 x 128 = 512 columns)
 size_t predtc_wpack_bytes(int M);
-// Pack W = L^{-1} (float32) and c into the predict kernel's operands: bf16 hi/lo blocks of W, then c in float32.
-void launch_pack_w_bf16x3(const float* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream);
+// The predict kernel's operands (predtc_wpack_bytes): bf16 hi/lo blocks of
+// W = L^{-1} (pack_w_item in gp_tc.cuh), then c in float32 (Mpad floats, zero
+// beyond M); written by the solve (launch_solve_refine) of a mixed fit.
 size_t predtc_smem_bytes(const GpShape& s);
 // Chunk table of the predict kernel (ints): built once per fitted model.
 size_t predtc_cinfo_ints(const GpShape& s);

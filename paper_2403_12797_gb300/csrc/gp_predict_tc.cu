@@ -338,41 +338,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// W (M x M float32, lower) -> packed bf16 hi/lo blocks: for chunk c (32
-// columns m) and block b (128 rows k), hi then lo, each 128 x 32 in the
-// K-major core-matrix layout of the MMA's B operand. Thread idx < Mpad also
-// writes the float32 copy of c (zero beyond M) that follows the blocks.
-__global__ void pack_w_kernel(const float* __restrict__ W, const double* __restrict__ cvec, int M,
-                              int Mpad, uint8_t* __restrict__ out) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int KBt = Mpad / KB;
-    const int nch = Mpad / BK;
-    const int64_t total = (int64_t)nch * KBt * KB * (BK / 8);
-    if (idx < Mpad) {
-        float* cf = reinterpret_cast<float*>(out + (size_t)4 * Mpad * Mpad);
-        cf[idx] = idx < M ? (float)cvec[idx] : 0.f;
-    }
-    if (idx >= total) return;
-    const int g = (int)(idx % (BK / 8));
-    const int r = (int)((idx / (BK / 8)) % KB);
-    const int b = (int)((idx / ((BK / 8) * KB)) % KBt);
-    const int c = (int)(idx / ((int64_t)(BK / 8) * KB * KBt));
-    const int k = b * KB + r;
-    float v[8];
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-        const int m = c * BK + g * 8 + kk;
-        v[kk] = (k < M && m < M && m <= k) ? W[(int64_t)k * M + m] : 0.f;
-    }
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-    uint8_t* blk = out + ((size_t)c * KBt + b) * 2 * WB_BYTES;
-    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
-    *reinterpret_cast<uint4*>(blk + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(blk + WB_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 }  // namespace
 
 // packed hi/lo blocks of W (4 Mpad^2 bytes), then c in float32 (Mpad floats)
@@ -381,11 +346,6 @@ size_t predtc_wpack_bytes(int M) {
     return 4 * Mpad * Mpad + 4 * Mpad;
 }
 
-void launch_pack_w_bf16x3(const float* W, const double* c, int M, uint16_t* Wpack, cudaStream_t stream) {
-    const int Mpad = (int)gp_round_up(M, KB);
-    const int64_t total = (int64_t)(Mpad / BK) * (Mpad / KB) * KB * (BK / 8);
-    pack_w_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(W, c, M, Mpad, (uint8_t*)Wpack);
-}
 
 namespace {
 int predtc_maxrows(const GpShape& s) { return gp_max_window_rows(s, BK); }

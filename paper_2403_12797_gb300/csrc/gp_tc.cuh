@@ -280,3 +280,37 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
     hi = *reinterpret_cast<uint32_t*>(&h);
     lo = *reinterpret_cast<uint32_t*>(&l);
 }
+
+// One item of the predict kernel's W operand (W = L^-1, M x M float32, lower
+// triangle): for chunk c (32 columns m) and block b (128 rows k) of W, row r
+// of the block and 8-column group g of the chunk, the bf16 hi and lo parts of
+// W[k][8g .. 8g+7] (zero above the diagonal and beyond M), stored in the
+// K-major core-matrix layout of the MMA's B operand (hi block, then lo
+// block, each 128 x 32). Items idx = 0 .. pack_w_items(Mpad) - 1.
+__host__ __device__ __forceinline__ int64_t pack_w_items(int Mpad) {
+    return (int64_t)(Mpad / 32) * (Mpad / 128) * 128 * (32 / 8);
+}
+__device__ __forceinline__ void pack_w_item(const float* __restrict__ W, int M, int Mpad, uint8_t* __restrict__ out,
+                                            int64_t idx) {
+    constexpr int KB = 128, BK = 32;
+    constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128, WB_BYTES = KB * BK * 2;
+    const int KBt = Mpad / KB;
+    const int g = (int)(idx % (BK / 8));
+    const int r = (int)((idx / (BK / 8)) % KB);
+    const int b = (int)((idx / ((BK / 8) * KB)) % KBt);
+    const int c = (int)(idx / ((int64_t)(BK / 8) * KB * KBt));
+    const int k = b * KB + r;
+    float v[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const int m = c * BK + g * 8 + kk;
+        v[kk] = (k < M && m < M && m <= k) ? W[(int64_t)k * M + m] : 0.f;
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
+    uint8_t* blk = out + ((size_t)c * KBt + b) * 2 * WB_BYTES;
+    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
+    *reinterpret_cast<uint4*>(blk + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(blk + WB_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
