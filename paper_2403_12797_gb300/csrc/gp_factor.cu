@@ -352,25 +352,31 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
         if (rest == 0) break;
         // ---- B: panel rows, x L_kk^T = a (lane j owns x_j). With s_j = 1 / L_jj,
         // x_j = a_j s_j - sum_{l<j} x_l (L_jl s_j): lane j holds the scaled row of
-        // L_kk in registers, and each step is one shuffle and one FMA.
+        // L_kk in registers, and each step is one shuffle and one FMA. The rows
+        // L_jl s_j are scaled once per CTA as they are loaded (a float64
+        // instruction holds its scheduler's float64 pipe for 64 cycles, so
+        // forming them in every warp cost more than the solves).
         if ((int)blockIdx.x < rest) {
-            double v[CB * CB / NT];
+            double v[CB * CB / NT], sv[CB * CB / NT];
 #pragma unroll
             for (int q = 0; q < CB * CB / NT; ++q) {
                 const int e = tid + q * NT, i = e / CB, j = e % CB;
                 v[q] = (i < w && j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
+                sv[q] = i < w ? rsd[kb + i] : 0.0;
             }
 #pragma unroll
             for (int q = 0; q < CB * CB / NT; ++q) {
                 const int e = tid + q * NT;
-                a[e / CB][e % CB] = v[q];
+                a[e / CB][e % CB] = v[q] * sv[q];
             }
             if (tid < CB) rdiag[tid] = tid < w ? rsd[kb + tid] : 0.0;
             __syncthreads();
             const double rd = rdiag[lane];
             double ls[CB];
+            if ((int)blockIdx.x + G * warp < rest) {
 #pragma unroll
-            for (int l = 0; l < CB; ++l) ls[l] = a[lane][l] * rd;
+                for (int l = 0; l < CB; ++l) ls[l] = a[lane][l];
+            }
             for (int rr = blockIdx.x + G * warp; rr < rest; rr += G * (NT / 32)) {
                 double* row = L + (int64_t)(kb + w + rr) * M + kb;
                 double acc = lane < w ? row[lane] * rd : 0.0;
