@@ -153,6 +153,53 @@ void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, i
     *nsplit = (int)((Npad + best_r - 1) / best_r);
 }
 
+// Row splits of the tensor-core Gram per pair class (SyrkSplit). When all
+// tile pairs fit in one wave of target_ctas CTAs, each class gets its own
+// split count: starting from one split each, the class whose CTAs would take
+// longest -- (blocks per split + 1) x its cost per block -- gets one more
+// split while the whole grid still fits in the wave. Costs per 1024-row block
+// relative to a diagonal pair, measured per CTA on GB300 (p = 2, n = 20):
+// 1.24 for the pairs (I, 0), which also form Phi^T y, and 1.17 for the other
+// off-diagonal pairs; a diagonal pair generates one operand tile instead of
+// two. Otherwise every class takes the uniform choice of choose_splits.
+void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp) {
+    if (target_ctas < 1) target_ctas = 1;
+    const int npairs = T * (T + 1) / 2;
+    const int64_t npc[3] = {T, T - 1, (int64_t)(T - 1) * (T - 2) / 2};
+    if (npairs > target_ctas) {
+        int ns;
+        int64_t rps;
+        choose_splits(npairs, Npad, target_ctas, GP_TAB_BLOCK, &ns, &rps);
+        for (int c = 0; c < 3; ++c) {
+            sp->n[c] = ns;
+            sp->rows[c] = rps;
+        }
+        sp->smax = ns;
+        return;
+    }
+    const int64_t nb = (Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK;
+    const double w[3] = {1.0, 1.24, 1.17};
+    int64_t n[3] = {1, 1, 1};
+    auto cost = [&](int c) { return (double)((nb + n[c] - 1) / n[c] + 1) * w[c]; };
+    while (true) {
+        int cmax = -1;
+        for (int c = 0; c < 3; ++c)
+            if (npc[c] > 0 && (cmax < 0 || cost(c) > cost(cmax))) cmax = c;
+        if ((nb + n[cmax] - 1) / n[cmax] <= 1) break;  // one block per split already
+        int64_t ctas = 0;
+        for (int c = 0; c < 3; ++c) ctas += npc[c] * n[c];
+        if (ctas + npc[cmax] > target_ctas) break;
+        ++n[cmax];
+    }
+    sp->smax = 1;
+    for (int c = 0; c < 3; ++c) {
+        const int64_t blocks = (nb + n[c] - 1) / n[c];
+        sp->rows[c] = blocks * GP_TAB_BLOCK;
+        sp->n[c] = (int)((Npad + sp->rows[c] - 1) / sp->rows[c]);
+        if (npc[c] > 0 && sp->n[c] > sp->smax) sp->smax = sp->n[c];
+    }
+}
+
 int num_sms(int dev) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
@@ -211,11 +258,10 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         if ((rc = sc.get(&tabc, syrktc_table_floats(s)))) return rc;
         const int T = s.Mpad / SYRKTC_TM;
         const int npairs = T * (T + 1) / 2;
-        int nsplit;
-        int64_t rps;
-        choose_splits(npairs, s.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), GP_TAB_BLOCK, &nsplit, &rps);
-        if ((rc = sc.get(&Gpart, (size_t)nsplit * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
-        if ((rc = sc.get(&bpart, (size_t)nsplit * s.Mpad))) return rc;
+        SyrkSplit spl;
+        choose_splits_tc(T, s.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &spl);
+        if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
+        if ((rc = sc.get(&bpart, (size_t)spl.smax * s.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
         int* colexp;
         signed char* ebx;
@@ -230,14 +276,13 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tabc, tmaxb, tmax, nsplit, rps, Gpart, bpart, colexp, ebx,
-                                           st, stream);
+            cudaError_t e = launch_syrk_tc(s, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream);
             if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
             gp_note_launches(2);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_scaled(Gpart, bpart, colexp, nsplit, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream, ex);
+            launch_assemble_scaled(Gpart, bpart, colexp, spl, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
             if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }

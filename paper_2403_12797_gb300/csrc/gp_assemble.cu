@@ -76,7 +76,7 @@ __device__ __forceinline__ double noise_diag_entry(const GpShape& s, const doubl
 // written there (the Cholesky's input), which saves a separate copy.
 __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __restrict__ Gpart,
                                                               const double* __restrict__ bpart,
-                                                              const int* __restrict__ colexp, int nsplit,
+                                                              const int* __restrict__ colexp, SyrkSplit spl,
                                                               int Mpad, int M, const double* __restrict__ d,
                                                               double* __restrict__ A, double* __restrict__ b,
                                                               GpShape sh, const double* __restrict__ loglam,
@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __r
         if (r < M && c < M && c <= r) {
             const int I = r / TT, J = c / TT;
             const int64_t off = (int64_t)(I * (I + 1) / 2 + J) * TT * TT + (int64_t)(r % TT) * TT + (c % TT);
+            const int pc = syrk_pair_class(I, J);
+            const int nsplit = pc == 0 ? spl.n[0] : (pc == 1 ? spl.n[1] : spl.n[2]);  // this pair's splits
             float hi = 0.f, lo = 0.f;
             for (int sp = 0; sp < nsplit; ++sp) {
                 const float2 g = Gpart[off + sp * sstride];
@@ -151,7 +153,8 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __r
         const int col = c0 + threadIdx.x;
         if (col < M) {
             double bb = 0.0;
-            for (int sp = 0; sp < nsplit; ++sp) bb += bpart[(int64_t)sp * Mpad + col];
+            const int nsb = col / TT == 0 ? spl.n[0] : spl.n[1];  // splits of the pair (I, 0) that formed it
+            for (int sp = 0; sp < nsb; ++sp) bb += bpart[(int64_t)sp * Mpad + col];
             b[col] = bb;
         }
     }
@@ -173,7 +176,7 @@ void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, i
                                                       Mpad, M, d, A, b);
 }
 
-void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
+void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& spl,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex) {
     (void)tile;  // the tensor-core Gram's tiles are 128 x 128
@@ -190,7 +193,7 @@ void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int*
         Lc = ex->L;
     }
     assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
-        Gpart, bpart, colexp, nsplit, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
+        Gpart, bpart, colexp, spl, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

@@ -34,17 +34,29 @@ cudaError_t launch_syrk64(const GpShape& s, const double* tab, const double* ypa
                           int64_t rows_per_split, double* Gpart, double* bpart, cudaStream_t stream);
 
 // ---- bf16x3 tensor-core Gram (gp_syrk_tc.cu) ---------------------------------
+// Row splits of the tensor-core Gram per class of tile pair (I, J): 0 the
+// diagonal pairs, 1 the pairs (I, 0), I > 0 (which also form Phi^T y), 2 the
+// other off-diagonal pairs. The classes cost different amounts per row (a
+// diagonal pair generates one operand tile, the others two), so each gets its
+// own split count n[c] and rows per split rows[c] (a multiple of
+// GP_TAB_BLOCK). Pair (I, J) of class c has partial tiles for splits
+// 0 .. n[c] - 1; smax is the largest n[c].
+struct SyrkSplit {
+    int n[3];
+    int64_t rows[3];
+    int smax;
+};
+__host__ __device__ __forceinline__ int syrk_pair_class(int I, int J) { return I == J ? 0 : (J == 0 ? 1 : 2); }
 size_t syrktc_smem_bytes(const GpShape& s);
 // bytes of the per-block column exponents the launch needs (ebx argument)
 size_t syrktc_ebx_bytes(const GpShape& s);
 // Gpart holds column-scaled partial tiles as float pairs hi + lo (units
-// 2^(14 - E_m - E_m')),
-// colexp[m] = E_m (Mpad, written here), bpart the unscaled float64 Phi^T y
-// partials. rows_per_split must be a multiple of GP_TAB_BLOCK.
+// 2^(14 - E_m - E_m')) at (split * npairs + pair), colexp[m] = E_m (Mpad,
+// written here), bpart the unscaled float64 Phi^T y partials at
+// (split * Mpad + m), from the pairs (I, 0).
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
-                           const unsigned int* tmax, int nsplit, int64_t rows_per_split,
-                           float2* Gpart, double* bpart, int* colexp, signed char* ebx,
-                           GpStatus* st, cudaStream_t stream);
+                           const unsigned int* tmax, const SyrkSplit& sp, float2* Gpart, double* bpart,
+                           int* colexp, signed char* ebx, GpStatus* st, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);
@@ -62,7 +74,7 @@ struct AssembleExtra {
     double* L;
 };
 // float-pair partials of the tensor-core Gram: A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
-void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, int nsplit,
+void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex = nullptr);
 // d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)

@@ -281,7 +281,7 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
 template <int P, int H>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
-                   const int* __restrict__ colexp, int64_t rps, int npairs, int maxrows, int nst, int nwr,
+                   const int* __restrict__ colexp, SyrkSplit sp, int T, int maxrows, int nst, int nwr,
                    float2* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
@@ -291,15 +291,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     smem_tc_layout(maxrows, s.p, nst, nwr, H, base, &sm);
     using GM = StageGeom<H>;
 
-    const int q = blockIdx.x, split = blockIdx.y;
-    int I, J;
-    tri_pair(q, &I, &J);
+    // work item -> (pair class, pair, split): the class-0 items (diagonal
+    // pairs (k, k)) first, then class 1 ((k + 1, 0)), then class 2 (the
+    // strictly lower pairs below row 0 and right of column 0); within a class
+    // the pair index runs fastest
+    int I, J, split, cls;
+    {
+        int item = blockIdx.x;
+        const int n0 = T, n1 = T - 1, n2 = (T - 1) * (T - 2) / 2;
+        if (item < n0 * sp.n[0]) {
+            cls = 0;
+            I = J = item % n0;
+            split = item / n0;
+        } else if ((item -= n0 * sp.n[0]) < n1 * sp.n[1]) {
+            cls = 1;
+            I = item % n1 + 1;
+            J = 0;
+            split = item / n1;
+        } else {
+            item -= n1 * sp.n[1];
+            cls = 2;
+            int a, b;
+            tri_pair(item % n2, &a, &b);
+            I = a + 2;
+            J = b + 1;
+            split = item / n2;
+        }
+    }
+    const int npairs = T * (T + 1) / 2;
+    const int q = I * (I + 1) / 2 + J;
     const bool diag = (I == J);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
-    const int64_t r0 = (int64_t)split * rps;
-    int64_t r1 = r0 + rps;
+    const int64_t rows_c = cls == 0 ? sp.rows[0] : (cls == 1 ? sp.rows[1] : sp.rows[2]);  // no local copy
+    const int64_t r0 = (int64_t)split * rows_c;
+    int64_t r1 = r0 + rows_c;
     if (r1 > s.Npad) r1 = s.Npad;
     // pipeline stages of KS rows (split boundaries are multiples of 1024
     // rows and Npad of 128, so KS divides every split)
@@ -671,10 +698,11 @@ size_t syrktc_ebx_bytes(const GpShape& s) {
 }
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
-                           const unsigned int* tmax, int nsplit, int64_t rows_per_split,
-                           float2* Gpart, double* bpart, int* colexp, signed char* ebx,
-                           GpStatus* st, cudaStream_t stream) {
-    if (rows_per_split % GP_TAB_BLOCK != 0 || s.Npad % (2 * CW) != 0) return cudaErrorInvalidValue;
+                           const unsigned int* tmax, const SyrkSplit& sp, float2* Gpart, double* bpart,
+                           int* colexp, signed char* ebx, GpStatus* st, cudaStream_t stream) {
+    if (s.Npad % (2 * CW) != 0) return cudaErrorInvalidValue;
+    for (int c = 0; c < 3; ++c)
+        if (sp.n[c] < 1 || sp.rows[c] < GP_TAB_BLOCK || sp.rows[c] % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
     const int maxrows = gp_max_window_rows(s, TM);
     size_t smem = 0;
     int nwr = 0, H = 1;
@@ -684,13 +712,12 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
     colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
         s, tmaxb, tmax, nblk, colexp, ebx);
     const int T = s.Mpad / TM;
-    const int npairs = T * (T + 1) / 2;
-    dim3 grid((unsigned)npairs, (unsigned)nsplit);
+    const int64_t items = (int64_t)T * sp.n[0] + (int64_t)(T - 1) * sp.n[1] + (int64_t)(T - 1) * (T - 2) / 2 * sp.n[2];
+    dim3 grid((unsigned)items);
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = gp_allow_max_smem((const void*)kern);
         if (e != cudaSuccess) return e;
-        kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, rows_per_split, npairs, maxrows, nst,
-                                               nwr, Gpart, bpart, st);
+        kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, Gpart, bpart, st);
         return cudaGetLastError();
     };
     if (H == 2) {
