@@ -22,6 +22,37 @@ struct GpStatus {
     int64_t detail;          // pivot column, timeout site, ...
 };
 
+// float64 -> float32, rounded to nearest even, in integer arithmetic: on
+// GB300 the conversion instruction runs on the float64 pipe (64 cycles per
+// warp instruction per scheduler), integer operations do not. A normal
+// result takes the top 23 mantissa bits plus the rounding of the 29 below
+// (a carry moves into the exponent, and to infinity at the top); tiny
+// results become subnormal or zero, large ones infinity, NaN stays NaN.
+__device__ __forceinline__ float gp_d2f_rn(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu, sgn = hi & 0x80000000u;
+    if (e - 897u < 254u || e == 0u) {  // float exponent 1 .. 254 before rounding, or zero
+        const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rem = lo & 0x1FFFFFFFu;
+        const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+        return __uint_as_float(e == 0u ? sgn : sgn | ((((e - 896u) << 23) | m) + up));
+    }
+    if (e == 0x7FFu) return __uint_as_float(sgn | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x00400000u : 0u));
+    if (e > 1150u) return __uint_as_float(sgn | 0x7F800000u);
+    // |x| < 2^-126: q = round(x 2^149) = round(sig 2^(e - 926)), sig with its hidden bit
+    const int sh = 926 - (int)e;
+    if (e == 0u || sh > 63) return __uint_as_float(sgn);
+    const uint64_t sig = (1ull << 52) | ((uint64_t)(hi & 0xFFFFFu) << 32) | lo;
+    uint64_t q = sig >> sh;
+    const uint64_t rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    return __uint_as_float(sgn | (uint32_t)q);
+}
+// x is finite (neither infinite nor NaN), from its exponent bits: the
+// float64 comparison would take the float64 pipe
+__device__ __forceinline__ bool gp_isfinite_bits(double x) {
+    return ((__double2hiint(x) >> 20) & 0x7FF) != 0x7FF;
+}
+
 __device__ __forceinline__ void gp_set_status(GpStatus* st, int code, int64_t detail) {
     // first error wins
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;

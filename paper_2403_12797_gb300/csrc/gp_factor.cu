@@ -463,32 +463,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
 // phases, so an M x M inverse takes 2 ceil(log2(M / LB)) + 1 phases whose
 // tiles run side by side. Every phase also stores the transposes of the
 // blocks it completes, so W^T is ready when the last phase ends.
-// float64 -> float32, rounded to nearest even, in integer arithmetic: on
-// GB300 the conversion instruction runs on the float64 pipe (64 cycles per
-// warp instruction per scheduler), integer operations do not. A normal
-// result takes the top 23 mantissa bits plus the rounding of the 29 below
-// (a carry moves into the exponent, and to infinity at the top); tiny
-// results become subnormal or zero, large ones infinity, NaN stays NaN.
-__device__ __forceinline__ float d2f_rn(double x) {
-    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const uint32_t e = (hi >> 20) & 0x7FFu, sgn = hi & 0x80000000u;
-    if (e - 897u < 254u || e == 0u) {  // float exponent 1 .. 254 before rounding, or zero
-        const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rem = lo & 0x1FFFFFFFu;
-        const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
-        return __uint_as_float(e == 0u ? sgn : sgn | ((((e - 896u) << 23) | m) + up));
-    }
-    if (e == 0x7FFu) return __uint_as_float(sgn | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x00400000u : 0u));
-    if (e > 1150u) return __uint_as_float(sgn | 0x7F800000u);
-    // |x| < 2^-126: q = round(x 2^149) = round(sig 2^(e - 926)), sig with its hidden bit
-    const int sh = 926 - (int)e;
-    if (e == 0u || sh > 63) return __uint_as_float(sgn);
-    const uint64_t sig = (1ull << 52) | ((uint64_t)(hi & 0xFFFFFu) << 32) | lo;
-    uint64_t q = sig >> sh;
-    const uint64_t rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
-    return __uint_as_float(sgn | (uint32_t)q);
-}
-__device__ __forceinline__ float to_t(double x, float*) { return d2f_rn(x); }
+__device__ __forceinline__ float to_t(double x, float*) { return gp_d2f_rn(x); }
 __device__ __forceinline__ double to_t(double x, double*) { return x; }
 
 template <typename T>

@@ -33,10 +33,18 @@ __device__ __forceinline__ float gp_sqrt<float>(float v) { return sqrtf(v); }
 template <>
 __device__ __forceinline__ double gp_sqrt<double>(double v) { return sqrt(v); }
 
+// float64 -> T without the float64 pipe (T = float: integer rounding)
+__device__ __forceinline__ float to_tab(double x, float*) { return gp_d2f_rn(x); }
+__device__ __forceinline__ double to_tab(double x, double*) { return x; }
+
+// abT, sbT, d2T: alpha_beta, sqrt_beta and delta2 of s rounded to T on the
+// host (on GB300 the conversion instruction, like every float64 operation,
+// holds its scheduler's float64 pipe for 64 cycles a warp).
 template <typename T>
 __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double* __restrict__ X,
                                                          const double* __restrict__ y,
-                                                         T* __restrict__ tab, GpStatus* st) {
+                                                         T* __restrict__ tab, GpStatus* st, T abT, T sbT,
+                                                         T d2T) {
     // recurrence coefficients sqrt(2/(k+1)), sqrt(k/(k+1)), once per block
     extern __shared__ __align__(16) unsigned char coef_raw[];
     T* ca = reinterpret_cast<T*>(coef_raw);
@@ -58,14 +66,14 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
         return;
     }
     const double xd = X[i * s.p + j];
-    if (!isfinite(xd) || (j == 0 && y != nullptr && !isfinite(y[i]))) {
+    if (!gp_isfinite_bits(xd) || (j == 0 && y != nullptr && !gp_isfinite_bits(y[i]))) {
         gp_set_status(st, GP_EINVAL, i);
         for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
         return;
     }
-    const T x = (T)xd;
-    const T t = (T)s.alpha_beta * x;
-    T q0 = (T)s.sqrt_beta * gp_exp<T>(-(T)s.delta2 * x * x);
+    const T x = to_tab(xd, (T*)nullptr);
+    const T t = abT * x;
+    T q0 = sbT * gp_exp<T>(-d2T * x * x);
     out[0] = q0;
     if (s.n == 1) return;
     T q1 = gp_sqrt<T>(T(2)) * t * q0;
@@ -91,7 +99,8 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
 __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, const double* __restrict__ X,
                                                                  const double* __restrict__ y,
                                                                  float* __restrict__ tab,
-                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st) {
+                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st,
+                                                                 float abf, float sbf, float d2f) {
     constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
     extern __shared__ __align__(16) unsigned char coef_raw[];
     float* ca = reinterpret_cast<float*>(coef_raw);
@@ -120,12 +129,12 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     double xd = 0.0;
     if (!zero) {
         xd = X[i * s.p + j];
-        if (!isfinite(xd) || (j == 0 && y != nullptr && !isfinite(y[i]))) {
+        if (!gp_isfinite_bits(xd) || (j == 0 && y != nullptr && !gp_isfinite_bits(y[i]))) {
             gp_set_status(st, GP_EINVAL, i);
             zero = true;
         }
     }
-    if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : (float)y[i];
+    if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : gp_d2f_rn(y[i]);
     // every lane runs the whole recurrence (rows beyond N or with bad input
     // are zero from q0 on), so the warp reductions see all 32 lanes
     // (|v| as bits orders like |v|, so one integer warp reduction gives the maximum)
@@ -134,9 +143,9 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
         const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v)));
         if ((threadIdx.x & 31) == 0) atomicMax(bmax + k, m);
     };
-    const float x = zero ? 0.f : (float)xd;
-    const float t = (float)s.alpha_beta * x;
-    float q0 = zero ? 0.f : (float)s.sqrt_beta * expf(-(float)s.delta2 * x * x);
+    const float x = zero ? 0.f : gp_d2f_rn(xd);
+    const float t = abf * x;
+    float q0 = zero ? 0.f : sbf * expf(-d2f * x * x);
     emit(0, q0);
     if (s.n == 1) return;
     float q1 = sqrtf(2.f) * t * q0;
@@ -178,13 +187,15 @@ size_t coef_bytes(const GpShape& s) {
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<double><<<grid, 256, coef_bytes<double>(s), stream>>>(s, X, y, tab, st);
+    eig_tables_kernel<double><<<grid, 256, coef_bytes<double>(s), stream>>>(s, X, y, tab, st, s.alpha_beta,
+                                                                            s.sqrt_beta, s.delta2);
 }
 
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tab, st);
+    eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(
+        s, X, y, tab, st, (float)s.alpha_beta, (float)s.sqrt_beta, (float)s.delta2);
 }
 
 size_t syrktc_table_floats(const GpShape& s) {
@@ -197,6 +208,7 @@ void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* 
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
     cudaMemsetAsync(tmaxb, 0, sizeof(unsigned int) * (size_t)rows * nblk, stream);
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, tmaxb, st);
+    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(
+        s, X, y, tabc, tmaxb, st, (float)s.alpha_beta, (float)s.sqrt_beta, (float)s.delta2);
     table_gmax_kernel<<<(unsigned)rows, 256, 0, stream>>>(tmaxb, rows, nblk, tmax);
 }
