@@ -328,6 +328,13 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k);
  * first attempt (k = 0 disarms), to exercise the float64 escalation. */
 GPFAGP_API void gp_debug_force_escalation(int k);
 
+/* Test hook, host only: the mixed Gram's row-split plan for T 128-column tile
+ * rows, Npad padded rows and a budget of target_ctas CTAs. out[0..2]: split
+ * counts of the pair classes (0 diagonal, 1 pairs (I, 0), 2 other pairs),
+ * out[3..5]: their rows per split, out[6]: the CTAs of the launch. Returns
+ * GP_OK, or GP_EINVAL for T < 1, Npad < 1, target_ctas < 1 or out NULL. */
+GPFAGP_API int gp_debug_gram_splits(int T, int64_t Npad, int target_ctas, int64_t* out);
+
 /* Library build tag (static string). */
 GPFAGP_API const char* gp_version(void);
 

@@ -96,6 +96,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_server_reset_stats": (i, [vp]),
         "gp_debug_fail_alloc_after": (None, [i]),
         "gp_debug_force_escalation": (None, [i]),
+        "gp_debug_gram_splits": (i, [i, i64, i, C.POINTER(i64)]),
         "gp_model_flags": (i, [vp]),
         "gp_version": (C.c_char_p, []),
     }
@@ -347,6 +348,14 @@ def predict_batch(reqs: Sequence[Tuple], stream=None):
         import torch
         st = torch.cuda.current_stream().cuda_stream
     _check(lib().gp_predict_batch(cnt, args, st), "gp_predict_batch")
+
+
+def debug_gram_splits(T: int, Npad: int, target_ctas: int):
+    """The mixed Gram's row-split plan (host only): ([splits per pair class],
+    [rows per split per class], CTAs)."""
+    out = (C.c_int64 * 7)()
+    _check(lib().gp_debug_gram_splits(int(T), int(Npad), int(target_ctas), out), "gp_debug_gram_splits")
+    return list(out[0:3]), list(out[3:6]), int(out[6])
 
 
 def debug_force_escalation(k: int):

@@ -702,6 +702,21 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k) { g_fail_after.store(k > 0 ? k 
 
 GPFAGP_API void gp_debug_force_escalation(int k) { g_force_escalate.store(k > 0 ? k : 0); }
 
+GPFAGP_API int gp_debug_gram_splits(int T, int64_t Npad, int target_ctas, int64_t* out) {
+    if (T < 1 || Npad < 1 || target_ctas < 1 || !out) return set_err(GP_EINVAL, 0);
+    SyrkSplit sp;
+    choose_splits_tc(T, Npad, target_ctas, &sp);
+    const int64_t npc[3] = {T, T - 1, (int64_t)(T - 1) * (T - 2) / 2};
+    int64_t ctas = 0;
+    for (int c = 0; c < 3; ++c) {
+        out[c] = sp.n[c];
+        out[3 + c] = sp.rows[c];
+        ctas += npc[c] * sp.n[c];
+    }
+    out[6] = ctas;
+    return GP_OK;
+}
+
 GPFAGP_API int gp_model_flags(const gp_model* h) { return h ? h->flags : 0; }
 
 GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
