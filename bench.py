@@ -236,7 +236,7 @@ def run_ours(args):
     L.gp_profile_enable(0)
     groups = {}
     for g in ("eig_tables", "syrk_tc", "syrk64", "assemble", "cholesky", "tri_inverse",
-              "solve_refine", "pack_w", "predict_tc", "predict64"):
+              "solve_refine", "predict_tc", "predict64"):
         n_, ms_ = C.c_int64(), C.c_double()
         if L.gp_profile_query(g.encode(), C.byref(n_), C.byref(ms_)) == 0:
             groups[g] = {"launches": n_.value, "total_ms": ms_.value}

@@ -50,6 +50,9 @@
 // Every warp waits on mbarriers by itself (bounded, decided by a warp vote):
 // there is no CTA-wide barrier inside the pipeline. The block exponents E_m
 // per 1024-row block and the global ones come from a small kernel run first.
+// The grid is one CTA per (pair, split) work item, the rows split per class
+// of pair (SyrkSplit: diagonal pairs generate one operand tile and take
+// longer splits; the pairs (I, 0) also form b), so the classes end together.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
