@@ -227,7 +227,7 @@ typedef struct gp_fit_args {
  *     rounded to a power of two) by timing the batch's Gram steps on the
  *     device; the choice is cached for the process.
  *   - Every problem's fit is enqueued on one of up to 8 streams and the whole
- *     batch is captured into ONE CUDA graph and launched once; if the driver
+ *     batch is captured into ONE CUDA graph and launched once; if CUDA
  *     refuses to capture or instantiate it, the same launches run directly on
  *     the streams (gp_batch_info reports which).
  *   - All statuses are read back once at the end.

@@ -6,5 +6,5 @@ dimensions (Sec. 2.3). All computation runs in the CUDA kernels of
 ``libgpfagp.so`` (C ABI in ``include/gpfagp.h``); this package only
 marshals arguments.
 """
-from ._lib import (GPError, Model, fit, fit_batch, fit_north_star, fit_predict, gram, lib, predict_batch,  # noqa: F401
+from ._lib import (GPError, Model, fit, fit_batch, fit_plain, fit_predict, gram, lib, predict_batch,  # noqa: F401
                    strerror, version)

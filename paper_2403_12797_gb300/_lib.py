@@ -279,7 +279,7 @@ def fit_gram(G, b, N: int, p: int, n: int, eps: float, alpha: float, sigma2: flo
     return Model(out.value)
 
 
-def fit_north_star(X, y, n, eps, alpha, sigma2) -> Model:
+def fit_plain(X, y, n, eps, alpha, sigma2) -> Model:
     """The plain ``gp_fit`` entry point (host arrays, mixed precision, default stream)."""
     X, y, N, p, _ = _prep_xy(X, y)
     h = lib().gp_fit(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),

@@ -223,9 +223,9 @@ def test_predict_edge_sizes(prec):
     np.testing.assert_array_equal(mean_only, mean_full)
 
 
-def test_north_star_entry_point():
+def test_plain_gp_fit_entry_point():
     pr = W.workload1()
-    m = _lib.fit_north_star(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+    m = _lib.fit_plain(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
     mean, var = np.empty(pr.Ns), np.empty(pr.Ns)
     rc = _lib.lib().gp_predict(m._h, pr.Xs.ctypes.data, pr.Ns, mean.ctypes.data, var.ctypes.data)
     assert rc == _lib.GP_OK
