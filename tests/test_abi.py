@@ -69,6 +69,33 @@ def test_no_gpu_fails_loudly():
     assert rc == _lib.GP_ENODEV and not h
     with pytest.raises(_lib.GPError):
         _lib.fit(np.zeros((4, 1)), np.zeros(4), 3, 1.0, 1.0, 0.1)
+    with pytest.raises(_lib.GPError) as e:
+        _lib.fit_predict(np.zeros((4, 1)), np.zeros(4), 3, 1.0, 1.0, 0.1, np.zeros((2, 1)))
+    assert e.value.status == _lib.GP_ENODEV
+
+
+def _fit_predict_rc(N=10, p=1, n=3, Ns=4, xs=True, mean=True, out=True, **kw):
+    L = _lib.lib()
+    X, y = np.zeros((max(N, 1), p)), np.zeros(max(N, 1))
+    Xs, m, v = np.zeros((max(Ns, 1), p)), np.zeros(max(Ns, 1)), np.zeros(max(Ns, 1))
+    h = C.c_void_p()
+    rc = L.gp_fit_predict_ex(X.ctypes.data, y.ctypes.data, N, p, n, kw.get("eps", 1.0), 1.0, 0.1,
+                             kw.get("prec", 3), Xs.ctypes.data if xs else None, Ns,
+                             m.ctypes.data if mean else None, v.ctypes.data, None, 0,
+                             C.byref(h) if out else None)
+    return rc, h.value
+
+
+@pytest.mark.parametrize("kw", [dict(Ns=-1), dict(xs=False), dict(mean=False), dict(out=False),
+                                dict(N=0), dict(eps=0.0), dict(prec=7)])
+def test_fit_predict_arguments_rejected_on_host(kw):
+    rc, h = _fit_predict_rc(**kw)
+    assert rc == _lib.GP_EINVAL and not h
+
+
+def test_fit_predict_python_rejects_mismatched_inputs():
+    with pytest.raises(ValueError):  # Xs with another column count
+        _lib.fit_predict(np.zeros((4, 2)), np.zeros(4), 3, 1.0, 1.0, 0.1, np.zeros((2, 3)))
 
 
 # ---- the mixed Gram's row-split plan (host logic, no GPU)
