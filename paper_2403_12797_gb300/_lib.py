@@ -142,6 +142,9 @@ def _stream_of(a, stream) -> Optional[int]:
         return int(stream)
     if _is_torch(a):
         import torch
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if raw is not None:  # the raw handle, without building a Stream object
+            return int(raw(a.device.index if a.device.index is not None else torch.cuda.current_device()))
         return torch.cuda.current_stream(a.device).cuda_stream
     return None
 
@@ -170,8 +173,12 @@ def _prep_xy(X, y):
 class Model:
     """A fitted decomposed-kernel GP (owns a gp_model handle)."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, shape=None):
+        """shape: (M, p, n, prec) when the caller knows them, else read from the model."""
         self._h = C.c_void_p(handle)
+        if shape is not None:
+            self.M, self.p, self.n, self.prec = (int(v) for v in shape)
+            return
         M, p, n, prec = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
         _check(lib().gp_model_info(self._h, C.byref(M), C.byref(p), C.byref(n), C.byref(prec)),
                "gp_model_info")
@@ -252,7 +259,7 @@ def fit_predict(X, y, n: int, eps: float, alpha: float, sigma2: float, Xs, prec:
                                  C.c_void_p(_ptr(mean)), C.c_void_p(_ptr(vv)) if vv is not None else None,
                                  _stream_of(X, stream), dev, C.byref(out))
     _check(rc, "gp_fit_predict_ex")
-    return Model(out.value), mean, vv
+    return Model(out.value, (int(n) ** p, p, int(n), PREC[prec])), mean, vv
 
 
 def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "mixed",
