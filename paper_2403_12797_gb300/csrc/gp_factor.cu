@@ -4,17 +4,19 @@
 // sigma^2 Lambda-bar is symmetric positive definite, so it is factored by
 // Cholesky. On GB300 the float64 pipe retires about 2 FMAs per clock per SM,
 // so an M x M factorisation only runs at speed when every SM works on it and
-// no time is lost between launches. Both kernels here are therefore single
-// persistent cooperative launches (one CTA per SM) that walk the block
-// algorithm step by step, separated by grid barriers whose waits are bounded
-// (GP_ETIMEOUT after GP_WAIT_NS; nothing can hang):
+// no time is lost between launches. The three kernels here (Cholesky,
+// inverse, solve) are therefore single persistent cooperative launches (at
+// most one CTA per SM) that walk their block algorithms step by step,
+// separated by grid barriers whose waits are bounded (GP_ETIMEOUT after
+// GP_WAIT_NS; nothing can hang):
 //
 //   Cholesky (float64, right-looking, 32-column panels, look-ahead), per step k:
 //     B  one warp per row below the factored diagonal block solves
 //        x L_kk^T = a (lane j owns x_j);
-//     C  16 x 16 tiles of the trailing lower triangle subtract L_ik L_jk^T;
-//        CTA 0 updates the next diagonal block's tiles first and factors it
-//        (32 x 32, in shared memory) while the other CTAs finish C.
+//     C  16 helper CTAs update the next diagonal block and count themselves
+//        done; CTA 0 waits for them and factors that block (32 x 32, in
+//        shared memory) while the other CTAs update the rest of the trailing
+//        lower triangle in 16 x 16 tiles (subtracting L_ik L_jk^T).
 //   A non-positive or NaN pivot sets GP_ENOTPD (detail = column); every CTA
 //   sees it after the next barrier and returns.
 //
@@ -22,6 +24,9 @@
 //   or float64 arithmetic. The mixed-precision fit uses float32 here: W
 //   feeds the bf16 hi/lo variance contraction, and as the preconditioner of
 //   c = A^{-1} b its error is removed by the float64 iterative refinement.
+//
+//   c = A^{-1} b through W (below); the mixed fit's solve also packs the
+//   predict kernel's operand from W and the final c.
 #include "gp_kernels.cuh"
 #include "gp_tc.cuh"
 
