@@ -8,7 +8,9 @@
 //
 // The partial Gram tiles of the N splits are summed in split order (float64
 // for the float64 Gram, float pairs for the mixed one), so the result does
-// not depend on scheduling.
+// not depend on scheduling. The mixed fit's assembly also forms d itself
+// (one warp per diagonal block) and writes A's lower triangle into L, the
+// Cholesky's input, which saves a kernel and a copy per fit.
 #include "gp_kernels.cuh"
 
 #include <math.h>
