@@ -248,6 +248,29 @@ def predict(model: Dict[str, np.ndarray], Xs: np.ndarray, row_block: int = 16384
     return mean, var
 
 
+def log_marginal_likelihood(model: Dict[str, np.ndarray], y: np.ndarray) -> float:
+    """log p(y) of the truncated-kernel GP, K = Phi Lambda Phi^T (Eq. 7-9),
+    from the fitted M x M factors (the quantity that hyperparameter learning,
+    named as future work in Sec. 4, maximises).
+
+    The definition is log N(y; 0, K + sigma^2 I) (Eq. 1-2). By the matrix
+    determinant lemma, |K + sigma^2 I| = sigma^(2N) |Lambda| |A| / sigma^(2M),
+    and sigma^(2M) / |Lambda| = prod_m d_m with d_m = sigma^2 / lambda_m; by
+    the Woodbury identity (Eq. 10), y^T (K + sigma^2 I)^{-1} y =
+    (y^T y - b^T c) / sigma^2 with b = Phi^T y, c = A^{-1} b. So
+      log p(y) = -1/2 [ (y^T y - b^T c) / sigma^2 + N log sigma^2
+                        + log|A| - sum_m log d_m + N log 2 pi ],
+    log|A| = 2 sum_j log L_jj. Clamped d_m stand for eigenvalues below
+    1e-200 sigma^2, whose columns add nothing measurable to K.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    N = y.shape[0]
+    s2 = model["sigma2"]
+    quad = (y @ y - model["b"] @ model["c"]) / s2
+    logdet = N * math.log(s2) + 2.0 * np.sum(np.log(np.diag(model["L"]))) - np.sum(np.log(model["d"]))
+    return -0.5 * (quad + logdet + N * math.log(2.0 * math.pi))
+
+
 # --------------------------------------------------------------------------
 # Other routes to the same posterior (used to pin the M x M form)
 # --------------------------------------------------------------------------
@@ -285,6 +308,16 @@ def posterior_fagp_w(X, y, Xs, n, eps, rho, sigma2):
     mean = W @ y
     cov = Phis @ Lam @ Phis.T - W @ Phi @ Lam @ Phis.T
     return mean, np.diag(cov).copy()
+
+
+def log_marginal_likelihood_nxn(X, y, n, eps, rho, sigma2) -> float:
+    """log N(y; 0, K + sigma^2 I) with the N x N truncated kernel, by a dense
+    log-determinant and solve; only for small N."""
+    K = kernel_approx(X, X, n, eps, rho) + sigma2 * np.eye(np.atleast_2d(X).shape[0])
+    sign, logdet = np.linalg.slogdet(K)
+    assert sign > 0
+    y = np.asarray(y, dtype=np.float64)
+    return -0.5 * (y @ np.linalg.solve(K, y) + logdet + y.shape[0] * math.log(2.0 * math.pi))
 
 
 def posterior_exact_se(X, y, Xs, eps, sigma2):

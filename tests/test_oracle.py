@@ -315,3 +315,51 @@ def test_single_point_posterior_sensitivity_to_gram_errors():
     m = O.phi_matrix(pr.Xs, pr.n, pr.eps, pr.alpha) @ c
     amp = O.relerr(m, mo) / 1e-6
     assert 10 < amp < 40
+
+
+# ---- log marginal likelihood (hyperparameter learning, the paper's future work)
+
+@pytest.mark.parametrize("N,p,n", [(5, 1, 8), (40, 1, 6), (150, 2, 4), (60, 2, 9), (30, 1, 60)])
+def test_log_marginal_likelihood_equals_the_nxn_definition(N, p, n):
+    # includes M > N (the truncated kernel is then full rank in y's space) and
+    # n = 60, where the smallest eigenvalues hit the clamp of d
+    rng = np.random.default_rng(N + 10 * p + n)
+    X = rng.uniform(-1.0, 1.0, size=(N, p))
+    y = np.sin(2.0 * X).sum(axis=1) + 0.1 * rng.standard_normal(N)
+    eps, rho, s2 = 0.9, 1.1, 0.02
+    mdl = O.fit(X, y, n, eps, rho, s2)
+    got = O.log_marginal_likelihood(mdl, y)
+    ref = O.log_marginal_likelihood_nxn(X, y, n, eps, rho, s2)
+    assert abs(got - ref) <= 1e-9 * max(1.0, abs(ref)), (got, ref)
+
+
+def test_log_marginal_likelihood_rank_one_closed_form():
+    # p = 1, n = 1: K = lambda phi phi^T. |s2 I + lambda phi phi^T| =
+    # s2^N (1 + lambda |phi|^2 / s2), and by Sherman-Morrison
+    # y^T (s2 I + lambda phi phi^T)^{-1} y = (|y|^2 - lambda (phi.y)^2 / (s2 + lambda |phi|^2)) / s2
+    rng = np.random.default_rng(7)
+    N, eps, rho, s2 = 25, 1.3, 0.7, 0.05
+    X = rng.uniform(-1.0, 1.0, size=(N, 1))
+    y = rng.standard_normal(N)
+    phi = O.eigenfunctions_1d(X[:, 0], 1, eps, rho)[:, 0]
+    lam = float(np.exp(O.log_eigenvalues_1d(1, eps, rho)[0]))
+    pp, py = float(phi @ phi), float(phi @ y)
+    quad = (float(y @ y) - lam * py * py / (s2 + lam * pp)) / s2
+    logdet = N * math.log(s2) + math.log1p(lam * pp / s2)
+    ref = -0.5 * (quad + logdet + N * math.log(2.0 * math.pi))
+    got = O.log_marginal_likelihood(O.fit(X, y, 1, eps, rho, s2), y)
+    assert abs(got - ref) <= 1e-12 * abs(ref)
+
+
+def test_log_marginal_likelihood_peaks_near_the_generating_noise():
+    # data drawn from the truncated-kernel prior with noise variance 0.04:
+    # the likelihood over sigma^2 is largest near the generating value
+    rng = np.random.default_rng(11)
+    N, n, eps, rho = 400, 6, 1.0, 1.0
+    X = rng.uniform(-1.0, 1.0, size=(N, 1))
+    Phi = O.eigenfunctions_1d(X[:, 0], n, eps, rho)
+    lam = np.exp(O.log_eigenvalues_1d(n, eps, rho))
+    y = Phi @ (np.sqrt(lam) * rng.standard_normal(n)) + 0.2 * rng.standard_normal(N)
+    grid = [0.01, 0.02, 0.04, 0.08, 0.16]
+    vals = [O.log_marginal_likelihood(O.fit(X, y, n, eps, rho, s2), y) for s2 in grid]
+    assert int(np.argmax(vals)) == 2, vals
