@@ -137,6 +137,20 @@ GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, in
                                  const double* Xs, int64_t Ns, double* mean, double* var,
                                  void* cuda_stream, int dev_ptrs, gp_model** out);
 
+/* Log marginal likelihood of the fitted model: log p(y) = log N(y; 0,
+ * K + sigma^2 I) for the truncated kernel K = Phi Lambda Phi^T (Eq. 1-2,
+ * 7-9), the quantity hyperparameter learning maximises (Sec. 4, future
+ * work). From the fit's factors, by the matrix determinant lemma and the
+ * Woodbury identity (Eq. 10):
+ *   log p(y) = -1/2 [ (y^T y - b^T c) / sigma^2 + N log sigma^2
+ *                     + 2 sum_j log L_jj - sum_m log d_m + N log 2 pi ].
+ * y: the N training targets the model was fitted on (the model does not keep
+ * them), host or device memory per dev_ptrs. The sums run on the device in
+ * float64 in a fixed order; *out receives log p(y). Returns GP_OK, GP_EINVAL
+ * (NULL h, y or out, or N different from the fit's), or an error status. */
+GPFAGP_API int gp_model_log_marginal(const gp_model* h, const double* y, int64_t N, double* out,
+                                     void* cuda_stream, int dev_ptrs);
+
 /* Model shape and mode: any output pointer may be NULL. */
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
 

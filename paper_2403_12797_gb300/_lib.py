@@ -79,6 +79,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_fit_predict_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i64, vp, vp, vp, i, C.POINTER(vp)]),
         "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "gp_model_read": (i, [vp, i, vp]),
+        "gp_model_log_marginal": (i, [vp, vp, i64, C.POINTER(d), vp, i]),
         "gp_gram_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, vp, i]),
         "gp_gram_static": (i, [vp, vp, i64, i, i, d, d, vp, vp, vp]),
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
@@ -205,6 +206,22 @@ class Model:
                                  _stream_of(Xs, stream), dev)
         _check(rc, "gp_predict_ex")
         return mean, vv
+
+    def log_marginal(self, y, stream=None) -> float:
+        """log p(y) of the fitted truncated-kernel GP (y: the training
+        targets of the fit, host array or device tensor)."""
+        if _is_torch(y):
+            import torch
+            if y.dtype != torch.float64 or not y.is_cuda or not y.is_contiguous():
+                raise TypeError("device inputs must be contiguous float64 CUDA tensors")
+            dev = 1
+        else:
+            y = _host(y).reshape(-1)
+            dev = 0
+        out = C.c_double()
+        _check(lib().gp_model_log_marginal(self._h, C.c_void_p(_ptr(y)), int(y.shape[0]), C.byref(out),
+                                           _stream_of(y, stream), dev), "gp_model_log_marginal")
+        return float(out.value)
 
     def read(self, field: str) -> np.ndarray:
         """Host copy of a fitted quantity: 'L' (M x M), 'c', 'b' or 'd' (M)."""

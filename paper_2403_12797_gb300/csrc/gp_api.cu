@@ -1001,6 +1001,40 @@ GPFAGP_API int gp_predict(const gp_model* h, const double* Xs, int64_t Ns, doubl
 
 GPFAGP_API void gp_free(gp_model* h) { free_model(h); }
 
+GPFAGP_API int gp_model_log_marginal(const gp_model* h, const double* y, int64_t N, double* out,
+                                     void* cuda_stream, int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!h || !y || !out) return set_err(GP_EINVAL, 0);
+    if (N != h->shape.N) return set_err(GP_EINVAL, 1);
+    if ((rc = check_device(&dev))) return rc;
+    if (dev != h->device) return set_err(GP_EINVAL, 5);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const int M = h->shape.M;
+    const int nparts = lml_partial_count(num_sms(dev));
+    Scratch sc(stream);
+    double *part, *terms;
+    if ((rc = sc.get(&part, (size_t)4 * nparts))) return rc;
+    if ((rc = sc.get(&terms, 4))) return rc;
+    const double* yd = y;
+    if (!dev_ptrs) {
+        double* yy;
+        if ((rc = sc.get(&yy, (size_t)N))) return rc;
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        yd = yy;
+    }
+    launch_lml_terms(yd, N, h->L, h->b, h->c, h->d, M, nparts, part, terms, stream);
+    gp_note_launches(2);
+    double t[4];
+    cudaError_t e = cudaMemcpyAsync(t, terms, sizeof(t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_err(e, "log marginal likelihood");
+    const double s2 = h->sigma2;
+    const double two_pi = 6.283185307179586476925286766559;
+    *out = -0.5 * ((t[0] - t[1]) / s2 + (double)N * log(s2) + 2.0 * t[2] - t[3] + (double)N * log(two_pi));
+    return GP_OK;
+}
+
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec) {
     if (!h) return set_err(GP_EINVAL, 0);
     if (M) *M = h->shape.M;

@@ -136,3 +136,10 @@ void predtc_build_cinfo(const GpShape& s, int* out);
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
                               const int* cinfo, double sigma2, double* mean, double* var,
                               GpStatus* st, cudaStream_t stream);
+
+// ---- log marginal likelihood terms (gp_lml.cu) ----------------------------------
+// out[0..3] = y^T y, b^T c, sum_j log L_jj, sum_m log d_m (float64, fixed
+// summation order), through nparts per-CTA partials in part (4 nparts doubles).
+int lml_partial_count(int sms);
+void launch_lml_terms(const double* y, int64_t N, const double* L, const double* b, const double* c,
+                      const double* d, int M, int nparts, double* part, double* out, cudaStream_t stream);

@@ -205,6 +205,30 @@ def test_fit_predict_in_one_call_matches_separate_calls(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_log_marginal_likelihood_matches_oracle(prec):
+    """gp_model_log_marginal against the oracle's value (itself pinned to the
+    dense N x N definition). Mixed tolerance: Gram errors of twice the mixed
+    level (2e-6 relative on G, 1e-8 on b) move log p(y) by at most 2.4e-5
+    relative on these problems (measured on the oracle), so 1e-3 leaves a 40x
+    margin; float64 is held to 1e-9."""
+    import torch
+    tol = 1e-9 if prec == "fp64" else 1e-3
+    for pr in (W.random_problem(31, 3_000, 10, 2, 6, eps=0.9, alpha=1.1, sigma2=0.02),
+               W.workload2(N=20_000, Ns=10)):
+        m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+        try:
+            got = m.log_marginal(pr.y)
+            ref = O.log_marginal_likelihood(O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2), pr.y)
+            assert abs(got - ref) <= tol * abs(ref), (got, ref, pr.name)
+            # the same sums in the same order from device memory
+            assert m.log_marginal(torch.from_numpy(pr.y).cuda()) == got
+            with pytest.raises(_lib.GPError):
+                m.log_marginal(pr.y[:-1])  # not the fit's N
+        finally:
+            m.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_predict_edge_sizes(prec):
     pr = W.workload1()
     m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
