@@ -174,7 +174,7 @@ int launch_request(gp_server* S, Request* r, int slot) {
         // pinned layout: X* | mean | var | status
         if ((rc = pin.reserve(in + 2 * out + sizeof(GpStatus)))) return set_err(rc);
         memcpy(pin.p, r->Xs, in);
-        double *xd, *md, *vd = nullptr;
+        double *xd = nullptr, *md = nullptr, *vd = nullptr;
         if ((rc = r->sc->get(&xd, (size_t)r->Ns * p))) return rc;
         if ((rc = r->sc->get(&md, (size_t)r->Ns))) return rc;
         if (r->var && (rc = r->sc->get(&vd, (size_t)r->Ns))) return rc;
@@ -195,7 +195,7 @@ int launch_request(gp_server* S, Request* r, int slot) {
         memcpy(pin.p, r->X, (size_t)r->N * s.p * 8);
         memcpy((char*)pin.p + (size_t)r->N * s.p * 8, r->y, (size_t)r->N * 8);
         // one device buffer holds X (N x p) followed by y (N), as staged
-        double *xd, *ll;
+        double *xd = nullptr, *ll = nullptr;
         if ((rc = r->sc->get(&xd, (size_t)r->N * (s.p + 1)))) return rc;
         if ((rc = r->sc->get(&ll, (size_t)s.n))) return rc;
         cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
@@ -219,7 +219,7 @@ bool escalate_refit(gp_server* S, Request* r) {
     const GpShape& s = r->fresh->shape;
     r->escalated = true;
     r->sc2 = new Scratch(st);
-    GpStatus* st2;
+    GpStatus* st2 = nullptr;
     if (r->sc2->get(&st2, 1)) return false;
     cudaMemsetAsync(st2, 0, sizeof(GpStatus), st);
     const double* yd = r->xd + (size_t)r->N * s.p;
