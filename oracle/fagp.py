@@ -271,6 +271,30 @@ def log_marginal_likelihood(model: Dict[str, np.ndarray], y: np.ndarray) -> floa
     return -0.5 * (quad + logdet + N * math.log(2.0 * math.pi))
 
 
+def log_marginal_likelihood_dsigma2(model: Dict[str, np.ndarray], y: np.ndarray) -> float:
+    """d log p(y) / d sigma^2 at fixed eps, rho (the noise part of the
+    gradient that hyperparameter learning follows).
+
+    A = G + diag(d) with d_m = sigma^2 / lambda_m (clamped at CLAMP_D, where
+    d no longer moves), so dA / dsigma^2 = E = diag(e), e_m = d_m / sigma^2 on
+    unclamped columns and 0 on clamped ones. Differentiating the terms of
+    ``log_marginal_likelihood``: d(b^T c) = -c^T E c, d log|A| = tr(A^{-1} E),
+    d sum log d_m = (unclamped count) / sigma^2, so
+      d log p / d sigma^2 = -1/2 [ c^T E c / sigma^2 - (y^T y - b^T c) / sigma^4
+                                   + N / sigma^2 + tr(A^{-1} E) - n_u / sigma^2 ].
+    """
+    y = np.asarray(y, dtype=np.float64)
+    N = y.shape[0]
+    s2 = model["sigma2"]
+    d, c, b, L = model["d"], model["c"], model["b"], model["L"]
+    free = d < CLAMP_D
+    e = np.where(free, d / s2, 0.0)
+    Linv = sla.solve_triangular(L, np.eye(L.shape[0]), lower=True)
+    diag_Ainv = np.sum(Linv * Linv, axis=0)  # (A^{-1})_mm = sum_k (L^{-1})_km^2
+    return -0.5 * (c @ (e * c) / s2 - (y @ y - b @ c) / s2 ** 2 + N / s2
+                   + e @ diag_Ainv - np.count_nonzero(free) / s2)
+
+
 # --------------------------------------------------------------------------
 # Other routes to the same posterior (used to pin the M x M form)
 # --------------------------------------------------------------------------

@@ -363,3 +363,34 @@ def test_log_marginal_likelihood_peaks_near_the_generating_noise():
     grid = [0.01, 0.02, 0.04, 0.08, 0.16]
     vals = [O.log_marginal_likelihood(O.fit(X, y, n, eps, rho, s2), y) for s2 in grid]
     assert int(np.argmax(vals)) == 2, vals
+
+
+@pytest.mark.parametrize("N,p,n", [(40, 1, 6), (150, 2, 4), (30, 1, 60)])
+def test_log_marginal_likelihood_sigma2_gradient_matches_finite_differences(N, p, n):
+    # central differences of the pinned log p(y) (n = 60 includes clamped d)
+    rng = np.random.default_rng(3 * N + p + n)
+    X = rng.uniform(-1.0, 1.0, size=(N, p))
+    y = np.cos(1.5 * X).sum(axis=1) + 0.1 * rng.standard_normal(N)
+    eps, rho, s2 = 1.1, 0.9, 0.03
+    g = O.log_marginal_likelihood_dsigma2(O.fit(X, y, n, eps, rho, s2), y)
+    h = 1e-6 * s2
+    lp = O.log_marginal_likelihood(O.fit(X, y, n, eps, rho, s2 + h), y)
+    lm = O.log_marginal_likelihood(O.fit(X, y, n, eps, rho, s2 - h), y)
+    fd = (lp - lm) / (2 * h)
+    assert abs(g - fd) <= 1e-5 * max(1.0, abs(fd)), (g, fd)
+
+
+def test_log_marginal_likelihood_sigma2_gradient_vanishes_at_the_maximum():
+    # on a fine grid of sigma^2 the gradient changes sign where log p(y) peaks
+    rng = np.random.default_rng(11)
+    N, n, eps, rho = 400, 6, 1.0, 1.0
+    X = rng.uniform(-1.0, 1.0, size=(N, 1))
+    Phi = O.eigenfunctions_1d(X[:, 0], n, eps, rho)
+    lam = np.exp(O.log_eigenvalues_1d(n, eps, rho))
+    y = Phi @ (np.sqrt(lam) * rng.standard_normal(n)) + 0.2 * rng.standard_normal(N)
+    grid = np.geomspace(0.01, 0.16, 21)
+    vals = [O.log_marginal_likelihood(O.fit(X, y, n, eps, rho, s2), y) for s2 in grid]
+    grads = [O.log_marginal_likelihood_dsigma2(O.fit(X, y, n, eps, rho, s2), y) for s2 in grid]
+    k = int(np.argmax(vals))
+    assert 0 < k < len(grid) - 1
+    assert grads[k - 1] > 0 > grads[k + 1]
