@@ -248,6 +248,16 @@ def predict(model: Dict[str, np.ndarray], Xs: np.ndarray, row_block: int = 16384
     return mean, var
 
 
+def predict_covariance(model: Dict[str, np.ndarray], Xs: np.ndarray) -> np.ndarray:
+    """The full predictive covariance block Sigma_* of Eq. 12 (latent f,
+    N_* x N_*) in the M x M form: Sigma_* = sigma^2 Phi_* A^{-1} Phi_*^T =
+    sigma^2 V^T V with V = L^{-1} Phi_*^T. Its diagonal is ``predict``'s
+    variance. Only for small N_*."""
+    Ps = phi_matrix(np.atleast_2d(np.asarray(Xs, dtype=np.float64)), model["n"], model["eps"], model["rho"])
+    V = sla.solve_triangular(model["L"], Ps.T, lower=True)
+    return model["sigma2"] * (V.T @ V)
+
+
 def log_marginal_likelihood(model: Dict[str, np.ndarray], y: np.ndarray) -> float:
     """log p(y) of the truncated-kernel GP, K = Phi Lambda Phi^T (Eq. 7-9),
     from the fitted M x M factors (the quantity that hyperparameter learning,

@@ -394,3 +394,24 @@ def test_log_marginal_likelihood_sigma2_gradient_vanishes_at_the_maximum():
     k = int(np.argmax(vals))
     assert 0 < k < len(grid) - 1
     assert grads[k - 1] > 0 > grads[k + 1]
+
+
+def test_predictive_covariance_block_equals_the_nxn_route():
+    # Eq. 12's full Sigma_* (the f2 row's quantity): the M x M form against
+    # the dense N x N posterior covariance with the truncated kernel, its
+    # diagonal against predict(), symmetry and positive semidefiniteness
+    rng = np.random.default_rng(21)
+    N, p, n, eps, rho, s2 = 80, 2, 5, 0.9, 1.1, 0.02
+    X = rng.uniform(-1.0, 1.0, size=(N, p))
+    y = np.sin(2.0 * X).sum(axis=1) + 0.1 * rng.standard_normal(N)
+    Xs = rng.uniform(-1.0, 1.0, size=(15, p))
+    mdl = O.fit(X, y, n, eps, rho, s2)
+    S = O.predict_covariance(mdl, Xs)
+    Kxx = O.kernel_approx(X, X, n, eps, rho) + s2 * np.eye(N)
+    Ksx = O.kernel_approx(Xs, X, n, eps, rho)
+    ref = O.kernel_approx(Xs, Xs, n, eps, rho) - Ksx @ np.linalg.solve(Kxx, Ksx.T)
+    assert np.max(np.abs(S - ref)) <= 1e-10 * np.max(np.abs(ref))
+    _, var = O.predict(mdl, Xs)
+    np.testing.assert_allclose(np.diag(S), var, rtol=1e-12)
+    np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-15 * np.max(np.abs(S)))
+    assert np.linalg.eigvalsh(S).min() > -1e-12 * np.max(np.abs(S))
