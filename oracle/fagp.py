@@ -142,20 +142,39 @@ def multi_index(n: int, p: int) -> np.ndarray:
     return np.ascontiguousarray(grids, dtype=np.int64)
 
 
-def log_eigenvalues(n: int, p: int, eps: float, rho: float) -> np.ndarray:
-    """log lambda_m = sum_j log lambda_{m_j} (Eq. 20, isotropic eps and rho)."""
-    l1 = log_eigenvalues_1d(n, eps, rho)
-    return l1[multi_index(n, p)].sum(axis=1)
+def per_dimension(v, p: int) -> np.ndarray:
+    """eps or rho for each of the p dimensions: a scalar applies to all (the
+    isotropic kernel, Eq. 13), a length-p sequence gives the ARD kernel's
+    eps_j (Eq. 17) and a scale factor per dimension."""
+    a = np.asarray(v, dtype=np.float64)
+    if a.ndim == 0:
+        return np.full(p, float(a))
+    if a.shape != (p,):
+        raise ValueError(f"expected a scalar or {p} values, got shape {a.shape}")
+    return a
 
 
-def phi_matrix(X: np.ndarray, n: int, eps: float, rho: float) -> np.ndarray:
-    """Phi[i, m] = prod_j phi_{m_j}(x_ij) (Eq. 19), shape (N, n^p)."""
+def log_eigenvalues(n: int, p: int, eps, rho) -> np.ndarray:
+    """log lambda_m = sum_j log lambda^{(j)}_{m_j} (Eq. 20; with ARD, Eq. 17,
+    dimension j has its own eps_j and rho_j)."""
+    e, r = per_dimension(eps, p), per_dimension(rho, p)
+    idx = multi_index(n, p)
+    out = np.zeros(idx.shape[0])
+    for j in range(p):
+        out += log_eigenvalues_1d(n, float(e[j]), float(r[j]))[idx[:, j]]
+    return out
+
+
+def phi_matrix(X: np.ndarray, n: int, eps, rho) -> np.ndarray:
+    """Phi[i, m] = prod_j phi^{(j)}_{m_j}(x_ij) (Eq. 19), shape (N, n^p); eps
+    and rho scalar or per dimension (ARD, Eq. 17)."""
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
     N, p = X.shape
+    e, r = per_dimension(eps, p), per_dimension(rho, p)
     idx = multi_index(n, p)
     Phi = np.ones((N, idx.shape[0]), dtype=np.float64)
     for j in range(p):
-        E = eigenfunctions_1d(X[:, j], n, eps, rho)      # (N, n)
+        E = eigenfunctions_1d(X[:, j], n, float(e[j]), float(r[j]))      # (N, n)
         Phi *= E[:, idx[:, j]]
     return Phi
 
@@ -169,12 +188,14 @@ def kernel_approx(X1: np.ndarray, X2: np.ndarray, n: int, eps: float, rho: float
     return (P1 * lam) @ P2.T
 
 
-def kernel_se(X1: np.ndarray, X2: np.ndarray, eps: float) -> np.ndarray:
-    """The SE kernel exp(-eps^2 |x - x'|^2) (Eq. 13, Eq. 17 with eps_j = eps)."""
+def kernel_se(X1: np.ndarray, X2: np.ndarray, eps) -> np.ndarray:
+    """The SE kernel exp(-sum_j eps_j^2 (x_j - x'_j)^2) (Eq. 13; Eq. 17, ARD,
+    with eps per dimension)."""
     X1 = np.atleast_2d(X1)
     X2 = np.atleast_2d(X2)
-    d2 = ((X1[:, None, :] - X2[None, :, :]) ** 2).sum(axis=2)
-    return np.exp(-eps ** 2 * d2)
+    e = per_dimension(eps, X1.shape[1])
+    d2 = (((X1[:, None, :] - X2[None, :, :]) * e) ** 2).sum(axis=2)
+    return np.exp(-d2)
 
 
 # --------------------------------------------------------------------------

@@ -415,3 +415,50 @@ def test_predictive_covariance_block_equals_the_nxn_route():
     np.testing.assert_allclose(np.diag(S), var, rtol=1e-12)
     np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-15 * np.max(np.abs(S)))
     assert np.linalg.eigvalsh(S).min() > -1e-12 * np.max(np.abs(S))
+
+
+# ---- ARD (Eq. 17): eps and rho per input dimension (the f1 row's oracle)
+
+def test_ard_with_equal_parameters_is_the_isotropic_model():
+    pr = W.random_problem(41, 300, 40, 2, 6, eps=0.9, alpha=1.1, sigma2=0.02)
+    iso = O.predict(O.fit(pr.X, pr.y, pr.n, 0.9, 1.1, 0.02), pr.Xs)
+    ard = O.predict(O.fit(pr.X, pr.y, pr.n, [0.9, 0.9], [1.1, 1.1], 0.02), pr.Xs)
+    for a, b in zip(iso, ard):
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=0)
+
+
+def test_ard_mercer_sum_converges_to_the_anisotropic_se_kernel():
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1.0, 1.0, size=(12, 2))
+    eps, rho = [0.6, 1.4], [1.0, 0.8]
+    K = O.kernel_approx(X, X, 40, eps, rho)
+    ref = O.kernel_se(X, X, eps)
+    assert np.max(np.abs(K - ref)) < 1e-10
+    # the per-dimension factors are really different: the isotropic kernels miss it
+    assert np.max(np.abs(O.kernel_se(X, X, 0.6) - ref)) > 1e-2
+
+
+def test_ard_dimension_permutation_invariance():
+    rng = np.random.default_rng(8)
+    X = rng.uniform(-1.0, 1.0, size=(200, 3))
+    y = np.sin(2.0 * X).sum(axis=1) + 0.1 * rng.standard_normal(200)
+    Xs = rng.uniform(-1.0, 1.0, size=(30, 3))
+    eps, rho = np.array([0.5, 1.0, 1.5]), np.array([0.9, 1.0, 1.2])
+    perm = [2, 0, 1]
+    a = O.predict(O.fit(X, y, 4, eps, rho, 0.03), Xs)
+    b = O.predict(O.fit(X[:, perm], y, 4, eps[perm], rho[perm], 0.03), Xs[:, perm])
+    for u, v in zip(a, b):
+        np.testing.assert_allclose(u, v, rtol=1e-10, atol=1e-14)
+
+
+def test_ard_mxm_form_equals_the_nxn_posterior():
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-1.0, 1.0, size=(60, 2))
+    y = np.cos(3.0 * X[:, 0]) * np.sin(X[:, 1]) + 0.05 * rng.standard_normal(60)
+    Xs = rng.uniform(-1.0, 1.0, size=(20, 2))
+    eps, rho, s2 = [0.7, 1.6], [1.2, 0.9], 0.01
+    mean, var = O.predict(O.fit(X, y, 7, eps, rho, s2), Xs)
+    m2, v2 = O.posterior_nxn(X, y, Xs, 7, eps, rho, s2)
+    assert O.relerr(mean, m2) < 1e-10 and O.relerr(var, v2) < 1e-8
+    with pytest.raises(ValueError):
+        O.phi_matrix(X, 7, [0.7, 1.6, 1.0], rho)  # one value per dimension
