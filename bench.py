@@ -481,6 +481,47 @@ def serving_bench(_lib, torch, dev):
     return out
 
 
+def run_sweep(args):
+    """The paper's own timing sweep (Sec. 3; row f4): y = sum_i cos(x_i) + nu
+    on N = 10,000 training and 1,000 test points for p in {1, 2, 4} over a
+    range of n, each fit + predict timed end to end as the paper times it
+    (host arrays in and out: allocation and copies inside), median of
+    --steps runs after --warmup. One JSON line; not part of the default run."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2403_12797_gb300 import _lib, workloads as W
+    grid = {1: (10, 50, 100, 200, 400), 2: (5, 10, 15, 20, 30), 4: (3, 5, 7, 9, 11)}
+    rows = []
+    for p, ns in grid.items():
+        for n in ns:
+            pr = W.workload6(p, n)
+            mean = np.empty(pr.Ns)
+            var = np.empty(pr.Ns)
+
+            def step():
+                m, _, _ = _lib.fit_predict(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, pr.Xs,
+                                           prec=args.prec, mean_out=mean, var_out=var)
+                m.free()
+
+            for _ in range(args.warmup):
+                step()
+            ts = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                step()
+                ts.append(time.perf_counter() - t0)
+            t = statistics.median(ts)
+            rows.append({"p": p, "n": n, "M": n ** p, "ms": t * 1e3,
+                         "points_per_s": (pr.N + pr.Ns) / t})
+    print(json.dumps({"metric": "paper sweep: fit+predict time, host arrays in and out",
+                      "unit": "ms", "prec": args.prec, "data": "synthetic",
+                      "config": {"workload": "y = sum cos(x_i) + 0.1 noise, x~U[-1,1]^p, "
+                                             "N = 10,000 train, 1,000 test points"},
+                      "steps": args.steps, "warmup": args.warmup, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -491,10 +532,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the comparisons (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fit and serving measurements")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the paper's timing sweep (p in {1, 2, 4}, N = 10,000) instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.quick else args.warmup
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 
