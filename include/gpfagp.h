@@ -204,8 +204,10 @@ GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, in
  * exceed GP_STATIC_SCRATCH_BYTES (gp_last_error_detail() = the bytes needed).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current: make it before any
- * stream capture. Every call shares the one array, so calls that overlap on
- * the GPU race; serialise them. */
+ * stream capture. The address is kept for the life of the process, so do
+ * not call this again after resetting the device (cudaDeviceReset). Every
+ * call shares the one array, so calls that overlap on the GPU race;
+ * serialise them. */
 GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p, int n,
                               double eps, double alpha, double* G, double* b, void* cuda_stream);
 
@@ -341,6 +343,15 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k);
 /* Make the next k mixed-precision fits report a non-positive pivot on their
  * first attempt (k = 0 disarms), to exercise the float64 escalation. */
 GPFAGP_API void gp_debug_force_escalation(int k);
+
+/* Failure-detection test hook: the float64 Cholesky's bounded grid-barrier
+ * waits give up after limit_s seconds (limit_s <= 0 restores the 2 s
+ * default), and in the next Cholesky launch the CTA with index skip_cta
+ * (skip_cta < 0: none) returns before its first grid-barrier arrival, so
+ * that the other CTAs' waits run out: the call then returns GP_ETIMEOUT
+ * (detail 100, the grid barrier) and the device stays usable. Nothing
+ * faults or hangs. The skip is one-shot; the limit stays until reset. */
+GPFAGP_API void gp_debug_barrier_timeout(double limit_s, int skip_cta);
 
 /* Test hook, host only: the mixed Gram's row-split plan for T 128-column tile
  * rows, Npad padded rows and a budget of target_ctas CTAs. out[0..2]: split

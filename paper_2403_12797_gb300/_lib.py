@@ -97,6 +97,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_server_reset_stats": (i, [vp]),
         "gp_debug_fail_alloc_after": (None, [i]),
         "gp_debug_force_escalation": (None, [i]),
+        "gp_debug_barrier_timeout": (None, [d, i]),
         "gp_debug_gram_splits": (i, [i, i64, i, C.POINTER(i64)]),
         "gp_model_flags": (i, [vp]),
         "gp_version": (C.c_char_p, []),
@@ -384,6 +385,12 @@ def debug_gram_splits(T: int, Npad: int, target_ctas: int):
 
 def debug_force_escalation(k: int):
     lib().gp_debug_force_escalation(int(k))
+
+
+def debug_barrier_timeout(limit_s: float, skip_cta: int = -1):
+    """Shorten the Cholesky's bounded waits to limit_s (<= 0: the default) and
+    make CTA skip_cta of the next Cholesky leave before its first barrier."""
+    lib().gp_debug_barrier_timeout(float(limit_s), int(skip_cta))
 
 
 def debug_fail_alloc_after(k: int):

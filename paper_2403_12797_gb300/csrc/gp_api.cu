@@ -702,6 +702,10 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k) { g_fail_after.store(k > 0 ? k 
 
 GPFAGP_API void gp_debug_force_escalation(int k) { g_force_escalate.store(k > 0 ? k : 0); }
 
+GPFAGP_API void gp_debug_barrier_timeout(double limit_s, int skip_cta) {
+    factor_debug_barrier_timeout(limit_s, skip_cta);
+}
+
 GPFAGP_API int gp_debug_gram_splits(int T, int64_t Npad, int target_ctas, int64_t* out) {
     if (T < 1 || Npad < 1 || target_ctas < 1 || !out) return set_err(GP_EINVAL, 0);
     SyrkSplit sp;

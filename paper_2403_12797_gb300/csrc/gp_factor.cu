@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <map>
 #include <mutex>
@@ -52,14 +53,15 @@ struct GridBar {
 };
 
 // Bounded grid-wide barrier for a cooperative launch. Returns false (and
-// sets GP_ETIMEOUT) if the other CTAs do not arrive within GP_WAIT_NS.
+// sets GP_ETIMEOUT, detail 100) if the other CTAs do not arrive within
+// wait_ns nanoseconds (GP_WAIT_NS unless a test shortened it).
 // `count` only grows (zeroed before the launch): the arrivals at the k-th
 // barrier are numbers k G .. k G + G - 1, so a CTA learns from its own
 // arrival number which total ends the barrier. The arrival is a release
 // and the wait an acquire at GPU scope; together with the CTA barriers on
 // both sides they order every thread's writes before the barrier with every
 // thread's reads after it.
-__device__ bool grid_sync(GridBar* gb, GpStatus* st) {
+__device__ bool grid_sync(GridBar* gb, GpStatus* st, uint64_t wait_ns = GP_WAIT_NS) {
     __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -77,7 +79,7 @@ __device__ bool grid_sync(GridBar* gb, GpStatus* st) {
                 const uint64_t now = globaltimer_ns();
                 if (t0 == 0) {
                     t0 = now;
-                } else if (now - t0 > GP_WAIT_NS) {
+                } else if (now - t0 > wait_ns) {
                     gp_set_status(st, GP_ETIMEOUT, 100);
                     s_fail = 1;
                     break;
@@ -334,8 +336,11 @@ __device__ __forceinline__ void chol_next_diag(double* __restrict__ L, int M, in
 //      themselves done; CTA 0 waits for the count and factors that block while
 //      CTAs 1..G-1 apply the rest of the trailing update;
 //   -- grid barrier --
+// wait_ns bounds every wait (GP_WAIT_NS normally). skip_cta >= 0 is a test of
+// failure detection only: that CTA leaves before its first barrier arrival,
+// so the others' bounded waits run out and report GP_ETIMEOUT.
 __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
-                                                       CholWork* cw) {
+                                                       CholWork* cw, uint64_t wait_ns, int skip_cta) {
     __shared__ double a[CB][CB + 1];
     __shared__ double ti[UT][CB + 1];
     __shared__ double tj[UT][CB + 1];
@@ -348,8 +353,9 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
     const int nh = (G > 1) ? min(NHELP, G - 1) : 1;
     double* rsd = (double*)((char*)cw + CHOL_RSD_OFFSET);
     GridBar* gb = &cw->bar;
+    if ((int)blockIdx.x == skip_cta) return;
     if (blockIdx.x == 0) chol_potrf(L, M, 0, min(CB, M), st, rsd, sm);
-    if (!grid_sync(gb, st)) return;
+    if (!grid_sync(gb, st, wait_ns)) return;
     if (status_code(st) != 0) return;
     for (int k = 0; k < nb; ++k) {
         const int kb = k * CB, w = min(CB, M - kb);
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
             }
             __syncthreads();
         }
-        if (!grid_sync(gb, st)) return;
+        if (!grid_sync(gb, st, wait_ns)) return;
         // ---- C
         const int wn = min(CB, rest);              // width of the next diagonal block
         const int ntr = (rest + UT - 1) / UT;
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
                         unsigned int cur;
                         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&cw->helped) : "memory");
                         if (cur >= target) break;
-                        if ((++it & 1023u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) {
+                        if ((++it & 1023u) == 0 && globaltimer_ns() - t0 > wait_ns) {
                             gp_set_status(st, GP_ETIMEOUT, 101);
                             s_fail = 1;
                             break;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
                 tri_pair(t, &I, &J);
                 chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
             }
-        if (!grid_sync(gb, st)) return;
+        if (!grid_sync(gb, st, wait_ns)) return;
         if (status_code(st) != 0) return;
     }
     // upper triangle = 0
@@ -1037,13 +1043,27 @@ int chol_grid(int M, int dev) {
     return want < 2 ? 2 : (want > g ? g : want);
 }
 
+namespace {
+// failure-detection test hooks (gp_debug_barrier_timeout)
+std::atomic<unsigned long long> g_chol_wait_ns{0};  // 0: GP_WAIT_NS
+std::atomic<int> g_chol_skip_cta{-1};               // one-shot
+}  // namespace
+
+void factor_debug_barrier_timeout(double limit_s, int skip_cta) {
+    g_chol_wait_ns.store(limit_s > 0.0 ? (unsigned long long)(limit_s * 1e9) : 0ull);
+    g_chol_skip_cta.store(skip_cta >= 0 ? skip_cta : -1);
+}
+
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
     CholWork* cw = (CholWork*)work;
     cudaMemsetAsync(cw, 0, CHOL_RSD_OFFSET, stream);
     dim3 grid((unsigned)chol_grid(M, dev)), block(NT);
-    void* args[] = {&L, &M, &st, &cw};
+    const unsigned long long lim = g_chol_wait_ns.load();
+    uint64_t wait_ns = lim ? (uint64_t)lim : (uint64_t)GP_WAIT_NS;
+    int skip = g_chol_skip_cta.exchange(-1);
+    void* args[] = {&L, &M, &st, &cw, &wait_ns, &skip};
     gp_note_launches(1);
     return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, grid, block, args, 0, stream);
 }

@@ -95,6 +95,10 @@ size_t factor_work_bytes(int M, bool fp32_inverse);
 // holds the grid barriers of launch_tri_inverse and launch_solve_refine too:
 // those two run after it, on the same workspace.
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream);
+// Test hook of gp_debug_barrier_timeout: the Cholesky's bounded waits give up
+// after limit_s seconds (<= 0: GP_WAIT_NS), and the next launch's CTA
+// skip_cta (< 0: none) leaves before its first grid-barrier arrival.
+void factor_debug_barrier_timeout(double limit_s, int skip_cta);
 // W = L^{-1} (lower, M x M row-major, upper part zeroed), one cooperative
 // launch: in float64 into W (fp32 = false), or in float32 into the workspace
 // (fp32 = true; W is not written and may be NULL), where the solve finds it

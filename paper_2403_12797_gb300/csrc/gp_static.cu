@@ -15,7 +15,10 @@
 // as a device address: the first call on each device (with that device
 // current) asks the runtime for the address with cudaGetSymbolAddress and
 // keeps it; later calls reuse it. That first call must not happen inside a
-// stream capture. All calls share the array and its contents persist
+// stream capture. The kept address belongs to the device's current context:
+// after cudaDeviceReset the module is loaded anew and the address is stale,
+// so this entry point must not be used again in a process that reset the
+// device. All calls share the array and its contents persist
 // between calls, so calls that overlap on the GPU (different streams or
 // threads at the same time) race with each other; serialise them.
 #include "gp_kernels.cuh"
@@ -120,7 +123,11 @@ int gp_static_gram(const double* X, const double* y, int64_t N, int p, int n, do
     double* ypad = (double*)(base + P.off_y);
     double* Gpart = (double*)(base + P.off_G);
     double* bpart = (double*)(base + P.off_b);
-    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);  // the array keeps the last call's status
+    e = cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);  // the array keeps the last call's status
+    if (e != cudaSuccess) {
+        *detail = e;
+        return GP_ECUDA;
+    }
     launch_eig_tables_f64(s, X, y, tab, st, stream);
     static_pad_y_kernel<<<(unsigned)((s.Npad + 255) / 256), 256, 0, stream>>>(y, s.N, s.Npad, ypad);
     e = launch_syrk64(s, tab, ypad, P.nsplit, P.rps, Gpart, bpart, stream);

@@ -1,7 +1,7 @@
 """Batched fit (one captured graph, autotuned Gram budgets) and batched predict.
 
 The batch is a small instance of the uneven-shape batched workload (p in
-1..4, M <= 256, N log-uniform up to 20,000). Every batched model is checked
+1..4, M <= 256, N log-uniform up to 20,000) plus one member at M = 1024. Every batched model is checked
 against the FP64 oracle with the precision mode's tolerances, batched
 predicts against single predicts bitwise, and a failing member against its
 index.
@@ -19,13 +19,17 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": dict(mean=1e-10, var=1e-10), "mixed": dict(mean=1e-4, var=1e-3)}
 
 
-def _batch(count=16, seed_offset=0):
-    return W.workload4(count=count, Ns=300, N_hi=20_000, M_max=256, seed_offset=seed_offset)
+def _batch(count=16, seed_offset=0, with_m1024=False):
+    out = W.workload4(count=count, Ns=300, N_hi=20_000, M_max=256, seed_offset=seed_offset)
+    if with_m1024:
+        # one member at the batched workload's largest M (p = 2, n = 32)
+        out.append(W.random_problem(61, 20_000, 300, 2, 32, eps=1.0, alpha=0.9, sigma2=0.01))
+    return out
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_fit_batch_matches_oracle(prec):
-    probs = _batch()
+    probs = _batch(with_m1024=True)
     models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs], prec=prec)
     used_graph, k = _lib.batch_info()
     assert k in (1, 2, 4)

@@ -100,6 +100,69 @@ def test_fit_predict_matches_oracle(prec, case):
     m.free()
 
 
+def _head(pr, N, Ns):
+    """The first N training and Ns test rows of a workload."""
+    import dataclasses
+    return dataclasses.replace(pr, X=pr.X[:N].copy(), y=pr.y[:N].copy(), Xs=pr.Xs[:Ns].copy())
+
+
+# Shapes at the sizes the benchmark, batched and served workloads run: the
+# p=3, n=16 (M = 4096) workload on its first 40,000 rows, M = 1024 (the
+# batched workload's largest), M = 1296 and 1728 (the served models' range),
+# and the paper's own sweep shapes that reach furthest (p = 1 with n = 200
+# and 400, where sigma^2 / lambda_m hits the 1e200 clamp and L's diagonal
+# spans ~1e100; p = 4 with n = 11, M = 14,641 > N). They cover the
+# Cholesky's many-wave trailing updates, the inverse's deeper doubling levels
+# and the predict kernel's super-tile loop, at M beyond 512.
+LARGE_CASES = {
+    "w3_m4096": lambda: _head(W.workload3(N=40_000, Ns=2_000), 40_000, 2_000),
+    "p2n32_m1024": lambda: W.random_problem(51, 30_000, 1_500, 2, 32, eps=1.0, alpha=0.9, sigma2=0.005),
+    "p3n12_m1728": lambda: W.random_problem(52, 30_000, 1_500, 3, 12, eps=1.1, alpha=1.0, sigma2=0.005,
+                                            law="normal", scale=0.5),
+    "p4n6_m1296": lambda: W.random_problem(53, 30_000, 1_500, 4, 6, eps=0.9, alpha=1.1, sigma2=0.01),
+    "sweep_p1n200": lambda: W.workload6(1, 200, Ns=500),
+    "sweep_p1n400": lambda: W.workload6(1, 400, Ns=500),
+    "sweep_p4n11": lambda: W.workload6(4, 11, Ns=500),
+}
+_ORACLE_CACHE = {}
+
+
+def _large(name):
+    if name not in _ORACLE_CACHE:
+        pr = LARGE_CASES[name]()
+        mdl, (mo, vo) = _oracle(pr)
+        _ORACLE_CACHE[name] = (pr, mdl, mo, vo)
+    return _ORACLE_CACHE[name]
+
+
+def _max_errs(mean, var, mo, vo):
+    """Largest mean error relative to the largest |mean|, and largest
+    elementwise relative error of the variance (reading A9 of the tolerances)."""
+    return (float(np.max(np.abs(mean - mo)) / np.max(np.abs(mo))),
+            float(np.max(np.abs(var - vo) / vo)))
+
+
+MAX_TOL = {"fp64": dict(mean=1e-9, var=1e-8), "mixed": dict(mean=1e-3, var=1e-2)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(LARGE_CASES))
+def test_fit_predict_large_m_matches_oracle(prec, name):
+    pr, mdl, mo, vo = _large(name)
+    m, mean, var = _fit_predict(pr, prec)
+    try:
+        assert np.isfinite(mean).all() and np.isfinite(var).all()
+        assert O.relerr(mean, mo) < TOL[prec]["mean"], (O.relerr(mean, mo), name)
+        assert O.relerr(var, vo) < TOL[prec]["var"], (O.relerr(var, vo), name)
+        em, ev = _max_errs(mean, var, mo, vo)
+        assert em < MAX_TOL[prec]["mean"], (em, name)
+        assert ev < MAX_TOL[prec]["var"], (ev, name)
+        if prec == "fp64":
+            assert O.relerr(m.read("c"), mdl["c"]) < 1e-9
+    finally:
+        m.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_workload2_full_size(prec):
     pr = W.workload2()

@@ -3,17 +3,21 @@
 Predict requests of uneven sizes against several resident models are all
 submitted at once (more than there are slots), so most start while others
 are on the GPU; each result must equal the same request run alone through
-gp_predict (bitwise: the same kernels with the same launch plans). A tight
+gp_predict (bitwise: the same kernels with the same launch plans) and match
+the FP64 oracle's posterior within the precision mode's tolerance. A tight
 memory budget must still complete everything. A refit swaps the model in:
 predicts after it equal a fresh fit of the new data.
 """
 import numpy as np
 import pytest
 
+from oracle import fagp as O
 from paper_2403_12797_gb300 import _lib
 from paper_2403_12797_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(mean=1e-10, var=1e-10), "mixed": dict(mean=1e-4, var=1e-3)}
 
 
 def _problems():
@@ -53,10 +57,14 @@ def test_mix_equals_alone(prec, budget):
         if budget == 0:
             assert st["peak_inflight"] >= 2  # requests overlapped on the device
         assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+        oracles = [O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs]
         for (k, Xs), (mean, var) in zip(reqs, outs):
             m1, v1 = alone[k].predict(Xs)
             np.testing.assert_array_equal(mean, m1)
             np.testing.assert_array_equal(var, v1)
+            mo, vo = O.predict(oracles[k], Xs)
+            assert O.relerr(mean, mo) < TOL[prec]["mean"], (k, O.relerr(mean, mo))
+            assert O.relerr(var, vo) < TOL[prec]["var"], (k, O.relerr(var, vo))
     finally:
         for m in alone:
             m.free()

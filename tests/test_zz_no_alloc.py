@@ -6,7 +6,9 @@ allocator, an allocator hook that must not be re-entered): its scratch is a
 static device array inside the library. The test calls it through the C ABI
 with device pointers and compares it with the allocating gp_gram_ex on
 several calls in a row, so that contents left in the shared array by one
-call cannot leak into the next. This file is collected last on purpose.
+call cannot leak into the next, with the library's allocator armed to fail
+its next allocation during each call (so any allocation would show as
+GP_ENOMEM). This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -39,7 +41,18 @@ def test_static_gram_matches_allocating_gram_on_consecutive_calls():
         pr = W.random_problem(seed, N, 1, p, n, eps=1.1, alpha=0.9)
         X = torch.from_numpy(pr.X).cuda()
         y = torch.from_numpy(pr.y).cuda()
-        rc, G, b = _static_gram(L, X, y, N, p, n, pr.eps, pr.alpha)
+        M = n ** p
+        G = torch.full((M, M), float("nan"), dtype=torch.float64, device="cuda")
+        b = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        # the library's allocator is armed to fail its next allocation: a call
+        # that allocated anything would return GP_ENOMEM
+        _lib.debug_fail_alloc_after(1)
+        try:
+            rc = L.gp_gram_static(X.data_ptr(), y.data_ptr(), N, p, n, pr.eps, pr.alpha, G.data_ptr(),
+                                  b.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        finally:
+            _lib.debug_fail_alloc_after(0)
         assert rc == _lib.GP_OK, _lib.strerror(rc)
         Gr, br = _lib.gram(X, y, n, pr.eps, pr.alpha, prec="fp64")
         torch.cuda.synchronize()
