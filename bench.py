@@ -260,6 +260,9 @@ def run_ours(args):
 
     main_w2 = args.workload == 2
     pr = W.workload2() if main_w2 else W.workload3()
+    if args.train_rows or args.test_rows:
+        # a smaller case of the same workload (profiling captures), never the default
+        pr = _sub(pr, args.train_rows or pr.N, args.test_rows or pr.Ns)
     dev = torch.device("cuda", local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -337,7 +340,7 @@ def run_ours(args):
            # host's turnaround inside the API calls (status reads, the fit -> predict handoff)
            "device_busy_ms_per_step": sum(g["total_ms"] for g in groups.values()) / args.steps}
 
-    if rank == 0 and not main_w2:
+    if rank == 0 and not main_w2 and not args.quick:
         # the p=2, n=20 workload as a secondary key (same step, same timing rules)
         pr2 = W.workload2()
         step2, _ = make_step(pr2)
@@ -606,6 +609,10 @@ def main():
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
                     help="3: p=3, n=16, M=4096, N=2e6 (the benchmark); 2: p=2, n=20, M=400, N=2e5")
     ap.add_argument("--quick", action="store_true", help="skip the comparisons (profiling runs)")
+    ap.add_argument("--train-rows", type=int, default=0,
+                    help="use only the first R training rows (smaller profiling captures)")
+    ap.add_argument("--test-rows", type=int, default=0,
+                    help="use only the first R test rows (smaller profiling captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-fit and serving measurements")
     ap.add_argument("--sweep", action="store_true",

@@ -2,12 +2,20 @@
 element by element on the same seeded inputs.
 
 Tolerances (relative L2 unless stated):
-  fp64 mode:   Gram 1e-12 (Frobenius), mean and variance 1e-10;
+  fp64 mode:   Gram 1e-12 (Frobenius), mean and variance 1e-10 (measured:
+               below 2e-13 on every case);
   mixed mode:  mean 1e-4 and variance 1e-3 (the targets the mixed path is
-               built for); Gram 1e-4 (Frobenius): each Phi value is held as
-               an integer plus a bf16 remainder of a column scaled to
-               |w| <= 128, i.e. to 2^-10 absolute, so small values carry
-               up to ~1e-3 relative error that averages out over the rows.
+               built for; measured: mean 3.7e-5 at M = 4096, below 1e-5
+               elsewhere; variance below 4e-5). Gram 1e-5 for p <= 4 and
+               1e-4 for p > 4 (Frobenius; measured at most 1.8e-6 and
+               2.5e-5): each Phi value is held as an integer plus an fp16
+               remainder of its column scaled to |w| <= 128 by the block
+               bound, i.e. to 2^-12 absolute; the bound is a product of p
+               per-dimension maxima, so it overestimates a column's values
+               more as p grows and fewer of the 19 bits are used.
+  largest elementwise errors (reading A9): the mean's largest error
+  relative to its largest magnitude and the variance's largest relative
+  error, mixed 1e-3 and 3e-3 (measured 3.7e-4 and 2.6e-4), fp64 1e-11.
 """
 import numpy as np
 import pytest
@@ -19,7 +27,9 @@ from paper_2403_12797_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": dict(G=1e-12, mean=1e-10, var=1e-10),
-       "mixed": dict(G=1e-4, mean=1e-4, var=1e-3)}
+       "mixed": dict(G=1e-5, mean=1e-4, var=1e-3)}
+TOL_G_MIXED_HIGH_P = 1e-4   # p > 4
+TOL_B = {"fp64": 1e-12, "mixed": 2e-6}   # b = Phi^T y (measured mixed: at most 2.5e-7)
 
 GRAM_CASES = [
     # (seed, N, p, n): ragged N, M not a multiple of the tile, several tiles, wrap of digits
@@ -43,8 +53,9 @@ def test_gram_matches_oracle(prec, seed, N, p, n):
     pr = W.random_problem(seed, N, 1, p, n, eps=1.1, alpha=0.9)
     G, b = _lib.gram(pr.X, pr.y, n, pr.eps, pr.alpha, prec=prec)
     Go, bo = O.gram(pr.X, pr.y, n, pr.eps, pr.alpha)
-    assert O.relerr(G, Go) < TOL[prec]["G"]
-    assert O.relerr(b, bo) < max(TOL[prec]["G"], 1e-12) * 10
+    tol_g = TOL_G_MIXED_HIGH_P if (prec == "mixed" and p > 4) else TOL[prec]["G"]
+    assert O.relerr(G, Go) < tol_g, O.relerr(G, Go)
+    assert O.relerr(b, bo) < TOL_B[prec], O.relerr(b, bo)
     np.testing.assert_array_equal(G, G.T)
 
 
@@ -85,10 +96,12 @@ def test_fit_predict_matches_oracle(prec, case):
     tol_mean = TOL[prec]["mean"]
     if prec == "mixed" and pr.N == 1:
         # One training point: G = phi phi^T has no rows to average over, so
-        # each entry keeps the full <= 2^-16 relative error of one product
-        # of two mixed-precision Phi values, and for this problem the mean
-        # amplifies relative errors of G by ~30 (checked on the oracle):
-        # 30 * 2^-16 = 4.6e-4.
+        # each entry keeps the full representation error of one product of
+        # two mixed-precision Phi values (up to 2^-12 absolute on values
+        # scaled to 128, i.e. ~2^-16 relative for the smaller ones), and for
+        # this problem the mean amplifies relative errors of G by ~30
+        # (checked on the oracle): 30 * 2^-16 = 4.6e-4. Measured with the
+        # exact-block Gram: 1.6e-4, so the 1e-4 target does not apply here.
         tol_mean = 1e-3
     assert O.relerr(mean, mo) < tol_mean, (O.relerr(mean, mo), pr.name)
     assert O.relerr(var, vo) < TOL[prec]["var"], (O.relerr(var, vo), pr.name)
@@ -142,7 +155,7 @@ def _max_errs(mean, var, mo, vo):
             float(np.max(np.abs(var - vo) / vo)))
 
 
-MAX_TOL = {"fp64": dict(mean=1e-9, var=1e-8), "mixed": dict(mean=1e-3, var=1e-2)}
+MAX_TOL = {"fp64": dict(mean=1e-11, var=1e-11), "mixed": dict(mean=1e-3, var=3e-3)}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -183,7 +196,8 @@ def test_workload3_full_size_gram_sampled():
     |dG_ac| <= 2^-19 sum_i (B_a |Phi_ic| + B_c |Phi_ia|), i.e. relative to
     |Phi_a| |Phi_c| at most 2^-19 (B_a sqrt(N)/|Phi_a| + B_c sqrt(N)/|Phi_c|);
     the columns' peak-to-RMS ratios stay below 10 here, giving 4e-5. The
-    block sums add ~1e-7 of G (truncation of the float32 remainder sums)."""
+    block sums add ~1e-7 of G (truncation of the float32 remainder sums).
+    Measured: at most 1.2e-6 (mean 1.3e-7), so the test holds it to 1e-5."""
     pr = W.workload3()
     M = pr.n ** 3
     G, b = _lib.gram(pr.X, pr.y, pr.n, pr.eps, pr.alpha, prec="mixed")
@@ -197,10 +211,10 @@ def test_workload3_full_size_gram_sampled():
     pairs = rng.integers(0, M, size=(200, 2))
     pairs[:40, 1] = pairs[:40, 0]
     errs = [abs(G[a, c] - float(col(a) @ col(c))) / np.sqrt(G[a, a] * G[c, c]) for a, c in pairs]
-    assert max(errs) < 4e-5, max(errs)
+    assert max(errs) < 1e-5, max(errs)
     ynorm = float(np.sqrt(pr.y @ pr.y))
     berr = [abs(b[k] - float(col(k) @ pr.y)) / (np.sqrt(G[k, k]) * ynorm) for k in rng.integers(0, M, size=50)]
-    assert max(berr) < 4e-5, max(berr)
+    assert max(berr) < 1e-5, max(berr)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -272,10 +286,11 @@ def test_log_marginal_likelihood_matches_oracle(prec):
     """gp_model_log_marginal against the oracle's value (itself pinned to the
     dense N x N definition). Mixed tolerance: Gram errors of twice the mixed
     level (2e-6 relative on G, 1e-8 on b) move log p(y) by at most 2.4e-5
-    relative on these problems (measured on the oracle), so 1e-3 leaves a 40x
-    margin; float64 is held to 1e-9."""
+    relative on these problems (measured on the oracle); the library's mixed
+    value was measured within 1.1e-5 of the oracle on every parity shape
+    (8e-7 on the p=2 workload), so 1e-4; float64 is held to 1e-9."""
     import torch
-    tol = 1e-9 if prec == "fp64" else 1e-3
+    tol = 1e-9 if prec == "fp64" else 1e-4
     for pr in (W.random_problem(31, 3_000, 10, 2, 6, eps=0.9, alpha=1.1, sigma2=0.02),
                W.workload2(N=20_000, Ns=10)):
         m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
