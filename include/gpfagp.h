@@ -344,6 +344,14 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k);
  * first attempt (k = 0 disarms), to exercise the float64 escalation. */
 GPFAGP_API void gp_debug_force_escalation(int k);
 
+/* Test hook: which mixed-precision Gram kernel the fits run. 0 (default):
+ * automatic -- for M > 512 (p <= 4) a cluster of two CTAs per 256 x 256 tile
+ * pair of G (tcgen05 cta_group::2), else one CTA per 128 x 128 tile pair;
+ * 1: always one CTA per 128 x 128 tile pair; 2: CTA pairs wherever they
+ * apply (p <= 4). Both compute the same arithmetic (the mixed mode above);
+ * the tests compare them with each other and with the FP64 oracle. */
+GPFAGP_API void gp_debug_gram_kernel(int kind);
+
 /* Failure-detection test hook: the float64 Cholesky's bounded grid-barrier
  * waits give up after limit_s seconds (limit_s <= 0 restores the 2 s
  * default), and in the next Cholesky launch the CTA with index skip_cta

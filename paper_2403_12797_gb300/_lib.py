@@ -98,6 +98,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_debug_fail_alloc_after": (None, [i]),
         "gp_debug_force_escalation": (None, [i]),
         "gp_debug_barrier_timeout": (None, [d, i]),
+        "gp_debug_gram_kernel": (None, [i]),
         "gp_debug_gram_splits": (i, [i, i64, i, C.POINTER(i64)]),
         "gp_model_flags": (i, [vp]),
         "gp_version": (C.c_char_p, []),
@@ -385,6 +386,11 @@ def debug_gram_splits(T: int, Npad: int, target_ctas: int):
 
 def debug_force_escalation(k: int):
     lib().gp_debug_force_escalation(int(k))
+
+
+def debug_gram_kernel(kind: int):
+    """0: automatic, 1: one CTA per 128 x 128 tile pair, 2: CTA pairs where they apply."""
+    lib().gp_debug_gram_kernel(int(kind))
 
 
 def debug_barrier_timeout(limit_s: float, skip_cta: int = -1):

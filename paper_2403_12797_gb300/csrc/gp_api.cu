@@ -27,6 +27,9 @@ namespace gpi {
 thread_local int g_err = GP_OK;
 thread_local int64_t g_detail = 0;
 std::atomic<int> g_fail_after{0};
+// which mixed-precision Gram kernel runs: 0 automatic (CTA pairs for M > 512),
+// 1 always one CTA per 128 x 128 tile pair, 2 CTA pairs wherever they apply
+std::atomic<int> g_gram_kernel{0};
 std::mutex g_pool_mu;
 std::vector<int> g_pool_ready;
 
@@ -132,7 +135,7 @@ int read_status(GpStatus* st, cudaStream_t s) {
 // one split takes 4 waves of the whole row range, two splits 7 waves of half
 // of it.
 void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, int* nsplit,
-                   int64_t* rps) {
+                   int64_t* rps, int max_waves = 8) {
     if (target_ctas < 1) target_ctas = 1;
     int64_t maxs = Npad / 256;  // at least 256 rows per split
     if (maxs < 1) maxs = 1;
@@ -142,7 +145,7 @@ void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, i
         const int64_t r = gp_round_up((Npad + want - 1) / want, granule);
         const int64_t ns = (Npad + r - 1) / r;
         const int64_t waves = (npairs * ns + target_ctas - 1) / target_ctas;
-        if (ns > 1 && ns * npairs > 8 * (int64_t)target_ctas) break;
+        if (ns > 1 && ns * npairs > (int64_t)max_waves * target_ctas) break;
         const int64_t cost = waves * (r + 1024);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -162,14 +165,20 @@ void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, i
 // 1.24 for the pairs (I, 0), which also form Phi^T y, and 1.17 for the other
 // off-diagonal pairs; a diagonal pair generates one operand tile instead of
 // two. Otherwise every class takes the uniform choice of choose_splits.
-void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp) {
+//
+// The CTA-pair kernel (tiles of 256) takes the same plan with clusters in
+// place of CTAs, class costs `wc` and up to `max_waves` waves.
+const double kClassCost1[3] = {1.0, 1.24, 1.17};
+const double kClassCost2[3] = {1.0, 1.05, 1.0};
+void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp, const double* wc = kClassCost1,
+                      int max_waves = 8) {
     if (target_ctas < 1) target_ctas = 1;
     const int npairs = T * (T + 1) / 2;
     const int64_t npc[3] = {T, T - 1, (int64_t)(T - 1) * (T - 2) / 2};
     if (npairs > target_ctas) {
         int ns;
         int64_t rps;
-        choose_splits(npairs, Npad, target_ctas, GP_TAB_BLOCK, &ns, &rps);
+        choose_splits(npairs, Npad, target_ctas, GP_TAB_BLOCK, &ns, &rps, max_waves);
         for (int c = 0; c < 3; ++c) {
             sp->n[c] = ns;
             sp->rows[c] = rps;
@@ -178,7 +187,7 @@ void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp) {
         return;
     }
     const int64_t nb = (Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK;
-    const double w[3] = {1.0, 1.24, 1.17};
+    const double* w = wc;
     int64_t n[3] = {1, 1, 1};
     auto cost = [&](int c) { return (double)((nb + n[c] - 1) / n[c] + 1) * w[c]; };
     while (true) {
@@ -252,37 +261,55 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             gp_note_launches(1);
         }
     } else {
+        // the CTA-pair kernel (256 x 256 tile pairs) for M > 512 where it
+        // applies, else one CTA per 128 x 128 tile pair
+        GpShape sg = s;
+        bool pair = false;
+        const int kind = g_gram_kernel.load();
+        if (kind != 1 && s.M > (kind == 2 ? 0 : 512)) {
+            sg.Mpad = (int)gp_round_up(s.M, 256);
+            pair = syrktc2_supported(sg);
+            if (!pair) sg.Mpad = s.Mpad;
+        }
+        const int TT = pair ? 256 : SYRKTC_TM;
         float* tabc;
         float2* Gpart;
         double* bpart;
-        if ((rc = sc.get(&tabc, syrktc_table_floats(s)))) return rc;
-        const int T = s.Mpad / SYRKTC_TM;
+        if ((rc = sc.get(&tabc, syrktc_table_floats(sg)))) return rc;
+        const int T = sg.Mpad / TT;
         const int npairs = T * (T + 1) / 2;
         SyrkSplit spl;
-        choose_splits_tc(T, s.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &spl);
-        if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
-        if ((rc = sc.get(&bpart, (size_t)spl.smax * s.Mpad))) return rc;
+        if (pair) {
+            int clusters = syrktc2_max_clusters(sg, dev);
+            if (target_ctas > 0) clusters = std::max(1, std::min(clusters, target_ctas / 2));
+            choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16);
+        } else {
+            choose_splits_tc(T, sg.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &spl);
+        }
+        if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * TT * TT))) return rc;
+        if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
         int* colexp;
         signed char* ebx;
-        if ((rc = sc.get(&tmax, (size_t)s.p * s.n))) return rc;
-        if ((rc = sc.get(&tmaxb, (size_t)s.p * s.n * ((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
-        if ((rc = sc.get(&colexp, (size_t)s.Mpad))) return rc;
-        if ((rc = sc.get(&ebx, syrktc_ebx_bytes(s)))) return rc;
+        if ((rc = sc.get(&tmax, (size_t)sg.p * sg.n))) return rc;
+        if ((rc = sc.get(&tmaxb, (size_t)sg.p * sg.n * ((sg.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
+        if ((rc = sc.get(&colexp, (size_t)sg.Mpad))) return rc;
+        if ((rc = sc.get(&ebx, syrktc_ebx_bytes(sg)))) return rc;
         {
             GpProf pf("eig_tables", stream);
-            launch_eig_tables_chunked(s, Xd, yd, tabc, tmaxb, tmax, st, stream);
+            launch_eig_tables_chunked(sg, Xd, yd, tabc, tmaxb, tmax, st, stream);
             gp_note_launches(2);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc(s, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream);
-            if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
+            cudaError_t e = pair ? launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream)
+                                 : launch_syrk_tc(sg, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream);
+            if (e != cudaSuccess) return cuda_err(e, pair ? "syrk_tc2 launch" : "syrk_tc launch");
             gp_note_launches(2);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_scaled(Gpart, bpart, colexp, spl, SYRKTC_TM, s.Mpad, s.M, d, A, b, stream, ex);
+            launch_assemble_scaled(Gpart, bpart, colexp, spl, TT, sg.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
             if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }
@@ -701,6 +728,8 @@ GPFAGP_API const char* gp_strerror(int status) {
 GPFAGP_API void gp_debug_fail_alloc_after(int k) { g_fail_after.store(k > 0 ? k : 0); }
 
 GPFAGP_API void gp_debug_force_escalation(int k) { g_force_escalate.store(k > 0 ? k : 0); }
+
+GPFAGP_API void gp_debug_gram_kernel(int kind) { g_gram_kernel.store(kind >= 0 && kind <= 2 ? kind : 0); }
 
 GPFAGP_API void gp_debug_barrier_timeout(double limit_s, int skip_cta) {
     factor_debug_barrier_timeout(limit_s, skip_cta);

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
 }
 
 // The mixed-precision Gram's assembly, per 32 x 32 block (bi >= bj) of the
-// lower triangle of A: the float-pair partial tiles of the splits (column-
+// lower triangle of A: the float-pair partial tiles (TT x TT) of the splits (column-
 // scaled by 2^(7 - E_m)) are read coalesced along their rows, summed in split
 // order as an unevaluated float pair (exact two-sum, ~46 bits), converted to
 // float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
@@ -79,12 +79,12 @@ __device__ __forceinline__ double noise_diag_entry(const GpShape& s, const doubl
 __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __restrict__ Gpart,
                                                               const double* __restrict__ bpart,
                                                               const int* __restrict__ colexp, SyrkSplit spl,
-                                                              int Mpad, int M, const double* __restrict__ d,
+                                                              int TT, int Mpad, int M, const double* __restrict__ d,
                                                               double* __restrict__ A, double* __restrict__ b,
                                                               GpShape sh, const double* __restrict__ loglam,
                                                               double log_sigma2, double* __restrict__ dout,
                                                               double* __restrict__ Lc) {
-    constexpr int TT = 128, B = 32;
+    constexpr int B = 32;  // TT: the Gram's tile (128, or 256 for the CTA-pair kernel)
     __shared__ double t[B][B + 1];
     __shared__ double sd[B];
     int bi, bj;
@@ -181,7 +181,6 @@ void launch_assemble_f64(const double* Gpart, const double* bpart, int nsplit, i
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& spl,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex) {
-    (void)tile;  // the tensor-core Gram's tiles are 128 x 128
     const int nb = (M + 31) / 32;
     GpShape sh{};
     const double* loglam = nullptr;
@@ -195,7 +194,7 @@ void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int*
         Lc = ex->L;
     }
     assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
-        Gpart, bpart, colexp, spl, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
+        Gpart, bpart, colexp, spl, tile, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

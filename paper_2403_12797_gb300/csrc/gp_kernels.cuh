@@ -73,7 +73,21 @@ struct AssembleExtra {
     double* dout;
     double* L;
 };
-// float-pair partials of the tensor-core Gram: A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
+// ---- the tensor-core Gram on CTA pairs (gp_syrk_tc2.cu) --------------------------
+// 256 x 256 tile pairs, one cluster of two CTAs each (tcgen05 cta_group::2); the
+// same arithmetic and outputs as launch_syrk_tc with tiles of 256: s.Mpad a
+// multiple of 256, SyrkSplit classes over the 256-column tiles, Gpart
+// (split * npairs + pair) x 256 x 256 float pairs. For p <= 4 when the
+// pipeline fits shared memory (syrktc2_supported).
+bool syrktc2_supported(const GpShape& s);
+// clusters of the kernel that are resident at once on device dev
+int syrktc2_max_clusters(const GpShape& s, int dev);
+cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned int* tmaxb, const unsigned int* tmax,
+                            const SyrkSplit& sp, float2* Gpart, double* bpart, int* colexp, signed char* ebx,
+                            GpStatus* st, cudaStream_t stream);
+
+// float-pair partials of the tensor-core Gram (tile x tile partial tiles, tile
+// 128 or 256): A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex = nullptr);

@@ -54,18 +54,17 @@
 // of pair (SyrkSplit: diagonal pairs generate one operand tile and take
 // longer splits; the pairs (I, 0) also form b), so the classes end together.
 // Split partials are summed and unscaled in float64 by gp_assemble.cu.
-#include "gp_kernels.cuh"
-#include "gp_tc.cuh"
+#include "gp_syrk_tc.cuh"
 
 namespace {
 
+using namespace gpsyrk;
+
 constexpr int TM = SYRKTC_TM;              // 128
 constexpr int CW = SYRKTC_BK;              // 32 rows per table chunk
-constexpr int WS = SYRKTC_WS;              // floats per window row (36: bank-conflict padding)
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
 constexpr int FLUSH_BLOCKS = 4;            // blocks summed in the TMEM float32 sum between flushes
-constexpr uint32_t LBO = 128;              // K-adjacent core matrices
 // A pipeline stage holds H table chunks (KS = 32 H rows; H = 2 unless the
 // windows of two chunks do not fit): per-stage costs -- waits, arrivals, the
 // MMA issue -- are paid once per KS rows.
@@ -101,9 +100,6 @@ struct SmemTC {
     uint64_t* drained;    // acc1 and acc2 have been read back (count NPROD)
     uint32_t* tmem_base;
 };
-
-__host__ __device__ inline int max_ranges(int p) { return 4 * p + 1; }
-__host__ __device__ inline int win_floats(int maxrows) { return (2 * maxrows + 1) * WS; }
 
 __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, int nwr, int H, char* base,
                                                   SmemTC* L) {
@@ -177,35 +173,6 @@ __global__ void colexp_kernel(GpShape s, const unsigned int* __restrict__ tmaxb,
     }
 }
 
-// 2^k for -126 <= k <= 127, exactly
-__device__ __forceinline__ float pow2i(int k) { return __int_as_float((127 + k) << 23); }
-// 2^k for k <= 0, flushed to 0 below 2^-126 (a block whose column bound is
-// that far below the column's global bound adds nothing representable)
-__device__ __forceinline__ float pow2_down(int k) { return k < -126 ? 0.f : __int_as_float((127 + k) << 23); }
-
-// Copy ranges of one tile's window (thread 0): dimension j's window rows
-// are the digits first .. first+count-1 (mod n), i.e. at most two
-// contiguous runs of table rows j*n + digit.
-__device__ int tile_ranges(const GpShape& s, const TileWindow& w, int dst0, int* rng, int nr) {
-    for (int j = 0; j < s.p; ++j) {
-        const int cnt = w.count[j];
-        if (cnt <= 0) continue;
-        const int first = w.first[j];
-        const int run = min(cnt, s.n - first);
-        rng[3 * nr] = j * s.n + first;
-        rng[3 * nr + 1] = run;
-        rng[3 * nr + 2] = dst0 + w.base[j];
-        ++nr;
-        if (cnt > run) {
-            rng[3 * nr] = j * s.n;
-            rng[3 * nr + 1] = cnt - run;
-            rng[3 * nr + 2] = dst0 + w.base[j] + run;
-            ++nr;
-        }
-    }
-    return nr;
-}
-
 // Phi values of one column for data rows 8g..8g+7 of the chunk: the product
 // over dimensions of the column's window rows, whose float offsets woff[j]
 // (window row x WS) are held in registers; woff[0] < 0 marks a padding
@@ -238,45 +205,6 @@ __device__ __forceinline__ void phi8(const float* win, const int* woff, const un
     } else {
         for (int j = 1; j < p; ++j) mul_row(crr[j] * WS);
     }
-}
-
-__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// Scale 8 values by sc and split each into the integer s1 = rint(w)
-// (|s1| <= 128, exact in fp16) and the remainder lo = fp16(w - s1)
-// (|lo| <= 1/2, 11-bit precision, subnormals below 2^-14); store both
-// core-matrix rows. The float-to-integer rounding and float16 packing
-// instructions run at a fraction of the FMA rate, so s1 avoids both: adding
-// the magic K = 1.5 * 2^23 + 0x6480 (still in [2^23, 2^24), where floats
-// are the integers) rounds w to the nearest integer k (ties to even), and
-// the low 16 bits of the sum t are then 0x6480 + k -- the float16 bit
-// pattern of 1152 + k (exponent 2^10) -- for |k| <= 128, with no carry out
-// of the half word. One byte permute packs two of them and one exact half2
-// subtraction of 1152 leaves k. Only the remainder takes a float16
-// conversion.
-template <uint32_t SBO>
-__device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile, int r, int g,
-                                             const float v[8], float sc) {
-    constexpr float kMagic = 12608640.0f;  // 1.5 * 2^23 + 0x6480
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        // v * sc is exact (sc is a power of two), so one rounding each: t rounds
-        // v sc + K to an integer, a = rint(v sc), lo = v sc - a exactly
-        const float t0 = __fmaf_rn(v[2 * q], sc, kMagic), t1 = __fmaf_rn(v[2 * q + 1], sc, kMagic);
-        const float a0 = __fsub_rn(t0, kMagic), a1 = __fsub_rn(t1, kMagic);
-        const uint32_t raw = __byte_perm((uint32_t)__float_as_int(t0), (uint32_t)__float_as_int(t1), 0x5410);
-        uint32_t k2;
-        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(k2) : "r"(raw), "r"(0x64806480u));  // - (1152, 1152)
-        h[q] = k2;
-        l[q] = pack_half2(__fmaf_rn(v[2 * q], sc, -a0), __fmaf_rn(v[2 * q + 1], sc, -a1));
-    }
-    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(r & 7) * 16;
-    *reinterpret_cast<uint4*>(s1_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise;
@@ -689,6 +617,13 @@ int syrk_tc_stages(const GpShape& s, int maxrows, int* H, int* nwr, size_t* smem
 
 }  // namespace
 
+void launch_colexp(const GpShape& s, const unsigned int* tmaxb, const unsigned int* tmax, int* colexp,
+                   signed char* ebx, cudaStream_t stream) {
+    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
+    colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
+        s, tmaxb, tmax, nblk, colexp, ebx);
+}
+
 size_t syrktc_smem_bytes(const GpShape& s) {
     size_t smem = 0;
     int nwr = 0, H = 0;
@@ -711,9 +646,7 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
     int nwr = 0, H = 1;
     const int nst = syrk_tc_stages(s, maxrows, &H, &nwr, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
-    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
-    colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
-        s, tmaxb, tmax, nblk, colexp, ebx);
+    launch_colexp(s, tmaxb, tmax, colexp, ebx, stream);
     const int T = s.Mpad / TM;
     const int64_t items = (int64_t)T * sp.n[0] + (int64_t)(T - 1) * sp.n[1] + (int64_t)(T - 1) * (T - 2) / 2 * sp.n[2];
     dim3 grid((unsigned)items);

@@ -47,16 +47,56 @@ GRAM_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec,kernel", [("fp64", 0), ("mixed", 1), ("mixed", 2)])
 @pytest.mark.parametrize("seed,N,p,n", GRAM_CASES)
-def test_gram_matches_oracle(prec, seed, N, p, n):
+def test_gram_matches_oracle(prec, kernel, seed, N, p, n):
+    """Mixed mode through both tensor-core Gram kernels: kernel 1 runs one CTA
+    per 128 x 128 tile pair, kernel 2 a CTA pair per 256 x 256 tile pair
+    (cta_group::2) wherever it applies (p <= 4; the p > 4 cases fall back to
+    kernel 1), on every shape here: one tile, ragged M and N, N = 1."""
     pr = W.random_problem(seed, N, 1, p, n, eps=1.1, alpha=0.9)
-    G, b = _lib.gram(pr.X, pr.y, n, pr.eps, pr.alpha, prec=prec)
+    _lib.debug_gram_kernel(kernel)
+    try:
+        G, b = _lib.gram(pr.X, pr.y, n, pr.eps, pr.alpha, prec=prec)
+    finally:
+        _lib.debug_gram_kernel(0)
     Go, bo = O.gram(pr.X, pr.y, n, pr.eps, pr.alpha)
     tol_g = TOL_G_MIXED_HIGH_P if (prec == "mixed" and p > 4) else TOL[prec]["G"]
     assert O.relerr(G, Go) < tol_g, O.relerr(G, Go)
     assert O.relerr(b, bo) < TOL_B[prec], O.relerr(b, bo)
     np.testing.assert_array_equal(G, G.T)
+
+
+@pytest.mark.parametrize("N,p,n", [(70_000, 3, 16), (40_000, 2, 32), (30_000, 4, 6), (25_000, 1, 700)])
+def test_gram_kernels_agree_at_large_m(N, p, n):
+    """The two mixed Gram kernels on the same rows at M = 4096, 1024, 1296, 700:
+    both within the mixed tolerance of the oracle, and within 1e-6 of each
+    other (the same Phi values and slices; only the order of the exact block
+    folds differs)."""
+    pr = W.random_problem(71 + p, N, 1, p, n, eps=1.2, alpha=1.0, law="normal", scale=0.5)
+    out = []
+    for kernel in (1, 2):
+        _lib.debug_gram_kernel(kernel)
+        try:
+            out.append(_lib.gram(pr.X, pr.y, n, pr.eps, pr.alpha, prec="mixed"))
+        finally:
+            _lib.debug_gram_kernel(0)
+    (G1, b1), (G2, b2) = out
+    assert O.relerr(G2, G1) < 1e-6, O.relerr(G2, G1)
+    assert O.relerr(b2, b1) < 1e-7, O.relerr(b2, b1)
+    np.testing.assert_array_equal(G2, G2.T)
+    # the oracle on a row sample: the Gram is a sum over rows, so the first
+    # 8,192 rows' Gram from each kernel must match the oracle's
+    Ns = 8192
+    Go, bo = O.gram(pr.X[:Ns], pr.y[:Ns], n, pr.eps, pr.alpha)
+    for kernel in (1, 2):
+        _lib.debug_gram_kernel(kernel)
+        try:
+            G, b = _lib.gram(pr.X[:Ns], pr.y[:Ns], n, pr.eps, pr.alpha, prec="mixed")
+        finally:
+            _lib.debug_gram_kernel(0)
+        assert O.relerr(G, Go) < TOL["mixed"]["G"], (kernel, O.relerr(G, Go))
+        assert O.relerr(b, bo) < TOL_B["mixed"], (kernel, O.relerr(b, bo))
 
 
 def _fit_predict(pr, prec, var=True):
