@@ -273,7 +273,8 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         const int TT = pair ? 256 : SYRKTC_TM;
         float* tabc;
-        float2* Gpart;
+        float2* Gpart = nullptr;   // one-CTA kernel: float-pair partial tiles
+        double* Gpart2 = nullptr;  // CTA pairs: float64 partial tiles
         double* bpart;
         if ((rc = sc.get(&tabc, syrktc_table_floats(sg)))) return rc;
         const int T = sg.Mpad / TT;
@@ -286,7 +287,11 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         } else {
             choose_splits_tc(T, sg.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &spl);
         }
-        if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * TT * TT))) return rc;
+        if (pair) {
+            if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
+        } else {
+            if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * TT * TT))) return rc;
+        }
         if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
         int* colexp;
@@ -302,14 +307,17 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = pair ? launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream)
+            cudaError_t e = pair ? launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart2, bpart, colexp, ebx, st, stream)
                                  : launch_syrk_tc(sg, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream);
             if (e != cudaSuccess) return cuda_err(e, pair ? "syrk_tc2 launch" : "syrk_tc launch");
             gp_note_launches(2);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_scaled(Gpart, bpart, colexp, spl, TT, sg.Mpad, s.M, d, A, b, stream, ex);
+            if (pair)
+                launch_assemble_pair(Gpart2, bpart, colexp, spl, sg.Mpad, s.M, d, A, b, stream, ex);
+            else
+                launch_assemble_scaled(Gpart, bpart, colexp, spl, TT, sg.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
             if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }

@@ -76,7 +76,11 @@ __device__ __forceinline__ double noise_diag_entry(const GpShape& s, const doubl
 // With loglam given, the diagonal of A gets d_m computed here (and stored in
 // dout) instead of read from d; with L given, the lower triangle of A is also
 // written there (the Cholesky's input), which saves a separate copy.
-__global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __restrict__ Gpart,
+// PAIR: float64 partials of the CTA-pair kernel (256 x 256 tiles in the order
+// of gp_pair_tile_offset), summed in split order in float64; otherwise
+// float-pair partials (TT x TT, row-major) summed as float pairs.
+template <bool PAIR>
+__global__ void __launch_bounds__(1024) assemble_scaled_kernel(const void* __restrict__ Gpv,
                                                               const double* __restrict__ bpart,
                                                               const int* __restrict__ colexp, SyrkSplit spl,
                                                               int TT, int Mpad, int M, const double* __restrict__ d,
@@ -124,17 +128,27 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const float2* __r
         double v = 0.0;
         if (r < M && c < M && c <= r) {
             const int I = r / TT, J = c / TT;
-            const int64_t off = (int64_t)(I * (I + 1) / 2 + J) * TT * TT + (int64_t)(r % TT) * TT + (c % TT);
             const int pc = syrk_pair_class(I, J);
             const int nsplit = pc == 0 ? spl.n[0] : (pc == 1 ? spl.n[1] : spl.n[2]);  // this pair's splits
-            float hi = 0.f, lo = 0.f;
-            for (int sp = 0; sp < nsplit; ++sp) {
-                const float2 g = Gpart[off + sp * sstride];
-                add2(hi, lo, g.x);
-                lo = __fadd_rn(lo, g.y);
+            double sum;
+            if constexpr (PAIR) {
+                const double* Gpart = reinterpret_cast<const double*>(Gpv);
+                const int64_t off = (int64_t)(I * (I + 1) / 2 + J) * TT * TT + gp_pair_tile_offset(r % TT, c % TT);
+                sum = 0.0;
+                for (int sp = 0; sp < nsplit; ++sp) sum += Gpart[off + sp * sstride];
+            } else {
+                const float2* Gpart = reinterpret_cast<const float2*>(Gpv);
+                const int64_t off = (int64_t)(I * (I + 1) / 2 + J) * TT * TT + (int64_t)(r % TT) * TT + (c % TT);
+                float hi = 0.f, lo = 0.f;
+                for (int sp = 0; sp < nsplit; ++sp) {
+                    const float2 g = Gpart[off + sp * sstride];
+                    add2(hi, lo, g.x);
+                    lo = __fadd_rn(lo, g.y);
+                }
+                sum = (double)hi + (double)lo;
             }
             const int e = colexp[r] + colexp[c] - 14;  // |e| well inside float64's exponent range
-            v = ((double)hi + (double)lo) * __hiloint2double((e + 1023) << 20, 0);
+            v = sum * __hiloint2double((e + 1023) << 20, 0);
             if (r == c) v += sd[ty];
             A[(int64_t)r * M + c] = v;
             if (Lc != nullptr) Lc[(int64_t)r * M + c] = v;
@@ -193,8 +207,27 @@ void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int*
         dout = ex->dout;
         Lc = ex->L;
     }
-    assemble_scaled_kernel<<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
+    assemble_scaled_kernel<false><<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
         Gpart, bpart, colexp, spl, tile, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
+}
+
+void launch_assemble_pair(const double* Gpart, const double* bpart, const int* colexp, const SyrkSplit& spl,
+                          int Mpad, int M, const double* d, double* A, double* b, cudaStream_t stream,
+                          const AssembleExtra* ex) {
+    const int nb = (M + 31) / 32;
+    GpShape sh{};
+    const double* loglam = nullptr;
+    double lsig = 0.0;
+    double *dout = nullptr, *Lc = nullptr;
+    if (ex != nullptr) {
+        sh = *ex->shape;
+        loglam = ex->loglam;
+        lsig = log(ex->sigma2);
+        dout = ex->dout;
+        Lc = ex->L;
+    }
+    assemble_scaled_kernel<true><<<(unsigned)(nb * (nb + 1) / 2), 1024, 0, stream>>>(
+        Gpart, bpart, colexp, spl, 256, Mpad, M, d, A, b, sh, loglam, lsig, dout, Lc);
 }
 
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,

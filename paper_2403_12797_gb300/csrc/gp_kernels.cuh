@@ -80,10 +80,20 @@ struct AssembleExtra {
 // (split * npairs + pair) x 256 x 256 float pairs. For p <= 4 when the
 // pipeline fits shared memory (syrktc2_supported).
 bool syrktc2_supported(const GpShape& s);
+// Partial tiles of the CTA-pair kernel: float64, one 256 x 256 tile per (split,
+// pair) at (split * npairs + pair) * 65536, element (R, C) of the tile (R the
+// A index, C the B index) at the offset below -- the order in which each warp
+// of the kernel drains TMEM (CTA rank, column group, 4-column chunk, lane
+// quarter, lane, column), so that one warp's 32 x 4 chunk is 1 KB contiguous.
+__host__ __device__ __forceinline__ int gp_pair_tile_offset(int R, int C) {
+    const int rank = R >> 7, quarter = (R >> 5) & 3, lane = R & 31;
+    const int cgrp = C >> 6, ch = (C >> 2) & 15, cc = C & 3;
+    return ((((rank * 4 + cgrp) * 16 + ch) * 4 + quarter) * 32 + lane) * 4 + cc;
+}
 // clusters of the kernel that are resident at once on device dev
 int syrktc2_max_clusters(const GpShape& s, int dev);
 cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned int* tmaxb, const unsigned int* tmax,
-                            const SyrkSplit& sp, float2* Gpart, double* bpart, int* colexp, signed char* ebx,
+                            const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
                             GpStatus* st, cudaStream_t stream);
 
 // float-pair partials of the tensor-core Gram (tile x tile partial tiles, tile
@@ -91,6 +101,10 @@ cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned 
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex = nullptr);
+// the same from the CTA-pair kernel's float64 partial tiles (gp_pair_tile_offset)
+void launch_assemble_pair(const double* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
+                          int Mpad, int M, const double* d, double* A, double* b, cudaStream_t stream,
+                          const AssembleExtra* ex = nullptr);
 // d_m = sigma2 * exp(-sum_j loglam[m_j]) clamped at 1e200 (Eq. 16, 20)
 void launch_noise_diag(const GpShape& s, const double* loglam, double sigma2, double* d,
                        cudaStream_t stream);

@@ -28,8 +28,17 @@
 //     that the 8 threads of a quarter-warp store into 8 different 16-byte
 //     rows of a core matrix (no bank conflicts).
 //   * TMEM holds acc1 (256 columns) and acc2 (256 columns): there is no room
-//     for a float32 sum of blocks, so every block is folded into the
-//     L2-resident partial tile directly; the next block's MMAs wait for it.
+//     for a float32 sum of blocks, so every block is folded into the split's
+//     float64 partial tile as soon as it is done. A producer warp turns its
+//     32 rows x 4 columns of the block sum into float64 (exactly, by integer
+//     bit manipulation: GB300's float64 pipe is slow), stages them in
+//     shared memory and hands them to the bulk-copy engine: a store for the
+//     split's first block, an atomic float64 add (cp.reduce.async.bulk) after
+//     that. The MMAs of the next block wait only for the TMEM reads, not for
+//     L2. Each drain first waits for the warp's previous block of bulk
+//     operations to complete, so every element's additions happen in block
+//     order and the result is bit-reproducible. The partial tile's layout
+//     (gp_pair_tile_offset) makes each warp's chunk one contiguous 1 KB.
 //
 // Roles (576 threads per CTA, one CTA per SM):
 //   warps 0-15  producers: generation (warps 0-7 the A half, 8-15 the B
@@ -82,6 +91,7 @@ struct Smem2 {
     int* rng;             // copy ranges (table row, rows, window row)
     double* bred;         // TM: b of the second row-group half (cross-warp sum)
     double* bsum;         // 256 x 4: float64 sums of b per A-half producer thread and column
+    double* dstage;       // NPW x 2 x 128: per warp, two 1 KB slices of block sums for the bulk engine
     uint64_t* full;       // STAGES: leader's, 2 NPROD arrivals (both CTAs)
     uint64_t* empty;      // STAGES: one commit (multicast) per phase
     uint64_t* tfull;      // WRMAX: window landed
@@ -108,6 +118,7 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
     size_t oR = take(sizeof(int) * 3 * max_ranges(p), 16);
     size_t oB = take(sizeof(double) * TM, 16);
     size_t oBS = take(sizeof(double) * 256 * 4, 16);
+    size_t oDS = take(sizeof(double) * NPW * 2 * 128, 128);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
     size_t oX = take(sizeof(uint64_t) * WRMAX, 8);
@@ -125,6 +136,7 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
         L->rng = (int*)(base + oR);
         L->bred = (double*)(base + oB);
         L->bsum = (double*)(base + oBS);
+        L->dstage = (double*)(base + oDS);
         L->full = (uint64_t*)(base + oF);
         L->empty = (uint64_t*)(base + oE);
         L->tfull = (uint64_t*)(base + oX);
@@ -153,7 +165,7 @@ template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc2_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
                     const int* __restrict__ colexp, SyrkSplit sp, int T, int maxrows, int nst, int nwr,
-                    float2* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
+                    double* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
     __shared__ int s_nrng;
@@ -297,12 +309,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // drain: TMEM lanes 32 quarter .. (A-half rows), columns CPT cgrp ..
         const int quarter = warp & 3, cgrp = warp >> 2;
         const int drow = quarter * 32 + lane;
-        float2* grow = Gpart + ((int64_t)split * npairs + q) * (TP * TP) + (int64_t)(rank * TM + drow) * TP +
-                       cgrp * CPT;
+        // this warp's chunks of the split's partial tile: chunk ch (4 columns
+        // x 32 rows, 128 float64) at gtile + ch * 512 (gp_pair_tile_offset)
+        double* gtile = Gpart + ((int64_t)split * npairs + q) * (TP * TP) +
+                        (int64_t)gp_pair_tile_offset((int)rank * TM + quarter * 32, cgrp * CPT);
+        double* dst = sm.dstage + warp * 256;  // two 1 KB slices
         const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + cgrp * CPT;
         const uint32_t full_l0 = mapa_shared(sm.full, 0);
         const uint32_t drained_l0 = mapa_shared(sm.drained, 0);
-        bool fresh = true;  // the partial tile holds no fold yet
+        bool fresh = true;  // the partial tile holds no block yet
         bool ok = true;
         const int blk0 = (int)(r0 / GP_TAB_BLOCK);
         auto arrive_leader = [&](uint64_t* local, uint32_t leader_addr) {
@@ -311,53 +326,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             else
                 mbar_arrive_remote(leader_addr);
         };
+        // float -> float64 bit pattern, exactly (zero and subnormals -> 0: a
+        // block value below 2^-126 of the global scale adds nothing measurable)
+        auto f64bits = [](float g) -> uint2 {
+            const uint32_t b = __float_as_uint(g);
+            const bool z = (b & 0x7F800000u) == 0u;
+            const uint32_t hi = (b & 0x80000000u) | (((b >> 3) & 0x0FFFFFFFu) + 0x38000000u);
+            return make_uint2(z ? 0u : (b << 29), z ? 0u : hi);  // (low word, high word)
+        };
         auto drain = [&](int d) -> bool {
             if (!__all_sync(FULLMASK, mbar_wait(sm.accf, d & 1))) {
                 if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 14);
                 return false;
             }
             tc_fence_after();
+            // the previous block's bulk operations of this warp are complete:
+            // its additions precede this block's, and the slices are free
+            if (lane == 0) bulk_wait_all();
+            __syncwarp();
             // back to the global column scaling: 2^(E_blk - E_glob) (exact powers of two)
             const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
             const float mrow = pow2_down((int)eb[I * TM + drow] - sm.egI[drow]);
             const signed char* ebc = eb + J2 * TP + cgrp * CPT;
             const int* egc = sm.egJ + cgrp * CPT;
-            float4* g4 = reinterpret_cast<float4*>(grow);  // (hi, lo) of two columns
-            auto add2 = [](float& hi, float& lo, float v) {  // hi + v = s + e exactly; lo collects e
-                const float sum = __fadd_rn(hi, v);
-                const float t = __fsub_rn(sum, hi);
-                const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, t)), __fsub_rn(v, t));
-                hi = sum;
-                lo = __fadd_rn(lo, e);
-            };
 #pragma unroll 1
             for (int ch = 0; ch < CPT / 4; ++ch) {
-                // four columns: acc1 + acc2 rescaled, two-summed into (hi, lo)
-                float4 o[2];
-                if (!fresh) {
-                    o[0] = g4[ch * 2];
-                    o[1] = g4[ch * 2 + 1];
-                } else {
-                    o[0] = o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                double* slice = dst + (ch & 1) * 128;
+                if (ch >= 2) {
+                    if (lane == 0) bulk_wait_read<1>();  // the slice's previous chunk has been read
+                    __syncwarp();
                 }
                 uint32_t a1[4], a2[4];
                 tmem_ld4_nowait(tmem + lrow + ch * 4, a1);
                 tmem_ld4_nowait(tmem + lrow + TP + ch * 4, a2);
                 const int e4 = *reinterpret_cast<const int*>(ebc + ch * 4);
                 tmem_wait_ld();
-                float g[4];
+                uint2 w[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int eblk = (int)(signed char)(e4 >> (8 * i));
-                    g[i] = (__uint_as_float(a1[i]) + __uint_as_float(a2[i])) *
-                           (mrow * pow2_down(eblk - egc[ch * 4 + i]));
+                    w[i] = f64bits((__uint_as_float(a1[i]) + __uint_as_float(a2[i])) *
+                                   (mrow * pow2_down(eblk - egc[ch * 4 + i])));
                 }
-                add2(o[0].x, o[0].y, g[0]);
-                add2(o[0].z, o[0].w, g[1]);
-                add2(o[1].x, o[1].y, g[2]);
-                add2(o[1].z, o[1].w, g[3]);
-                g4[ch * 2] = o[0];
-                g4[ch * 2 + 1] = o[1];
+                uint4* sl = reinterpret_cast<uint4*>(slice + lane * 4);
+                sl[0] = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
+                sl[1] = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (fresh)
+                        bulk_s2g(gtile + ch * 512, slice, 1024);
+                    else
+                        bulk_add_f64_s2g(gtile + ch * 512, slice, 1024);
+                    bulk_commit();
+                }
             }
             fresh = false;
             tc_fence_before();
@@ -491,9 +513,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
         if (nblocks == 0) {  // a split without rows: its partial tile is zero
-#pragma unroll 4
-            for (int k = 0; k < CPT; ++k) grow[k] = make_float2(0.f, 0.f);
+            for (int ch = 0; ch < CPT / 4; ++ch)
+                reinterpret_cast<double4*>(gtile + ch * 512)[lane] = make_double4(0.0, 0.0, 0.0, 0.0);
         }
+        // every bulk operation of this warp has completed before the CTA ends
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer (leader CTA)
         if (rank == 0 && lane == 0) {
@@ -609,7 +634,7 @@ int syrk_tc2_stages(const GpShape& s, int maxrows, int* nwr, size_t* smem) {
 
 template <int P>
 cudaError_t go2(const GpShape& s, const float* tabc, const signed char* ebx, const int* colexp, const SyrkSplit& sp,
-                int T, int maxrows, int nst, int nwr, size_t smem, float2* Gpart, double* bpart, GpStatus* st,
+                int T, int maxrows, int nst, int nwr, size_t smem, double* Gpart, double* bpart, GpStatus* st,
                 cudaStream_t stream) {
     const void* kern = (const void*)syrk_tc2_kernel<P>;
     cudaError_t e = gp_allow_max_smem(kern);
@@ -689,7 +714,7 @@ int syrktc2_max_clusters(const GpShape& s, int dev) {
 }
 
 cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned int* tmaxb, const unsigned int* tmax,
-                            const SyrkSplit& sp, float2* Gpart, double* bpart, int* colexp, signed char* ebx,
+                            const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
                             GpStatus* st, cudaStream_t stream) {
     if (!syrktc2_supported(s)) return cudaErrorInvalidValue;
     for (int c = 0; c < 3; ++c)
