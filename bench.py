@@ -206,8 +206,11 @@ def roofline_of(name, groups, pr, prec, steps, pk, profile_name, peak_kind):
     """Roofline object of one kernel group: algorithmic work per launch over its
     average CUDA-event launch time inside the timed steps."""
     M, N, Ns = pr.M, pr.N, pr.Ns
+    # the mixed Gram runs on CTA pairs (gp_syrk_tc2.cu) for M > 512 (p <= 4)
+    pair = M > 512 and pr.p <= 4
     work = {
-        "syrk_tc": ("tensor", N * M * (M + 1) + 2 * N * M, "TFLOP/s", "gp_syrk_tc.cu"),
+        "syrk_tc": ("tensor", N * M * (M + 1) + 2 * N * M, "TFLOP/s",
+                    "gp_syrk_tc2.cu" if pair else "gp_syrk_tc.cu"),
         "predict_tc": ("tensor", Ns * M * (M + 1) + 4 * Ns * M, "TFLOP/s", "gp_predict_tc.cu"),
         "cholesky": ("alu", M ** 3 / 3, "TFLOP/s", "gp_factor.cu"),
         "tri_inverse": ("alu", M ** 3 / 3, "TFLOP/s", "gp_factor.cu"),
@@ -226,6 +229,8 @@ def roofline_of(name, groups, pr, prec, steps, pk, profile_name, peak_kind):
         peak, psrc = FP64_PEAK_TFLOPS, "nominal fp64 (2 DFMA/clock/SM x 152 SMs x 2.07 GHz)"
     else:
         peak, psrc = FP32_SIMT_PEAK_TFLOPS, "fp32 SIMT from unit counts and clocks"
+    if name == "syrk_tc" and pair:
+        profile_name = profile_name.replace("syrk_tc", "syrk_tc2")
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic_from_profile(src, profile_name),
             "peak_source": psrc, "avg_launch_ms": per_launch_ms, "units_per_launch": units}

@@ -84,6 +84,36 @@ __device__ __forceinline__ void store_slices(uint8_t* s1_tile, uint8_t* lo_tile,
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// 32-bit shared-space accesses (no generic-address arithmetic). Volatile, so
+// they keep their order relative to the pipeline's barrier waits.
+__device__ __forceinline__ void lds_row8(uint32_t a, float v[8]) {
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(a));
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4+16];"
+                 : "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "r"(a));
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+// The split of store_slices into registers: s1 (h) and lo (l) of 8 values
+// scaled by the power of two sc, two fp16 per word, low element first.
+__device__ __forceinline__ void split8(const float v[8], float sc, uint32_t h[4], uint32_t l[4]) {
+    constexpr float kMagic = 12608640.0f;  // 1.5 * 2^23 + 0x6480
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float t0 = __fmaf_rn(v[2 * q], sc, kMagic), t1 = __fmaf_rn(v[2 * q + 1], sc, kMagic);
+        const float a0 = __fsub_rn(t0, kMagic), a1 = __fsub_rn(t1, kMagic);
+        const uint32_t raw = __byte_perm((uint32_t)__float_as_int(t0), (uint32_t)__float_as_int(t1), 0x5410);
+        uint32_t k2;
+        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(k2) : "r"(raw), "r"(0x64806480u));  // - (1152, 1152)
+        h[q] = k2;
+        l[q] = pack_half2(__fmaf_rn(v[2 * q], sc, -a0), __fmaf_rn(v[2 * q + 1], sc, -a1));
+    }
+}
+
 }  // namespace gpsyrk
 
 // column exponents of the mixed Gram (gp_syrk_tc.cu): ebx[b * Mpad + m] = E_m of

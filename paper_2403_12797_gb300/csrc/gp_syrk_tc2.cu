@@ -297,6 +297,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (((wpk[k][j >> 1] >> (16 * (j & 1))) & 0xFFFFu) != ((wpk[0][j >> 1] >> (16 * (j & 1))) & 0xFFFFu))
                     shared = false;
         auto woff = [&](int k, int j) -> int { return (int)((wpk[k][j >> 1] >> (16 * (j & 1))) & 0xFFFFu); };
+        // 32-bit shared-space addresses: the stage's operand tiles and the
+        // window slot move per stage, the thread's offsets inside them do not
+        const uint32_t stage_s = smem_u32(sm.stage) + (uint32_t)(tsel * 2 * TILE);
+        const uint32_t win_s = smem_u32(sm.win) + 4u * (uint32_t)(hh * wsz1 + 8 * gg);
+        uint32_t so[4];  // the columns' core-matrix rows in an operand tile (K group g8)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            so[k] = (uint32_t)(colk(k) >> 3) * SBO + (uint32_t)g8 * LBO + (uint32_t)(colk(k) & 7) * 16;
         const int twin = (tsel == 1 && !diag) ? nrowsI * WS : 0;  // this tile's window in the chunk window
         const int ywin = (nwin - 1) * WS;
         const int mtile = (tsel ? J : I) * TM;
@@ -422,25 +430,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             if (gen) {
-                uint8_t* s1t = sm.stage + (size_t)stg * SBYTES + tsel * 2 * TILE;
-                uint8_t* lot = s1t + TILE;
-                const float* wbase = sm.win + wsl * wsz + hh * wsz1 + 8 * gg;
-                const float* wt = wbase + twin;
+                const uint32_t sb = stage_s + (uint32_t)(stg * SBYTES);
+                const uint32_t wb = win_s + 4u * (uint32_t)(wsl * wsz);
+                const uint32_t wt = wb + 4u * (uint32_t)twin;
                 float yv[8];
-                if (with_b) ld_row8(wbase + ywin, yv);
+                if (with_b) lds_row8(wb + 4u * (uint32_t)ywin, yv);
                 if (P >= 2 && shared) {
                     // the upper dimensions' product once, then one row and one multiply a column
                     float pre[8];
-                    ld_row8(wt + woff(0, 0), pre);
+                    lds_row8(wt + 4u * (uint32_t)woff(0, 0), pre);
 #pragma unroll
-                    for (int j = 1; j + 1 < P; ++j) mul_row8(wt + woff(0, j), pre);
+                    for (int j = 1; j + 1 < P; ++j) {
+                        float r[8];
+                        lds_row8(wt + 4u * (uint32_t)woff(0, j), r);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) pre[i] *= r[i];
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         float v[8];
-                        ld_row8(wt + woff(k, P - 1), v);
+                        lds_row8(wt + 4u * (uint32_t)woff(k, P - 1), v);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) v[i] = pre[i] * v[i];
-                        store_slices<SBO>(s1t, lot, colk(k), g8, v, sc[k]);
+                        uint32_t h[4], l[4];
+                        split8(v, sc[k], h, l);
+                        sts128(sb + so[k], h[0], h[1], h[2], h[3]);
+                        sts128(sb + TILE + so[k], l[0], l[1], l[2], l[3]);
                         if (with_b) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) bacc[k] = fmaf(v[i], yv[i], bacc[k]);
@@ -454,11 +469,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int i = 0; i < 8; ++i) v[i] = 0.f;
                         } else {
-                            ld_row8(wt + woff(k, 0), v);
+                            lds_row8(wt + 4u * (uint32_t)woff(k, 0), v);
 #pragma unroll
-                            for (int j = 1; j < P; ++j) mul_row8(wt + woff(k, j), v);
+                            for (int j = 1; j < P; ++j) {
+                                float r[8];
+                                lds_row8(wt + 4u * (uint32_t)woff(k, j), r);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) v[i] *= r[i];
+                            }
                         }
-                        store_slices<SBO>(s1t, lot, colk(k), g8, v, sc[k]);
+                        uint32_t h[4], l[4];
+                        split8(v, sc[k], h, l);
+                        sts128(sb + so[k], h[0], h[1], h[2], h[3]);
+                        sts128(sb + TILE + so[k], l[0], l[1], l[2], l[3]);
                         if (with_b) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) bacc[k] = fmaf(v[i], yv[i], bacc[k]);
