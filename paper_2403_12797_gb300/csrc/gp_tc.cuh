@@ -76,15 +76,32 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity, uint32_
     return ok != 0;
 }
 
+// One potentially blocking try without a suspend-time hint: the hardware
+// holds the thread for a short, system-defined time and returns as soon as
+// the phase completes. (With a long hint the wait is served by sleeping and
+// re-polling, whose wake-up granularity delays the pipeline.)
+__device__ __forceinline__ bool mbar_try0(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete; false on timeout.
-// The first suspended try normally returns with the phase complete; the
-// clock (a slow special-register read) is consulted only after that.
+// The clock (a slow special-register read) is consulted only every 64 tries
+// after the first failed one.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (mbar_try(bar, parity, 1000000u)) return true;
+    if (mbar_try0(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
+    uint32_t it = 0;
     while (true) {
-        if (mbar_try(bar, parity, 1000000u)) return true;
-        if (globaltimer_ns() - t0 > GP_WAIT_NS) return false;
+        if (mbar_try0(bar, parity)) return true;
+        if ((++it & 63u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) return false;
     }
 }
 
@@ -371,12 +388,24 @@ __device__ __forceinline__ bool mbar_try_cl(uint64_t* bar, uint32_t parity, uint
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_try0_cl(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity) {
-    if (mbar_try_cl(bar, parity, 1000000u)) return true;
+    if (mbar_try0_cl(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
+    uint32_t it = 0;
     while (true) {
-        if (mbar_try_cl(bar, parity, 1000000u)) return true;
-        if (globaltimer_ns() - t0 > GP_WAIT_NS) return false;
+        if (mbar_try0_cl(bar, parity)) return true;
+        if ((++it & 63u) == 0 && globaltimer_ns() - t0 > GP_WAIT_NS) return false;
     }
 }
 
