@@ -129,12 +129,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (tid == 0) {
         for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&full[i], NPROD);
+            mbar_init(&full[i], NPW);
             mbar_init(&wfull[i], 1);
             mbar_init(&empty[i], 1);
         }
         mbar_init(accf, 1);
-        mbar_init(tfree, NPROD);
+        mbar_init(tfree, NPW);
         mbar_fence_init();
     }
     // the zero window row of every stage (columns beyond M map to it)
@@ -202,8 +202,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     *reinterpret_cast<uint4*>(sb + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
                 if (last) macc += (double)mpart;
+                // every lane's operand writes before the async proxy's reads;
+                // one arrival per warp
                 fence_proxy_async_smem();
-                mbar_arrive(&full[stg]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[stg]);
             }
             if (!ok) break;
             // epilogue of this super-tile: rows of Z from TMEM
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(tfree);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tfree);
         }
         pok = ok;
         if (hf == 1) {

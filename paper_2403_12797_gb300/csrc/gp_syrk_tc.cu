@@ -92,12 +92,12 @@ struct SmemTC {
     unsigned short* crI;  // TM x p: window row of (column, dimension)
     unsigned short* crJ;
     int* rng;             // copy ranges (table row, rows, window row), 3 ints each
-    uint64_t* full;       // STAGES: producers' tiles published (count NPROD)
+    uint64_t* full;       // STAGES: producers' tiles published (one arrival per producer warp)
     uint64_t* empty;      // STAGES: MMAs of the stage done
     uint64_t* tfull;      // WRMAX: window landed (count 1 + tx bytes)
     uint64_t* wempty;     // WRMAX: every producer warp has read the window (count NPW)
     uint64_t* accf;       // the block's MMAs are done (acc1, acc2 final)
-    uint64_t* drained;    // acc1 and acc2 have been read back (count NPROD)
+    uint64_t* drained;    // acc1 and acc2 have been read back (one arrival per producer warp)
     uint32_t* tmem_base;
 };
 
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         sm.rng[3 * nr + 2] = nwin0;
         s_nrng = nr + 1;
         for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&sm.full[i], NPROD);
+            mbar_init(&sm.full[i], NPW);
             mbar_init(&sm.empty[i], 1);
         }
         for (int i = 0; i < WRMAX; ++i) {
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.wempty[i], NPW);
         }
         mbar_init(sm.accf, 1);
-        mbar_init(sm.drained, NPROD);
+        mbar_init(sm.drained, NPW);
         mbar_fence_init();
     }
     if (warp == MMA_WARP) tmem_alloc(sm.tmem_base, TMEM_COLS);
@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (fold) flushed = true;
             tmem_wait_st();
             tc_fence_before();
-            mbar_arrive(sm.drained);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(sm.drained);
             return true;
         };
 
@@ -460,10 +461,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     store_slices<GM::SBO>(sb + 2 * GM::TILE, sb + 3 * GM::TILE, r, kg, v, scJ);
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
+            // every lane's operand writes are ordered before the async proxy's
+            // reads; one arrival per warp after the warp barrier
             fence_proxy_async_smem();
-            mbar_arrive(&sm.full[stg]);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
+                mbar_arrive(&sm.full[stg]);
+            }
             if (++stg == nst) {
                 stg = 0;
                 sph ^= 1;

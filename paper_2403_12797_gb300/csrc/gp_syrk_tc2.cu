@@ -47,10 +47,13 @@
 //   warp 16     TMEM allocation (both CTAs); in the leader, one lane issues
 //               the pair's MMAs and commits them to both CTAs' barriers;
 //   warp 17     bulk (TMA) copies of this CTA's table windows.
-// Handshakes across the pair: the producers of both CTAs arrive on the
-// leader's `full` and `drained` barriers (the peer through its shared::cluster
-// address, release at cluster scope); the leader's commits arrive on `empty`
-// and `accf` in both CTAs. Every wait is bounded (GP_ETIMEOUT).
+// Handshakes across the pair: one lane of each producer warp of both CTAs
+// arrives on the leader's `full` and `drained` barriers (the peer through its
+// shared::cluster address, release at cluster scope) once the warp is done;
+// the leader's commits arrive on `empty` and `accf` in both CTAs. Arriving
+// per warp instead of per thread matters: a remote arrival crosses the SM
+// pair, and 512 of them per stage cost more than the stage's MMAs. Every
+// wait is bounded (GP_ETIMEOUT).
 #include "gp_syrk_tc.cuh"
 
 #include <algorithm>
@@ -92,12 +95,12 @@ struct Smem2 {
     double* bred;         // TM: b of the second row-group half (cross-warp sum)
     double* bsum;         // 256 x 4: float64 sums of b per A-half producer thread and column
     double* dstage;       // NPW x 2 x 128: per warp, two 1 KB slices of block sums for the bulk engine
-    uint64_t* full;       // STAGES: leader's, 2 NPROD arrivals (both CTAs)
+    uint64_t* full;       // STAGES: leader's, one arrival per producer warp of both CTAs
     uint64_t* empty;      // STAGES: one commit (multicast) per phase
     uint64_t* tfull;      // WRMAX: window landed
     uint64_t* wempty;     // WRMAX: every producer warp has read the window
     uint64_t* accf;       // the block's MMAs are done (multicast commit)
-    uint64_t* drained;    // leader's: both CTAs have folded the block
+    uint64_t* drained;    // leader's: every producer warp of both CTAs has read the block's TMEM
     uint32_t* tmem_base;
 };
 
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         sm.rng[3 * nr + 2] = nwin0;
         s_nrng = nr + 1;
         for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&sm.full[i], 2 * NPROD);
+            mbar_init(&sm.full[i], 2 * NPW);
             mbar_init(&sm.empty[i], 1);
         }
         for (int i = 0; i < WRMAX; ++i) {
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.wempty[i], NPW);
         }
         mbar_init(sm.accf, 1);
-        mbar_init(sm.drained, 2 * NPROD);
+        mbar_init(sm.drained, 2 * NPW);
         mbar_fence_init();
     }
     if (warp == MMA_WARP) tmem_alloc_pair(sm.tmem_base, TMEM_COLS);
@@ -391,7 +394,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             fresh = false;
             tc_fence_before();
-            arrive_leader(sm.drained, drained_l0);
+            __syncwarp();
+            if (lane == 0) arrive_leader(sm.drained, drained_l0);
             return true;
         };
 
@@ -489,10 +493,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
+            // every lane's operand writes are ordered before the async proxy's
+            // reads, then one arrival for the warp (release: it carries the
+            // lanes' writes, ordered before it by the warp barrier)
             fence_proxy_async_smem();
-            arrive_leader(&sm.full[stg], full_l0 + 8u * (uint32_t)stg);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sm.wempty[wsl]);  // this warp is done with the window
+                arrive_leader(&sm.full[stg], full_l0 + 8u * (uint32_t)stg);
+            }
             if (++stg == nst) {
                 stg = 0;
                 sph ^= 1;
