@@ -83,12 +83,14 @@ bool syrktc2_supported(const GpShape& s);
 // Partial tiles of the CTA-pair kernel: float64, one 256 x 256 tile per (split,
 // pair) at (split * npairs + pair) * 65536, element (R, C) of the tile (R the
 // A index, C the B index) at the offset below -- the order in which each warp
-// of the kernel drains TMEM (CTA rank, column group, 4-column chunk, lane
-// quarter, lane, column), so that one warp's 32 x 4 chunk is 1 KB contiguous.
+// of the kernel drains TMEM (CTA rank, column group, round of 16 columns, lane
+// quarter; inside a round, column pairs, lane, column), so that one warp's
+// round (32 rows x 16 columns) is 4 KB contiguous and is staged in shared
+// memory without bank conflicts.
 __host__ __device__ __forceinline__ int gp_pair_tile_offset(int R, int C) {
     const int rank = R >> 7, quarter = (R >> 5) & 3, lane = R & 31;
-    const int cgrp = C >> 6, ch = (C >> 2) & 15, cc = C & 3;
-    return ((((rank * 4 + cgrp) * 16 + ch) * 4 + quarter) * 32 + lane) * 4 + cc;
+    const int cgrp = C >> 6, rnd = (C >> 4) & 3, cc = C & 15;
+    return ((((rank * 4 + cgrp) * 4 + rnd) * 4 + quarter) << 9) + (((cc >> 1) * 32 + lane) << 1) + (cc & 1);
 }
 // clusters of the kernel that are resident at once on device dev
 int syrktc2_max_clusters(const GpShape& s, int dev);

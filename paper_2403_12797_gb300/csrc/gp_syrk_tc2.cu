@@ -29,16 +29,18 @@
 //     rows of a core matrix (no bank conflicts).
 //   * TMEM holds acc1 (256 columns) and acc2 (256 columns): there is no room
 //     for a float32 sum of blocks, so every block is folded into the split's
-//     float64 partial tile as soon as it is done. A producer warp turns its
-//     32 rows x 4 columns of the block sum into float64 (exactly, by integer
-//     bit manipulation: GB300's float64 pipe is slow), stages them in
-//     shared memory and hands them to the bulk-copy engine: a store for the
-//     split's first block, an atomic float64 add (cp.reduce.async.bulk) after
-//     that. The MMAs of the next block wait only for the TMEM reads, not for
-//     L2. Each drain first waits for the warp's previous block of bulk
-//     operations to complete, so every element's additions happen in block
-//     order and the result is bit-reproducible. The partial tile's layout
-//     (gp_pair_tile_offset) makes each warp's chunk one contiguous 1 KB.
+//     float64 partial tile as soon as it is done. In four rounds of 16
+//     columns a producer warp reads its 32 rows of acc1 and acc2, rescales
+//     the block sums (factors the loader warp prepared per block), turns them
+//     into float64 exactly by integer bit manipulation (GB300's float64 pipe
+//     is slow), stages the 4 KB in the operand slot of the block's last stage
+//     (its MMAs are done) and hands it to the bulk-copy engine: a store for
+//     the split's first block, an atomic float64 add (cp.reduce.async.bulk)
+//     after that. The next block's MMAs wait only for the TMEM reads, not for
+//     L2. Each drain first waits for the warp's previous bulk operations to
+//     complete, so every element's additions happen in block order and the
+//     result is bit-reproducible. The partial tile's layout
+//     (gp_pair_tile_offset) makes each warp's round one contiguous 4 KB.
 //
 // Roles (576 threads per CTA, one CTA per SM):
 //   warps 0-15  producers: generation (warps 0-7 the A half, 8-15 the B
@@ -46,7 +48,8 @@
 //               the pairs (I2, 0), and the per-block drain of TMEM;
 //   warp 16     TMEM allocation (both CTAs); in the leader, one lane issues
 //               the pair's MMAs and commits them to both CTAs' barriers;
-//   warp 17     bulk (TMA) copies of this CTA's table windows.
+//   warp 17     bulk (TMA) copies of this CTA's table windows, and each
+//               block's rescaling factors for the drains.
 // Handshakes across the pair: one lane of each producer warp of both CTAs
 // arrives on the leader's `full` and `drained` barriers (the peer through its
 // shared::cluster address, release at cluster scope) once the warp is done;
@@ -94,13 +97,15 @@ struct Smem2 {
     int* rng;             // copy ranges (table row, rows, window row)
     double* bred;         // TM: b of the second row-group half (cross-warp sum)
     double* bsum;         // 256 x 4: float64 sums of b per A-half producer thread and column
-    double* dstage;       // NPW x 2 x 128: per warp, two 1 KB slices of block sums for the bulk engine
+    float* msc;           // 2 x (TP + TM): per 1024-row block (double-buffered by parity), the
+                          // B columns' and A-half rows' scales 2^(E_blk - E_glob), from the loader
     uint64_t* full;       // STAGES: leader's, one arrival per producer warp of both CTAs
     uint64_t* empty;      // STAGES: one commit (multicast) per phase
     uint64_t* tfull;      // WRMAX: window landed
     uint64_t* wempty;     // WRMAX: every producer warp has read the window
     uint64_t* accf;       // the block's MMAs are done (multicast commit)
     uint64_t* drained;    // leader's: every producer warp of both CTAs has read the block's TMEM
+    uint64_t* staged;     // every producer warp of this CTA has finished its drain's staging reads
     uint32_t* tmem_base;
 };
 
@@ -121,13 +126,14 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
     size_t oR = take(sizeof(int) * 3 * max_ranges(p), 16);
     size_t oB = take(sizeof(double) * TM, 16);
     size_t oBS = take(sizeof(double) * 256 * 4, 16);
-    size_t oDS = take(sizeof(double) * NPW * 2 * 128, 128);
+    size_t oMS = take(sizeof(float) * 2 * (TP + TM), 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
     size_t oX = take(sizeof(uint64_t) * WRMAX, 8);
     size_t oY = take(sizeof(uint64_t) * WRMAX, 8);
     size_t oA = take(sizeof(uint64_t), 8);
     size_t oD = take(sizeof(uint64_t), 8);
+    size_t oG = take(sizeof(uint64_t), 8);
     size_t oT = take(sizeof(uint32_t), 8);
     if (L) {
         L->stage = (uint8_t*)(base + oS);
@@ -139,13 +145,14 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
         L->rng = (int*)(base + oR);
         L->bred = (double*)(base + oB);
         L->bsum = (double*)(base + oBS);
-        L->dstage = (double*)(base + oDS);
+        L->msc = (float*)(base + oMS);
         L->full = (uint64_t*)(base + oF);
         L->empty = (uint64_t*)(base + oE);
         L->tfull = (uint64_t*)(base + oX);
         L->wempty = (uint64_t*)(base + oY);
         L->accf = (uint64_t*)(base + oA);
         L->drained = (uint64_t*)(base + oD);
+        L->staged = (uint64_t*)(base + oG);
         L->tmem_base = (uint32_t*)(base + oT);
     }
     return off + 1024;  // slack for aligning the dynamic base
@@ -240,6 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mbar_init(sm.accf, 1);
         mbar_init(sm.drained, 2 * NPW);
+        mbar_init(sm.staged, NPW);
         mbar_fence_init();
     }
     if (warp == MMA_WARP) tmem_alloc_pair(sm.tmem_base, TMEM_COLS);
@@ -320,17 +328,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // drain: TMEM lanes 32 quarter .. (A-half rows), columns CPT cgrp ..
         const int quarter = warp & 3, cgrp = warp >> 2;
         const int drow = quarter * 32 + lane;
-        // this warp's chunks of the split's partial tile: chunk ch (4 columns
-        // x 32 rows, 128 float64) at gtile + ch * 512 (gp_pair_tile_offset)
+        // this warp's rounds of the split's partial tile: round r (16 columns
+        // x 32 rows, 512 float64) at gtile + r * 2048 (gp_pair_tile_offset)
         double* gtile = Gpart + ((int64_t)split * npairs + q) * (TP * TP) +
                         (int64_t)gp_pair_tile_offset((int)rank * TM + quarter * 32, cgrp * CPT);
-        double* dst = sm.dstage + warp * 256;  // two 1 KB slices
         const uint32_t lrow = ((uint32_t)(quarter * 32) << 16) + cgrp * CPT;
         const uint32_t full_l0 = mapa_shared(sm.full, 0);
         const uint32_t drained_l0 = mapa_shared(sm.drained, 0);
         bool fresh = true;  // the partial tile holds no block yet
         bool ok = true;
-        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
         auto arrive_leader = [&](uint64_t* local, uint32_t leader_addr) {
             if (rank == 0)
                 mbar_arrive(local);
@@ -352,53 +358,69 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
             // the previous block's bulk operations of this warp are complete:
-            // its additions precede this block's, and the slices are free
+            // its additions precede this block's
             if (lane == 0) bulk_wait_all();
             __syncwarp();
-            // back to the global column scaling: 2^(E_blk - E_glob) (exact powers of two)
-            const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
-            const float mrow = pow2_down((int)eb[I * TM + drow] - sm.egI[drow]);
-            const signed char* ebc = eb + J2 * TP + cgrp * CPT;
-            const int* egc = sm.egJ + cgrp * CPT;
-#pragma unroll 1
-            for (int ch = 0; ch < CPT / 4; ++ch) {
-                double* slice = dst + (ch & 1) * 128;
-                if (ch >= 2) {
-                    if (lane == 0) bulk_wait_read<1>();  // the slice's previous chunk has been read
+            // scales back to the global column scaling (the loader formed them
+            // for this block and published them with the block's first window)
+            const float* ms = sm.msc + (d & 1) * (TP + TM);
+            const float mrow = ms[TP + drow];
+            const float* mcp = ms + cgrp * CPT;
+            // staging: the operand slot of the block's last stage, whose MMAs
+            // are done and which the producers fill again only after this drain
+            const int clast = min((d + 1) * BLOCK, nchunks) - 1;
+            const uint32_t stg_s = smem_u32(sm.stage) + (uint32_t)((clast % nst) * SBYTES) + (uint32_t)warp * 4096u;
+#pragma unroll
+            for (int rnd = 0; rnd < CPT / 16; ++rnd) {
+                uint32_t a1[16], a2[16];
+                tmem_ld16_nowait(tmem + lrow + rnd * 16, a1);
+                tmem_ld16_nowait(tmem + lrow + TP + rnd * 16, a2);
+                tmem_wait_ld();
+                if (rnd == CPT / 16 - 1) {
+                    // every TMEM read of this warp is done: the next block's MMAs may begin
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) arrive_leader(sm.drained, drained_l0);
+                }
+                if (rnd > 0) {
+                    if (lane == 0) bulk_wait_read<0>();  // the previous round has left the staging
                     __syncwarp();
                 }
-                uint32_t a1[4], a2[4];
-                tmem_ld4_nowait(tmem + lrow + ch * 4, a1);
-                tmem_ld4_nowait(tmem + lrow + TP + ch * 4, a2);
-                const int e4 = *reinterpret_cast<const int*>(ebc + ch * 4);
-                tmem_wait_ld();
-                uint2 w[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int eblk = (int)(signed char)(e4 >> (8 * i));
-                    w[i] = f64bits((__uint_as_float(a1[i]) + __uint_as_float(a2[i])) *
-                                   (mrow * pow2_down(eblk - egc[ch * 4 + i])));
+                for (int qq = 0; qq < 8; ++qq) {
+                    const float2 mc = *reinterpret_cast<const float2*>(mcp + rnd * 16 + 2 * qq);
+                    const uint2 w0 = f64bits((__uint_as_float(a1[2 * qq]) + __uint_as_float(a2[2 * qq])) * (mrow * mc.x));
+                    const uint2 w1 =
+                        f64bits((__uint_as_float(a1[2 * qq + 1]) + __uint_as_float(a2[2 * qq + 1])) * (mrow * mc.y));
+                    sts128(stg_s + (uint32_t)((qq * 32 + lane) * 16), w0.x, w0.y, w1.x, w1.y);
                 }
-                uint4* sl = reinterpret_cast<uint4*>(slice + lane * 4);
-                sl[0] = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
-                sl[1] = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
+                    const void* src = __cvta_shared_to_generic(stg_s);
                     if (fresh)
-                        bulk_s2g(gtile + ch * 512, slice, 1024);
+                        bulk_s2g(gtile + rnd * 2048, src, 4096);
                     else
-                        bulk_add_f64_s2g(gtile + ch * 512, slice, 1024);
+                        bulk_add_f64_s2g(gtile + rnd * 2048, src, 4096);
                     bulk_commit();
                 }
             }
             fresh = false;
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) arrive_leader(sm.drained, drained_l0);
+            // the staging slot is written again by the next stages -- of any
+            // producer warp, whose tiles span the slot: wait until every warp's
+            // staging has been read
+            if (lane == 0) {
+                bulk_wait_read<0>();
+                mbar_arrive(sm.staged);
+            }
+            if (!__all_sync(FULLMASK, mbar_wait(sm.staged, d & 1))) {
+                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 17);
+                return false;
+            }
             return true;
         };
 
+        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
         // per-column block exponents, loaded one block ahead
         int e[4] = {0, 0, 0, 0};
         if (nblocks > 0) {
@@ -545,8 +567,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
         if (nblocks == 0) {  // a split without rows: its partial tile is zero
-            for (int ch = 0; ch < CPT / 4; ++ch)
-                reinterpret_cast<double4*>(gtile + ch * 512)[lane] = make_double4(0.0, 0.0, 0.0, 0.0);
+            for (int k = lane; k < (CPT / 16) * 512 / 4; k += 32)
+                reinterpret_cast<double4*>(gtile)[(k / 128) * 512 + (k % 128)] = make_double4(0.0, 0.0, 0.0, 0.0);
         }
         // every bulk operation of this warp has completed before the CTA ends
         if (lane == 0) bulk_wait_all();
@@ -555,7 +577,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ MMA issuer (leader CTA)
         if (rank == 0 && lane == 0) {
             const uint32_t idesc = idesc_f16_f32(TP, TP);
-            const uint32_t sbase = smem_u32(sm.stage);
+            // descriptors of stage 0's four tiles; a stage adds SBYTES / 16 and
+            // a 16-row K step 2 LBO / 16 to the address field (no carry out of
+            // it: shared addresses stay below 256 KB)
+            const uint64_t dA1_0 = smem_desc(smem_u32(sm.stage), LBO, SBO);
+            const uint64_t dA2_0 = dA1_0 + (uint64_t)(TILE >> 4);
+            const uint64_t dB1_0 = diag ? dA1_0 : dA1_0 + (uint64_t)(2 * TILE >> 4);
+            const uint64_t dB2_0 = diag ? dA2_0 : dA1_0 + (uint64_t)(3 * TILE >> 4);
             int stg = 0, sph = 0, issued = 0;
             for (int c = 0; c < nchunks; ++c) {
                 const int d = c / BLOCK, cb = c % BLOCK;
@@ -571,22 +599,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t acc1 = tmem;
                 const uint32_t acc2 = tmem + TP;
-                const uint32_t a1 = sbase + stg * SBYTES;
-                const uint32_t a2 = a1 + TILE;
-                const uint32_t b1 = diag ? a1 : a1 + 2 * TILE;
-                const uint32_t b2 = diag ? a2 : a1 + 3 * TILE;
+                const uint64_t so = (uint64_t)(stg * (SBYTES >> 4));
 #pragma unroll
                 for (int ks = 0; ks < KS / 16; ++ks) {
-                    const uint32_t ko = ks * 2 * LBO;
-                    const uint64_t dA1 = smem_desc(a1 + ko, LBO, SBO);
-                    const uint64_t dA2 = smem_desc(a2 + ko, LBO, SBO);
-                    const uint64_t dB1 = smem_desc(b1 + ko, LBO, SBO);
-                    const uint64_t dB2 = smem_desc(b2 + ko, LBO, SBO);
+                    const uint64_t ko = so + (uint64_t)(ks * (2 * LBO >> 4));
                     const uint32_t acc = (cb > 0 || ks > 0) ? 1u : 0u;
-                    mma_f16_pair(acc1, dA1, dB1, idesc, acc);  // s1 s1'  (exact)
-                    mma_f16_pair(acc2, dA1, dB2, idesc, acc);  // s1 lo'
-                    mma_f16_pair(acc2, dA2, dB1, idesc, 1u);   // lo s1'
-                    mma_f16_pair(acc2, dA2, dB2, idesc, 1u);   // lo lo'
+                    mma_f16_pair(acc1, dA1_0 + ko, dB1_0 + ko, idesc, acc);  // s1 s1'  (exact)
+                    mma_f16_pair(acc2, dA1_0 + ko, dB2_0 + ko, idesc, acc);  // s1 lo'
+                    mma_f16_pair(acc2, dA2_0 + ko, dB1_0 + ko, idesc, 1u);   // lo s1'
+                    mma_f16_pair(acc2, dA2_0 + ko, dB2_0 + ko, idesc, 1u);   // lo lo'
                 }
                 mma_commit_pair(&sm.empty[stg], (uint16_t)3);
                 if (cb == BLOCK - 1 || c == nchunks - 1) mma_commit_pair(sm.accf, (uint16_t)3);
@@ -613,12 +634,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             rsrc = sm.rng[3 * k] * WS;
             rlen = sm.rng[3 * k + 1] * WS * 4;
         }
+        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
         int c = 0, wsl = 0, wph = 0;
         for (; c < nchunks; ++c) {
             const bool e = c < nwr || mbar_wait(&sm.wempty[wsl], wph ^ 1);
             if (!__all_sync(FULLMASK, e)) {
                 if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 16);
                 break;
+            }
+            if (c % BLOCK == 0) {
+                // the block's rescaling factors 2^(E_blk - E_glob) for the drains
+                // (exact powers of two); the buffer of this parity was last read
+                // by the drain of block d - 2, which every producer warp finished
+                // before releasing the window slot this copy waited for; the
+                // arrival below publishes them with the block's first window
+                const int d = c / BLOCK;
+                const signed char* eb = ebx + (int64_t)(blk0 + d) * s.Mpad;
+                float* ms = sm.msc + (d & 1) * (TP + TM);
+                for (int k = lane; k < TP + TM; k += 32)
+                    ms[k] = k < TP ? pow2_down((int)eb[J2 * TP + k] - sm.egJ[k])
+                                   : pow2_down((int)eb[I * TM + (k - TP)] - sm.egI[k - TP]);
+                __syncwarp();
             }
             if (lane == 0) mbar_arrive_expect_tx(&sm.tfull[wsl], wbytes);
             __syncwarp();
