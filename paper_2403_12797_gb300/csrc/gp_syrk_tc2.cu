@@ -343,13 +343,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             else
                 mbar_arrive_remote(leader_addr);
         };
-        // float -> float64 bit pattern, exactly (zero and subnormals -> 0: a
-        // block value below 2^-126 of the global scale adds nothing measurable)
+        // float -> float64 bit pattern by integer operations: exact for normal
+        // floats; zero and subnormals become +-2^-127-ish values, below any
+        // block sum's rounding (the block sums are of order one or larger in
+        // these units, and a column whose scale would underflow is flushed to
+        // zero by pow2_down before this)
         auto f64bits = [](float g) -> uint2 {
             const uint32_t b = __float_as_uint(g);
-            const bool z = (b & 0x7F800000u) == 0u;
-            const uint32_t hi = (b & 0x80000000u) | (((b >> 3) & 0x0FFFFFFFu) + 0x38000000u);
-            return make_uint2(z ? 0u : (b << 29), z ? 0u : hi);  // (low word, high word)
+            const uint32_t hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u);
+            return make_uint2(b << 29, hi);  // (low word, high word)
         };
         auto drain = [&](int d) -> bool {
             if (!__all_sync(FULLMASK, mbar_wait(sm.accf, d & 1))) {
@@ -382,18 +384,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     __syncwarp();
                     if (lane == 0) arrive_leader(sm.drained, drained_l0);
                 }
+                uint2 w[16];
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const float2 mc = *reinterpret_cast<const float2*>(mcp + rnd * 16 + i);
+                    w[i] = f64bits((__uint_as_float(a1[i]) + __uint_as_float(a2[i])) * (mrow * mc.x));
+                    w[i + 1] = f64bits((__uint_as_float(a1[i + 1]) + __uint_as_float(a2[i + 1])) * (mrow * mc.y));
+                }
                 if (rnd > 0) {
-                    if (lane == 0) bulk_wait_read<0>();  // the previous round has left the staging
+                    // the previous round has left the staging (its read overlapped
+                    // this round's TMEM read and conversion)
+                    if (lane == 0) bulk_wait_read<0>();
                     __syncwarp();
                 }
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    const float2 mc = *reinterpret_cast<const float2*>(mcp + rnd * 16 + 2 * qq);
-                    const uint2 w0 = f64bits((__uint_as_float(a1[2 * qq]) + __uint_as_float(a2[2 * qq])) * (mrow * mc.x));
-                    const uint2 w1 =
-                        f64bits((__uint_as_float(a1[2 * qq + 1]) + __uint_as_float(a2[2 * qq + 1])) * (mrow * mc.y));
-                    sts128(stg_s + (uint32_t)((qq * 32 + lane) * 16), w0.x, w0.y, w1.x, w1.y);
-                }
+                for (int qq = 0; qq < 8; ++qq)
+                    sts128(stg_s + (uint32_t)((qq * 32 + lane) * 16), w[2 * qq].x, w[2 * qq].y, w[2 * qq + 1].x,
+                           w[2 * qq + 1].y);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
