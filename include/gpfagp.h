@@ -118,6 +118,19 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
                          double eps, double alpha, double sigma2, int prec,
                          void* cuda_stream, int dev_ptrs, gp_model** out);
 
+/* gp_fit_ex for the ARD kernel (Eq. 17): eps[j] and alpha[j], j = 0 .. p-1
+ * (host arrays of p values, copied), give dimension j its own SE shape
+ * parameter epsilon_j and eigen-decomposition scale rho_j, hence its own
+ * eigenvalues and eigenfunctions (Eq. 14-16 per dimension); the
+ * tensor-product basis (Eq. 18-20) and everything after it are unchanged.
+ * With all eps[j] equal and all alpha[j] equal it computes exactly what
+ * gp_fit_ex computes. The model predicts, reports its likelihood and serves
+ * like any other. Errors as gp_fit_ex (GP_EINVAL for a non-positive or
+ * non-finite eps[j] or alpha[j], or NULL arrays). */
+GPFAGP_API int gp_fit_ard_ex(const double* X, const double* y, int64_t N, int p, int n,
+                             const double* eps, const double* alpha, double sigma2, int prec,
+                             void* cuda_stream, int dev_ptrs, gp_model** out);
+
 /* gp_predict with an explicit stream and pointer kind. The prediction uses
  * the model's precision mode. */
 GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
@@ -150,6 +163,22 @@ GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, in
  * (NULL h, y or out, or N different from the fit's), or an error status. */
 GPFAGP_API int gp_model_log_marginal(const gp_model* h, const double* y, int64_t N, double* out,
                                      void* cuda_stream, int dev_ptrs);
+
+/* log p(y) as gp_model_log_marginal, and its derivative with respect to the
+ * noise variance sigma^2 at fixed eps and alpha -- the noise part of the
+ * gradient that hyperparameter learning follows (Sec. 4, future work).
+ * Differentiating the terms above, with A = G + diag(d), d_m = sigma^2 /
+ * lambda_m and E = dA / d sigma^2 = diag(e), e_m = d_m / sigma^2 (0 where d_m
+ * is clamped at 1e200):
+ *   d log p / d sigma^2 = -1/2 [ c^T E c / sigma^2 - (y^T y - b^T c) / sigma^4
+ *                                + N / sigma^2 + tr(A^{-1} E) - n_u / sigma^2 ],
+ * n_u the unclamped columns, tr(A^{-1} E) = sum_m e_m |W[:, m]|^2 with
+ * W = L^{-1}. The float64 model keeps W; for a mixed model W is formed again
+ * from L (float32, the inverse kernel of the fit) during the call. Sums in
+ * float64, fixed order. y, N, pointer kind and errors as
+ * gp_model_log_marginal; *lml and *dlml_dsigma2 receive the results. */
+GPFAGP_API int gp_model_log_marginal_grad(const gp_model* h, const double* y, int64_t N, double* lml,
+                                          double* dlml_dsigma2, void* cuda_stream, int dev_ptrs);
 
 /* Model shape and mode: any output pointer may be NULL. */
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);

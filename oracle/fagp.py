@@ -326,6 +326,104 @@ def log_marginal_likelihood_dsigma2(model: Dict[str, np.ndarray], y: np.ndarray)
                    + e @ diag_Ainv - np.count_nonzero(free) / s2)
 
 
+def se_constants_grad(eps: float, rho: float):
+    """Partial derivatives of beta, delta^2 and rho beta (Eq. 14, delta^2 with
+    the rho^2 reading) with respect to eps and rho, by the chain rule:
+      beta = (1 + 4 eps^2 / rho^2)^(1/4):
+        d beta / d eps = 2 eps / (rho^2 beta^3),  d beta / d rho = -2 eps^2 / (rho^3 beta^3);
+      delta^2 = rho^2 (beta^2 - 1) / 2:
+        d delta^2 / d eps = rho^2 beta d beta / d eps,
+        d delta^2 / d rho = rho (beta^2 - 1) + rho^2 beta d beta / d rho.
+    Returns {theta: (d beta, d delta^2, d (rho beta))} for theta in 'eps', 'rho'."""
+    beta, _ = se_constants(eps, rho)
+    db_de = 2.0 * eps / (rho ** 2 * beta ** 3)
+    db_dr = -2.0 * eps ** 2 / (rho ** 3 * beta ** 3)
+    dd_de = rho ** 2 * beta * db_de
+    dd_dr = rho * (beta ** 2 - 1.0) + rho ** 2 * beta * db_dr
+    return {"eps": (db_de, dd_de, rho * db_de), "rho": (db_dr, dd_dr, beta + rho * db_dr)}
+
+
+def eigenfunctions_1d_grad(x: np.ndarray, n: int, eps: float, rho: float, theta: str) -> np.ndarray:
+    """d phi_i(x) / d theta for theta in 'eps', 'rho' (Eq. 15), shape x.shape + (n,).
+
+    phi_i = gamma_i e^{-delta^2 x^2} H_{i-1}(t), t = rho beta x, gamma_i^2 =
+    beta / (2^{i-1} (i-1)!). The product rule gives
+      d phi_i = phi_i (d log gamma_i - x^2 d delta^2) + gamma_i e^{-delta^2 x^2} H'_{i-1}(t) x d(rho beta),
+    with d log gamma_i = (d beta) / (2 beta) and H'_k = 2k H_{k-1}, so that
+    gamma_i H'_{i-1} = sqrt(2 (i-1)) (gamma_{i-1} H_{i-2}) -- the previous
+    column of the same eigenfunction table without its envelope.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    beta, delta2 = se_constants(eps, rho)
+    dbeta, ddelta2, drb = se_constants_grad(eps, rho)[theta]
+    phi = eigenfunctions_1d(x, n, eps, rho)
+    env = np.exp(-delta2 * x * x)[..., None]
+    q = phi / env                                   # gamma_i H_{i-1}(t)
+    dq = np.zeros_like(q)                           # gamma_i H'_{i-1}(t)
+    k = np.arange(1, n, dtype=np.float64)
+    dq[..., 1:] = np.sqrt(2.0 * k) * q[..., :-1]
+    xx = x[..., None]
+    return phi * (0.5 * dbeta / beta - xx * xx * ddelta2) + env * dq * xx * drb
+
+
+def log_eigenvalues_grad(n: int, p: int, eps: float, rho: float, theta: str) -> np.ndarray:
+    """d log lambda_m / d theta for the tensor-product eigenvalues (Eq. 16, 20):
+    log lambda_k = 1/2 log(rho^2 / D) + k log(eps^2 / D), D = rho^2 + delta^2 + eps^2,
+    differentiated through D (and delta^2), summed over the dimensions."""
+    _, delta2 = se_constants(eps, rho)
+    _, ddelta2, _ = se_constants_grad(eps, rho)[theta]
+    D = rho ** 2 + delta2 + eps ** 2
+    if theta == "eps":
+        dD = ddelta2 + 2.0 * eps
+        dl0 = -0.5 * dD / D
+        dr = 2.0 / eps - dD / D
+    else:
+        dD = 2.0 * rho + ddelta2
+        dl0 = 1.0 / rho - 0.5 * dD / D
+        dr = -dD / D
+    dk = dl0 + np.arange(n, dtype=np.float64) * dr  # d log lambda_k, k = 0..n-1
+    idx = multi_index(n, p)
+    return dk[idx].sum(axis=1)
+
+
+def log_marginal_likelihood_grad(X, y, n: int, eps: float, rho: float, sigma2: float):
+    """Gradient (d/d eps, d/d rho, d/d sigma^2) of log p(y) = log N(y; 0, K +
+    sigma^2 I), K = Phi Lambda Phi^T (Eq. 1-2, 7-9), the objective of the
+    hyperparameter learning named as future work in Sec. 4.
+
+    For a parameter theta of K, d log p / d theta = 1/2 a^T (dK) a - 1/2
+    tr(Ky^{-1} dK) with Ky = K + sigma^2 I and a = Ky^{-1} y; dK = dPhi Lambda
+    Phi^T + Phi dLambda Phi^T + Phi Lambda dPhi^T, with dPhi from
+    eigenfunctions_1d_grad through the tensor product (Eq. 19) and dLambda =
+    Lambda diag(d log lambda). For sigma^2, dK = I. Dense N x N; only for
+    small N. (Clamped eigenvalues are not treated: the test problems keep
+    sigma^2 / lambda_m below the clamp.)"""
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    y = np.asarray(y, dtype=np.float64)
+    N, p = X.shape
+    idx = multi_index(n, p)
+    Phi = phi_matrix(X, n, eps, rho)
+    lam = np.exp(log_eigenvalues(n, p, eps, rho))
+    Ky = (Phi * lam) @ Phi.T + sigma2 * np.eye(N)
+    Kinv = np.linalg.inv(Ky)
+    a = Kinv @ y
+    out = []
+    for theta in ("eps", "rho"):
+        E = [eigenfunctions_1d(X[:, j], n, eps, rho) for j in range(p)]
+        dE = [eigenfunctions_1d_grad(X[:, j], n, eps, rho, theta) for j in range(p)]
+        dPhi = np.zeros_like(Phi)
+        for j in range(p):
+            term = np.ones_like(Phi)
+            for i in range(p):
+                term *= (dE[i] if i == j else E[i])[:, idx[:, i]]
+            dPhi += term
+        dlam = lam * log_eigenvalues_grad(n, p, eps, rho, theta)
+        dK = (dPhi * lam) @ Phi.T + (Phi * dlam) @ Phi.T + (Phi * lam) @ dPhi.T
+        out.append(0.5 * a @ dK @ a - 0.5 * np.sum(Kinv * dK.T))
+    out.append(0.5 * a @ a - 0.5 * np.trace(Kinv))
+    return tuple(out)
+
+
 # --------------------------------------------------------------------------
 # Other routes to the same posterior (used to pin the M x M form)
 # --------------------------------------------------------------------------

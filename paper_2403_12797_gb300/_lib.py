@@ -75,11 +75,13 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_last_error_where": (C.c_char_p, []),
         "gp_strerror": (C.c_char_p, [i]),
         "gp_fit_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
+        "gp_fit_ard_ex": (i, [vp, vp, i64, i, i, vp, vp, d, i, vp, i, C.POINTER(vp)]),
         "gp_predict_ex": (i, [vp, vp, i64, vp, vp, vp, i]),
         "gp_fit_predict_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i64, vp, vp, vp, i, C.POINTER(vp)]),
         "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "gp_model_read": (i, [vp, i, vp]),
         "gp_model_log_marginal": (i, [vp, vp, i64, C.POINTER(d), vp, i]),
+        "gp_model_log_marginal_grad": (i, [vp, vp, i64, C.POINTER(d), C.POINTER(d), vp, i]),
         "gp_gram_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, vp, i]),
         "gp_gram_static": (i, [vp, vp, i64, i, i, d, d, vp, vp, vp]),
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
@@ -225,6 +227,22 @@ class Model:
                                            _stream_of(y, stream), dev), "gp_model_log_marginal")
         return float(out.value)
 
+    def log_marginal_grad(self, y, stream=None):
+        """(log p(y), d log p(y) / d sigma^2) of the fitted model (y as in log_marginal)."""
+        if _is_torch(y):
+            import torch
+            if y.dtype != torch.float64 or not y.is_cuda or not y.is_contiguous():
+                raise TypeError("device inputs must be contiguous float64 CUDA tensors")
+            dev = 1
+        else:
+            y = _host(y).reshape(-1)
+            dev = 0
+        v, g = C.c_double(), C.c_double()
+        _check(lib().gp_model_log_marginal_grad(self._h, C.c_void_p(_ptr(y)), int(y.shape[0]), C.byref(v),
+                                                C.byref(g), _stream_of(y, stream), dev),
+               "gp_model_log_marginal_grad")
+        return float(v.value), float(g.value)
+
     def read(self, field: str) -> np.ndarray:
         """Host copy of a fitted quantity: 'L' (M x M), 'c', 'b' or 'd' (M)."""
         out = np.empty((self.M, self.M) if field == "L" else self.M)
@@ -290,6 +308,21 @@ def fit(X, y, n: int, eps: float, alpha: float, sigma2: float, prec: str = "mixe
                          float(alpha), float(sigma2), PREC[prec], _stream_of(X, stream), dev,
                          C.byref(out))
     _check(rc, "gp_fit_ex")
+    return Model(out.value)
+
+
+def fit_ard(X, y, n: int, eps, alpha, sigma2: float, prec: str = "mixed", stream=None) -> Model:
+    """Fit the ARD kernel (Eq. 17): eps and alpha are sequences of p values, one
+    per input dimension (host arrays, copied)."""
+    X, y, N, p, dev = _prep_xy(X, y)
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1))
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+    if e.shape != (p,) or a.shape != (p,):
+        raise ValueError(f"eps and alpha need {p} values each")
+    out = C.c_void_p()
+    rc = lib().gp_fit_ard_ex(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), e.ctypes.data,
+                             a.ctypes.data, float(sigma2), PREC[prec], _stream_of(X, stream), dev, C.byref(out))
+    _check(rc, "gp_fit_ard_ex")
     return Model(out.value)
 
 

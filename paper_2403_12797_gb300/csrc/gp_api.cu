@@ -355,16 +355,28 @@ int model_alloc(gp_model* h, size_t bytes, void** p, cudaStream_t s) {
     return GP_OK;
 }
 
-gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, double alpha, double sigma2) {
+gp_model* new_model(int dev, int prec, int64_t N, int p, int n, const double* eps, const double* alpha,
+                    double sigma2) {
     gp_model* h = new gp_model();
     memset(h, 0, sizeof(*h));
     h->device = dev;
     h->prec = prec;
-    h->eps = eps;
-    h->alpha = alpha;
+    for (int j = 0; j < p; ++j) {
+        h->eps[j] = eps[j];
+        h->alpha[j] = alpha[j];
+    }
     h->sigma2 = sigma2;
-    gp_fill_shape(&h->shape, N, p, n, eps, alpha, tile_of(prec));
+    gp_fill_shape_ard(&h->shape, N, p, n, eps, alpha, tile_of(prec));
     return h;
+}
+
+gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, double alpha, double sigma2) {
+    double e[GP_PMAX], a[GP_PMAX];
+    for (int j = 0; j < GP_PMAX; ++j) {
+        e[j] = eps;
+        a[j] = alpha;
+    }
+    return new_model(dev, prec, N, p, n, e, a, sigma2);
 }
 
 // The model's own device buffers (kept until gp_free).
@@ -427,16 +439,17 @@ void pinned_put(PinnedBlock b) {
     g_pin_free.emplace(b.cap, b.p);
 }
 
-// Copy the shape-only inputs (log eigenvalues, and the predict chunk table
-// into the model) to the device, from pinned staging memory.
+// Copy the shape-only inputs (log eigenvalues of every dimension, loglam[j n +
+// k], and the predict chunk table into the model) to the device, from pinned
+// staging memory.
 int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream) {
     const GpShape& s = h->shape;
     const size_t nci = h->prec != GP_PREC_FP64 ? predtc_cinfo_ints(s) : 0;
-    const size_t lbytes = sizeof(double) * (size_t)s.n;
+    const size_t lbytes = sizeof(double) * (size_t)s.p * s.n;
     stage.buf = pinned_get(lbytes + sizeof(int) * nci);
     if (!stage.buf.p) return set_err(GP_ENOMEM, (int64_t)(lbytes + sizeof(int) * nci));
     double* ll = (double*)stage.buf.p;
-    log_eigenvalues(s.n, h->eps, h->alpha, ll);
+    for (int j = 0; j < s.p; ++j) log_eigenvalues(s.n, h->eps[j], h->alpha[j], ll + (size_t)j * s.n);
     cudaError_t e = cudaMemcpyAsync(loglam_d, ll, lbytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && nci > 0) {
         int* ci = (int*)((char*)stage.buf.p + lbytes);
@@ -689,7 +702,7 @@ int tune_batch(const std::vector<gp_model*>& hs, const std::vector<const double*
 
 using namespace gpi;
 
-int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile) {
+int gp_fill_shape_ard(GpShape* s, int64_t N, int p, int n, const double* eps, const double* alpha, int tile) {
     memset(s, 0, sizeof(*s));
     s->N = N;
     s->Npad = gp_round_up(N > 0 ? N : 1, 128);
@@ -704,11 +717,27 @@ int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha,
         s->stride[j] = (int)st;
         st *= n;
     }
-    const double beta = pow(1.0 + (2.0 * eps / alpha) * (2.0 * eps / alpha), 0.25);
-    s->alpha_beta = alpha * beta;
-    s->delta2 = alpha * alpha * (beta * beta - 1.0) / 2.0;
-    s->sqrt_beta = sqrt(beta);
+    // Eq. 14 per dimension (delta^2 with the rho^2 reading)
+    for (int j = 0; j < p && j < GP_PMAX; ++j) {
+        const double e = eps[j], a = alpha[j];
+        const double beta = pow(1.0 + (2.0 * e / a) * (2.0 * e / a), 0.25);
+        s->ab[j] = a * beta;
+        s->d2[j] = a * a * (beta * beta - 1.0) / 2.0;
+        s->sb[j] = sqrt(beta);
+        s->abf[j] = (float)s->ab[j];
+        s->d2f[j] = (float)s->d2[j];
+        s->sbf[j] = (float)s->sb[j];
+    }
     return GP_OK;
+}
+
+int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile) {
+    double e[GP_PMAX], a[GP_PMAX];
+    for (int j = 0; j < GP_PMAX; ++j) {
+        e[j] = eps;
+        a[j] = alpha;
+    }
+    return gp_fill_shape_ard(s, N, p, n, e, a, tile);
 }
 
 extern "C" {
@@ -810,15 +839,11 @@ GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p
     return GP_OK;
 }
 
-GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
-                         double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
-                         gp_model** out) {
-    set_err(GP_OK);
+namespace {
+// gp_fit_ex with eps_j, alpha_j per dimension (already validated)
+int fit_ex_impl(const double* X, const double* y, int64_t N, int p, int n, const double* eps, const double* alpha,
+                double sigma2, int prec, void* cuda_stream, int dev_ptrs, gp_model** out) {
     int rc, dev;
-    if (!out) return set_err(GP_EINVAL, 0);
-    *out = nullptr;
-    if (!X || !y) return set_err(GP_EINVAL, 0);
-    if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
     if ((rc = check_prec(prec))) return rc;
     if ((rc = check_device(&dev))) return rc;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -837,7 +862,7 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     GpStatus* st;
     double* loglam;
     if ((rc = sc.get(&st, 1))) return fail(rc);
-    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)p * n))) return fail(rc);
     cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
     const double *Xd = X, *yd = y;
     if (!dev_ptrs) {
@@ -864,6 +889,38 @@ GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int
     if (rc) return fail(rc);
     *out = h;
     return GP_OK;
+}
+}  // namespace
+
+GPFAGP_API int gp_fit_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                         double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                         gp_model** out) {
+    set_err(GP_OK);
+    int rc;
+    if (!out) return set_err(GP_EINVAL, 0);
+    *out = nullptr;
+    if (!X || !y) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
+    double e[GP_PMAX], a[GP_PMAX];
+    for (int j = 0; j < GP_PMAX; ++j) {
+        e[j] = eps;
+        a[j] = alpha;
+    }
+    return fit_ex_impl(X, y, N, p, n, e, a, sigma2, prec, cuda_stream, dev_ptrs, out);
+}
+
+GPFAGP_API int gp_fit_ard_ex(const double* X, const double* y, int64_t N, int p, int n, const double* eps,
+                             const double* alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                             gp_model** out) {
+    set_err(GP_OK);
+    int rc;
+    if (!out) return set_err(GP_EINVAL, 0);
+    *out = nullptr;
+    if (!X || !y || !eps || !alpha) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, 1.0, 1.0, sigma2))) return rc;
+    for (int j = 0; j < p; ++j)
+        if (!finite_pos(eps[j]) || !finite_pos(alpha[j])) return set_err(GP_EINVAL, 2);
+    return fit_ex_impl(X, y, N, p, n, eps, alpha, sigma2, prec, cuda_stream, dev_ptrs, out);
 }
 
 namespace {
@@ -919,7 +976,7 @@ GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, in
     GpStatus* st;
     double* loglam;
     if ((rc = sc.get(&st, 1))) return fail(rc);
-    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)p * n))) return fail(rc);
     cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
     const double *Xd = X, *yd = y;
     if (!dev_ptrs) {
@@ -979,7 +1036,7 @@ GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p
     double *loglam, *A, *work;
     unsigned char* fwork;
     if ((rc = sc.get(&st, 1))) return fail(rc);
-    if ((rc = sc.get(&loglam, (size_t)n))) return fail(rc);
+    if ((rc = sc.get(&loglam, (size_t)p * n))) return fail(rc);
     if ((rc = sc.get(&A, (size_t)M * M))) return fail(rc);
     if ((rc = sc.get(&work, solve_refine_work_elems(M)))) return fail(rc);
     if ((rc = sc.get(&fwork, factor_work_bytes(M, prec != GP_PREC_FP64)))) return fail(rc);
@@ -1076,6 +1133,64 @@ GPFAGP_API int gp_model_log_marginal(const gp_model* h, const double* y, int64_t
     return GP_OK;
 }
 
+GPFAGP_API int gp_model_log_marginal_grad(const gp_model* h, const double* y, int64_t N, double* lml,
+                                          double* dlml_dsigma2, void* cuda_stream, int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!h || !y || !lml || !dlml_dsigma2) return set_err(GP_EINVAL, 0);
+    if (N != h->shape.N) return set_err(GP_EINVAL, 1);
+    if ((rc = check_device(&dev))) return rc;
+    if (dev != h->device) return set_err(GP_EINVAL, 5);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const int M = h->shape.M;
+    const int nparts = lml_partial_count(num_sms(dev));
+    Scratch sc(stream);
+    double *part, *terms, *ainv;
+    GpStatus* st;
+    if ((rc = sc.get(&part, (size_t)4 * nparts))) return rc;
+    if ((rc = sc.get(&terms, 8))) return rc;
+    if ((rc = sc.get(&ainv, (size_t)M))) return rc;
+    if ((rc = sc.get(&st, 1))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    const double* yd = y;
+    if (!dev_ptrs) {
+        double* yy;
+        if ((rc = sc.get(&yy, (size_t)N))) return rc;
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        yd = yy;
+    }
+    // diag(A^{-1}) from W = L^{-1}: the float64 model keeps W; for the mixed
+    // model it is formed again from L in float32 (the precision its own
+    // variance uses), in a factor workspace whose barrier header is zeroed here
+    if (h->W != nullptr) {
+        launch_ainv_diag(h->W, false, M, ainv, stream);
+        gp_note_launches(1);
+    } else {
+        unsigned char* fwork;
+        if ((rc = sc.get(&fwork, factor_work_bytes(M, true)))) return rc;
+        cudaMemsetAsync(fwork, 0, 256, stream);
+        cudaError_t e = launch_tri_inverse(h->L, nullptr, M, true, st, fwork, stream);
+        if (e != cudaSuccess) return cuda_err(e, "inverse for the likelihood gradient");
+        const float* Wf = (const float*)(fwork + 256) + (size_t)M * M;
+        launch_ainv_diag(Wf, true, M, ainv, stream);
+        gp_note_launches(1);
+    }
+    launch_lml_terms(yd, N, h->L, h->b, h->c, h->d, M, nparts, part, terms, stream);
+    launch_lml_grad_terms(h->c, h->d, ainv, h->sigma2, M, nparts, part, terms + 4, stream);
+    gp_note_launches(4);
+    double t[8];
+    cudaError_t e = cudaMemcpyAsync(t, terms, sizeof(t), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_err(e, "log marginal likelihood gradient");
+    if ((rc = read_status(st, stream))) return rc;
+    const double s2 = h->sigma2;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double quad = t[0] - t[1];  // y^T y - b^T c
+    *lml = -0.5 * (quad / s2 + (double)N * log(s2) + 2.0 * t[2] - t[3] + (double)N * log(two_pi));
+    // d log p / d sigma^2 = -1/2 [ c^T E c / s2 - quad / s2^2 + N / s2 + tr(A^{-1} E) - n_u / s2 ]
+    *dlml_dsigma2 = -0.5 * (t[4] / s2 - quad / (s2 * s2) + (double)N / s2 + t[5] - t[6] / s2);
+    return GP_OK;
+}
+
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec) {
     if (!h) return set_err(GP_EINVAL, 0);
     if (M) *M = h->shape.M;
@@ -1163,7 +1278,7 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
         const gp_fit_args& a = args[i];
         hs[i] = new_model(dev, prec, a.N, a.p, a.n, a.eps, a.alpha, a.sigma2);
         if ((rc = fit_alloc(hs[i], origin))) return fail_all(rc, i);
-        if ((rc = keep.get(&loglam[i], (size_t)a.n))) return fail_all(rc, i);
+        if ((rc = keep.get(&loglam[i], (size_t)a.p * a.n))) return fail_all(rc, i);
         if ((rc = fit_stage(hs[i], stages[i], loglam[i], origin))) return fail_all(rc, i);
         Xd[i] = a.X;
         yd[i] = a.y;

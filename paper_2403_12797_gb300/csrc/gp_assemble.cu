@@ -62,12 +62,13 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
 // float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
 // block is written to A and, through shared memory, transposed into the
 // upper triangle (A is exactly symmetric). Diagonal blocks also sum b.
-// d_m = sigma2 / lambda_m = exp(log sigma2 - sum_j log lambda_{m_j}) (Eq. 16,
-// 20), clamped at 1e200
+// d_m = sigma2 / lambda_m = exp(log sigma2 - sum_j log lambda^(j)_{m_j}) (Eq. 16,
+// 20; with ARD, Eq. 17, each dimension has its own eigenvalues), clamped at
+// 1e200; loglam[j * n + k] = log lambda_k of dimension j
 __device__ __forceinline__ double noise_diag_entry(const GpShape& s, const double* __restrict__ loglam,
                                                    double log_sigma2, int m) {
     double ll = 0.0;
-    for (int j = 0; j < s.p; ++j) ll += loglam[(m / s.stride[j]) % s.n];
+    for (int j = 0; j < s.p; ++j) ll += loglam[j * s.n + (m / s.stride[j]) % s.n];
     const double logd = log_sigma2 - ll;
     const double lclamp = 460.51701859880913680;  // log(1e200)
     return logd >= lclamp ? 1e200 : exp(logd);

@@ -59,8 +59,11 @@ __device__ __forceinline__ void gp_set_status(GpStatus* st, int code, int64_t de
 }
 
 // ---------------------------------------------------------------------------
-// One problem's shape and SE eigen-parameters (Eq. 14-16), computed on the
-// host in float64 and passed by value to kernels.
+// One problem's shape and SE eigen-parameters (Eq. 14-16), per input
+// dimension j (one eps_j and rho_j per dimension: the ARD kernel of Eq. 17;
+// all equal for the isotropic kernel of Eq. 13), computed on the host in
+// float64 (and rounded to float there for the float32 tables) and passed by
+// value to kernels.
 // ---------------------------------------------------------------------------
 struct GpShape {
     int64_t N;               // data rows (training or test points)
@@ -69,9 +72,10 @@ struct GpShape {
     int     M;               // n^p
     int     Mpad;            // M rounded up to the tile size of the kernel in use
     int     stride[GP_PMAX]; // n^(p-1-j): column m has digit (m / stride[j]) % n
-    double  alpha_beta;      // rho * beta   (Hermite argument scale, Eq. 15)
-    double  delta2;          // delta^2      (envelope exponent, Eq. 15)
-    double  sqrt_beta;       // gamma_1 = sqrt(beta)
+    double  ab[GP_PMAX];     // rho_j beta_j   (Hermite argument scale, Eq. 15)
+    double  d2[GP_PMAX];     // delta_j^2      (envelope exponent, Eq. 15)
+    double  sb[GP_PMAX];     // gamma_1 = sqrt(beta_j)
+    float   abf[GP_PMAX], d2f[GP_PMAX], sbf[GP_PMAX];  // the same rounded to float
 };
 
 // ---------------------------------------------------------------------------
@@ -154,6 +158,8 @@ static inline int64_t gp_round_up(int64_t v, int64_t m) { return (v + m - 1) / m
 // Host-side helpers implemented in gp_api.cu
 // ---------------------------------------------------------------------------
 int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha, int tile);
+// the same with eps_j, alpha_j per dimension (p values each)
+int gp_fill_shape_ard(GpShape* s, int64_t N, int p, int n, const double* eps, const double* alpha, int tile);
 
 // Let `kern` use as much dynamic shared memory as the device allows next to
 // its static shared memory. Always the same value, so it can be set before

@@ -11,7 +11,9 @@ struct gp_model {
     int device;
     int prec;
     GpShape shape;          // N / Npad of the training set (informational)
-    double eps, alpha, sigma2;
+    double eps[GP_PMAX];    // eps_j and alpha_j (rho_j) per input dimension (equal: isotropic)
+    double alpha[GP_PMAX];
+    double sigma2;
     double* L;              // M x M lower Cholesky factor of A
     double* W;              // M x M, L^{-1}
     double* c;              // M, A^{-1} b
@@ -78,6 +80,8 @@ int tile_of(int prec);
 void free_model(gp_model* h);
 
 gp_model* new_model(int dev, int prec, int64_t N, int p, int n, double eps, double alpha, double sigma2);
+// eps[j], alpha[j] for the p input dimensions (ARD)
+gp_model* new_model(int dev, int prec, int64_t N, int p, int n, const double* eps, const double* alpha, double sigma2);
 // the model's own device buffers
 int fit_alloc(gp_model* h, cudaStream_t stream);
 

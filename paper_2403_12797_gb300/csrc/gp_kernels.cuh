@@ -177,3 +177,10 @@ cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t
 int lml_partial_count(int sms);
 void launch_lml_terms(const double* y, int64_t N, const double* L, const double* b, const double* c,
                       const double* d, int M, int nparts, double* part, double* out, cudaStream_t stream);
+// out[m] = (A^{-1})_mm = sum_k W_km^2 for W = L^{-1} (M x M row-major, lower;
+// float32 or float64), in float64
+void launch_ainv_diag(const void* W, bool fp32, int M, double* out, cudaStream_t stream);
+// out[0..2] = c^T E c, tr(A^{-1} E), unclamped columns (E = d/sigma^2 on them),
+// through nparts per-CTA partials in part (4 nparts doubles); out[3] = 0
+void launch_lml_grad_terms(const double* c, const double* d, const double* ainv, double sigma2, int M, int nparts,
+                           double* part, double* out, cudaStream_t stream);

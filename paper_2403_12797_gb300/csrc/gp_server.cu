@@ -197,7 +197,7 @@ int launch_request(gp_server* S, Request* r, int slot) {
         // one device buffer holds X (N x p) followed by y (N), as staged
         double *xd = nullptr, *ll = nullptr;
         if ((rc = r->sc->get(&xd, (size_t)r->N * (s.p + 1)))) return rc;
-        if ((rc = r->sc->get(&ll, (size_t)s.n))) return rc;
+        if ((rc = r->sc->get(&ll, (size_t)s.p * s.n))) return rc;
         cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
         const double* yd = xd + (size_t)r->N * s.p;
         r->xd = xd;

@@ -37,14 +37,24 @@ __device__ __forceinline__ double gp_sqrt<double>(double v) { return sqrt(v); }
 __device__ __forceinline__ float to_tab(double x, float*) { return gp_d2f_rn(x); }
 __device__ __forceinline__ double to_tab(double x, double*) { return x; }
 
-// abT, sbT, d2T: alpha_beta, sqrt_beta and delta2 of s rounded to T on the
-// host (on GB300 the conversion instruction, like every float64 operation,
-// holds its scheduler's float64 pipe for 64 cycles a warp).
+// The shape constants of dimension j (rho_j beta_j, sqrt(beta_j), delta_j^2),
+// in T: the float ones were rounded on the host (on GB300 the conversion
+// instruction, like every float64 operation, holds its scheduler's float64
+// pipe for 64 cycles a warp).
+__device__ __forceinline__ void shape_consts(const GpShape& s, int j, double& ab, double& sb, double& d2) {
+    ab = s.ab[j];
+    sb = s.sb[j];
+    d2 = s.d2[j];
+}
+__device__ __forceinline__ void shape_consts(const GpShape& s, int j, float& ab, float& sb, float& d2) {
+    ab = s.abf[j];
+    sb = s.sbf[j];
+    d2 = s.d2f[j];
+}
 template <typename T>
 __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double* __restrict__ X,
                                                          const double* __restrict__ y,
-                                                         T* __restrict__ tab, GpStatus* st, T abT, T sbT,
-                                                         T d2T) {
+                                                         T* __restrict__ tab, GpStatus* st) {
     // recurrence coefficients sqrt(2/(k+1)), sqrt(k/(k+1)), once per block
     extern __shared__ __align__(16) unsigned char coef_raw[];
     T* ca = reinterpret_cast<T*>(coef_raw);
@@ -60,6 +70,8 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= s.Npad) return;
+    T abT, sbT, d2T;
+    shape_consts(s, j, abT, sbT, d2T);
     T* out = tab + (int64_t)j * s.n * s.Npad + i;
     if (i >= s.N) {
         for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
@@ -99,8 +111,7 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
 __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, const double* __restrict__ X,
                                                                  const double* __restrict__ y,
                                                                  float* __restrict__ tab,
-                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st,
-                                                                 float abf, float sbf, float d2f) {
+                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st) {
     constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
     extern __shared__ __align__(16) unsigned char coef_raw[];
     float* ca = reinterpret_cast<float*>(coef_raw);
@@ -116,6 +127,7 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= s.Npad) return;  // whole warps: Npad is a multiple of 128
+    const float abf = s.abf[j], sbf = s.sbf[j], d2f = s.d2f[j];
     const int rows = s.p * s.n + 1;
     float* chunk = tab + (i / CW) * (int64_t)rows * WS;
     const int k0 = (int)(i % CW);
@@ -187,15 +199,13 @@ size_t coef_bytes(const GpShape& s) {
 void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, double* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<double><<<grid, 256, coef_bytes<double>(s), stream>>>(s, X, y, tab, st, s.alpha_beta,
-                                                                            s.sqrt_beta, s.delta2);
+    eig_tables_kernel<double><<<grid, 256, coef_bytes<double>(s), stream>>>(s, X, y, tab, st);
 }
 
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(
-        s, X, y, tab, st, (float)s.alpha_beta, (float)s.sqrt_beta, (float)s.delta2);
+    eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tab, st);
 }
 
 size_t syrktc_table_floats(const GpShape& s) {
@@ -208,7 +218,6 @@ void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* 
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
     cudaMemsetAsync(tmaxb, 0, sizeof(unsigned int) * (size_t)rows * nblk, stream);
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(
-        s, X, y, tabc, tmaxb, st, (float)s.alpha_beta, (float)s.sqrt_beta, (float)s.delta2);
+    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, tmaxb, st);
     table_gmax_kernel<<<(unsigned)rows, 256, 0, stream>>>(tmaxb, rows, nblk, tmax);
 }

@@ -458,3 +458,73 @@ def test_mixed_fit_escalates_to_fp64_gram():
         assert not plain.gram_fp64
     finally:
         plain.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_log_marginal_likelihood_sigma2_gradient_matches_oracle(prec):
+    """gp_model_log_marginal_grad: log p(y) as gp_model_log_marginal, and
+    d log p / d sigma^2 against the oracle's closed form (pinned to central
+    differences and to the dense N x N gradient). The derivative carries
+    (y^T y - b^T c) / sigma^4, whose cancellation amplifies the mixed Gram's
+    error; mixed tolerance 1e-3 relative, float64 1e-8."""
+    tol = 1e-8 if prec == "fp64" else 1e-3
+    cases = [W.random_problem(31, 3_000, 10, 2, 6, eps=0.9, alpha=1.1, sigma2=0.02),
+             W.workload2(N=20_000, Ns=10),
+             W.random_problem(32, 4_000, 10, 3, 9, eps=1.1, alpha=1.0, sigma2=0.01),  # M = 729 > 512
+             W.workload6(1, 200, N=2_000, Ns=10)]                                     # clamped d_m
+    for pr in cases:
+        m = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec)
+        try:
+            v, g = m.log_marginal_grad(pr.y)
+            assert v == m.log_marginal(pr.y)
+            mdl = O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2)
+            ref = O.log_marginal_likelihood_dsigma2(mdl, pr.y)
+            assert abs(g - ref) <= tol * abs(ref), (g, ref, pr.name)
+        finally:
+            m.free()
+
+
+ARD_CASES = [
+    # (seed, N, Ns, p, n, eps per dimension, alpha per dimension)
+    (81, 20_000, 1_000, 2, 12, (0.6, 1.8), (1.2, 0.7)),
+    (82, 30_000, 1_500, 3, 9, (1.4, 0.5, 1.0), (0.9, 1.3, 1.0)),     # M = 729: CTA-pair Gram
+    (83, 8_000, 500, 4, 4, (0.7, 1.1, 1.6, 0.9), (1.0, 0.8, 1.2, 1.5)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(len(ARD_CASES)))
+def test_ard_fit_predict_matches_oracle(prec, case):
+    """The ARD kernel (Eq. 17, an eps_j and rho_j per dimension) through
+    gp_fit_ard_ex against the oracle's per-dimension path (itself pinned to
+    the isotropic limit, the anisotropic Mercer sum and the dense posterior),
+    with the same tolerances as the isotropic fits."""
+    seed, N, Ns, p, n, eps, alpha = ARD_CASES[case]
+    pr = W.random_problem(seed, N, Ns, p, n, sigma2=0.01)
+    m = _lib.fit_ard(pr.X, pr.y, n, eps, alpha, pr.sigma2, prec=prec)
+    try:
+        mean, var = m.predict(pr.Xs)
+        mdl = O.fit(pr.X, pr.y, n, np.array(eps), np.array(alpha), pr.sigma2)
+        mo, vo = O.predict(mdl, pr.Xs)
+        assert O.relerr(mean, mo) < TOL[prec]["mean"], O.relerr(mean, mo)
+        assert O.relerr(var, vo) < TOL[prec]["var"], O.relerr(var, vo)
+        np.testing.assert_allclose(m.read("d"), mdl["d"], rtol=1e-13)
+        # the likelihood of the ARD model as well
+        lo = O.log_marginal_likelihood(mdl, pr.y)
+        assert abs(m.log_marginal(pr.y) - lo) <= (1e-9 if prec == "fp64" else 1e-4) * abs(lo)
+    finally:
+        m.free()
+
+
+def test_ard_with_equal_parameters_is_the_isotropic_fit():
+    pr = W.workload2(N=20_000, Ns=500)
+    a = _lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec="mixed")
+    b = _lib.fit_ard(pr.X, pr.y, pr.n, [pr.eps, pr.eps], [pr.alpha, pr.alpha], pr.sigma2, prec="mixed")
+    try:
+        ma, va = a.predict(pr.Xs)
+        mb, vb = b.predict(pr.Xs)
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+    finally:
+        a.free()
+        b.free()

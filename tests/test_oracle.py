@@ -462,3 +462,62 @@ def test_ard_mxm_form_equals_the_nxn_posterior():
     assert O.relerr(mean, m2) < 1e-10 and O.relerr(var, v2) < 1e-8
     with pytest.raises(ValueError):
         O.phi_matrix(X, 7, [0.7, 1.6, 1.0], rho)  # one value per dimension
+
+
+# ---------------------------------------------------------------- likelihood gradient (eps, rho, sigma^2)
+
+def _lml_at(pr, n, eps, rho, s2):
+    return O.log_marginal_likelihood(O.fit(pr.X, pr.y, n, eps, rho, s2), pr.y)
+
+
+@pytest.mark.parametrize("N,p,n,eps,rho,s2", [(60, 1, 6, 1.1, 0.9, 0.02), (80, 2, 4, 0.8, 1.3, 0.05),
+                                              (50, 3, 3, 1.3, 1.0, 0.03), (40, 1, 120, 1.0, 1.0, 0.01)])
+def test_log_marginal_likelihood_gradient_matches_central_differences(N, p, n, eps, rho, s2):
+    """The analytic gradient (chain rule through beta, delta^2, gamma_i, the
+    Hermite argument and the eigenvalues; dense N x N trace formula) against
+    central differences of the M x M log-likelihood (itself pinned to the dense
+    definition), including n > 100 (the normalised-recurrence branch)."""
+    pr = W.random_problem(9, N, 1, p, n, eps=eps, alpha=rho, sigma2=s2)
+    g = O.log_marginal_likelihood_grad(pr.X, pr.y, n, eps, rho, s2)
+    h = 1e-5
+    fd = ((_lml_at(pr, n, eps + h, rho, s2) - _lml_at(pr, n, eps - h, rho, s2)) / (2 * h),
+          (_lml_at(pr, n, eps, rho + h, s2) - _lml_at(pr, n, eps, rho - h, s2)) / (2 * h),
+          (_lml_at(pr, n, eps, rho, s2 * (1 + h)) - _lml_at(pr, n, eps, rho, s2 * (1 - h))) / (2 * h * s2))
+    for a, b in zip(g, fd):
+        assert abs(a - b) <= 1e-5 * max(1.0, abs(b)), (g, fd)
+    # the sigma^2 component equals the M x M closed form used on the device
+    ds = O.log_marginal_likelihood_dsigma2(O.fit(pr.X, pr.y, n, eps, rho, s2), pr.y)
+    assert abs(g[2] - ds) <= 1e-8 * abs(ds)
+
+
+@pytest.mark.parametrize("theta", ["eps", "rho"])
+def test_eigenfunction_derivative_matches_central_differences(theta):
+    x = np.linspace(-2.0, 2.0, 41)
+    for n in (8, 130):
+        d = O.eigenfunctions_1d_grad(x, n, 1.2, 0.9, theta)
+        h = 1e-6
+        if theta == "eps":
+            fd = (O.eigenfunctions_1d(x, n, 1.2 + h, 0.9) - O.eigenfunctions_1d(x, n, 1.2 - h, 0.9)) / (2 * h)
+        else:
+            fd = (O.eigenfunctions_1d(x, n, 1.2, 0.9 + h) - O.eigenfunctions_1d(x, n, 1.2, 0.9 - h)) / (2 * h)
+        np.testing.assert_allclose(d, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_dropped_term_in_delta_derivative_is_caught(monkeypatch):
+    """Planted mistake: d delta^2 / d rho without its rho (beta^2 - 1) term
+    makes the rho component disagree with central differences."""
+    good = O.se_constants_grad
+
+    def bad(eps, rho):
+        out = good(eps, rho)
+        db, dd, drb = out["rho"]
+        beta, _ = O.se_constants(eps, rho)
+        out["rho"] = (db, dd - rho * (beta ** 2 - 1.0), drb)
+        return out
+
+    monkeypatch.setattr(O, "se_constants_grad", bad)
+    pr = W.random_problem(9, 60, 1, 1, 6, eps=1.1, alpha=0.9, sigma2=0.02)
+    g = O.log_marginal_likelihood_grad(pr.X, pr.y, 6, 1.1, 0.9, 0.02)
+    h = 1e-5
+    fd = (_lml_at(pr, 6, 1.1, 0.9 + h, 0.02) - _lml_at(pr, 6, 1.1, 0.9 - h, 0.02)) / (2 * h)
+    assert abs(g[1] - fd) > 1e-3 * max(1.0, abs(fd))
