@@ -280,12 +280,23 @@ def run_ours(args):
         mean = torch.empty(p.Ns, dtype=torch.float64, device=dev)
         var = torch.empty(p.Ns, dtype=torch.float64, device=dev)
 
-        def step():
-            # fit and predict through the one-call entry point (the same kernels
-            # as fit() then predict(), without the host round trip between them)
-            m, _, _ = _lib.fit_predict(X, y, p.n, p.eps, p.alpha, p.sigma2, Xs, prec=prec,
-                                       mean_out=mean, var_out=var)
-            m.free()
+        if world == 1:
+            def step():
+                # fit and predict through the one-call entry point (the same kernels
+                # as fit() then predict(), without the host round trip between them)
+                m, _, _ = _lib.fit_predict(X, y, p.n, p.eps, p.alpha, p.sigma2, Xs, prec=prec,
+                                           mean_out=mean, var_out=var)
+                m.free()
+        else:
+            from paper_2403_12797_gb300 import dist as D
+
+            def step():
+                # this rank's shard of the training rows: its packed Gram, one
+                # NCCL all-reduce of it in device memory, the same fit on
+                # every rank; then this rank's own test points
+                m = D.fit_sharded(X, y, p.n, p.eps, p.alpha, p.sigma2, prec=prec, device=dev, local=True)
+                m.predict(Xs, mean_out=mean, var_out=var)
+                m.free()
         return step, (X, y, Xs, mean, var)
 
     step, (X, y, Xs, mean, var) = make_step(pr)
@@ -338,15 +349,20 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": WORKLOAD2 if main_w2 else WORKLOAD, "prec": prec,
                       "l2": "flushed between steps (256 MiB write); inputs and tables exceed L2",
-                      "replicas": world},
+                      "parallelism": ("single GPU" if world == 1 else
+                                      f"row-sharded fit over {world} GPUs: every rank holds one shard of "
+                                      "the workload's size (the same rows), one NCCL all-reduce of the "
+                                      "packed Gram in device memory, the factorisation replicated, each "
+                                      "rank predicting its own test points")},
            "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
            "kernels": kernels, "kernel_shares": shares,
            # device time of the kernel groups per step; the rest of ms_per_step is the
            # host's turnaround inside the API calls (status reads, the fit -> predict handoff)
            "device_busy_ms_per_step": sum(g["total_ms"] for g in groups.values()) / args.steps}
 
-    if rank == 0 and not main_w2 and not args.quick:
-        # the p=2, n=20 workload as a secondary key (same step, same timing rules)
+    if world == 1 and not main_w2 and not args.quick:
+        # the p=2, n=20 workload as a secondary key (same step, same timing rules;
+        # on one GPU only: with several, the step holds a collective)
         pr2 = W.workload2()
         step2, _ = make_step(pr2)
         for _ in range(3):
@@ -371,6 +387,7 @@ def run_ours(args):
         if not args.no_extras:
             out["batched_fit"] = batched_fit_bench(_lib, torch, dev)
             out["serving"] = serving_bench(_lib, torch, dev)
+            out["serving_fp64"] = serving_bench(_lib, torch, dev, prec="fp64")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -497,24 +514,43 @@ def batched_fit_bench(_lib, torch, dev):
             "speedup": t_seq / t_batch, "one_graph": bool(graph), "tuned_k": k}
 
 
-def serving_bench(_lib, torch, dev):
+def serving_bench(_lib, torch, dev, prec="mixed"):
     """The serving workload: 64 resident models (p in {2,3,4}, M <= 2048, N up
     to 5e5, fitted by one batched fit); a closed-loop burst gives the
     saturating request rate, then open-loop Poisson streams at 50 % and 80 %
     of it (predict sizes log-uniform on [1, 65536], 5 % refits with N
-    log-uniform on [1e4, 5e5]) give p50/p99 latency and throughput."""
+    log-uniform on [1e4, 5e5]) give p50/p99 latency and throughput.
+
+    prec="fp64": the same models, streams and server with float64 models.
+    Their training sets (and the refits') are cut to their first 20,000 rows,
+    since float64 fits at 5e5 rows would take minutes on this GPU's float64
+    units; a predict's cost does not depend on N."""
     from paper_2403_12797_gb300 import workloads as W
+    cap = None if prec == "mixed" else 20_000
     mods = W.workload5_models(count=64)
-    models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in mods])
+    if cap:
+        mods = [_sub(pr, cap, 0) for pr in mods]
+    models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in mods], prec=prec)
     n_esc = sum(1 for m in models if m.gram_fp64)
     out = {"workload": "64 resident models: p in {2,3,4}, M <= 2048, N log-uniform [1e4, 5e5]; "
-                       "predict sizes log-uniform [1, 65536], 5 % refits (N log-uniform [1e4, 5e5])",
+                       "predict sizes log-uniform [1, 65536], 5 % refits (N log-uniform [1e4, 5e5])"
+                       + ("" if not cap else "; float64 models on the first 20,000 rows of each training "
+                                             "set and of each refit"),
+           "prec": prec,
            "models_fit_points": sum(pr.X.shape[0] for pr in mods),
            "models_gram_fp64": n_esc}
+
+    def stream_of(count, rate, seed):
+        st_ = W.workload5_stream(mods, count, rate, refit_frac=0.05, seed=seed)
+        if cap:
+            for r in st_:
+                if r.kind == "refit":
+                    r.refit = _sub(r.refit, cap, 0)
+        return st_
     with _lib.Server(slots=8) as srv:
         ids = [srv.add_model(m) for m in models]
         # closed loop: a burst of the same request mix (5 % refits) submitted at once
-        burst = W.workload5_stream(mods, 200, 1e9, refit_frac=0.05, seed=1)
+        burst = stream_of(200, 1e9, 1)
         srv.reset_stats()
         t0 = time.perf_counter()
         tk = [srv.submit_refit(ids[r.model], r.refit.X, r.refit.y) if r.kind == "refit"
@@ -526,11 +562,12 @@ def serving_bench(_lib, torch, dev):
         sat_rate = len(burst) / wall
         out["saturation"] = {"requests_per_s": sat_rate, "points_per_s": st["points_per_s"],
                              "refits": st["refits_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                             "peak_inflight": st["peak_inflight"]}
+                             "peak_inflight": st["peak_inflight"], "batches": st["batches"],
+                             "peak_batch": st["peak_batch"]}
         out["refits_gram_fp64"] = sum(1 for i in ids if _lib.lib().gp_model_flags(srv.model_handle(i)) & 1)
         for frac in (0.5, 0.8):
             rate = frac * sat_rate
-            stream = W.workload5_stream(mods, max(20, int(rate * 3.0)), rate, refit_frac=0.05, seed=2)
+            stream = stream_of(max(20, int(rate * 3.0)), rate, 2)
             srv.reset_stats()
             t0 = time.perf_counter()
             tk = []
@@ -548,7 +585,8 @@ def serving_bench(_lib, torch, dev):
             out[f"load_{int(frac * 100)}"] = {
                 "offered_requests_per_s": rate, "requests": len(stream),
                 "refits": st["refits_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                "points_per_s": st["points_per_s"], "peak_inflight": st["peak_inflight"]}
+                "points_per_s": st["points_per_s"], "peak_inflight": st["peak_inflight"],
+                "batches": st["batches"], "peak_batch": st["peak_batch"]}
     return out
 
 

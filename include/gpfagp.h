@@ -136,6 +136,24 @@ GPFAGP_API int gp_fit_ard_ex(const double* X, const double* y, int64_t N, int p,
 GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns,
                              double* mean, double* var, void* cuda_stream, int dev_ptrs);
 
+/* The full predictive covariance block of Eq. 12 at Ns test points:
+ *   cov[i * Ns + j] = sigma^2 phi(x*_i)^T A^{-1} phi(x*_j)
+ * (Ns x Ns, row-major, exactly symmetric, the covariance of the latent f;
+ * with noisy != 0, sigma^2 is added on the diagonal: the covariance of the
+ * noisy observations y*). Its diagonal is gp_predict_ex's variance, up to
+ * the precision mode's rounding. Formed as sigma^2 Z Z^T with
+ * Z = Phi_* L^{-T}: the mixed model takes Z from the predict kernel as
+ * bf16 hi/lo and multiplies on the tensor cores (hi*hi + hi*lo + lo*hi,
+ * float32 accumulation); the float64 model in float64. mean (Ns values) may
+ * be NULL; it is the predictive mean as gp_predict_ex computes it. Xs, mean
+ * and cov are device pointers when dev_ptrs != 0, else host (cov then needs
+ * Ns^2 doubles of device scratch). GP_EINVAL for Ns > GP_COV_MAX_NS
+ * (detail 6), a NULL Xs or cov, or a model on another device (detail 5). */
+#define GP_COV_MAX_NS 65536
+GPFAGP_API int gp_predict_cov_ex(const gp_model* h, const double* Xs, int64_t Ns,
+                                 double* mean, double* cov, int noisy,
+                                 void* cuda_stream, int dev_ptrs);
+
 /* gp_fit_ex followed by gp_predict_ex on the fitted model (Sec. 2.2 and
  * Eq. 8-9, the same kernels), with the prediction enqueued right behind the
  * fit and a single status read at the end, so the device does not wait for
@@ -174,7 +192,9 @@ GPFAGP_API int gp_model_log_marginal(const gp_model* h, const double* y, int64_t
  *                                + N / sigma^2 + tr(A^{-1} E) - n_u / sigma^2 ],
  * n_u the unclamped columns, tr(A^{-1} E) = sum_m e_m |W[:, m]|^2 with
  * W = L^{-1}. The float64 model keeps W; for a mixed model W is formed again
- * from L (float32, the inverse kernel of the fit) during the call. Sums in
+ * from L in float64 during the call (float32's exponent range loses
+ * (A^{-1})_mm where d_m nears its clamp, and the gradient weights those
+ * entries by d_m / sigma^2). Sums in
  * float64, fixed order. y, N, pointer kind and errors as
  * gp_model_log_marginal; *lml and *dlml_dsigma2 receive the results. */
 GPFAGP_API int gp_model_log_marginal_grad(const gp_model* h, const double* y, int64_t N, double* lml,
@@ -255,6 +275,25 @@ GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p
                               double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
                               gp_model** out);
 
+/* The exchange step of a row-sharded fit, in one buffer. G = Phi^T Phi and
+ * b = Phi^T y are sums over training rows (Sec. 2.2), so ranks that hold
+ * disjoint row blocks of one training set sum their partial Grams with one
+ * all-reduce of M (M + 1) / 2 + M float64 values and then each factor the
+ * same A.
+ * gp_gram_packed_ex: the Gram of X (N x p), y (N), as gp_gram_ex computes
+ *   it, written as packed[i (i + 1) / 2 + j] = G[i][j] for j <= i (the lower
+ *   triangle row by row), then packed[M (M + 1) / 2 + m] = b[m].
+ * gp_fit_gram_packed_ex: gp_fit_gram_ex from such a buffer (N = all ranks'
+ *   rows together).
+ * Pointers are device pointers when dev_ptrs != 0, else host; errors as
+ * gp_gram_ex and gp_fit_gram_ex. */
+GPFAGP_API int gp_gram_packed_ex(const double* X, const double* y, int64_t N, int p, int n,
+                                 double eps, double alpha, int prec, double* packed,
+                                 void* cuda_stream, int dev_ptrs);
+GPFAGP_API int gp_fit_gram_packed_ex(const double* packed, int64_t N, int p, int n, double eps,
+                                     double alpha, double sigma2, int prec, void* cuda_stream,
+                                     int dev_ptrs, gp_model** out);
+
 typedef struct gp_fit_args {
     const double* X;   /* N x p */
     const double* y;   /* N     */
@@ -300,13 +339,19 @@ typedef struct gp_predict_args {
     double* var;       /* Ns, or NULL */
 } gp_predict_args;
 
-/* Run `count` predict requests against (possibly different) models side by
- * side: each request's kernels are enqueued on one of up to 8 streams
- * behind `cuda_stream` (no host synchronisation in between), then the call
- * waits once and reads every request's status. Device pointers only. Each
- * result is bitwise the same as gp_predict_ex on that request alone (the
- * same kernels with the same launch configuration). Returns the first
- * failing request's status (detail = its index). */
+/* Run `count` predict requests against (possibly different) models as one
+ * batch (Eq. 11-12 per request). The requests against mixed-precision
+ * models share one upload of a request table, one launch that evaluates
+ * every request's eigenfunction tables, and one persistent tensor-core
+ * predict launch per basis dimension p among them, whose CTAs walk the
+ * (request, 128-point tile) items, heavier models first. Requests against
+ * float64 models run their own kernels on up to 8 streams behind
+ * `cuda_stream`. The call then waits once and reads every request's
+ * status. Device pointers only. Each result is bitwise the same as
+ * gp_predict_ex on that request alone (the same per-point arithmetic in the
+ * same order). Returns the first failing request's status (detail = its
+ * index; GP_EINVAL with detail 7 if a model's predict stages do not fit in
+ * shared memory). */
 GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cuda_stream);
 
 /* ---- request server (continuous batching over resident models) ----------- */
@@ -337,11 +382,16 @@ typedef struct gp_server_report {
     double p50_ms, p99_ms, max_ms;  /* predict latency, submit to results   */
     double wall_s;          /* first submit to last completion              */
     double points_per_s;    /* points / wall_s                              */
-    int peak_inflight;      /* most requests running at once               */
+    int peak_inflight;      /* most requests on the device at once          */
+    int peak_batch;         /* most predicts in one batch                   */
+    int64_t batches;        /* predict batches started                      */
 } gp_server_report;
 
-/* slots: 1..64 concurrent requests; mem_budget_bytes: scratch budget
- * (<= 0: half the free device memory at creation). */
+/* slots: 1..64 concurrent jobs (a refit, or a batch of the predicts queued
+ * at the head: up to 256 requests and 2^20 points, all test points in one
+ * upload, one table launch and one persistent predict launch per basis
+ * dimension p, all results in one download); mem_budget_bytes: scratch
+ * budget (<= 0: half the free device memory at creation). */
 GPFAGP_API int gp_server_create(int slots, int64_t mem_budget_bytes, gp_server** out);
 /* Register (and hand over) a fitted model; *model_id identifies it in requests. */
 GPFAGP_API int gp_server_add_model(gp_server* s, gp_model* m, int* model_id);

@@ -36,7 +36,8 @@ class GPError(RuntimeError):
 class ServerReport(C.Structure):
     _fields_ = [("predicts_done", C.c_int64), ("refits_done", C.c_int64), ("points", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
-                ("wall_s", C.c_double), ("points_per_s", C.c_double), ("peak_inflight", C.c_int)]
+                ("wall_s", C.c_double), ("points_per_s", C.c_double), ("peak_inflight", C.c_int),
+                ("peak_batch", C.c_int), ("batches", C.c_int64)]
 
 
 class FitArgs(C.Structure):
@@ -77,6 +78,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_fit_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_fit_ard_ex": (i, [vp, vp, i64, i, i, vp, vp, d, i, vp, i, C.POINTER(vp)]),
         "gp_predict_ex": (i, [vp, vp, i64, vp, vp, vp, i]),
+        "gp_predict_cov_ex": (i, [vp, vp, i64, vp, vp, i, vp, i]),
         "gp_fit_predict_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i64, vp, vp, vp, i, C.POINTER(vp)]),
         "gp_model_info": (i, [vp, C.POINTER(i64), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "gp_model_read": (i, [vp, i, vp]),
@@ -88,6 +90,8 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
         "gp_batch_info": (i, [C.POINTER(i), C.POINTER(i)]),
         "gp_fit_gram_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
+        "gp_gram_packed_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, i]),
+        "gp_fit_gram_packed_ex": (i, [vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_server_create": (i, [i, i64, C.POINTER(vp)]),
         "gp_server_add_model": (i, [vp, vp, C.POINTER(i)]),
         "gp_server_model": (vp, [vp, i]),
@@ -210,6 +214,23 @@ class Model:
                                  _stream_of(Xs, stream), dev)
         _check(rc, "gp_predict_ex")
         return mean, vv
+
+    def predict_cov(self, Xs, noisy: bool = False, stream=None):
+        """Predictive mean and full covariance block (Ns x Ns) at Xs; with
+        noisy, sigma^2 is added on the diagonal (covariance of y*)."""
+        Xs, _, Ns, p, dev = _prep_xy(Xs, None)
+        if p != self.p:
+            raise ValueError(f"Xs has {p} columns, model has p={self.p}")
+        if dev:
+            import torch
+            mean = torch.empty(Ns, dtype=torch.float64, device=Xs.device)
+            cov = torch.empty((Ns, Ns), dtype=torch.float64, device=Xs.device)
+        else:
+            mean, cov = np.empty(Ns), np.empty((Ns, Ns))
+        rc = lib().gp_predict_cov_ex(self._h, C.c_void_p(_ptr(Xs)), Ns, C.c_void_p(_ptr(mean)),
+                                     C.c_void_p(_ptr(cov)), 1 if noisy else 0, _stream_of(Xs, stream), dev)
+        _check(rc, "gp_predict_cov_ex")
+        return mean, cov
 
     def log_marginal(self, y, stream=None) -> float:
         """log p(y) of the fitted truncated-kernel GP (y: the training
@@ -335,6 +356,50 @@ def fit_gram(G, b, N: int, p: int, n: int, eps: float, alpha: float, sigma2: flo
     rc = lib().gp_fit_gram_ex(G.ctypes.data, b.ctypes.data, int(N), int(p), int(n), float(eps), float(alpha),
                               float(sigma2), PREC[prec], None, 0, C.byref(out))
     _check(rc, "gp_fit_gram_ex")
+    return Model(out.value)
+
+
+def packed_size(p: int, n: int) -> int:
+    """Length of the packed Gram exchange buffer: M (M + 1) / 2 + M."""
+    M = int(n) ** int(p)
+    return M * (M + 1) // 2 + M
+
+
+def gram_packed(X, y, n: int, eps: float, alpha: float, prec: str = "mixed", out=None, stream=None):
+    """Lower triangle of G = Phi^T Phi (row by row) then b = Phi^T y, as one
+    float64 vector (a device tensor for device inputs, else a host array)."""
+    X, y, N, p, dev = _prep_xy(X, y)
+    size = packed_size(p, n)
+    if out is None:
+        if dev:
+            import torch
+            out = torch.empty(size, dtype=torch.float64, device=X.device)
+        else:
+            out = np.empty(size)
+    rc = lib().gp_gram_packed_ex(C.c_void_p(_ptr(X)), C.c_void_p(_ptr(y)), N, p, int(n), float(eps),
+                                 float(alpha), PREC[prec], C.c_void_p(_ptr(out)), _stream_of(X, stream), dev)
+    _check(rc, "gp_gram_packed_ex")
+    return out
+
+
+def fit_gram_packed(buf, N: int, p: int, n: int, eps: float, alpha: float, sigma2: float,
+                    prec: str = "mixed", stream=None) -> Model:
+    """Fit from a packed Gram exchange buffer (gram_packed, summed over the
+    row blocks of N training rows); device tensor or host array."""
+    if _is_torch(buf):
+        import torch
+        if buf.dtype != torch.float64 or not buf.is_cuda or not buf.is_contiguous():
+            raise TypeError("device inputs must be contiguous float64 CUDA tensors")
+        dev = 1
+    else:
+        buf = np.ascontiguousarray(np.asarray(buf, dtype=np.float64))
+        dev = 0
+    if buf.shape[0] != packed_size(p, n):
+        raise ValueError("packed buffer has the wrong length")
+    out = C.c_void_p()
+    rc = lib().gp_fit_gram_packed_ex(C.c_void_p(_ptr(buf)), int(N), int(p), int(n), float(eps), float(alpha),
+                                     float(sigma2), PREC[prec], _stream_of(buf, stream), dev, C.byref(out))
+    _check(rc, "gp_fit_gram_packed_ex")
     return Model(out.value)
 
 

@@ -467,6 +467,37 @@ __global__ void add_diag_kernel(double* __restrict__ A, const double* __restrict
     if (i < M) A[(int64_t)i * M + i] += d[i];
 }
 
+// The exchange layout of a row-sharded Gram: the lower triangle of G row by
+// row (entry (i, j), j <= i, at i (i + 1) / 2 + j), then b. One thread per
+// element of the packed vector.
+__global__ void pack_lower_kernel(const double* __restrict__ G, const double* __restrict__ b, int M,
+                                  double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nl = (int64_t)M * (M + 1) / 2;
+    if (q >= nl + M) return;
+    if (q >= nl) {
+        out[q] = b[q - nl];
+        return;
+    }
+    // row i of the lower triangle holding q: i (i + 1) / 2 <= q
+    int64_t i = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    while (i * (i + 1) / 2 > q) --i;
+    const int64_t j = q - i * (i + 1) / 2;
+    out[q] = G[i * M + j];
+}
+
+// The inverse: the full symmetric A (M x M) and b from the packed vector.
+__global__ void unpack_lower_kernel(const double* __restrict__ in, int M, double* __restrict__ A,
+                                    double* __restrict__ b) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = blockIdx.y;
+    if (col >= M) return;
+    const int64_t r = row >= col ? row : col, c = row >= col ? col : row;
+    A[(int64_t)row * M + col] = in[r * (r + 1) / 2 + c];
+    if (row == 0) b[col] = in[(int64_t)M * (M + 1) / 2 + col];
+}
+
 // Every device step of one fit, enqueued on `stream` with no host
 // synchronisation (so that it can be captured into a graph). Inputs are
 // device pointers; scratch comes from `sc` (stream-ordered); errors found on
@@ -569,6 +600,99 @@ int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md,
         gp_note_launches(2);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "predict launch");
+}
+
+// ---------------------------------------------------------------- batched predicts
+
+int pred_batch_build(const std::vector<PredEntry>& es, Scratch& sc, PredBatch& pb) {
+    pb = PredBatch();
+    std::vector<int> order;
+    for (int i = 0; i < (int)es.size(); ++i)
+        if (es[i].Ns > 0) order.push_back(i);
+    // by p (one launch each), heavier models first within a launch
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const GpShape &sa = es[a].m->shape, &sb = es[b].m->shape;
+        if (sa.p != sb.p) return sa.p < sb.p;
+        return sa.M > sb.M;
+    });
+    for (int idx : order) {
+        const PredEntry& e = es[idx];
+        const GpShape& s = e.m->shape;
+        PredReq r{};
+        r.Ns = e.Ns;
+        r.Npad = gp_round_up(e.Ns, 128);
+        r.p = s.p;
+        r.n = s.n;
+        r.M = s.M;
+        r.Mpad = (int)gp_round_up(s.M, PREDTC_KB);
+        r.maxrows = predtc_window_rows(s);
+        r.Xs = e.Xd;
+        int rc;
+        if ((rc = sc.get(&r.tab, (size_t)s.p * s.n * r.Npad))) return rc;
+        r.Wpack = (const uint8_t*)e.m->Wpack;
+        r.cf = reinterpret_cast<const float*>((const uint8_t*)e.m->Wpack + 4 * (size_t)r.Mpad * r.Mpad);
+        r.cinfo = e.m->cinfo;
+        r.sigma2 = e.m->sigma2;
+        r.mean = e.md;
+        r.var = e.vd;
+        r.st = e.st;
+        r.consts = reinterpret_cast<const float*>((uintptr_t)pb.consts.size());  // offset until pack()
+        for (int j = 0; j < s.p; ++j) {
+            pb.consts.push_back(s.abf[j]);
+            pb.consts.push_back(s.sbf[j]);
+            pb.consts.push_back(s.d2f[j]);
+        }
+        const int ridx = (int)pb.reqs.size();
+        pb.boff.push_back(pb.nblocks);
+        pb.nblocks += (int)((r.Npad + 255) / 256) * s.p;
+        pb.max_n = std::max(pb.max_n, s.n);
+        if (pb.groups.empty() || pb.groups.back().p != s.p)
+            pb.groups.push_back(PredBatch::Group{s.p, (int)pb.items.size(), 0, 0});
+        PredBatch::Group& g = pb.groups.back();
+        for (int64_t t = 0; t < r.Npad / 128; ++t) pb.items.push_back(make_int2(ridx, (int)t));
+        g.count = (int)pb.items.size() - g.first;
+        g.maxrows = std::max(g.maxrows, r.maxrows);
+        pb.reqs.push_back(r);
+    }
+    pb.boff.push_back(pb.nblocks);
+    for (const PredBatch::Group& g : pb.groups)
+        if (predtc_batch_smem_bytes(g.maxrows, g.p) > (227 - 5) * 1024) return set_err(GP_EINVAL, 7);
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    pb.off_items = al(sizeof(PredReq) * pb.reqs.size());
+    pb.off_boff = pb.off_items + al(sizeof(int2) * pb.items.size());
+    pb.off_consts = pb.off_boff + al(sizeof(int) * pb.boff.size());
+    pb.total = pb.off_consts + al(sizeof(float) * pb.consts.size());
+    return GP_OK;
+}
+
+void pred_batch_pack(PredBatch& pb, void* host, const uint8_t* dev) {
+    uint8_t* h = (uint8_t*)host;
+    for (PredReq& r : pb.reqs)
+        r.consts = reinterpret_cast<const float*>(dev + pb.off_consts) + (uintptr_t)r.consts;
+    memcpy(h, pb.reqs.data(), sizeof(PredReq) * pb.reqs.size());
+    memcpy(h + pb.off_items, pb.items.data(), sizeof(int2) * pb.items.size());
+    memcpy(h + pb.off_boff, pb.boff.data(), sizeof(int) * pb.boff.size());
+    memcpy(h + pb.off_consts, pb.consts.data(), sizeof(float) * pb.consts.size());
+}
+
+int pred_batch_enqueue(const PredBatch& pb, const uint8_t* dev, cudaStream_t stream) {
+    if (pb.reqs.empty()) return GP_OK;
+    const PredReq* dreqs = reinterpret_cast<const PredReq*>(dev);
+    const int2* ditems = reinterpret_cast<const int2*>(dev + pb.off_items);
+    {
+        GpProf pf("eig_tables_batch", stream);
+        launch_eig_tables_batch(dreqs, reinterpret_cast<const int*>(dev + pb.off_boff), (int)pb.reqs.size(),
+                                pb.nblocks, pb.max_n, stream);
+    }
+    int nl = 1;
+    for (const PredBatch::Group& g : pb.groups) {
+        GpProf pf("predict_tc_batch", stream);
+        cudaError_t e = launch_predict_tc_batch(dreqs, ditems + g.first, g.count, g.p, g.maxrows, stream);
+        if (e != cudaSuccess) return cuda_err(e, "batched predict launch");
+        ++nl;
+    }
+    gp_note_launches(nl);
+    return GP_OK;
 }
 
 // ---------------------------------------------------------------- batches
@@ -826,6 +950,44 @@ GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, in
     return read_status(st, stream);
 }
 
+GPFAGP_API int gp_gram_packed_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
+                                 double alpha, int prec, double* packed, void* cuda_stream, int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!X || !y || !packed) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, 1.0))) return rc;
+    if ((rc = check_prec(prec))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    GpShape s;
+    gp_fill_shape(&s, N, p, n, eps, alpha, tile_of(prec));
+    const int M = s.M;
+    const size_t np = (size_t)M * (M + 1) / 2 + M;
+    Scratch sc(stream);
+    const double *Xd = X, *yd = y;
+    double *Gd, *bd, *pd = packed;
+    GpStatus* st;
+    if ((rc = sc.get(&st, 1))) return rc;
+    if ((rc = sc.get(&Gd, (size_t)M * M))) return rc;
+    if ((rc = sc.get(&bd, (size_t)M))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    if (!dev_ptrs) {
+        double *xx, *yy;
+        if ((rc = sc.get(&xx, (size_t)N * p))) return rc;
+        if ((rc = sc.get(&yy, (size_t)N))) return rc;
+        if ((rc = sc.get(&pd, np))) return rc;
+        cudaMemcpyAsync(xx, X, sizeof(double) * N * p, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(yy, y, sizeof(double) * N, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+        yd = yy;
+    }
+    if ((rc = gram_device(s, prec, dev, Xd, yd, nullptr, Gd, bd, st, stream))) return rc;
+    pack_lower_kernel<<<(unsigned)((np + 255) / 256), 256, 0, stream>>>(Gd, bd, M, pd);
+    gp_note_launches(1);
+    if (!dev_ptrs) cudaMemcpyAsync(packed, pd, sizeof(double) * np, cudaMemcpyDeviceToHost, stream);
+    return read_status(st, stream);
+}
+
 GPFAGP_API int gp_gram_static(const double* X, const double* y, int64_t N, int p, int n, double eps,
                               double alpha, double* G, double* b, void* cuda_stream) {
     set_err(GP_OK);
@@ -1008,14 +1170,16 @@ GPFAGP_API int gp_fit_predict_ex(const double* X, const double* y, int64_t N, in
     return GP_OK;
 }
 
-GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p, int n, double eps,
-                              double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
-                              gp_model** out) {
+namespace {
+// A fit continued from a Gram: full G and b (packed == false) or the packed
+// lower triangle and b of gp_gram_packed_ex (packed == true, in G).
+int fit_from_gram(const double* G, const double* b, bool packed, int64_t N, int p, int n, double eps, double alpha,
+                  double sigma2, int prec, void* cuda_stream, int dev_ptrs, gp_model** out) {
     set_err(GP_OK);
     int rc, dev;
     if (!out) return set_err(GP_EINVAL, 0);
     *out = nullptr;
-    if (!G || !b) return set_err(GP_EINVAL, 0);
+    if (!G || (!packed && !b)) return set_err(GP_EINVAL, 0);
     if ((rc = check_hyper(N, p, n, eps, alpha, sigma2))) return rc;
     if ((rc = check_prec(prec))) return rc;
     if ((rc = check_device(&dev))) return rc;
@@ -1042,8 +1206,22 @@ GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p
     if ((rc = sc.get(&fwork, factor_work_bytes(M, prec != GP_PREC_FP64)))) return fail(rc);
     cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
     const cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaMemcpyAsync(A, G, sizeof(double) * M * M, kind, stream);
-    cudaMemcpyAsync(h->b, b, sizeof(double) * M, kind, stream);
+    if (packed) {
+        const size_t np = (size_t)M * (M + 1) / 2 + M;
+        const double* pd = G;
+        if (!dev_ptrs) {
+            double* tmp;
+            if ((rc = sc.get(&tmp, np))) return fail(rc);
+            cudaMemcpyAsync(tmp, G, sizeof(double) * np, kind, stream);
+            pd = tmp;
+        }
+        dim3 grid((unsigned)((M + 255) / 256), (unsigned)M);
+        unpack_lower_kernel<<<grid, 256, 0, stream>>>(pd, M, A, h->b);
+        gp_note_launches(1);
+    } else {
+        cudaMemcpyAsync(A, G, sizeof(double) * M * M, kind, stream);
+        cudaMemcpyAsync(h->b, b, sizeof(double) * M, kind, stream);
+    }
     if ((rc = fit_stage(h, stage, loglam, stream))) return fail(rc);
     launch_noise_diag(h->shape, loglam, sigma2, h->d, stream);
     add_diag_kernel<<<(M + 255) / 256, 256, 0, stream>>>(A, h->d, M);
@@ -1052,6 +1230,18 @@ GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p
     if ((rc = read_status(st, stream))) return fail(rc);
     *out = h;
     return GP_OK;
+}
+}  // namespace
+
+GPFAGP_API int gp_fit_gram_ex(const double* G, const double* b, int64_t N, int p, int n, double eps,
+                              double alpha, double sigma2, int prec, void* cuda_stream, int dev_ptrs,
+                              gp_model** out) {
+    return fit_from_gram(G, b, false, N, p, n, eps, alpha, sigma2, prec, cuda_stream, dev_ptrs, out);
+}
+
+GPFAGP_API int gp_fit_gram_packed_ex(const double* packed, int64_t N, int p, int n, double eps, double alpha,
+                                     double sigma2, int prec, void* cuda_stream, int dev_ptrs, gp_model** out) {
+    return fit_from_gram(packed, nullptr, true, N, p, n, eps, alpha, sigma2, prec, cuda_stream, dev_ptrs, out);
 }
 
 GPFAGP_API gp_model* gp_fit(const double* X, const double* y, int64_t N, int p, int n, double eps,
@@ -1089,6 +1279,71 @@ GPFAGP_API int gp_predict_ex(const gp_model* h, const double* Xs, int64_t Ns, do
     if (!dev_ptrs) {
         cudaMemcpyAsync(mean, md, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
         if (var) cudaMemcpyAsync(var, vd, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+    }
+    return read_status(st, stream);
+}
+
+GPFAGP_API int gp_predict_cov_ex(const gp_model* h, const double* Xs, int64_t Ns, double* mean, double* cov,
+                                 int noisy, void* cuda_stream, int dev_ptrs) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!h || Ns < 0) return set_err(GP_EINVAL, 0);
+    if (Ns == 0) return GP_OK;
+    if (!Xs || !cov) return set_err(GP_EINVAL, 0);
+    if (Ns > GP_COV_MAX_NS) return set_err(GP_EINVAL, 6);
+    if ((rc = check_device(&dev))) return rc;
+    if (dev != h->device) return set_err(GP_EINVAL, 5);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    Scratch sc(stream);
+    GpStatus* st;
+    if ((rc = sc.get(&st, 1))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    GpShape s = h->shape;
+    s.N = Ns;
+    s.Npad = gp_round_up(Ns, 128);
+    const double* Xd = Xs;
+    double *md = mean, *cd = cov;
+    const size_t ncov = (size_t)Ns * (size_t)Ns;
+    if (!dev_ptrs) {
+        double* xx;
+        if ((rc = sc.get(&xx, (size_t)Ns * s.p))) return rc;
+        if ((rc = sc.get(&cd, ncov))) return rc;
+        cudaMemcpyAsync(xx, Xs, sizeof(double) * Ns * s.p, cudaMemcpyHostToDevice, stream);
+        Xd = xx;
+        md = nullptr;
+    }
+    if (md == nullptr && (rc = sc.get(&md, (size_t)Ns))) return rc;  // the kernels always form the mean
+    cudaError_t e;
+    if (h->prec == GP_PREC_FP64) {
+        double *tab, *part, *z;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&part, predict64_part_elems(s.Npad, s.M)))) return rc;
+        if ((rc = sc.get(&z, predict64_z_elems(s.Npad, s.M)))) return rc;
+        launch_eig_tables_f64(s, Xd, nullptr, tab, st, stream);
+        e = launch_predict64(s, tab, h->W, h->c, h->sigma2, part, md, nullptr, stream, z);
+        if (e == cudaSuccess) {
+            GpProf pf("cov64", stream);
+            e = launch_cov64(z, Ns, (int)(predict64_z_elems(s.Npad, s.M) / (size_t)s.Npad), h->sigma2, noisy, cd,
+                             stream);
+        }
+        gp_note_launches(4);
+    } else {
+        float* tab;
+        uint8_t* zpack;
+        if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        if ((rc = sc.get(&zpack, predtc_zpack_bytes(s.Npad, s.M)))) return rc;
+        launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
+        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->sigma2, md, nullptr, st, stream, zpack);
+        if (e == cudaSuccess) {
+            GpProf pf("cov_tc", stream);
+            e = launch_cov_tc(zpack, Ns, s.Npad, s.M, h->sigma2, noisy, cd, st, stream);
+        }
+        gp_note_launches(3);
+    }
+    if (e != cudaSuccess) return cuda_err(e, "covariance launch");
+    if (!dev_ptrs) {
+        if (mean) cudaMemcpyAsync(mean, md, sizeof(double) * Ns, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(cov, cd, sizeof(double) * ncov, cudaMemcpyDeviceToHost, stream);
     }
     return read_status(st, stream);
 }
@@ -1160,21 +1415,25 @@ GPFAGP_API int gp_model_log_marginal_grad(const gp_model* h, const double* y, in
         yd = yy;
     }
     // diag(A^{-1}) from W = L^{-1}: the float64 model keeps W; for the mixed
-    // model it is formed again from L in float32 (the precision its own
-    // variance uses), in a factor workspace whose barrier header is zeroed here
-    if (h->W != nullptr) {
-        launch_ainv_diag(h->W, false, M, ainv, stream);
-        gp_note_launches(1);
-    } else {
+    // model it is formed again from L in float64 (in a factor workspace whose
+    // barrier header is zeroed here). Not in float32 as its variance does:
+    // where d_m nears its clamp, L_mm reaches 1e100 and 1/L_mm underflows in
+    // float32, and tr(A^{-1} E) weights (A^{-1})_mm ~ 1/d_m by e_m = d_m/sigma^2,
+    // so each such column would lose a whole 1/sigma^2 from the gradient.
+    const double* Wsrc = h->W;
+    if (Wsrc == nullptr) {
         unsigned char* fwork;
-        if ((rc = sc.get(&fwork, factor_work_bytes(M, true)))) return rc;
+        double* Wd;
+        if ((rc = sc.get(&fwork, factor_work_bytes(M, false)))) return rc;
+        if ((rc = sc.get(&Wd, (size_t)M * M))) return rc;
         cudaMemsetAsync(fwork, 0, 256, stream);
-        cudaError_t e = launch_tri_inverse(h->L, nullptr, M, true, st, fwork, stream);
+        cudaError_t e = launch_tri_inverse(h->L, Wd, M, false, st, fwork, stream);
         if (e != cudaSuccess) return cuda_err(e, "inverse for the likelihood gradient");
-        const float* Wf = (const float*)(fwork + 256) + (size_t)M * M;
-        launch_ainv_diag(Wf, true, M, ainv, stream);
         gp_note_launches(1);
+        Wsrc = Wd;
     }
+    launch_ainv_diag(Wsrc, false, M, ainv, stream);
+    gp_note_launches(1);
     launch_lml_terms(yd, N, h->L, h->b, h->c, h->d, M, nparts, part, terms, stream);
     launch_lml_grad_terms(h->c, h->d, ainv, h->sigma2, M, nparts, part, terms + 4, stream);
     gp_note_launches(4);
@@ -1406,16 +1665,43 @@ GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cu
     GpStatus* sts;
     if ((rc = keep.get(&sts, (size_t)count))) return rc;
     cudaMemsetAsync(sts, 0, sizeof(GpStatus) * count, origin);
-    StreamSet ss(count < 8 ? count : 8);
-    ss.fork(origin);
+    // mixed-precision models: one batched launch sequence on `origin`;
+    // float64 models: their own kernels, side by side on a few streams
+    std::vector<PredEntry> mixed;
+    std::vector<int> f64;
+    for (int i = 0; i < count; ++i) {
+        const gp_predict_args& a = args[i];
+        if (a.Ns == 0) continue;
+        if (a.model->prec == GP_PREC_FP64) f64.push_back(i);
+        else mixed.push_back(PredEntry{a.model, a.Xs, a.Ns, a.mean, a.var, &sts[i]});
+    }
     int first = GP_OK;
     int64_t first_idx = 0;
-    {
+    if (!mixed.empty()) {
+        PredBatch pb;
+        uint8_t* up = nullptr;
+        rc = pred_batch_build(mixed, keep, pb);
+        if (rc == GP_OK) rc = keep.get(&up, pb.total);
+        if (rc == GP_OK) {
+            std::vector<uint8_t> img(pb.total);
+            pred_batch_pack(pb, img.data(), up);
+            // from pageable memory: returns once the image is staged
+            cudaError_t e = cudaMemcpyAsync(up, img.data(), pb.total, cudaMemcpyHostToDevice, origin);
+            rc = e == cudaSuccess ? pred_batch_enqueue(pb, up, origin) : cuda_err(e, "batch upload");
+        }
+        if (rc != GP_OK) {
+            first = rc;
+            first_idx = 0;
+        }
+    }
+    if (!f64.empty() && first == GP_OK) {
+        StreamSet ss(f64.size() < 8 ? (int)f64.size() : 8);
+        ss.fork(origin);
         std::vector<Scratch*> scs;
-        for (int i = 0; i < count; ++i) {
+        for (size_t k = 0; k < f64.size(); ++k) {
+            const int i = f64[k];
             const gp_predict_args& a = args[i];
-            if (a.Ns == 0) continue;
-            cudaStream_t s = ss.st[i % ss.st.size()];
+            cudaStream_t s = ss.st[k % ss.st.size()];
             Scratch* sc = new Scratch(s);
             scs.push_back(sc);
             rc = predict_compute(a.model, a.Xs, a.Ns, a.mean, a.var, &sts[i], *sc, s);
@@ -1425,8 +1711,8 @@ GPFAGP_API int gp_predict_batch(int count, const gp_predict_args* args, void* cu
             }
         }
         for (Scratch* sc : scs) delete sc;
+        ss.join(origin);
     }
-    ss.join(origin);
     cudaError_t e = cudaStreamSynchronize(origin);
     if (e != cudaSuccess) return cuda_err(e, "batch synchronise");
     if (first != GP_OK) return set_err(first, first_idx);

@@ -123,4 +123,36 @@ bool mixed_escalates(const gp_model* h, int code);
 int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md, double* vd, GpStatus* st,
                     Scratch& sc, cudaStream_t stream);
 
+// ---- batched predicts ----------------------------------------------------
+// Predicts against mixed-precision models, laid out for one upload and run
+// as one table launch plus one persistent predict launch per basis
+// dimension p among them. Each request's results are those of
+// predict_compute (the same per-point arithmetic and summation order).
+struct PredEntry {
+    const gp_model* m;  // GP_PREC_MIXED
+    const double* Xd;   // Ns x p test points (device)
+    int64_t Ns;
+    double* md;         // device outputs
+    double* vd;         // or NULL
+    GpStatus* st;       // this request's status word (device)
+};
+struct PredBatch {
+    std::vector<PredReq> reqs;
+    std::vector<int2> items;    // (request, tile), grouped by p, heavier requests first
+    std::vector<int> boff;      // table blocks of each request (nreq + 1)
+    std::vector<float> consts;  // 3p per request; PredReq::consts holds the float offset until pack()
+    struct Group {
+        int p, first, count, maxrows;
+    };
+    std::vector<Group> groups;
+    int max_n = 0, nblocks = 0;
+    size_t off_items = 0, off_boff = 0, off_consts = 0, total = 0;  // upload layout (bytes)
+};
+// Lays out the entries (tables of X* taken from sc) and sizes the upload.
+int pred_batch_build(const std::vector<PredEntry>& es, Scratch& sc, PredBatch& pb);
+// Writes the upload image for device address dev into host (pb.total bytes).
+void pred_batch_pack(PredBatch& pb, void* host, const uint8_t* dev);
+// The launches, once the image is on the device at dev (stream-ordered).
+int pred_batch_enqueue(const PredBatch& pb, const uint8_t* dev, cudaStream_t stream);
+
 }  // namespace gpi

@@ -150,9 +150,11 @@ size_t solve_refine_work_elems(int M);
 constexpr int PRED64_TT = 64;   // test points per CTA
 constexpr int PRED64_TK = 64;   // columns of Z = Phi_* W^T per CTA
 size_t predict64_part_elems(int64_t Ns, int M);
+// zout (optional): Z = Phi_* W^T, Npad x zld row-major, zld = 64 * ceil(M / 64)
 cudaError_t launch_predict64(const GpShape& s, const double* tab, const double* W, const double* c,
                              double sigma2, double* part, double* mean, double* var,
-                             cudaStream_t stream);
+                             cudaStream_t stream, double* zout = nullptr);
+size_t predict64_z_elems(int64_t Npad, int M);
 
 // ---- bf16x3 tensor-core predict (gp_predict_tc.cu) ------------------------------
 constexpr int PREDTC_TT = 128;  // test points per CTA (MMA M)
@@ -167,9 +169,56 @@ size_t predtc_smem_bytes(const GpShape& s);
 // Chunk table of the predict kernel (ints): built once per fitted model.
 size_t predtc_cinfo_ints(const GpShape& s);
 void predtc_build_cinfo(const GpShape& s, int* out);
+// One predict request of a mixed-precision model, as the predict kernel and
+// the batched table kernel read it (device tables of these, or one by value).
+struct PredReq {
+    int64_t Ns, Npad;       // test points; table rows (a multiple of 128)
+    int p, n, M, Mpad;      // the model's basis; Mpad a multiple of 128
+    int maxrows;            // the model's largest chunk window (= its zero window row)
+    int pad_;
+    const double* Xs;       // Ns x p test points
+    const float* consts;    // 3p floats: rho_j beta_j, sqrt(beta_j), delta_j^2 (batched tables)
+    float* tab;             // the eigenfunction tables of X*: (j n + k) Npad + i
+    const uint8_t* Wpack;   // the model's operand blocks (predtc_wpack_bytes)
+    const float* cf;        // the model's float32 c (in Wpack)
+    const int* cinfo;       // the model's chunk table (predtc_build_cinfo)
+    double sigma2;
+    double* mean;           // Ns outputs
+    double* var;            // Ns outputs, or NULL
+    uint8_t* zpack;         // optional rows of Z (predtc_zpack_bytes)
+    GpStatus* st;           // this request's status word
+};
+int predtc_window_rows(const GpShape& s);  // a model's PredReq::maxrows
+
+// The batched form (one launch per basis dimension p): the kernel's CTAs walk
+// items[0 .. nitems) = (request, 128-point tile) in a fixed round-robin order;
+// maxrows_all and crp4_all bound the requests' windows and column maps
+// (they size the pipeline stages). Every request's p must equal `p`.
+cudaError_t launch_predict_tc_batch(const PredReq* reqs, const int2* items, int nitems, int p, int maxrows_all,
+                                    cudaStream_t stream);
+size_t predtc_batch_smem_bytes(int maxrows_all, int p);
+// Tables of every request of a batch: the grid's blocks [boff[r], boff[r+1])
+// belong to request r (256 points x one dimension each; boff has nreq + 1
+// entries); max_n bounds the requests' n.
+void launch_eig_tables_batch(const PredReq* reqs, const int* boff, int nreq, int nblocks, int max_n,
+                             cudaStream_t stream);
+
+// zpack (optional, predtc_zpack_bytes): the rows of Z = Phi_* W^T as bf16
+// hi/lo, per 128-point tile and 32-column chunk an 8 KB hi block and an 8 KB
+// lo block in the K-major core-matrix layout of a tcgen05 operand
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
                               const int* cinfo, double sigma2, double* mean, double* var,
-                              GpStatus* st, cudaStream_t stream);
+                              GpStatus* st, cudaStream_t stream, uint8_t* zpack = nullptr);
+size_t predtc_zpack_bytes(int64_t Npad, int M);
+
+// ---- predictive covariance block (gp_cov.cu) ------------------------------------
+// cov (Ns x Ns row-major, leading dimension Ns) = sigma2 Z Z^T (+ sigma2 on
+// the diagonal when noisy): from the packed Z of launch_predict_tc (tensor
+// cores, 128 x 128 tiles) or the float64 Z of launch_predict64 (CUDA cores)
+cudaError_t launch_cov_tc(const uint8_t* zpack, int64_t Ns, int64_t Npad, int M, double sigma2, int noisy,
+                          double* cov, GpStatus* st, cudaStream_t stream);
+cudaError_t launch_cov64(const double* Z, int64_t Ns, int zld, double sigma2, int noisy, double* cov,
+                         cudaStream_t stream);
 
 // ---- log marginal likelihood terms (gp_lml.cu) ----------------------------------
 // out[0..3] = y^T y, b^T c, sum_j log L_jj, sum_m log d_m (float64, fixed

@@ -8,7 +8,9 @@
 // Phi_* is regenerated in shared memory from the test points' eigenfunction
 // tables. Each CTA writes the partial sum of squares of its Z tile and the
 // partial mean over its 64 values of m; a second kernel adds the partials
-// in column-tile order (deterministic).
+// in column-tile order (deterministic). With zout given, the Z tile itself is
+// also stored (row-major, zld = 64 x column tiles doubles per test point) for
+// the covariance block of Eq. 12 (gp_cov.cu).
 #include "gp_kernels.cuh"
 
 namespace {
@@ -20,7 +22,7 @@ constexpr int CK = 16;  // m columns per chunk
 __global__ void __launch_bounds__(256) predict64_kernel(GpShape s, const double* __restrict__ tab,
                                                         const double* __restrict__ W,
                                                         const double* __restrict__ cvec, int maxrows,
-                                                        double* __restrict__ part) {
+                                                        double* __restrict__ part, double* __restrict__ zout) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ TileWindow wv;
     double* win = (double*)smem_raw;                       // maxrows x TT
@@ -84,6 +86,13 @@ __global__ void __launch_bounds__(256) predict64_kernel(GpShape s, const double*
         }
         __syncthreads();
     }
+    if (zout != nullptr) {
+        const int64_t zld = (int64_t)nkt * TK;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) zout[(t0 + ty + 16 * a) * zld + k0 + tx + 16 * b] = acc[a][b];
+    }
     // partial sums of squares per test point
     double* pvar = part;                               // [nkt][Npad]
     double* pmean = part + (int64_t)nkt * s.Npad;      // [nkt][Npad]
@@ -121,7 +130,7 @@ size_t predict64_part_elems(int64_t Npad, int M) {
 
 cudaError_t launch_predict64(const GpShape& s, const double* tab, const double* W, const double* c,
                              double sigma2, double* part, double* mean, double* var,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, double* zout) {
     const int maxrows = gp_max_window_rows(s, CK);
     const size_t smem = sizeof(double) * ((size_t)maxrows * TT + TT * (CK + 1) + CK * TK) +
                         sizeof(int) * maxrows + sizeof(unsigned short) * CK * s.p + 16;
@@ -131,8 +140,12 @@ cudaError_t launch_predict64(const GpShape& s, const double* tab, const double* 
     }
     const int nkt = (s.M + TK - 1) / TK;
     dim3 grid((unsigned)(s.Npad / TT), (unsigned)nkt);
-    predict64_kernel<<<grid, 256, smem, stream>>>(s, tab, W, c, maxrows, part);
+    predict64_kernel<<<grid, 256, smem, stream>>>(s, tab, W, c, maxrows, part, zout);
     predict64_reduce_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, stream>>>(part, nkt, s.Npad, s.N,
                                                                             sigma2, mean, var);
     return cudaGetLastError();
+}
+
+size_t predict64_z_elems(int64_t Npad, int M) {
+    return (size_t)Npad * (size_t)(((M + TK - 1) / TK) * TK);
 }

@@ -22,7 +22,11 @@
 //              (W is lower triangular).
 // After a super-tile, the producers read their rows of Z from TMEM (each
 // half every other 32 columns) and add the squares into the variance; the
-// two halves' sums meet in shared memory at the end. Every wait is bounded; a warp decides with a
+// two halves' sums meet in shared memory at the end. With zpack given, the
+// rows of Z are also stored (bf16 hi/lo, the operand layout of the MMAs
+// here: per 128-point tile and 32-column chunk an 8 KB hi and an 8 KB lo
+// block) for the covariance block of Eq. 12 (gp_cov.cu).
+// Every wait is bounded; a warp decides with a
 // vote, so tcgen05 loads stay warp-uniform and no CTA-wide barrier is left
 // waiting for a warp that gave up.
 #include "gp_kernels.cuh"
@@ -54,9 +58,9 @@ __host__ __device__ inline uint32_t stage_bytes(int maxrows, int crp4) {
 }
 __host__ __device__ inline uint32_t map_off(int maxrows) { return WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4; }
 
-// barriers after the stages: full[S], wfull[S], empty[S], accf, tfree, tmem base
+// barriers after the stages: full[S], wfull[S], empty[S], accf, tfree, combf[2], tmem base
 __host__ __device__ inline size_t smem_bytes(int maxrows, int crp4) {
-    return 1024 + (size_t)STAGES * stage_bytes(maxrows, crp4) + 8 * (3 * STAGES + 2) + 8;
+    return 1024 + (size_t)STAGES * stage_bytes(maxrows, crp4) + 8 * (3 * STAGES + 4) + 8;
 }
 
 // number of 32-column chunks of Phi_* that meet the blocks b0 .. b0+nblk-1
@@ -97,35 +101,41 @@ __device__ __forceinline__ void gen8(const float* win, const int* map, int p, in
     }
 }
 
+// Item w of the launch: (request, 128-point tile). A plain predict passes
+// its one request by value and no item table (item w = tile w).
+__device__ __forceinline__ const PredReq& item_req(const PredReq& r0, const PredReq* __restrict__ reqs,
+                                                   const int2* __restrict__ items, int w, int& tile) {
+    if (items == nullptr) {
+        tile = w;
+        return r0;
+    }
+    const int2 it = __ldg(items + w);
+    tile = it.y;
+    return reqs[it.x];
+}
+
 template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    predict_tc_kernel(GpShape s, const float* __restrict__ tab, const uint8_t* __restrict__ Wpack,
-                      const float* __restrict__ cf, const int* __restrict__ cinfo, int maxrows,
-                      double sigma2, double* __restrict__ mean, double* __restrict__ var,
-                      GpStatus* st) {
+    predict_tc_kernel(const __grid_constant__ PredReq r0, const PredReq* __restrict__ reqs,
+                      const int2* __restrict__ items,
+                      int nitems, int maxrows_all, int crp4_all) {
     extern __shared__ __align__(1024) char smem_raw[];
     // 1 KB alignment by offsetting the shared array itself (keeps the
     // shared state space visible to the compiler)
     char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int p = P > 0 ? P : s.p;
-    const int maxrows4 = (maxrows + 3) & ~3;
-    const int crp4 = (BK * p + 3) & ~3;
-    const int cstride = 4 + maxrows4 + crp4;
-    const uint32_t SB = stage_bytes(maxrows, crp4);
-    const uint32_t MAPO = map_off(maxrows);
+    // the stage layout is sized for the largest window and map of the launch
+    const uint32_t SB = stage_bytes(maxrows_all, crp4_all);
+    const uint32_t MAPO = map_off(maxrows_all);
     uint8_t* stage = (uint8_t*)base;
     uint64_t* full = (uint64_t*)(base + (size_t)STAGES * SB);
     uint64_t* wfull = full + STAGES;
     uint64_t* empty = wfull + STAGES;
     uint64_t* accf = empty + STAGES;
     uint64_t* tfree = accf + 1;
-    uint32_t* tmem_base = (uint32_t*)(tfree + 1);
+    uint64_t* combf = tfree + 1;  // [2]
+    uint32_t* tmem_base = (uint32_t*)(combf + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t t0 = (int64_t)blockIdx.x * TT;
-    const int nblocks = (s.M + KB - 1) / KB;     // blocks of W rows with k < M
-    const int nsuper = (nblocks + SUPER - 1) / SUPER;
-    const int KBtot = s.Mpad / KB;               // blocks in the packed layout
 
     if (tid == 0) {
         for (int i = 0; i < STAGES; ++i) {
@@ -135,193 +145,272 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mbar_init(accf, 1);
         mbar_init(tfree, NPW);
+        mbar_init(&combf[0], NPW / 2);
+        mbar_init(&combf[1], NPW / 2);
         mbar_fence_init();
     }
-    // the zero window row of every stage (columns beyond M map to it)
-    if (tid < TT)
-        for (int i = 0; i < STAGES; ++i)
-            reinterpret_cast<float*>(stage + (size_t)i * SB + WIN_OFF)[maxrows * TT + tid] = 0.f;
     if (warp == MMA_W) tmem_alloc(tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
-    // the two producer threads of a test point combine their sums here
-    __shared__ double comb_m[TT], comb_v[TT];
-    __shared__ int comb_ok[TT];
+    // the second half of a test point's producer threads hands its sums to
+    // the first here, double-buffered by item
+    __shared__ double comb_m[2][TT], comb_v[2][TT];
     const int t = tid & (TT - 1);     // test point (and TMEM lane) of a producer thread
     const int hf = tid / TT;          // its half of every 32-column chunk
-    double macc = 0.0, vacc = 0.0;
-    bool pok = false;
 
+    // Pipeline counters run on across the items of this CTA (chunks gc,
+    // super-tiles gs, items li), so every barrier's phase follows from them.
     if (warp < NPW) {
         // ------------------------------------------------------------ producers + epilogue
         bool ok = true;
-        int gc = 0;
-        for (int sup = 0; sup < nsuper && ok; ++sup) {
-            const int b0 = sup * SUPER;
-            const int nblk = min(SUPER, nblocks - b0);
-            const int nch = super_chunks(s.M, b0, nblk);
-            const bool last = (sup == nsuper - 1);
-            for (int c = 0; c < nch; ++c, ++gc) {
-                const int stg = gc % STAGES;
-                // the stage's A tile is free (MMAs of chunk gc - STAGES done)
-                // and its window and map have landed
-                bool w = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
-                w = w && mbar_wait(&wfull[stg], (gc / STAGES) & 1);
-                if (!__all_sync(FULLMASK, w)) {
-                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 11);
+        int gc = 0, gs = 0, li = 0;
+        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++li) {
+            int tile;
+            const PredReq& R = item_req(r0, reqs, items, w, tile);
+            const int p = P > 0 ? P : R.p;
+            const int M = R.M;
+            const int64_t t0 = (int64_t)tile * TT;
+            const int nblocks = (M + KB - 1) / KB;  // blocks of W rows with k < M
+            const int nsuper = (nblocks + SUPER - 1) / SUPER;
+            const int KBtot = R.Mpad / KB;           // blocks in the packed layout
+            const float* cf = R.cf;
+            uint8_t* zpack = R.zpack;
+            GpStatus* st = R.st;
+            double macc = 0.0, vacc = 0.0;
+            for (int sup = 0; sup < nsuper && ok; ++sup, ++gs) {
+                const int b0 = sup * SUPER;
+                const int nblk = min(SUPER, nblocks - b0);
+                const int nch = super_chunks(M, b0, nblk);
+                const bool last = (sup == nsuper - 1);
+                for (int c = 0; c < nch; ++c, ++gc) {
+                    const int stg = gc % STAGES;
+                    // the stage's A tile is free (MMAs of chunk gc - STAGES done)
+                    // and its window and map have landed
+                    bool wt = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
+                    wt = wt && mbar_wait(&wfull[stg], (gc / STAGES) & 1);
+                    if (!__all_sync(FULLMASK, wt)) {
+                        if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 11);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sb = stage + (size_t)stg * SB;
+                    const float* win = reinterpret_cast<const float*>(sb + WIN_OFF);
+                    const int* map = reinterpret_cast<const int*>(sb + MAPO);
+                    float mpart = 0.f;
+#pragma unroll
+                    for (int g = 2 * hf; g < 2 * hf + 2; ++g) {
+                        float v[8];
+                        gen8<P>(win, map + g * 8 * p, p, t, v);
+                        if (last) {
+                            const float4 ca = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8));
+                            const float4 cb = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8 + 4));
+                            mpart = fmaf(v[0], ca.x, mpart);
+                            mpart = fmaf(v[1], ca.y, mpart);
+                            mpart = fmaf(v[2], ca.z, mpart);
+                            mpart = fmaf(v[3], ca.w, mpart);
+                            mpart = fmaf(v[4], cb.x, mpart);
+                            mpart = fmaf(v[5], cb.y, mpart);
+                            mpart = fmaf(v[6], cb.z, mpart);
+                            mpart = fmaf(v[7], cb.w, mpart);
+                        }
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
+                        const uint32_t off = (uint32_t)(t >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(t & 7) * 16;
+                        *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4*>(sb + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
+                    if (last) macc += (double)mpart;
+                    // every lane's operand writes before the async proxy's reads;
+                    // one arrival per warp
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[stg]);
+                }
+                if (!ok) break;
+                // epilogue of this super-tile: rows of Z from TMEM
+                const bool got = __all_sync(FULLMASK, mbar_wait(accf, gs & 1));
+                if (!got) {
+                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 12);
                     ok = false;
                     break;
                 }
-                uint8_t* sb = stage + (size_t)stg * SB;
-                const float* win = reinterpret_cast<const float*>(sb + WIN_OFF);
-                const int* map = reinterpret_cast<const int*>(sb + MAPO);
-                float mpart = 0.f;
+                tc_fence_after();
+                for (int bb = 0; bb < nblk; ++bb) {
+#pragma unroll 1
+                    for (int ch = hf; ch < KB / 32; ch += 2) {  // this half's 32-column pieces
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + bb * KB + ch * 32, v);
+                        float q = 0.f;
 #pragma unroll
-                for (int g = 2 * hf; g < 2 * hf + 2; ++g) {
-                    float v[8];
-                    gen8<P>(win, map + g * 8 * p, p, t, v);
-                    if (last) {
-                        const float4 ca = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8));
-                        const float4 cb = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8 + 4));
-                        mpart = fmaf(v[0], ca.x, mpart);
-                        mpart = fmaf(v[1], ca.y, mpart);
-                        mpart = fmaf(v[2], ca.z, mpart);
-                        mpart = fmaf(v[3], ca.w, mpart);
-                        mpart = fmaf(v[4], cb.x, mpart);
-                        mpart = fmaf(v[5], cb.y, mpart);
-                        mpart = fmaf(v[6], cb.z, mpart);
-                        mpart = fmaf(v[7], cb.w, mpart);
+                        for (int i = 0; i < 32; ++i) q = fmaf(v[i], v[i], q);
+                        vacc += (double)q;
+                        if (zpack != nullptr) {
+                            // chunk (b0 + bb) * 4 + ch of this tile's rows of Z
+                            uint8_t* zb = zpack + ((size_t)tile * (KBtot * (KB / BK)) +
+                                                   (size_t)(b0 + bb) * (KB / BK) + ch) * (2 * A_BYTES);
+#pragma unroll
+                            for (int g = 0; g < BK / 8; ++g) {
+                                uint32_t h[4], l[4];
+#pragma unroll
+                                for (int q2 = 0; q2 < 4; ++q2)
+                                    split_bf16x2(v[8 * g + 2 * q2], v[8 * g + 2 * q2 + 1], h[q2], l[q2]);
+                                const uint32_t off =
+                                    (uint32_t)(t >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(t & 7) * 16;
+                                *reinterpret_cast<uint4*>(zb + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                                *reinterpret_cast<uint4*>(zb + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                            }
+                        }
                     }
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-                    const uint32_t off = (uint32_t)(t >> 3) * SBO + (uint32_t)g * LBO + (uint32_t)(t & 7) * 16;
-                    *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(sb + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                if (last) macc += (double)mpart;
-                // every lane's operand writes before the async proxy's reads;
-                // one arrival per warp
-                fence_proxy_async_smem();
+                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&full[stg]);
+                if (lane == 0) mbar_arrive(tfree);
             }
             if (!ok) break;
-            // epilogue of this super-tile: rows of Z from TMEM
-            const bool got = __all_sync(FULLMASK, mbar_wait(accf, sup & 1));
-            if (!got) {
-                if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 12);
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            for (int bb = 0; bb < nblk; ++bb) {
-#pragma unroll 1
-                for (int ch = hf; ch < KB / 32; ch += 2) {  // this half's 32-column pieces
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + bb * KB + ch * 32, v);
-                    float q = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) q = fmaf(v[i], v[i], q);
-                    vacc += (double)q;
+            // the two halves' sums of each test point meet: the first half
+            // writes mean and variance
+            const int cbuf = li & 1;
+            if (hf == 1) {
+                comb_m[cbuf][t] = macc;
+                comb_v[cbuf][t] = vacc;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&combf[cbuf]);
+            } else {
+                if (!__all_sync(FULLMASK, mbar_wait(&combf[cbuf], (li >> 1) & 1))) {
+                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 16);
+                    ok = false;
+                    break;
+                }
+                if (t0 + t < R.Ns) {
+                    R.mean[t0 + t] = macc + comb_m[cbuf][t];
+                    if (R.var) R.var[t0 + t] = R.sigma2 * (vacc + comb_v[cbuf][t]);
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tfree);
-        }
-        pok = ok;
-        if (hf == 1) {
-            comb_m[t] = macc;
-            comb_v[t] = vacc;
-            comb_ok[t] = ok ? 1 : 0;
         }
     } else if (warp == MMA_W) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(TT, KB);
             const uint32_t sbase = smem_u32(stage);
-            int gc = 0;
+            int gc = 0, gs = 0;
             bool ok = true;
-            for (int sup = 0; sup < nsuper && ok; ++sup) {
-                const int b0 = sup * SUPER;
-                const int nblk = min(SUPER, nblocks - b0);
-                const int nch = super_chunks(s.M, b0, nblk);
-                if (sup > 0 && !mbar_wait(tfree, (sup - 1) & 1)) {
-                    gp_set_status(st, GP_ETIMEOUT, 13);
-                    break;
-                }
-                tc_fence_after();
-                for (int c = 0; c < nch; ++c, ++gc) {
-                    const int stg = gc % STAGES;
-                    if (!mbar_wait(&full[stg], (gc / STAGES) & 1) ||
-                        !mbar_wait(&wfull[stg], (gc / STAGES) & 1)) {
-                        gp_set_status(st, GP_ETIMEOUT, 14);
+            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                int tile;
+                const PredReq& R = item_req(r0, reqs, items, w, tile);
+                const int M = R.M;
+                GpStatus* st = R.st;
+                const int nblocks = (M + KB - 1) / KB;
+                const int nsuper = (nblocks + SUPER - 1) / SUPER;
+                for (int sup = 0; sup < nsuper && ok; ++sup, ++gs) {
+                    const int b0 = sup * SUPER;
+                    const int nblk = min(SUPER, nblocks - b0);
+                    const int nch = super_chunks(M, b0, nblk);
+                    if (gs > 0 && !mbar_wait(tfree, (gs - 1) & 1)) {
+                        gp_set_status(st, GP_ETIMEOUT, 13);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_hi = sbase + stg * SB;
-                    const uint32_t a_lo = a_hi + A_BYTES;
-                    const uint32_t wbase = a_hi + 2 * A_BYTES;
-                    for (int bb = 0; bb < nblk; ++bb) {
-                        if (c > 4 * (b0 + bb) + 3) continue;  // W[k][m] = 0 for m > k
-                        const uint32_t w_hi = wbase + bb * 2 * WB_BYTES;
-                        const uint32_t w_lo = w_hi + WB_BYTES;
-                        const uint32_t d = tmem + bb * KB;
-#pragma unroll
-                        for (int ks = 0; ks < BK / 16; ++ks) {
-                            const uint32_t ko = ks * 2 * LBO;
-                            const uint64_t dAh = smem_desc(a_hi + ko, LBO, SBO);
-                            const uint64_t dAl = smem_desc(a_lo + ko, LBO, SBO);
-                            const uint64_t dBh = smem_desc(w_hi + ko, LBO, SBO);
-                            const uint64_t dBl = smem_desc(w_lo + ko, LBO, SBO);
-                            mma_bf16(d, dAh, dBh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_bf16(d, dAh, dBl, idesc, 1u);
-                            mma_bf16(d, dAl, dBh, idesc, 1u);
+                    for (int c = 0; c < nch; ++c, ++gc) {
+                        const int stg = gc % STAGES;
+                        if (!mbar_wait(&full[stg], (gc / STAGES) & 1) ||
+                            !mbar_wait(&wfull[stg], (gc / STAGES) & 1)) {
+                            gp_set_status(st, GP_ETIMEOUT, 14);
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t a_hi = sbase + stg * SB;
+                        const uint32_t a_lo = a_hi + A_BYTES;
+                        const uint32_t wbase = a_hi + 2 * A_BYTES;
+                        for (int bb = 0; bb < nblk; ++bb) {
+                            if (c > 4 * (b0 + bb) + 3) continue;  // W[k][m] = 0 for m > k
+                            const uint32_t w_hi = wbase + bb * 2 * WB_BYTES;
+                            const uint32_t w_lo = w_hi + WB_BYTES;
+                            const uint32_t d = tmem + bb * KB;
+#pragma unroll
+                            for (int ks = 0; ks < BK / 16; ++ks) {
+                                const uint32_t ko = ks * 2 * LBO;
+                                const uint64_t dAh = smem_desc(a_hi + ko, LBO, SBO);
+                                const uint64_t dAl = smem_desc(a_lo + ko, LBO, SBO);
+                                const uint64_t dBh = smem_desc(w_hi + ko, LBO, SBO);
+                                const uint64_t dBl = smem_desc(w_lo + ko, LBO, SBO);
+                                mma_bf16(d, dAh, dBh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                                mma_bf16(d, dAh, dBl, idesc, 1u);
+                                mma_bf16(d, dAl, dBh, idesc, 1u);
+                            }
+                        }
+                        mma_commit(&empty[stg]);
                     }
-                    mma_commit(&empty[stg]);
+                    if (!ok) break;
+                    mma_commit(accf);
                 }
-                mma_commit(accf);
             }
+            // the MMAs issued so far complete before TMEM is freed
+            if (gc > 0) mbar_wait(&empty[(gc - 1) % STAGES], ((gc - 1) / STAGES) & 1);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ loader (bulk copies, all lanes)
         int gc = 0;
         bool ok = true;
-        for (int sup = 0; sup < nsuper && ok; ++sup) {
-            const int b0 = sup * SUPER;
-            const int nblk = min(SUPER, nblocks - b0);
-            const int nch = super_chunks(s.M, b0, nblk);
-            for (int c = 0; c < nch; ++c, ++gc) {
-                const int stg = gc % STAGES;
-                const int* ci = cinfo + (int64_t)c * cstride;
-                const int nrows = __ldg(ci);
-                // table rows of this lane's window rows (read before the wait)
-                const int row0 = lane < nrows ? __ldg(ci + 4 + lane) : 0;
-                const bool e = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
-                if (!__all_sync(FULLMASK, e)) {
-                    if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 15);
-                    ok = false;
-                    break;
-                }
-                uint8_t* sb = stage + (size_t)stg * SB;
-                const uint32_t wbytes = (uint32_t)nblk * 2 * WB_BYTES;
-                if (lane == 0)
-                    mbar_arrive_expect_tx(&wfull[stg], wbytes + (uint32_t)nrows * TT * 4 + (uint32_t)crp4 * 4);
-                __syncwarp();
-                if (lane == 0)
-                    bulk_g2s(sb + 2 * A_BYTES, Wpack + ((size_t)c * KBtot + b0) * 2 * WB_BYTES, wbytes,
-                             &wfull[stg]);
-                if (lane == 1) bulk_g2s(sb + MAPO, ci + 4 + maxrows4, (uint32_t)crp4 * 4, &wfull[stg]);
-                for (int r = lane; r < nrows; r += 32) {
-                    const int row = r < 32 ? row0 : __ldg(ci + 4 + r);
-                    bulk_g2s(sb + WIN_OFF + (size_t)r * TT * 4, tab + (int64_t)row * s.Npad + t0, TT * 4,
-                             &wfull[stg]);
+        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            int tile;
+            const PredReq& R = item_req(r0, reqs, items, w, tile);
+            const int p = P > 0 ? P : R.p;
+            const int M = R.M;
+            GpStatus* st = R.st;
+            const int64_t t0 = (int64_t)tile * TT;
+            const int nblocks = (M + KB - 1) / KB;
+            const int nsuper = (nblocks + SUPER - 1) / SUPER;
+            const int KBtot = R.Mpad / KB;
+            const int mrows = R.maxrows;
+            const int crp4 = (BK * p + 3) & ~3;
+            const int cstride = 4 + ((mrows + 3) & ~3) + crp4;
+            const int* cinfo = R.cinfo;
+            const uint8_t* Wpack = R.Wpack;
+            const float* tab = R.tab;
+            const int64_t Npad = R.Npad;
+            for (int sup = 0; sup < nsuper && ok; ++sup) {
+                const int b0 = sup * SUPER;
+                const int nblk = min(SUPER, nblocks - b0);
+                const int nch = super_chunks(M, b0, nblk);
+                for (int c = 0; c < nch; ++c, ++gc) {
+                    const int stg = gc % STAGES;
+                    const int* ci = cinfo + (int64_t)c * cstride;
+                    const int nrows = __ldg(ci);
+                    // table rows of this lane's window rows (read before the wait)
+                    const int row0 = lane < nrows ? __ldg(ci + 4 + lane) : 0;
+                    const bool e = gc < STAGES || mbar_wait(&empty[stg], ((gc / STAGES) - 1) & 1);
+                    if (!__all_sync(FULLMASK, e)) {
+                        if (lane == 0) gp_set_status(st, GP_ETIMEOUT, 15);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sb = stage + (size_t)stg * SB;
+                    // the model's zero window row (columns beyond M map to
+                    // it): 128 floats, one float4 a lane, before the arrival
+                    reinterpret_cast<float4*>(sb + WIN_OFF + (size_t)mrows * TT * 4)[lane] =
+                        make_float4(0.f, 0.f, 0.f, 0.f);
+                    __syncwarp();
+                    const uint32_t wbytes = (uint32_t)nblk * 2 * WB_BYTES;
+                    if (lane == 0)
+                        mbar_arrive_expect_tx(&wfull[stg],
+                                              wbytes + (uint32_t)nrows * TT * 4 + (uint32_t)crp4 * 4);
+                    __syncwarp();
+                    if (lane == 0)
+                        bulk_g2s(sb + 2 * A_BYTES, Wpack + ((size_t)c * KBtot + b0) * 2 * WB_BYTES, wbytes,
+                                 &wfull[stg]);
+                    if (lane == 1)
+                        bulk_g2s(sb + MAPO, ci + 4 + ((mrows + 3) & ~3), (uint32_t)crp4 * 4, &wfull[stg]);
+                    for (int r = lane; r < nrows; r += 32) {
+                        const int row = r < 32 ? row0 : __ldg(ci + 4 + r);
+                        bulk_g2s(sb + WIN_OFF + (size_t)r * TT * 4, tab + (int64_t)row * Npad + t0, TT * 4,
+                                 &wfull[stg]);
+                    }
                 }
             }
         }
@@ -335,10 +424,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == MMA_W) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
-    }
-    if (tid < TT && pok && comb_ok[t] && t0 + t < s.N) {
-        mean[t0 + t] = macc + comb_m[t];
-        if (var) var[t0 + t] = sigma2 * (vacc + comb_v[t]);
     }
 }
 
@@ -389,31 +474,80 @@ size_t predtc_smem_bytes(const GpShape& s) {
     return smem_bytes(predtc_maxrows(s), (BK * s.p + 3) & ~3);
 }
 
+int predtc_window_rows(const GpShape& s) { return predtc_maxrows(s); }
+
+size_t predtc_batch_smem_bytes(int maxrows_all, int p) { return smem_bytes(maxrows_all, (BK * p + 3) & ~3); }
+
 namespace {
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
 template <int P>
-cudaError_t predict_tc_launch(const GpShape& s, const float* tab, const uint16_t* Wpack, const int* cinfo,
-                              double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream) {
-    const int maxrows = predtc_maxrows(s);
-    const size_t smem = predtc_smem_bytes(s);
-    if (smem > (227 - 4) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
+cudaError_t predict_tc_launch_t(const PredReq& r0, const PredReq* reqs, const int2* items, int nitems,
+                                int maxrows_all, int p, cudaStream_t stream) {
+    if (nitems <= 0) return cudaSuccess;
+    const int crp4 = (BK * p + 3) & ~3;
+    const size_t smem = smem_bytes(maxrows_all, crp4);
+    if (smem > (227 - 5) * 1024) return cudaErrorInvalidConfiguration;  // static shared memory beside it
     cudaError_t e = gp_allow_max_smem((const void*)predict_tc_kernel<P>);
     if (e != cudaSuccess) return e;
-    const size_t Mpad = (size_t)gp_round_up(s.M, KB);
-    const float* cf = reinterpret_cast<const float*>((const uint8_t*)Wpack + 4 * Mpad * Mpad);
-    const unsigned grid = (unsigned)(s.Npad / TT);
-    predict_tc_kernel<P><<<grid, NTHREADS, smem, stream>>>(s, tab, (const uint8_t*)Wpack, cf, cinfo, maxrows,
-                                                           sigma2, mean, var, st);
+    // persistent: one CTA per SM (the stages take most of its shared memory)
+    const int grid = nitems < sm_count() ? nitems : sm_count();
+    predict_tc_kernel<P><<<(unsigned)grid, NTHREADS, smem, stream>>>(r0, reqs, items, nitems, maxrows_all, crp4);
     return cudaGetLastError();
+}
+
+cudaError_t predict_tc_dispatch(const PredReq& r0, const PredReq* reqs, const int2* items, int nitems,
+                                int maxrows_all, int p, cudaStream_t stream) {
+    switch (p) {
+        case 1: return predict_tc_launch_t<1>(r0, reqs, items, nitems, maxrows_all, p, stream);
+        case 2: return predict_tc_launch_t<2>(r0, reqs, items, nitems, maxrows_all, p, stream);
+        case 3: return predict_tc_launch_t<3>(r0, reqs, items, nitems, maxrows_all, p, stream);
+        case 4: return predict_tc_launch_t<4>(r0, reqs, items, nitems, maxrows_all, p, stream);
+        default: return predict_tc_launch_t<0>(r0, reqs, items, nitems, maxrows_all, p, stream);
+    }
 }
 }  // namespace
 
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack, const int* cinfo,
-                              double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream) {
-    switch (s.p) {
-        case 1: return predict_tc_launch<1>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
-        case 2: return predict_tc_launch<2>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
-        case 3: return predict_tc_launch<3>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
-        case 4: return predict_tc_launch<4>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
-        default: return predict_tc_launch<0>(s, tab, Wpack, cinfo, sigma2, mean, var, st, stream);
-    }
+                              double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream,
+                              uint8_t* zpack) {
+    PredReq r{};
+    r.Ns = s.N;
+    r.Npad = s.Npad;
+    r.p = s.p;
+    r.n = s.n;
+    r.M = s.M;
+    r.Mpad = (int)gp_round_up(s.M, KB);
+    r.maxrows = predtc_maxrows(s);
+    r.tab = const_cast<float*>(tab);
+    r.Wpack = (const uint8_t*)Wpack;
+    r.cf = reinterpret_cast<const float*>((const uint8_t*)Wpack + 4 * (size_t)r.Mpad * r.Mpad);
+    r.cinfo = cinfo;
+    r.sigma2 = sigma2;
+    r.mean = mean;
+    r.var = var;
+    r.zpack = zpack;
+    r.st = st;
+    return predict_tc_dispatch(r, nullptr, nullptr, (int)(s.Npad / TT), r.maxrows, s.p, stream);
+}
+
+cudaError_t launch_predict_tc_batch(const PredReq* reqs, const int2* items, int nitems, int p, int maxrows_all,
+                                    cudaStream_t stream) {
+    PredReq none{};
+    return predict_tc_dispatch(none, reqs, items, nitems, maxrows_all, p, stream);
+}
+
+size_t predtc_zpack_bytes(int64_t Npad, int M) {
+    return (size_t)Npad * (size_t)gp_round_up(M, KB) * 4;
 }

@@ -4,19 +4,24 @@
 // The server owns a worker thread, `slots` CUDA streams and a device-memory
 // budget for request scratch. Models stay resident on the device. Requests
 // (predict: X* -> mean, var; refit: new training set for a resident model)
-// queue in arrival order; the worker admits the queue head whenever a slot
-// is free and the head's scratch estimate fits the budget, so requests that
-// arrive while others are on the GPU start as soon as room frees up, and the
-// admitted requests run side by side on their own streams. Each request's
-// kernels are exactly those of gp_predict_ex / gp_fit_ex (same launch
-// plans), so its result does not depend on what else is running.
+// queue in arrival order. Whenever a slot is free the worker starts a job
+// on it: a refit at the queue head, or every predict queued at the head (up
+// to a request and point limit, and within the budget) packed into one
+// batch. A batch makes one host-to-device copy of all its test points and
+// of a request table, one launch that evaluates all their eigenfunction
+// tables, one persistent tensor-core predict launch per basis dimension p
+// whose CTAs walk the (request, 128-point tile) items, and one copy of all
+// results back (float64 models run their own predict kernels inside the
+// batch). So requests that arrive while the GPU is busy leave together
+// with little per-request cost, and each request's result is the same as
+// gp_predict_ex's on it alone (the same per-point arithmetic and order).
 //
 // Host buffers are staged through pinned per-slot memory so that no copy
 // blocks the worker; results are copied to the caller's buffers when the
-// request's completion event has fired. A refit builds a new model on its
-// slot and swaps it in at completion; requests already admitted against the
-// old model finish on it, and it is freed when the last of them completes.
-// The server owns the models registered with it and frees them at destroy.
+// job's completion event has fired. A refit builds a new model on its slot
+// and swaps it in at completion; requests already admitted against the old
+// model finish on it, and it is freed when the last of them completes. The
+// server owns the models registered with it and frees them at destroy.
 #include "gp_internal.cuh"
 
 #include <math.h>
@@ -80,6 +85,7 @@ struct Request {
     int64_t Ns = 0;
     double* mean = nullptr;
     double* var = nullptr;
+    int64_t xoff = 0, ooff = 0;  // its rows in the batch's packed X* and outputs
     // refit
     const double* X = nullptr;
     const double* y = nullptr;
@@ -87,15 +93,23 @@ struct Request {
     size_t bytes = 0;  // scratch estimate charged against the budget
     Clock::time_point t_submit, t_start, t_end;
     int status = 1;  // 1 = pending / running, else a GP_* status
-    // while running
-    int slot = -1;
     gp_model* used = nullptr;  // the model a predict runs against
-    gp_model* fresh = nullptr; // the model a refit builds
+};
+
+// What a slot runs: a batch of predicts, or one refit.
+struct Job {
+    int kind = 0;  // 0 predicts, 1 refit
+    std::vector<Request*> reqs;
+    size_t bytes = 0;
     Scratch* sc = nullptr;
+    // predicts: pinned layout [X* | request table image | mean | var | statuses]
+    size_t xbytes = 0, img_bytes = 0;
+    int64_t points = 0;
+    // refit
+    gp_model* fresh = nullptr;
     GpStatus* st = nullptr;
     FitStage stage;
-    // refit: staged device inputs, and the float64-Gram retry
-    double* xd = nullptr;
+    double* xd = nullptr;  // staged device inputs (X then y) for the float64-Gram retry
     double* ll = nullptr;
     Scratch* sc2 = nullptr;
     bool escalated = false;
@@ -110,7 +124,7 @@ struct gp_server {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done_ev;
     std::vector<Pinned> pin;
-    std::vector<Request*> slot_req;
+    std::vector<Job*> slot_job;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -121,8 +135,11 @@ struct gp_server {
     std::map<int64_t, Request*> all;
     int64_t next_id = 1;
     size_t mem_used = 0;
-    int inflight = 0;
-    int peak_inflight = 0;
+    int inflight = 0;       // jobs on the slots
+    int inflight_reqs = 0;  // requests in those jobs
+    int peak_inflight = 0;  // most requests on the device at once
+    int peak_batch = 0;     // most predicts in one batch
+    int64_t batches = 0;    // predict batches started
     // statistics of finished predicts
     std::vector<double> lat_ms;
     int64_t points = 0;
@@ -158,54 +175,98 @@ size_t refit_bytes(const gp_model* m, int64_t N, int sms) {
     return b + (4 << 20);
 }
 
-// Start request r on `slot` (worker thread, lock held).
-int launch_request(gp_server* S, Request* r, int slot) {
+constexpr int kBatchRequests = 256;          // most predicts in one batch
+constexpr int64_t kBatchPoints = 1 << 20;      // most test points in one batch (unless one request has more)
+
+// Start a batch of predicts on `slot` (worker thread, lock held).
+int launch_predicts(gp_server* S, Job* J, int slot) {
     cudaStream_t st = S->streams[slot];
     Pinned& pin = S->pin[slot];
-    r->slot = slot;
-    r->sc = new Scratch(st);
-    int rc;
-    if ((rc = r->sc->get(&r->st, 1))) return rc;
-    cudaMemsetAsync(r->st, 0, sizeof(GpStatus), st);
-    if (r->kind == 0) {
-        gp_model* m = r->used;
-        const int p = m->shape.p;
-        const size_t in = (size_t)r->Ns * p * 8, out = (size_t)r->Ns * 8;
-        // pinned layout: X* | mean | var | status
-        if ((rc = pin.reserve(in + 2 * out + sizeof(GpStatus)))) return set_err(rc);
-        memcpy(pin.p, r->Xs, in);
-        double *xd = nullptr, *md = nullptr, *vd = nullptr;
-        if ((rc = r->sc->get(&xd, (size_t)r->Ns * p))) return rc;
-        if ((rc = r->sc->get(&md, (size_t)r->Ns))) return rc;
-        if (r->var && (rc = r->sc->get(&vd, (size_t)r->Ns))) return rc;
-        cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
-        if ((rc = predict_compute(m, xd, r->Ns, md, vd, r->st, *r->sc, st))) return rc;
-        char* hp = (char*)pin.p;
-        cudaMemcpyAsync(hp + in, md, out, cudaMemcpyDeviceToHost, st);
-        if (vd) cudaMemcpyAsync(hp + in + out, vd, out, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(hp + in + 2 * out, r->st, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
-    } else {
-        const gp_model* old = S->models[r->model].model;
-        const GpShape& s = old->shape;
-        gp_model* h = new_model(S->device, old->prec, r->N, s.p, s.n, old->eps, old->alpha, old->sigma2);
-        r->fresh = h;
-        if ((rc = fit_alloc(h, st))) return rc;
-        const size_t in = (size_t)r->N * (s.p + 1) * 8;
-        if ((rc = pin.reserve(in + sizeof(GpStatus)))) return set_err(rc);
-        memcpy(pin.p, r->X, (size_t)r->N * s.p * 8);
-        memcpy((char*)pin.p + (size_t)r->N * s.p * 8, r->y, (size_t)r->N * 8);
-        // one device buffer holds X (N x p) followed by y (N), as staged
-        double *xd = nullptr, *ll = nullptr;
-        if ((rc = r->sc->get(&xd, (size_t)r->N * (s.p + 1)))) return rc;
-        if ((rc = r->sc->get(&ll, (size_t)s.p * s.n))) return rc;
-        cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
-        const double* yd = xd + (size_t)r->N * s.p;
-        r->xd = xd;
-        r->ll = ll;
-        if ((rc = fit_stage(h, r->stage, ll, st))) return rc;
-        if ((rc = fit_compute(h, xd, yd, ll, r->st, 0, *r->sc, st))) return rc;
-        cudaMemcpyAsync((char*)pin.p + in, r->st, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
+    J->sc = new Scratch(st);
+    Scratch& sc = *J->sc;
+    const int cnt = (int)J->reqs.size();
+    int64_t xs = 0, pts = 0;
+    for (Request* r : J->reqs) {
+        r->xoff = xs;
+        r->ooff = pts;
+        xs += r->Ns * r->used->shape.p;
+        pts += r->Ns;
     }
+    J->points = pts;
+    J->xbytes = (size_t)xs * 8;
+    const size_t obytes = 2 * (size_t)pts * 8 + sizeof(GpStatus) * cnt;  // mean | var | statuses
+    int rc;
+    double* xd = nullptr;
+    uint8_t* od = nullptr;
+    if ((rc = sc.get(&xd, (size_t)xs))) return rc;
+    if ((rc = sc.get(&od, obytes))) return rc;
+    double* md = reinterpret_cast<double*>(od);
+    double* vd = md + pts;
+    GpStatus* sts = reinterpret_cast<GpStatus*>(vd + pts);
+    cudaMemsetAsync(sts, 0, sizeof(GpStatus) * cnt, st);
+    std::vector<PredEntry> mixed;
+    std::vector<int> f64;
+    for (int i = 0; i < cnt; ++i) {
+        Request* r = J->reqs[i];
+        if (r->used->prec == GP_PREC_FP64) {
+            f64.push_back(i);
+        } else {
+            mixed.push_back(PredEntry{r->used, xd + r->xoff, r->Ns, md + r->ooff, r->var ? vd + r->ooff : nullptr,
+                                      &sts[i]});
+        }
+    }
+    PredBatch pb;
+    uint8_t* up = nullptr;
+    if ((rc = pred_batch_build(mixed, sc, pb))) return rc;
+    if (pb.total && (rc = sc.get(&up, pb.total))) return rc;
+    J->img_bytes = (pb.total + 15) & ~(size_t)15;
+    if ((rc = pin.reserve(J->xbytes + J->img_bytes + obytes))) return set_err(rc);
+    uint8_t* hp = (uint8_t*)pin.p;
+    for (Request* r : J->reqs) memcpy(hp + r->xoff * 8, r->Xs, (size_t)r->Ns * r->used->shape.p * 8);
+    if (pb.total) pred_batch_pack(pb, hp + J->xbytes, up);
+    cudaMemcpyAsync(xd, hp, J->xbytes, cudaMemcpyHostToDevice, st);
+    if (pb.total) cudaMemcpyAsync(up, hp + J->xbytes, pb.total, cudaMemcpyHostToDevice, st);
+    if ((rc = pred_batch_enqueue(pb, up, st))) return rc;
+    for (int i : f64) {
+        Request* r = J->reqs[i];
+        if ((rc = predict_compute(r->used, xd + r->xoff, r->Ns, md + r->ooff, r->var ? vd + r->ooff : nullptr,
+                                  &sts[i], sc, st)))
+            return rc;
+    }
+    cudaMemcpyAsync(hp + J->xbytes + J->img_bytes, od, obytes, cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(S->done_ev[slot], st);
+    return GP_OK;
+}
+
+// Start a refit on `slot` (worker thread, lock held).
+int launch_refit(gp_server* S, Job* J, int slot) {
+    cudaStream_t st = S->streams[slot];
+    Pinned& pin = S->pin[slot];
+    Request* r = J->reqs[0];
+    J->sc = new Scratch(st);
+    int rc;
+    if ((rc = J->sc->get(&J->st, 1))) return rc;
+    cudaMemsetAsync(J->st, 0, sizeof(GpStatus), st);
+    const gp_model* old = S->models[r->model].model;
+    const GpShape& s = old->shape;
+    gp_model* h = new_model(S->device, old->prec, r->N, s.p, s.n, old->eps, old->alpha, old->sigma2);
+    J->fresh = h;
+    if ((rc = fit_alloc(h, st))) return rc;
+    const size_t in = (size_t)r->N * (s.p + 1) * 8;
+    if ((rc = pin.reserve(in + sizeof(GpStatus)))) return set_err(rc);
+    memcpy(pin.p, r->X, (size_t)r->N * s.p * 8);
+    memcpy((char*)pin.p + (size_t)r->N * s.p * 8, r->y, (size_t)r->N * 8);
+    // one device buffer holds X (N x p) followed by y (N), as staged
+    double *xd = nullptr, *ll = nullptr;
+    if ((rc = J->sc->get(&xd, (size_t)r->N * (s.p + 1)))) return rc;
+    if ((rc = J->sc->get(&ll, (size_t)s.p * s.n))) return rc;
+    cudaMemcpyAsync(xd, pin.p, in, cudaMemcpyHostToDevice, st);
+    const double* yd = xd + (size_t)r->N * s.p;
+    J->xd = xd;
+    J->ll = ll;
+    if ((rc = fit_stage(h, J->stage, ll, st))) return rc;
+    if ((rc = fit_compute(h, xd, yd, ll, J->st, 0, *J->sc, st))) return rc;
+    cudaMemcpyAsync((char*)pin.p + in, J->st, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(S->done_ev[slot], st);
     return GP_OK;
 }
@@ -213,78 +274,85 @@ int launch_request(gp_server* S, Request* r, int slot) {
 // A refit whose mixed Gram met a non-positive pivot: redo the fit on the same
 // slot with the float64 Gram (its staged inputs are still on the device).
 // Returns false if the retry could not be enqueued.
-bool escalate_refit(gp_server* S, Request* r) {
-    const int slot = r->slot;
+bool escalate_refit(gp_server* S, Job* J, int slot) {
     cudaStream_t st = S->streams[slot];
-    const GpShape& s = r->fresh->shape;
-    r->escalated = true;
-    r->sc2 = new Scratch(st);
+    Request* r = J->reqs[0];
+    const GpShape& s = J->fresh->shape;
+    J->escalated = true;
+    J->sc2 = new Scratch(st);
     GpStatus* st2 = nullptr;
-    if (r->sc2->get(&st2, 1)) return false;
+    if (J->sc2->get(&st2, 1)) return false;
     cudaMemsetAsync(st2, 0, sizeof(GpStatus), st);
-    const double* yd = r->xd + (size_t)r->N * s.p;
-    if (fit_compute(r->fresh, r->xd, yd, r->ll, st2, 0, *r->sc2, st, GP_PREC_FP64)) return false;
+    const double* yd = J->xd + (size_t)r->N * s.p;
+    if (fit_compute(J->fresh, J->xd, yd, J->ll, st2, 0, *J->sc2, st, GP_PREC_FP64)) return false;
     const size_t in = (size_t)r->N * (s.p + 1) * 8;
     cudaMemcpyAsync((char*)S->pin[slot].p + in, st2, sizeof(GpStatus), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(S->done_ev[slot], st);
-    r->st = st2;
+    J->st = st2;
     return true;
 }
 
-// Request r has completed (or failed to launch): results out, accounting (lock held).
-void finish_request(gp_server* S, Request* r, int launch_rc) {
-    r->t_end = Clock::now();
+// release the user count on the model a predict ran against (lock held)
+void release_model(gp_server* S, const gp_model* m) {
+    for (Resident& res : S->models)
+        if (res.model == m) {
+            res.users -= 1;
+            break;
+        }
+}
+
+// The job on `slot` has completed (or failed to launch): results out,
+// accounting (lock held).
+void finish_job(gp_server* S, int slot, int launch_rc) {
+    Job* J = S->slot_job[slot];
+    const Clock::time_point now = Clock::now();
     int code = launch_rc;
-    Pinned& pin = S->pin[r->slot];
     if (code == GP_OK) {
-        if (cudaEventSynchronize(S->done_ev[r->slot]) != cudaSuccess) code = GP_ECUDA;
+        if (cudaEventSynchronize(S->done_ev[slot]) != cudaSuccess) code = GP_ECUDA;
     } else {
-        cudaStreamSynchronize(S->streams[r->slot]);
+        cudaStreamSynchronize(S->streams[slot]);
     }
-    if (code == GP_OK) {
-        GpStatus hs;
-        if (r->kind == 0) {
-            const size_t in = (size_t)r->Ns * r->used->shape.p * 8, out = (size_t)r->Ns * 8;
-            const char* hp = (const char*)pin.p;
-            memcpy(&hs, hp + in + 2 * out, sizeof(hs));
-            if (hs.code == GP_OK) {
-                memcpy(r->mean, hp + in, out);
-                if (r->var) memcpy(r->var, hp + in + out, out);
+    const Pinned& pin = S->pin[slot];
+    if (J->kind == 0) {
+        const uint8_t* hp = (const uint8_t*)pin.p;
+        const double* hm = reinterpret_cast<const double*>(hp + J->xbytes + J->img_bytes);
+        const double* hv = hm + J->points;
+        const GpStatus* hs = reinterpret_cast<const GpStatus*>(hv + J->points);
+        for (size_t i = 0; i < J->reqs.size(); ++i) {
+            Request* r = J->reqs[i];
+            int rc = code;
+            if (rc == GP_OK) {
+                rc = hs[i].code;
+                if (rc == GP_OK) {
+                    memcpy(r->mean, hm + r->ooff, (size_t)r->Ns * 8);
+                    if (r->var) memcpy(r->var, hv + r->ooff, (size_t)r->Ns * 8);
+                }
             }
-        } else {
+            r->t_end = now;
+            r->status = rc;
+            release_model(S, r->used);
+            if (rc == GP_OK) {
+                S->lat_ms.push_back(ms_between(r->t_submit, r->t_end));
+                S->points += r->Ns;
+            }
+        }
+    } else {
+        Request* r = J->reqs[0];
+        if (code == GP_OK) {
+            GpStatus hs;
             memcpy(&hs, (const char*)pin.p + (size_t)r->N * (S->models[r->model].model->shape.p + 1) * 8,
                    sizeof(hs));
-            if (!r->escalated && mixed_escalates(r->fresh, hs.code) && escalate_refit(S, r))
+            if (!J->escalated && mixed_escalates(J->fresh, hs.code) && escalate_refit(S, J, slot))
                 return;  // still running: finished when the retry completes
+            code = hs.code;
         }
-        code = hs.code;
-    }
-    delete r->sc;  // stream-ordered frees behind the finished work
-    r->sc = nullptr;
-    delete r->sc2;
-    r->sc2 = nullptr;
-    r->status = code;
-    S->slot_req[r->slot] = nullptr;
-    S->mem_used -= r->bytes;
-    S->inflight -= 1;
-    if (r->kind == 0) {
-        // release the user count on the model this request ran against
-        for (Resident& res : S->models)
-            if (res.model == r->used) {
-                res.users -= 1;
-                break;
-            }
-        // a retired model is kept in a side list until its users drain
-        if (code == GP_OK) {
-            S->lat_ms.push_back(ms_between(r->t_submit, r->t_end));
-            S->points += r->Ns;
-        }
-    } else {
+        r->t_end = now;
+        r->status = code;
         Resident& res = S->models[r->model];
         if (code == GP_OK) {
             gp_model* old = res.model;
-            res.model = r->fresh;
-            r->fresh = nullptr;
+            res.model = J->fresh;
+            J->fresh = nullptr;
             S->refits_done += 1;
             if (res.users == 0) {
                 free_model(old);
@@ -296,18 +364,60 @@ void finish_request(gp_server* S, Request* r, int launch_rc) {
                 res.users = 0;
                 S->models.push_back(ret);
             }
-        } else if (r->fresh) {
-            free_model(r->fresh);
-            r->fresh = nullptr;
+        } else if (J->fresh) {
+            free_model(J->fresh);
+            J->fresh = nullptr;
         }
     }
+    delete J->sc;  // stream-ordered frees behind the finished work
+    delete J->sc2;
+    S->slot_job[slot] = nullptr;
+    S->mem_used -= J->bytes;
+    S->inflight -= 1;
+    S->inflight_reqs -= (int)J->reqs.size();
     // free retired models whose users have drained
     for (Resident& res : S->models)
         if (res.retired && res.users == 0 && res.model) {
             free_model(res.model);
             res.model = nullptr;
         }
-    S->last_end = r->t_end;
+    S->last_end = now;
+    delete J;
+}
+
+// The next job from the queue head, or nullptr if the budget does not allow
+// one now (lock held).
+Job* take_job(gp_server* S) {
+    Request* head = S->pending.front();
+    const bool idle = S->inflight == 0;
+    if (head->kind == 1) {
+        if (!idle && S->mem_used + head->bytes > S->budget) return nullptr;
+        S->pending.pop_front();
+        Job* J = new Job();
+        J->kind = 1;
+        J->reqs.push_back(head);
+        J->bytes = head->bytes;
+        return J;
+    }
+    Job* J = new Job();
+    int64_t pts = 0;
+    while (!S->pending.empty() && S->pending.front()->kind == 0 && (int)J->reqs.size() < kBatchRequests) {
+        Request* r = S->pending.front();
+        const bool first = J->reqs.empty();
+        if (!first && pts + r->Ns > kBatchPoints) break;
+        if (!(first && idle) && S->mem_used + J->bytes + r->bytes > S->budget) break;
+        S->pending.pop_front();
+        r->used = S->models[r->model].model;
+        S->models[r->model].users += 1;
+        J->reqs.push_back(r);
+        J->bytes += r->bytes;
+        pts += r->Ns;
+    }
+    if (J->reqs.empty()) {
+        delete J;
+        return nullptr;
+    }
+    return J;
 }
 
 void worker_loop(gp_server* S) {
@@ -315,37 +425,35 @@ void worker_loop(gp_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         // completions
-        for (int k = 0; k < S->slots; ++k) {
-            Request* r = S->slot_req[k];
-            if (r && cudaEventQuery(S->done_ev[k]) == cudaSuccess) finish_request(S, r, GP_OK);
-        }
+        for (int k = 0; k < S->slots; ++k)
+            if (S->slot_job[k] && cudaEventQuery(S->done_ev[k]) == cudaSuccess) finish_job(S, k, GP_OK);
         (void)cudaGetLastError();  // cudaEventQuery's "not ready" is not an error here
         // admissions, in arrival order
         while (!S->pending.empty() && S->inflight < S->slots) {
-            Request* r = S->pending.front();
-            if (S->inflight > 0 && S->mem_used + r->bytes > S->budget) break;
+            Job* J = take_job(S);
+            if (J == nullptr) break;
             int slot = 0;
-            while (S->slot_req[slot]) ++slot;
-            S->pending.pop_front();
-            if (r->kind == 0) {
-                r->used = S->models[r->model].model;
-                S->models[r->model].users += 1;
-            }
-            S->slot_req[slot] = r;
-            S->mem_used += r->bytes;
+            while (S->slot_job[slot]) ++slot;
+            S->slot_job[slot] = J;
+            S->mem_used += J->bytes;
             S->inflight += 1;
-            S->peak_inflight = std::max(S->peak_inflight, S->inflight);
-            r->t_start = Clock::now();
-            r->slot = slot;
-            const int rc = launch_request(S, r, slot);
-            if (rc != GP_OK) finish_request(S, r, rc);
+            S->inflight_reqs += (int)J->reqs.size();
+            S->peak_inflight = std::max(S->peak_inflight, S->inflight_reqs);
+            const Clock::time_point now = Clock::now();
+            for (Request* r : J->reqs) r->t_start = now;
+            if (J->kind == 0) {
+                S->batches += 1;
+                S->peak_batch = std::max(S->peak_batch, (int)J->reqs.size());
+            }
+            const int rc = J->kind == 0 ? launch_predicts(S, J, slot) : launch_refit(S, J, slot);
+            if (rc != GP_OK) finish_job(S, slot, rc);
         }
         S->cv_done.notify_all();
         if (S->stop && S->pending.empty() && S->inflight == 0) break;
         if (S->inflight == 0) {
             S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
         } else {
-            // poll the running requests
+            // poll the running jobs
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
@@ -387,7 +495,7 @@ GPFAGP_API int gp_server_create(int slots, int64_t mem_budget_bytes, gp_server**
     S->streams.resize(slots);
     S->done_ev.resize(slots);
     S->pin.resize(slots);
-    S->slot_req.assign(slots, nullptr);
+    S->slot_job.assign(slots, nullptr);
     for (int k = 0; k < slots; ++k) {
         cudaStreamCreateWithFlags(&S->streams[k], cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&S->done_ev[k], cudaEventDisableTiming);
@@ -493,6 +601,8 @@ GPFAGP_API int gp_server_stats(gp_server* S, gp_server_report* out) {
     out->refits_done = S->refits_done;
     out->points = S->points;
     out->peak_inflight = S->peak_inflight;
+    out->peak_batch = S->peak_batch;
+    out->batches = S->batches;
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
         std::sort(v.begin(), v.end());
@@ -518,7 +628,9 @@ GPFAGP_API int gp_server_reset_stats(gp_server* S) {
     S->lat_ms.clear();
     S->points = 0;
     S->refits_done = 0;
-    S->peak_inflight = S->inflight;
+    S->peak_inflight = S->inflight_reqs;
+    S->peak_batch = 0;
+    S->batches = 0;
     S->have_first = false;
     return GP_OK;
 }

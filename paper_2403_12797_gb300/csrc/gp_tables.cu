@@ -51,6 +51,50 @@ __device__ __forceinline__ void shape_consts(const GpShape& s, int j, float& ab,
     sb = s.sbf[j];
     d2 = s.d2f[j];
 }
+// Table column i (one point) of dimension j: out[k * Npad] = phi_k(x_ij),
+// k = 0 .. n-1 (zero for padding rows i >= N and for non-finite input, which
+// also records GP_EINVAL with the row). ca, cb: the recurrence coefficients
+// when staged.
+template <typename T>
+__device__ __forceinline__ void eig_column(const double* __restrict__ X, const double* __restrict__ y, int64_t i,
+                                           int j, int64_t N, int64_t Npad, int p, int n, T abT, T sbT, T d2T,
+                                           const T* ca, const T* cb, bool staged, T* __restrict__ out,
+                                           GpStatus* st) {
+    if (i >= N) {
+        for (int k = 0; k < n; ++k) out[(int64_t)k * Npad] = T(0);
+        return;
+    }
+    const double xd = X[i * p + j];
+    if (!gp_isfinite_bits(xd) || (j == 0 && y != nullptr && !gp_isfinite_bits(y[i]))) {
+        gp_set_status(st, GP_EINVAL, i);
+        for (int k = 0; k < n; ++k) out[(int64_t)k * Npad] = T(0);
+        return;
+    }
+    const T x = to_tab(xd, (T*)nullptr);
+    const T t = abT * x;
+    T q0 = sbT * gp_exp<T>(-d2T * x * x);
+    out[0] = q0;
+    if (n == 1) return;
+    T q1 = gp_sqrt<T>(T(2)) * t * q0;
+    out[Npad] = q1;
+    for (int k = 1; k + 1 < n; ++k) {
+        const T a = staged ? ca[k] : gp_sqrt<T>(T(2) / T(k + 1));
+        const T b = staged ? cb[k] : gp_sqrt<T>(T(k) / T(k + 1));
+        const T q2 = a * t * q1 - b * q0;
+        out[(int64_t)(k + 1) * Npad] = q2;
+        q0 = q1;
+        q1 = q2;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_coefs(int n, T* ca, T* cb) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        ca[k] = gp_sqrt<T>(T(2) / T(k + 1));
+        cb[k] = gp_sqrt<T>(T(k) / T(k + 1));
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double* __restrict__ X,
                                                          const double* __restrict__ y,
@@ -61,10 +105,7 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     T* cb = ca + s.n;
     const bool staged = s.n <= COEF_SMEM_N;
     if (staged) {
-        for (int k = threadIdx.x; k < s.n; k += blockDim.x) {
-            ca[k] = gp_sqrt<T>(T(2) / T(k + 1));
-            cb[k] = gp_sqrt<T>(T(k) / T(k + 1));
-        }
+        stage_coefs<T>(s.n, ca, cb);
         __syncthreads();
     }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,32 +113,41 @@ __global__ void __launch_bounds__(256) eig_tables_kernel(GpShape s, const double
     if (i >= s.Npad) return;
     T abT, sbT, d2T;
     shape_consts(s, j, abT, sbT, d2T);
-    T* out = tab + (int64_t)j * s.n * s.Npad + i;
-    if (i >= s.N) {
-        for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
-        return;
+    eig_column<T>(X, y, i, j, s.N, s.Npad, s.p, s.n, abT, sbT, d2T, ca, cb, staged,
+                  tab + (int64_t)j * s.n * s.Npad + i, st);
+}
+
+// Every request of a predict batch: block b belongs to the request r with
+// boff[r] <= b < boff[r + 1]; within it, dimension j = (b - boff[r]) % p and
+// points 256 ((b - boff[r]) / p) + threadIdx.x. The per-point work is
+// eig_column, as in eig_tables_kernel, so a request's tables are the same
+// bits either way.
+__global__ void __launch_bounds__(256) eig_tables_batch_kernel(const PredReq* __restrict__ reqs,
+                                                               const int* __restrict__ boff, int nreq) {
+    extern __shared__ __align__(16) unsigned char coef_raw[];
+    const int b = blockIdx.x;
+    int lo = 0, hi = nreq - 1;  // the last r with boff[r] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(boff + mid) <= b) lo = mid;
+        else hi = mid - 1;
     }
-    const double xd = X[i * s.p + j];
-    if (!gp_isfinite_bits(xd) || (j == 0 && y != nullptr && !gp_isfinite_bits(y[i]))) {
-        gp_set_status(st, GP_EINVAL, i);
-        for (int k = 0; k < s.n; ++k) out[(int64_t)k * s.Npad] = T(0);
-        return;
+    const PredReq& R = reqs[lo];
+    const int p = R.p, n = R.n;
+    const int local = b - __ldg(boff + lo);
+    const int j = local % p;
+    float* ca = reinterpret_cast<float*>(coef_raw);
+    float* cb = ca + n;
+    const bool staged = n <= COEF_SMEM_N;
+    if (staged) {
+        stage_coefs<float>(n, ca, cb);
+        __syncthreads();
     }
-    const T x = to_tab(xd, (T*)nullptr);
-    const T t = abT * x;
-    T q0 = sbT * gp_exp<T>(-d2T * x * x);
-    out[0] = q0;
-    if (s.n == 1) return;
-    T q1 = gp_sqrt<T>(T(2)) * t * q0;
-    out[s.Npad] = q1;
-    for (int k = 1; k + 1 < s.n; ++k) {
-        const T a = staged ? ca[k] : gp_sqrt<T>(T(2) / T(k + 1));
-        const T b = staged ? cb[k] : gp_sqrt<T>(T(k) / T(k + 1));
-        const T q2 = a * t * q1 - b * q0;
-        out[(int64_t)(k + 1) * s.Npad] = q2;
-        q0 = q1;
-        q1 = q2;
-    }
+    const int64_t i = (int64_t)(local / p) * blockDim.x + threadIdx.x;
+    if (i >= R.Npad) return;
+    const float abT = R.consts[3 * j], sbT = R.consts[3 * j + 1], d2T = R.consts[3 * j + 2];
+    eig_column<float>(R.Xs, nullptr, i, j, R.Ns, R.Npad, p, n, abT, sbT, d2T, ca, cb, staged,
+                      R.tab + (int64_t)j * n * R.Npad + i, R.st);
 }
 
 // The same recurrence, written in the chunk-major layout of the mixed-precision
@@ -206,6 +256,13 @@ void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, f
                            GpStatus* st, cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
     eig_tables_kernel<float><<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tab, st);
+}
+
+void launch_eig_tables_batch(const PredReq* reqs, const int* boff, int nreq, int nblocks, int max_n,
+                             cudaStream_t stream) {
+    if (nblocks <= 0) return;
+    const size_t smem = max_n <= COEF_SMEM_N ? 2 * sizeof(float) * (size_t)max_n : 0;
+    eig_tables_batch_kernel<<<(unsigned)nblocks, 256, smem, stream>>>(reqs, boff, nreq);
 }
 
 size_t syrktc_table_floats(const GpShape& s) {

@@ -99,3 +99,45 @@ def test_predict_batch_bitwise_equals_single():
         finally:
             for m in models:
                 m.free()
+
+
+def test_predict_batch_mixed_dimensions_and_modes():
+    """One gp_predict_batch over models of p = 1..4 in both precision modes
+    (one persistent predict launch per p for the mixed models), requests
+    with and without the variance, sizes from 1 point to several tiles with
+    ragged tails: each result bitwise equal to the request alone, and within
+    the mode's tolerance of the oracle."""
+    shapes = [(1, 30, 5_000), (2, 12, 8_000), (3, 7, 6_000), (4, 4, 6_000), (2, 20, 12_000), (3, 10, 9_000)]
+    probs = [W.random_problem(90 + k, N, 700, p, n, eps=0.9 + 0.1 * k, alpha=1.0, sigma2=0.01)
+             for k, (p, n, N) in enumerate(shapes)]
+    dev = torch.device("cuda", 0)
+    models, precs = [], []
+    for k, pr in enumerate(probs):
+        for prec in ("mixed", "fp64"):
+            models.append((_lib.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2, prec=prec), k, prec))
+    try:
+        rng = np.random.default_rng(9)
+        reqs, meta = [], []
+        for r in range(30):
+            m, k, prec = models[int(rng.integers(len(models)))]
+            ns = int(rng.choice([1, 5, 127, 128, 129, 300, 700]))
+            with_var = bool(rng.integers(4))
+            Xs = torch.from_numpy(probs[k].Xs[:ns].copy()).to(dev)
+            mo = torch.empty(ns, dtype=torch.float64, device=dev)
+            vo = torch.empty(ns, dtype=torch.float64, device=dev) if with_var else None
+            reqs.append((m, Xs, mo, vo))
+            meta.append((k, prec, ns))
+        _lib.predict_batch(reqs)
+        torch.cuda.synchronize()
+        oracles = [O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs]
+        for (m, Xs, mo, vo), (k, prec, ns) in zip(reqs, meta):
+            ms, vs = m.predict(probs[k].Xs[:ns])
+            np.testing.assert_array_equal(mo.cpu().numpy(), ms)
+            if vo is not None:
+                np.testing.assert_array_equal(vo.cpu().numpy(), vs)
+            mref, vref = O.predict(oracles[k], probs[k].Xs[:ns])
+            assert O.relerr(ms, mref) < TOL[prec]["mean"], (k, prec, ns)
+            assert O.relerr(vs, vref) < TOL[prec]["var"], (k, prec, ns)
+    finally:
+        for m, _, _ in models:
+            m.free()

@@ -2,7 +2,8 @@
 
 Predict requests of uneven sizes against several resident models are all
 submitted at once (more than there are slots), so most start while others
-are on the GPU; each result must equal the same request run alone through
+are on the GPU and queued predicts leave in batches (one persistent predict
+launch per basis dimension); each result must equal the same request run alone through
 gp_predict (bitwise: the same kernels with the same launch plans) and match
 the FP64 oracle's posterior within the precision mode's tolerance. A tight
 memory budget must still complete everything. A refit swaps the model in:
@@ -53,9 +54,12 @@ def test_mix_equals_alone(prec, budget):
             st = srv.stats()
         assert st["predicts_done"] == len(reqs)
         assert st["points"] == sum(Xs.shape[0] for _, Xs in reqs)
-        assert 1 <= st["peak_inflight"] <= 6
+        assert 1 <= st["peak_inflight"] <= len(reqs)
+        assert 1 <= st["peak_batch"] <= st["peak_inflight"]
+        assert 1 <= st["batches"] <= len(reqs)
         if budget == 0:
-            assert st["peak_inflight"] >= 2  # requests overlapped on the device
+            # 40 requests queue faster than 6 slots drain: predicts travel in batches
+            assert st["peak_batch"] >= 2 and st["batches"] < len(reqs)
         assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
         oracles = [O.fit(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs]
         for (k, Xs), (mean, var) in zip(reqs, outs):
