@@ -303,25 +303,36 @@ typedef struct gp_fit_args {
 } gp_fit_args;
 
 /* Fit `count` independent problems of uneven N, p and n (and precision
- * `prec` for all) side by side.
+ * `prec` for all) side by side (Sec. 2.2 per problem).
  *   - Inputs, model buffers and the shape-only tables are staged first.
- *   - The launch plan comes from an autotuner: each problem's Gram gets a
- *     share of k waves of the GPU in proportion to its contraction work, with
- *     k in {1, 2, 4} chosen once per distinct batch (multiset of p, n, N
- *     rounded to a power of two) by timing the batch's Gram steps on the
- *     device; the choice is cached for the process.
- *   - Every problem's fit is enqueued on one of up to 8 streams and the whole
- *     batch is captured into ONE CUDA graph and launched once; if CUDA
- *     refuses to capture or instantiate it, the same launches run directly on
- *     the streams (gp_batch_info reports which).
- *   - All statuses are read back once at the end.
+ *   - Mixed precision runs stage-major: every problem's eigenfunction tables
+ *     and column exponents on its stream; then the Grams of ALL problems in
+ *     one tensor-core launch per basis dimension p, whose CTAs find their
+ *     (problem, tile pair, row split) in a device table of the problems --
+ *     each problem's splits sized to its share of k waves of the GPU in
+ *     proportion to its contraction work; then every problem's assembly,
+ *     Cholesky, inverse and solve on its stream. Float64: each problem's own
+ *     steps on its stream.
+ *   - The plan (streams S in {8, 16, 32}, at most `count`, and k in
+ *     {1, 2, 4}) comes from an autotuner that runs the whole batch once per
+ *     candidate the first time a batch of its kind is seen (the multiset of
+ *     p, n, N rounded down to a power of two and precision, on the same GPU
+ *     model and library version), keeps the fastest for the process and, if
+ *     the environment variable GPFAGP_TUNE_CACHE names a file, appends it
+ *     there and reads that file in later processes (gp_batch_plan reports
+ *     the plan and whether it came from the cache).
+ *   - The run is captured into ONE CUDA graph and launched once; if CUDA
+ *     refuses to capture or instantiate it, the same launches run directly
+ *     on the streams (gp_batch_info reports which).
+ *   - All statuses are read back once at the end; a mixed problem whose
+ *     Cholesky met a non-positive pivot is refit with the float64 Gram.
  * out[i] receives problem i's model, or NULL if it failed; the return value
  * is GP_OK when every problem succeeded, else the first failing problem's
  * status with gp_last_error_detail() = its index. X, y are device pointers
  * when dev_ptrs != 0, else host pointers (copied during the call). Each
  * model equals the one gp_fit_ex computes for the same problem up to the
- * order of the Gram's split sums (the autotuned split count), i.e. within
- * the precision mode's tolerance. Blocks until the batch has run. */
+ * order of the Gram's split sums (the plan's split count), i.e. within the
+ * precision mode's tolerance. Blocks until the batch has run. */
 GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec,
                             void* cuda_stream, int dev_ptrs, gp_model** out);
 
@@ -329,6 +340,13 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec,
  * as one captured graph (0 if directly on streams), *tuned_k = the Gram
  * budget factor of its plan. Either pointer may be NULL. */
 GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k);
+
+/* Of the last gp_fit_batch on this thread: its plan (*streams, *k; k = 0
+ * for float64 batches), *from_cache = 1 if the plan came from the tuning
+ * cache (this process's or GPFAGP_TUNE_CACHE's) rather than from timing
+ * the candidates in this call, and *tuned_ms = the plan's timed run.
+ * Any pointer may be NULL. */
+GPFAGP_API int gp_batch_plan(int* streams, int* k, int* from_cache, double* tuned_ms);
 
 /* One predict request of a batched predict. */
 typedef struct gp_predict_args {

@@ -221,6 +221,56 @@ int num_sms(int dev) {
 // A's lower triangle in ex->L. The mixed assembly does both in its kernel
 // (*l_written = true); the float64 path launches the diagonal kernel first and
 // leaves L to the caller.
+// The mixed Gram of one problem on the one-CTA kernel (128 x 128 tile
+// pairs), in three steps so that a batch can contract many problems in one
+// launch: prepare (scratch, split plan, chunk-major tables, column
+// exponents), contract (launch_syrk_tc, or a batched launch), assemble.
+struct MixedGram {
+    GpShape sg;
+    SyrkSplit spl;
+    float* tabc = nullptr;
+    float2* Gpart = nullptr;
+    double* bpart = nullptr;
+    unsigned int *tmax = nullptr, *tmaxb = nullptr;
+    int* colexp = nullptr;
+    signed char* ebx = nullptr;
+};
+
+int mixed_gram_prepare(const GpShape& s, int dev, const double* Xd, const double* yd, GpStatus* st, Scratch& sc,
+                       cudaStream_t stream, int target_ctas, MixedGram& g, bool exponents) {
+    int rc;
+    g.sg = s;
+    const GpShape& sg = g.sg;
+    const int T = sg.Mpad / SYRKTC_TM;
+    const int npairs = T * (T + 1) / 2;
+    choose_splits_tc(T, sg.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &g.spl);
+    if ((rc = sc.get(&g.tabc, syrktc_table_floats(sg)))) return rc;
+    if ((rc = sc.get(&g.Gpart, (size_t)g.spl.smax * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
+    if ((rc = sc.get(&g.bpart, (size_t)g.spl.smax * sg.Mpad))) return rc;
+    if ((rc = sc.get(&g.tmax, (size_t)sg.p * sg.n))) return rc;
+    if ((rc = sc.get(&g.tmaxb, (size_t)sg.p * sg.n * ((sg.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
+    if ((rc = sc.get(&g.colexp, (size_t)sg.Mpad))) return rc;
+    if ((rc = sc.get(&g.ebx, syrktc_ebx_bytes(sg)))) return rc;
+    {
+        GpProf pf("eig_tables", stream);
+        launch_eig_tables_chunked(sg, Xd, yd, g.tabc, g.tmaxb, g.tmax, st, stream);
+        gp_note_launches(2);
+    }
+    if (exponents) {  // (launch_syrk_tc forms them itself)
+        launch_colexp(sg, g.tmaxb, g.tmax, g.colexp, g.ebx, stream);
+        gp_note_launches(1);
+    }
+    return GP_OK;
+}
+
+void mixed_gram_assemble(const MixedGram& g, int M, const double* d, double* A, double* b, cudaStream_t stream,
+                         const AssembleExtra* ex, bool* l_written) {
+    GpProf pf("assemble", stream);
+    launch_assemble_scaled(g.Gpart, g.bpart, g.colexp, g.spl, SYRKTC_TM, g.sg.Mpad, M, d, A, b, stream, ex);
+    gp_note_launches(1);
+    if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
+}
+
 int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const double* yd,
                 const double* d, double* A, double* b, GpStatus* st, cudaStream_t stream,
                 int target_ctas = 0, const AssembleExtra* ex = nullptr, bool* l_written = nullptr) {
@@ -271,27 +321,33 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             pair = syrktc2_supported(sg);
             if (!pair) sg.Mpad = s.Mpad;
         }
-        const int TT = pair ? 256 : SYRKTC_TM;
+        if (!pair) {
+            MixedGram g;
+            if ((rc = mixed_gram_prepare(s, dev, Xd, yd, st, sc, stream, target_ctas, g, false))) return rc;
+            {
+                GpProf pf("syrk_tc", stream);
+                cudaError_t e = launch_syrk_tc(g.sg, g.tabc, g.tmaxb, g.tmax, g.spl, g.Gpart, g.bpart, g.colexp,
+                                               g.ebx, st, stream);
+                if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
+                gp_note_launches(2);
+            }
+            mixed_gram_assemble(g, s.M, d, A, b, stream, ex, l_written);
+            cudaError_t e = cudaGetLastError();
+            return e == cudaSuccess ? GP_OK : cuda_err(e, "Gram step");
+        }
+        // CTA pairs: 256 x 256 tile pairs, float64 partial tiles
+        constexpr int TT = 256;
         float* tabc;
-        float2* Gpart = nullptr;   // one-CTA kernel: float-pair partial tiles
-        double* Gpart2 = nullptr;  // CTA pairs: float64 partial tiles
+        double* Gpart2;
         double* bpart;
         if ((rc = sc.get(&tabc, syrktc_table_floats(sg)))) return rc;
         const int T = sg.Mpad / TT;
         const int npairs = T * (T + 1) / 2;
         SyrkSplit spl;
-        if (pair) {
-            int clusters = syrktc2_max_clusters(sg, dev);
-            if (target_ctas > 0) clusters = std::max(1, std::min(clusters, target_ctas / 2));
-            choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16);
-        } else {
-            choose_splits_tc(T, sg.Npad, target_ctas > 0 ? target_ctas : num_sms(dev), &spl);
-        }
-        if (pair) {
-            if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
-        } else {
-            if ((rc = sc.get(&Gpart, (size_t)spl.smax * npairs * TT * TT))) return rc;
-        }
+        int clusters = syrktc2_max_clusters(sg, dev);
+        if (target_ctas > 0) clusters = std::max(1, std::min(clusters, target_ctas / 2));
+        choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16);
+        if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
         if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
         unsigned int *tmax, *tmaxb;
         int* colexp;
@@ -307,17 +363,13 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = pair ? launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart2, bpart, colexp, ebx, st, stream)
-                                 : launch_syrk_tc(sg, tabc, tmaxb, tmax, spl, Gpart, bpart, colexp, ebx, st, stream);
-            if (e != cudaSuccess) return cuda_err(e, pair ? "syrk_tc2 launch" : "syrk_tc launch");
+            cudaError_t e = launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart2, bpart, colexp, ebx, st, stream);
+            if (e != cudaSuccess) return cuda_err(e, "syrk_tc2 launch");
             gp_note_launches(2);
         }
         {
             GpProf pf("assemble", stream);
-            if (pair)
-                launch_assemble_pair(Gpart2, bpart, colexp, spl, sg.Mpad, s.M, d, A, b, stream, ex);
-            else
-                launch_assemble_scaled(Gpart, bpart, colexp, spl, TT, sg.Mpad, s.M, d, A, b, stream, ex);
+            launch_assemble_pair(Gpart2, bpart, colexp, spl, sg.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
             if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }
@@ -553,7 +605,10 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
     cudaError_t e;
     {
         GpProf pf("cholesky", stream);
-        e = launch_cholesky(h->L, M, st, fwork, stream);
+        // a mixed fit forms the trailing updates in float32, unless its Gram
+        // had to be redone in float64 (then the factorisation is float64 too)
+        const bool f32 = prec != GP_PREC_FP64 && !(h->flags & GP_MODEL_GRAM_FP64);
+        e = launch_cholesky(h->L, M, st, fwork, stream, f32);
     }
     if (e == cudaSuccess) {
         GpProf pf("tri_inverse", stream);
@@ -726,7 +781,9 @@ struct StreamSet {
 };
 
 // Gram CTA budget of problem i for the budget factor k: k waves of the GPU
-// shared out in proportion to each problem's contraction work.
+// shared out in proportion to each problem's contraction work. The mixed
+// batch contracts all its problems in one launch, so the budgets add up to
+// that launch's grid.
 std::vector<int> gram_budgets(const std::vector<gp_model*>& hs, int k, int sms) {
     std::vector<double> w(hs.size());
     double tot = 0.0;
@@ -744,16 +801,63 @@ std::vector<int> gram_budgets(const std::vector<gp_model*>& hs, int k, int sms) 
     return out;
 }
 
-// The autotuner: for each distinct batch (multiset of p, n, N rounded to a
-// power of two, precision) the Gram budget factor k in {1, 2, 4} is chosen
-// once by timing the batch's Gram steps under each value on the device; the
-// choice is cached for the process.
-std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
-thread_local int g_batch_graph = 0;
-thread_local int g_batch_k = 0;
+// ---------------------------------------------------------------- batch plans
+//
+// A batch's launch plan: the streams its per-problem steps are spread over
+// and (mixed precision) the Gram budget factor k. The autotuner times every
+// candidate on the batch itself the first time a batch of that kind is seen
+// (the same multiset of p, n, N rounded down to a power of two, precision,
+// on the same GPU model), keeps the fastest for the process and, when the
+// environment variable GPFAGP_TUNE_CACHE names a file, appends it there and
+// reads it back in later processes (one line per plan: key, streams, k, ms).
 
-std::string batch_signature(const std::vector<gp_model*>& hs) {
+struct BatchPlan {
+    int streams = 8;
+    int k = 2;
+    float ms = 0.f;
+    bool cached = false;  // taken from the cache (this process's or the file's)
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, BatchPlan> g_tune;
+bool g_tune_loaded = false;
+thread_local int g_batch_graph = 0;
+thread_local BatchPlan g_last_plan;
+
+const char* tune_file() {
+    const char* e = getenv("GPFAGP_TUNE_CACHE");
+    return (e != nullptr && e[0] != '\0') ? e : nullptr;
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = tune_file();
+    if (path == nullptr) return;
+    FILE* f = fopen(path, "r");
+    if (f == nullptr) return;
+    char line[512];
+    while (fgets(line, sizeof(line), f) != nullptr) {
+        char key[384];
+        BatchPlan p;
+        if (sscanf(line, "%383s %d %d %f", key, &p.streams, &p.k, &p.ms) == 4 && p.streams >= 1 && p.k >= 0)
+            g_tune[key] = p;  // later lines win
+    }
+    fclose(f);
+}
+
+void tune_store_locked(const std::string& key, const BatchPlan& p) {
+    g_tune[key] = p;
+    const char* path = tune_file();
+    if (path == nullptr) return;
+    FILE* f = fopen(path, "a");
+    if (f == nullptr) return;
+    fprintf(f, "%s %d %d %.4f\n", key.c_str(), p.streams, p.k, p.ms);
+    fclose(f);
+}
+
+// device model + library version + FNV-1a hash of the sorted problem kinds
+std::string batch_key(const std::vector<gp_model*>& hs, int dev) {
     std::vector<std::string> parts;
     for (gp_model* h : hs) {
         int lg = 0;
@@ -763,63 +867,263 @@ std::string batch_signature(const std::vector<gp_model*>& hs) {
         parts.push_back(buf);
     }
     std::sort(parts.begin(), parts.end());
-    std::string sig;
-    for (auto& x : parts) sig += x + ";";
-    return sig;
+    uint64_t hsh = 1469598103934665603ull;
+    for (auto& x : parts)
+        for (char ch : x + ";") {
+            hsh ^= (unsigned char)ch;
+            hsh *= 1099511628211ull;
+        }
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        name = prop.name;
+        for (char& ch : name)
+            if (ch == ' ' || ch == '\t') ch = '_';
+        name += "_" + std::to_string(prop.multiProcessorCount);
+    }
+    char buf[128];
+    snprintf(buf, sizeof(buf), "batch/%s/%s/n%zu/%016llx", name.c_str(), gp_version(), hs.size(),
+             (unsigned long long)hsh);
+    std::string key = buf;
+    for (char& ch : key)
+        if (ch == ' ') ch = '_';
+    return key;
 }
 
-int tune_batch(const std::vector<gp_model*>& hs, const std::vector<const double*>& Xd,
-               const std::vector<const double*>& yd, GpStatus* sts, StreamSet& ss, cudaStream_t origin,
-               int sms) {
-    const std::string sig = batch_signature(hs);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune.find(sig);
-        if (it != g_tune.end()) return it->second;
+// Everything one enqueue of the batch needs.
+struct BatchCtx {
+    std::vector<gp_model*>* hs;
+    std::vector<const double*>* Xd;
+    std::vector<const double*>* yd;
+    std::vector<double*>* loglam;
+    GpStatus* sts;
+    int dev, sms;
+    cudaStream_t origin;
+    StreamSet* ss;                     // the largest stream set; a plan uses its first `streams`
+    std::vector<PinnedBlock> pinned;   // host images read by copies not yet run
+};
+
+void fork_n(StreamSet& ss, cudaStream_t origin, int n) {
+    cudaEventRecord(ss.ev.back(), origin);
+    for (int i = 0; i < n; ++i) cudaStreamWaitEvent(ss.st[i], ss.ev.back(), 0);
+}
+void join_n(StreamSet& ss, cudaStream_t origin, int n) {
+    for (int i = 0; i < n; ++i) {
+        cudaEventRecord(ss.ev[i], ss.st[i]);
+        cudaStreamWaitEvent(origin, ss.ev[i], 0);
     }
-    int best = 1;
-    float best_ms = 1e30f;
+}
+
+void maybe_force_notpd(GpStatus* st, cudaStream_t stream) {
+    int k = g_force_escalate.load();
+    while (k > 0 && !g_force_escalate.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k > 0) force_notpd_kernel<<<1, 1, 0, stream>>>(st);
+}
+
+// Enqueue every problem's fit under a plan, behind and ahead of `origin`.
+// Float64: each problem's own steps on stream i mod S. Mixed (stage-major):
+// every problem's tables and column exponents on its stream, then the Grams
+// of all problems in one launch per p on `origin` (a device table of the
+// problems; launch_syrk_tc_batch), then every problem's assembly and
+// factorisation on its stream.
+int enqueue_batch(BatchCtx& c, const BatchPlan& plan) {
+    std::vector<gp_model*>& hs = *c.hs;
+    const int count = (int)hs.size();
+    const int S = std::min(plan.streams, (int)c.ss->st.size());
+    StreamSet& ss = *c.ss;
+    fork_n(ss, c.origin, S);
+    int rc = GP_OK;
+    if (hs[0]->prec == GP_PREC_FP64) {
+        std::vector<Scratch*> scs;
+        for (int i = 0; i < count && rc == GP_OK; ++i) {
+            cudaStream_t s = ss.st[i % S];
+            Scratch* sc = new Scratch(s);
+            scs.push_back(sc);
+            rc = fit_compute(hs[i], (*c.Xd)[i], (*c.yd)[i], (*c.loglam)[i], &c.sts[i], 0, *sc, s);
+        }
+        for (Scratch* sc : scs) delete sc;  // scratch frees are stream-ordered
+        join_n(ss, c.origin, S);
+        return rc;
+    }
+    const std::vector<int> bud = gram_budgets(hs, plan.k, c.sms);
+    std::vector<Scratch*> scs(count, nullptr);
+    std::vector<MixedGram> gs(count);
+    std::vector<double*> A(count), work(count);
+    std::vector<unsigned char*> fw(count);
+    for (int i = 0; i < count && rc == GP_OK; ++i) {
+        cudaStream_t s = ss.st[i % S];
+        scs[i] = new Scratch(s);
+        const GpShape& sh = hs[i]->shape;
+        if ((rc = scs[i]->get(&A[i], (size_t)sh.M * sh.M))) break;
+        if ((rc = scs[i]->get(&work[i], solve_refine_work_elems(sh.M)))) break;
+        if ((rc = scs[i]->get(&fw[i], factor_work_bytes(sh.M, true)))) break;
+        rc = mixed_gram_prepare(sh, c.dev, (*c.Xd)[i], (*c.yd)[i], &c.sts[i], *scs[i], s, bud[i], gs[i], true);
+    }
+    join_n(ss, c.origin, S);
+    if (rc == GP_OK) {
+        // the problem table, grouped by p (one launch each)
+        std::map<int, std::vector<int>> byp;
+        for (int i = 0; i < count; ++i) byp[hs[i]->shape.p].push_back(i);
+        std::vector<SyrkBatchProb> probs;
+        struct Launch {
+            int p, first, n, maxrows;
+            int64_t items;
+        };
+        std::vector<Launch> launches;
+        for (auto& kv : byp) {
+            Launch L{kv.first, (int)probs.size(), 0, 0, 0};
+            for (int i : kv.second) {
+                SyrkBatchProb b{};
+                b.s = gs[i].sg;
+                b.tabc = gs[i].tabc;
+                b.ebx = gs[i].ebx;
+                b.colexp = gs[i].colexp;
+                b.sp = gs[i].spl;
+                b.T = gs[i].sg.Mpad / SYRKTC_TM;
+                b.Gpart = gs[i].Gpart;
+                b.bpart = gs[i].bpart;
+                b.st = &c.sts[i];
+                b.item0 = L.items;
+                L.items += syrktc_items(gs[i].sg, gs[i].spl);
+                L.maxrows = std::max(L.maxrows, gp_max_window_rows(gs[i].sg, SYRKTC_TM));
+                probs.push_back(b);
+                ++L.n;
+            }
+            launches.push_back(L);
+        }
+        const size_t bytes = sizeof(SyrkBatchProb) * probs.size();
+        PinnedBlock pb = pinned_get(bytes);
+        Scratch tsc(c.origin);
+        SyrkBatchProb* dprobs = nullptr;
+        if (pb.p == nullptr) rc = set_err(GP_ENOMEM, (int64_t)bytes);
+        if (rc == GP_OK) rc = tsc.get(&dprobs, probs.size());
+        if (rc == GP_OK) {
+            c.pinned.push_back(pb);
+            memcpy(pb.p, probs.data(), bytes);
+            cudaMemcpyAsync(dprobs, pb.p, bytes, cudaMemcpyHostToDevice, c.origin);
+            for (const Launch& L : launches) {
+                GpProf pf("syrk_tc", c.origin);
+                cudaError_t e = launch_syrk_tc_batch(dprobs + L.first, L.n, L.items, L.p, L.maxrows, c.origin);
+                if (e != cudaSuccess) {
+                    rc = cuda_err(e, "batched Gram launch");
+                    break;
+                }
+                gp_note_launches(1);
+            }
+        } else if (pb.p != nullptr) {
+            pinned_put(pb);
+        }
+    }
+    fork_n(ss, c.origin, S);
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t s = ss.st[i % S];
+        if (rc == GP_OK) {
+            gp_model* h = hs[i];
+            const AssembleExtra ex{&h->shape, (*c.loglam)[i], h->sigma2, h->d, h->L};
+            bool lw = false;
+            mixed_gram_assemble(gs[i], h->shape.M, nullptr, A[i], h->b, s, &ex, &lw);
+            maybe_force_notpd(&c.sts[i], s);
+            rc = fit_factor(h, A[i], work[i], fw[i], &c.sts[i], s, lw);
+        }
+        delete scs[i];  // stream-ordered frees behind this problem's steps
+    }
+    join_n(ss, c.origin, S);
+    return rc;
+}
+
+// One run of the batch under `plan`: captured into one CUDA graph and
+// launched (if capture or instantiation is refused, enqueued directly), then
+// synchronised. *ms = the device time of the run, *graph = whether a graph ran.
+int run_batch(BatchCtx& c, const BatchPlan& plan, float* ms, int* graph) {
+    cudaMemsetAsync(c.sts, 0, sizeof(GpStatus) * c.hs->size(), c.origin);
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    const int cand[3] = {1, 2, 4};
-    for (int k : cand) {
-        const std::vector<int> bud = gram_budgets(hs, k, sms);
-        cudaEventRecord(t0, origin);
-        ss.fork(origin);
-        int rc = GP_OK;
-        {
-            std::vector<Scratch*> scs;
-            for (size_t i = 0; i < hs.size() && rc == GP_OK; ++i) {
-                cudaStream_t s = ss.st[i % ss.st.size()];
-                Scratch* sc = new Scratch(s);
-                scs.push_back(sc);
-                const GpShape& sh = hs[i]->shape;
-                double *A, *b;
-                if ((rc = sc->get(&A, (size_t)sh.M * sh.M))) break;
-                if ((rc = sc->get(&b, (size_t)sh.M))) break;
-                rc = gram_device(sh, hs[i]->prec, hs[i]->device, Xd[i], yd[i], nullptr, A, b, &sts[i], s,
-                                 bud[i]);
-            }
-            for (Scratch* sc : scs) delete sc;
+    const int prof = gp_prof_suspend();
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ran = false;
+    int rc = GP_OK;
+    if (cudaStreamBeginCapture(c.origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const int erc = enqueue_batch(c, plan);
+        const cudaError_t ce = cudaStreamEndCapture(c.origin, &g);
+        if (erc == GP_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+            cudaEventRecord(t0, c.origin);
+            if (cudaGraphLaunch(exec, c.origin) == cudaSuccess) ran = true;
+            cudaEventRecord(t1, c.origin);
         }
-        ss.join(origin);
-        cudaEventRecord(t1, origin);
-        cudaEventSynchronize(t1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (rc != GP_OK) break;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = k;
+        if (!ran) {
+            (void)cudaGetLastError();
+            set_err(GP_OK);
         }
+    } else {
+        (void)cudaGetLastError();
     }
+    if (!ran) {
+        cudaEventRecord(t0, c.origin);
+        rc = enqueue_batch(c, plan);
+        cudaEventRecord(t1, c.origin);
+    }
+    cudaError_t e = cudaStreamSynchronize(c.origin);
+    gp_prof_resume(prof);
+    for (PinnedBlock& b : c.pinned) pinned_put(b);
+    c.pinned.clear();
+    float t = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, t0, t1);
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    cudaMemsetAsync(sts, 0, sizeof(GpStatus) * hs.size(), origin);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    if (ms) *ms = t;
+    if (graph) *graph = ran ? 1 : 0;
+    if (rc != GP_OK) return rc;
+    return e == cudaSuccess ? GP_OK : cuda_err(e, "batch synchronise");
+}
+
+// The plan for this batch: from the cache, or timed over the candidates
+// (streams 8, 16, 32 -- at most the problem count -- and, for mixed
+// precision, k = 1, 2, 4); each candidate runs the whole batch once.
+int plan_batch(BatchCtx& c, BatchPlan* out) {
+    const std::string key = batch_key(*c.hs, c.dev);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *out = it->second;
+            out->cached = true;
+            return GP_OK;
+        }
+    }
+    const int count = (int)c.hs->size();
+    const bool mixed = (*c.hs)[0]->prec != GP_PREC_FP64;
+    BatchPlan best;
+    best.ms = 1e30f;
+    bool any = false;
+    for (int S : {8, 16, 32}) {
+        if (S > count && S != 8) break;
+        for (int k : {1, 2, 4}) {
+            if (!mixed && k != 1) break;
+            BatchPlan cand;
+            cand.streams = std::min(S, count);
+            cand.k = mixed ? k : 0;
+            float ms = 0.f;
+            const int rc = run_batch(c, cand, &ms, nullptr);
+            if (rc != GP_OK) return rc;
+            if (ms < best.ms) {
+                best = cand;
+                best.ms = ms;
+                any = true;
+            }
+        }
+    }
+    if (!any) best = BatchPlan();
+    best.cached = false;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[sig] = best;
-    return best;
+    tune_store_locked(key, best);
+    *out = best;
+    return GP_OK;
 }
 
 }  // namespace gpi
@@ -866,7 +1170,7 @@ int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha,
 
 extern "C" {
 
-GPFAGP_API const char* gp_version(void) { return "gpfagp 0.1 sm_103a"; }
+GPFAGP_API const char* gp_version(void) { return "gpfagp 0.2 sm_103a"; }
 
 GPFAGP_API int gp_last_error(void) { return g_err; }
 GPFAGP_API int64_t gp_last_error_detail(void) { return g_detail; }
@@ -1485,7 +1789,7 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
                             int dev_ptrs, gp_model** out) {
     set_err(GP_OK);
     g_batch_graph = 0;
-    g_batch_k = 0;
+    g_last_plan = BatchPlan();
     int rc, dev;
     if (count < 0 || (count > 0 && (!args || !out))) return set_err(GP_EINVAL, 0);
     for (int i = 0; i < count; ++i) out[i] = nullptr;
@@ -1554,61 +1858,14 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
     cudaError_t e = cudaStreamSynchronize(origin);  // staged host inputs have been read
     if (e != cudaSuccess) return fail_all(cuda_err(e, "batch input staging"), -1);
 
-    StreamSet ss(count < 8 ? count : 8);
-    const int k = tune_batch(hs, Xd, yd, sts, ss, origin, sms);
-    g_batch_k = k;
-    const std::vector<int> bud = gram_budgets(hs, k, sms);
-
-    // enqueue every problem's fit, problem i on stream i mod S
-    auto enqueue_all = [&]() -> int {
-        ss.fork(origin);
-        int first = GP_OK;
-        std::vector<Scratch*> scs;
-        for (int i = 0; i < count && first == GP_OK; ++i) {
-            cudaStream_t s = ss.st[i % ss.st.size()];
-            Scratch* sc = new Scratch(s);
-            scs.push_back(sc);
-            first = fit_compute(hs[i], Xd[i], yd[i], loglam[i], &sts[i], bud[i], *sc, s);
-        }
-        for (Scratch* sc : scs) delete sc;  // scratch frees are stream-ordered
-        ss.join(origin);
-        return first;
-    };
-
-    // One graph for the whole batch; if capturing or instantiating it is
-    // refused, the same launches run directly on the streams.
-    const int prof = gp_prof_suspend();
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    bool ran = false;
-    if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-        const int erc = enqueue_all();
-        const cudaError_t ce = cudaStreamEndCapture(origin, &graph);
-        if (erc == GP_OK && ce == cudaSuccess && graph &&
-            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess &&
-            cudaGraphLaunch(exec, origin) == cudaSuccess) {
-            ran = true;
-            g_batch_graph = 1;
-        }
-        if (!ran) {
-            (void)cudaGetLastError();
-            set_err(GP_OK);
-        }
-    } else {
-        (void)cudaGetLastError();
-    }
-    if (!ran) {
-        rc = enqueue_all();
-        if (rc != GP_OK) {
-            gp_prof_resume(prof);
-            return fail_all(rc, -1);
-        }
-    }
-    e = cudaStreamSynchronize(origin);
-    gp_prof_resume(prof);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail_all(cuda_err(e, "batch synchronise"), -1);
+    StreamSet ss(std::min(count, 32));
+    BatchCtx ctx{&hs, &Xd, &yd, &loglam, sts, dev, sms, origin, &ss, {}};
+    BatchPlan plan;
+    if ((rc = plan_batch(ctx, &plan))) return fail_all(rc, -1);
+    int graph = 0;
+    if ((rc = run_batch(ctx, plan, nullptr, &graph))) return fail_all(rc, -1);
+    g_batch_graph = graph;
+    g_last_plan = plan;
 
     std::vector<GpStatus> hst(count);
     e = cudaMemcpy(hst.data(), sts, sizeof(GpStatus) * count, cudaMemcpyDeviceToHost);
@@ -1644,7 +1901,15 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec, void* 
 
 GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k) {
     if (used_graph) *used_graph = g_batch_graph;
-    if (tuned_k) *tuned_k = g_batch_k;
+    if (tuned_k) *tuned_k = g_last_plan.k;
+    return GP_OK;
+}
+
+GPFAGP_API int gp_batch_plan(int* streams, int* k, int* from_cache, double* tuned_ms) {
+    if (streams) *streams = g_last_plan.streams;
+    if (k) *k = g_last_plan.k;
+    if (from_cache) *from_cache = g_last_plan.cached ? 1 : 0;
+    if (tuned_ms) *tuned_ms = g_last_plan.ms;
     return GP_OK;
 }
 

@@ -47,6 +47,16 @@ __device__ __forceinline__ float gp_d2f_rn(double x) {
     q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
     return __uint_as_float(sgn | (uint32_t)q);
 }
+// float -> float64 without the float64 pipe (exact for normal floats and
+// zero; float subnormals, below 1.2e-38, become signed zero)
+__device__ __forceinline__ double gp_f2d_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (e == 0xFFu) return (double)f;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
 // x is finite (neither infinite nor NaN), from its exponent bits: the
 // float64 comparison would take the float64 pipe
 __device__ __forceinline__ bool gp_isfinite_bits(double x) {

@@ -10,7 +10,8 @@
 // separated by grid barriers whose waits are bounded (GP_ETIMEOUT after
 // GP_WAIT_NS; nothing can hang):
 //
-//   Cholesky (float64, right-looking, 32-column panels, look-ahead), per step k:
+//   Cholesky (float64, right-looking, 32-column panels, look-ahead; a mixed
+//   fit forms the trailing-update products in float32), per step k:
 //     B  one warp per row below the factored diagonal block solves
 //        x L_kk^T = a (lane j owns x_j);
 //     C  16 helper CTAs update the next diagonal block and count themselves
@@ -269,16 +270,37 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     return true;
 }
 
+// Element type of the trailing-update products: float64, or float32 for a
+// mixed-precision fit (F32). The float32 form rounds the panel to float,
+// forms each panel's <= 32-term inner products in float (about 3e-7 of the
+// products' magnitude, the order of the mixed Gram's own error) and
+// subtracts them from the float64 trailing matrix, so rounding does not
+// compound from panel to panel; the diagonal blocks and panel solves stay
+// float64. On GB300 a float FMA issues 64 times as fast as a float64 one,
+// and these updates are nearly all of the M^3 / 3 flops.
+template <bool F32> struct UpdType { using T = double; };
+template <> struct UpdType<true> { using T = float; };
+
 // L[r0.., c0..] -= L[r0.., kb..kb+w) L[c0.., kb..kb+w)^T on one 16 x 16 lower tile.
+template <bool F32>
 __device__ __forceinline__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
-                                 double (*ti)[CB + 1], double (*tj)[CB + 1]) {
+                                                 typename UpdType<F32>::T (*ti)[CB + 1],
+                                                 typename UpdType<F32>::T (*tj)[CB + 1]) {
+    using T = typename UpdType<F32>::T;
     const int tid = threadIdx.x;
-    double vi[UT * CB / NT], vj[UT * CB / NT];
+    T vi[UT * CB / NT], vj[UT * CB / NT];
 #pragma unroll
     for (int q = 0; q < UT * CB / NT; ++q) {  // all loads in flight before the stores
         const int e = tid + q * NT, r = e / CB, l = e % CB;
-        vi[q] = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
-        vj[q] = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+        const double a = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+        const double b = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
+        if constexpr (F32) {
+            vi[q] = gp_d2f_rn(a);
+            vj[q] = gp_d2f_rn(b);
+        } else {
+            vi[q] = a;
+            vj[q] = b;
+        }
     }
 #pragma unroll
     for (int q = 0; q < UT * CB / NT; ++q) {
@@ -288,10 +310,15 @@ __device__ __forceinline__ void chol_update_tile(double* __restrict__ L, int M, 
     }
     __syncthreads();
     const int ty = tid / UT, tx = tid % UT;
-    double s = 0.0;
+    T s = 0;
     for (int l = 0; l < w; ++l) s = fma(ti[ty][l], tj[tx][l], s);
     const int i = r0 + ty, j = c0 + tx;
-    if (i < M && j <= i) L[(int64_t)i * M + j] -= s;
+    if (i < M && j <= i) {
+        if constexpr (F32)
+            L[(int64_t)i * M + j] -= gp_f2d_exact(s);
+        else
+            L[(int64_t)i * M + j] -= s;
+    }
     __syncthreads();
 }
 
@@ -339,11 +366,12 @@ __device__ __forceinline__ void chol_next_diag(double* __restrict__ L, int M, in
 // wait_ns bounds every wait (GP_WAIT_NS normally). skip_cta >= 0 is a test of
 // failure detection only: that CTA leaves before its first barrier arrival,
 // so the others' bounded waits run out and report GP_ETIMEOUT.
+template <bool F32>
 __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
                                                        CholWork* cw, uint64_t wait_ns, int skip_cta) {
     __shared__ double a[CB][CB + 1];
-    __shared__ double ti[UT][CB + 1];
-    __shared__ double tj[UT][CB + 1];
+    __shared__ typename UpdType<F32>::T ti[UT][CB + 1];
+    __shared__ typename UpdType<F32>::T tj[UT][CB + 1];
     __shared__ double rdiag[CB];
     __shared__ PotrfSmem sm;
     __shared__ int s_fail;
@@ -446,7 +474,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
             for (int t = ndiag + first; t < ntiles; t += stride) {
                 int I, J;
                 tri_pair(t, &I, &J);
-                chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
+                chol_update_tile<F32>(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
             }
         if (!grid_sync(gb, st, wait_ns)) return;
         if (status_code(st) != 0) return;
@@ -1039,7 +1067,7 @@ int chol_grid(int M, int dev) {
     if (M <= CB) return 1;
     const int T = (M - CB + UT - 1) / UT;
     const int want = (T * (T + 1) / 2 + 1) / 2;
-    const int g = coop_grid((const void*)chol_coop_kernel, dev);
+    const int g = coop_grid((const void*)chol_coop_kernel<false>, dev);
     return want < 2 ? 2 : (want > g ? g : want);
 }
 
@@ -1054,7 +1082,7 @@ void factor_debug_barrier_timeout(double limit_s, int skip_cta) {
     g_chol_skip_cta.store(skip_cta >= 0 ? skip_cta : -1);
 }
 
-cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream) {
+cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream, bool f32_update) {
     int dev = 0;
     cudaGetDevice(&dev);
     CholWork* cw = (CholWork*)work;
@@ -1065,7 +1093,8 @@ cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStre
     int skip = g_chol_skip_cta.exchange(-1);
     void* args[] = {&L, &M, &st, &cw, &wait_ns, &skip};
     gp_note_launches(1);
-    return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, grid, block, args, 0, stream);
+    const void* k = f32_update ? (const void*)chol_coop_kernel<true> : (const void*)chol_coop_kernel<false>;
+    return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }
 
 namespace {

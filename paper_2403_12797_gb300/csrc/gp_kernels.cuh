@@ -58,6 +58,32 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
                            const unsigned int* tmax, const SyrkSplit& sp, float2* Gpart, double* bpart,
                            int* colexp, signed char* ebx, GpStatus* st, cudaStream_t stream);
 
+// One problem of a batched Gram launch: the arguments launch_syrk_tc takes
+// (its column exponents already formed by launch_colexp), and the launch's
+// first item of this problem (problems in ascending item0).
+struct SyrkBatchProb {
+    GpShape s;
+    const float* tabc;
+    const signed char* ebx;
+    const int* colexp;
+    SyrkSplit sp;
+    int T;
+    float2* Gpart;
+    double* bpart;
+    GpStatus* st;
+    int64_t item0;
+};
+constexpr size_t SYRK_BATCH_SHAPE_BYTES = (sizeof(GpShape) + 1023) / 1024 * 1024;
+// CTAs (work items) of launch_syrk_tc for this shape and split plan
+int64_t syrktc_items(const GpShape& s, const SyrkSplit& sp);
+// The Grams of several problems with the same p in one launch: items in
+// [probs[k].item0, probs[k].item0 + syrktc_items) are problem k's; maxrows
+// bounds every problem's tile window (gp_max_window_rows(s, 128)).
+cudaError_t launch_syrk_tc_batch(const SyrkBatchProb* probs, int nprob, int64_t items, int p, int maxrows,
+                                 cudaStream_t stream);
+void launch_colexp(const GpShape& s, const unsigned int* tmaxb, const unsigned int* tmax, int* colexp,
+                   signed char* ebx, cudaStream_t stream);
+
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);
 // b = sum_s bpart[s]. d may be NULL (plain Gram).
@@ -124,7 +150,11 @@ size_t factor_work_bytes(int M, bool fp32_inverse);
 // status GP_ENOTPD, detail = column. It zeroes the workspace header, which
 // holds the grid barriers of launch_tri_inverse and launch_solve_refine too:
 // those two run after it, on the same workspace.
-cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream);
+// f32_update: the trailing-update products in float32, subtracted from the
+// float64 trailing matrix (mixed-precision fits); the diagonal blocks and
+// panel solves are float64 either way.
+cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream,
+                            bool f32_update = false);
 // Test hook of gp_debug_barrier_timeout: the Cholesky's bounded waits give up
 // after limit_s seconds (<= 0: GP_WAIT_NS), and the next launch's CTA
 // skip_cta (< 0: none) leaves before its first grid-barrier arrival.

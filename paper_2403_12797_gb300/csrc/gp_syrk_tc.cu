@@ -208,16 +208,48 @@ __device__ __forceinline__ void phi8(const float* win, const int* woff, const un
 }
 
 // P = p for p <= 4 (offsets in registers, products unrolled), 0 otherwise;
-// H = table chunks per pipeline stage.
-template <int P, int H>
+// H = table chunks per pipeline stage. BATCH: the launch covers several
+// problems (SyrkBatchProb table, all with this p): a CTA finds its problem
+// by its item number, copies the problem's shape to the head of its dynamic
+// shared memory (the layout follows it) and runs the problem's item as a
+// launch of that problem alone would.
+template <int P, int H, bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    syrk_tc_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
-                   const int* __restrict__ colexp, SyrkSplit sp, int T, int maxrows, int nst, int nwr,
-                   float2* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
+    syrk_tc_kernel(const __grid_constant__ GpShape s_arg, const float* __restrict__ tabc_arg,
+                   const signed char* __restrict__ ebx_arg, const int* __restrict__ colexp_arg,
+                   const __grid_constant__ SyrkSplit sp_arg, int T_arg, int maxrows, int nst, int nwr,
+                   float2* __restrict__ Gpart_arg, double* __restrict__ bpart_arg, GpStatus* st_arg,
+                   const SyrkBatchProb* __restrict__ probs, int nprob) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
     __shared__ int s_nrng;
     char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    int item0 = blockIdx.x;
+    const SyrkBatchProb* pb = nullptr;
+    if constexpr (BATCH) {
+        int lo = 0, hi = nprob - 1;  // the last problem whose first item is <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].item0 <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        pb = probs + lo;
+        item0 = (int)(blockIdx.x - pb->item0);
+        const int* src = reinterpret_cast<const int*>(&pb->s);
+        int* dst = reinterpret_cast<int*>(base);
+        for (int i = threadIdx.x; i < (int)(sizeof(GpShape) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        base += SYRK_BATCH_SHAPE_BYTES;
+    }
+    const GpShape& s = BATCH ? *reinterpret_cast<const GpShape*>(base - SYRK_BATCH_SHAPE_BYTES) : s_arg;
+    const float* __restrict__ tabc = BATCH ? pb->tabc : tabc_arg;
+    const signed char* __restrict__ ebx = BATCH ? pb->ebx : ebx_arg;
+    const int* __restrict__ colexp = BATCH ? pb->colexp : colexp_arg;
+    const SyrkSplit& sp = BATCH ? pb->sp : sp_arg;
+    const int T = BATCH ? pb->T : T_arg;
+    float2* __restrict__ Gpart = BATCH ? pb->Gpart : Gpart_arg;
+    double* __restrict__ bpart = BATCH ? pb->bpart : bpart_arg;
+    GpStatus* st = BATCH ? pb->st : st_arg;
     SmemTC sm;
     smem_tc_layout(maxrows, s.p, nst, nwr, H, base, &sm);
     using GM = StageGeom<H>;
@@ -228,7 +260,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // the pair index runs fastest
     int I, J, split, cls;
     {
-        int item = blockIdx.x;
+        int item = item0;
         const int n0 = T, n1 = T - 1, n2 = (T - 1) * (T - 2) / 2;
         if (item < n0 * sp.n[0]) {
             cls = 0;
@@ -605,8 +637,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // memory fits one CTA next to the kernel's static shared memory (tile
 // windows and flags, under 2 KB). Returns the operand stages (0 if nothing
 // fits).
-int syrk_tc_stages(const GpShape& s, int maxrows, int* H, int* nwr, size_t* smem) {
-    constexpr size_t kDynamicBudget = (227 - 2) * 1024;
+int syrk_tc_stages(const GpShape& s, int maxrows, int* H, int* nwr, size_t* smem, size_t reserve = 0) {
+    const size_t kDynamicBudget = (227 - 2) * 1024 - reserve;
     for (int h = 2; h >= 1; --h)
         for (int nst = STAGES; nst >= 2; --nst)
             for (int w = WRMAX; w >= 2; --w) {
@@ -658,23 +690,66 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = gp_allow_max_smem((const void*)kern);
         if (e != cudaSuccess) return e;
-        kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, Gpart, bpart, st);
+        kern<<<grid, NTHREADS, smem, stream>>>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, Gpart, bpart, st,
+                                               nullptr, 0);
         return cudaGetLastError();
     };
     if (H == 2) {
         switch (s.p) {
-            case 1: return go(syrk_tc_kernel<1, 2>);
-            case 2: return go(syrk_tc_kernel<2, 2>);
-            case 3: return go(syrk_tc_kernel<3, 2>);
-            case 4: return go(syrk_tc_kernel<4, 2>);
-            default: return go(syrk_tc_kernel<0, 2>);
+            case 1: return go(syrk_tc_kernel<1, 2, false>);
+            case 2: return go(syrk_tc_kernel<2, 2, false>);
+            case 3: return go(syrk_tc_kernel<3, 2, false>);
+            case 4: return go(syrk_tc_kernel<4, 2, false>);
+            default: return go(syrk_tc_kernel<0, 2, false>);
         }
     }
     switch (s.p) {
-        case 1: return go(syrk_tc_kernel<1, 1>);
-        case 2: return go(syrk_tc_kernel<2, 1>);
-        case 3: return go(syrk_tc_kernel<3, 1>);
-        case 4: return go(syrk_tc_kernel<4, 1>);
-        default: return go(syrk_tc_kernel<0, 1>);
+        case 1: return go(syrk_tc_kernel<1, 1, false>);
+        case 2: return go(syrk_tc_kernel<2, 1, false>);
+        case 3: return go(syrk_tc_kernel<3, 1, false>);
+        case 4: return go(syrk_tc_kernel<4, 1, false>);
+        default: return go(syrk_tc_kernel<0, 1, false>);
+    }
+}
+
+int64_t syrktc_items(const GpShape& s, const SyrkSplit& sp) {
+    const int T = s.Mpad / TM;
+    return (int64_t)T * sp.n[0] + (int64_t)(T - 1) * sp.n[1] + (int64_t)(T - 1) * (T - 2) / 2 * sp.n[2];
+}
+
+cudaError_t launch_syrk_tc_batch(const SyrkBatchProb* probs, int nprob, int64_t items, int p, int maxrows,
+                                 cudaStream_t stream) {
+    if (items <= 0) return cudaSuccess;
+    GpShape sh{};
+    sh.p = p;
+    size_t smem = 0;
+    int nwr = 0, H = 1;
+    const int nst = syrk_tc_stages(sh, maxrows, &H, &nwr, &smem, SYRK_BATCH_SHAPE_BYTES);
+    if (nst == 0) return cudaErrorInvalidConfiguration;
+    smem += SYRK_BATCH_SHAPE_BYTES;
+    const GpShape none{};
+    const SyrkSplit nosp{};
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = gp_allow_max_smem((const void*)kern);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)items, NTHREADS, smem, stream>>>(none, nullptr, nullptr, nullptr, nosp, 0, maxrows, nst, nwr,
+                                                          nullptr, nullptr, nullptr, probs, nprob);
+        return cudaGetLastError();
+    };
+    if (H == 2) {
+        switch (p) {
+            case 1: return go(syrk_tc_kernel<1, 2, true>);
+            case 2: return go(syrk_tc_kernel<2, 2, true>);
+            case 3: return go(syrk_tc_kernel<3, 2, true>);
+            case 4: return go(syrk_tc_kernel<4, 2, true>);
+            default: return go(syrk_tc_kernel<0, 2, true>);
+        }
+    }
+    switch (p) {
+        case 1: return go(syrk_tc_kernel<1, 1, true>);
+        case 2: return go(syrk_tc_kernel<2, 1, true>);
+        case 3: return go(syrk_tc_kernel<3, 1, true>);
+        case 4: return go(syrk_tc_kernel<4, 1, true>);
+        default: return go(syrk_tc_kernel<0, 1, true>);
     }
 }

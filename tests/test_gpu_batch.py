@@ -1,4 +1,5 @@
-"""Batched fit (one captured graph, autotuned Gram budgets) and batched predict.
+"""Batched fit (one captured graph; the mixed Grams of all problems in one
+launch per p; an autotuned plan with an on-disk cache) and batched predict.
 
 The batch is a small instance of the uneven-shape batched workload (p in
 1..4, M <= 256, N log-uniform up to 20,000) plus one member at M = 1024. Every batched model is checked
@@ -32,7 +33,9 @@ def test_fit_batch_matches_oracle(prec):
     probs = _batch(with_m1024=True)
     models = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs], prec=prec)
     used_graph, k = _lib.batch_info()
-    assert k in (1, 2, 4)
+    plan = _lib.batch_plan()
+    assert k == plan["k"] and k in ((1, 2, 4) if prec == "mixed" else (0,))
+    assert plan["streams"] in (8, 16, 17) and plan["tuned_ms"] > 0
     assert used_graph in (0, 1)
     try:
         for pr, m in zip(probs, models):
@@ -141,3 +144,38 @@ def test_predict_batch_mixed_dimensions_and_modes():
     finally:
         for m, _, _ in models:
             m.free()
+
+
+_CACHE_PROBE = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_2403_12797_gb300 import _lib, workloads as W
+probs = W.workload4(count=12, Ns=1, N_hi=20_000, M_max=256, seed_offset=21)
+ms = _lib.fit_batch([(pr.X, pr.y, pr.n, pr.eps, pr.alpha, pr.sigma2) for pr in probs])
+print(json.dumps(_lib.batch_plan()))
+for m in ms:
+    m.free()
+"""
+
+
+def test_batch_plan_cache_persists_across_processes(tmp_path):
+    """The first process times the candidates and appends the winner to
+    GPFAGP_TUNE_CACHE; a second process with the same batch reads it back
+    and runs the same plan without tuning."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.tsv"
+    env = dict(os.environ, GPFAGP_TUNE_CACHE=str(cache))
+    code = _CACHE_PROBE.format(root=root)
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert not runs[0]["from_cache"] and runs[1]["from_cache"]
+    assert (runs[1]["streams"], runs[1]["k"]) == (runs[0]["streams"], runs[0]["k"])
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("batch/")
