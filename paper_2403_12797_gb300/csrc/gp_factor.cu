@@ -270,37 +270,16 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     return true;
 }
 
-// Element type of the trailing-update products: float64, or float32 for a
-// mixed-precision fit (F32). The float32 form rounds the panel to float,
-// forms each panel's <= 32-term inner products in float (about 3e-7 of the
-// products' magnitude, the order of the mixed Gram's own error) and
-// subtracts them from the float64 trailing matrix, so rounding does not
-// compound from panel to panel; the diagonal blocks and panel solves stay
-// float64. On GB300 a float FMA issues 64 times as fast as a float64 one,
-// and these updates are nearly all of the M^3 / 3 flops.
-template <bool F32> struct UpdType { using T = double; };
-template <> struct UpdType<true> { using T = float; };
-
 // L[r0.., c0..] -= L[r0.., kb..kb+w) L[c0.., kb..kb+w)^T on one 16 x 16 lower tile.
-template <bool F32>
 __device__ __forceinline__ void chol_update_tile(double* __restrict__ L, int M, int kb, int w, int r0, int c0,
-                                                 typename UpdType<F32>::T (*ti)[CB + 1],
-                                                 typename UpdType<F32>::T (*tj)[CB + 1]) {
-    using T = typename UpdType<F32>::T;
+                                 double (*ti)[CB + 1], double (*tj)[CB + 1]) {
     const int tid = threadIdx.x;
-    T vi[UT * CB / NT], vj[UT * CB / NT];
+    double vi[UT * CB / NT], vj[UT * CB / NT];
 #pragma unroll
     for (int q = 0; q < UT * CB / NT; ++q) {  // all loads in flight before the stores
         const int e = tid + q * NT, r = e / CB, l = e % CB;
-        const double a = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
-        const double b = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
-        if constexpr (F32) {
-            vi[q] = gp_d2f_rn(a);
-            vj[q] = gp_d2f_rn(b);
-        } else {
-            vi[q] = a;
-            vj[q] = b;
-        }
+        vi[q] = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+        vj[q] = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < UT * CB / NT; ++q) {
@@ -310,15 +289,72 @@ __device__ __forceinline__ void chol_update_tile(double* __restrict__ L, int M, 
     }
     __syncthreads();
     const int ty = tid / UT, tx = tid % UT;
-    T s = 0;
+    double s = 0.0;
     for (int l = 0; l < w; ++l) s = fma(ti[ty][l], tj[tx][l], s);
     const int i = r0 + ty, j = c0 + tx;
-    if (i < M && j <= i) {
-        if constexpr (F32)
-            L[(int64_t)i * M + j] -= gp_f2d_exact(s);
-        else
-            L[(int64_t)i * M + j] -= s;
+    if (i < M && j <= i) L[(int64_t)i * M + j] -= s;
+    __syncthreads();
+}
+
+// The mixed-precision fit's trailing update (F32): products in float32 on
+// 64 x 64 tiles. The panel is rounded to float, each panel's <= 32-term inner
+// products are formed in float (about 3e-7 of the products' magnitude, the
+// order of the mixed Gram's own error) and subtracted from the float64
+// trailing matrix, so rounding does not compound from panel to panel; the
+// diagonal blocks and panel solves stay float64. On GB300 a float FMA issues
+// 64 times as fast as a float64 one, and these updates are nearly all of the
+// M^3 / 3 flops. Each thread owns a 4 x 4 block (rows ty + 16a, columns
+// tx + 16b); the tile's old values are loaded with the panel, so a tile
+// makes one round trip to L2. Entries above the diagonal and inside the next
+// diagonal block (rows and columns base .. base + wn - 1, the helpers' share)
+// are left alone.
+constexpr int UF = 64;
+__device__ __forceinline__ void chol_update_tile_f32(double* __restrict__ L, int M, int kb, int w, int wn,
+                                                     int r0, int c0, float (*ti)[CB + 1], float (*tj)[CB + 1]) {
+    const int tid = threadIdx.x;
+    const int ty = tid / 16, tx = tid % 16;
+    const int base = kb + w;
+    double vi[UF * CB / NT], vj[UF * CB / NT], old[4][4];
+#pragma unroll
+    for (int q = 0; q < UF * CB / NT; ++q) {
+        const int e = tid + q * NT, r = e / CB, l = e % CB;
+        vi[q] = (l < w && r0 + r < M) ? L[(int64_t)(r0 + r) * M + kb + l] : 0.0;
+        vj[q] = (l < w && c0 + r < M) ? L[(int64_t)(c0 + r) * M + kb + l] : 0.0;
     }
+    bool own[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
+            own[a][b] = i < M && j <= i && !(i - base < wn && j - base < wn);
+            old[a][b] = own[a][b] ? L[(int64_t)i * M + j] : 0.0;
+        }
+#pragma unroll
+    for (int q = 0; q < UF * CB / NT; ++q) {
+        const int e = tid + q * NT;
+        ti[e / CB][e % CB] = gp_d2f_rn(vi[q]);
+        tj[e / CB][e % CB] = gp_d2f_rn(vj[q]);
+    }
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int l = 0; l < w; ++l) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = ti[ty + 16 * a][l];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = tj[tx + 16 * b][l];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (own[a][b])
+                L[(int64_t)(r0 + ty + 16 * a) * M + c0 + tx + 16 * b] = old[a][b] - gp_f2d_exact(acc[a][b]);
     __syncthreads();
 }
 
@@ -370,8 +406,9 @@ template <bool F32>
 __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
                                                        CholWork* cw, uint64_t wait_ns, int skip_cta) {
     __shared__ double a[CB][CB + 1];
-    __shared__ typename UpdType<F32>::T ti[UT][CB + 1];
-    __shared__ typename UpdType<F32>::T tj[UT][CB + 1];
+    // the update tiles' panel rows: 16-row float64 tiles, or 64-row float32 (F32)
+    constexpr int TBYTES = F32 ? 2 * UF * (CB + 1) * 4 : 2 * UT * (CB + 1) * 8;
+    __shared__ __align__(16) unsigned char tbuf[TBYTES];
     __shared__ double rdiag[CB];
     __shared__ PotrfSmem sm;
     __shared__ int s_fail;
@@ -470,12 +507,26 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
         }
         const int first = (G > 1) ? (int)blockIdx.x - 1 : 0;
         const int stride = (G > 1) ? G - 1 : 1;
-        if (G == 1 || blockIdx.x > 0)
-            for (int t = ndiag + first; t < ntiles; t += stride) {
-                int I, J;
-                tri_pair(t, &I, &J);
-                chol_update_tile<F32>(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
+        if (G == 1 || blockIdx.x > 0) {
+            if constexpr (F32) {
+                float(*fi)[CB + 1] = reinterpret_cast<float(*)[CB + 1]>(tbuf);
+                float(*fj)[CB + 1] = fi + UF;
+                const int nfr = (rest + UF - 1) / UF;
+                for (int t = first; t < nfr * (nfr + 1) / 2; t += stride) {
+                    int I, J;
+                    tri_pair(t, &I, &J);
+                    chol_update_tile_f32(L, M, kb, w, wn, kb + w + I * UF, kb + w + J * UF, fi, fj);
+                }
+            } else {
+                double(*ti)[CB + 1] = reinterpret_cast<double(*)[CB + 1]>(tbuf);
+                double(*tj)[CB + 1] = ti + UT;
+                for (int t = ndiag + first; t < ntiles; t += stride) {
+                    int I, J;
+                    tri_pair(t, &I, &J);
+                    chol_update_tile(L, M, kb, w, kb + w + I * UT, kb + w + J * UT, ti, tj);
+                }
             }
+        }
         if (!grid_sync(gb, st, wait_ns)) return;
         if (status_code(st) != 0) return;
     }
@@ -1063,10 +1114,14 @@ size_t factor_work_bytes(int M, bool fp32_inverse) {
 // per CTA in the first step (one CTA when there is none), at most one per SM,
 // so that small problems -- e.g. the many problems of a batch running side by
 // side -- do not claim the whole GPU.
-int chol_grid(int M, int dev) {
+int chol_grid(int M, int dev, bool f32_update) {
     if (M <= CB) return 1;
-    const int T = (M - CB + UT - 1) / UT;
-    const int want = (T * (T + 1) / 2 + 1) / 2;
+    // about two 16-row (one 64-row, float32) trailing-update tiles per CTA in
+    // the first step; with float32 tiles also at least one panel row per warp
+    // (the float64 panel solves then set the step time at small M)
+    const int T = f32_update ? (M - CB + UF - 1) / UF : (M - CB + UT - 1) / UT;
+    const int want = f32_update ? std::max(T * (T + 1) / 2, (M - CB + NT / 32 - 1) / (NT / 32))
+                                : (T * (T + 1) / 2 + 1) / 2;
     const int g = coop_grid((const void*)chol_coop_kernel<false>, dev);
     return want < 2 ? 2 : (want > g ? g : want);
 }
@@ -1087,7 +1142,7 @@ cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStre
     cudaGetDevice(&dev);
     CholWork* cw = (CholWork*)work;
     cudaMemsetAsync(cw, 0, CHOL_RSD_OFFSET, stream);
-    dim3 grid((unsigned)chol_grid(M, dev)), block(NT);
+    dim3 grid((unsigned)chol_grid(M, dev, f32_update)), block(NT);
     const unsigned long long lim = g_chol_wait_ns.load();
     uint64_t wait_ns = lim ? (uint64_t)lim : (uint64_t)GP_WAIT_NS;
     int skip = g_chol_skip_cta.exchange(-1);
