@@ -313,17 +313,18 @@ typedef struct gp_fit_args {
  *     proportion to its contraction work; then every problem's assembly,
  *     Cholesky, inverse and solve on its stream. Float64: each problem's own
  *     steps on its stream.
- *   - The plan (streams S in {8, 16, 32}, at most `count`, and k in
- *     {1, 2, 4}) comes from an autotuner that runs the whole batch once per
- *     candidate the first time a batch of its kind is seen (the multiset of
+ *   - The plan (streams S in {8, 16, 32}, at most `count`; k in {1, 2, 4};
+ *     and whether the run is captured into ONE CUDA graph and launched once
+ *     or enqueued directly on the streams) comes from an autotuner that runs
+ *     the whole batch once per candidate, timed on the host clock from call
+ *     to return, the first time a batch of its kind is seen (the multiset of
  *     p, n, N rounded down to a power of two and precision, on the same GPU
- *     model and library version), keeps the fastest for the process and, if
- *     the environment variable GPFAGP_TUNE_CACHE names a file, appends it
+ *     model and library version). It keeps the fastest for the process and,
+ *     if the environment variable GPFAGP_TUNE_CACHE names a file, appends it
  *     there and reads that file in later processes (gp_batch_plan reports
  *     the plan and whether it came from the cache).
- *   - The run is captured into ONE CUDA graph and launched once; if CUDA
- *     refuses to capture or instantiate it, the same launches run directly
- *     on the streams (gp_batch_info reports which).
+ *   - If CUDA refuses to capture or instantiate the graph, the same launches
+ *     run directly on the streams (gp_batch_info reports which ran).
  *   - All statuses are read back once at the end; a mixed problem whose
  *     Cholesky met a non-positive pivot is refit with the float64 Gram.
  * out[i] receives problem i's model, or NULL if it failed; the return value
@@ -344,7 +345,8 @@ GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k);
 /* Of the last gp_fit_batch on this thread: its plan (*streams, *k; k = 0
  * for float64 batches), *from_cache = 1 if the plan came from the tuning
  * cache (this process's or GPFAGP_TUNE_CACHE's) rather than from timing
- * the candidates in this call, and *tuned_ms = the plan's timed run.
+ * the candidates in this call, and *tuned_ms = the plan's timed run (host
+ * time from call to return).
  * Any pointer may be NULL. */
 GPFAGP_API int gp_batch_plan(int* streams, int* k, int* from_cache, double* tuned_ms);
 
@@ -442,7 +444,7 @@ GPFAGP_API void gp_debug_fail_alloc_after(int k);
 GPFAGP_API void gp_debug_force_escalation(int k);
 
 /* Test hook: which mixed-precision Gram kernel the fits run. 0 (default):
- * automatic -- for M > 512 (p <= 4) a cluster of two CTAs per 256 x 256 tile
+ * automatic -- for M > 384 (p <= 4) a cluster of two CTAs per 256 x 256 tile
  * pair of G (tcgen05 cta_group::2), else one CTA per 128 x 128 tile pair;
  * 1: always one CTA per 128 x 128 tile pair; 2: CTA pairs wherever they
  * apply (p <= 4). Both compute the same arithmetic (the mixed mode above);

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -27,7 +28,7 @@ namespace gpi {
 thread_local int g_err = GP_OK;
 thread_local int64_t g_detail = 0;
 std::atomic<int> g_fail_after{0};
-// which mixed-precision Gram kernel runs: 0 automatic (CTA pairs for M > 512),
+// which mixed-precision Gram kernel runs: 0 automatic (CTA pairs for M > 384),
 // 1 always one CTA per 128 x 128 tile pair, 2 CTA pairs wherever they apply
 std::atomic<int> g_gram_kernel{0};
 std::mutex g_pool_mu;
@@ -311,12 +312,14 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
             gp_note_launches(1);
         }
     } else {
-        // the CTA-pair kernel (256 x 256 tile pairs) for M > 512 where it
-        // applies, else one CTA per 128 x 128 tile pair
+        // the CTA-pair kernel (256 x 256 tile pairs) for M > 384 where it
+        // applies (from there both kernels pad M to the same multiple of 256,
+        // or the pairs' padding is outweighed: measured at M = 400, 0.28 ms
+        // against 0.31 ms), else one CTA per 128 x 128 tile pair
         GpShape sg = s;
         bool pair = false;
         const int kind = g_gram_kernel.load();
-        if (kind != 1 && s.M > (kind == 2 ? 0 : 512)) {
+        if (kind != 1 && s.M > (kind == 2 ? 0 : 384)) {
             sg.Mpad = (int)gp_round_up(s.M, 256);
             pair = syrktc2_supported(sg);
             if (!pair) sg.Mpad = s.Mpad;
@@ -803,18 +806,23 @@ std::vector<int> gram_budgets(const std::vector<gp_model*>& hs, int k, int sms) 
 
 // ---------------------------------------------------------------- batch plans
 //
-// A batch's launch plan: the streams its per-problem steps are spread over
-// and (mixed precision) the Gram budget factor k. The autotuner times every
-// candidate on the batch itself the first time a batch of that kind is seen
-// (the same multiset of p, n, N rounded down to a power of two, precision,
-// on the same GPU model), keeps the fastest for the process and, when the
-// environment variable GPFAGP_TUNE_CACHE names a file, appends it there and
-// reads it back in later processes (one line per plan: key, streams, k, ms).
+// A batch's launch plan: the streams its per-problem steps are spread over,
+// (mixed precision) the Gram budget factor k, and whether the run is
+// captured into one CUDA graph or enqueued directly (capturing and
+// instantiating thousands of launches costs host time that can exceed what
+// the graph saves). The autotuner times candidates on the batch itself, on
+// the host clock from call to return, the first time a batch of that kind is
+// seen (the same multiset of p, n, N rounded down to a power of two,
+// precision, on the same GPU model), keeps the fastest for the process and,
+// when the environment variable GPFAGP_TUNE_CACHE names a file, appends it
+// there and reads it back in later processes (one line per plan: key,
+// streams, k, ms, graph).
 
 struct BatchPlan {
     int streams = 8;
     int k = 2;
     float ms = 0.f;
+    int graph = 1;
     bool cached = false;  // taken from the cache (this process's or the file's)
 };
 
@@ -840,8 +848,11 @@ void tune_load_locked() {
     while (fgets(line, sizeof(line), f) != nullptr) {
         char key[384];
         BatchPlan p;
-        if (sscanf(line, "%383s %d %d %f", key, &p.streams, &p.k, &p.ms) == 4 && p.streams >= 1 && p.k >= 0)
+        const int nf = sscanf(line, "%383s %d %d %f %d", key, &p.streams, &p.k, &p.ms, &p.graph);
+        if (nf >= 4 && p.streams >= 1 && p.k >= 0) {
+            if (nf == 4) p.graph = 1;
             g_tune[key] = p;  // later lines win
+        }
     }
     fclose(f);
 }
@@ -852,7 +863,7 @@ void tune_store_locked(const std::string& key, const BatchPlan& p) {
     if (path == nullptr) return;
     FILE* f = fopen(path, "a");
     if (f == nullptr) return;
-    fprintf(f, "%s %d %d %.4f\n", key.c_str(), p.streams, p.k, p.ms);
+    fprintf(f, "%s %d %d %.4f %d\n", key.c_str(), p.streams, p.k, p.ms, p.graph);
     fclose(f);
 }
 
@@ -1033,26 +1044,23 @@ int enqueue_batch(BatchCtx& c, const BatchPlan& plan) {
 }
 
 // One run of the batch under `plan`: captured into one CUDA graph and
-// launched (if capture or instantiation is refused, enqueued directly), then
-// synchronised. *ms = the device time of the run, *graph = whether a graph ran.
+// launched if plan.graph (if capture or instantiation is refused, enqueued
+// directly), else enqueued directly; then synchronised. *ms = the host time
+// from the call to the synchronisation, *graph = whether a graph ran.
 int run_batch(BatchCtx& c, const BatchPlan& plan, float* ms, int* graph) {
+    const auto h0 = std::chrono::steady_clock::now();
     cudaMemsetAsync(c.sts, 0, sizeof(GpStatus) * c.hs->size(), c.origin);
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
     const int prof = gp_prof_suspend();
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool ran = false;
     int rc = GP_OK;
-    if (cudaStreamBeginCapture(c.origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    if (plan.graph && cudaStreamBeginCapture(c.origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
         const int erc = enqueue_batch(c, plan);
         const cudaError_t ce = cudaStreamEndCapture(c.origin, &g);
-        if (erc == GP_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
-            cudaEventRecord(t0, c.origin);
-            if (cudaGraphLaunch(exec, c.origin) == cudaSuccess) ran = true;
-            cudaEventRecord(t1, c.origin);
-        }
+        if (erc == GP_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess &&
+            cudaGraphLaunch(exec, c.origin) == cudaSuccess)
+            ran = true;
         if (!ran) {
             (void)cudaGetLastError();
             set_err(GP_OK);
@@ -1060,19 +1068,12 @@ int run_batch(BatchCtx& c, const BatchPlan& plan, float* ms, int* graph) {
     } else {
         (void)cudaGetLastError();
     }
-    if (!ran) {
-        cudaEventRecord(t0, c.origin);
-        rc = enqueue_batch(c, plan);
-        cudaEventRecord(t1, c.origin);
-    }
+    if (!ran) rc = enqueue_batch(c, plan);
     cudaError_t e = cudaStreamSynchronize(c.origin);
     gp_prof_resume(prof);
     for (PinnedBlock& b : c.pinned) pinned_put(b);
     c.pinned.clear();
-    float t = 0.f;
-    if (e == cudaSuccess) cudaEventElapsedTime(&t, t0, t1);
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    const float t = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - h0).count();
     if (exec) cudaGraphExecDestroy(exec);
     if (g) cudaGraphDestroy(g);
     if (ms) *ms = t;
@@ -1083,7 +1084,8 @@ int run_batch(BatchCtx& c, const BatchPlan& plan, float* ms, int* graph) {
 
 // The plan for this batch: from the cache, or timed over the candidates
 // (streams 8, 16, 32 -- at most the problem count -- and, for mixed
-// precision, k = 1, 2, 4); each candidate runs the whole batch once.
+// precision, k = 1, 2, 4, each run enqueued directly; then the best of these
+// once more as a captured graph); each candidate runs the whole batch once.
 int plan_batch(BatchCtx& c, BatchPlan* out) {
     const std::string key = batch_key(*c.hs, c.dev);
     {
@@ -1108,6 +1110,7 @@ int plan_batch(BatchCtx& c, BatchPlan* out) {
             BatchPlan cand;
             cand.streams = std::min(S, count);
             cand.k = mixed ? k : 0;
+            cand.graph = 0;
             float ms = 0.f;
             const int rc = run_batch(c, cand, &ms, nullptr);
             if (rc != GP_OK) return rc;
@@ -1119,6 +1122,17 @@ int plan_batch(BatchCtx& c, BatchPlan* out) {
         }
     }
     if (!any) best = BatchPlan();
+    if (any) {
+        BatchPlan g = best;
+        g.graph = 1;
+        float ms = 0.f;
+        const int rc = run_batch(c, g, &ms, nullptr);
+        if (rc != GP_OK) return rc;
+        if (ms < best.ms) {
+            best = g;
+            best.ms = ms;
+        }
+    }
     best.cached = false;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_store_locked(key, best);
