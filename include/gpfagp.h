@@ -314,17 +314,19 @@ typedef struct gp_fit_args {
  *     Cholesky, inverse and solve on its stream. Float64: each problem's own
  *     steps on its stream.
  *   - The plan (streams S in {8, 16, 32}, at most `count`; k in {1, 2, 4};
- *     and whether the run is captured into ONE CUDA graph and launched once
- *     or enqueued directly on the streams) comes from an autotuner that runs
- *     the whole batch once per candidate, timed on the host clock from call
- *     to return, the first time a batch of its kind is seen (the multiset of
- *     p, n, N rounded down to a power of two and precision, on the same GPU
- *     model and library version). It keeps the fastest for the process and,
- *     if the environment variable GPFAGP_TUNE_CACHE names a file, appends it
- *     there and reads that file in later processes (gp_batch_plan reports
- *     the plan and whether it came from the cache).
- *   - If CUDA refuses to capture or instantiate the graph, the same launches
- *     run directly on the streams (gp_batch_info reports which ran).
+ *     and whether each problem's Cholesky, inverse and solve run on at most
+ *     max(4, SMs / S) CTAs, so that more problems' factorisations overlap)
+ *     comes from an autotuner that runs the whole batch once per
+ *     candidate after one untimed warm-up run, timed on the host clock from
+ *     call to return, the first time a batch of its kind is seen (the
+ *     multiset of p, n, N rounded down to a power of two and precision, on
+ *     the same GPU model and library version). It keeps the fastest for the
+ *     process and, if the environment variable GPFAGP_TUNE_CACHE names a
+ *     file, appends it there and reads that file in later processes
+ *     (gp_batch_plan reports the plan and whether it came from the cache).
+ *   - The run is captured into ONE CUDA graph and launched once; if CUDA
+ *     refuses to capture or instantiate it, the same launches run directly
+ *     on the streams (gp_batch_info reports which ran).
  *   - All statuses are read back once at the end; a mixed problem whose
  *     Cholesky met a non-positive pivot is refit with the float64 Gram.
  * out[i] receives problem i's model, or NULL if it failed; the return value
@@ -343,12 +345,12 @@ GPFAGP_API int gp_fit_batch(int count, const gp_fit_args* args, int prec,
 GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k);
 
 /* Of the last gp_fit_batch on this thread: its plan (*streams, *k; k = 0
- * for float64 batches), *from_cache = 1 if the plan came from the tuning
- * cache (this process's or GPFAGP_TUNE_CACHE's) rather than from timing
- * the candidates in this call, and *tuned_ms = the plan's timed run (host
- * time from call to return).
- * Any pointer may be NULL. */
-GPFAGP_API int gp_batch_plan(int* streams, int* k, int* from_cache, double* tuned_ms);
+ * for float64 batches; *factor_ctas = the CTA cap of each problem's
+ * Cholesky, inverse and solve, 0 if uncapped), *from_cache = 1 if the plan
+ * came from the tuning cache (this process's or GPFAGP_TUNE_CACHE's) rather
+ * than from timing the candidates in this call, and *tuned_ms = the plan's
+ * timed run (host time from call to return). Any pointer may be NULL. */
+GPFAGP_API int gp_batch_plan(int* streams, int* k, int* factor_ctas, int* from_cache, double* tuned_ms);
 
 /* One predict request of a batched predict. */
 typedef struct gp_predict_args {

@@ -89,7 +89,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_fit_batch": (i, [i, C.POINTER(FitArgs), i, vp, i, C.POINTER(vp)]),
         "gp_predict_batch": (i, [i, C.POINTER(PredictArgs), vp]),
         "gp_batch_info": (i, [C.POINTER(i), C.POINTER(i)]),
-        "gp_batch_plan": (i, [C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)]),
+        "gp_batch_plan": (i, [C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)]),
         "gp_fit_gram_ex": (i, [vp, vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
         "gp_gram_packed_ex": (i, [vp, vp, i64, i, i, d, d, i, vp, vp, i]),
         "gp_fit_gram_packed_ex": (i, [vp, i64, i, i, d, d, d, i, vp, i, C.POINTER(vp)]),
@@ -455,10 +455,11 @@ def fit_batch(problems: Sequence[Tuple], prec: str = "mixed", stream=None) -> Li
 
 
 def batch_plan() -> dict:
-    """The plan of this thread's last fit_batch: streams, k, from_cache, tuned_ms."""
-    st, k, fc, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
-    lib().gp_batch_plan(C.byref(st), C.byref(k), C.byref(fc), C.byref(ms))
-    return {"streams": st.value, "k": k.value, "from_cache": bool(fc.value), "tuned_ms": ms.value}
+    """The plan of this thread's last fit_batch: streams, k, factor_ctas, from_cache, tuned_ms."""
+    st, k, fcta, fc, ms = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    lib().gp_batch_plan(C.byref(st), C.byref(k), C.byref(fcta), C.byref(fc), C.byref(ms))
+    return {"streams": st.value, "k": k.value, "factor_ctas": fcta.value, "from_cache": bool(fc.value),
+            "tuned_ms": ms.value}
 
 
 def batch_info() -> Tuple[int, int]:

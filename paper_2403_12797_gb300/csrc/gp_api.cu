@@ -515,7 +515,7 @@ int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t strea
 }
 
 int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
-               cudaStream_t stream, bool l_ready = false);
+               cudaStream_t stream, bool l_ready = false, int max_ctas = 0);
 
 __global__ void add_diag_kernel(double* __restrict__ A, const double* __restrict__ d, int M) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,7 +568,7 @@ bool mixed_escalates(const gp_model* h, int code) {
 __global__ void force_notpd_kernel(GpStatus* st) { gp_set_status(st, GP_ENOTPD, 0); }
 
 int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
-                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec) {
+                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec, int factor_ctas) {
     const GpShape& s = h->shape;
     const int M = s.M;
     const int prec = h->prec;
@@ -593,14 +593,14 @@ int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* l
         }
         if (k > 0) force_notpd_kernel<<<1, 1, 0, stream>>>(st);
     }
-    return fit_factor(h, A, work, fwork, st, stream, l_written);
+    return fit_factor(h, A, work, fwork, st, stream, l_written, factor_ctas);
 }
 
 // The factorisation steps of a fit from the assembled A (device, M x M, kept
 // for the refinement residual): L, W = L^{-1}, c, and the predict operand.
 // l_ready: h->L already holds A's lower triangle.
 int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork, GpStatus* st,
-               cudaStream_t stream, bool l_ready) {
+               cudaStream_t stream, bool l_ready, int max_ctas) {
     const int M = h->shape.M;
     const int prec = h->prec;
     const bool fp32_inverse = (prec != GP_PREC_FP64);
@@ -611,17 +611,17 @@ int fit_factor(gp_model* h, const double* A, double* work, unsigned char* fwork,
         // a mixed fit forms the trailing updates in float32, unless its Gram
         // had to be redone in float64 (then the factorisation is float64 too)
         const bool f32 = prec != GP_PREC_FP64 && !(h->flags & GP_MODEL_GRAM_FP64);
-        e = launch_cholesky(h->L, M, st, fwork, stream, f32);
+        e = launch_cholesky(h->L, M, st, fwork, stream, f32, max_ctas);
     }
     if (e == cudaSuccess) {
         GpProf pf("tri_inverse", stream);
-        e = launch_tri_inverse(h->L, h->W, M, fp32_inverse, st, fwork, stream);
+        e = launch_tri_inverse(h->L, h->W, M, fp32_inverse, st, fwork, stream, max_ctas);
     }
     if (e == cudaSuccess) {
         GpProf pf("solve_refine", stream);
         // a mixed fit's solve also packs the predict operand (W and c)
         e = launch_solve_refine(A, h->W, fwork, fp32_inverse, h->b, h->c, work, M, fp32_inverse ? 3 : 2, st,
-                                stream, prec != GP_PREC_FP64 ? h->Wpack : nullptr);
+                                stream, prec != GP_PREC_FP64 ? h->Wpack : nullptr, max_ctas);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "factorisation or solve launch");
 }
@@ -806,25 +806,32 @@ std::vector<int> gram_budgets(const std::vector<gp_model*>& hs, int k, int sms) 
 
 // ---------------------------------------------------------------- batch plans
 //
-// A batch's launch plan: the streams its per-problem steps are spread over,
-// (mixed precision) the Gram budget factor k, and whether the run is
-// captured into one CUDA graph or enqueued directly (capturing and
-// instantiating thousands of launches costs host time that can exceed what
-// the graph saves). The autotuner times candidates on the batch itself, on
-// the host clock from call to return, the first time a batch of that kind is
-// seen (the same multiset of p, n, N rounded down to a power of two,
-// precision, on the same GPU model), keeps the fastest for the process and,
-// when the environment variable GPFAGP_TUNE_CACHE names a file, appends it
-// there and reads it back in later processes (one line per plan: key,
-// streams, k, ms, graph).
+// A batch's launch plan: the streams its per-problem steps are spread over
+// and (mixed precision) the Gram budget factor k; the run is one captured
+// CUDA graph. (Enqueued directly instead, a batch is as fast only on a
+// process's first call: later calls wait on the scratch pool's
+// stream-ordered frees across the streams, 1.2-1.9 times slower measured.)
+// The autotuner times candidates on the batch itself, on the host clock from
+// call to return, after one untimed run that warms the scratch pool, the
+// first time a batch of that kind is seen (the same multiset of p, n, N
+// rounded down to a power of two, precision, on the same GPU model), keeps
+// the fastest for the process and, when the environment variable
+// GPFAGP_TUNE_CACHE names a file, appends it there and reads it back in
+// later processes (one line per plan: key, streams, k, ms, graph).
 
 struct BatchPlan {
     int streams = 8;
     int k = 2;
     float ms = 0.f;
     int graph = 1;
+    int fcap = 0;         // factorisation grids capped at max(4, SMs / streams) CTAs (1) or not (0)
     bool cached = false;  // taken from the cache (this process's or the file's)
 };
+int plan_factor_ctas(const BatchPlan& p, int sms) {
+    if (!p.fcap) return 0;
+    const int c = sms / (p.streams > 0 ? p.streams : 1);
+    return c < 4 ? 4 : c;
+}
 
 std::mutex g_tune_mu;
 std::map<std::string, BatchPlan> g_tune;
@@ -848,9 +855,10 @@ void tune_load_locked() {
     while (fgets(line, sizeof(line), f) != nullptr) {
         char key[384];
         BatchPlan p;
-        const int nf = sscanf(line, "%383s %d %d %f %d", key, &p.streams, &p.k, &p.ms, &p.graph);
+        const int nf = sscanf(line, "%383s %d %d %f %d %d", key, &p.streams, &p.k, &p.ms, &p.graph, &p.fcap);
         if (nf >= 4 && p.streams >= 1 && p.k >= 0) {
-            if (nf == 4) p.graph = 1;
+            if (nf < 5) p.graph = 1;
+            if (nf < 6) p.fcap = 0;
             g_tune[key] = p;  // later lines win
         }
     }
@@ -863,7 +871,7 @@ void tune_store_locked(const std::string& key, const BatchPlan& p) {
     if (path == nullptr) return;
     FILE* f = fopen(path, "a");
     if (f == nullptr) return;
-    fprintf(f, "%s %d %d %.4f %d\n", key.c_str(), p.streams, p.k, p.ms, p.graph);
+    fprintf(f, "%s %d %d %.4f %d %d\n", key.c_str(), p.streams, p.k, p.ms, p.graph, p.fcap);
     fclose(f);
 }
 
@@ -951,7 +959,8 @@ int enqueue_batch(BatchCtx& c, const BatchPlan& plan) {
             cudaStream_t s = ss.st[i % S];
             Scratch* sc = new Scratch(s);
             scs.push_back(sc);
-            rc = fit_compute(hs[i], (*c.Xd)[i], (*c.yd)[i], (*c.loglam)[i], &c.sts[i], 0, *sc, s);
+            rc = fit_compute(hs[i], (*c.Xd)[i], (*c.yd)[i], (*c.loglam)[i], &c.sts[i], 0, *sc, s, -1,
+                             plan_factor_ctas(plan, c.sms));
         }
         for (Scratch* sc : scs) delete sc;  // scratch frees are stream-ordered
         join_n(ss, c.origin, S);
@@ -1035,7 +1044,7 @@ int enqueue_batch(BatchCtx& c, const BatchPlan& plan) {
             bool lw = false;
             mixed_gram_assemble(gs[i], h->shape.M, nullptr, A[i], h->b, s, &ex, &lw);
             maybe_force_notpd(&c.sts[i], s);
-            rc = fit_factor(h, A[i], work[i], fw[i], &c.sts[i], s, lw);
+            rc = fit_factor(h, A[i], work[i], fw[i], &c.sts[i], s, lw, plan_factor_ctas(plan, c.sms));
         }
         delete scs[i];  // stream-ordered frees behind this problem's steps
     }
@@ -1084,8 +1093,8 @@ int run_batch(BatchCtx& c, const BatchPlan& plan, float* ms, int* graph) {
 
 // The plan for this batch: from the cache, or timed over the candidates
 // (streams 8, 16, 32 -- at most the problem count -- and, for mixed
-// precision, k = 1, 2, 4, each run enqueued directly; then the best of these
-// once more as a captured graph); each candidate runs the whole batch once.
+// precision, k = 1, 2, 4); each candidate runs the whole batch once, after
+// one untimed run.
 int plan_batch(BatchCtx& c, BatchPlan* out) {
     const std::string key = batch_key(*c.hs, c.dev);
     {
@@ -1098,6 +1107,14 @@ int plan_batch(BatchCtx& c, BatchPlan* out) {
             return GP_OK;
         }
     }
+    {
+        // warm the scratch pool, so that the first candidate is not charged for it
+        BatchPlan w;
+        w.streams = std::min(8, (int)c.hs->size());
+        w.k = (*c.hs)[0]->prec != GP_PREC_FP64 ? 2 : 0;
+        const int rc = run_batch(c, w, nullptr, nullptr);
+        if (rc != GP_OK) return rc;
+    }
     const int count = (int)c.hs->size();
     const bool mixed = (*c.hs)[0]->prec != GP_PREC_FP64;
     BatchPlan best;
@@ -1107,32 +1124,23 @@ int plan_batch(BatchCtx& c, BatchPlan* out) {
         if (S > count && S != 8) break;
         for (int k : {1, 2, 4}) {
             if (!mixed && k != 1) break;
-            BatchPlan cand;
-            cand.streams = std::min(S, count);
-            cand.k = mixed ? k : 0;
-            cand.graph = 0;
-            float ms = 0.f;
-            const int rc = run_batch(c, cand, &ms, nullptr);
-            if (rc != GP_OK) return rc;
-            if (ms < best.ms) {
-                best = cand;
-                best.ms = ms;
-                any = true;
+            for (int fcap : {0, 1}) {
+                BatchPlan cand;
+                cand.streams = std::min(S, count);
+                cand.k = mixed ? k : 0;
+                cand.fcap = fcap;
+                float ms = 0.f;
+                const int rc = run_batch(c, cand, &ms, nullptr);
+                if (rc != GP_OK) return rc;
+                if (ms < best.ms) {
+                    best = cand;
+                    best.ms = ms;
+                    any = true;
+                }
             }
         }
     }
     if (!any) best = BatchPlan();
-    if (any) {
-        BatchPlan g = best;
-        g.graph = 1;
-        float ms = 0.f;
-        const int rc = run_batch(c, g, &ms, nullptr);
-        if (rc != GP_OK) return rc;
-        if (ms < best.ms) {
-            best = g;
-            best.ms = ms;
-        }
-    }
     best.cached = false;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_store_locked(key, best);
@@ -1184,7 +1192,7 @@ int gp_fill_shape(GpShape* s, int64_t N, int p, int n, double eps, double alpha,
 
 extern "C" {
 
-GPFAGP_API const char* gp_version(void) { return "gpfagp 0.2 sm_103a"; }
+GPFAGP_API const char* gp_version(void) { return "gpfagp 0.3 sm_103a"; }
 
 GPFAGP_API int gp_last_error(void) { return g_err; }
 GPFAGP_API int64_t gp_last_error_detail(void) { return g_detail; }
@@ -1919,9 +1927,14 @@ GPFAGP_API int gp_batch_info(int* used_graph, int* tuned_k) {
     return GP_OK;
 }
 
-GPFAGP_API int gp_batch_plan(int* streams, int* k, int* from_cache, double* tuned_ms) {
+GPFAGP_API int gp_batch_plan(int* streams, int* k, int* factor_ctas, int* from_cache, double* tuned_ms) {
     if (streams) *streams = g_last_plan.streams;
     if (k) *k = g_last_plan.k;
+    if (factor_ctas) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        *factor_ctas = plan_factor_ctas(g_last_plan, num_sms(dev));
+    }
     if (from_cache) *from_cache = g_last_plan.cached ? 1 : 0;
     if (tuned_ms) *tuned_ms = g_last_plan.ms;
     return GP_OK;

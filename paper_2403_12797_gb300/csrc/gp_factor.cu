@@ -1110,6 +1110,14 @@ size_t factor_work_bytes(int M, bool fp32_inverse) {
     return CHOL_RSD_OFFSET + (inv > chol ? inv : chol);
 }
 
+// A grid capped at max_ctas (> 0), never below lo: the batched fit runs many
+// problems' factorisations side by side, each on a few CTAs (every phase of
+// these kernels walks its work with grid strides, so any grid size is correct).
+int cap_grid(int g, int max_ctas, int lo = 1) {
+    if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+    return g < lo ? lo : g;
+}
+
 // CTAs for the Cholesky of an M x M matrix: about two trailing-update tiles
 // per CTA in the first step (one CTA when there is none), at most one per SM,
 // so that small problems -- e.g. the many problems of a batch running side by
@@ -1137,12 +1145,13 @@ void factor_debug_barrier_timeout(double limit_s, int skip_cta) {
     g_chol_skip_cta.store(skip_cta >= 0 ? skip_cta : -1);
 }
 
-cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream, bool f32_update) {
+cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream, bool f32_update,
+                            int max_ctas) {
     int dev = 0;
     cudaGetDevice(&dev);
     CholWork* cw = (CholWork*)work;
     cudaMemsetAsync(cw, 0, CHOL_RSD_OFFSET, stream);
-    dim3 grid((unsigned)chol_grid(M, dev, f32_update)), block(NT);
+    dim3 grid((unsigned)cap_grid(chol_grid(M, dev, f32_update), max_ctas, M > CB ? 2 : 1)), block(NT);
     const unsigned long long lim = g_chol_wait_ns.load();
     uint64_t wait_ns = lim ? (uint64_t)lim : (uint64_t)GP_WAIT_NS;
     int skip = g_chol_skip_cta.exchange(-1);
@@ -1166,7 +1175,7 @@ int trinv_want(int M, int LB) {
 }  // namespace
 
 cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, int max_ctas) {
     int dev = 0;
     cudaGetDevice(&dev);
     GridBar* gb = (GridBar*)((char*)work + TRINV_BAR_OFFSET);  // zeroed by launch_cholesky
@@ -1180,7 +1189,8 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
         float* WT = Lt;  // W^T goes where L in float is no longer read
         const void* k = (const void*)trinv_rec_kernel<float>;
         const size_t smem = trinv_smem_bytes<float>();
-        dim3 grid((unsigned)std::min(trinv_want(M, InvGeom<float>::LB), coop_grid(k, dev, smem))), block(NT);
+        dim3 grid((unsigned)cap_grid(std::min(trinv_want(M, InvGeom<float>::LB), coop_grid(k, dev, smem)), max_ctas)),
+            block(NT);
         void* args[] = {(void*)&L, &M, &Lt, &Wt, &X, &WT, &st, &gb};
         return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
     }
@@ -1190,7 +1200,8 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
     double* WT = X;  // above the diagonal, where X is never used
     const void* k = (const void*)trinv_rec_kernel<double>;
     const size_t smem = trinv_smem_bytes<double>();
-    dim3 grid((unsigned)std::min(trinv_want(M, InvGeom<double>::LB), coop_grid(k, dev, smem))), block(NT);
+    dim3 grid((unsigned)cap_grid(std::min(trinv_want(M, InvGeom<double>::LB), coop_grid(k, dev, smem)), max_ctas)),
+        block(NT);
     void* args[] = {(void*)&L, &M, &Lt, &Wt, &X, &WT, &st, &gb};
     return cudaLaunchCooperativeKernel(k, grid, block, args, smem, stream);
 }
@@ -1201,7 +1212,7 @@ size_t solve_refine_work_elems(int M) {
 
 cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
                                 double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream,
-                                uint16_t* Wpack) {
+                                uint16_t* Wpack, int max_ctas) {
     uint8_t* wp = fp32 ? reinterpret_cast<uint8_t*>(Wpack) : nullptr;
     int Mpad = (int)gp_round_up(M, PREDTC_KB);
     int dev = 0;
@@ -1217,7 +1228,7 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const void* fw
         float* t = (float*)(work + 32);
         float* r = t + M;
         const void* k = (const void*)solve_coop_kernel<float>;
-        dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+        dim3 grid((unsigned)cap_grid(std::min(want, coop_grid(k, dev)), max_ctas)), block(NT);
         void* args[] = {(void*)&A, (void*)&Wf, (void*)&WTf, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb, &wp, &Mpad};
         return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
     }
@@ -1225,7 +1236,7 @@ cudaError_t launch_solve_refine(const double* A, const double* W, const void* fw
     double* t = work + 32;
     double* r = t + M;
     const void* k = (const void*)solve_coop_kernel<double>;
-    dim3 grid((unsigned)std::min(want, coop_grid(k, dev))), block(NT);
+    dim3 grid((unsigned)cap_grid(std::min(want, coop_grid(k, dev)), max_ctas)), block(NT);
     void* args[] = {(void*)&A, (void*)&W, (void*)&WTd, (void*)&b, &c, &t, &r, &M, &refine, &st, &gb, &wp, &Mpad};
     return cudaLaunchCooperativeKernel(k, grid, block, args, 0, stream);
 }

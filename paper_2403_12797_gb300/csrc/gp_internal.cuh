@@ -113,10 +113,11 @@ struct FitStage {
 // shape-only inputs to the device (log eigenvalues; predict chunk table into the model)
 int fit_stage(gp_model* h, FitStage& stage, double* loglam_d, cudaStream_t stream);
 // every device step of a fit / of a predict, enqueued without host synchronisation
-// gram_prec: precision of the Gram step (-1: the model's); the mixed mode
+// gram_prec: precision of the Gram step (-1: the model's); factor_ctas > 0
+// caps the factorisation kernels' grids (batched fits); the mixed mode
 // escalates to GP_PREC_FP64 after a non-positive pivot (see mixed_escalates)
 int fit_compute(gp_model* h, const double* Xd, const double* yd, const double* loglam_d, GpStatus* st,
-                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec = -1);
+                int gram_ctas, Scratch& sc, cudaStream_t stream, int gram_prec = -1, int factor_ctas = 0);
 // whether a fit that ended with `code` is redone with the float64 Gram: a
 // mixed-precision fit whose Cholesky met a non-positive pivot
 bool mixed_escalates(const gp_model* h, int code);

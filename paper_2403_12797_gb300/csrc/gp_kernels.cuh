@@ -153,8 +153,10 @@ size_t factor_work_bytes(int M, bool fp32_inverse);
 // f32_update: the trailing-update products in float32, subtracted from the
 // float64 trailing matrix (mixed-precision fits); the diagonal blocks and
 // panel solves are float64 either way.
+// max_ctas > 0 caps the grid of this and the two launches below (the
+// batched fit runs several problems' factorisations side by side).
 cudaError_t launch_cholesky(double* L, int M, GpStatus* st, void* work, cudaStream_t stream,
-                            bool f32_update = false);
+                            bool f32_update = false, int max_ctas = 0);
 // Test hook of gp_debug_barrier_timeout: the Cholesky's bounded waits give up
 // after limit_s seconds (<= 0: GP_WAIT_NS), and the next launch's CTA
 // skip_cta (< 0: none) leaves before its first grid-barrier arrival.
@@ -164,7 +166,7 @@ void factor_debug_barrier_timeout(double limit_s, int skip_cta);
 // (fp32 = true; W is not written and may be NULL), where the solve finds it
 // and its transpose.
 cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpStatus* st, void* work,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int max_ctas = 0);
 // c = A^{-1} b through W = L^{-1}: c = W^T (W b), then `refine` steps of
 // c += W^T W (b - A c) with the float64 residual, one cooperative launch.
 // fp32: the products use the float32 W that launch_tri_inverse left in
@@ -173,7 +175,7 @@ cudaError_t launch_tri_inverse(const double* L, double* W, int M, bool fp32, GpS
 // (predtc_wpack_bytes), from the float32 W and the final c.
 cudaError_t launch_solve_refine(const double* A, const double* W, const void* fwork, bool fp32, const double* b,
                                 double* c, double* work, int M, int refine, GpStatus* st, cudaStream_t stream,
-                                uint16_t* Wpack = nullptr);
+                                uint16_t* Wpack = nullptr, int max_ctas = 0);
 size_t solve_refine_work_elems(int M);
 
 // ---- float64 predict (gp_predict64.cu) -----------------------------------------

@@ -176,6 +176,6 @@ def test_batch_plan_cache_persists_across_processes(tmp_path):
         assert r.returncode == 0, r.stderr[-2000:]
         runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
     assert not runs[0]["from_cache"] and runs[1]["from_cache"]
-    assert (runs[1]["streams"], runs[1]["k"]) == (runs[0]["streams"], runs[0]["k"])
+    assert [runs[1][k] for k in ("streams", "k", "factor_ctas")] == [runs[0][k] for k in ("streams", "k", "factor_ctas")]
     lines = cache.read_text().strip().splitlines()
     assert len(lines) == 1 and lines[0].startswith("batch/")
