@@ -206,8 +206,8 @@ def roofline_of(name, groups, pr, prec, steps, pk, profile_name, peak_kind):
     """Roofline object of one kernel group: algorithmic work per launch over its
     average CUDA-event launch time inside the timed steps."""
     M, N, Ns = pr.M, pr.N, pr.Ns
-    # the mixed Gram runs on CTA pairs (gp_syrk_tc2.cu) for M > 512 (p <= 4)
-    pair = M > 512 and pr.p <= 4
+    # the mixed Gram runs on CTA pairs (gp_syrk_tc2.cu) for M > 384 (p <= 4)
+    pair = M > 384 and pr.p <= 4 and prec != "fp64"
     work = {
         "syrk_tc": ("tensor", N * M * (M + 1) + 2 * N * M, "TFLOP/s",
                     "gp_syrk_tc2.cu" if pair else "gp_syrk_tc.cu"),
@@ -225,9 +225,11 @@ def roofline_of(name, groups, pr, prec, steps, pk, profile_name, peak_kind):
         peak = pk["bf16_sus"] if peak_kind == "sustained" else pk["bf16"]
         psrc = (f"measured bf16 dense, {peak_kind} (fp16 operands run at the bf16 rate)"
                 if pk["src"] == "measured" else "fallback")
-    elif name == "cholesky" or prec == "fp64":
+    elif prec == "fp64":
         peak, psrc = FP64_PEAK_TFLOPS, "nominal fp64 (2 DFMA/clock/SM x 152 SMs x 2.07 GHz)"
     else:
+        # mixed: the inverse is float32, and the Cholesky's trailing updates
+        # (nearly all of its M^3 / 3 flops) are float32 products
         peak, psrc = FP32_SIMT_PEAK_TFLOPS, "fp32 SIMT from unit counts and clocks"
     if name == "syrk_tc" and pair:
         profile_name = profile_name.replace("syrk_tc", "syrk_tc2")

@@ -105,12 +105,13 @@ def test_predict_batch_bitwise_equals_single():
 
 
 def test_predict_batch_mixed_dimensions_and_modes():
-    """One gp_predict_batch over models of p = 1..4 in both precision modes
+    """One gp_predict_batch over models of p = 1..5 in both precision modes
     (one persistent predict launch per p for the mixed models), requests
     with and without the variance, sizes from 1 point to several tiles with
     ragged tails: each result bitwise equal to the request alone, and within
     the mode's tolerance of the oracle."""
-    shapes = [(1, 30, 5_000), (2, 12, 8_000), (3, 7, 6_000), (4, 4, 6_000), (2, 20, 12_000), (3, 10, 9_000)]
+    shapes = [(1, 30, 5_000), (2, 12, 8_000), (3, 7, 6_000), (4, 4, 6_000), (2, 20, 12_000), (3, 10, 9_000),
+              (5, 3, 4_000)]
     probs = [W.random_problem(90 + k, N, 700, p, n, eps=0.9 + 0.1 * k, alpha=1.0, sigma2=0.01)
              for k, (p, n, N) in enumerate(shapes)]
     dev = torch.device("cuda", 0)

@@ -30,6 +30,7 @@ CASES = [
     ("p3n12_m1728", lambda: W.random_problem(63, 20_000, 385, 3, 12, eps=1.1, alpha=1.0, sigma2=0.005)),
     ("p4n5", lambda: W.random_problem(64, 8_000, 200, 4, 5, eps=0.8, alpha=1.2, sigma2=0.02)),
     ("ns1", lambda: W.random_problem(65, 2_000, 1, 2, 8, eps=1.0, alpha=0.9, sigma2=0.01)),
+    ("p5n3", lambda: W.random_problem(67, 3_000, 200, 5, 3, eps=0.9, alpha=1.1, sigma2=0.02)),
 ]
 
 TOL = {"fp64": 1e-11, "mixed": 2e-4}

@@ -126,11 +126,15 @@ def _small_cases():
     out.append(W.random_problem(24, 3_000, 200, 1, 129, eps=1.0, alpha=1.0, sigma2=0.02))
     out.append(W.random_problem(25, 4_000, 200, 1, 201, eps=1.0, alpha=1.0, sigma2=0.02))
     out.append(W.random_problem(26, 6_000, 200, 3, 7, eps=0.9, alpha=1.1, sigma2=0.02))
+    # p > 4: the predict kernel's run-time-p generation path, one tile of W
+    # rows and several
+    out.append(W.random_problem(27, 4_000, 300, 5, 3, eps=0.9, alpha=1.1, sigma2=0.02))
+    out.append(W.random_problem(28, 5_000, 260, 6, 3, eps=1.0, alpha=1.0, sigma2=0.02))
     return out
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", range(9))
+@pytest.mark.parametrize("case", range(11))
 def test_fit_predict_matches_oracle(prec, case):
     pr = _small_cases()[case]
     m, mean, var = _fit_predict(pr, prec)
