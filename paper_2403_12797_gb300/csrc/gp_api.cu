@@ -648,14 +648,17 @@ int predict_compute(const gp_model* h, const double* Xd, int64_t Ns, double* md,
         gp_note_launches(3);
     } else {
         float* tab;
+        double* vpart = nullptr;  // partial variances of the super-tiles
         if ((rc = sc.get(&tab, (size_t)s.p * s.n * s.Npad))) return rc;
+        const size_t nv = vd ? predtc_vpart_elems(s.Npad, s.M) : 0;
+        if (nv && (rc = sc.get(&vpart, nv))) return rc;
         {
             GpProf pf("eig_tables", stream);
             launch_eig_tables_f32(s, Xd, nullptr, tab, st, stream);
         }
         GpProf pf("predict_tc", stream);
-        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->sigma2, md, vd, st, stream);
-        gp_note_launches(2);
+        e = launch_predict_tc(s, tab, h->Wpack, h->cinfo, h->sigma2, md, vd, st, stream, nullptr, vpart);
+        gp_note_launches(nv ? 3 : 2);
     }
     return e == cudaSuccess ? GP_OK : cuda_err(e, "predict launch");
 }
@@ -694,6 +697,10 @@ int pred_batch_build(const std::vector<PredEntry>& es, Scratch& sc, PredBatch& p
         r.mean = e.md;
         r.var = e.vd;
         r.st = e.st;
+        const size_t nv = e.vd ? predtc_vpart_elems(r.Npad, s.M) : 0;
+        if (nv && (rc = sc.get(&r.vpart, nv))) return rc;
+        if (nv) pb.reduce = true;
+        pb.max_npad = std::max(pb.max_npad, r.Npad);
         r.consts = reinterpret_cast<const float*>((uintptr_t)pb.consts.size());  // offset until pack()
         for (int j = 0; j < s.p; ++j) {
             pb.consts.push_back(s.abf[j]);
@@ -707,12 +714,34 @@ int pred_batch_build(const std::vector<PredEntry>& es, Scratch& sc, PredBatch& p
         if (pb.groups.empty() || pb.groups.back().p != s.p)
             pb.groups.push_back(PredBatch::Group{s.p, (int)pb.items.size(), 0, 0});
         PredBatch::Group& g = pb.groups.back();
-        for (int64_t t = 0; t < r.Npad / 128; ++t) pb.items.push_back(make_int2(ridx, (int)t));
+        // (tile, super-tile) items, or only the last super-tiles without a
+        // variance; each super-tile's cost grows with its W rows' chunks
+        const int ns = predtc_nsuper(s.M);
+        const int nblocks = (s.M + PREDTC_KB - 1) / PREDTC_KB;
+        for (int sp = (e.vd ? 0 : ns - 1); sp < ns; ++sp) {
+            const int b0 = sp * PREDTC_SUPER, nblk = std::min(PREDTC_SUPER, nblocks - b0);
+            const int mend = std::min(s.M, (b0 + nblk) * PREDTC_KB);
+            const int64_t cost = (int64_t)((mend + PREDTC_BK - 1) / PREDTC_BK) * nblk;
+            for (int64_t t = 0; t < r.Npad / 128; ++t) {
+                pb.items.push_back(make_int2(ridx, (int)(t * ns + sp)));
+                pb.cost.push_back(cost);
+            }
+        }
         g.count = (int)pb.items.size() - g.first;
         g.maxrows = std::max(g.maxrows, r.maxrows);
         pb.reqs.push_back(r);
     }
     pb.boff.push_back(pb.nblocks);
+    // costlier items first within each launch (round-robin over the CTAs)
+    for (const PredBatch::Group& g : pb.groups) {
+        std::vector<int> ord(g.count);
+        for (int i = 0; i < g.count; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return pb.cost[g.first + a] > pb.cost[g.first + b]; });
+        std::vector<int2> tmp(g.count);
+        for (int i = 0; i < g.count; ++i) tmp[i] = pb.items[g.first + ord[i]];
+        std::copy(tmp.begin(), tmp.end(), pb.items.begin() + g.first);
+    }
     for (const PredBatch::Group& g : pb.groups)
         if (predtc_batch_smem_bytes(g.maxrows, g.p) > (227 - 5) * 1024) return set_err(GP_EINVAL, 7);
     auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
@@ -747,6 +776,10 @@ int pred_batch_enqueue(const PredBatch& pb, const uint8_t* dev, cudaStream_t str
         GpProf pf("predict_tc_batch", stream);
         cudaError_t e = launch_predict_tc_batch(dreqs, ditems + g.first, g.count, g.p, g.maxrows, stream);
         if (e != cudaSuccess) return cuda_err(e, "batched predict launch");
+        ++nl;
+    }
+    if (pb.reduce) {
+        launch_predict_reduce_batch(dreqs, (int)pb.reqs.size(), pb.max_npad, stream);
         ++nl;
     }
     gp_note_launches(nl);

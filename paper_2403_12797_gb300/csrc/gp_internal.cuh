@@ -139,7 +139,8 @@ struct PredEntry {
 };
 struct PredBatch {
     std::vector<PredReq> reqs;
-    std::vector<int2> items;    // (request, tile), grouped by p, heavier requests first
+    std::vector<int2> items;    // (request, tile * nsuper + super-tile), grouped by p, costlier first
+    std::vector<int64_t> cost;  // per item while building
     std::vector<int> boff;      // table blocks of each request (nreq + 1)
     std::vector<float> consts;  // 3p per request; PredReq::consts holds the float offset until pack()
     struct Group {
@@ -147,6 +148,8 @@ struct PredBatch {
     };
     std::vector<Group> groups;
     int max_n = 0, nblocks = 0;
+    bool reduce = false;        // some request sums partial variances (launch_predict_reduce_batch)
+    int64_t max_npad = 0;
     size_t off_items = 0, off_boff = 0, off_consts = 0, total = 0;  // upload layout (bytes)
 };
 // Lays out the entries (tables of X* taken from sc) and sizes the upload.

@@ -218,16 +218,28 @@ struct PredReq {
     double* mean;           // Ns outputs
     double* var;            // Ns outputs, or NULL
     uint8_t* zpack;         // optional rows of Z (predtc_zpack_bytes)
+    double* vpart;          // with var and more than one super-tile: the items' partial
+                            // variances, predtc_vpart_elems (summed by the reduce launch)
     GpStatus* st;           // this request's status word
 };
 int predtc_window_rows(const GpShape& s);  // a model's PredReq::maxrows
+// Super-tiles of W rows (512 each) of a model with M columns: the items of a
+// request are its (128-point tile, super-tile) pairs when the variance or
+// Z is wanted, else its tiles' last super-tiles only (the mean).
+int predtc_nsuper(int M);
+size_t predtc_vpart_elems(int64_t Npad, int M);  // 0 when there is one super-tile
 
 // The batched form (one launch per basis dimension p): the kernel's CTAs walk
-// items[0 .. nitems) = (request, 128-point tile) in a fixed round-robin order;
-// maxrows_all and crp4_all bound the requests' windows and column maps
-// (they size the pipeline stages). Every request's p must equal `p`.
+// items[0 .. nitems) = (request, tile * nsuper + super-tile) in a fixed
+// round-robin order; maxrows_all bounds the requests' windows (it sizes the
+// pipeline stages). Every request's p must equal `p`. Requests with several
+// super-tiles and a variance then need launch_predict_reduce_batch.
 cudaError_t launch_predict_tc_batch(const PredReq* reqs, const int2* items, int nitems, int p, int maxrows_all,
                                     cudaStream_t stream);
+// var = sigma2 * (the sum of the partial variances over the super-tiles, in
+// their order) for every request of the table with several super-tiles and a
+// variance (max_npad bounds the requests' Npad).
+void launch_predict_reduce_batch(const PredReq* reqs, int nreq, int64_t max_npad, cudaStream_t stream);
 size_t predtc_batch_smem_bytes(int maxrows_all, int p);
 // Tables of every request of a batch: the grid's blocks [boff[r], boff[r+1])
 // belong to request r (256 points x one dimension each; boff has nreq + 1
@@ -238,9 +250,12 @@ void launch_eig_tables_batch(const PredReq* reqs, const int* boff, int nreq, int
 // zpack (optional, predtc_zpack_bytes): the rows of Z = Phi_* W^T as bf16
 // hi/lo, per 128-point tile and 32-column chunk an 8 KB hi block and an 8 KB
 // lo block in the K-major core-matrix layout of a tcgen05 operand
+// vpart: predtc_vpart_elems(s.Npad, s.M) doubles of scratch, needed when var
+// is given and the model has more than one super-tile
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack,
                               const int* cinfo, double sigma2, double* mean, double* var,
-                              GpStatus* st, cudaStream_t stream, uint8_t* zpack = nullptr);
+                              GpStatus* st, cudaStream_t stream, uint8_t* zpack = nullptr,
+                              double* vpart = nullptr);
 size_t predtc_zpack_bytes(int64_t Npad, int M);
 
 // ---- predictive covariance block (gp_cov.cu) ------------------------------------

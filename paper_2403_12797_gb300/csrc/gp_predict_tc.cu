@@ -101,17 +101,26 @@ __device__ __forceinline__ void gen8(const float* win, const int* map, int p, in
     }
 }
 
-// Item w of the launch: (request, 128-point tile). A plain predict passes
-// its one request by value and no item table (item w = tile w).
+__host__ __device__ inline int nsuper_of(int M) { return ((M + KB - 1) / KB + SUPER - 1) / SUPER; }
+
+// Item w of the launch: (request, 128-point tile, super-tile). A plain
+// predict passes its one request by value and no item table: its items are
+// the tiles' super-tiles, the costlier (later) super-tiles first, or only
+// the last super-tiles when neither the variance nor Z is wanted.
 __device__ __forceinline__ const PredReq& item_req(const PredReq& r0, const PredReq* __restrict__ reqs,
-                                                   const int2* __restrict__ items, int w, int& tile) {
+                                                   const int2* __restrict__ items, int w, int& tile, int& sup) {
     if (items == nullptr) {
-        tile = w;
+        const int ntiles = (int)(r0.Npad / TT), ns = nsuper_of(r0.M);
+        tile = w % ntiles;
+        sup = ns - 1 - w / ntiles;
         return r0;
     }
     const int2 it = __ldg(items + w);
-    tile = it.y;
-    return reqs[it.x];
+    const PredReq& R = reqs[it.x];
+    const int ns = nsuper_of(R.M);
+    tile = it.y / ns;
+    sup = it.y % ns;
+    return R;
 }
 
 template <int P>
@@ -167,8 +176,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         int gc = 0, gs = 0, li = 0;
         for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++li) {
-            int tile;
-            const PredReq& R = item_req(r0, reqs, items, w, tile);
+            int tile, isup;
+            const PredReq& R = item_req(r0, reqs, items, w, tile, isup);
             const int p = P > 0 ? P : R.p;
             const int M = R.M;
             const int64_t t0 = (int64_t)tile * TT;
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint8_t* zpack = R.zpack;
             GpStatus* st = R.st;
             double macc = 0.0, vacc = 0.0;
-            for (int sup = 0; sup < nsuper && ok; ++sup, ++gs) {
+            for (int sup = isup; sup <= isup && ok; ++sup, ++gs) {  // this item's super-tile
                 const int b0 = sup * SUPER;
                 const int nblk = min(SUPER, nblocks - b0);
                 const int nch = super_chunks(M, b0, nblk);
@@ -285,8 +294,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 if (t0 + t < R.Ns) {
-                    R.mean[t0 + t] = macc + comb_m[cbuf][t];
-                    if (R.var) R.var[t0 + t] = R.sigma2 * (vacc + comb_v[cbuf][t]);
+                    // the last super-tile meets every chunk of Phi_*: it forms the mean
+                    if (isup == nsuper - 1) R.mean[t0 + t] = macc + comb_m[cbuf][t];
+                    if (R.var) {
+                        const double v = vacc + comb_v[cbuf][t];
+                        if (nsuper == 1) R.var[t0 + t] = R.sigma2 * v;
+                        else R.vpart[(int64_t)isup * R.Npad + t0 + t] = v;
+                    }
                 }
             }
         }
@@ -298,13 +312,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int gc = 0, gs = 0;
             bool ok = true;
             for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
-                int tile;
-                const PredReq& R = item_req(r0, reqs, items, w, tile);
+                int tile, isup;
+                const PredReq& R = item_req(r0, reqs, items, w, tile, isup);
                 const int M = R.M;
                 GpStatus* st = R.st;
                 const int nblocks = (M + KB - 1) / KB;
-                const int nsuper = (nblocks + SUPER - 1) / SUPER;
-                for (int sup = 0; sup < nsuper && ok; ++sup, ++gs) {
+                for (int sup = isup; sup <= isup && ok; ++sup, ++gs) {
                     const int b0 = sup * SUPER;
                     const int nblk = min(SUPER, nblocks - b0);
                     const int nch = super_chunks(M, b0, nblk);
@@ -358,14 +371,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int gc = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
-            int tile;
-            const PredReq& R = item_req(r0, reqs, items, w, tile);
+            int tile, isup;
+            const PredReq& R = item_req(r0, reqs, items, w, tile, isup);
             const int p = P > 0 ? P : R.p;
             const int M = R.M;
             GpStatus* st = R.st;
             const int64_t t0 = (int64_t)tile * TT;
             const int nblocks = (M + KB - 1) / KB;
-            const int nsuper = (nblocks + SUPER - 1) / SUPER;
             const int KBtot = R.Mpad / KB;
             const int mrows = R.maxrows;
             const int crp4 = (BK * p + 3) & ~3;
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint8_t* Wpack = R.Wpack;
             const float* tab = R.tab;
             const int64_t Npad = R.Npad;
-            for (int sup = 0; sup < nsuper && ok; ++sup) {
+            for (int sup = isup; sup <= isup && ok; ++sup) {
                 const int b0 = sup * SUPER;
                 const int nblk = min(SUPER, nblocks - b0);
                 const int nch = super_chunks(M, b0, nblk);
@@ -427,6 +439,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// var = sigma2 * sum over the super-tiles (in their order) of the partial
+// variances; blockIdx.y = request (the one by value when reqs is NULL)
+__global__ void __launch_bounds__(256) predict_reduce_kernel(const __grid_constant__ PredReq r0,
+                                                             const PredReq* __restrict__ reqs) {
+    const PredReq& R = reqs ? reqs[blockIdx.y] : r0;
+    const int ns = nsuper_of(R.M);
+    if (ns == 1 || R.var == nullptr) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R.Ns) return;
+    double v = 0.0;
+    for (int k = 0; k < ns; ++k) v += R.vpart[(int64_t)k * R.Npad + t];
+    R.var[t] = R.sigma2 * v;
+}
+
 }  // namespace
 
 // packed hi/lo blocks of W (4 Mpad^2 bytes), then c in float32 (Mpad floats)
@@ -476,6 +502,13 @@ size_t predtc_smem_bytes(const GpShape& s) {
 
 int predtc_window_rows(const GpShape& s) { return predtc_maxrows(s); }
 
+int predtc_nsuper(int M) { return nsuper_of(M); }
+
+size_t predtc_vpart_elems(int64_t Npad, int M) {
+    const int ns = nsuper_of(M);
+    return ns > 1 ? (size_t)ns * (size_t)Npad : 0;
+}
+
 size_t predtc_batch_smem_bytes(int maxrows_all, int p) { return smem_bytes(maxrows_all, (BK * p + 3) & ~3); }
 
 namespace {
@@ -521,7 +554,7 @@ cudaError_t predict_tc_dispatch(const PredReq& r0, const PredReq* reqs, const in
 
 cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t* Wpack, const int* cinfo,
                               double sigma2, double* mean, double* var, GpStatus* st, cudaStream_t stream,
-                              uint8_t* zpack) {
+                              uint8_t* zpack, double* vpart) {
     PredReq r{};
     r.Ns = s.N;
     r.Npad = s.Npad;
@@ -538,8 +571,22 @@ cudaError_t launch_predict_tc(const GpShape& s, const float* tab, const uint16_t
     r.mean = mean;
     r.var = var;
     r.zpack = zpack;
+    r.vpart = vpart;
     r.st = st;
-    return predict_tc_dispatch(r, nullptr, nullptr, (int)(s.Npad / TT), r.maxrows, s.p, stream);
+    const int ns = nsuper_of(s.M);
+    if (var != nullptr && ns > 1 && vpart == nullptr) return cudaErrorInvalidValue;
+    const int ntiles = (int)(s.Npad / TT);
+    const int nitems = ntiles * ((var != nullptr || zpack != nullptr) ? ns : 1);
+    cudaError_t e = predict_tc_dispatch(r, nullptr, nullptr, nitems, r.maxrows, s.p, stream);
+    if (e != cudaSuccess || var == nullptr || ns == 1 || s.N == 0) return e;
+    predict_reduce_kernel<<<dim3((unsigned)((s.N + 255) / 256), 1), 256, 0, stream>>>(r, nullptr);
+    return cudaGetLastError();
+}
+
+void launch_predict_reduce_batch(const PredReq* reqs, int nreq, int64_t max_npad, cudaStream_t stream) {
+    if (nreq <= 0 || max_npad <= 0) return;
+    PredReq none{};
+    predict_reduce_kernel<<<dim3((unsigned)((max_npad + 255) / 256), (unsigned)nreq), 256, 0, stream>>>(none, reqs);
 }
 
 cudaError_t launch_predict_tc_batch(const PredReq* reqs, const int2* items, int nitems, int p, int maxrows_all,

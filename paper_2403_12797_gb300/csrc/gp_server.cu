@@ -157,7 +157,7 @@ size_t predict_bytes(const gp_model* m, int64_t Ns) {
     if (m->prec == GP_PREC_FP64)
         b += (size_t)s.p * s.n * Npad * 8 + predict64_part_elems((int64_t)Npad, s.M) * 8;
     else
-        b += (size_t)s.p * s.n * Npad * 4;
+        b += (size_t)s.p * s.n * Npad * 4 + predtc_vpart_elems((int64_t)Npad, s.M) * 8;
     return b + (1 << 20);  // pool granularity slack
 }
 
