@@ -232,7 +232,6 @@ struct MixedGram {
     float* tabc = nullptr;
     float2* Gpart = nullptr;
     double* bpart = nullptr;
-    unsigned int *tmax = nullptr, *tmaxb = nullptr;
     int* colexp = nullptr;
     signed char* ebx = nullptr;
 };
@@ -248,18 +247,17 @@ int mixed_gram_prepare(const GpShape& s, int dev, const double* Xd, const double
     if ((rc = sc.get(&g.tabc, syrktc_table_floats(sg)))) return rc;
     if ((rc = sc.get(&g.Gpart, (size_t)g.spl.smax * npairs * SYRKTC_TM * SYRKTC_TM))) return rc;
     if ((rc = sc.get(&g.bpart, (size_t)g.spl.smax * sg.Mpad))) return rc;
-    if ((rc = sc.get(&g.tmax, (size_t)sg.p * sg.n))) return rc;
-    if ((rc = sc.get(&g.tmaxb, (size_t)sg.p * sg.n * ((sg.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
     if ((rc = sc.get(&g.colexp, (size_t)sg.Mpad))) return rc;
     if ((rc = sc.get(&g.ebx, syrktc_ebx_bytes(sg)))) return rc;
     {
         GpProf pf("eig_tables", stream);
-        launch_eig_tables_chunked(sg, Xd, yd, g.tabc, g.tmaxb, g.tmax, st, stream);
-        gp_note_launches(2);
-    }
-    if (exponents) {  // (launch_syrk_tc forms them itself)
-        launch_colexp(sg, g.tmaxb, g.tmax, g.colexp, g.ebx, stream);
+        launch_eig_tables_chunked(sg, Xd, yd, g.tabc, st, stream);
         gp_note_launches(1);
+    }
+    if (exponents) {
+        GpProf pf("colexp", stream);
+        launch_colexp(sg, g.tabc, g.colexp, g.ebx, stream);
+        gp_note_launches(2);
     }
     return GP_OK;
 }
@@ -326,13 +324,12 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         if (!pair) {
             MixedGram g;
-            if ((rc = mixed_gram_prepare(s, dev, Xd, yd, st, sc, stream, target_ctas, g, false))) return rc;
+            if ((rc = mixed_gram_prepare(s, dev, Xd, yd, st, sc, stream, target_ctas, g, true))) return rc;
             {
                 GpProf pf("syrk_tc", stream);
-                cudaError_t e = launch_syrk_tc(g.sg, g.tabc, g.tmaxb, g.tmax, g.spl, g.Gpart, g.bpart, g.colexp,
-                                               g.ebx, st, stream);
+                cudaError_t e = launch_syrk_tc(g.sg, g.tabc, g.spl, g.Gpart, g.bpart, g.colexp, g.ebx, st, stream);
                 if (e != cudaSuccess) return cuda_err(e, "syrk_tc launch");
-                gp_note_launches(2);
+                gp_note_launches(1);
             }
             mixed_gram_assemble(g, s.M, d, A, b, stream, ex, l_written);
             cudaError_t e = cudaGetLastError();
@@ -352,23 +349,25 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16);
         if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
         if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
-        unsigned int *tmax, *tmaxb;
         int* colexp;
         signed char* ebx;
-        if ((rc = sc.get(&tmax, (size_t)sg.p * sg.n))) return rc;
-        if ((rc = sc.get(&tmaxb, (size_t)sg.p * sg.n * ((sg.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK)))) return rc;
         if ((rc = sc.get(&colexp, (size_t)sg.Mpad))) return rc;
         if ((rc = sc.get(&ebx, syrktc_ebx_bytes(sg)))) return rc;
         {
             GpProf pf("eig_tables", stream);
-            launch_eig_tables_chunked(sg, Xd, yd, tabc, tmaxb, tmax, st, stream);
+            launch_eig_tables_chunked(sg, Xd, yd, tabc, st, stream);
+            gp_note_launches(1);
+        }
+        {
+            GpProf pf("colexp", stream);
+            launch_colexp(sg, tabc, colexp, ebx, stream);
             gp_note_launches(2);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc2(sg, tabc, tmaxb, tmax, spl, Gpart2, bpart, colexp, ebx, st, stream);
+            cudaError_t e = launch_syrk_tc2(sg, tabc, spl, Gpart2, bpart, colexp, ebx, st, stream);
             if (e != cudaSuccess) return cuda_err(e, "syrk_tc2 launch");
-            gp_note_launches(2);
+            gp_note_launches(1);
         }
         {
             GpProf pf("assemble", stream);

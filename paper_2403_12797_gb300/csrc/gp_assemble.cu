@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
     for (int s = 0; s < nsplit; ++s) acc += to_f64(Gpart[off + s * sstride]);
     if (row == col && dpart != nullptr)
         for (int s = 0; s < nsplit; ++s) acc += to_f64(dpart[(int64_t)s * Mpad + row]);
-    if (colexp != nullptr) acc = ldexp(acc, colexp[r] + colexp[c] - 14);
+    if (colexp != nullptr) acc = ldexp(acc, colexp[r] + colexp[c] - 12);
     if (row == col && d != nullptr) acc += d[row];
     A[(int64_t)row * M + col] = acc;
     if (row == 0) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const void* __res
                 }
                 sum = (double)hi + (double)lo;
             }
-            const int e = colexp[r] + colexp[c] - 14;  // |e| well inside float64's exponent range
+            const int e = colexp[r] + colexp[c] - 12;  // |e| well inside float64's exponent range
             v = sum * __hiloint2double((e + 1023) << 20, 0);
             if (r == c) v += sd[ty];
             A[(int64_t)r * M + c] = v;

@@ -12,18 +12,17 @@ void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, d
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream);
 
-// Rows per block of the mixed-precision Gram (exact tensor-core sums) and of
-// the per-block table maxima.
-constexpr int GP_TAB_BLOCK = 1024;
+// Rows per block of the mixed-precision Gram: the tensor-core integer sums
+// are exact over one block, and each block scales its columns by their own
+// maxima.
+constexpr int GP_TAB_BLOCK = 4096;
 // Chunk-major float32 table of the mixed-precision Gram: chunk q of 32 rows
 // holds table row R = j*n + k at tabc[q*RC + R*SYRKTC_WS + i%32] and y in row
 // p*n, RC = (p*n + 1) * SYRKTC_WS (row stride 36 floats, 4 of them zero).
 constexpr int SYRKTC_WS = 36;
 size_t syrktc_table_floats(const GpShape& s);
-void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
-                               unsigned int* tmaxb, unsigned int* tmax, GpStatus* st, cudaStream_t stream);
-// (also fills) tmaxb[b * p*n + j*n + k] = max |tabc row j*n+k| over rows i of
-// block b, and tmax[j*n + k] = the maximum over all rows (float bits).
+void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc, GpStatus* st,
+                               cudaStream_t stream);
 
 // ---- float64 Gram (gp_syrk64.cu) ---------------------------------------------
 // Tile 64 x 64, lower-triangular tile pairs x N splits.
@@ -51,11 +50,10 @@ size_t syrktc_smem_bytes(const GpShape& s);
 // bytes of the per-block column exponents the launch needs (ebx argument)
 size_t syrktc_ebx_bytes(const GpShape& s);
 // Gpart holds column-scaled partial tiles as float pairs hi + lo (units
-// 2^(14 - E_m - E_m')) at (split * npairs + pair), colexp[m] = E_m (Mpad,
-// written here), bpart the unscaled float64 Phi^T y partials at
+// 2^(12 - E_m - E_m')) at (split * npairs + pair), with colexp and ebx formed
+// before by launch_colexp, bpart the unscaled float64 Phi^T y partials at
 // (split * Mpad + m), from the pairs (I, 0).
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
-                           const unsigned int* tmax, const SyrkSplit& sp, float2* Gpart, double* bpart,
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const SyrkSplit& sp, float2* Gpart, double* bpart,
                            int* colexp, signed char* ebx, GpStatus* st, cudaStream_t stream);
 
 // One problem of a batched Gram launch: the arguments launch_syrk_tc takes
@@ -81,8 +79,9 @@ int64_t syrktc_items(const GpShape& s, const SyrkSplit& sp);
 // bounds every problem's tile window (gp_max_window_rows(s, 128)).
 cudaError_t launch_syrk_tc_batch(const SyrkBatchProb* probs, int nprob, int64_t items, int p, int maxrows,
                                  cudaStream_t stream);
-void launch_colexp(const GpShape& s, const unsigned int* tmaxb, const unsigned int* tmax, int* colexp,
-                   signed char* ebx, cudaStream_t stream);
+// ebx[b * Mpad + m] = E_m of block b (the exact maximum of |Phi[:, m]| over the
+// block's rows is below 2^E_m), colexp[m] = the largest of them
+void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);
@@ -120,12 +119,11 @@ __host__ __device__ __forceinline__ int gp_pair_tile_offset(int R, int C) {
 }
 // clusters of the kernel that are resident at once on device dev
 int syrktc2_max_clusters(const GpShape& s, int dev);
-cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned int* tmaxb, const unsigned int* tmax,
-                            const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
+cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
                             GpStatus* st, cudaStream_t stream);
 
 // float-pair partials of the tensor-core Gram (tile x tile partial tiles, tile
-// 128 or 256): A[m][m'] = split sum * 2^(E_m + E_m' - 14) (+ d)
+// 128 or 256): A[m][m'] = split sum * 2^(E_m + E_m' - 12) (+ d)
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex = nullptr);

@@ -64,7 +64,7 @@ constexpr int TM = SYRKTC_TM;              // 128
 constexpr int CW = SYRKTC_BK;              // 32 rows per table chunk
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
-constexpr int FLUSH_BLOCKS = 4;            // blocks summed in the TMEM float32 sum between flushes
+constexpr int FLUSH_BLOCKS = 1;            // blocks summed in the TMEM float32 sum between flushes
 // A pipeline stage holds H table chunks (KS = 32 H rows; H = 2 unless the
 // windows of two chunks do not fit): per-stage costs -- waits, arrivals, the
 // MMA issue -- are paid once per KS rows.
@@ -143,34 +143,237 @@ __host__ __device__ inline size_t smem_tc_layout(int maxrows, int p, int nst, in
     return off + 1024;  // slack for aligning the dynamic base
 }
 
-// exponent e with |x| < 2^e (0 for x == 0)
-__device__ __forceinline__ int bound_exp(unsigned int bits) {
-    int e = 0;
-    frexpf(__uint_as_float(bits), &e);
-    return e;
+// 8 consecutive floats of the table in global memory (read-only path)
+__device__ __forceinline__ void ld_row8g(const float* p, float v[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
-// sum over dimensions of the table-maximum exponents of column m
-__device__ __forceinline__ int column_exp(const GpShape& s, const unsigned int* __restrict__ tm, int m) {
-    int E = 0;
-    for (int j = 0; j < s.p; ++j) E += bound_exp(tm[j * s.n + (m / s.stride[j]) % s.n]);
-    return E < -100 ? -100 : E;
+// the same from shared memory (generic pointer), and the product with one
+__device__ __forceinline__ void ld_row8s(const float* p, float v[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void mul_row8s(const float* p, float v[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] *= a.x; v[1] *= a.y; v[2] *= a.z; v[3] *= a.w;
+    v[4] *= b.x; v[5] *= b.y; v[6] *= b.z; v[7] *= b.w;
 }
 
-// Column exponents: ebx[b * Mpad + m] = E_m of 1024-row block b (b < nblk),
-// colexp[m] = the global E_m (blockIdx.y == nblk); 0 for padding columns.
-__global__ void colexp_kernel(GpShape s, const unsigned int* __restrict__ tmaxb,
-                              const unsigned int* __restrict__ tmax, int nblk, int* __restrict__ colexp,
-                              signed char* __restrict__ ebx) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= s.Mpad) return;
+// Column exponents from exact block maxima. For block b (GP_TAB_BLOCK rows)
+// and column m, bmax[b * Mpad + m] = max over the block's rows i of
+// |Phi[i, m]| (float bits; non-negative floats order as their bits), with
+// Phi formed from the chunk-major float32 table exactly as the Gram kernels
+// form it: the left-to-right product over the dimensions (Eq. 19). Then
+// ebx[b * Mpad + m] = E with that maximum times (1 + 2^-20) below 2^E (so
+// any other rounding order of the products also stays below 2^E), -100 for
+// a column that is zero in the block, and colexp[m] = the largest E over the
+// blocks: the Gram kernels' scaled values w = Phi 2^(6 - E) have |w| < 64.
+// Columns are m = u n + k: u the digits of the upper p - 1 dimensions, k the
+// last dimension's digit (stride 1).
+
+// One thread: one u, 8 consecutive k, rows 8g .. 8g + 7 of every 32-row
+// chunk of block b (g = lane & 3), table read through the read-only cache.
+// The general form (any p, any table size), one CTA column per block.
+template <int P>  // p (1..4), or 0: p at run time
+__global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float* __restrict__ tabc, int U, int K8,
+                                                         unsigned int* __restrict__ bmax) {
     const int b = blockIdx.y;
-    if (b == nblk) {
-        colexp[m] = m < s.M ? column_exp(s, tmax, m) : 0;
-    } else {
-        const int E = m < s.M ? column_exp(s, tmaxb + (int64_t)b * s.p * s.n, m) : 0;
-        ebx[(int64_t)b * s.Mpad + m] = (signed char)(E > 127 ? 127 : E);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t & 3, item = t >> 2;
+    const int k8 = item % K8, u = item / K8;
+    const bool active = u < U;
+    const int n = s.n, p = P > 0 ? P : s.p;
+    const int64_t RC = (int64_t)(p * n + 1) * WS;
+    const int64_t q0 = (int64_t)b * (GP_TAB_BLOCK / CW);
+    const int64_t q1 = min(q0 + GP_TAB_BLOCK / CW, s.Npad / CW);
+    int uoff[GP_PMAX];
+    {
+        int rest = u;
+#pragma unroll
+        for (int j = GP_PMAX - 2; j >= 0; --j) {  // digit of dimension j
+            if (j < p - 1) {
+                uoff[j] = (j * n + rest % n) * WS + 8 * g;
+                rest /= n;
+            }
+        }
     }
+    const int kbase = k8 * 8;
+    const int nk = min(8, n - kbase);
+    const int koff = ((p - 1) * n + kbase) * WS + 8 * g;
+    float mx[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        for (int64_t q = q0; q < q1; ++q) {
+            const float* c = tabc + q * RC;
+            float pre[8];
+            if (p > 1) {
+                ld_row8g(c + uoff[0], pre);
+                for (int j = 1; j + 1 < p; ++j) {
+                    float r[8];
+                    ld_row8g(c + uoff[j], r);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) pre[i] *= r[i];
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                if (kk < nk) {
+                    float v[8];
+                    ld_row8g(c + koff + kk * WS, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) mx[kk] = fmaxf(mx[kk], fabsf(p > 1 ? pre[i] * v[i] : v[i]));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        mx[kk] = fmaxf(mx[kk], __shfl_xor_sync(0xffffffffu, mx[kk], 1));
+        mx[kk] = fmaxf(mx[kk], __shfl_xor_sync(0xffffffffu, mx[kk], 2));
+    }
+    if (!active || g != 0) return;
+    for (int kk = 0; kk < nk; ++kk) bmax[(int64_t)b * s.Mpad + u * n + kbase + kk] = __float_as_uint(mx[kk]);
+}
+
+constexpr int CM_UT = 4;       // upper-digit products per thread of colmax_ring_kernel
+constexpr int CM_ITEMS = 64;   // (UT products x 8 digits) items per CTA: 4 threads each
+constexpr int CM_STAGES = 4;   // deepest chunk ring
+
+// The staged form for p <= 4: the chunks of a range of block b's rows pass
+// through a shared-memory ring (cp.async, CM_STAGES deep, so the copies run
+// several chunks ahead of the arithmetic). A thread keeps its 8 digits' rows
+// of the last dimension in registers and forms the products with CM_UT
+// upper-digit products; item i of the CTA's tile takes u = (i / K8) UT .. and
+// k = (i % K8) 8 ... blockIdx = (item tile, row range, block). Each CTA
+// folds its maxima into bmax with one atomicMax per column.
+template <int P>
+__global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const float* __restrict__ tabc, int U, int K8,
+                                                          int nitems, int rr, unsigned int* __restrict__ bmax) {
+    extern __shared__ __align__(16) float ring[];
+    const int n = s.n;
+    const int rows = P * n + 1;
+    const int cf = rows * WS;  // floats of one chunk
+    const int b = blockIdx.z;
+    const int64_t qb0 = (int64_t)b * (GP_TAB_BLOCK / CW);
+    const int64_t qb1 = min(qb0 + GP_TAB_BLOCK / CW, s.Npad / CW);
+    const int64_t per = (qb1 - qb0 + rr - 1) / rr;
+    const int64_t q0 = qb0 + (int64_t)blockIdx.y * per;
+    const int nq = (int)max((int64_t)0, min(qb1, q0 + per) - q0);
+    const int g = threadIdx.x & 3;
+    const int item = blockIdx.x * CM_ITEMS + (threadIdx.x >> 2);
+    const bool active = item < nitems;
+    const int k8 = item % K8, uq = item / K8;
+    const int kbase = k8 * 8;
+    const int nk = active ? min(8, n - kbase) : 0;
+    const int koff = ((P - 1) * n + kbase) * WS + 8 * g;
+    int uoff[CM_UT][P > 1 ? P - 1 : 1];
+    int nu = 0;  // valid upper-digit products of this thread
+#pragma unroll
+    for (int uu = 0; uu < CM_UT; ++uu) {
+        const int u = uq * CM_UT + uu;
+        if (active && u < U) nu = uu + 1;
+        int rest = u < U ? u : 0;
+#pragma unroll
+        for (int j = P - 2; j >= 0; --j) {
+            uoff[uu][j] = (j * n + rest % n) * WS + 8 * g;
+            rest /= n;
+        }
+    }
+    float mx[CM_UT][8];
+#pragma unroll
+    for (int uu = 0; uu < CM_UT; ++uu)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mx[uu][kk] = 0.f;
+    const uint32_t ring_s = smem_u32(ring);
+    auto load = [&](int slot, int64_t q) {
+        const float* src = tabc + q * (int64_t)cf;
+        for (int f = threadIdx.x * 4; f < cf; f += blockDim.x * 4)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ring_s + 4u * (uint32_t)(slot * cf + f)),
+                         "l"(src + f)
+                         : "memory");
+    };
+#pragma unroll
+    for (int st = 0; st < CM_STAGES - 1; ++st) {
+        if (st < nq) load(st, q0 + st);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int i = 0; i < nq; ++i) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(CM_STAGES - 2) : "memory");
+        __syncthreads();  // chunk i is in; every thread is done with chunk i - 1's slot
+        if (i + CM_STAGES - 1 < nq) load((i + CM_STAGES - 1) % CM_STAGES, q0 + i + CM_STAGES - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const float* c = ring + (i % CM_STAGES) * cf;
+        float last[8][8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            if (kk < nk) ld_row8s(c + koff + kk * WS, last[kk]);
+#pragma unroll
+        for (int uu = 0; uu < CM_UT; ++uu) {
+            if (uu < nu) {
+                if constexpr (P > 1) {
+                    float pre[8];
+                    ld_row8s(c + uoff[uu][0], pre);
+#pragma unroll
+                    for (int j = 1; j < P - 1; ++j) mul_row8s(c + uoff[uu][j], pre);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        if (kk < nk)
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) mx[uu][kk] = fmaxf(mx[uu][kk], fabsf(pre[r] * last[kk][r]));
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        if (kk < nk)
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) mx[uu][kk] = fmaxf(mx[uu][kk], fabsf(last[kk][r]));
+                }
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+    for (int uu = 0; uu < CM_UT; ++uu)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            mx[uu][kk] = fmaxf(mx[uu][kk], __shfl_xor_sync(0xffffffffu, mx[uu][kk], 1));
+            mx[uu][kk] = fmaxf(mx[uu][kk], __shfl_xor_sync(0xffffffffu, mx[uu][kk], 2));
+        }
+    if (g != 0 || nq == 0) return;
+#pragma unroll
+    for (int uu = 0; uu < CM_UT; ++uu)
+        if (uu < nu)
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                if (kk < nk)
+                    atomicMax(bmax + (int64_t)b * s.Mpad + (uq * CM_UT + uu) * n + kbase + kk,
+                              __float_as_uint(mx[uu][kk]));
+}
+
+// ebx and colexp from bmax: one warp per column, lanes over the blocks.
+__global__ void __launch_bounds__(256) colexp_kernel(GpShape s, int nblk, const unsigned int* __restrict__ bmax,
+                                                     signed char* __restrict__ ebx, int* __restrict__ colexp) {
+    const int m = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (m >= s.Mpad) return;  // whole warps
+    int emax = -100;
+    for (int b = lane; b < nblk; b += 32) {
+        int E = 0;
+        if (m < s.M) {
+            const float x = __uint_as_float(bmax[(int64_t)b * s.Mpad + m]);
+            E = -100;
+            if (x > 0.f) {
+                frexpf(x * 1.00000095367431640625f, &E);  // (1 + 2^-20) max < 2^E
+                E = E < -100 ? -100 : (E > 127 ? 127 : E);
+            }
+            emax = max(emax, E);
+        }
+        ebx[(int64_t)b * s.Mpad + m] = (signed char)E;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if (lane == 0) colexp[m] = m < s.M ? emax : 0;
 }
 
 // Phi values of one column for data rows 8g..8g+7 of the chunk: the product
@@ -457,8 +660,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (c % GM::BLOCK == 0) {
                 // a new 1024-row block: quantisation scales 2^(7 - E_blk)
-                scI = pow2i(7 - eI);
-                scJ = pow2i(7 - eJ);
+                scI = pow2i(6 - eI);
+                scJ = pow2i(6 - eJ);
                 const int nb = c / GM::BLOCK + 1;
                 if (nb < nblocks) {
                     eI = ebx[(int64_t)(blk0 + nb) * s.Mpad + mI];
@@ -654,11 +857,67 @@ int syrk_tc_stages(const GpShape& s, int maxrows, int* H, int* nwr, size_t* smem
 
 }  // namespace
 
-void launch_colexp(const GpShape& s, const unsigned int* tmaxb, const unsigned int* tmax, int* colexp,
-                   signed char* ebx, cudaStream_t stream) {
+namespace {
+int colexp_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+size_t ebx_exp_bytes(const GpShape& s) {
+    return ((size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * (size_t)s.Mpad + 15) & ~(size_t)15;
+}
+}  // namespace
+
+// the block maxima (float bits) follow the exponents in the ebx buffer
+void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream) {
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
-    colexp_kernel<<<dim3((unsigned)((s.Mpad + 255) / 256), (unsigned)(nblk + 1)), 256, 0, stream>>>(
-        s, tmaxb, tmax, nblk, colexp, ebx);
+    unsigned int* bmax = reinterpret_cast<unsigned int*>(ebx + ebx_exp_bytes(s));
+    int U = 1;
+    for (int j = 0; j + 1 < s.p; ++j) U *= s.n;
+    const int K8 = (s.n + 7) / 8;
+    const size_t chunk_bytes = (size_t)(s.p * s.n + 1) * WS * sizeof(float);
+    if (nblk > 0) {
+        cudaMemsetAsync(bmax, 0, sizeof(unsigned int) * (size_t)nblk * s.Mpad, stream);
+        const size_t ring = CM_STAGES * chunk_bytes;
+        if (s.p <= 4 && ring <= 96 * 1024) {
+            const int nitems = (U + CM_UT - 1) / CM_UT * K8;
+            const int tiles = (nitems + CM_ITEMS - 1) / CM_ITEMS;
+            // row ranges per block: about two CTAs per SM in all
+            const int64_t want = 2 * (int64_t)colexp_sms();
+            int rr = (int)std::min<int64_t>(GP_TAB_BLOCK / CW, std::max<int64_t>(1, (want + (int64_t)tiles * nblk - 1) /
+                                                                                      ((int64_t)tiles * nblk)));
+            const dim3 grid((unsigned)tiles, (unsigned)rr, (unsigned)nblk);
+            auto go = [&](auto kern) {
+                if (ring > 48 * 1024) gp_allow_max_smem((const void*)kern);
+                kern<<<grid, CM_ITEMS * 4, ring, stream>>>(s, tabc, U, K8, nitems, rr, bmax);
+            };
+            switch (s.p) {
+                case 1: go(colmax_ring_kernel<1>); break;
+                case 2: go(colmax_ring_kernel<2>); break;
+                case 3: go(colmax_ring_kernel<3>); break;
+                default: go(colmax_ring_kernel<4>); break;
+            }
+        } else {
+            const int64_t threads = (int64_t)U * K8 * 4;
+            const dim3 g2((unsigned)((threads + 255) / 256), (unsigned)nblk);
+            switch (s.p) {
+                case 1: colmax_ldg_kernel<1><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+                case 2: colmax_ldg_kernel<2><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+                case 3: colmax_ldg_kernel<3><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+                case 4: colmax_ldg_kernel<4><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+                default: colmax_ldg_kernel<0><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+            }
+        }
+    }
+    const int64_t warps = s.Mpad;
+    colexp_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(s, nblk, bmax, ebx, colexp);
 }
 
 size_t syrktc_smem_bytes(const GpShape& s) {
@@ -669,11 +928,10 @@ size_t syrktc_smem_bytes(const GpShape& s) {
 }
 
 size_t syrktc_ebx_bytes(const GpShape& s) {
-    return (size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * (size_t)s.Mpad;
+    return ebx_exp_bytes(s) + sizeof(unsigned int) * (size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * s.Mpad;
 }
 
-cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned int* tmaxb,
-                           const unsigned int* tmax, const SyrkSplit& sp, float2* Gpart, double* bpart,
+cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const SyrkSplit& sp, float2* Gpart, double* bpart,
                            int* colexp, signed char* ebx, GpStatus* st, cudaStream_t stream) {
     if (s.Npad % (2 * CW) != 0) return cudaErrorInvalidValue;
     for (int c = 0; c < 3; ++c)
@@ -683,7 +941,6 @@ cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const unsigned i
     int nwr = 0, H = 1;
     const int nst = syrk_tc_stages(s, maxrows, &H, &nwr, &smem);
     if (nst == 0) return cudaErrorInvalidConfiguration;
-    launch_colexp(s, tmaxb, tmax, colexp, ebx, stream);
     const int T = s.Mpad / TM;
     const int64_t items = (int64_t)T * sp.n[0] + (int64_t)(T - 1) * sp.n[1] + (int64_t)(T - 1) * (T - 2) / 2 * sp.n[2];
     dim3 grid((unsigned)items);

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (c % BLOCK == 0) {
                 // a new 1024-row block: quantisation scales 2^(7 - E_blk)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) sc[k] = pow2i(7 - e[k]);
+                for (int k = 0; k < 4; ++k) sc[k] = pow2i(6 - e[k]);
                 const int nb = c / BLOCK + 1;
                 if (nb < nblocks) {
 #pragma unroll
@@ -788,8 +788,7 @@ int syrktc2_max_clusters(const GpShape& s, int dev) {
     return n;
 }
 
-cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned int* tmaxb, const unsigned int* tmax,
-                            const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
+cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
                             GpStatus* st, cudaStream_t stream) {
     if (!syrktc2_supported(s)) return cudaErrorInvalidValue;
     for (int c = 0; c < 3; ++c)
@@ -798,7 +797,6 @@ cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const unsigned 
     size_t smem = 0;
     int nwr = 0;
     const int nst = syrk_tc2_stages(s, maxrows, &nwr, &smem);
-    launch_colexp(s, tmaxb, tmax, colexp, ebx, stream);
     const int T = s.Mpad / TP;
     switch (s.p) {
         case 1: return go2<1>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);

@@ -154,14 +154,10 @@ __global__ void __launch_bounds__(256) eig_tables_batch_kernel(const PredReq* __
 // Gram: for chunk q = i / 32 of the rows, table row R = j * n + k at
 // T[q * RC + R * WS + i % 32] (WS = 36 floats, the last 4 zero) and y in row
 // R = p * n, RC = (p * n + 1) * WS. One chunk's rows of every table row are
-// thus one contiguous block that a single bulk copy can move. Each warp (32
-// rows of one chunk, hence of one GP_TAB_BLOCK-row block) also folds the
-// maxima |T[R][i]| of its rows into tmaxb[block][R] (float bits, zeroed
-// before): the bounds of the Gram's per-block column scaling.
+// thus one contiguous block that a single bulk copy can move.
 __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, const double* __restrict__ X,
                                                                  const double* __restrict__ y,
-                                                                 float* __restrict__ tab,
-                                                                 unsigned int* __restrict__ tmaxb, GpStatus* st) {
+                                                                 float* __restrict__ tab, GpStatus* st) {
     constexpr int WS = SYRKTC_WS, CW = SYRKTC_BK;
     extern __shared__ __align__(16) unsigned char coef_raw[];
     float* ca = reinterpret_cast<float*>(coef_raw);
@@ -182,7 +178,6 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
     float* chunk = tab + (i / CW) * (int64_t)rows * WS;
     const int k0 = (int)(i % CW);
     float* out = chunk + (int64_t)j * s.n * WS + k0;
-    unsigned int* bmax = tmaxb + (i / GP_TAB_BLOCK) * (int64_t)(s.p * s.n) + (int64_t)j * s.n;
     if (k0 < WS - CW) {  // zero the padding of this thread's share of the rows
         for (int k = 0; k < s.n; ++k) out[k * WS + CW] = 0.f;
         if (j == 0) chunk[(int64_t)(rows - 1) * WS + CW + k0] = 0.f;
@@ -197,14 +192,8 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
         }
     }
     if (j == 0) chunk[(int64_t)(rows - 1) * WS + k0] = (zero || y == nullptr) ? 0.f : gp_d2f_rn(y[i]);
-    // every lane runs the whole recurrence (rows beyond N or with bad input
-    // are zero from q0 on), so the warp reductions see all 32 lanes
-    // (|v| as bits orders like |v|, so one integer warp reduction gives the maximum)
-    auto emit = [&](int k, float v) {
-        out[k * WS] = v;
-        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v)));
-        if ((threadIdx.x & 31) == 0) atomicMax(bmax + k, m);
-    };
+    // rows beyond N or with bad input are zero from q0 on
+    auto emit = [&](int k, float v) { out[k * WS] = v; };
     const float x = zero ? 0.f : gp_d2f_rn(xd);
     const float t = abf * x;
     float q0 = zero ? 0.f : sbf * expf(-d2f * x * x);
@@ -219,23 +208,6 @@ __global__ void __launch_bounds__(256) eig_tables_chunked_kernel(GpShape s, cons
         emit(k + 1, q2);
         q0 = q1;
         q1 = q2;
-    }
-}
-
-// tmax[R] = max over blocks b of tmaxb[b][R] (one CTA per table row R).
-__global__ void __launch_bounds__(256) table_gmax_kernel(const unsigned int* __restrict__ tmaxb, int rows,
-                                                         int nblk, unsigned int* __restrict__ tmax) {
-    __shared__ unsigned int wm[8];
-    const int R = blockIdx.x;
-    unsigned int m = 0u;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) m = max(m, tmaxb[(int64_t)b * rows + R]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < 8; ++w) m = max(m, wm[w]);
-        tmax[R] = m;
     }
 }
 
@@ -269,12 +241,8 @@ size_t syrktc_table_floats(const GpShape& s) {
     return (size_t)(s.Npad / SYRKTC_BK) * (size_t)(s.p * s.n + 1) * SYRKTC_WS;
 }
 
-void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc,
-                               unsigned int* tmaxb, unsigned int* tmax, GpStatus* st, cudaStream_t stream) {
-    const int rows = s.p * s.n;
-    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
-    cudaMemsetAsync(tmaxb, 0, sizeof(unsigned int) * (size_t)rows * nblk, stream);
+void launch_eig_tables_chunked(const GpShape& s, const double* X, const double* y, float* tabc, GpStatus* st,
+                               cudaStream_t stream) {
     dim3 grid((unsigned)((s.Npad + 255) / 256), (unsigned)s.p);
-    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, tmaxb, st);
-    table_gmax_kernel<<<(unsigned)rows, 256, 0, stream>>>(tmaxb, rows, nblk, tmax);
+    eig_tables_chunked_kernel<<<grid, 256, coef_bytes<float>(s), stream>>>(s, X, y, tabc, st);
 }

@@ -101,11 +101,12 @@ def test_fit_predict_python_rejects_mismatched_inputs():
 # ---- the mixed Gram's row-split plan (host logic, no GPU)
 
 _W = (1.0, 1.24, 1.17)  # per-block costs of the pair classes the planner uses
+_BLOCK = 4096            # rows of one exact block of the mixed Gram (GP_TAB_BLOCK)
 
 
 def _plan_cost(T, n, rows):
     npc = (T, T - 1, (T - 1) * (T - 2) // 2)
-    return max((rows[c] // 1024 + 1) * _W[c] for c in range(3) if npc[c] > 0)
+    return max((rows[c] // _BLOCK + 1) * _W[c] for c in range(3) if npc[c] > 0)
 
 
 @pytest.mark.parametrize("T,Npad,target", [(1, 50_048, 152), (2, 100_096, 152), (3, 300_032, 152),
@@ -116,7 +117,7 @@ def test_gram_split_plan_invariants(T, Npad, target):
     npairs = T * (T + 1) // 2
     npc = (T, T - 1, (T - 1) * (T - 2) // 2)
     for c in range(3):
-        assert rows[c] % 1024 == 0 and rows[c] >= 1024
+        assert rows[c] % _BLOCK == 0 and rows[c] >= _BLOCK
         # every split has rows, and the splits cover every row
         assert (n[c] - 1) * rows[c] < Npad <= n[c] * rows[c]
     assert ctas == sum(npc[c] * n[c] for c in range(3))
@@ -124,18 +125,19 @@ def test_gram_split_plan_invariants(T, Npad, target):
         assert ctas <= target  # one wave
         # never worse than the best uniform split that fits the same wave
         ns = target // npairs
-        r = -(-((Npad + 1023) // 1024) // ns) * 1024
+        r = -(-((Npad + _BLOCK - 1) // _BLOCK) // ns) * _BLOCK
         assert _plan_cost(T, n, rows) <= _plan_cost(T, [ns] * 3, [r] * 3) + 1e-9
     else:  # more pairs than CTAs: one split size for every class
         assert n[0] == n[1] == n[2] and rows[0] == rows[1] == rows[2]
 
 
 def test_gram_split_plan_of_the_benchmark_workload():
-    # M = 400 (four 128-column tile rows), N = 200,000 (Npad 200,064), 152 SMs:
-    # 13 / 17 / 16 splits of 16 / 12 / 13 blocks, 151 CTAs (one uniform split
-    # would need 14 blocks per split for every pair)
+    # M = 400 (four 128-column tile rows), N = 200,000 (Npad 200,064, 49
+    # blocks), 152 SMs: 13 / 17 / 13 splits of 4 / 3 / 4 blocks, 142 CTAs,
+    # whose costliest class (4 + 1) * 1.17 beats a uniform split of 15 (4
+    # blocks each: (4 + 1) * 1.24)
     n, rows, ctas = _lib.debug_gram_splits(4, 200_064, 152)
-    assert n == [13, 17, 16] and rows == [16 * 1024, 12 * 1024, 13 * 1024] and ctas == 151
+    assert n == [13, 17, 13] and rows == [4 * _BLOCK, 3 * _BLOCK, 4 * _BLOCK] and ctas == 142
 
 
 def test_gram_split_plan_rejects_bad_arguments():
