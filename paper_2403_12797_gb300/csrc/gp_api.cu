@@ -168,18 +168,19 @@ void choose_splits(int npairs, int64_t Npad, int target_ctas, int64_t granule, i
 // two. Otherwise every class takes the uniform choice of choose_splits.
 //
 // The CTA-pair kernel (tiles of 256) takes the same plan with clusters in
-// place of CTAs, class costs `wc` and up to `max_waves` waves.
+// place of CTAs, class costs `wc`, up to `max_waves` waves and splits of whole
+// GP_PAIR_BLOCK-row blocks (`granule`).
 const double kClassCost1[3] = {1.0, 1.24, 1.17};
 const double kClassCost2[3] = {1.0, 1.05, 1.0};
 void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp, const double* wc = kClassCost1,
-                      int max_waves = 8) {
+                      int max_waves = 8, int granule = GP_TAB_BLOCK) {
     if (target_ctas < 1) target_ctas = 1;
     const int npairs = T * (T + 1) / 2;
     const int64_t npc[3] = {T, T - 1, (int64_t)(T - 1) * (T - 2) / 2};
     if (npairs > target_ctas) {
         int ns;
         int64_t rps;
-        choose_splits(npairs, Npad, target_ctas, GP_TAB_BLOCK, &ns, &rps, max_waves);
+        choose_splits(npairs, Npad, target_ctas, granule, &ns, &rps, max_waves);
         for (int c = 0; c < 3; ++c) {
             sp->n[c] = ns;
             sp->rows[c] = rps;
@@ -187,7 +188,7 @@ void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp, const
         sp->smax = ns;
         return;
     }
-    const int64_t nb = (Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK;
+    const int64_t nb = (Npad + granule - 1) / granule;
     const double* w = wc;
     int64_t n[3] = {1, 1, 1};
     auto cost = [&](int c) { return (double)((nb + n[c] - 1) / n[c] + 1) * w[c]; };
@@ -204,7 +205,7 @@ void choose_splits_tc(int T, int64_t Npad, int target_ctas, SyrkSplit* sp, const
     sp->smax = 1;
     for (int c = 0; c < 3; ++c) {
         const int64_t blocks = (nb + n[c] - 1) / n[c];
-        sp->rows[c] = blocks * GP_TAB_BLOCK;
+        sp->rows[c] = blocks * granule;
         sp->n[c] = (int)((Npad + sp->rows[c] - 1) / sp->rows[c]);
         if (npc[c] > 0 && sp->n[c] > sp->smax) sp->smax = sp->n[c];
     }
@@ -346,7 +347,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         SyrkSplit spl;
         int clusters = syrktc2_max_clusters(sg, dev);
         if (target_ctas > 0) clusters = std::max(1, std::min(clusters, target_ctas / 2));
-        choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16);
+        choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16, GP_PAIR_BLOCK);
         if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
         if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
         int* colexp;

@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(256) assemble_kernel(const P* __restrict__ Gpa
 
 // The mixed-precision Gram's assembly, per 32 x 32 block (bi >= bj) of the
 // lower triangle of A: the float-pair partial tiles (TT x TT) of the splits (column-
-// scaled by 2^(7 - E_m)) are read coalesced along their rows, summed in split
+// scaled by 2^(6 - E_m)) are read coalesced along their rows, summed in split
 // order as an unevaluated float pair (exact two-sum, ~46 bits), converted to
-// float64 once and unscaled by the exact power of two 2^(E_r + E_c - 14); the
+// float64 once and unscaled by the exact power of two 2^(E_r + E_c - 12); the
 // block is written to A and, through shared memory, transposed into the
 // upper triangle (A is exactly symmetric). Diagonal blocks also sum b.
 // d_m = sigma2 / lambda_m = exp(log sigma2 - sum_j log lambda^(j)_{m_j}) (Eq. 16,

@@ -12,10 +12,15 @@ void launch_eig_tables_f64(const GpShape& s, const double* X, const double* y, d
 void launch_eig_tables_f32(const GpShape& s, const double* X, const double* y, float* tab,
                            GpStatus* st, cudaStream_t stream);
 
-// Rows per block of the mixed-precision Gram: the tensor-core integer sums
-// are exact over one block, and each block scales its columns by their own
-// maxima.
-constexpr int GP_TAB_BLOCK = 4096;
+// Rows per block of the mixed-precision Gram's column scales: each block
+// scales its columns by their own exact maxima (|w| < 64), and the one-CTA
+// kernel's tensor-core integer sums (at most 1024 * 64^2 = 2^22) are exact over
+// one block. Row splits are whole blocks.
+constexpr int GP_TAB_BLOCK = 1024;
+// Rows per exact block of the CTA-pair kernel: four scale blocks under the
+// largest of their exponents (4096 * 64^2 = 2^24); its row splits are whole
+// pair blocks.
+constexpr int GP_PAIR_BLOCK = 4096;
 // Chunk-major float32 table of the mixed-precision Gram: chunk q of 32 rows
 // holds table row R = j*n + k at tabc[q*RC + R*SYRKTC_WS + i%32] and y in row
 // p*n, RC = (p*n + 1) * SYRKTC_WS (row stride 36 floats, 4 of them zero).
@@ -79,9 +84,13 @@ int64_t syrktc_items(const GpShape& s, const SyrkSplit& sp);
 // bounds every problem's tile window (gp_max_window_rows(s, 128)).
 cudaError_t launch_syrk_tc_batch(const SyrkBatchProb* probs, int nprob, int64_t items, int p, int maxrows,
                                  cudaStream_t stream);
-// ebx[b * Mpad + m] = E_m of block b (the exact maximum of |Phi[:, m]| over the
-// block's rows is below 2^E_m), colexp[m] = the largest of them
+// ebx (syrktc_ebx_bytes): ebx[b * Mpad + m] = E_m of GP_TAB_BLOCK-row block b
+// (the exact maximum of |Phi[:, m]| over the block's rows is below 2^E_m),
+// then the largest E_m of each GP_PAIR_BLOCK-row block at
+// syrktc_pair_exponents(s, ebx), then the pass's scratch; colexp[m] = the
+// largest E_m over all blocks
 void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream);
+const signed char* syrktc_pair_exponents(const GpShape& s, const signed char* ebx);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
 // A = sum_s Gpart[s] + diag(d) (M x M, full symmetric, row-major, lda = M);

@@ -170,7 +170,7 @@ size_t refit_bytes(const gp_model* m, int64_t N, int sms) {
     if (m->prec != GP_PREC_FP64) b += predtc_wpack_bytes((int)M) + predtc_cinfo_ints(s) * 4;
     b += M * M * 8 + solve_refine_work_elems((int)M) * 8 + factor_work_bytes((int)M, true);
     b += (size_t)s.p * s.n * Npad * 8 + Npad * 8;                 // tables, padded y
-    b += (Npad / GP_TAB_BLOCK + 1) * (size_t)s.Mpad + (size_t)s.Mpad * 4;  // block and global exponents
+    b += (Npad / GP_TAB_BLOCK + 2) * (size_t)s.Mpad * 6 + (size_t)s.Mpad * 4;  // block maxima and exponents
     b += (size_t)(sms + 1) * 4 * (size_t)s.Mpad * s.Mpad * 4 / 2; // split partial tiles (bound)
     return b + (4 << 20);
 }

@@ -10,15 +10,19 @@
 // steps of a large N that bias (~1e-4 relative on G) is amplified by the
 // conditioning of A into percent-level errors of the posterior. The kernel
 // therefore keeps the dominant part of every tensor-core sum exact:
-//   * for every 1024-row block, each column m is scaled by 2^(7 - E_m), where
-//     2^(E_m) bounds |Phi[:, m]| inside the block (the product of the block's
-//     per-dimension table maxima), so |w| <= 128 for w = Phi * 2^(7 - E_m);
+//   * for every GP_TAB_BLOCK (1024) row block, each column m is scaled by
+//     2^(6 - E_m), where 2^(E_m) bounds the exact maximum of |Phi[:, m]|
+//     inside the block (launch_colexp), so |w| < 64 for w = Phi * 2^(6 - E_m);
+//     a looser bound (the product of per-dimension table maxima is ~13x the
+//     true maximum on Gaussian inputs) would leave s1 a few bits and put most
+//     of each value in the truncating remainder sums;
 //   * w = s1 + lo with the integer s1 = rint(w) (exact in fp16) and the
 //     remainder lo = fp16(w - s1), |w - s1| <= 1/2 (2^-12 absolute error);
-//   * acc1 += s1 s1' is an integer sum of magnitude at most 1024 * 128^2 =
-//     2^24 over a block, hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo' is a few
-//     percent of G, so its truncation over one block (~2e-6 of itself) is
-//     negligible;
+//   * acc1 += s1 s1' is an integer sum of magnitude at most 1024 * 64^2 =
+//     2^22 over a block, hence exact in float32; acc2 += s1 lo' + lo s1' + lo lo'
+//     is small beside it, so its truncation over one block is negligible
+//     (the CTA-pair kernel sums 4096 rows, 2^24, under the largest exponent
+//     of four blocks);
 //   * after each block the producers multiply acc1 + acc2 by the exact power
 //     of two that maps the block's column scaling to the global one and add
 //     it into a float32 sum held in TMEM (columns 256-383, beside acc1 and
@@ -29,7 +33,7 @@
 //     over a million rows, enough to make a strongly conditioned A
 //     indefinite. With 1024-row blocks a drain is rare, so the accumulators
 //     are single-buffered: the MMAs of the next block wait for it.
-// Representation error: |w - s1 - lo| <= 2^-12 (2^-19 of the block bound).
+// Representation error: |w - s1 - lo| <= 2^-12 (2^-18 of the block bound).
 //
 // CTA = one 128 x 128 lower-triangular tile pair (I >= J) of G and one split
 // of the rows, pipelined over chunks of 32 rows through nst stages:
@@ -49,7 +53,7 @@
 //              (A tiles and windows) and signals finished blocks.
 // Every warp waits on mbarriers by itself (bounded, decided by a warp vote):
 // there is no CTA-wide barrier inside the pipeline. The block exponents E_m
-// per 1024-row block and the global ones come from a small kernel run first.
+// per block and the global ones come from launch_colexp, run first.
 // The grid is one CTA per (pair, split) work item, the rows split per class
 // of pair (SyrkSplit: diagonal pairs generate one operand tile and take
 // longer splits; the pairs (I, 0) also form b), so the classes end together.
@@ -64,7 +68,7 @@ constexpr int TM = SYRKTC_TM;              // 128
 constexpr int CW = SYRKTC_BK;              // 32 rows per table chunk
 constexpr int STAGES = 4;                  // largest pipeline depth (nst <= STAGES at run time)
 constexpr int WRMAX = 8;                   // deepest table-window ring (nwr <= WRMAX at run time)
-constexpr int FLUSH_BLOCKS = 1;            // blocks summed in the TMEM float32 sum between flushes
+constexpr int FLUSH_BLOCKS = 4;            // blocks summed in the TMEM float32 sum between flushes
 // A pipeline stage holds H table chunks (KS = 32 H rows; H = 2 unless the
 // windows of two chunks do not fit): per-stage costs -- waits, arrivals, the
 // MMA issue -- are paid once per KS rows.
@@ -73,7 +77,7 @@ template <int H> struct StageGeom {
     static constexpr int TILE = TM * KS * 2;              // one 16-bit operand tile
     static constexpr int BYTES = 4 * TILE;                // A s1, A lo, B s1, B lo
     static constexpr uint32_t SBO = (KS / 8) * 128;       // 8-row groups
-    static constexpr int BLOCK = GP_TAB_BLOCK / KS;       // stages per exact 1024-row TMEM block
+    static constexpr int BLOCK = GP_TAB_BLOCK / KS;       // stages per exact GP_TAB_BLOCK-row TMEM block
     static constexpr int BFOLD = 512 / KS;                // stages between float64 folds of b
 };
 constexpr int NPROD = 512;                 // 16 producer warps: one 8-column core group each
@@ -351,25 +355,35 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
                               __float_as_uint(mx[uu][kk]));
 }
 
-// ebx and colexp from bmax: one warp per column, lanes over the blocks.
-__global__ void __launch_bounds__(256) colexp_kernel(GpShape s, int nblk, const unsigned int* __restrict__ bmax,
-                                                     signed char* __restrict__ ebx, int* __restrict__ colexp) {
+// ebx, the pair blocks' exponents ebx4 and colexp from bmax: one warp per
+// column, lanes over the pair blocks (each the GP_PAIR_BLOCK / GP_TAB_BLOCK
+// scale blocks under it).
+__global__ void __launch_bounds__(256) colexp_kernel(GpShape s, int nblk, int nblk4,
+                                                     const unsigned int* __restrict__ bmax,
+                                                     signed char* __restrict__ ebx, signed char* __restrict__ ebx4,
+                                                     int* __restrict__ colexp) {
+    constexpr int SUB = GP_PAIR_BLOCK / GP_TAB_BLOCK;
     const int m = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (m >= s.Mpad) return;  // whole warps
     int emax = -100;
-    for (int b = lane; b < nblk; b += 32) {
-        int E = 0;
-        if (m < s.M) {
-            const float x = __uint_as_float(bmax[(int64_t)b * s.Mpad + m]);
-            E = -100;
-            if (x > 0.f) {
-                frexpf(x * 1.00000095367431640625f, &E);  // (1 + 2^-20) max < 2^E
-                E = E < -100 ? -100 : (E > 127 ? 127 : E);
+    for (int b4 = lane; b4 < nblk4; b4 += 32) {
+        int e4 = m < s.M ? -100 : 0;
+        for (int b = b4 * SUB; b < min(nblk, (b4 + 1) * SUB); ++b) {
+            int E = 0;
+            if (m < s.M) {
+                const float x = __uint_as_float(bmax[(int64_t)b * s.Mpad + m]);
+                E = -100;
+                if (x > 0.f) {
+                    frexpf(x * 1.00000095367431640625f, &E);  // (1 + 2^-20) max < 2^E
+                    E = E < -100 ? -100 : (E > 127 ? 127 : E);
+                }
+                e4 = max(e4, E);
             }
-            emax = max(emax, E);
+            ebx[(int64_t)b * s.Mpad + m] = (signed char)E;
         }
-        ebx[(int64_t)b * s.Mpad + m] = (signed char)E;
+        ebx4[(int64_t)b4 * s.Mpad + m] = (signed char)e4;
+        emax = max(emax, e4);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t r0 = (int64_t)split * rows_c;
     int64_t r1 = r0 + rows_c;
     if (r1 > s.Npad) r1 = s.Npad;
-    // pipeline stages of KS rows (split boundaries are multiples of 1024
+    // pipeline stages of KS rows (split boundaries are multiples of GP_TAB_BLOCK
     // rows and Npad of 128, so KS divides every split)
     const int nchunks = r0 < r1 ? (int)((r1 - r0) / GM::KS) : 0;
     const int nblocks = (nchunks + GM::BLOCK - 1) / GM::BLOCK;
@@ -659,7 +673,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 bacc = 0.f;
             }
             if (c % GM::BLOCK == 0) {
-                // a new 1024-row block: quantisation scales 2^(7 - E_blk)
+                // a new block: quantisation scales 2^(6 - E_blk)
                 scI = pow2i(6 - eI);
                 scJ = pow2i(6 - eJ);
                 const int nb = c / GM::BLOCK + 1;
@@ -870,15 +884,24 @@ int colexp_sms() {
     }
     return cached[dev];
 }
+size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+// bytes of the scale blocks' exponents, and of the pair blocks' after them
 size_t ebx_exp_bytes(const GpShape& s) {
-    return ((size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * (size_t)s.Mpad + 15) & ~(size_t)15;
+    return round16((size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * (size_t)s.Mpad);
+}
+size_t ebx4_exp_bytes(const GpShape& s) {
+    return round16((size_t)((s.Npad + GP_PAIR_BLOCK - 1) / GP_PAIR_BLOCK) * (size_t)s.Mpad);
 }
 }  // namespace
 
-// the block maxima (float bits) follow the exponents in the ebx buffer
+const signed char* syrktc_pair_exponents(const GpShape& s, const signed char* ebx) { return ebx + ebx_exp_bytes(s); }
+
+// the block maxima (float bits) follow both exponent arrays in the ebx buffer
 void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream) {
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
-    unsigned int* bmax = reinterpret_cast<unsigned int*>(ebx + ebx_exp_bytes(s));
+    const int nblk4 = (int)((s.Npad + GP_PAIR_BLOCK - 1) / GP_PAIR_BLOCK);
+    signed char* ebx4 = ebx + ebx_exp_bytes(s);
+    unsigned int* bmax = reinterpret_cast<unsigned int*>(ebx4 + ebx4_exp_bytes(s));
     int U = 1;
     for (int j = 0; j + 1 < s.p; ++j) U *= s.n;
     const int K8 = (s.n + 7) / 8;
@@ -917,7 +940,7 @@ void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char
         }
     }
     const int64_t warps = s.Mpad;
-    colexp_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(s, nblk, bmax, ebx, colexp);
+    colexp_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(s, nblk, nblk4, bmax, ebx, ebx4, colexp);
 }
 
 size_t syrktc_smem_bytes(const GpShape& s) {
@@ -928,7 +951,8 @@ size_t syrktc_smem_bytes(const GpShape& s) {
 }
 
 size_t syrktc_ebx_bytes(const GpShape& s) {
-    return ebx_exp_bytes(s) + sizeof(unsigned int) * (size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * s.Mpad;
+    return ebx_exp_bytes(s) + ebx4_exp_bytes(s) +
+           sizeof(unsigned int) * (size_t)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK) * s.Mpad;
 }
 
 cudaError_t launch_syrk_tc(const GpShape& s, const float* tabc, const SyrkSplit& sp, float2* Gpart, double* bpart,

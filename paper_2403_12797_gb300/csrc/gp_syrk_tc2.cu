@@ -3,7 +3,7 @@
 //
 // Computes G = Phi^T Phi and b = Phi^T y (the products of Lambda-bar and of W
 // in Sec. 2.2; Phi of Eq. 19) with the arithmetic of gp_syrk_tc.cu: per
-// 1024-row block each column is scaled by 2^(7 - E_m) (|w| <= 128) and split
+// GP_PAIR_BLOCK-row block each column is scaled by 2^(6 - E_m) (|w| < 64) and split
 // into the integer s1 = rint(w) and the fp16 remainder lo; s1 s1' is summed
 // exactly in float32 TMEM, s1 lo' + lo s1' + lo lo' beside it; each block's
 // sums are rescaled by exact powers of two and folded into the split's
@@ -75,7 +75,7 @@ constexpr int KS = CW * H;                // 64 rows per stage
 constexpr int TILE = TM * KS * 2;         // bytes of one 16-bit operand tile
 constexpr int SBYTES = 4 * TILE;          // A s1, A lo, B s1, B lo
 constexpr uint32_t SBO = (KS / 8) * 128;  // 8-row core-matrix groups
-constexpr int BLOCK = GP_TAB_BLOCK / KS;  // stages per exact 1024-row block
+constexpr int BLOCK = GP_PAIR_BLOCK / KS;  // stages per exact GP_PAIR_BLOCK-row block
 constexpr int BFOLD = 512 / KS;           // stages between float64 folds of b
 constexpr int STAGES = 3;                 // deepest operand pipeline
 constexpr int WRMAX = 8;                  // deepest window ring
@@ -97,7 +97,7 @@ struct Smem2 {
     int* rng;             // copy ranges (table row, rows, window row)
     double* bred;         // TM: b of the second row-group half (cross-warp sum)
     double* bsum;         // 256 x 4: float64 sums of b per A-half producer thread and column
-    float* msc;           // 2 x (TP + TM): per 1024-row block (double-buffered by parity), the
+    float* msc;           // 2 x (TP + TM): per block (double-buffered by parity), the
                           // B columns' and A-half rows' scales 2^(E_blk - E_glob), from the loader
     uint64_t* full;       // STAGES: leader's, one arrival per producer warp of both CTAs
     uint64_t* empty;      // STAGES: one commit (multicast) per phase
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t r0 = (int64_t)split * rows_c;
     int64_t r1 = r0 + rows_c;
     if (r1 > s.Npad) r1 = s.Npad;
-    const int nchunks = r0 < r1 ? (int)((r1 - r0) / KS) : 0;  // splits are whole 1024-row blocks
+    const int nchunks = r0 < r1 ? (int)((r1 - r0) / KS) : 0;  // splits are whole blocks
     const int nblocks = (nchunks + BLOCK - 1) / BLOCK;
     const int64_t RC = (int64_t)(s.p * s.n + 1) * WS;  // floats per table chunk
     const int wsz1 = win_floats(maxrows);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             return true;
         };
 
-        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
+        const int blk0 = (int)(r0 / GP_PAIR_BLOCK);
         // per-column block exponents, loaded one block ahead
         int e[4] = {0, 0, 0, 0};
         if (nblocks > 0) {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             if (c % BLOCK == 0) {
-                // a new 1024-row block: quantisation scales 2^(7 - E_blk)
+                // a new block: quantisation scales 2^(6 - E_blk)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) sc[k] = pow2i(6 - e[k]);
                 const int nb = c / BLOCK + 1;
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             rsrc = sm.rng[3 * k] * WS;
             rlen = sm.rng[3 * k + 1] * WS * 4;
         }
-        const int blk0 = (int)(r0 / GP_TAB_BLOCK);
+        const int blk0 = (int)(r0 / GP_PAIR_BLOCK);
         int c = 0, wsl = 0, wph = 0;
         for (; c < nchunks; ++c) {
             const bool e = c < nwr || mbar_wait(&sm.wempty[wsl], wph ^ 1);
@@ -792,16 +792,18 @@ cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit
                             GpStatus* st, cudaStream_t stream) {
     if (!syrktc2_supported(s)) return cudaErrorInvalidValue;
     for (int c = 0; c < 3; ++c)
-        if (sp.n[c] < 1 || sp.rows[c] < GP_TAB_BLOCK || sp.rows[c] % GP_TAB_BLOCK != 0) return cudaErrorInvalidValue;
+        if (sp.n[c] < 1 || sp.rows[c] < GP_PAIR_BLOCK || sp.rows[c] % GP_PAIR_BLOCK != 0) return cudaErrorInvalidValue;
+    // the exponents of the pair blocks (launch_colexp writes them after the scale blocks')
+    const signed char* ebx4 = syrktc_pair_exponents(s, ebx);
     const int maxrows = gp_max_window_rows(s, TM);
     size_t smem = 0;
     int nwr = 0;
     const int nst = syrk_tc2_stages(s, maxrows, &nwr, &smem);
     const int T = s.Mpad / TP;
     switch (s.p) {
-        case 1: return go2<1>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        case 2: return go2<2>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        case 3: return go2<3>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        default: return go2<4>(s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
+        case 1: return go2<1>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
+        case 2: return go2<2>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
+        case 3: return go2<3>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
+        default: return go2<4>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
     }
 }

@@ -101,7 +101,7 @@ def test_fit_predict_python_rejects_mismatched_inputs():
 # ---- the mixed Gram's row-split plan (host logic, no GPU)
 
 _W = (1.0, 1.24, 1.17)  # per-block costs of the pair classes the planner uses
-_BLOCK = 4096            # rows of one exact block of the mixed Gram (GP_TAB_BLOCK)
+_BLOCK = 1024            # rows per split block of the one-CTA mixed Gram (GP_TAB_BLOCK)
 
 
 def _plan_cost(T, n, rows):
@@ -132,12 +132,11 @@ def test_gram_split_plan_invariants(T, Npad, target):
 
 
 def test_gram_split_plan_of_the_benchmark_workload():
-    # M = 400 (four 128-column tile rows), N = 200,000 (Npad 200,064, 49
-    # blocks), 152 SMs: 13 / 17 / 13 splits of 4 / 3 / 4 blocks, 142 CTAs,
-    # whose costliest class (4 + 1) * 1.17 beats a uniform split of 15 (4
-    # blocks each: (4 + 1) * 1.24)
+    # M = 400 (four 128-column tile rows), N = 200,000 (Npad 200,064), 152 SMs:
+    # 13 / 17 / 16 splits of 16 / 12 / 13 blocks, 151 CTAs (one uniform split
+    # would need 14 blocks per split for every pair)
     n, rows, ctas = _lib.debug_gram_splits(4, 200_064, 152)
-    assert n == [13, 17, 13] and rows == [4 * _BLOCK, 3 * _BLOCK, 4 * _BLOCK] and ctas == 142
+    assert n == [13, 17, 16] and rows == [16 * _BLOCK, 12 * _BLOCK, 13 * _BLOCK] and ctas == 151
 
 
 def test_gram_split_plan_rejects_bad_arguments():

@@ -70,11 +70,13 @@ def test_gram_matches_oracle(prec, kernel, seed, N, p, n):
 @pytest.mark.parametrize("N,p,n", [(70_000, 3, 16), (40_000, 2, 32), (30_000, 4, 6), (25_000, 1, 700)])
 def test_gram_kernels_agree_at_large_m(N, p, n):
     """The two mixed Gram kernels on the same rows at M = 4096, 1024, 1296, 700:
-    within 1e-6 of each other (the same Phi values and slices; only the order
-    of the exact block folds differs), and both within 5e-5 of the oracle on
-    a row sample. At M = 4096 (p = 3, x ~ N(0, 0.5^2)) the product bound of a
-    column overestimates its values most, and the one-CTA kernel was measured
-    at 2.1e-5 there (at most 1.8e-6 on the smaller parity shapes)."""
+    within 5e-6 of each other, and both within 5e-5 of the oracle on a row
+    sample. They form the same Phi values but slice them under different
+    scales: the one-CTA kernel per 1024-row block, the CTA-pair kernel under
+    the largest exponent of four such blocks (its exact blocks are 4096
+    rows). So they agree only to the sum of their own errors. Measured
+    against the float64 Gram of the same rows: one-CTA 0.45-1.5e-6, pairs
+    0.45-2.1e-6, and the two kernels 0-1.7e-6 apart."""
     pr = W.random_problem(71 + p, N, 1, p, n, eps=1.2, alpha=1.0, law="normal", scale=0.5)
     out = []
     for kernel in (1, 2):
@@ -84,7 +86,7 @@ def test_gram_kernels_agree_at_large_m(N, p, n):
         finally:
             _lib.debug_gram_kernel(0)
     (G1, b1), (G2, b2) = out
-    assert O.relerr(G2, G1) < 1e-6, O.relerr(G2, G1)
+    assert O.relerr(G2, G1) < 5e-6, O.relerr(G2, G1)
     assert O.relerr(b2, b1) < 1e-7, O.relerr(b2, b1)
     np.testing.assert_array_equal(G2, G2.T)
     # the oracle on a row sample: the Gram is a sum over rows, so the first
@@ -237,13 +239,16 @@ def test_workload3_full_size_gram_sampled():
     (40 of them diagonal) and 50 of b = Phi^T y against dot products of the
     oracle's eigenfunction columns (Eq. 19), computed one by one.
 
-    Bound: each Phi value is represented within 2^-19 of its 1024-row block
-    bound B (integer + fp16 remainder split), so
-    |dG_ac| <= 2^-19 sum_i (B_a |Phi_ic| + B_c |Phi_ia|), i.e. relative to
-    |Phi_a| |Phi_c| at most 2^-19 (B_a sqrt(N)/|Phi_a| + B_c sqrt(N)/|Phi_c|);
-    the columns' peak-to-RMS ratios stay below 10 here, giving 4e-5. The
-    block sums add ~1e-7 of G (truncation of the float32 remainder sums).
-    Measured: at most 1.2e-6 (mean 1.3e-7), so the test holds it to 1e-5."""
+    Bound: each Phi value is represented within 2^-18 of its 4096-row block
+    bound B (integer + fp16 remainder split; B < 2 x the column's exact block
+    maximum), so |dG_ac| <= 2^-18 sum_i (B_a |Phi_ic| + B_c |Phi_ia|), i.e.
+    relative to |Phi_a| |Phi_c| at most 2^-18 (B_a sqrt(N)/|Phi_a| +
+    B_c sqrt(N)/|Phi_c|); with the columns' peak-to-RMS ratios below 10 here
+    that is 1.5e-4 in the worst case, and the rounding errors are random, so
+    the sums stay far below it. The float32 eigenfunction tables add ~1e-7.
+    Measured: at most 3.7e-7 over every entry against the float64 Gram of the
+    same rows (1.2e-6 with the earlier, looser block bound); the test holds
+    the samples to 1e-5."""
     pr = W.workload3()
     M = pr.n ** 3
     G, b = _lib.gram(pr.X, pr.y, pr.n, pr.eps, pr.alpha, prec="mixed")
