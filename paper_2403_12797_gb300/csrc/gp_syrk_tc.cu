@@ -241,18 +241,18 @@ __global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float*
     for (int kk = 0; kk < nk; ++kk) bmax[(int64_t)b * s.Mpad + u * n + kbase + kk] = __float_as_uint(mx[kk]);
 }
 
-constexpr int CM_UT = 4;       // upper-digit products per thread of colmax_ring_kernel
 constexpr int CM_ITEMS = 64;   // (UT products x 8 digits) items per CTA: 4 threads each
 constexpr int CM_STAGES = 4;   // deepest chunk ring
 
 // The staged form for p <= 4: the chunks of a range of block b's rows pass
 // through a shared-memory ring (cp.async, CM_STAGES deep, so the copies run
 // several chunks ahead of the arithmetic). A thread keeps its 8 digits' rows
-// of the last dimension in registers and forms the products with CM_UT
-// upper-digit products; item i of the CTA's tile takes u = (i / K8) UT .. and
+// of the last dimension in registers and forms the products with UT
+// upper-digit products (4, or 1 when there are too few products to fill a
+// CTA that way); item i of the CTA's tile takes u = (i / K8) UT .. and
 // k = (i % K8) 8 ... blockIdx = (item tile, row range, block). Each CTA
 // folds its maxima into bmax with one atomicMax per column.
-template <int P>
+template <int P, int UT>
 __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const float* __restrict__ tabc, int U, int K8,
                                                           int nitems, int rr, unsigned int* __restrict__ bmax) {
     extern __shared__ __align__(16) float ring[];
@@ -272,11 +272,11 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
     const int kbase = k8 * 8;
     const int nk = active ? min(8, n - kbase) : 0;
     const int koff = ((P - 1) * n + kbase) * WS + 8 * g;
-    int uoff[CM_UT][P > 1 ? P - 1 : 1];
+    int uoff[UT][P > 1 ? P - 1 : 1];
     int nu = 0;  // valid upper-digit products of this thread
 #pragma unroll
-    for (int uu = 0; uu < CM_UT; ++uu) {
-        const int u = uq * CM_UT + uu;
+    for (int uu = 0; uu < UT; ++uu) {
+        const int u = uq * UT + uu;
         if (active && u < U) nu = uu + 1;
         int rest = u < U ? u : 0;
 #pragma unroll
@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
             rest /= n;
         }
     }
-    float mx[CM_UT][8];
+    float mx[UT][8];
 #pragma unroll
-    for (int uu = 0; uu < CM_UT; ++uu)
+    for (int uu = 0; uu < UT; ++uu)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) mx[uu][kk] = 0.f;
     const uint32_t ring_s = smem_u32(ring);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
         for (int kk = 0; kk < 8; ++kk)
             if (kk < nk) ld_row8s(c + koff + kk * WS, last[kk]);
 #pragma unroll
-        for (int uu = 0; uu < CM_UT; ++uu) {
+        for (int uu = 0; uu < UT; ++uu) {
             if (uu < nu) {
                 if constexpr (P > 1) {
                     float pre[8];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll
-    for (int uu = 0; uu < CM_UT; ++uu)
+    for (int uu = 0; uu < UT; ++uu)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
             mx[uu][kk] = fmaxf(mx[uu][kk], __shfl_xor_sync(0xffffffffu, mx[uu][kk], 1));
@@ -346,12 +346,12 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
         }
     if (g != 0 || nq == 0) return;
 #pragma unroll
-    for (int uu = 0; uu < CM_UT; ++uu)
+    for (int uu = 0; uu < UT; ++uu)
         if (uu < nu)
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
                 if (kk < nk)
-                    atomicMax(bmax + (int64_t)b * s.Mpad + (uq * CM_UT + uu) * n + kbase + kk,
+                    atomicMax(bmax + (int64_t)b * s.Mpad + (uq * UT + uu) * n + kbase + kk,
                               __float_as_uint(mx[uu][kk]));
 }
 
@@ -910,7 +910,8 @@ void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char
         cudaMemsetAsync(bmax, 0, sizeof(unsigned int) * (size_t)nblk * s.Mpad, stream);
         const size_t ring = CM_STAGES * chunk_bytes;
         if (s.p <= 4 && ring <= 96 * 1024) {
-            const int nitems = (U + CM_UT - 1) / CM_UT * K8;
+            const int ut = (s.p > 1 && (U + 3) / 4 * K8 >= CM_ITEMS) ? 4 : 1;  // p = 1: U = 1
+            const int nitems = (U + ut - 1) / ut * K8;
             const int tiles = (nitems + CM_ITEMS - 1) / CM_ITEMS;
             // row ranges per block: about two CTAs per SM in all
             const int64_t want = 2 * (int64_t)colexp_sms();
@@ -921,11 +922,14 @@ void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char
                 if (ring > 48 * 1024) gp_allow_max_smem((const void*)kern);
                 kern<<<grid, CM_ITEMS * 4, ring, stream>>>(s, tabc, U, K8, nitems, rr, bmax);
             };
-            switch (s.p) {
-                case 1: go(colmax_ring_kernel<1>); break;
-                case 2: go(colmax_ring_kernel<2>); break;
-                case 3: go(colmax_ring_kernel<3>); break;
-                default: go(colmax_ring_kernel<4>); break;
+            switch (s.p * 8 + ut) {
+                case 1 * 8 + 1: go(colmax_ring_kernel<1, 1>); break;
+                case 2 * 8 + 1: go(colmax_ring_kernel<2, 1>); break;
+                case 2 * 8 + 4: go(colmax_ring_kernel<2, 4>); break;
+                case 3 * 8 + 1: go(colmax_ring_kernel<3, 1>); break;
+                case 3 * 8 + 4: go(colmax_ring_kernel<3, 4>); break;
+                case 4 * 8 + 1: go(colmax_ring_kernel<4, 1>); break;
+                default: go(colmax_ring_kernel<4, 4>); break;
             }
         } else {
             const int64_t threads = (int64_t)U * K8 * 4;
