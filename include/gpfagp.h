@@ -469,7 +469,21 @@ GPFAGP_API void gp_debug_barrier_timeout(double limit_s, int skip_cta);
  * GP_OK, or GP_EINVAL for T < 1, Npad < 1, target_ctas < 1 or out NULL. */
 GPFAGP_API int gp_debug_gram_splits(int T, int64_t Npad, int target_ctas, int64_t* out);
 
-/* Library build tag (static string). */
+/* Test hook: the mixed Gram's column exponents for the rows X (N x p,
+ * row-major float64, host) and the hyperparameters (n, eps, alpha), as the
+ * fits form them: for every 1024-row block b (rows padded to a multiple of
+ * 128 are zero) and column m < M = n^p, ebx[b * M + m] = E, where the exact
+ * maximum of |Phi[i, m]| over the block's rows (Eq. 19, float32 tables)
+ * times (1 + 2^-20) lies in [2^(E-1), 2^E), except that E is at least -100
+ * (a column that is zero in the block, or below 2^-101 there, gets -100). ebx4[b * M + m]: the largest E of each
+ * 4096-row block (the CTA-pair kernel's); colexp[m]: the largest E over all
+ * blocks. ebx holds ceil(Npad / 1024) x M bytes, ebx4 ceil(Npad / 4096) x M,
+ * colexp M ints (Npad = N rounded up to 128); all are host memory owned by
+ * the caller. Returns GP_OK, GP_EINVAL for bad arguments, or a CUDA error. */
+GPFAGP_API int gp_debug_column_exponents(const double* X, int64_t N, int p, int n, double eps, double alpha,
+                                         signed char* ebx, signed char* ebx4, int* colexp);
+
+/* Library build tag (static string). *//* Library build tag (static string). */
 GPFAGP_API const char* gp_version(void);
 
 /* ---- measurement hooks ------------------------------------------------------ */

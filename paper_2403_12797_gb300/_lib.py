@@ -107,6 +107,7 @@ def lib(build: bool = True) -> C.CDLL:
         "gp_debug_barrier_timeout": (None, [d, i]),
         "gp_debug_gram_kernel": (None, [i]),
         "gp_debug_gram_splits": (i, [i, i64, i, C.POINTER(i64)]),
+        "gp_debug_column_exponents": (i, [vp, i64, i, i, d, d, vp, vp, vp]),
         "gp_model_flags": (i, [vp]),
         "gp_version": (C.c_char_p, []),
     }
@@ -489,6 +490,25 @@ def debug_gram_splits(T: int, Npad: int, target_ctas: int):
     out = (C.c_int64 * 7)()
     _check(lib().gp_debug_gram_splits(int(T), int(Npad), int(target_ctas), out), "gp_debug_gram_splits")
     return list(out[0:3]), list(out[3:6]), int(out[6])
+
+
+def debug_column_exponents(X, n: int, eps: float, alpha: float):
+    """The mixed Gram's column exponents for host rows X (N x p): (E per
+    1024-row block [blocks, M], the largest per 4096-row block [blocks4, M],
+    the largest overall [M]), int arrays."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    N, p = X.shape
+    M = int(n) ** p
+    npad = -(-N // 128) * 128
+    ebx = np.empty((-(-npad // 1024), M), dtype=np.int8)
+    ebx4 = np.empty((-(-npad // 4096), M), dtype=np.int8)
+    ce = np.empty(M, dtype=np.int32)
+    _check(lib().gp_debug_column_exponents(X.ctypes.data, N, p, int(n), float(eps), float(alpha),
+                                           ebx.ctypes.data, ebx4.ctypes.data, ce.ctypes.data),
+           "gp_debug_column_exponents")
+    return ebx.astype(np.int64), ebx4.astype(np.int64), ce.astype(np.int64)
 
 
 def debug_force_escalation(k: int):

@@ -1270,6 +1270,46 @@ GPFAGP_API int gp_debug_gram_splits(int T, int64_t Npad, int target_ctas, int64_
     return GP_OK;
 }
 
+GPFAGP_API int gp_debug_column_exponents(const double* X, int64_t N, int p, int n, double eps, double alpha,
+                                         signed char* ebx, signed char* ebx4, int* colexp) {
+    set_err(GP_OK);
+    int rc, dev;
+    if (!X || !ebx || !ebx4 || !colexp) return set_err(GP_EINVAL, 0);
+    if ((rc = check_hyper(N, p, n, eps, alpha, 1.0))) return rc;
+    if ((rc = check_device(&dev))) return rc;
+    GpShape s;
+    gp_fill_shape(&s, N, p, n, eps, alpha, SYRKTC_TM);
+    cudaStream_t stream = 0;
+    Scratch sc(stream);
+    GpStatus* st;
+    double* xd;
+    float* tabc;
+    int* ce;
+    signed char* eb;
+    if ((rc = sc.get(&st, 1))) return rc;
+    if ((rc = sc.get(&xd, (size_t)N * p))) return rc;
+    if ((rc = sc.get(&tabc, syrktc_table_floats(s)))) return rc;
+    if ((rc = sc.get(&ce, (size_t)s.Mpad))) return rc;
+    if ((rc = sc.get(&eb, syrktc_ebx_bytes(s)))) return rc;
+    cudaMemsetAsync(st, 0, sizeof(GpStatus), stream);
+    cudaMemcpyAsync(xd, X, sizeof(double) * N * p, cudaMemcpyHostToDevice, stream);
+    launch_eig_tables_chunked(s, xd, nullptr, tabc, st, stream);
+    launch_colexp(s, tabc, ce, eb, stream);
+    const int64_t nblk = (s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK, nblk4 = (s.Npad + GP_PAIR_BLOCK - 1) / GP_PAIR_BLOCK;
+    std::vector<signed char> h1((size_t)nblk * s.Mpad), h4((size_t)nblk4 * s.Mpad);
+    std::vector<int> hc(s.Mpad);
+    cudaMemcpyAsync(h1.data(), eb, h1.size(), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(h4.data(), syrktc_pair_exponents(s, eb), h4.size(), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(hc.data(), ce, sizeof(int) * s.Mpad, cudaMemcpyDeviceToHost, stream);
+    if ((rc = read_status(st, stream))) return rc;  // synchronises the stream
+    for (int64_t b = 0; b < nblk; ++b)
+        for (int m = 0; m < s.M; ++m) ebx[b * s.M + m] = h1[(size_t)b * s.Mpad + m];
+    for (int64_t b = 0; b < nblk4; ++b)
+        for (int m = 0; m < s.M; ++m) ebx4[b * s.M + m] = h4[(size_t)b * s.Mpad + m];
+    for (int m = 0; m < s.M; ++m) colexp[m] = hc[m];
+    return GP_OK;
+}
+
 GPFAGP_API int gp_model_flags(const gp_model* h) { return h ? h->flags : 0; }
 
 GPFAGP_API int gp_gram_ex(const double* X, const double* y, int64_t N, int p, int n, double eps,
