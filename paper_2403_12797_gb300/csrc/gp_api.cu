@@ -340,7 +340,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         constexpr int TT = 256;
         float* tabc;
         double* Gpart2;
-        double* bpart;
+        float* bblk = nullptr;  // b's partials per block and row range (the exponent pass forms b)
         if ((rc = sc.get(&tabc, syrktc_table_floats(sg)))) return rc;
         const int T = sg.Mpad / TT;
         const int npairs = T * (T + 1) / 2;
@@ -349,7 +349,7 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         if (target_ctas > 0) clusters = std::max(1, std::min(clusters, target_ctas / 2));
         choose_splits_tc(T, sg.Npad, clusters, &spl, kClassCost2, 16, GP_PAIR_BLOCK);
         if ((rc = sc.get(&Gpart2, (size_t)spl.smax * npairs * TT * TT))) return rc;
-        if ((rc = sc.get(&bpart, (size_t)spl.smax * sg.Mpad))) return rc;
+        if (b != nullptr && (rc = sc.get(&bblk, colexp_b_floats(sg)))) return rc;
         int* colexp;
         signed char* ebx;
         if ((rc = sc.get(&colexp, (size_t)sg.Mpad))) return rc;
@@ -361,18 +361,18 @@ int gram_device(const GpShape& s, int prec, int dev, const double* Xd, const dou
         }
         {
             GpProf pf("colexp", stream);
-            launch_colexp(sg, tabc, colexp, ebx, stream);
-            gp_note_launches(2);
+            launch_colexp(sg, tabc, colexp, ebx, stream, bblk, b);
+            gp_note_launches(b != nullptr ? 3 : 2);
         }
         {
             GpProf pf("syrk_tc", stream);
-            cudaError_t e = launch_syrk_tc2(sg, tabc, spl, Gpart2, bpart, colexp, ebx, st, stream);
+            cudaError_t e = launch_syrk_tc2(sg, tabc, spl, Gpart2, colexp, ebx, st, stream);
             if (e != cudaSuccess) return cuda_err(e, "syrk_tc2 launch");
             gp_note_launches(1);
         }
         {
             GpProf pf("assemble", stream);
-            launch_assemble_pair(Gpart2, bpart, colexp, spl, sg.Mpad, s.M, d, A, b, stream, ex);
+            launch_assemble_pair(Gpart2, nullptr, colexp, spl, sg.Mpad, s.M, d, A, b, stream, ex);
             gp_note_launches(1);
             if (ex != nullptr && ex->L != nullptr && l_written) *l_written = true;
         }

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(1024) assemble_scaled_kernel(const void* __res
             A[(int64_t)(r0 + rr) * M + c0 + tx] = t[tx][rr];
         }
     }
-    if (bi == bj && threadIdx.x < B) {
+    if (bpart != nullptr && bi == bj && threadIdx.x < B) {  // (the CTA-pair path forms b elsewhere)
         const int col = c0 + threadIdx.x;
         if (col < M) {
             double bb = 0.0;

@@ -88,8 +88,13 @@ cudaError_t launch_syrk_tc_batch(const SyrkBatchProb* probs, int nprob, int64_t 
 // (the exact maximum of |Phi[:, m]| over the block's rows is below 2^E_m),
 // then the largest E_m of each GP_PAIR_BLOCK-row block at
 // syrktc_pair_exponents(s, ebx), then the pass's scratch; colexp[m] = the
-// largest E_m over all blocks
-void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream);
+// largest E_m over all blocks. With bblk (colexp_b_floats(s) floats of
+// scratch) and b (M float64) it also forms b = Phi^T y from the same Phi
+// values: float32 partials per block and row range, summed in float64 in a
+// fixed order (bit-reproducible).
+void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream,
+                   float* bblk = nullptr, double* b = nullptr);
+size_t colexp_b_floats(const GpShape& s);
 const signed char* syrktc_pair_exponents(const GpShape& s, const signed char* ebx);
 
 // ---- split-N reduction and assembly (gp_assemble.cu) --------------------------
@@ -109,10 +114,11 @@ struct AssembleExtra {
 };
 // ---- the tensor-core Gram on CTA pairs (gp_syrk_tc2.cu) --------------------------
 // 256 x 256 tile pairs, one cluster of two CTAs each (tcgen05 cta_group::2); the
-// same arithmetic and outputs as launch_syrk_tc with tiles of 256: s.Mpad a
-// multiple of 256, SyrkSplit classes over the 256-column tiles, Gpart
-// (split * npairs + pair) x 256 x 256 float pairs. For p <= 4 when the
-// pipeline fits shared memory (syrktc2_supported).
+// same arithmetic as launch_syrk_tc with tiles of 256: s.Mpad a multiple of
+// 256, SyrkSplit classes over the 256-column tiles, Gpart (split * npairs +
+// pair) x 256 x 256 float64 partials. It forms G only: b = Phi^T y of its
+// fits comes from launch_colexp. For p <= 4 when the pipeline fits shared
+// memory (syrktc2_supported).
 bool syrktc2_supported(const GpShape& s);
 // Partial tiles of the CTA-pair kernel: float64, one 256 x 256 tile per (split,
 // pair) at (split * npairs + pair) * 65536, element (R, C) of the tile (R the
@@ -128,15 +134,16 @@ __host__ __device__ __forceinline__ int gp_pair_tile_offset(int R, int C) {
 }
 // clusters of the kernel that are resident at once on device dev
 int syrktc2_max_clusters(const GpShape& s, int dev);
-cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
-                            GpStatus* st, cudaStream_t stream);
+cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, int* colexp,
+                            signed char* ebx, GpStatus* st, cudaStream_t stream);
 
 // float-pair partials of the tensor-core Gram (tile x tile partial tiles, tile
 // 128 or 256): A[m][m'] = split sum * 2^(E_m + E_m' - 12) (+ d)
 void launch_assemble_scaled(const float2* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                             int tile, int Mpad, int M, const double* d, double* A, double* b,
                             cudaStream_t stream, const AssembleExtra* ex = nullptr);
-// the same from the CTA-pair kernel's float64 partial tiles (gp_pair_tile_offset)
+// the same from the CTA-pair kernel's float64 partial tiles (gp_pair_tile_offset); bpart NULL:
+// b is left alone (the CTA-pair path forms it in launch_colexp)
 void launch_assemble_pair(const double* Gpart, const double* bpart, const int* colexp, const SyrkSplit& sp,
                           int Mpad, int M, const double* d, double* A, double* b, cudaStream_t stream,
                           const AssembleExtra* ex = nullptr);

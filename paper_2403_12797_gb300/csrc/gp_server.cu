@@ -171,6 +171,7 @@ size_t refit_bytes(const gp_model* m, int64_t N, int sms) {
     b += M * M * 8 + solve_refine_work_elems((int)M) * 8 + factor_work_bytes((int)M, true);
     b += (size_t)s.p * s.n * Npad * 8 + Npad * 8;                 // tables, padded y
     b += (Npad / GP_TAB_BLOCK + 2) * (size_t)s.Mpad * 6 + (size_t)s.Mpad * 4;  // block maxima and exponents
+    b += (Npad / GP_TAB_BLOCK + 2 * (size_t)sms + 2) * (size_t)s.Mpad * 4;       // partials of b (bound)
     b += (size_t)(sms + 1) * 4 * (size_t)s.Mpad * s.Mpad * 4 / 2; // split partial tiles (bound)
     return b + (4 << 20);
 }

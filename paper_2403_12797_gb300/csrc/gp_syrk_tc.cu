@@ -180,10 +180,11 @@ __device__ __forceinline__ void mul_row8s(const float* p, float v[8]) {
 
 // One thread: one u, 8 consecutive k, rows 8g .. 8g + 7 of every 32-row
 // chunk of block b (g = lane & 3), table read through the read-only cache.
-// The general form (any p, any table size), one CTA column per block.
-template <int P>  // p (1..4), or 0: p at run time
+// The general form (any p, any table size), one CTA column per block. WB:
+// also the block's partials of b = Phi^T y (one row range: bblk[b * Mpad + m]).
+template <int P, bool WB>  // p (1..4), or 0: p at run time
 __global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float* __restrict__ tabc, int U, int K8,
-                                                         unsigned int* __restrict__ bmax) {
+                                                         unsigned int* __restrict__ bmax, float* __restrict__ bblk) {
     const int b = blockIdx.y;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = t & 3, item = t >> 2;
@@ -207,10 +208,14 @@ __global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float*
     const int kbase = k8 * 8;
     const int nk = min(8, n - kbase);
     const int koff = ((p - 1) * n + kbase) * WS + 8 * g;
+    const int yoff = p * n * WS + 8 * g;  // the chunk's y row
     float mx[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float bs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (active) {
         for (int64_t q = q0; q < q1; ++q) {
             const float* c = tabc + q * RC;
+            float yr[8];
+            if constexpr (WB) ld_row8g(c + yoff, yr);
             float pre[8];
             if (p > 1) {
                 ld_row8g(c + uoff[0], pre);
@@ -227,7 +232,11 @@ __global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float*
                     float v[8];
                     ld_row8g(c + koff + kk * WS, v);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) mx[kk] = fmaxf(mx[kk], fabsf(p > 1 ? pre[i] * v[i] : v[i]));
+                    for (int i = 0; i < 8; ++i) {
+                        const float x = p > 1 ? pre[i] * v[i] : v[i];
+                        mx[kk] = fmaxf(mx[kk], fabsf(x));
+                        if constexpr (WB) bs[kk] = fmaf(x, yr[i], bs[kk]);
+                    }
                 }
             }
         }
@@ -236,9 +245,16 @@ __global__ void __launch_bounds__(256) colmax_ldg_kernel(GpShape s, const float*
     for (int kk = 0; kk < 8; ++kk) {
         mx[kk] = fmaxf(mx[kk], __shfl_xor_sync(0xffffffffu, mx[kk], 1));
         mx[kk] = fmaxf(mx[kk], __shfl_xor_sync(0xffffffffu, mx[kk], 2));
+        if constexpr (WB) {
+            bs[kk] += __shfl_xor_sync(0xffffffffu, bs[kk], 1);
+            bs[kk] += __shfl_xor_sync(0xffffffffu, bs[kk], 2);
+        }
     }
     if (!active || g != 0) return;
-    for (int kk = 0; kk < nk; ++kk) bmax[(int64_t)b * s.Mpad + u * n + kbase + kk] = __float_as_uint(mx[kk]);
+    for (int kk = 0; kk < nk; ++kk) {
+        bmax[(int64_t)b * s.Mpad + u * n + kbase + kk] = __float_as_uint(mx[kk]);
+        if constexpr (WB) bblk[(int64_t)b * s.Mpad + u * n + kbase + kk] = bs[kk];
+    }
 }
 
 constexpr int CM_ITEMS = 64;   // (UT products x 8 digits) items per CTA: 4 threads each
@@ -246,15 +262,18 @@ constexpr int CM_STAGES = 4;   // deepest chunk ring
 
 // The staged form for p <= 4: the chunks of a range of block b's rows pass
 // through a shared-memory ring (cp.async, CM_STAGES deep, so the copies run
-// several chunks ahead of the arithmetic). A thread keeps its 8 digits' rows
-// of the last dimension in registers and forms the products with UT
-// upper-digit products (4, or 1 when there are too few products to fill a
-// CTA that way); item i of the CTA's tile takes u = (i / K8) UT .. and
-// k = (i % K8) 8 ... blockIdx = (item tile, row range, block). Each CTA
-// folds its maxima into bmax with one atomicMax per column.
-template <int P, int UT>
+// several chunks ahead of the arithmetic). A thread forms its UT upper-digit
+// products for its 8 rows once per chunk, then takes the last dimension's 8
+// digits one row at a time (UT = 4, 2 with b, or 1 when there are too few
+// products to fill a CTA that way); item i of the CTA's tile takes
+// u = (i / K8) UT .. and k = (i % K8) 8 ... blockIdx = (item tile, row range,
+// block). Each CTA folds its maxima into bmax with one atomicMax per column.
+// WB: also b = Phi^T y, one FMA a value with the chunk's y row, summed in
+// float32 over the CTA's rows and written per (block, row range) to bblk.
+template <int P, int UT, bool WB>
 __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const float* __restrict__ tabc, int U, int K8,
-                                                          int nitems, int rr, unsigned int* __restrict__ bmax) {
+                                                          int nitems, int rr, unsigned int* __restrict__ bmax,
+                                                          float* __restrict__ bblk) {
     extern __shared__ __align__(16) float ring[];
     const int n = s.n;
     const int rows = P * n + 1;
@@ -272,6 +291,7 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
     const int kbase = k8 * 8;
     const int nk = active ? min(8, n - kbase) : 0;
     const int koff = ((P - 1) * n + kbase) * WS + 8 * g;
+    const int yoff = P * n * WS + 8 * g;  // the chunk's y row
     int uoff[UT][P > 1 ? P - 1 : 1];
     int nu = 0;  // valid upper-digit products of this thread
 #pragma unroll
@@ -285,11 +305,11 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
             rest /= n;
         }
     }
-    float mx[UT][8];
+    float mx[UT][8], bs[UT][8];
 #pragma unroll
     for (int uu = 0; uu < UT; ++uu)
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mx[uu][kk] = 0.f;
+        for (int kk = 0; kk < 8; ++kk) mx[uu][kk] = bs[uu][kk] = 0.f;
     const uint32_t ring_s = smem_u32(ring);
     auto load = [&](int slot, int64_t q) {
         const float* src = tabc + q * (int64_t)cf;
@@ -309,29 +329,34 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
         if (i + CM_STAGES - 1 < nq) load((i + CM_STAGES - 1) % CM_STAGES, q0 + i + CM_STAGES - 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
         const float* c = ring + (i % CM_STAGES) * cf;
-        float last[8][8];
+        float pre[UT][8];
+        if constexpr (P > 1) {
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-            if (kk < nk) ld_row8s(c + koff + kk * WS, last[kk]);
+            for (int uu = 0; uu < UT; ++uu) {
+                if (uu < nu) {
+                    ld_row8s(c + uoff[uu][0], pre[uu]);
 #pragma unroll
-        for (int uu = 0; uu < UT; ++uu) {
-            if (uu < nu) {
-                if constexpr (P > 1) {
-                    float pre[8];
-                    ld_row8s(c + uoff[uu][0], pre);
+                    for (int j = 1; j < P - 1; ++j) mul_row8s(c + uoff[uu][j], pre[uu]);
+                }
+            }
+        }
+        float yr[8];
+        if constexpr (WB) ld_row8s(c + yoff, yr);
 #pragma unroll
-                    for (int j = 1; j < P - 1; ++j) mul_row8s(c + uoff[uu][j], pre);
+        for (int kk = 0; kk < 8; ++kk) {
+            if (kk < nk) {
+                float lr[8];
+                ld_row8s(c + koff + kk * WS, lr);
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        if (kk < nk)
+                for (int uu = 0; uu < UT; ++uu) {
+                    if (uu < nu) {
 #pragma unroll
-                            for (int r = 0; r < 8; ++r) mx[uu][kk] = fmaxf(mx[uu][kk], fabsf(pre[r] * last[kk][r]));
-                } else {
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        if (kk < nk)
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) mx[uu][kk] = fmaxf(mx[uu][kk], fabsf(last[kk][r]));
+                        for (int r = 0; r < 8; ++r) {
+                            const float x = P > 1 ? pre[uu][r] * lr[r] : lr[r];
+                            mx[uu][kk] = fmaxf(mx[uu][kk], fabsf(x));
+                            if constexpr (WB) bs[uu][kk] = fmaf(x, yr[r], bs[uu][kk]);
+                        }
+                    }
                 }
             }
         }
@@ -343,16 +368,37 @@ __global__ void __launch_bounds__(256, 2) colmax_ring_kernel(GpShape s, const fl
         for (int kk = 0; kk < 8; ++kk) {
             mx[uu][kk] = fmaxf(mx[uu][kk], __shfl_xor_sync(0xffffffffu, mx[uu][kk], 1));
             mx[uu][kk] = fmaxf(mx[uu][kk], __shfl_xor_sync(0xffffffffu, mx[uu][kk], 2));
+            if constexpr (WB) {
+                bs[uu][kk] += __shfl_xor_sync(0xffffffffu, bs[uu][kk], 1);
+                bs[uu][kk] += __shfl_xor_sync(0xffffffffu, bs[uu][kk], 2);
+            }
         }
-    if (g != 0 || nq == 0) return;
+    if (g != 0) return;
 #pragma unroll
     for (int uu = 0; uu < UT; ++uu)
         if (uu < nu)
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-                if (kk < nk)
-                    atomicMax(bmax + (int64_t)b * s.Mpad + (uq * UT + uu) * n + kbase + kk,
-                              __float_as_uint(mx[uu][kk]));
+                if (kk < nk) {
+                    const int m = (uq * UT + uu) * n + kbase + kk;
+                    if (nq > 0) atomicMax(bmax + (int64_t)b * s.Mpad + m, __float_as_uint(mx[uu][kk]));
+                    // every (block, row range) writes its partial, zero for an empty range
+                    if constexpr (WB) bblk[((int64_t)b * rr + blockIdx.y) * s.Mpad + m] = bs[uu][kk];
+                }
+}
+
+// b = Phi^T y from the partials: one warp per column, lanes over the
+// (block, row range) partials in a fixed order, a fixed shuffle tree.
+__global__ void __launch_bounds__(256) colb_kernel(GpShape s, int nparts, const float* __restrict__ bblk,
+                                                   double* __restrict__ b) {
+    const int m = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (m >= s.M) return;  // whole warps
+    double v = 0.0;
+    for (int q = lane; q < nparts; q += 32) v += (double)bblk[(int64_t)q * s.Mpad + m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) b[m] = v;
 }
 
 // ebx, the pair blocks' exponents ebx4 and colexp from bmax: one warp per
@@ -896,55 +942,104 @@ size_t ebx4_exp_bytes(const GpShape& s) {
 
 const signed char* syrktc_pair_exponents(const GpShape& s, const signed char* ebx) { return ebx + ebx_exp_bytes(s); }
 
+namespace {
+// The exponent pass's launch: staged (ring) or general, products per thread,
+// items, item tiles and row ranges per block. wb: b is formed too.
+struct ColPlan {
+    bool ring;
+    int U, K8, ut, nitems, tiles, rr;
+};
+ColPlan colexp_plan(const GpShape& s, bool wb) {
+    ColPlan c{};
+    c.U = 1;
+    for (int j = 0; j + 1 < s.p; ++j) c.U *= s.n;
+    c.K8 = (s.n + 7) / 8;
+    const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
+    const size_t chunk_bytes = (size_t)(s.p * s.n + 1) * WS * sizeof(float);
+    c.ring = s.p <= 4 && CM_STAGES * chunk_bytes <= 96 * 1024;
+    c.rr = 1;
+    if (!c.ring || nblk == 0) return c;
+    // four products a thread (two with b, for its accumulators' registers),
+    // or one when that would leave most of a CTA idle; p = 1 has U = 1
+    c.ut = (s.p > 1 && (c.U + 3) / 4 * c.K8 >= CM_ITEMS) ? (wb ? 2 : 4) : 1;
+    c.nitems = (c.U + c.ut - 1) / c.ut * c.K8;
+    c.tiles = (c.nitems + CM_ITEMS - 1) / CM_ITEMS;
+    // row ranges per block: about two CTAs per SM in all
+    const int64_t want = 2 * (int64_t)colexp_sms();
+    c.rr = (int)std::min<int64_t>(GP_TAB_BLOCK / CW,
+                                  std::max<int64_t>(1, (want + (int64_t)c.tiles * nblk - 1) / ((int64_t)c.tiles * nblk)));
+    return c;
+}
+}  // namespace
+
+size_t colexp_b_floats(const GpShape& s) {
+    const int64_t nblk = (s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK;
+    return (size_t)nblk * (size_t)colexp_plan(s, true).rr * (size_t)s.Mpad;
+}
+
 // the block maxima (float bits) follow both exponent arrays in the ebx buffer
-void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream) {
+void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream,
+                   float* bblk, double* b) {
+    const bool wb = bblk != nullptr && b != nullptr;
     const int nblk = (int)((s.Npad + GP_TAB_BLOCK - 1) / GP_TAB_BLOCK);
     const int nblk4 = (int)((s.Npad + GP_PAIR_BLOCK - 1) / GP_PAIR_BLOCK);
     signed char* ebx4 = ebx + ebx_exp_bytes(s);
     unsigned int* bmax = reinterpret_cast<unsigned int*>(ebx4 + ebx4_exp_bytes(s));
-    int U = 1;
-    for (int j = 0; j + 1 < s.p; ++j) U *= s.n;
-    const int K8 = (s.n + 7) / 8;
-    const size_t chunk_bytes = (size_t)(s.p * s.n + 1) * WS * sizeof(float);
+    const ColPlan c = colexp_plan(s, wb);
     if (nblk > 0) {
         cudaMemsetAsync(bmax, 0, sizeof(unsigned int) * (size_t)nblk * s.Mpad, stream);
-        const size_t ring = CM_STAGES * chunk_bytes;
-        if (s.p <= 4 && ring <= 96 * 1024) {
-            const int ut = (s.p > 1 && (U + 3) / 4 * K8 >= CM_ITEMS) ? 4 : 1;  // p = 1: U = 1
-            const int nitems = (U + ut - 1) / ut * K8;
-            const int tiles = (nitems + CM_ITEMS - 1) / CM_ITEMS;
-            // row ranges per block: about two CTAs per SM in all
-            const int64_t want = 2 * (int64_t)colexp_sms();
-            int rr = (int)std::min<int64_t>(GP_TAB_BLOCK / CW, std::max<int64_t>(1, (want + (int64_t)tiles * nblk - 1) /
-                                                                                      ((int64_t)tiles * nblk)));
-            const dim3 grid((unsigned)tiles, (unsigned)rr, (unsigned)nblk);
+        if (c.ring) {
+            const size_t ring = CM_STAGES * (size_t)(s.p * s.n + 1) * WS * sizeof(float);
+            const dim3 grid((unsigned)c.tiles, (unsigned)c.rr, (unsigned)nblk);
             auto go = [&](auto kern) {
                 if (ring > 48 * 1024) gp_allow_max_smem((const void*)kern);
-                kern<<<grid, CM_ITEMS * 4, ring, stream>>>(s, tabc, U, K8, nitems, rr, bmax);
+                kern<<<grid, CM_ITEMS * 4, ring, stream>>>(s, tabc, c.U, c.K8, c.nitems, c.rr, bmax, bblk);
             };
-            switch (s.p * 8 + ut) {
-                case 1 * 8 + 1: go(colmax_ring_kernel<1, 1>); break;
-                case 2 * 8 + 1: go(colmax_ring_kernel<2, 1>); break;
-                case 2 * 8 + 4: go(colmax_ring_kernel<2, 4>); break;
-                case 3 * 8 + 1: go(colmax_ring_kernel<3, 1>); break;
-                case 3 * 8 + 4: go(colmax_ring_kernel<3, 4>); break;
-                case 4 * 8 + 1: go(colmax_ring_kernel<4, 1>); break;
-                default: go(colmax_ring_kernel<4, 4>); break;
+            switch ((s.p * 8 + c.ut) * 2 + (wb ? 1 : 0)) {
+                case (1 * 8 + 1) * 2: go(colmax_ring_kernel<1, 1, false>); break;
+                case (1 * 8 + 1) * 2 + 1: go(colmax_ring_kernel<1, 1, true>); break;
+                case (2 * 8 + 1) * 2: go(colmax_ring_kernel<2, 1, false>); break;
+                case (2 * 8 + 1) * 2 + 1: go(colmax_ring_kernel<2, 1, true>); break;
+                case (2 * 8 + 2) * 2 + 1: go(colmax_ring_kernel<2, 2, true>); break;
+                case (2 * 8 + 4) * 2: go(colmax_ring_kernel<2, 4, false>); break;
+                case (3 * 8 + 1) * 2: go(colmax_ring_kernel<3, 1, false>); break;
+                case (3 * 8 + 1) * 2 + 1: go(colmax_ring_kernel<3, 1, true>); break;
+                case (3 * 8 + 2) * 2 + 1: go(colmax_ring_kernel<3, 2, true>); break;
+                case (3 * 8 + 4) * 2: go(colmax_ring_kernel<3, 4, false>); break;
+                case (4 * 8 + 1) * 2: go(colmax_ring_kernel<4, 1, false>); break;
+                case (4 * 8 + 1) * 2 + 1: go(colmax_ring_kernel<4, 1, true>); break;
+                case (4 * 8 + 2) * 2 + 1: go(colmax_ring_kernel<4, 2, true>); break;
+                default: go(colmax_ring_kernel<4, 4, false>); break;
             }
         } else {
-            const int64_t threads = (int64_t)U * K8 * 4;
+            const int64_t threads = (int64_t)c.U * c.K8 * 4;
             const dim3 g2((unsigned)((threads + 255) / 256), (unsigned)nblk);
-            switch (s.p) {
-                case 1: colmax_ldg_kernel<1><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
-                case 2: colmax_ldg_kernel<2><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
-                case 3: colmax_ldg_kernel<3><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
-                case 4: colmax_ldg_kernel<4><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
-                default: colmax_ldg_kernel<0><<<g2, 256, 0, stream>>>(s, tabc, U, K8, bmax); break;
+            auto go = [&](auto kern) { kern<<<g2, 256, 0, stream>>>(s, tabc, c.U, c.K8, bmax, bblk); };
+            switch (s.p * 2 + (wb ? 1 : 0)) {
+                case 1 * 2: go(colmax_ldg_kernel<1, false>); break;
+                case 1 * 2 + 1: go(colmax_ldg_kernel<1, true>); break;
+                case 2 * 2: go(colmax_ldg_kernel<2, false>); break;
+                case 2 * 2 + 1: go(colmax_ldg_kernel<2, true>); break;
+                case 3 * 2: go(colmax_ldg_kernel<3, false>); break;
+                case 3 * 2 + 1: go(colmax_ldg_kernel<3, true>); break;
+                case 4 * 2: go(colmax_ldg_kernel<4, false>); break;
+                case 4 * 2 + 1: go(colmax_ldg_kernel<4, true>); break;
+                default:
+                    if (wb) go(colmax_ldg_kernel<0, true>);
+                    else go(colmax_ldg_kernel<0, false>);
+                    break;
             }
         }
     }
     const int64_t warps = s.Mpad;
     colexp_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(s, nblk, nblk4, bmax, ebx, ebx4, colexp);
+    if (wb) {
+        if (nblk > 0) {
+            colb_kernel<<<(unsigned)(((int64_t)s.M * 32 + 255) / 256), 256, 0, stream>>>(s, nblk * c.rr, bblk, b);
+        } else {
+            cudaMemsetAsync(b, 0, sizeof(double) * s.M, stream);
+        }
+    }
 }
 
 size_t syrktc_smem_bytes(const GpShape& s) {

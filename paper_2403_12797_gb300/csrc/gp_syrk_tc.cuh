@@ -116,6 +116,3 @@ __device__ __forceinline__ void split8(const float v[8], float sc, uint32_t h[4]
 
 }  // namespace gpsyrk
 
-// column exponents of the mixed Gram (gp_syrk_tc.cu): ebx[b * Mpad + m] = E_m of
-// GP_TAB_BLOCK-row block b, colexp[m] = the largest E_m over the blocks
-void launch_colexp(const GpShape& s, const float* tabc, int* colexp, signed char* ebx, cudaStream_t stream);

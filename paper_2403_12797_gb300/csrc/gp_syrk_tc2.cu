@@ -1,8 +1,11 @@
 // gp_syrk_tc2.cu -- fused Phi generation + tensor-core Gram on CTA pairs
 // (tcgen05 cta_group::2, 256 x 256 tile pairs).
 //
-// Computes G = Phi^T Phi and b = Phi^T y (the products of Lambda-bar and of W
-// in Sec. 2.2; Phi of Eq. 19) with the arithmetic of gp_syrk_tc.cu: per
+// Computes G = Phi^T Phi (the product of Lambda-bar in Sec. 2.2; Phi of
+// Eq. 19) with the arithmetic of gp_syrk_tc.cu; b = Phi^T y of these fits is
+// formed by the exponent pass (launch_colexp) from the same Phi values, which
+// keeps the producers within their 96 registers (accumulating b here made
+// them spill and cost 4 % of the kernel's time). Per
 // GP_PAIR_BLOCK-row block each column is scaled by 2^(6 - E_m) (|w| < 64) and split
 // into the integer s1 = rint(w) and the fp16 remainder lo; s1 s1' is summed
 // exactly in float32 TMEM, s1 lo' + lo s1' + lo lo' beside it; each block's
@@ -44,8 +47,8 @@
 //
 // Roles (576 threads per CTA, one CTA per SM):
 //   warps 0-15  producers: generation (warps 0-7 the A half, 8-15 the B
-//               half; a diagonal pair's B half is its A half), b = Phi^T y on
-//               the pairs (I2, 0), and the per-block drain of TMEM;
+//               half; a diagonal pair's B half is its A half) and the
+//               per-block drain of TMEM;
 //   warp 16     TMEM allocation (both CTAs); in the leader, one lane issues
 //               the pair's MMAs and commits them to both CTAs' barriers;
 //   warp 17     bulk (TMA) copies of this CTA's table windows, and each
@@ -76,7 +79,6 @@ constexpr int TILE = TM * KS * 2;         // bytes of one 16-bit operand tile
 constexpr int SBYTES = 4 * TILE;          // A s1, A lo, B s1, B lo
 constexpr uint32_t SBO = (KS / 8) * 128;  // 8-row core-matrix groups
 constexpr int BLOCK = GP_PAIR_BLOCK / KS;  // stages per exact GP_PAIR_BLOCK-row block
-constexpr int BFOLD = 512 / KS;           // stages between float64 folds of b
 constexpr int STAGES = 3;                 // deepest operand pipeline
 constexpr int WRMAX = 8;                  // deepest window ring
 constexpr int NPROD = 512;                // 16 producer warps
@@ -95,8 +97,6 @@ struct Smem2 {
     unsigned short* crI;  // TM x p: window row of (column, dimension), A half
     unsigned short* crJ;  // TM x p: B half
     int* rng;             // copy ranges (table row, rows, window row)
-    double* bred;         // TM: b of the second row-group half (cross-warp sum)
-    double* bsum;         // 256 x 4: float64 sums of b per A-half producer thread and column
     float* msc;           // 2 x (TP + TM): per block (double-buffered by parity), the
                           // B columns' and A-half rows' scales 2^(E_blk - E_glob), from the loader
     uint64_t* full;       // STAGES: leader's, one arrival per producer warp of both CTAs
@@ -124,8 +124,6 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
     size_t oCI = take(sizeof(unsigned short) * TM * p, 16);
     size_t oCJ = take(sizeof(unsigned short) * TM * p, 16);
     size_t oR = take(sizeof(int) * 3 * max_ranges(p), 16);
-    size_t oB = take(sizeof(double) * TM, 16);
-    size_t oBS = take(sizeof(double) * 256 * 4, 16);
     size_t oMS = take(sizeof(float) * 2 * (TP + TM), 16);
     size_t oF = take(sizeof(uint64_t) * STAGES, 8);
     size_t oE = take(sizeof(uint64_t) * STAGES, 8);
@@ -143,8 +141,6 @@ __host__ __device__ inline size_t smem_tc2_layout(int maxrows, int p, int nst, i
         L->crI = (unsigned short*)(base + oCI);
         L->crJ = (unsigned short*)(base + oCJ);
         L->rng = (int*)(base + oR);
-        L->bred = (double*)(base + oB);
-        L->bsum = (double*)(base + oBS);
         L->msc = (float*)(base + oMS);
         L->full = (uint64_t*)(base + oF);
         L->empty = (uint64_t*)(base + oE);
@@ -175,7 +171,7 @@ template <int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc2_kernel(GpShape s, const float* __restrict__ tabc, const signed char* __restrict__ ebx,
                     const int* __restrict__ colexp, SyrkSplit sp, int T, int maxrows, int nst, int nwr,
-                    double* __restrict__ Gpart, double* __restrict__ bpart, GpStatus* st) {
+                    double* __restrict__ Gpart, GpStatus* st) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ TileWindow wI, wJ;
     __shared__ int s_nrng;
@@ -278,7 +274,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int kq = (wl & 3) * 8 + (lane & 7);    // column quad of the tile (0..31)
         const int rot = (lane & 7) >> 1;
         const bool gen = !(diag && tsel == 1);
-        const bool with_b = (J2 == 0) && tsel == 0;
         const unsigned short* cr = tsel ? sm.crJ : sm.crI;
         // the tile column visited at step k (the rotation keeps a quarter-warp's
         // stores on 8 different core-matrix rows)
@@ -317,14 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int k = 0; k < 4; ++k)
             so[k] = (uint32_t)(colk(k) >> 3) * SBO + (uint32_t)g8 * LBO + (uint32_t)(colk(k) & 7) * 16;
         const int twin = (tsel == 1 && !diag) ? nrowsI * WS : 0;  // this tile's window in the chunk window
-        const int ywin = (nwin - 1) * WS;
         const int mtile = (tsel ? J : I) * TM;
-        float bacc[4] = {0.f, 0.f, 0.f, 0.f};
-        double* bsum = sm.bsum + 4 * (tid & 255);  // this thread's float64 sums of b (A half only)
-        if (with_b) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) bsum[k] = 0.0;
-        }
         // drain: TMEM lanes 32 quarter .. (A-half rows), columns CPT cgrp ..
         const int quarter = warp & 3, cgrp = warp >> 2;
         const int drow = quarter * 32 + lane;
@@ -445,13 +433,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = false;
                 break;
             }
-            if (with_b && c % BFOLD == 0 && c > 0) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    bsum[k] += (double)bacc[k];
-                    bacc[k] = 0.f;
-                }
-            }
             if (c % BLOCK == 0) {
                 // a new block: quantisation scales 2^(6 - E_blk)
 #pragma unroll
@@ -466,8 +447,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t sb = stage_s + (uint32_t)(stg * SBYTES);
                 const uint32_t wb = win_s + 4u * (uint32_t)(wsl * wsz);
                 const uint32_t wt = wb + 4u * (uint32_t)twin;
-                float yv[8];
-                if (with_b) lds_row8(wb + 4u * (uint32_t)ywin, yv);
                 if (P >= 2 && shared) {
                     // the upper dimensions' product once, then one row and one multiply a column
                     float pre[8];
@@ -489,10 +468,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         split8(v, sc[k], h, l);
                         sts128(sb + so[k], h[0], h[1], h[2], h[3]);
                         sts128(sb + TILE + so[k], l[0], l[1], l[2], l[3]);
-                        if (with_b) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) bacc[k] = fmaf(v[i], yv[i], bacc[k]);
-                        }
                     }
                 } else {
 #pragma unroll
@@ -515,10 +490,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         split8(v, sc[k], h, l);
                         sts128(sb + so[k], h[0], h[1], h[2], h[3]);
                         sts128(sb + TILE + so[k], l[0], l[1], l[2], l[3]);
-                        if (with_b) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) bacc[k] = fmaf(v[i], yv[i], bacc[k]);
-                        }
                     }
                 }
             }
@@ -551,27 +522,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         while (ok && next_drain < nblocks) {
             if (!drain(next_drain)) ok = false;
             ++next_drain;
-        }
-        if (J2 == 0 && tsel == 0) {
-            // b of this CTA's 128 columns: the 8 row groups of a column are 4
-            // lanes (8 apart) of two warps (wl and wl + 4)
-            double v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = (nchunks > 0 ? bsum[k] : 0.0) + (double)bacc[k];
-                v[k] += __shfl_xor_sync(FULLMASK, v[k], 8);
-                v[k] += __shfl_xor_sync(FULLMASK, v[k], 16);
-            }
-            if (wl >= 4 && lane < 8) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) sm.bred[colk(k)] = v[k];
-            }
-            named_bar_sync(1, 256);
-            if (wl < 4 && lane < 8) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    bpart[(int64_t)split * s.Mpad + I * TM + colk(k)] = v[k] + sm.bred[colk(k)];
-            }
         }
         if (nblocks == 0) {  // a split without rows: its partial tile is zero
             for (int k = lane; k < (CPT / 16) * 512 / 4; k += 32)
@@ -709,7 +659,7 @@ int syrk_tc2_stages(const GpShape& s, int maxrows, int* nwr, size_t* smem) {
 
 template <int P>
 cudaError_t go2(const GpShape& s, const float* tabc, const signed char* ebx, const int* colexp, const SyrkSplit& sp,
-                int T, int maxrows, int nst, int nwr, size_t smem, double* Gpart, double* bpart, GpStatus* st,
+                int T, int maxrows, int nst, int nwr, size_t smem, double* Gpart, GpStatus* st,
                 cudaStream_t stream) {
     const void* kern = (const void*)syrk_tc2_kernel<P>;
     cudaError_t e = gp_allow_max_smem(kern);
@@ -727,8 +677,7 @@ cudaError_t go2(const GpShape& s, const float* tabc, const signed char* ebx, con
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, syrk_tc2_kernel<P>, s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, Gpart,
-                              bpart, st);
+    return cudaLaunchKernelEx(&cfg, syrk_tc2_kernel<P>, s, tabc, ebx, colexp, sp, T, maxrows, nst, nwr, Gpart, st);
 }
 
 }  // namespace
@@ -788,7 +737,7 @@ int syrktc2_max_clusters(const GpShape& s, int dev) {
     return n;
 }
 
-cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, double* bpart, int* colexp, signed char* ebx,
+cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit& sp, double* Gpart, int* colexp, signed char* ebx,
                             GpStatus* st, cudaStream_t stream) {
     if (!syrktc2_supported(s)) return cudaErrorInvalidValue;
     for (int c = 0; c < 3; ++c)
@@ -801,9 +750,9 @@ cudaError_t launch_syrk_tc2(const GpShape& s, const float* tabc, const SyrkSplit
     const int nst = syrk_tc2_stages(s, maxrows, &nwr, &smem);
     const int T = s.Mpad / TP;
     switch (s.p) {
-        case 1: return go2<1>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        case 2: return go2<2>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        case 3: return go2<3>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
-        default: return go2<4>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, bpart, st, stream);
+        case 1: return go2<1>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, st, stream);
+        case 2: return go2<2>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, st, stream);
+        case 3: return go2<3>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, st, stream);
+        default: return go2<4>(s, tabc, ebx4, colexp, sp, T, maxrows, nst, nwr, smem, Gpart, st, stream);
     }
 }
