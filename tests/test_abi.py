@@ -98,6 +98,24 @@ def test_fit_predict_python_rejects_mismatched_inputs():
         _lib.fit_predict(np.zeros((4, 2)), np.zeros(4), 3, 1.0, 1.0, 0.1, np.zeros((2, 3)))
 
 
+@pytest.mark.parametrize("kw", [dict(N=0), dict(p=0), dict(n=0), dict(eps=0.0), dict(alpha=-1.0),
+                                dict(null="X"), dict(null="ebx"), dict(null="ebx4"), dict(null="colexp")])
+def test_column_exponents_arguments_rejected_on_host(kw):
+    # argument checks come before any device work, so these run without a GPU
+    a = dict(N=16, p=2, n=3, eps=1.0, alpha=1.0)
+    a.update({k: v for k, v in kw.items() if k != "null"})
+    X = np.zeros((16, 2))
+    ebx = np.zeros(64, dtype=np.int8)
+    ebx4 = np.zeros(64, dtype=np.int8)
+    ce = np.zeros(16, dtype=np.int32)
+    ptr = {"X": X.ctypes.data, "ebx": ebx.ctypes.data, "ebx4": ebx4.ctypes.data, "colexp": ce.ctypes.data}
+    if "null" in kw:
+        ptr[kw["null"]] = None
+    rc = _lib.lib().gp_debug_column_exponents(ptr["X"], a["N"], a["p"], a["n"], a["eps"], a["alpha"],
+                                              ptr["ebx"], ptr["ebx4"], ptr["colexp"])
+    assert rc == _lib.GP_EINVAL
+
+
 # ---- the mixed Gram's row-split plan (host logic, no GPU)
 
 _W = (1.0, 1.24, 1.17)  # per-block costs of the pair classes the planner uses
