@@ -51,9 +51,11 @@ constexpr int NTHREADS = NPROD + 64;         // + warp 9: loader
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 // Stage: [A hi | A lo | W blocks (hi, lo) x SUPER | window (maxrows + 1 rows
-// of TT floats; the last row is zero) | column map (crp4 ints)], 1 KB aligned.
+// of TT floats; the last row is zero) | column map (crp4 ints) | the chunk's
+// BK float32 coefficients of c (the last super-tile's chunks, which form the
+// mean)], 1 KB aligned.
 __host__ __device__ inline uint32_t stage_bytes(int maxrows, int crp4) {
-    const uint32_t end = WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4 + (uint32_t)crp4 * 4;
+    const uint32_t end = WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4 + (uint32_t)crp4 * 4 + BK * 4;
     return (end + 1023u) & ~1023u;
 }
 __host__ __device__ inline uint32_t map_off(int maxrows) { return WIN_OFF + (uint32_t)(maxrows + 1) * TT * 4; }
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // the stage layout is sized for the largest window and map of the launch
     const uint32_t SB = stage_bytes(maxrows_all, crp4_all);
     const uint32_t MAPO = map_off(maxrows_all);
+    const uint32_t CFO = MAPO + (uint32_t)crp4_all * 4;  // the chunk's coefficients of c (16-byte aligned)
     uint8_t* stage = (uint8_t*)base;
     uint64_t* full = (uint64_t*)(base + (size_t)STAGES * SB);
     uint64_t* wfull = full + STAGES;
@@ -184,7 +187,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int nblocks = (M + KB - 1) / KB;  // blocks of W rows with k < M
             const int nsuper = (nblocks + SUPER - 1) / SUPER;
             const int KBtot = R.Mpad / KB;           // blocks in the packed layout
-            const float* cf = R.cf;
             uint8_t* zpack = R.zpack;
             GpStatus* st = R.st;
             double macc = 0.0, vacc = 0.0;
@@ -213,8 +215,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         float v[8];
                         gen8<P>(win, map + g * 8 * p, p, t, v);
                         if (last) {
-                            const float4 ca = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8));
-                            const float4 cb = __ldg(reinterpret_cast<const float4*>(cf + c * BK + g * 8 + 4));
+                            const float4* cs = reinterpret_cast<const float4*>(sb + CFO) + 2 * g;
+                            const float4 ca = cs[0], cb = cs[1];
                             mpart = fmaf(v[0], ca.x, mpart);
                             mpart = fmaf(v[1], ca.y, mpart);
                             mpart = fmaf(v[2], ca.z, mpart);
@@ -385,11 +387,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int* cinfo = R.cinfo;
             const uint8_t* Wpack = R.Wpack;
             const float* tab = R.tab;
+            const float* cfg = R.cf;
             const int64_t Npad = R.Npad;
+            const int nsuper = (nblocks + SUPER - 1) / SUPER;
             for (int sup = isup; sup <= isup && ok; ++sup) {
                 const int b0 = sup * SUPER;
                 const int nblk = min(SUPER, nblocks - b0);
                 const int nch = super_chunks(M, b0, nblk);
+                const bool last = (sup == nsuper - 1);  // its chunks also form the mean
                 for (int c = 0; c < nch; ++c, ++gc) {
                     const int stg = gc % STAGES;
                     const int* ci = cinfo + (int64_t)c * cstride;
@@ -410,9 +415,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     __syncwarp();
                     const uint32_t wbytes = (uint32_t)nblk * 2 * WB_BYTES;
                     if (lane == 0)
-                        mbar_arrive_expect_tx(&wfull[stg],
-                                              wbytes + (uint32_t)nrows * TT * 4 + (uint32_t)crp4 * 4);
+                        mbar_arrive_expect_tx(&wfull[stg], wbytes + (uint32_t)nrows * TT * 4 + (uint32_t)crp4 * 4 +
+                                                               (last ? (uint32_t)BK * 4 : 0u));
                     __syncwarp();
+                    if (last && lane == 2) bulk_g2s(sb + CFO, cfg + (size_t)c * BK, (uint32_t)BK * 4, &wfull[stg]);
                     if (lane == 0)
                         bulk_g2s(sb + 2 * A_BYTES, Wpack + ((size_t)c * KBtot + b0) * 2 * WB_BYTES, wbytes,
                                  &wfull[stg]);
