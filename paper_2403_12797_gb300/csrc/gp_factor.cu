@@ -132,17 +132,54 @@ constexpr int TRINV_BAR_OFFSET = 64;
 constexpr int SOLVE_BAR_OFFSET = 128;
 constexpr int CHOL_RSD_OFFSET = 256;
 
+// T = double: the block as it is. T = float (the mixed fit): the block
+// equilibrated by powers of two, C = S A_kk S with S = diag(2^-h_i) and h_i =
+// floor(log2(a_ii) / 2), so that 1 <= c_ii < 4 and |c_im| < 4 (A_kk is
+// positive definite), which float32 holds whatever the range of A (the noise
+// diagonal reaches 1e200). Then L_kk = S^-1 L_C.
+template <typename T>
 struct PotrfSmem {
-    double a[CB][CB + 1];                  // the block: lower part updated in place
-    double l[2][CB];                       // multipliers a_ij / d_j of the last two pivots
-    double pu[2][CB];                      // a_ij a_{j+1,j} of the last two pivots
-    double r[2];                           // 1 / d_j of the last two pivots
-    double d[CB];                          // pivots d_j
+    T a[CB][CB + 1];                       // the block: lower part updated in place
+    T l[2][CB];                            // multipliers a_ij / d_j of the last two pivots
+    T pu[2][CB];                           // a_ij a_{j+1,j} of the last two pivots
+    T r[2];                                // 1 / d_j of the last two pivots
+    T d[CB];                               // pivots d_j
     double s[CB];                          // sqrt(d_j)
     double rs[CB];                         // 1 / sqrt(d_j)
+    int h[CB];                             // T = float: the row scales' exponents h_i
     unsigned short tri[CB * (CB + 1) / 2]; // lower entries (i << 8 | m), columns in decreasing order
     int bad;
 };
+
+// 2^k as a double, for -1022 <= k <= 1023 (built from its bits).
+__device__ __forceinline__ double pow2d(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+// 1 / x in float32 for a positive normal x below 2^126: the rcp.approx.f32
+// estimate (relative error below 2^-22) refined by one Newton-Raphson step,
+// r <- r + r (1 - x r), to within about an ulp.
+__device__ __forceinline__ float rcp_newton_f32(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
+// The pivot check on the bits of a float64 or float32 pivot: a positive
+// normal number whose reciprocal is normal too ([2^-1022, 2^1021) or
+// [2^-126, 2^126)); zero, negative, NaN and infinity fail.
+__device__ __forceinline__ bool pivot_ok(double v) {
+    const int hi = __double2hiint(v);
+    return hi >= 0x00100000 && hi < 0x7FD00000;
+}
+__device__ __forceinline__ bool pivot_ok(float v) {
+    const int b = __float_as_int(v);
+    return b >= 0x00800000 && b < 0x7E800000;
+}
+__device__ __forceinline__ double pivot_rcp(double v) { return fast_rcp(v); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float pivot_rcp(float v) { return rcp_newton_f32(v); }
+__device__ __forceinline__ double quiet_nan(double*) { return __longlong_as_double(0x7FF8000000000000ll); }
+__device__ __forceinline__ float quiet_nan(float*) { return __int_as_float(0x7FC00000); }
 
 // Named barriers of the pivot loop, each a pair used alternately (pivot j
 // takes id + (j & 1)), so an arrival for pivot j + 1 never lands on a barrier
@@ -162,7 +199,11 @@ constexpr int POTRF_PAIR_N = 64;                 // chain + helper
 constexpr int POTRF_FOLLOW_N = 32 + POTRF_FOLLOW; // (helper or chain) + followers
 
 // Factor the w x w diagonal block at (kb, kb) in place (one CTA, w <= 32),
-// right-looking L D L^T in shared memory. Every float64 warp instruction
+// right-looking L D L^T in shared memory, in float64 (T = double) or, for
+// the mixed fit, in float32 on the equilibrated block (T = float): a float64
+// pivot chain costs ~735 clocks a pivot, and the mixed fit already rounds
+// its trailing-update products to float32 (errors of the same order) and
+// refines c in float64. Every float64 warp instruction
 // holds its scheduler's float64 pipe for 64 cycles, so the pivot chain gets a
 // scheduler to itself and as few of them as possible: warp 0 (lane i = row i,
 // the current pivot column in a register) broadcasts d_j, forms 1 / d_j
@@ -176,14 +217,29 @@ constexpr int POTRF_FOLLOW_N = 32 + POTRF_FOLLOW; // (helper or chain) + followe
 // it reads the next column. Control flow does not depend on the data: a
 // pivot outside [2^-1022, 2^1021) (zero, negative, NaN, beyond any value a
 // Gram matrix plus the clamped noise diagonal reaches) is checked on its
-// high word, recorded as GP_ENOTPD and replaced by NaN. At the end
-// L_jj = sqrt(d_j), L_ij = a_ij / sqrt(d_j) and rsd[kb + j] = 1 / L_jj.
+// high word, recorded as GP_ENOTPD and replaced by NaN (a mixed fit then
+// redoes its Gram and factorisation in float64). At the end L_jj =
+// 2^h_j sqrt(d_j), L_ij = 2^h_i a_ij / sqrt(d_j) and rsd[kb + j] = 1 / L_jj
+// (h = 0 for T = double).
+template <typename T>
 __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb, int w, GpStatus* st,
-                                           double* __restrict__ rsd, PotrfSmem& sm) {
+                                           double* __restrict__ rsd, PotrfSmem<T>& sm) {
+    constexpr bool EQ = sizeof(T) == 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (EQ) {
+        if (tid < CB) {  // h_i = floor(E_i / 2), a_ii in [2^E_i, 2^(E_i + 1)); 0 if a_ii is not positive normal
+            const double dii = tid < w ? L[(int64_t)(kb + tid) * M + kb + tid] : 1.0;
+            const int hi = __double2hiint(dii);
+            const bool pn = hi >= 0x00100000 && hi < 0x7FF00000;
+            sm.h[tid] = pn ? ((((hi >> 20) & 0x7ff) - 1023) >> 1) : 0;
+        }
+        __syncthreads();
+    }
     for (int e = tid; e < CB * CB; e += NT) {
         const int i = e / CB, m = e % CB;
-        sm.a[i][m] = (i < w && m <= i) ? L[(int64_t)(kb + i) * M + kb + m] : 0.0;
+        double v = (i < w && m <= i) ? L[(int64_t)(kb + i) * M + kb + m] : 0.0;
+        if (EQ) v *= pow2d(-(sm.h[i] + sm.h[m]));  // exact: a power of two, |h_i + h_m| <= 1022
+        sm.a[i][m] = (T)v;
     }
     if (tid < w) {  // column m's entries start after those of the columns > m
         const int m = tid;
@@ -194,15 +250,14 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     __syncthreads();
     if (warp == 0) {
         // ---- the pivot chain
-        double col = sm.a[lane][0];
+        T col = sm.a[lane][0];
         for (int j = 0; j < w; ++j) {
             sm.a[lane][j] = col;  // column j is final (every pivot < j applied)
             __syncwarp();
             named_bar_arrive(POTRF_BAR_COL + (j & 1), POTRF_PAIR_N);
-            const double piv = __shfl_sync(0xffffffffu, col, j);
-            const int hi = __double2hiint(piv);
-            const bool ok = hi >= 0x00100000 && hi < 0x7FD00000;
-            const double r = ok ? fast_rcp(piv) : __longlong_as_double(0x7FF8000000000000ll);
+            const T piv = __shfl_sync(0xffffffffu, col, j);
+            const bool ok = pivot_ok(piv);
+            const T r = ok ? pivot_rcp(piv) : quiet_nan((T*)nullptr);
             if (lane == 0) {
                 sm.r[j & 1] = r;
                 sm.d[j] = piv;
@@ -217,7 +272,7 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
                 named_bar_sync(POTRF_BAR_PU + (j & 1), POTRF_PAIR_N);
                 // the followers have applied pivot j - 1 to the columns >= j + 1
                 if (j >= 1) named_bar_sync(POTRF_BAR_DONE + ((j - 1) & 1), POTRF_FOLLOW_N);
-                col = fma(-sm.pu[j & 1][lane], r, sm.a[lane][j + 1]);
+                col = fmaT(-sm.pu[j & 1][lane], r, sm.a[lane][j + 1]);
             }
         }
         for (int q = (w > 2 ? w - 2 : 0); q < w; ++q) named_bar_sync(POTRF_BAR_DONE + (q & 1), POTRF_FOLLOW_N);
@@ -225,15 +280,15 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
         // ---- the helper: a_ij a_{j+1,j} for the chain, then the multipliers
         for (int j = 0; j < w; ++j) {
             named_bar_sync(POTRF_BAR_COL + (j & 1), POTRF_PAIR_N);
-            const double cj = sm.a[lane][j];
+            const T cj = sm.a[lane][j];
             const bool below = lane > j && lane < w;
             if (j + 1 < w) {
-                sm.pu[j & 1][lane] = below ? cj * sm.a[j + 1][j] : 0.0;
+                sm.pu[j & 1][lane] = below ? cj * sm.a[j + 1][j] : (T)0;
                 __syncwarp();
                 named_bar_arrive(POTRF_BAR_PU + (j & 1), POTRF_PAIR_N);
             }
             named_bar_sync(POTRF_BAR_R + (j & 1), POTRF_PAIR_N);
-            sm.l[j & 1][lane] = below ? cj * sm.r[j & 1] : 0.0;
+            sm.l[j & 1][lane] = below ? cj * sm.r[j & 1] : (T)0;
             __syncwarp();
             named_bar_arrive(POTRF_BAR_PUB + (j & 1), POTRF_FOLLOW_N);
         }
@@ -241,13 +296,13 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
         const int ft = (warp < 4 ? warp - 2 : warp - 3) * 32 + lane;
         for (int j = 0; j < w; ++j) {
             named_bar_sync(POTRF_BAR_PUB + (j & 1), POTRF_FOLLOW_N);
-            const int T = w - j - 2;
-            const int cnt = T > 0 ? T * (T + 1) / 2 : 0;  // entries of the columns m >= j + 2
-            const double* lj = sm.l[j & 1];
+            const int nc = w - j - 2;
+            const int cnt = nc > 0 ? nc * (nc + 1) / 2 : 0;  // entries of the columns m >= j + 2
+            const T* lj = sm.l[j & 1];
             for (int e = ft; e < cnt; e += POTRF_FOLLOW) {
                 const unsigned v = sm.tri[e];
                 const int i = (int)(v >> 8), m = (int)(v & 255u);
-                sm.a[i][m] = fma(-lj[i], sm.a[m][j], sm.a[i][m]);
+                sm.a[i][m] = fmaT(-lj[i], sm.a[m][j], sm.a[i][m]);
             }
             named_bar_arrive(POTRF_BAR_DONE + (j & 1), POTRF_FOLLOW_N);
         }
@@ -255,16 +310,20 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     __syncthreads();
     if (sm.bad) return false;  // uniform: read after the barrier
     if (tid < w) {
-        const double sq = sqrt(sm.d[tid]);
+        const double sq = sqrt((double)sm.d[tid]);
         const double rs = 1.0 / sq;
-        sm.s[tid] = sq;
+        sm.s[tid] = EQ ? sq * pow2d(sm.h[tid]) : sq;
         sm.rs[tid] = rs;
-        rsd[kb + tid] = rs;
+        rsd[kb + tid] = EQ ? rs * pow2d(-sm.h[tid]) : rs;
     }
     __syncthreads();
     for (int e = tid; e < CB * CB; e += NT) {
         const int i = e / CB, m = e % CB;
-        if (i < w && m <= i) L[(int64_t)(kb + i) * M + kb + m] = (i == m) ? sm.s[m] : sm.a[i][m] * sm.rs[m];
+        if (i < w && m <= i) {
+            double v = (i == m) ? sm.s[m] : (double)sm.a[i][m] * sm.rs[m];
+            if (EQ && i != m) v *= pow2d(sm.h[i]);
+            L[(int64_t)(kb + i) * M + kb + m] = v;
+        }
     }
     __syncthreads();
     return true;
@@ -410,7 +469,7 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
     constexpr int TBYTES = F32 ? 2 * UF * (CB + 1) * 4 : 2 * UT * (CB + 1) * 8;
     __shared__ __align__(16) unsigned char tbuf[TBYTES];
     __shared__ double rdiag[CB];
-    __shared__ PotrfSmem sm;
+    __shared__ PotrfSmem<typename std::conditional<F32, float, double>::type> sm;
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = (M + CB - 1) / CB;
