@@ -248,7 +248,62 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     }
     if (tid == 0) sm.bad = 0;
     __syncthreads();
-    if (warp == 0) {
+    if (EQ) {
+        // float32: the chain forms the multipliers itself (a float multiply
+        // costs it a few clocks, not a float64 pipe slot), so there is no
+        // helper; warps 1-7 apply pivot j to the columns >= j + 2, every
+        // thread its fixed entries of the packed table (indexes in registers)
+        constexpr int NF = NT - 32;
+        static_assert(3 * NF >= (CB - 2) * (CB - 1) / 2, "three table entries per follower thread");
+        if (warp == 0) {
+            T col = sm.a[lane][0];
+            for (int j = 0; j < w; ++j) {
+                sm.a[lane][j] = col;  // column j is final (every pivot < j applied)
+                const T piv = __shfl_sync(0xffffffffu, col, j);
+                const T a1 = __shfl_sync(0xffffffffu, col, (j + 1) & 31);  // a_{j+1,j}
+                const bool ok = pivot_ok(piv);
+                const T r = ok ? pivot_rcp(piv) : quiet_nan((T*)nullptr);
+                const T l = (lane > j && lane < w) ? col * r : (T)0;
+                sm.l[j & 1][lane] = l;
+                if (lane == 0) {
+                    sm.d[j] = piv;
+                    if (!ok) {
+                        sm.bad = 1;
+                        gp_set_status(st, GP_ENOTPD, kb + j);
+                    }
+                }
+                __syncwarp();
+                named_bar_arrive(POTRF_BAR_PUB + (j & 1), NT);
+                if (j + 1 < w) {
+                    // the followers have applied pivot j - 1 to the columns >= j + 1
+                    if (j >= 1) named_bar_sync(POTRF_BAR_DONE + ((j - 1) & 1), NT);
+                    col = fmaT(-l, a1, sm.a[lane][j + 1]);
+                }
+            }
+            for (int q = (w > 2 ? w - 2 : 0); q < w; ++q) named_bar_sync(POTRF_BAR_DONE + (q & 1), NT);
+        } else {
+            const int ft = tid - 32;
+            const int ntri = w * (w + 1) / 2;
+            int ei[3], em[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int e = ft + k * NF;
+                const unsigned v = e < ntri ? sm.tri[e] : 0u;
+                ei[k] = (int)(v >> 8);
+                em[k] = (int)(v & 255u);
+            }
+            for (int j = 0; j < w; ++j) {
+                named_bar_sync(POTRF_BAR_PUB + (j & 1), NT);
+                const int nc = w - j - 2;
+                const int cnt = nc > 0 ? nc * (nc + 1) / 2 : 0;  // entries of the columns m >= j + 2
+                const T* lj = sm.l[j & 1];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (ft + k * NF < cnt) sm.a[ei[k]][em[k]] = fmaT(-lj[ei[k]], sm.a[em[k]][j], sm.a[ei[k]][em[k]]);
+                named_bar_arrive(POTRF_BAR_DONE + (j & 1), NT);
+            }
+        }
+    } else if (warp == 0) {
         // ---- the pivot chain
         T col = sm.a[lane][0];
         for (int j = 0; j < w; ++j) {
