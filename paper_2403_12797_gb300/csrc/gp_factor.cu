@@ -154,6 +154,42 @@ struct PotrfSmem {
 // 2^k as a double, for -1022 <= k <= 1023 (built from its bits).
 __device__ __forceinline__ double pow2d(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
+// Conversions between float64 and float32 with a power-of-two scale, in
+// integer operations on the IEEE-754 fields (a float64 conversion or
+// multiply holds its scheduler's float64 pipe for 64 clocks on GB300).
+// f32_of_f64_pow2: v * 2^k rounded to nearest, ties to even, for |k| <= 1022;
+// results below 2^-126 become a signed zero, above the float range or from
+// an infinity or NaN an infinity (the pivot check rejects it).
+__device__ __forceinline__ float f32_of_f64_pow2(double v, int k) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned sign = hi & 0x80000000u;
+    const int ed = (int)((hi >> 20) & 0x7ffu);
+    int e = ed - 1023 + 127 + k;                                // biased float32 exponent
+    unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);         // the leading 23 fraction bits
+    const unsigned rest = lo & 0x1FFFFFFFu;                    // the 29 bits below them
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));
+    m += up ? 1u : 0u;
+    if (m == 0x800000u) {                                      // rounding carried into the exponent
+        m = 0u;
+        ++e;
+    }
+    if (ed == 0 || e <= 0) return __uint_as_float(sign);
+    if (ed == 0x7ff || e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | m);
+}
+
+// f64_of_f32_pow2: f * 2^k exactly, for |k| <= 511 (zero and float32
+// subnormals give a signed zero; an infinity or NaN stays one).
+__device__ __forceinline__ double f64_of_f32_pow2(float f, int k) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const int ef = (int)((b >> 23) & 0xffu);
+    if (ef == 0) return __hiloint2double((int)sign, 0);
+    const unsigned ex = ef == 0xff ? 0x7ffu : (unsigned)(ef - 127 + 1023 + k);
+    const unsigned hi = sign | (ex << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // 1 / x in float32 for a positive normal x below 2^126: the rcp.approx.f32
 // estimate (relative error below 2^-22) refined by one Newton-Raphson step,
 // r <- r + r (1 - x r), to within about an ulp.
@@ -226,6 +262,13 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
                                            double* __restrict__ rsd, PotrfSmem<T>& sm) {
     constexpr bool EQ = sizeof(T) == 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NQ = CB * CB / NT;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {  // every load in flight before the first use
+        const int e = tid + q * NT, i = e / CB, m = e % CB;
+        v[q] = (i < w && m <= i) ? L[(int64_t)(kb + i) * M + kb + m] : 0.0;
+    }
     if (EQ) {
         if (tid < CB) {  // h_i = floor(E_i / 2), a_ii in [2^E_i, 2^(E_i + 1)); 0 if a_ii is not positive normal
             const double dii = tid < w ? L[(int64_t)(kb + tid) * M + kb + tid] : 1.0;
@@ -235,11 +278,13 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
         }
         __syncthreads();
     }
-    for (int e = tid; e < CB * CB; e += NT) {
-        const int i = e / CB, m = e % CB;
-        double v = (i < w && m <= i) ? L[(int64_t)(kb + i) * M + kb + m] : 0.0;
-        if (EQ) v *= pow2d(-(sm.h[i] + sm.h[m]));  // exact: a power of two, |h_i + h_m| <= 1022
-        sm.a[i][m] = (T)v;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int e = tid + q * NT, i = e / CB, m = e % CB;
+        if (EQ)
+            sm.a[i][m] = (T)f32_of_f64_pow2(v[q], -(sm.h[i] + sm.h[m]));  // |h_i + h_m| <= 1022
+        else
+            sm.a[i][m] = (T)v[q];
     }
     if (tid < w) {  // column m's entries start after those of the columns > m
         const int m = tid;
@@ -365,19 +410,30 @@ __device__ __forceinline__ bool chol_potrf(double* __restrict__ L, int M, int kb
     __syncthreads();
     if (sm.bad) return false;  // uniform: read after the barrier
     if (tid < w) {
-        const double sq = sqrt((double)sm.d[tid]);
-        const double rs = 1.0 / sq;
-        sm.s[tid] = EQ ? sq * pow2d(sm.h[tid]) : sq;
-        sm.rs[tid] = rs;
-        rsd[kb + tid] = EQ ? rs * pow2d(-sm.h[tid]) : rs;
+        if (EQ) {  // float32 square root and reciprocal; d_j is a positive normal float here
+            const float sq = sqrtf((float)sm.d[tid]);
+            const float rs = rcp_newton_f32(sq);
+            sm.s[tid] = f64_of_f32_pow2(sq, sm.h[tid]);
+            sm.d[tid] = (T)rs;  // d_j is not needed any more: 1 / sqrt(d_j) for the products below
+            rsd[kb + tid] = f64_of_f32_pow2(rs, -sm.h[tid]);
+        } else {
+            const double sq = sqrt((double)sm.d[tid]);
+            const double rs = 1.0 / sq;
+            sm.s[tid] = sq;
+            sm.rs[tid] = rs;
+            rsd[kb + tid] = rs;
+        }
     }
     __syncthreads();
     for (int e = tid; e < CB * CB; e += NT) {
         const int i = e / CB, m = e % CB;
         if (i < w && m <= i) {
-            double v = (i == m) ? sm.s[m] : (double)sm.a[i][m] * sm.rs[m];
-            if (EQ && i != m) v *= pow2d(sm.h[i]);
-            L[(int64_t)(kb + i) * M + kb + m] = v;
+            double o;
+            if (EQ)
+                o = (i == m) ? sm.s[m] : f64_of_f32_pow2((float)(sm.a[i][m] * sm.d[m]), sm.h[i]);
+            else
+                o = (i == m) ? sm.s[m] : (double)sm.a[i][m] * sm.rs[m];
+            L[(int64_t)(kb + i) * M + kb + m] = o;
         }
     }
     __syncthreads();
@@ -517,7 +573,7 @@ __device__ __forceinline__ void chol_next_diag(double* __restrict__ L, int M, in
 // failure detection only: that CTA leaves before its first barrier arrival,
 // so the others' bounded waits run out and report GP_ETIMEOUT.
 template <bool F32>
-__global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
+__global__ void __launch_bounds__(NT, 1) chol_coop_kernel(double* __restrict__ L, int M, GpStatus* st,
                                                        CholWork* cw, uint64_t wait_ns, int skip_cta) {
     __shared__ double a[CB][CB + 1];
     // the update tiles' panel rows: 16-row float64 tiles, or 64-row float32 (F32)
@@ -545,7 +601,12 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
         // L_kk in registers, and each step is one shuffle and one FMA. The rows
         // L_jl s_j are scaled once per CTA as they are loaded (a float64
         // instruction holds its scheduler's float64 pipe for 64 cycles, so
-        // forming them in every warp cost more than the solves).
+        // forming them in every warp cost more than the solves). A mixed fit
+        // (F32) solves in float32, each row scaled by 2^-h_i with h_i =
+        // floor(log2(a_ii) / 2) of its current diagonal: the row's squared
+        // entries sum to less than a_ii, so the scaled x lie below 2 and the
+        // scaled L_kk rows are those of the equilibrated block, which
+        // float32 holds whatever the noise diagonal's range.
         if ((int)blockIdx.x < rest) {
             double v[CB * CB / NT], sv[CB * CB / NT];
 #pragma unroll
@@ -554,30 +615,44 @@ __global__ void __launch_bounds__(NT) chol_coop_kernel(double* __restrict__ L, i
                 v[q] = (i < w && j <= i) ? L[(int64_t)(kb + i) * M + kb + j] : 0.0;
                 sv[q] = i < w ? rsd[kb + i] : 0.0;
             }
+            // F32: the scaled rows in float32, converted once per CTA (in the
+            // first half of a's storage)
+            float(*af)[CB + 1] = reinterpret_cast<float(*)[CB + 1]>(a);
 #pragma unroll
             for (int q = 0; q < CB * CB / NT; ++q) {
                 const int e = tid + q * NT;
-                a[e / CB][e % CB] = v[q] * sv[q];
+                if (F32)
+                    af[e / CB][e % CB] = f32_of_f64_pow2(v[q] * sv[q], 0);
+                else
+                    a[e / CB][e % CB] = v[q] * sv[q];
             }
             if (tid < CB) rdiag[tid] = tid < w ? rsd[kb + tid] : 0.0;
             __syncthreads();
             const double rd = rdiag[lane];
-            double ls[CB];
+            using TS = typename std::conditional<F32, float, double>::type;
+            TS ls[CB];
             if ((int)blockIdx.x + G * warp < rest) {
 #pragma unroll
-                for (int l = 0; l < CB; ++l) ls[l] = a[lane][l];
+                for (int l = 0; l < CB; ++l) ls[l] = F32 ? (TS)af[lane][l] : (TS)a[lane][l];
             }
             for (int rr = blockIdx.x + G * warp; rr < rest; rr += G * (NT / 32)) {
-                double* row = L + (int64_t)(kb + w + rr) * M + kb;
-                double acc = lane < w ? row[lane] * rd : 0.0;
+                const int gi = kb + w + rr;
+                double* row = L + (int64_t)gi * M + kb;
+                int h = 0;
+                if (F32) {
+                    const int dhi = __double2hiint(L[(int64_t)gi * M + gi]);
+                    if (dhi >= 0x00100000 && dhi < 0x7FF00000) h = (((dhi >> 20) & 0x7ff) - 1023) >> 1;
+                }
+                TS acc = (TS)0;
+                if (lane < w) acc = F32 ? (TS)f32_of_f64_pow2(row[lane] * rd, -h) : (TS)(row[lane] * rd);
 #pragma unroll
                 for (int l = 0; l < CB; ++l) {
                     if (l < w) {
-                        const double xl = __shfl_sync(0xffffffffu, acc, l);
-                        if (lane > l) acc = fma(-xl, ls[l], acc);
+                        const TS xl = __shfl_sync(0xffffffffu, acc, l);
+                        if (lane > l) acc = fmaT(-xl, ls[l], acc);
                     }
                 }
-                if (lane < w) row[lane] = acc;
+                if (lane < w) row[lane] = F32 ? f64_of_f32_pow2((float)acc, h) : (double)acc;
             }
             __syncthreads();
         }
