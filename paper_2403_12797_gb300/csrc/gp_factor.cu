@@ -10,14 +10,17 @@
 // separated by grid barriers whose waits are bounded (GP_ETIMEOUT after
 // GP_WAIT_NS; nothing can hang):
 //
-//   Cholesky (float64, right-looking, 32-column panels, look-ahead; a mixed
-//   fit forms the trailing-update products in float32), per step k:
+//   Cholesky (right-looking, 32-column panels, look-ahead; float64, or for a
+//   mixed fit float32 pivots and panel solves on power-of-two equilibrated
+//   blocks and rows, and float32 trailing-update products subtracted from the
+//   float64 trailing matrix), per step k:
 //     B  one warp per row below the factored diagonal block solves
 //        x L_kk^T = a (lane j owns x_j);
 //     C  16 helper CTAs update the next diagonal block and count themselves
 //        done; CTA 0 waits for them and factors that block (32 x 32, in
 //        shared memory) while the other CTAs update the rest of the trailing
-//        lower triangle in 16 x 16 tiles (subtracting L_ik L_jk^T).
+//        lower triangle in tiles (16 x 16, or 64 x 64 with float32 products),
+//        subtracting L_ik L_jk^T.
 //   A non-positive or NaN pivot sets GP_ENOTPD (detail = column); every CTA
 //   sees it after the next barrier and returns.
 //
