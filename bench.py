@@ -2,8 +2,9 @@
 """Benchmark of the decomposed-kernel GP hot path on GB300.
 
 One step = one full fit (eigenfunction tables, fused Phi generation + Gram
-on the tensor cores, split reduction and assembly of A, float64 Cholesky,
-inverse, solve + refinement, operand packing) followed by one full predict
+on the tensor cores, split reduction and assembly of A, Cholesky (float32
+pivots, panels and update products on a float64 trailing matrix), inverse,
+solve + float64 refinement, operand packing) followed by one full predict
 (mean and variance) of the largest single-GPU workload: p=3, n=16 (M=4096),
 N=2,000,000 training points x ~ N(0, 0.5^2 I_3), 200,000 test points. Inputs
 are resident in device memory when the timed region starts; L2 is flushed
@@ -353,7 +354,8 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": ("f16 tensor (integer + remainder slices, f32 acc in exact 4096-row blocks) "
-                     "+ f64 factorisation") if prec != "fp64" else "f64",
+                     "+ f32 pivots, panels and update products on an f64 trailing matrix, "
+                     "f64 refinement") if prec != "fp64" else "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD2 if main_w2 else WORKLOAD, "prec": prec,
                       "l2": "flushed between steps (256 MiB write); inputs and tables exceed L2",

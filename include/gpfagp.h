@@ -68,18 +68,26 @@ typedef struct gp_model gp_model;
 /* ---- precision modes ---------------------------------------------------- */
 /* GP_PREC_FP64:  every step in float64 on the CUDA cores.
  * GP_PREC_MIXED: Phi generated in float32; the contractions run on the
- *                tensor cores with bf16 operands:
- *                - Phi^T Phi: each column is scaled by a power of two so that
- *                  |w| <= 128 and split into the integer s1 = rint(w) (exact
- *                  in fp16) and lo = fp16(w - s1); s1*s1' is summed EXACTLY
- *                  in float32 TMEM over 1024-row blocks, s1*lo' + lo*s1' +
- *                  lo*lo' beside it; blocks are folded into float pairs
- *                  hi + lo by an exact two-sum (no truncation drift);
+ *                tensor cores with 16-bit operands:
+ *                - Phi^T Phi: within each row block (1024 rows, or 4096 on
+ *                  CTA pairs) every column is scaled by the power of two
+ *                  that its exact block maximum sets, so that |w| < 64, and
+ *                  split into the integer s1 = rint(w) (exact in fp16) and
+ *                  lo = fp16(w - s1); s1*s1' is summed EXACTLY in float32
+ *                  TMEM over the block, s1*lo' + lo*s1' + lo*lo' beside it;
+ *                  the block sums are rescaled exactly and folded into float
+ *                  pairs hi + lo by an exact two-sum (no truncation drift);
  *                - Phi_* L^{-T} (variance): bf16 hi/lo split of both
  *                  operands, hi*hi + hi*lo + lo*hi in float32;
  *                Phi^T y and the predictive mean use float32 products;
- *                split-N partials are summed, A assembled, factored and
- *                inverted, and c solved and refined, in float64.           */
+ *                split-N partials are summed and A assembled in float64;
+ *                the Cholesky keeps its trailing matrix in float64 and
+ *                takes its pivots and panel solves (on power-of-two
+ *                equilibrated blocks and rows) and its update products in
+ *                float32; W = L^{-1} is float32; c is solved through W and
+ *                refined against A in float64. A mixed fit whose float32
+ *                pivot is not a positive normal number redoes its Gram and
+ *                factorisation in float64.                                 */
 #define GP_PREC_FP64   0
 #define GP_PREC_MIXED  3
 
