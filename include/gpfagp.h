@@ -212,12 +212,13 @@ GPFAGP_API int gp_model_log_marginal_grad(const gp_model* h, const double* y, in
 GPFAGP_API int gp_model_info(const gp_model* h, int64_t* M, int* p, int* n, int* prec);
 
 /* Model flags: GP_MODEL_GRAM_FP64 when a mixed-precision fit recomputed its
- * Gram in float64. The mixed Gram keeps its 1024-row block sums exact and
- * folds the blocks into ~46-bit float pairs; when A = G + sigma^2 Lambda^{-1} is conditioned
- * beyond what that carries (large N with a small noise variance) the
- * float64 Cholesky meets a non-positive pivot, and the fit (gp_fit_ex,
- * gp_fit_batch, server refits) then redoes the Gram with the float64 kernel
- * and factors again instead of failing. */
+ * Gram in float64. The mixed Gram keeps its row-block sums exact and folds
+ * the blocks into ~46-bit float pairs; when A = G + sigma^2 Lambda^{-1} is
+ * conditioned beyond what that and the float32 pivots carry (large N with a
+ * small noise variance) the Cholesky meets a pivot that is not a positive
+ * normal number, and the fit (gp_fit_ex, gp_fit_batch, server refits) then
+ * redoes the Gram with the float64 kernel and factors again in float64
+ * instead of failing. */
 #define GP_MODEL_GRAM_FP64 1
 GPFAGP_API int gp_model_flags(const gp_model* h);
 
@@ -461,7 +462,7 @@ GPFAGP_API void gp_debug_force_escalation(int k);
  * the tests compare them with each other and with the FP64 oracle. */
 GPFAGP_API void gp_debug_gram_kernel(int kind);
 
-/* Failure-detection test hook: the float64 Cholesky's bounded grid-barrier
+/* Failure-detection test hook: the Cholesky's bounded grid-barrier
  * waits give up after limit_s seconds (limit_s <= 0 restores the 2 s
  * default), and in the next Cholesky launch the CTA with index skip_cta
  * (skip_cta < 0: none) returns before its first grid-barrier arrival, so
